@@ -1,0 +1,243 @@
+"""Python front end of the CPU FP64 oracle (``hm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: used by ``tests/``, the smoke check and the
+benchmark's CPU-baseline leg.  It never imports the CUDA package; inputs are
+plain numpy arrays or duck-typed objects with the attributes of the scene
+generator's ``Camera``/``Gaussians``/``Mesh``.
+
+All parameters are widened to float64 before the C code sees them (float32
+and float16 values widen exactly), so finite differences can perturb them in
+FP64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from types import SimpleNamespace
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+# relative margin under which a threshold decision is "ambiguous" between an
+# FP64 evaluation and an FP32 one (see the tolerance derivation in the design notes)
+DEFAULT_EPS = 2e-4
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.or_sort_order.restype = ctypes.c_int
+        _lib.or_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _d(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def cam_array(cam) -> np.ndarray:
+    """16 doubles: R (row-major), t, fx, fy, cx, cy."""
+    if hasattr(cam, "as_array"):
+        return _d(cam.as_array())
+    return _d(np.concatenate([np.asarray(cam.R).reshape(9), np.asarray(cam.t).reshape(3),
+                              [cam.fx, cam.fy, cam.cx, cam.cy]]))
+
+
+def _pix(pix, W, H):
+    if pix is None:
+        return None, W * H
+    pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+    return pix, len(pix)
+
+
+# --------------------------------------------------------------------------
+# mesh
+# --------------------------------------------------------------------------
+
+def texture_unit(tex) -> np.ndarray:
+    """Texture as float64 in [0,1]: RGB8 / 255, float textures as given."""
+    t = np.asarray(tex)
+    if t.dtype == np.uint8:
+        return np.ascontiguousarray(t.astype(np.float64) / 255.0)
+    return _d(t)
+
+
+def mesh_raster(cam, mesh, bg=(0, 0, 0), znear=0.01, pix=None, tex=None):
+    W, H = int(cam.width), int(cam.height)
+    c = cam_array(cam)
+    verts, uvs = _d(mesh.verts), _d(mesh.uvs)
+    faces = np.ascontiguousarray(np.asarray(mesh.faces, dtype=np.int32))
+    tx = texture_unit(mesh.texture) if tex is None else _d(tex)
+    th, tw = tx.shape[:2]
+    pix, n = _pix(pix, W, H)
+    tri = np.empty(n, np.int32)
+    dep = np.empty(n, np.float32)
+    rgb = np.empty((3, n))
+    uv = np.empty((2, n))
+    bary = np.empty((3, n))
+    lib().or_mesh_raster(_p(c), W, H, _p(verts), _p(uvs), len(verts), _p(faces), len(faces),
+                         _p(tx), tw, th, _p(_d(bg)), ctypes.c_double(znear),
+                         _p(pix) if pix is not None else None, ctypes.c_int64(n),
+                         _p(tri), _p(dep), _p(rgb), _p(uv), _p(bary))
+    return SimpleNamespace(tri_id=tri, depth=dep, rgb=rgb, uv=uv, bary=bary)
+
+
+def empty_mesh_result(n, bg=(0, 0, 0)):
+    return SimpleNamespace(tri_id=np.full(n, -1, np.int32), depth=np.full(n, np.inf, np.float32),
+                           rgb=np.repeat(_d(bg)[:, None], n, 1), uv=np.zeros((2, n)),
+                           bary=np.zeros((3, n)))
+
+
+def mesh_raycast(cam, mesh, znear=0.01, pix=None):
+    W, H = int(cam.width), int(cam.height)
+    c = cam_array(cam)
+    verts = _d(mesh.verts)
+    faces = np.ascontiguousarray(np.asarray(mesh.faces, dtype=np.int32))
+    pix, n = _pix(pix, W, H)
+    tri = np.empty(n, np.int32)
+    tz = np.empty(n)
+    ed = np.empty(n)
+    lib().or_mesh_raycast(_p(c), W, H, _p(verts), _p(faces), len(faces), ctypes.c_double(znear),
+                          _p(pix) if pix is not None else None, ctypes.c_int64(n),
+                          _p(tri), _p(tz), _p(ed))
+    return SimpleNamespace(tri_id=tri, z=tz, edge_bary=ed)
+
+
+# --------------------------------------------------------------------------
+# Gaussians
+# --------------------------------------------------------------------------
+
+def sh_basis(deg: int, d) -> np.ndarray:
+    d = _d(d)
+    out = np.empty((deg + 1) ** 2)
+    lib().or_sh_basis(deg, _p(d), _p(out))
+    return out
+
+
+def project(cam, g, W=None, H=None):
+    W = int(cam.width) if W is None else W
+    H = int(cam.height) if H is None else H
+    n = int(np.asarray(g.means).shape[0])
+    c = cam_array(cam)
+    means, scales, quats = _d(g.means), _d(g.scales), _d(g.quats)
+    sh = _d(np.asarray(g.sh).astype(np.float64))
+    vis = np.empty(n, np.int32)
+    dep = np.empty(n, np.float32)
+    m2 = np.empty((n, 2))
+    cov = np.empty((n, 3))
+    con = np.empty((n, 3))
+    col = np.empty((n, 3))
+    clamped = np.empty((n, 3), np.int32)
+    lib().or_project(_p(c), W, H, n, _p(means), _p(scales), _p(quats), _p(sh), int(g.sh_degree),
+                     _p(vis), _p(dep), _p(m2), _p(cov), _p(con), _p(col), _p(clamped))
+    return SimpleNamespace(visible=vis, depth=dep, mean2d=m2, cov2d=cov, conic=con, color=col,
+                           clamped=clamped)
+
+
+def sort_order(proj) -> np.ndarray:
+    n = len(proj.visible)
+    order = np.empty(max(n, 1), np.int32)
+    m = lib().or_sort_order(n, _p(proj.visible), _p(proj.depth), _p(order))
+    return order[:m].copy()
+
+
+# --------------------------------------------------------------------------
+# blending
+# --------------------------------------------------------------------------
+
+def blend(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, pix=None, order=None):
+    W, H = int(cam.width), int(cam.height)
+    if order is None:
+        order = sort_order(proj)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    pix, n = _pix(pix, W, H)
+    rgb = np.empty((3, n))
+    T = np.empty(n)
+    nc = np.empty(n, np.int32)
+    na = np.empty(n, np.int32)
+    mg = np.empty(n)
+    ev = np.empty(n, np.int64)
+    fp = np.empty(n, np.uint64)
+    lib().or_blend(W, H, len(proj.visible), _p(order), len(order), _p(proj.depth),
+                   _p(_d(proj.mean2d)), _p(_d(proj.conic)), _p(_d(opacity)), _p(_d(proj.color)),
+                   _p(np.ascontiguousarray(mesh_res.tri_id, dtype=np.int32)),
+                   _p(np.ascontiguousarray(mesh_res.depth, dtype=np.float32)),
+                   _p(_d(mesh_res.rgb)), _p(_d(bg)), ctypes.c_double(eps),
+                   _p(pix) if pix is not None else None, ctypes.c_int64(n),
+                   _p(rgb), _p(T), _p(nc), _p(na), _p(mg), _p(ev), _p(fp))
+    return SimpleNamespace(rgb=rgb, T=T, n_contrib=nc, n_amb=na, margin=mg, evaluated=ev, fp=fp)
+
+
+def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, cell=16, rows=None,
+               order=None):
+    """Full-image blend with the exact cell prefilter; ``rows=(r0, r1)``
+    restricts the work to a band of rows (outputs elsewhere are undefined)."""
+    W, H = int(cam.width), int(cam.height)
+    if order is None:
+        order = sort_order(proj)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    r0, r1 = (0, H) if rows is None else rows
+    n = W * H
+    rgb = np.zeros((3, n))
+    T = np.zeros(n)
+    nc = np.zeros(n, np.int32)
+    na = np.zeros(n, np.int32)
+    mg = np.zeros(n)
+    ev = np.zeros(n, np.int64)
+    fp = np.zeros(n, np.uint64)
+    lib().or_blend_grid(W, H, cell, _p(order), len(order), _p(proj.depth), _p(_d(proj.mean2d)),
+                        _p(_d(proj.cov2d)), _p(_d(proj.conic)), _p(_d(opacity)), _p(_d(proj.color)),
+                        _p(np.ascontiguousarray(mesh_res.tri_id, dtype=np.int32)),
+                        _p(np.ascontiguousarray(mesh_res.depth, dtype=np.float32)),
+                        _p(_d(mesh_res.rgb)), _p(_d(bg)), ctypes.c_double(eps), int(r0), int(r1),
+                        _p(rgb), _p(T), _p(nc), _p(na), _p(mg), _p(ev), _p(fp))
+    return SimpleNamespace(rgb=rgb, T=T, n_contrib=nc, n_amb=na, margin=mg, evaluated=ev, fp=fp)
+
+
+def render(scene, view=0, pix=None, eps=DEFAULT_EPS, mode="brute", gaussians=None, tex=None,
+           rows=None, znear=0.01):
+    """Full hybrid render of one view: mesh pass, projection, blend.  Returns
+    a namespace with the mesh pass (``mesh``), the projection (``proj``) and
+    the blend (``out``)."""
+    cam = scene.cameras[view]
+    g = scene.gaussians if gaussians is None else gaussians
+    bg = np.asarray(scene.bg, np.float64)
+    W, H = int(cam.width), int(cam.height)
+    if mode == "grid":
+        pix = None
+    n = W * H if pix is None else len(pix)
+    if scene.mesh is not None:
+        mr = mesh_raster(cam, scene.mesh, bg=bg, znear=znear, pix=pix, tex=tex)
+    else:
+        mr = empty_mesh_result(n, bg)
+    pr = project(cam, g)
+    if mode == "grid":
+        out = blend_grid(cam, pr, g.opacity, mr, bg=bg, eps=eps, rows=rows)
+    else:
+        out = blend(cam, pr, g.opacity, mr, bg=bg, eps=eps, pix=pix)
+    return SimpleNamespace(mesh=mr, proj=pr, out=out)
