@@ -1,0 +1,450 @@
+"""Benchmark of the hybrid mesh-Gaussian renderer on B300.
+
+Workload (N=1): the seeded indoor-room scene at 1920x1080 -- 8 camera poses,
+300k Gaussians (SH degree 3), a 6x5x3 m room of ~50k triangles with 10%
+pruned in clusters, 2048^2 RGB8 atlas.  A step is one pass of the whole hot
+path over the 8 views: mesh rasterisation, projection, bin/sort, hybrid blend
+(forward) and the backward pass (blend, texture and projection gradients)
+for a fixed seeded upstream gradient dL/dI.  Metric: frames/s (views per
+second) and Mpixel/s, forward+backward; the forward-only rate is reported
+beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N>1) every rank renders its own 8 views of the scene (weak
+scaling; no collective on the data path) and rank 0 prints the line with the
+max-over-ranks time.  ``--impl reference`` times the CPU FP64 oracle (the
+correctness reference; there is no other implementation of this path) on the
+host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hybrid render frames/s & Mpixel/s at 1080p (fwd, fwd+bwd) and % of roofline"
+UNIT = "frames/s"
+WORKLOAD = ("indoor room 1920x1080 x 8 poses, 300k Gaussians SH3, 50k-triangle room mesh "
+            "(10% pruned), 2048^2 RGB8 atlas; forward + backward")
+# FP32 work per evaluated (pixel, Gaussian) pair in the blend: the quadratic
+# form (2 sub, 2 mul, 2 fma), alpha (mul, min, 2 compares), T update (fma,
+# compare), weight (mul), colour (3 fma), counting an FMA as 2 FLOPs
+FLOPS_PER_EVAL = 26
+FLOPS_PER_EVAL_BWD = 70
+KERNELS_PER_STEP = {"rasterize_mesh": 7, "project": 1, "bin_sort": 14, "blend_forward": 1,
+                    "texture_backward": 1, "blend_backward": 1, "project_backward": 1}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, local, dist
+
+
+def _max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    import torch
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ----------------------------------------------------------------------------
+
+def cpu_oracle_sample(scene, rows=8, crop=12):
+    """Time the CPU FP64 oracle on a bounded sample of one 1080p view: the
+    mesh pass and the blend over a band of `rows` full rows (exact grid
+    prefilter), the projection of all Gaussians, and the FP64 gradient
+    oracle (autograd) over a crop x crop pixel block.  Returns seconds per
+    full frame for forward and forward+backward."""
+    import torch
+    from oracle import oracle as O
+    from oracle import torch_ref as TR
+
+    cam = scene.cameras[0]
+    W, H = cam.width, cam.height
+    y0 = H // 2 - rows // 2
+    t0 = time.perf_counter()
+    pr = O.project(cam, scene.gaussians)
+    t_proj = time.perf_counter() - t0
+    pix = np.arange(y0 * W, (y0 + rows) * W, dtype=np.int64)
+    t0 = time.perf_counter()
+    mr = O.mesh_raster(cam, scene.mesh, bg=scene.bg, pix=pix)
+    t_mesh = time.perf_counter() - t0
+    full = O.empty_mesh_result(W * H, scene.bg)
+    full.tri_id[pix], full.depth[pix] = mr.tri_id, mr.depth
+    full.rgb[:, pix] = mr.rgb
+    t0 = time.perf_counter()
+    O.blend_grid(cam, pr, scene.gaussians.opacity, full, bg=scene.bg, rows=(y0, y0 + rows))
+    t_blend = time.perf_counter() - t0
+    fwd = t_proj + (t_mesh + t_blend) * (H / rows)
+    # backward over a crop x crop block centred in the view (single view scene)
+    cx0, cy0 = W // 2 - crop // 2, H // 2 - crop // 2
+    cpix = np.array([(cy0 + j) * W + cx0 + i for j in range(crop) for i in range(crop)], np.int64)
+    gI = np.random.default_rng(0).standard_normal((3, len(cpix)))
+    sub = type(scene)(scene.name, scene.seed, scene.gaussians, scene.mesh, [cam], scene.bg)
+    torch.set_num_threads(O.num_threads())
+    # per-frame part (projection through autograd) from a 1-pixel run, per-pixel
+    # part from the crop
+    t0 = time.perf_counter()
+    TR.render_grad(sub, 0, gI[:, :1], pix=cpix[:1], chunk=8)
+    t_fixed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    TR.render_grad(sub, 0, gI, pix=cpix, chunk=8)
+    t_bwd = time.perf_counter() - t0
+    bwd = t_fixed + max(t_bwd - t_fixed, 0.0) * (W * H) / len(cpix)
+    return fwd, fwd + bwd, {"rows": rows, "crop": crop, "t_proj": t_proj, "t_mesh": t_mesh,
+                            "t_blend": t_blend, "t_bwd_crop": t_bwd, "t_bwd_fixed": t_fixed}
+
+
+def run_reference(args):
+    rank, ws, _, dist = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2506_06988_b300 import scenes
+    scene = scenes.config1_scene()
+    steps, warm = args.steps, args.warmup
+    times = []
+    info = {}
+    for i in range(warm + steps):
+        fwd, fb, info = cpu_oracle_sample(scene, rows=4, crop=4)
+        if i >= warm:
+            times.append(fb)
+    sec_per_frame = float(np.mean(times))
+    value = 1.0 / sec_per_frame
+    mpx = value * 1920 * 1080 / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 8 * sec_per_frame * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "mpixel_per_s": mpx,
+            "config": {"workload": WORKLOAD, "views": 8, "width": 1920, "height": 1080, "gaussians": 300000,
+                       "sh_degree": 3},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "each step: oracle forward over 4 rows of one 1080p view "
+                                       "(+ full projection) and FP64 autograd backward over a 4x4 "
+                                       "block, scaled to a full frame"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# CUDA path
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2506_06988_b300 import lib, scenes
+    from paper_2506_06988_b300.render import HybridRender, MeshInput, Renderer
+
+    rank, world, local, dist = _dist()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lib.load()
+    scene = scenes.config1_scene()
+    scene.cameras = scene.cameras[:args.views]
+    g = scene.gaussians
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    V = len(scene.cameras)
+    r = Renderer(scene.cameras, g.n, g.sh_degree, n_verts=len(scene.mesh.verts),
+                 n_faces=len(scene.mesh.faces), tex_shape=scene.mesh.texture.shape, tile=tile,
+                 batch=args.batch, bg=tuple(scene.bg), device=dev)
+    P = {k: torch.as_tensor(getattr(g, k), device=dev).contiguous()
+         for k in ("means", "scales", "quats", "opacity", "sh")}
+    mesh = MeshInput.from_numpy(scene.mesh, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    dI = torch.randn(3 * r.npix, device=dev, generator=gen) * 1e-3
+    r.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh)   # settles capacities
+    grads = r.grad_buffers(scene.mesh.texture.shape[:2])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    PM = (P["means"], P["scales"], P["quats"], P["opacity"], P["sh"])
+    names = ["rasterize_mesh", "project", "bin_sort", "blend_forward", "zero_grads",
+             "texture_backward", "blend_backward", "project_backward"]
+
+    def step(ev=None):
+        def mark(j):
+            if ev is not None:
+                ev[j].record(stream)
+        mark(0)
+        r.status_word.zero_()
+        r.rasterize_mesh(mesh)
+        mark(1)
+        r.project(*PM)
+        mark(2)
+        r.bin_sort()
+        mark(3)
+        r.blend()
+        mark(4)
+        for v in grads.values():            # the caller zero-initialises gradients
+            v.zero_()
+        mark(5)
+        # the backward pass as its three kernels, each bracketed by events
+        for j, stg in ((6, lib.HM_BWD_TEXTURE), (7, lib.HM_BWD_BLEND), (8, lib.HM_BWD_PROJECT)):
+            r.backward(*PM, dI, None, mesh=mesh, tex_grad=True, out=grads, stages=stg, zero=False)
+            mark(j)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.fill_(1.0)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(args.steps)]
+    _barrier(dist)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            step(events[k])
+            flush.fill_(float(k))          # L2 flush between steps (outside the events)
+        _barrier(dist)
+    st, npairs, nitems = r.status()
+    if st:
+        raise RuntimeError(f"device status {st} during the timed region")
+    stage = np.array([[events[k][j].elapsed_time(events[k][j + 1]) for j in range(8)]
+                      for k in range(args.steps)])           # ms
+    step_ms_local = float(stage.sum(1).mean())
+    step_ms = _max_over_ranks(step_ms_local, dist)
+    fwd_ms = _max_over_ranks(float(stage[:, :4].sum(1).mean()), dist)
+    stage_ms = {n: float(stage[:, j].mean()) for j, n in enumerate(names)}
+
+    # algorithmic work of the blend (instrumented re-run, outside the timing)
+    n_blended = int(r.n_contrib.to(torch.int64).sum().item())
+    n_mesh_px = int(torch.isfinite(r.mesh_depth).sum().item())
+    n_eval, n_exam = r.count_evaluations()
+    peaks, peak_kind = _peaks()
+    clocks = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at the max clock
+    frames = V * world
+    value = frames * 1e3 / step_ms
+    mpx = value * 1920 * 1080 / 1e6
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    tsuf = f"<{tile[0]},{tile[1]}>"
+    N, M = g.n, V * g.n
+    K = (g.sh_degree + 1) ** 2
+    # per single-kernel stage: (kernel, bound, algorithmic units, work per unit)
+    kern = {
+        "blend_forward": ("blend_fwd_kernel" + tsuf, "alu", n_eval, FLOPS_PER_EVAL, "evaluated (pixel, Gaussian) pairs"),
+        "blend_backward": ("blend_bwd_kernel" + tsuf, "alu", n_blended, FLOPS_PER_EVAL_BWD, "replayed blended pairs"),
+        "project": ("project_kernel<3,false>", "hbm", N, 12 + 12 + 16 + 4 + 12 * K + V * 48, "Gaussians (params read + V records written, bytes)"),
+        "project_backward": ("project_bwd_kernel<3,false>", "hbm", N, 2 * (12 + 12 + 16 + 4 + 12 * K) + 12 + 12 + 16 + 4 + 12 * K + V * 36,
+                             "Gaussians (params read, grads read+written, V partial rows read, bytes)"),
+        "texture_backward": ("texture_bwd_kernel", "hbm", n_mesh_px, 4 + 4 + 8 + 12, "mesh pixels (depth, T, uv, dL/dI read, bytes)"),
+    }
+    per_kernel = {}
+    for st_name, (kname, bound, units, per, what) in kern.items():
+        t = stage_ms[st_name] * 1e-3
+        if bound == "alu":
+            ach = units * per / t / 1e12
+            per_kernel[st_name] = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                                   "unit": "TFLOP/s", "frac": ach / fp32_peak, "units": units,
+                                   "per_unit": per, "unit_kind": what, "ms": stage_ms[st_name]}
+        else:
+            ach = units * per / t / 1e9
+            per_kernel[st_name] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm,
+                                   "unit": "GB/s", "frac": ach / hbm, "units": units, "per_unit": per,
+                                   "unit_kind": what, "ms": stage_ms[st_name]}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    roof = dict(per_kernel[dom])
+    roof["traffic"] = None
+    roof["peak_source"] = (f"FP32: {nsm} SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (unit counts x max clock)"
+                           if roof["bound"] == "alu" else f"HBM copy bandwidth, {peak_kind}")
+    if roof["bound"] == "alu" and clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = roof["achieved"] / (nsm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    sort_bytes = M * (4 * 2 * 4 * 2 + 8) + npairs * (8 + 2 * 2 * 8 + 8)
+    stage_roof = {"bin_sort": {"bytes": sort_bytes, "GB/s": sort_bytes / (stage_ms["bin_sort"] * 1e-3) / 1e9}}
+    stage_roof["bin_sort"]["frac_of_hbm"] = stage_roof["bin_sort"]["GB/s"] / hbm
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, scene, r, mesh, dev, dist, V * world)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "mpixel_per_s": mpx,
+        "fwd": {"frames_per_s": frames * 1e3 / fwd_ms, "ms_per_step": fwd_ms,
+                "mpixel_per_s": frames * 1e3 / fwd_ms * 1920 * 1080 / 1e6},
+        "stage_ms": stage_ms,
+        "config": {"workload": WORKLOAD, "views": V, "width": 1920, "height": 1080, "gaussians": g.n,
+                   "sh_degree": g.sh_degree, "faces": len(scene.mesh.faces), "tile": list(tile),
+                   "batch": r.opt.batch, "pairs": npairs, "mesh_items": nitems,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "parallelism": f"views per rank, {world} rank(s)"},
+        "roofline": roof, "kernels": per_kernel, "stage_roofline_hbm": stage_roof,
+        "blend_units": {"evaluated_pairs": n_eval, "examined_pairs": n_exam, "blended_pairs": n_blended},
+        "peak_kind": peak_kind,
+        "clocks": clocks,
+        "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and rank == 0:
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        fwd_s, fb_s, info = cpu_oracle_sample(scene)
+        line["cpu_baseline"] = {"value": 1.0 / fb_s, "unit": UNIT, "cores": O.num_threads(),
+                                "kind": "oracle", "forward_frames_per_s": 1.0 / fwd_s,
+                                "sample": f"one 1080p view: oracle forward over {info['rows']} rows "
+                                          f"(+ full projection) and FP64 autograd backward over a "
+                                          f"{info['crop']}x{info['crop']} block, scaled to a full frame "
+                                          f"({time.perf_counter() - t0:.1f} s of CPU work)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, scene, r, mesh, dev, dist, frames):
+    """Through the public API (HybridRender autograd Function + an L1 loss):
+    every step copies the Gaussian parameters and the 8 target images (uint8)
+    from pinned host memory, renders forward+backward and reads the loss back."""
+    import torch
+    from paper_2506_06988_b300.render import HybridRender
+    g = scene.gaussians
+    host = {k: torch.as_tensor(getattr(g, k)).contiguous().pin_memory()
+            for k in ("means", "scales", "quats", "opacity", "sh")}
+    tgt_host = (torch.rand(3 * r.npix, generator=torch.Generator().manual_seed(5)) * 255).to(torch.uint8).pin_memory()
+    devp = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    tgt = torch.empty(3 * r.npix, dtype=torch.uint8, device=dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + tgt_host.numel()
+    d2h = 4
+
+    def step():
+        for k in host:
+            devp[k].copy_(host[k], non_blocking=True)
+        tgt.copy_(tgt_host, non_blocking=True)
+        params = {k: v.requires_grad_() for k, v in devp.items()}
+        rgb, T = HybridRender.apply(r, mesh, params["means"], params["scales"], params["quats"],
+                                    params["opacity"], params["sh"], None)
+        loss = (rgb - tgt.float() * (1.0 / 255.0)).abs().mean()
+        loss.backward()
+        for v in devp.values():
+            v.grad = None
+            v.requires_grad_(False)
+        return float(loss.item())
+
+    for _ in range(3):
+        step()
+    n = max(3, min(args.steps, 10))
+    _barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    _barrier(dist)
+    sec = _max_over_ranks((time.perf_counter() - t0) / n, dist)
+    return {"value": frames / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+            "ms_per_step": sec * 1e3, "api": "HybridRender.apply + L1 loss + backward; loss.item()"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--views", type=int, default=8, help="fewer views: small case for profiling")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * hm.h -- C ABI of the B300-native hybrid mesh-Gaussian renderer.
+ *
+ * The library renders the hybrid representation of "Hybrid Mesh-Gaussian
+ * Representation for Efficient Indoor Scene Reconstruction" (arXiv
+ * 2506.06988): an opaque textured triangle mesh gives per-pixel colour I_m and
+ * depth D_m (Sec. 3.4 "Joint rasterization"); 3D Gaussians (Eq. 1, with
+ * Sigma = R S S^T R^T and the EWA projection Sigma' = J W Sigma W^T J^T of
+ * Sec. 3.1) are alpha-blended front to back (Eq. 2) only while they lie in
+ * front of the mesh (D_gs < D_m), and the remaining transmittance T weights
+ * the mesh colour, or the background I_bg where no triangle covers the pixel:
+ *     I_h = I_gs + T * I_m   (triangle)      I_h = I_gs + T * I_bg   (none).
+ * The texture map is optimisable (Sec. 3.4): the backward pass returns
+ * gradients for the texels as well as for the Gaussian parameters.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every array argument is a DEVICE pointer owned by the caller, except
+ *    `cams` and `opt`, which are HOST pointers read during the call.  The
+ *    library allocates nothing; scratch memory is a caller-provided workspace
+ *    of at least the size returned by the matching *_workspace_size query.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream) and capturable into a CUDA graph.
+ *  - Return value: host-side status (argument validation, launch errors).
+ *    Errors found on the device (pair capacity exceeded, a bounded wait that
+ *    gave up) are OR-ed into the caller's device word `d_status` (HM_DEV_*
+ *    bits), to be read after the stream is synchronised.
+ *  - Camera k renders into a contiguous block of pixels starting at the sum
+ *    of the previous cameras' width*height; per-pixel outputs are float32 or
+ *    uint32 in row-major order; colour images are planar per camera
+ *    ([3][height][width] at 3x the pixel offset).  Per-tile outputs start at
+ *    the sum of the previous cameras' tile counts, tiles row-major.
+ *  - Gaussian data of camera k, Gaussian i lives at record index k*n + i.
+ *  - Parameters are the activated values: scales = exp(log-scale),
+ *    opacity = sigmoid(logit); quaternions (w,x,y,z) need not be normalised.
+ *  - A pixel (x,y) is sampled at its centre (x+1/2, y+1/2).
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hm_status;
+
+/* host-side return codes */
+#define HM_OK 0
+#define HM_ERR_INVALID_ARG 1   /* bad size, null required pointer, unsupported option */
+#define HM_ERR_CUDA 2          /* a CUDA launch or runtime call failed */
+#define HM_ERR_WORKSPACE 3     /* ws_bytes smaller than the *_workspace_size query */
+
+/* device status bits (OR-ed into *d_status) */
+#define HM_DEV_CAPACITY 1      /* more (Gaussian,tile) or (face,tile) pairs than capacity */
+#define HM_DEV_TIMEOUT 2       /* a bounded inter-CTA wait gave up; outputs are invalid */
+
+#define HM_MAX_VIEWS 32        /* cameras per call */
+#define HM_MAX_PAIRS 0x3FFFFFFF /* pair capacities must stay below 2^30 */
+
+/* texture formats */
+#define HM_TEX_RGB8 0          /* [tex_h][tex_w][3] uint8, value/255 */
+#define HM_TEX_RGBF32 1        /* [tex_h][tex_w][3] float32 */
+
+/* SH storage formats */
+#define HM_SH_F32 0
+#define HM_SH_F16 1            /* IEEE binary16, widened in-kernel */
+
+/* Pinhole camera, world -> camera: p_cam = R p_world + t (R row-major);
+ * OpenCV axes (+x right, +y down, +z forward); u = fx X/Z + cx. */
+typedef struct hm_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} hm_camera;
+
+typedef struct hm_options {
+    int32_t tile_w, tile_h;  /* screen tile: 16x16, 32x8 or 8x8 */
+    int32_t batch;           /* blend staging batch: 32, 64, 128 or 256 (<= tile pixels) */
+    int32_t mesh_cull;       /* 1: drop (Gaussian, tile) pairs at or behind the tile's
+                                farthest mesh depth (result-preserving) */
+    float near_gauss;        /* Gaussians with FP32 view depth <= this are culled (0.2) */
+    float near_mesh;         /* faces with a vertex at view z <= this are culled (0.01) */
+    float bg[3];             /* I_bg */
+    int32_t bwd_stages;      /* hm_blend_backward parts to run (HM_BWD_* bits; 0 = all) */
+} hm_options;
+
+/* hm_blend_backward parts.  HM_BWD_PROJECT consumes the per-record partials
+ * that HM_BWD_BLEND leaves in the workspace, so a caller splitting the pass
+ * runs BLEND before PROJECT on the same workspace. */
+#define HM_BWD_TEXTURE 1       /* texel gradients */
+#define HM_BWD_BLEND 2         /* blend replay -> per-record partials (workspace) */
+#define HM_BWD_PROJECT 4       /* partials -> Gaussian parameter gradients */
+
+/* Fill `opt` with the defaults: 16x16 tiles, batch 256, mesh_cull 1,
+ * near planes 0.2 / 0.01, black background, all backward parts. */
+void hm_default_options(hm_options *opt);
+
+/* Thread-local text of the last host-side error. */
+const char *hm_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* hm_rasterize_mesh -- Sec. 3.1 "Textured mesh" and the I_m, D_m of Sec. 3.4.
+ *
+ * Per pixel: the nearest covering triangle (two-sided; vertices projected in
+ * FP64, snapped to 1/256 px, exact integer edge functions, top-left fill
+ * rule; faces with a vertex at z <= near_mesh or beyond +-2^21 px culled),
+ * its view depth z = W / sum_k(w_k / z_k) evaluated in FP64 with a fixed
+ * operation order and rounded once to FP32 (nearest FP32 depth wins, ties to
+ * the lower face index), perspective-correct UVs and a bilinear,
+ * clamp-to-edge texture fetch (texel centres at half-integers, row 0 at v=0).
+ *
+ *  verts [n_verts][3], uvs [n_verts][2] float32; faces [n_faces][3] int32.
+ *  tex   texture in `tex_format` layout.
+ *  Outputs (per pixel of all cameras): tri_id int32 (-1 none), depth float32
+ *  (+inf none), rgb planar float32 (I_m, or opt->bg where none), uv planar
+ *  [2] float32 (0 where none); per tile: tile_max_depth float32 = the
+ *  largest depth of the tile's in-image pixels, +inf if any has no triangle.
+ *  item_capacity: (face, tile) work items the workspace holds; if exceeded,
+ *  HM_DEV_CAPACITY is set, *n_items_out (device int64) gets the need and the
+ *  outputs are invalid.  Any of rgb/uv may be NULL.
+ */
+size_t hm_rasterize_mesh_workspace_size(const hm_camera *cams, int32_t n_views, int32_t n_verts,
+                                        int32_t n_faces, int64_t item_capacity,
+                                        const hm_options *opt);
+hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, const float *verts,
+                            const float *uvs, int32_t n_verts, const int32_t *faces,
+                            int32_t n_faces, const void *tex, int32_t tex_w, int32_t tex_h,
+                            int32_t tex_format, const hm_options *opt, int32_t *tri_id,
+                            float *depth, float *rgb, float *uv, float *tile_max_depth,
+                            int64_t item_capacity, int64_t *n_items_out, int32_t *d_status,
+                            void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* hm_project_gaussians -- Eq. 1 and Sec. 3.1: per (camera, Gaussian) the
+ * 48-byte record consumed by hm_bin_sort / hm_blend_*:
+ *   mean2d (FP32 pixels), conic = Sigma'^-1 (xx, xy, yy) with
+ *   Sigma' = J W R S S^T R^T W^T J^T + 0.3 I (J: affine Jacobian with the view
+ *   x/z, y/z clamped to 1.3 x the half field of view), opacity, depth key
+ *   z = fp32(fma(R20,x,fma(R21,y,fma(R22,z,t2)))) in FP64, colour
+ *   max(0, 0.5 + SH(normalised mean - camera centre)) and the tile rectangle
+ *   covering the 3-sigma ellipse d^2 <= 9.  Culled (z <= near_gauss, or no
+ *   tile) records carry an empty rectangle.
+ *  sh [n][(sh_degree+1)^2][3] in sh_format; sh_degree 0..3.
+ *  records: n_views*n*48 bytes, 16-byte aligned.
+ */
+hm_status hm_project_gaussians(const hm_camera *cams, int32_t n_views, int32_t n,
+                               const float *means, const float *scales, const float *quats,
+                               const float *opacity, const void *sh, int32_t sh_degree,
+                               int32_t sh_format, const hm_options *opt, void *records,
+                               void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* hm_bin_sort -- the tile-wise sort the paper's rasteriser relies on (Sec. 1:
+ * tile-wise sorting and pixel-wise blending are the cost that grows with the
+ * number of Gaussians).  Emits one (tile, depth) key per (record, tile) pair
+ * whose tile the record's rectangle covers (minus pairs at or behind the
+ * tile's farthest mesh depth when opt->mesh_cull and tile_max_depth are
+ * given), and sorts them by (tile, FP32 depth, Gaussian index) with an LSD
+ * device radix sort.  Outputs: pair_vals[capacity] uint32 record indices in
+ * sorted order, *n_pairs_out (device int64) the pair count, tile_ranges
+ * [total_tiles][2] uint32 [begin, end) into pair_vals.  If the count exceeds
+ * `capacity` (<= HM_MAX_PAIRS), HM_DEV_CAPACITY is set, *n_pairs_out holds
+ * the need and the other outputs are invalid.
+ */
+size_t hm_bin_sort_workspace_size(const hm_camera *cams, int32_t n_views, int32_t n,
+                                  int64_t capacity, const hm_options *opt);
+hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t n, const void *records,
+                      const float *tile_max_depth, const hm_options *opt, uint32_t *pair_vals,
+                      int64_t capacity, int64_t *n_pairs_out, uint32_t *tile_ranges,
+                      int32_t *d_status, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* hm_blend_forward -- Eq. 2 with the joint-rasterisation cut-off of Sec. 3.4.
+ * Per pixel, front to back over its tile's sorted list: stop at the first
+ * Gaussian with depth >= D_m (mesh_depth finite); skip it unless
+ * d^2 = D^T conic D <= 9; alpha = min(0.99, o exp(-d^2/2)); skip if
+ * alpha < 1/255; stop before a Gaussian that would drop T below 1e-4;
+ * C += alpha T c, T *= 1 - alpha.  Finally I_h = C + T * back, with back =
+ * mesh_rgb (I_m, or I_bg where no triangle) or opt->bg if mesh_rgb is NULL.
+ *  mesh_depth, mesh_rgb: hm_rasterize_mesh outputs, or NULL (no mesh).
+ *  Outputs: out_rgb planar, out_T, n_contrib (Gaussians blended), last_idx
+ *  (1 + position in pair_vals of the last blended Gaussian, 0 if none; used
+ *  by the backward pass; may be NULL).
+ *  eval_stats (device uint64[2], may be NULL): when given, [0] += the number
+ *  of (pixel, Gaussian) pairs whose alpha was evaluated (inside the 3-sigma
+ *  ellipse, before the pixel stopped) and [1] += the list entries examined.
+ */
+hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, const void *records,
+                           const uint32_t *pair_vals, const uint32_t *tile_ranges,
+                           const float *mesh_depth, const float *mesh_rgb, const hm_options *opt,
+                           float *out_rgb, float *out_T, uint32_t *n_contrib, uint32_t *last_idx,
+                           unsigned long long *eval_stats, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* hm_blend_backward -- gradients of a loss L through hm_blend_forward and
+ * hm_project_gaussians (and, if d_tex is given, through the bilinear texture
+ * fetch of hm_rasterize_mesh: dL/dtexel = sum over pixels of
+ * T * bilinear weight * dL/dI_h on pixels with a triangle).  Discrete
+ * decisions (the blended set, clamps, the mesh hit) carry no gradient; vertex
+ * positions and UVs get none.
+ *  Inputs: the forward's parameters, records, sorted pairs and ranges, mesh
+ *  outputs (depth, rgb, uv; NULL for no mesh), out_T and last_idx, and
+ *  dL_drgb (planar, like out_rgb) and dL_dT (per pixel, may be NULL).
+ *  Outputs, ACCUMULATED into caller-zeroed buffers: d_means [n][3],
+ *  d_scales [n][3], d_quats [n][4], d_opacity [n], d_sh [n][K][3] float32
+ *  (also for F16 SH storage), d_tex [tex_h][tex_w][3] float32 (may be NULL).
+ */
+size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n);
+hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, const float *means,
+                            const float *scales, const float *quats, const float *opacity,
+                            const void *sh, int32_t sh_degree, int32_t sh_format,
+                            const void *records, const uint32_t *pair_vals,
+                            const uint32_t *tile_ranges, const float *mesh_depth,
+                            const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
+                            int32_t tex_h, const hm_options *opt, const float *out_T,
+                            const uint32_t *last_idx, const float *dL_drgb, const float *dL_dT,
+                            float *d_means, float *d_scales, float *d_quats, float *d_opacity,
+                            float *d_sh, float *d_tex, void *ws, size_t ws_bytes, void *stream);
+
+/* Number of tiles of all cameras for the tile shape in `opt`. */
+int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options *opt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -1,0 +1,495 @@
+// blend_bwd.cu -- gradients of the hybrid render (Eq. 2 blending with the
+// Sec. 3.4 composite I_h = I_gs + T * back) with respect to the Gaussian
+// parameters and the texels (the texture map is optimisable, Sec. 3.4).
+//
+// Three kernels:
+//  * blend_bwd: per tile, per pixel, the blended Gaussians are replayed back
+//    to front from the pixel's last blended list position.  With
+//    B = (colour behind Gaussian i) / T_{i+1}, running from B = back:
+//        dI/dc_i     = alpha_i T_i
+//        dI/dalpha_i = T_i (c_i - B),  dT_final/dalpha_i = -T_final/(1-alpha_i)
+//        B <- alpha_i c_i + (1 - alpha_i) B,  T_i = T_{i+1} / (1 - alpha_i).
+//    Decisions are re-evaluated with the forward's exact arithmetic
+//    (blend_common.cuh).  Per Gaussian the 9 partials (mean2d, conic,
+//    opacity, colour) are summed over the warp with shuffles and added to
+//    per-record accumulators with one atomic per value per warp.
+//  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
+//    triangle (the mesh colour enters I_h weighted by T).
+//  * project_bwd: one thread per Gaussian chains the per-record partials
+//    through the conic inverse, Sigma' = V V^T, V = (J W)(R S), the clamped
+//    Jacobian, the projection of the mean, the quaternion normalisation and
+//    the SH colour (including its dependence on the mean through the view
+//    direction), summing over cameras without atomics.
+#include "blend_common.cuh"
+#include "hm_host.h"
+#include "sh.cuh"
+
+namespace hm {
+
+namespace {
+
+constexpr int kG = 9;   // dmx, dmy, dconic_xx, dconic_xy, dconic_yy, dopacity, dr, dg, db
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH)
+blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
+                 const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_rgb, float bg0,
+                 float bg1, float bg2, const float *__restrict__ out_T,
+                 const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
+                 const float *__restrict__ dL_dT, float *__restrict__ g2d) {
+    constexpr int NT = TW * TH;
+    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+    __shared__ uint32_t s_item[NT];
+    __shared__ uint32_t s_hi;
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(vt, gt);
+    const ViewDev &V = vt.v[v];
+    const int local = gt - V.tile_off;
+    const int tx = local % V.tiles_x, ty = local / V.tiles_x;
+    const int t = threadIdx.x, lane = t & 31;
+    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
+    const bool inside = px < V.W && py < V.H;
+    const long long npx = (long long)V.W * V.H;
+    const long long lp = (long long)py * V.W + px;
+    const long long gp = V.pix_off + lp;
+    float Tf = 1.f, gI0 = 0.f, gI1 = 0.f, gI2 = 0.f, gT = 0.f;
+    float B0 = bg0, B1 = bg1, B2 = bg2;
+    uint32_t my_last = 0;
+    if (inside) {
+        Tf = out_T[gp];
+        my_last = last_idx[gp];
+        const float *g = dL_drgb + 3 * V.pix_off + lp;
+        gI0 = g[0]; gI1 = g[npx]; gI2 = g[2 * npx];
+        if (dL_dT) gT = dL_dT[gp];
+        if (mesh_rgb) {
+            const float *m = mesh_rgb + 3 * V.pix_off + lp;
+            B0 = m[0]; B1 = m[npx]; B2 = m[2 * npx];
+        }
+    }
+    const uint32_t begin = ranges[2 * gt];
+    if (t == 0) s_hi = 0;
+    __syncthreads();
+    if (my_last > 0) atomicMax(&s_hi, my_last);
+    __syncthreads();
+    const uint32_t hi_all = s_hi;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    float T = Tf;
+    const float gTT = gT * Tf;
+    for (uint32_t hi = hi_all; hi > begin;) {
+        const uint32_t lo = hi - begin > (uint32_t)NT ? hi - NT : begin;
+        const int nb = (int)(hi - lo);
+        __syncthreads();
+        if (t < nb) {
+            const uint32_t it = vals[lo + t];
+            s_item[t] = it;
+            stage_record(rec[it], s_a[t], s_b[t], s_c[t]);
+        }
+        __syncthreads();
+        for (int k = nb - 1; k >= 0; --k) {
+            const uint32_t j = lo + k;
+            float g[kG];
+#pragma unroll
+            for (int q = 0; q < kG; ++q) g[q] = 0.f;
+            bool active = false;
+            if (j < my_last) {
+                const float4 A = s_a[k], Bs = s_b[k], c = s_c[k];
+                float dx, dy;
+                const float q = eval_q(A, Bs, fpx, fpy, dx, dy);
+                if (q >= kQ3) {
+                    const float G = ex2_approx(q);
+                    const float araw = __fmul_rn(Bs.y, G);
+                    const float alpha = fminf(kAlphaMax, araw);
+                    if (alpha >= kAlphaMin) {
+                        active = true;
+                        const float om = 1.f - alpha;
+                        const float Ti = T / om;
+                        const float wgt = alpha * Ti;
+                        g[6] = wgt * gI0;
+                        g[7] = wgt * gI1;
+                        g[8] = wgt * gI2;
+                        float dLda = Ti * (gI0 * (c.x - B0) + gI1 * (c.y - B1) + gI2 * (c.z - B2)) - gTT / om;
+                        if (araw < kAlphaMax) {
+                            const float gq = dLda * araw * kLn2;     // d alpha / d q = o G ln 2
+                            g[0] = -gq * (2.f * A.z * dx + A.w * dy);
+                            g[1] = -gq * (A.w * dx + 2.f * Bs.x * dy);
+                            g[2] = gq * kNegHalfLog2e * dx * dx;
+                            g[3] = gq * 2.f * kNegHalfLog2e * dx * dy;
+                            g[4] = gq * kNegHalfLog2e * dy * dy;
+                            g[5] = dLda * G;
+                        }
+                        B0 = fmaf(alpha, c.x, om * B0);
+                        B1 = fmaf(alpha, c.y, om * B1);
+                        B2 = fmaf(alpha, c.z, om * B2);
+                        T = Ti;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, active)) {
+#pragma unroll
+                for (int q = 0; q < kG; ++q) {
+                    float x = g[q];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    g[q] = x;
+                }
+                if (lane == 0) {
+                    float *dst = g2d + (size_t)s_item[k] * kG;
+#pragma unroll
+                    for (int q = 0; q < kG; ++q)
+                        if (g[q] != 0.f) atomicAdd(dst + q, g[q]);
+                }
+            }
+        }
+        hi = lo;
+    }
+}
+
+template <bool F32TEX>
+__global__ void __launch_bounds__(256)
+texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const float *__restrict__ uv,
+                   const float *__restrict__ out_T, const float *__restrict__ dL_drgb, int tw, int th,
+                   float *__restrict__ d_tex) {
+    const long long total = vt.total_pixels;
+    for (long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x; gp < total;
+         gp += (long long)gridDim.x * blockDim.x) {
+        if (!(mesh_depth[gp] < INFINITY)) continue;
+        const int v = view_of_pixel(vt, gp);
+        const ViewDev &V = vt.v[v];
+        const long long npx = (long long)V.W * V.H;
+        const long long lp = gp - V.pix_off;
+        const float T = out_T[gp];
+        const float *g = dL_drgb + 3 * V.pix_off + lp;
+        const float g0 = T * g[0], g1 = T * g[npx], g2 = T * g[2 * npx];
+        const float *u = uv + 2 * V.pix_off + lp;
+        const float ss = u[0] * (float)tw - 0.5f, tt = u[npx] * (float)th - 0.5f;
+        const float x0 = floorf(ss), y0 = floorf(tt);
+        const float fx = ss - x0, fy = tt - y0;
+        const int ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f), iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
+        const float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+        const int xs[4] = {ix, ix + 1, ix, ix + 1}, ys[4] = {iy, iy, iy + 1, iy + 1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (w[k] == 0.f) continue;
+            const int x = min(max(xs[k], 0), tw - 1), y = min(max(ys[k], 0), th - 1);
+            float *d = d_tex + ((size_t)y * tw + x) * 3;
+            atomicAdd(d, w[k] * g0);
+            atomicAdd(d + 1, w[k] * g1);
+            atomicAdd(d + 2, w[k] * g2);
+        }
+    }
+}
+
+__device__ __forceinline__ float ratio_ff(double x, float zf, float zl, float rz) {
+    float xf = __double2float_rn(x);
+    float xl = __double2float_rn(x - (double)xf);
+    float q0 = xf * rz;
+    float e = fmaf(-q0, zf, xf);
+    e += xl - q0 * zl;
+    return fmaf(e, rz, q0);
+}
+
+template <int DEG, bool F16>
+__global__ void __launch_bounds__(128)
+project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
+                   const float *__restrict__ scales, const float *__restrict__ quats,
+                   const float *__restrict__ opac, const void *__restrict__ sh_raw, float near_z,
+                   const float *__restrict__ g2d, float *__restrict__ d_means,
+                   float *__restrict__ d_scales, float *__restrict__ d_quats,
+                   float *__restrict__ d_opac, float *__restrict__ d_sh) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+    const float qinv = rsqrtf(qn2);
+    const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+    float M[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[a][k] = R[a][k] * s[k];
+    float sh[K][3];
+    if (F16) {
+        const __half *h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[k][c] = __half2float(h[3 * k + c]);
+    } else {
+        const float *f = reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sh[k][c] = __ldg(f + 3 * k + c);
+    }
+    float gmean[3] = {0.f, 0.f, 0.f};
+    float gM[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float gsh[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+    float gop = 0.f;
+    const double dxw = mx, dyw = my, dzw = mz;
+    for (int v = 0; v < vt.n_views; ++v) {
+        const float *gg = g2d + ((size_t)v * n + i) * kG;
+        float g[kG];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kG; ++q) {
+            g[q] = gg[q];
+            any |= g[q] != 0.f;
+        }
+        if (!any) continue;
+        const ViewDev &V = vt.v[v];
+        const double tzd = fma((double)V.R[6], dxw, fma((double)V.R[7], dyw, fma((double)V.R[8], dzw, (double)V.t[2])));
+        const float zf = __double2float_rn(tzd);
+        if (!(zf > near_z)) continue;
+        const double txd = fma((double)V.R[0], dxw, fma((double)V.R[1], dyw, fma((double)V.R[2], dzw, (double)V.t[0])));
+        const double tyd = fma((double)V.R[3], dxw, fma((double)V.R[4], dyw, fma((double)V.R[5], dzw, (double)V.t[1])));
+        const float zl = __double2float_rn(tzd - (double)zf);
+        const float rz = __frcp_rn(zf);
+        const float rx = ratio_ff(txd, zf, zl, rz), ry = ratio_ff(tyd, zf, zl, rz);
+        const float limx = 1.3f * (0.5f * (float)V.W / V.fx), limy = 1.3f * (0.5f * (float)V.H / V.fy);
+        const bool inx = rx > -limx && rx < limx, iny = ry > -limy && ry < limy;
+        const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
+        const float J00 = V.fx * rz, J02 = -V.fx * rxc * rz, J11 = V.fy * rz, J12 = -V.fy * ryc * rz;
+        float T0[3], T1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = fmaf(J00, V.R[k], J02 * V.R[6 + k]);
+            T1[k] = fmaf(J11, V.R[3 + k], J12 * V.R[6 + k]);
+        }
+        float V0[3], V1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V0[k] = T0[0] * M[0][k] + T0[1] * M[1][k] + T0[2] * M[2][k];
+            V1[k] = T1[0] * M[0][k] + T1[1] * M[1][k] + T1[2] * M[2][k];
+        }
+        const float a = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2] + 0.3f;
+        const float c = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2] + 0.3f;
+        const float b = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
+        const float cx_ = V0[1] * V1[2] - V0[2] * V1[1], cy_ = V0[2] * V1[0] - V0[0] * V1[2],
+                    cz_ = V0[0] * V1[1] - V0[1] * V1[0];
+        const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + 0.3f * (a + c - 0.6f) + 0.09f;
+        const float rd2 = 1.f / (det * det);
+        // conic (c/det, -b/det, a/det) -> Sigma' entries
+        const float gA = g[2], gB = g[3], gC = g[4];
+        const float ga = (-c * c * gA + b * c * gB - b * b * gC) * rd2;
+        const float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * rd2;
+        const float gc = (-b * b * gA + a * b * gB - a * a * gC) * rd2;
+        // Sigma' = V V^T: dV0 = 2 ga V0 + gb V1, dV1 = gb V0 + 2 gc V1
+        float gV0[3], gV1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gV0[k] = 2.f * ga * V0[k] + gb * V1[k];
+            gV1[k] = gb * V0[k] + 2.f * gc * V1[k];
+        }
+        // V = T M: dM += T^T dV, dT = dV M^T
+        float gT0[3], gT1[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gM[r][k] += T0[r] * gV0[k] + T1[r] * gV1[k];
+            gT0[r] = gV0[0] * M[r][0] + gV0[1] * M[r][1] + gV0[2] * M[r][2];
+            gT1[r] = gV1[0] * M[r][0] + gV1[1] * M[r][1] + gV1[2] * M[r][2];
+        }
+        // T = J W (J01 = J10 = 0)
+        float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gJ00 += gT0[k] * V.R[k];
+            gJ02 += gT0[k] * V.R[6 + k];
+            gJ11 += gT1[k] * V.R[3 + k];
+            gJ12 += gT1[k] * V.R[6 + k];
+        }
+        const float rz2 = rz * rz;
+        float gtx = 0.f, gty = 0.f, gtz = 0.f;
+        gtz += -gJ00 * V.fx * rz2 - gJ11 * V.fy * rz2;
+        // J02 = -fx xc / z with xc = clamp(x/z)
+        gtz += gJ02 * V.fx * rxc * rz2;
+        gtz += gJ12 * V.fy * ryc * rz2;
+        if (inx) {
+            gtx += -gJ02 * V.fx * rz2;
+            gtz += gJ02 * V.fx * rx * rz2;
+        }
+        if (iny) {
+            gty += -gJ12 * V.fy * rz2;
+            gtz += gJ12 * V.fy * ry * rz2;
+        }
+        // mean2d = (fx x/z + cx, fy y/z + cy)
+        gtx += g[0] * V.fx * rz;
+        gty += g[1] * V.fy * rz;
+        gtz += -(g[0] * V.fx * rx + g[1] * V.fy * ry) * rz;
+        // t = W mean + t_cam
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gmean[k] += V.R[k] * gtx + V.R[3 + k] * gty + V.R[6 + k] * gtz;
+        gop += g[5];
+        // colour
+        float d0 = mx - V.campos[0], d1 = my - V.campos[1], d2 = mz - V.campos[2];
+        const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+        d0 *= dinv; d1 *= dinv; d2 *= dinv;
+        float Y[K];
+        sh_basis<DEG>(d0, d1, d2, Y);
+        float gcol[3] = {g[6], g[7], g[8]};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
+            if (acc < 0.f) gcol[ch] = 0.f;   // clamped at 0: no gradient
+#pragma unroll
+            for (int k = 0; k < K; ++k) gsh[k][ch] += Y[k] * gcol[ch];
+        }
+        if (DEG > 0) {
+            float GY[K][3];
+            sh_basis_grad<DEG>(d0, d1, d2, GY);
+            float gd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 1; k < K; ++k) {
+                const float w = sh[k][0] * gcol[0] + sh[k][1] * gcol[1] + sh[k][2] * gcol[2];
+                gd[0] += w * GY[k][0];
+                gd[1] += w * GY[k][1];
+                gd[2] += w * GY[k][2];
+            }
+            const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+            gmean[0] += (gd[0] - dd * d0) * dinv;
+            gmean[1] += (gd[1] - dd * d1) * dinv;
+            gmean[2] += (gd[2] - dd * d2) * dinv;
+        }
+    }
+    // M = R S: dS_k = sum_a dM[a][k] R[a][k], dR[a][k] = dM[a][k] s_k
+    float gR[3][3];
+    float gs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gs[k] += gM[a][k] * R[a][k];
+            gR[a][k] = gM[a][k] * s[k];
+        }
+    // R(q^) -> q^ (w, x, y, z)
+    float gqw = 2.f * (qz * (gR[1][0] - gR[0][1]) + qy * (gR[0][2] - gR[2][0]) + qx * (gR[2][1] - gR[1][2]));
+    float gqx = 2.f * (qy * (gR[0][1] + gR[1][0]) + qz * (gR[0][2] + gR[2][0]) + qw * (gR[2][1] - gR[1][2])) -
+                4.f * qx * (gR[1][1] + gR[2][2]);
+    float gqy = 2.f * (qx * (gR[0][1] + gR[1][0]) + qz * (gR[1][2] + gR[2][1]) + qw * (gR[0][2] - gR[2][0])) -
+                4.f * qy * (gR[0][0] + gR[2][2]);
+    float gqz = 2.f * (qx * (gR[0][2] + gR[2][0]) + qy * (gR[1][2] + gR[2][1]) + qw * (gR[1][0] - gR[0][1])) -
+                4.f * qz * (gR[0][0] + gR[1][1]);
+    // normalisation q^ = q / |q|
+    const float dot = gqw * qw + gqx * qx + gqy * qy + gqz * qz;
+    gqw = (gqw - dot * qw) * qinv;
+    gqx = (gqx - dot * qx) * qinv;
+    gqy = (gqy - dot * qy) * qinv;
+    gqz = (gqz - dot * qz) * qinv;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d_means[3 * i + k] += gmean[k];
+        d_scales[3 * i + k] += gs[k];
+    }
+    d_quats[4 * i] += gqw;
+    d_quats[4 * i + 1] += gqx;
+    d_quats[4 * i + 2] += gqy;
+    d_quats[4 * i + 3] += gqz;
+    d_opac[i] += gop;
+    float *ds = d_sh + (size_t)i * K * 3;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[k][c];
+}
+
+template <int DEG>
+cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const float *scales,
+                        const float *quats, const float *opac, const void *sh, bool f16, float near_z,
+                        const float *g2d, float *dm, float *ds, float *dq, float *dop, float *dsh,
+                        cudaStream_t s) {
+    dim3 grid((n + 127) / 128);
+    if (f16)
+        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, g2d, dm, ds, dq, dop, dsh);
+    else
+        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, g2d, dm, ds, dq, dop, dsh);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n) {
+    if (n_views < 1 || n < 0) return 0;
+    return sizeof(float) * kG * (size_t)n_views * (size_t)n + 256;
+}
+
+extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n,
+                                       const float *means, const float *scales, const float *quats,
+                                       const float *opacity, const void *sh, int32_t sh_degree,
+                                       int32_t sh_format, const void *records,
+                                       const uint32_t *pair_vals, const uint32_t *tile_ranges,
+                                       const float *mesh_depth, const float *mesh_rgb,
+                                       const float *mesh_uv, int32_t tex_w, int32_t tex_h,
+                                       const hm_options *opt, const float *out_T,
+                                       const uint32_t *last_idx, const float *dL_drgb,
+                                       const float *dL_dT, float *d_means, float *d_scales,
+                                       float *d_quats, float *d_opacity, float *d_sh, float *d_tex,
+                                       void *ws, size_t ws_bytes, void *stream) {
+    ViewTable vt;
+    if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
+    if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
+    if (sh_degree < 0 || sh_degree > 3) return fail(HM_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (sh_format != HM_SH_F32 && sh_format != HM_SH_F16) return fail(HM_ERR_INVALID_ARG, "sh_format");
+    if (!tile_ranges || !out_T || !last_idx || !dL_drgb) return fail(HM_ERR_INVALID_ARG, "null pointer");
+    if (n > 0 && (!means || !scales || !quats || !opacity || !sh || !records || !pair_vals ||
+                  !d_means || !d_scales || !d_quats || !d_opacity || !d_sh))
+        return fail(HM_ERR_INVALID_ARG, "null pointer");
+    if (d_tex && (!mesh_depth || !mesh_uv || tex_w <= 0 || tex_h <= 0))
+        return fail(HM_ERR_INVALID_ARG, "texture gradient needs mesh_depth, mesh_uv and the texture size");
+    if (((uintptr_t)records & 15) || ((uintptr_t)quats & 15))
+        return fail(HM_ERR_INVALID_ARG, "records and quats must be 16-byte aligned");
+    const size_t need = hm_blend_backward_workspace_size(n_views, n);
+    if (n > 0 && (!ws || ws_bytes < need)) return fail(HM_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, need);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    const float *bg = opt->bg;
+    const int stages = opt->bwd_stages ? opt->bwd_stages : (HM_BWD_TEXTURE | HM_BWD_BLEND | HM_BWD_PROJECT);
+    if (d_tex && (stages & HM_BWD_TEXTURE)) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        long long g = (vt.total_pixels + 255) / 256;
+        if (g > (long long)sms * 16) g = (long long)sms * 16;
+        texture_bwd_kernel<false><<<(unsigned)g, 256, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, tex_w, tex_h, d_tex);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    if (n == 0) return HM_OK;
+    float *g2d = reinterpret_cast<float *>(ws);
+    const Record *rec = reinterpret_cast<const Record *>(records);
+    dim3 grid(vt.total_tiles);
+    if (stages & HM_BWD_BLEND) {
+    e = cudaMemsetAsync(g2d, 0, sizeof(float) * kG * (size_t)n_views * n, s);
+    if (e != cudaSuccess) return cuda_status(e);
+#define HM_BBWD(TW, TH)                                                                          \
+    blend_bwd_kernel<TW, TH><<<grid, TW * TH, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_rgb, \
+                                                      bg[0], bg[1], bg[2], out_T, last_idx,      \
+                                                      dL_drgb, dL_dT, g2d)
+    if (opt->tile_w == 16) HM_BBWD(16, 16);
+    else if (opt->tile_w == 32) HM_BBWD(32, 8);
+    else HM_BBWD(8, 8);
+#undef HM_BBWD
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    if (!(stages & HM_BWD_PROJECT)) return HM_OK;
+    const bool f16 = sh_format == HM_SH_F16;
+    switch (sh_degree) {
+        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+    }
+    return cuda_status(e);
+}

@@ -1,0 +1,148 @@
+// hm_internal.cuh -- device-side types and helpers shared by the kernels of
+// libhm (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "hm.h"
+
+namespace hm {
+
+// ---------------------------------------------------------------------------
+// per-camera constants, passed by value in kernel parameter space
+// ---------------------------------------------------------------------------
+struct ViewDev {
+    float R[9];
+    float t[3];
+    float campos[3];       // camera centre -R^T t (world)
+    float fx, fy, cx, cy;
+    int W, H, tiles_x, tiles_y;
+    int tile_off;          // first global tile id of this camera
+    int pad;
+    long long pix_off;     // first global pixel of this camera
+};
+
+struct ViewTable {
+    int n_views, tile_w, tile_h, total_tiles;
+    long long total_pixels;
+    ViewDev v[HM_MAX_VIEWS];
+};
+
+// camera owning global tile `gt` (tile_off is increasing)
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, int gt) {
+    int v = 0;
+    for (int k = 1; k < vt.n_views; ++k)
+        if (vt.v[k].tile_off <= gt) v = k;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_pixel(const ViewTable &vt, long long gp) {
+    int v = 0;
+    for (int k = 1; k < vt.n_views; ++k)
+        if (vt.v[k].pix_off <= gp) v = k;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// projected Gaussian record (48 bytes)
+//   a = {mean_x, mean_y, conic_xx, conic_xy}
+//   b = {conic_yy, opacity, depth, tile x-range (u16 x0 | u16 x1 << 16)}
+//   c = {r, g, b, tile y-range (u16 y0 | u16 y1 << 16)}
+// An empty range has x0 > x1.
+// ---------------------------------------------------------------------------
+struct __align__(16) Record {
+    float4 a, b, c;
+};
+static_assert(sizeof(Record) == 48, "record layout");
+
+__host__ __device__ __forceinline__ uint32_t pack_range(uint32_t lo, uint32_t hi) {
+    return (lo & 0xFFFFu) | (hi << 16);
+}
+__host__ __device__ __forceinline__ void unpack_range(uint32_t r, int &lo, int &hi) {
+    lo = (int)(r & 0xFFFFu);
+    hi = (int)(r >> 16);
+}
+constexpr uint32_t kEmptyRange = 0x0000FFFFu;   // lo = 65535 > hi = 0
+
+// ---------------------------------------------------------------------------
+// status words and bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int32_t *st, int32_t bit) {
+    if (st) atomicOr(st, bit);
+}
+
+// polls of a not-yet-published predecessor before a wait gives up (each poll
+// sleeps ~100 ns, so the bound is several hundred milliseconds)
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_volatile_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_volatile_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers (one per .cu file)
+// ---------------------------------------------------------------------------
+struct ScanWs {
+    unsigned long long *tile_status;   // [max_tiles]
+    unsigned int *ticket;              // [1]
+};
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+inline long long scan_tiles(long long n) { return (n + kScanTile - 1) / kScanTile; }
+
+// out[i] = sum_{j<i} in[idx ? idx[j] : j] (uint32, exclusive); *total (int64)
+// = the full sum; if capacity >= 0 and the sum exceeds it, HM_DEV_CAPACITY.
+cudaError_t launch_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, long long n,
+                        long long *total, long long capacity, int32_t *d_status, ScanWs ws,
+                        cudaStream_t s);
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+struct SortWs {
+    uint32_t *hist;        // [4][256]
+    uint32_t *lookback;    // [4][max_tiles][256]
+    unsigned int *ticket;  // [4]
+    long long max_tiles;
+};
+inline long long sort_tiles(long long n) { return (n + kSortTile - 1) / kSortTile; }
+// Stable LSD radix sort of (key, value) uint32 pairs on key bits
+// [0, 8*passes); the count is *n_dev (<= n_max).  Ping-pongs between
+// (k0,v0) and (k1,v1); with an even number of passes the result ends in
+// (k0,v0), otherwise in (k1,v1).  identity_vals: the input values are the
+// input positions (v0 is not read, only written).
+cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+                              const long long *n_dev, long long n_max, int passes,
+                              bool identity_vals, int32_t *d_status, SortWs ws, cudaStream_t s);
+
+cudaError_t launch_fill_i64(long long *p, long long v, cudaStream_t s);
+
+}  // namespace hm

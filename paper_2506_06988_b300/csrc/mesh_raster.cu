@@ -1,0 +1,416 @@
+// mesh_raster.cu -- textured-mesh rasterisation (Sec. 3.1 "Textured mesh":
+// barycentric UV interpolation and a texture lookup per pixel) producing the
+// I_m and D_m of the joint rasterisation (Sec. 3.4).
+//
+// Pipeline (all cameras of a call at once):
+//   vertex pass   FP64 view transform (fixed FMA order), projection, snap to
+//                 1/256 px, 1/z;
+//   face pass     orientation, bounding box, tiles touched (count);
+//   scan + emit   one (face, tile) work item per touched tile;
+//   coverage      one warp per item: exact int64 edge functions with the
+//                 top-left rule at the tile's pixel centres; the FP64 depth
+//                 W / sum_k(w_k / z_k), rounded once to FP32, is packed with
+//                 the face index into a 64-bit key and merged with
+//                 atomicMin into a per-pixel visibility word -- the minimum
+//                 is (nearest FP32 depth, lowest face index) whatever the
+//                 order the items run in;
+//   resolve       one CTA per tile: perspective-correct UVs, bilinear
+//                 clamp-to-edge texel fetch, outputs, per-tile farthest mesh
+//                 depth (for the Gaussian pair cull).
+#include <limits.h>
+
+#include "hm_host.h"
+
+namespace hm {
+
+namespace {
+
+constexpr double kSnap = 256.0;
+constexpr double kGuard = 2097152.0;   // 2^21 px
+constexpr int kInvalid = INT_MIN;
+
+struct FaceSetup {
+    int x[3], y[3];          // snapped positions in the face's vertex order
+    long long area2;         // |signed double area| (1/256 px)^2
+    int flip;                // signed area negative: traverse 0 -> 2 -> 1
+    int tx0, tx1, ty0, ty1;  // touched tiles (empty: tx0 > tx1)
+    int pad;
+    double iz[3];            // 1 / view z per vertex
+};
+
+__global__ void __launch_bounds__(256)
+mesh_vertex_kernel(ViewTable vt, int nv, const float *__restrict__ verts, double znear,
+                   int2 *__restrict__ sxy, double *__restrict__ iz) {
+    const long long m = (long long)vt.n_views * nv;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(it / nv);
+        const long long k = it - (long long)v * nv;
+        const ViewDev &V = vt.v[v];
+        const double x = verts[3 * k], y = verts[3 * k + 1], z = verts[3 * k + 2];
+        const double X = fma((double)V.R[0], x, fma((double)V.R[1], y, fma((double)V.R[2], z, (double)V.t[0])));
+        const double Y = fma((double)V.R[3], x, fma((double)V.R[4], y, fma((double)V.R[5], z, (double)V.t[1])));
+        const double Z = fma((double)V.R[6], x, fma((double)V.R[7], y, fma((double)V.R[8], z, (double)V.t[2])));
+        int2 o = make_int2(kInvalid, kInvalid);
+        double r = 0.0;
+        if (Z > znear) {
+            const double sx = fma((double)V.fx, X / Z, (double)V.cx);
+            const double sy = fma((double)V.fy, Y / Z, (double)V.cy);
+            if (fabs(sx) <= kGuard && fabs(sy) <= kGuard) {
+                o.x = (int)__double2ll_rn(sx * kSnap);
+                o.y = (int)__double2ll_rn(sy * kSnap);
+                r = 1.0 / Z;
+            }
+        }
+        sxy[it] = o;
+        iz[it] = r;
+    }
+}
+
+__device__ __forceinline__ long long floor_div(long long a, long long b) {
+    long long q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+__global__ void __launch_bounds__(256)
+mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces,
+                 const int2 *__restrict__ sxy, const double *__restrict__ iz,
+                 FaceSetup *__restrict__ setup, uint32_t *__restrict__ cnt) {
+    const long long m = (long long)vt.n_views * nf;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(it / nf);
+        const long long f = it - (long long)v * nf;
+        const ViewDev &V = vt.v[v];
+        FaceSetup s;
+        s.tx0 = 1; s.tx1 = 0; s.ty0 = 1; s.ty1 = 0;
+        s.flip = 0; s.area2 = 0; s.pad = 0;
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) {
+            const int vi = faces[3 * f + k];
+            if (vi < 0 || vi >= nv) { ok = false; s.x[k] = s.y[k] = 0; s.iz[k] = 0; continue; }
+            const int2 p = sxy[(long long)v * nv + vi];
+            s.x[k] = p.x; s.y[k] = p.y;
+            s.iz[k] = iz[(long long)v * nv + vi];
+            if (p.x == kInvalid) ok = false;
+        }
+        uint32_t c = 0;
+        if (ok) {
+            const long long a2 = (long long)(s.x[1] - s.x[0]) * (s.y[2] - s.y[0]) -
+                                 (long long)(s.y[1] - s.y[0]) * (s.x[2] - s.x[0]);
+            if (a2 != 0) {
+                s.flip = a2 < 0;
+                s.area2 = a2 < 0 ? -a2 : a2;
+                const long long mnx = min(s.x[0], min(s.x[1], s.x[2])), mxx = max(s.x[0], max(s.x[1], s.x[2]));
+                const long long mny = min(s.y[0], min(s.y[1], s.y[2])), mxy = max(s.y[0], max(s.y[1], s.y[2]));
+                // pixel centres 256 x + 128 inside [mn, mx]
+                long long x0 = -floor_div(-(mnx - 128), 256), x1 = floor_div(mxx - 128, 256);
+                long long y0 = -floor_div(-(mny - 128), 256), y1 = floor_div(mxy - 128, 256);
+                x0 = max(x0, 0ll); x1 = min(x1, (long long)V.W - 1);
+                y0 = max(y0, 0ll); y1 = min(y1, (long long)V.H - 1);
+                if (x0 <= x1 && y0 <= y1) {
+                    s.tx0 = (int)(x0 / vt.tile_w); s.tx1 = (int)(x1 / vt.tile_w);
+                    s.ty0 = (int)(y0 / vt.tile_h); s.ty1 = (int)(y1 / vt.tile_h);
+                    c = (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1));
+                }
+            }
+        }
+        setup[it] = s;
+        cnt[it] = c;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+mesh_emit_kernel(long long m, const FaceSetup *__restrict__ setup, const uint32_t *__restrict__ cnt,
+                 const uint32_t *__restrict__ offs, long long capacity,
+                 unsigned long long *__restrict__ items) {
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
+         it += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[it];
+        if (c == 0) continue;
+        long long o = offs[it];
+        if (o + c > capacity) continue;
+        const FaceSetup &s = setup[it];
+        for (int ty = s.ty0; ty <= s.ty1; ++ty)
+            for (int tx = s.tx0; tx <= s.tx1; ++tx)
+                items[o++] = ((unsigned long long)it << 32) | ((unsigned)ty << 16) | (unsigned)tx;
+    }
+}
+
+// edge a->b of a positively oriented triangle (y down): inside E > 0; a
+// centre exactly on an edge belongs to it iff the edge is top or left
+__device__ __forceinline__ bool edge_in(long long ax, long long ay, long long bx, long long by,
+                                        long long px, long long py, long long &E) {
+    const long long dx = bx - ax, dy = by - ay;
+    E = dx * (py - ay) - dy * (px - ax);
+    return E > 0 || (E == 0 && (dy < 0 || (dy == 0 && dx > 0)));
+}
+
+// barycentric numerators w[k] (face vertex order) if the centre is covered
+__device__ __forceinline__ bool face_cover(const FaceSetup &s, long long px, long long py,
+                                           long long w[3]) {
+    const int b = s.flip ? 2 : 1, c = s.flip ? 1 : 2;   // oriented order 0, b, c
+    long long e0b, ebc, ec0;
+    if (!edge_in(s.x[0], s.y[0], s.x[b], s.y[b], px, py, e0b)) return false;
+    if (!edge_in(s.x[b], s.y[b], s.x[c], s.y[c], px, py, ebc)) return false;
+    if (!edge_in(s.x[c], s.y[c], s.x[0], s.y[0], px, py, ec0)) return false;
+    w[0] = ebc;   // weight of a vertex: edge function of the opposite edge
+    w[b] = ec0;
+    w[c] = e0b;
+    return true;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(256)
+mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
+                  const unsigned long long *__restrict__ items, const long long *n_items,
+                  unsigned long long *__restrict__ vis) {
+    const long long n = *n_items;
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = warp0; w < n; w += nwarps) {
+        const unsigned long long item = items[w];
+        const long long vf = (long long)(item >> 32);
+        const int tx = (int)(item & 0xFFFFu), ty = (int)((item >> 16) & 0xFFFFu);
+        const int v = (int)(vf / nf);
+        const unsigned f = (unsigned)(vf - (long long)v * nf);
+        const ViewDev &V = vt.v[v];
+        const FaceSetup s = setup[vf];
+        const double area = (double)s.area2;
+#pragma unroll
+        for (int p = lane; p < TW * TH; p += 32) {
+            const int px = tx * TW + (p % TW), py = ty * TH + (p / TW);
+            if (px >= V.W || py >= V.H) continue;
+            long long wgt[3];
+            if (!face_cover(s, (long long)px * 256 + 128, (long long)py * 256 + 128, wgt)) continue;
+            const double S = fma((double)wgt[2], s.iz[2], fma((double)wgt[1], s.iz[1], (double)wgt[0] * s.iz[0]));
+            const float D = __double2float_rn(area / S);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(D) << 32) | f;
+            atomicMin(&vis[V.pix_off + (long long)py * V.W + px], key);
+        }
+    }
+}
+
+template <bool F32TEX>
+__device__ __forceinline__ float texel(const void *tex, int tw, int th, int x, int y, int ch) {
+    x = min(max(x, 0), tw - 1);
+    y = min(max(y, 0), th - 1);
+    const size_t o = ((size_t)y * tw + x) * 3 + ch;
+    if (F32TEX) return __ldg(reinterpret_cast<const float *>(tex) + o);
+    return (float)__ldg(reinterpret_cast<const unsigned char *>(tex) + o) * (1.0f / 255.0f);
+}
+
+template <int TW, int TH, bool F32TEX>
+__global__ void __launch_bounds__(TW *TH)
+mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
+                    const int32_t *__restrict__ faces, const float *__restrict__ uvs,
+                    const void *__restrict__ tex, int tw, int th, float bg0, float bg1, float bg2,
+                    const unsigned long long *__restrict__ vis, int32_t *__restrict__ tri_id,
+                    float *__restrict__ depth, float *__restrict__ rgb, float *__restrict__ uv_out,
+                    float *__restrict__ tile_max) {
+    __shared__ float s_max[TW * TH / 32];
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(vt, gt);
+    const ViewDev &V = vt.v[v];
+    const int local = gt - V.tile_off;
+    const int tx = local % V.tiles_x, ty = local / V.tiles_x;
+    const int t = threadIdx.x;
+    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
+    const bool inside = px < V.W && py < V.H;
+    float D = -INFINITY;   // neutral for the max over in-image pixels
+    if (inside) {
+        const long long npx = (long long)V.W * V.H;
+        const long long lp = (long long)py * V.W + px;
+        const long long gp = V.pix_off + lp;
+        const unsigned long long key = vis[gp];
+        int id = -1;
+        float c0 = bg0, c1 = bg1, c2 = bg2, u = 0.f, w = 0.f;
+        if (key == ~0ull) {
+            D = INFINITY;
+        } else {
+            id = (int)(unsigned)(key & 0xFFFFFFFFu);
+            D = __uint_as_float((unsigned)(key >> 32));
+            const FaceSetup s = setup[(long long)v * nf + id];
+            long long wgt[3];
+            face_cover(s, (long long)px * 256 + 128, (long long)py * 256 + 128, wgt);
+            float b[3], sum = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                b[k] = (float)wgt[k] * (float)s.iz[k];
+                sum += b[k];
+            }
+            const float rs = 1.f / sum;
+            // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
+            // for small faces, so uv keeps close to FP32 rounding of its value
+            const int v0i = faces[3 * (long long)id], v1i = faces[3 * (long long)id + 1],
+                      v2i = faces[3 * (long long)id + 2];
+            const float u0 = __ldg(uvs + 2 * (long long)v0i), w0 = __ldg(uvs + 2 * (long long)v0i + 1);
+            const float b1 = b[1] * rs, b2 = b[2] * rs;
+            u = u0 + fmaf(b1, __ldg(uvs + 2 * (long long)v1i) - u0, b2 * (__ldg(uvs + 2 * (long long)v2i) - u0));
+            w = w0 + fmaf(b1, __ldg(uvs + 2 * (long long)v1i + 1) - w0, b2 * (__ldg(uvs + 2 * (long long)v2i + 1) - w0));
+            const float ss = u * (float)tw - 0.5f, tt = w * (float)th - 0.5f;
+            const float x0 = floorf(ss), y0 = floorf(tt);
+            const float fx = ss - x0, fy = tt - y0;
+            const int ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f), iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
+            const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
+            const float w01 = (1.f - fx) * fy, w11 = fx * fy;
+            float cc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                cc[ch] = w00 * texel<F32TEX>(tex, tw, th, ix, iy, ch) + w10 * texel<F32TEX>(tex, tw, th, ix + 1, iy, ch) +
+                         w01 * texel<F32TEX>(tex, tw, th, ix, iy + 1, ch) + w11 * texel<F32TEX>(tex, tw, th, ix + 1, iy + 1, ch);
+            c0 = cc[0]; c1 = cc[1]; c2 = cc[2];
+        }
+        if (tri_id) tri_id[gp] = id;
+        if (depth) depth[gp] = D;
+        if (rgb) {
+            float *o = rgb + 3 * V.pix_off + lp;
+            o[0] = c0; o[npx] = c1; o[2 * npx] = c2;
+        }
+        if (uv_out) {
+            float *o = uv_out + 2 * V.pix_off + lp;
+            o[0] = u; o[npx] = w;
+        }
+    }
+    // farthest mesh depth of the tile (+inf if any in-image pixel misses)
+    float m = D;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0) s_max[t >> 5] = m;
+    __syncthreads();
+    if (t == 0) {
+        float r = s_max[0];
+        for (int k = 1; k < TW * TH / 32; ++k) r = fmaxf(r, s_max[k]);
+        if (tile_max) tile_max[gt] = r;
+    }
+}
+
+struct RasterWs {
+    int2 *sxy;
+    double *iz;
+    FaceSetup *setup;
+    uint32_t *cnt, *offs;
+    unsigned long long *items, *vis;
+    long long *n_clamped;
+    ScanWs scan;
+};
+
+RasterWs carve(void *ws, long long mv, long long mf, long long cap, long long npix, size_t *bytes) {
+    WsCarver c(ws);
+    RasterWs r;
+    r.sxy = c.take<int2>(mv);
+    r.iz = c.take<double>(mv);
+    r.setup = c.take<FaceSetup>(mf);
+    r.cnt = c.take<uint32_t>(mf);
+    r.offs = c.take<uint32_t>(mf);
+    r.items = c.take<unsigned long long>(cap);
+    r.vis = c.take<unsigned long long>(npix);
+    r.n_clamped = c.take<long long>(1);
+    r.scan.tile_status = c.take<unsigned long long>(scan_tiles(mf) + 1);
+    r.scan.ticket = c.take<unsigned int>(1);
+    *bytes = c.off + 256;
+    return r;
+}
+
+int grid_for(long long work, int threads) {
+    long long g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 148 * 16) g = 148 * 16;
+    return (int)g;
+}
+
+// work items to run: all of them, or none when the capacity was exceeded
+__global__ void clamp_items_kernel(const long long *total, long long capacity, long long *n_out) {
+    long long t = *total;
+    *n_out = t <= capacity ? t : 0;
+}
+
+}  // namespace
+
+}  // namespace hm
+
+using namespace hm;
+
+extern "C" size_t hm_rasterize_mesh_workspace_size(const hm_camera *cams, int32_t n_views,
+                                                   int32_t n_verts, int32_t n_faces,
+                                                   int64_t item_capacity, const hm_options *opt) {
+    ViewTable vt;
+    if (!build_view_table(cams, n_views, opt, &vt) || n_verts < 0 || n_faces < 0 || item_capacity < 0)
+        return 0;
+    size_t bytes = 0;
+    carve(nullptr, (long long)n_views * n_verts, (long long)n_views * n_faces, item_capacity,
+          vt.total_pixels, &bytes);
+    return bytes;
+}
+
+extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, const float *verts,
+                                       const float *uvs, int32_t n_verts, const int32_t *faces,
+                                       int32_t n_faces, const void *tex, int32_t tex_w,
+                                       int32_t tex_h, int32_t tex_format, const hm_options *opt,
+                                       int32_t *tri_id, float *depth, float *rgb, float *uv,
+                                       float *tile_max_depth, int64_t item_capacity,
+                                       int64_t *n_items_out, int32_t *d_status, void *ws,
+                                       size_t ws_bytes, void *stream) {
+    ViewTable vt;
+    if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
+    if (n_verts < 0 || n_faces < 0) return fail(HM_ERR_INVALID_ARG, "negative mesh size");
+    if ((long long)n_views * n_faces >= (1ll << 31) || (long long)n_views * n_verts >= (1ll << 31))
+        return fail(HM_ERR_INVALID_ARG, "mesh too large");
+    if (tex_format != HM_TEX_RGB8 && tex_format != HM_TEX_RGBF32) return fail(HM_ERR_INVALID_ARG, "tex_format");
+    if (tex_w <= 0 || tex_h <= 0 || !tex) return fail(HM_ERR_INVALID_ARG, "texture");
+    if (item_capacity < 0 || item_capacity > HM_MAX_PAIRS) return fail(HM_ERR_INVALID_ARG, "item_capacity");
+    if (!tri_id || !depth || !tile_max_depth || !n_items_out ||
+        (n_faces > 0 && (!verts || !uvs || !faces)))
+        return fail(HM_ERR_INVALID_ARG, "null pointer");
+    const long long mv = (long long)n_views * n_verts, mf = (long long)n_views * n_faces;
+    size_t need = 0;
+    carve(nullptr, mv, mf, item_capacity, vt.total_pixels, &need);
+    if (!ws || ws_bytes < need) return fail(HM_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, need);
+    cudaStream_t s = (cudaStream_t)stream;
+    RasterWs r = carve(ws, mv, mf, item_capacity, vt.total_pixels, &need);
+    cudaError_t e;
+    if (mv > 0) {
+        mesh_vertex_kernel<<<grid_for(mv, 256), 256, 0, s>>>(vt, n_verts, verts, (double)opt->near_mesh, r.sxy, r.iz);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    if (mf > 0) {
+        mesh_face_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_verts, n_faces, faces, r.sxy, r.iz, r.setup, r.cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    e = launch_scan(r.cnt, nullptr, r.offs, mf, (long long *)n_items_out, item_capacity, d_status, r.scan, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    clamp_items_kernel<<<1, 1, 0, s>>>((const long long *)n_items_out, item_capacity, r.n_clamped);
+    if (mf > 0) {
+        mesh_emit_kernel<<<grid_for(mf, 256), 256, 0, s>>>(mf, r.setup, r.cnt, r.offs, item_capacity, r.items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    e = cudaMemsetAsync(r.vis, 0xFF, sizeof(unsigned long long) * (size_t)vt.total_pixels, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long cgrid = item_capacity > 0 ? (item_capacity + 7) / 8 : 1;
+    if (cgrid > (long long)sms * 8) cgrid = (long long)sms * 8;
+    const float *bg = opt->bg;
+    const bool f32 = tex_format == HM_TEX_RGBF32;
+    dim3 tgrid(vt.total_tiles);
+#define HM_RASTER(TW, TH)                                                                               \
+    do {                                                                                                \
+        mesh_cover_kernel<TW, TH><<<(unsigned)cgrid, 256, 0, s>>>(vt, n_faces, r.setup, r.items,       \
+                                                                 r.n_clamped, r.vis);                  \
+        if (f32)                                                                                        \
+            mesh_resolve_kernel<TW, TH, true><<<tgrid, TW * TH, 0, s>>>(                                \
+                vt, n_faces, r.setup, faces, uvs, tex, tex_w, tex_h, bg[0], bg[1], bg[2], r.vis,       \
+                tri_id, depth, rgb, uv, tile_max_depth);                                                \
+        else                                                                                            \
+            mesh_resolve_kernel<TW, TH, false><<<tgrid, TW * TH, 0, s>>>(                               \
+                vt, n_faces, r.setup, faces, uvs, tex, tex_w, tex_h, bg[0], bg[1], bg[2], r.vis,       \
+                tri_id, depth, rgb, uv, tile_max_depth);                                                \
+    } while (0)
+    if (opt->tile_w == 16) HM_RASTER(16, 16);
+    else if (opt->tile_w == 32) HM_RASTER(32, 8);
+    else HM_RASTER(8, 8);
+#undef HM_RASTER
+    return cuda_status(cudaGetLastError());
+}

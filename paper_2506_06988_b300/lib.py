@@ -1,0 +1,207 @@
+"""ctypes binding of libhm.so (the C ABI declared in include/hm.h).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name.  Device buffers are passed as integer addresses (e.g.
+``tensor.data_ptr()``), ``cams``/``opt`` as ctypes structures, the stream as
+an integer ``cudaStream_t``.  Loading raises if the library has not been built
+(``python -m paper_2506_06988_b300.build``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_float, c_int32, c_int64, c_size_t, c_void_p
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhm.so")
+
+HM_OK = 0
+HM_ERR_INVALID_ARG = 1
+HM_ERR_CUDA = 2
+HM_ERR_WORKSPACE = 3
+HM_DEV_CAPACITY = 1
+HM_DEV_TIMEOUT = 2
+HM_MAX_VIEWS = 32
+HM_MAX_PAIRS = 0x3FFFFFFF
+HM_TEX_RGB8 = 0
+HM_TEX_RGBF32 = 1
+HM_SH_F32 = 0
+HM_SH_F16 = 1
+HM_BWD_TEXTURE = 1
+HM_BWD_BLEND = 2
+HM_BWD_PROJECT = 4
+
+EXPORTS = [
+    "hm_default_options", "hm_last_error", "hm_total_tiles",
+    "hm_rasterize_mesh_workspace_size", "hm_rasterize_mesh",
+    "hm_project_gaussians",
+    "hm_bin_sort_workspace_size", "hm_bin_sort",
+    "hm_blend_forward",
+    "hm_blend_backward_workspace_size", "hm_blend_backward",
+]
+
+
+class HmCamera(ctypes.Structure):
+    _fields_ = [("R", c_float * 9), ("t", c_float * 3), ("fx", c_float), ("fy", c_float),
+                ("cx", c_float), ("cy", c_float), ("width", c_int32), ("height", c_int32)]
+
+
+class HmOptions(ctypes.Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32),
+                ("mesh_cull", c_int32), ("near_gauss", c_float), ("near_mesh", c_float),
+                ("bg", c_float * 3), ("bwd_stages", c_int32)]
+
+
+class HmError(RuntimeError):
+    pass
+
+
+_lib = None
+_CAM_P = POINTER(HmCamera)
+_OPT_P = POINTER(HmOptions)
+
+_SIGS = {
+    "hm_default_options": (None, [_OPT_P]),
+    "hm_last_error": (ctypes.c_char_p, []),
+    "hm_total_tiles": (c_int64, [_CAM_P, c_int32, _OPT_P]),
+    "hm_rasterize_mesh_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int32, c_int64, _OPT_P]),
+    "hm_rasterize_mesh": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_int32,
+                                    c_void_p, c_int32, c_int32, c_int32, _OPT_P, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
+                                    c_void_p, c_size_t, c_void_p]),
+    "hm_project_gaussians": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_int32, c_int32, _OPT_P, c_void_p,
+                                       c_void_p]),
+    "hm_bin_sort_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int64, _OPT_P]),
+    "hm_bin_sort": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, _OPT_P, c_void_p,
+                              c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "hm_blend_forward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p]),
+    "hm_blend_backward_workspace_size": (c_size_t, [c_int32, c_int32]),
+    "hm_blend_backward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                    _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_size_t, c_void_p]),
+}
+
+
+def load():
+    """Load libhm.so (raises HmError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise HmError(f"{LIB_PATH} not built: run `python -m paper_2506_06988_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().hm_last_error().decode()
+
+
+def check(status: int, what: str = ""):
+    if status != HM_OK:
+        raise HmError(f"{what}: status {status}: {last_error()}")
+
+
+def cameras(cams) -> ctypes.Array:
+    """Array of HmCamera from objects with R, t, fx, fy, cx, cy, width, height."""
+    arr = (HmCamera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k].R[:] = [float(x) for x in c.R.reshape(9)]
+        arr[k].t[:] = [float(x) for x in c.t.reshape(3)]
+        arr[k].fx, arr[k].fy, arr[k].cx, arr[k].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        arr[k].width, arr[k].height = int(c.width), int(c.height)
+    return arr
+
+
+def options(tile=(16, 16), batch=None, mesh_cull=True, bg=(0.0, 0.0, 0.0), near_gauss=0.2,
+            near_mesh=0.01) -> HmOptions:
+    o = HmOptions()
+    load().hm_default_options(ctypes.byref(o))
+    o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+    o.batch = int(batch) if batch is not None else int(tile[0] * tile[1])
+    o.mesh_cull = int(bool(mesh_cull))
+    o.near_gauss, o.near_mesh = float(near_gauss), float(near_mesh)
+    o.bg[:] = [float(x) for x in bg]
+    return o
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+
+def hm_total_tiles(cams, opt) -> int:
+    return load().hm_total_tiles(cams, len(cams), ctypes.byref(opt))
+
+
+def hm_rasterize_mesh_workspace_size(cams, n_verts, n_faces, item_capacity, opt) -> int:
+    return load().hm_rasterize_mesh_workspace_size(cams, len(cams), n_verts, n_faces, item_capacity,
+                                                   ctypes.byref(opt))
+
+
+def hm_rasterize_mesh(cams, verts, uvs, n_verts, faces, n_faces, tex, tex_w, tex_h, tex_format,
+                      opt, tri_id, depth, rgb, uv, tile_max_depth, item_capacity, n_items_out,
+                      d_status, ws, ws_bytes, stream):
+    return load().hm_rasterize_mesh(cams, len(cams), _ptr(verts), _ptr(uvs), n_verts, _ptr(faces),
+                                    n_faces, _ptr(tex), tex_w, tex_h, tex_format, ctypes.byref(opt),
+                                    _ptr(tri_id), _ptr(depth), _ptr(rgb), _ptr(uv),
+                                    _ptr(tile_max_depth), item_capacity, _ptr(n_items_out),
+                                    _ptr(d_status), _ptr(ws), ws_bytes, stream)
+
+
+def hm_project_gaussians(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format, opt,
+                         records, stream):
+    return load().hm_project_gaussians(cams, len(cams), n, _ptr(means), _ptr(scales), _ptr(quats),
+                                       _ptr(opacity), _ptr(sh), sh_degree, sh_format,
+                                       ctypes.byref(opt), _ptr(records), stream)
+
+
+def hm_bin_sort_workspace_size(cams, n, capacity, opt) -> int:
+    return load().hm_bin_sort_workspace_size(cams, len(cams), n, capacity, ctypes.byref(opt))
+
+
+def hm_bin_sort(cams, n, records, tile_max_depth, opt, pair_vals, capacity, n_pairs_out,
+                tile_ranges, d_status, ws, ws_bytes, stream):
+    return load().hm_bin_sort(cams, len(cams), n, _ptr(records), _ptr(tile_max_depth),
+                              ctypes.byref(opt), _ptr(pair_vals), capacity, _ptr(n_pairs_out),
+                              _ptr(tile_ranges), _ptr(d_status), _ptr(ws), ws_bytes, stream)
+
+
+def hm_blend_forward(cams, n, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, opt, out_rgb,
+                     out_T, n_contrib, last_idx, eval_stats, stream):
+    return load().hm_blend_forward(cams, len(cams), n, _ptr(records), _ptr(pair_vals),
+                                   _ptr(tile_ranges), _ptr(mesh_depth), _ptr(mesh_rgb),
+                                   ctypes.byref(opt), _ptr(out_rgb), _ptr(out_T), _ptr(n_contrib),
+                                   _ptr(last_idx), _ptr(eval_stats), stream)
+
+
+def hm_blend_backward_workspace_size(n_views, n) -> int:
+    return load().hm_blend_backward_workspace_size(n_views, n)
+
+
+def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format, records,
+                      pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w, tex_h, opt,
+                      out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats, d_opacity, d_sh,
+                      d_tex, ws, ws_bytes, stream):
+    return load().hm_blend_backward(cams, len(cams), n, _ptr(means), _ptr(scales), _ptr(quats),
+                                    _ptr(opacity), _ptr(sh), sh_degree, sh_format, _ptr(records),
+                                    _ptr(pair_vals), _ptr(tile_ranges), _ptr(mesh_depth),
+                                    _ptr(mesh_rgb), _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
+                                    _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
+                                    _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacity),
+                                    _ptr(d_sh), _ptr(d_tex), _ptr(ws), ws_bytes, stream)

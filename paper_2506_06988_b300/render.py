@@ -1,0 +1,289 @@
+"""Hybrid mesh-Gaussian rendering on one GPU through the libhm C ABI.
+
+``Renderer`` owns the device buffers for a fixed set of cameras and scene
+sizes and runs the four stages of a frame on the current CUDA stream:
+
+    hm_rasterize_mesh     I_m, D_m, per-tile farthest mesh depth
+    hm_project_gaussians  per (camera, Gaussian) records
+    hm_bin_sort           (tile, depth)-sorted pairs and tile ranges
+    hm_blend_forward      I_h = I_gs + T * back (Eq. 2 with the Sec. 3.4 cut-off)
+
+and ``hm_blend_backward`` for gradients.  PyTorch provides memory and the
+stream; every step of the path runs in libhm's kernels.  ``HybridRender`` is
+the ``torch.autograd.Function`` over it (activations such as exp/sigmoid of
+the raw parameters stay in PyTorch).
+
+Pair and work-item capacities grow on demand: a frame whose device status
+reports HM_DEV_CAPACITY is re-run with the reported need (``render``); the
+asynchronous ``forward`` leaves the check to the caller (``status``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import lib
+
+__all__ = ["MeshInput", "Renderer", "HybridRender"]
+
+
+@dataclass
+class MeshInput:
+    verts: torch.Tensor      # [V,3] f32
+    uvs: torch.Tensor        # [V,2] f32
+    faces: torch.Tensor      # [F,3] i32
+    texture: torch.Tensor    # [H,W,3] u8 or f32
+
+    @property
+    def tex_format(self) -> int:
+        return lib.HM_TEX_RGBF32 if self.texture.dtype == torch.float32 else lib.HM_TEX_RGB8
+
+    @staticmethod
+    def from_numpy(m, device="cuda") -> "MeshInput":
+        return MeshInput(torch.as_tensor(m.verts, dtype=torch.float32, device=device).contiguous(),
+                         torch.as_tensor(m.uvs, dtype=torch.float32, device=device).contiguous(),
+                         torch.as_tensor(m.faces, dtype=torch.int32, device=device).contiguous(),
+                         torch.as_tensor(m.texture, device=device).contiguous())
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Renderer:
+    """Buffers and stage launches for a fixed camera set and scene size.
+
+    Per-pixel outputs (``rgb`` planar per camera, ``T``, ``n_contrib``,
+    ``last_idx``, mesh ``tri_id``/``depth``/``mesh_rgb``/``uv``) are flat
+    tensors over the concatenated pixels of all cameras; ``image(k)`` gives
+    camera k's [3,H,W] view of ``rgb``.
+    """
+
+    def __init__(self, cams, n: int, sh_degree: int, *, sh_f16: bool = False,
+                 n_verts: int = 0, n_faces: int = 0, tex_shape=None, tile=(16, 16),
+                 batch: Optional[int] = None, mesh_cull: bool = True, bg=(0.0, 0.0, 0.0),
+                 pair_capacity: Optional[int] = None, item_capacity: Optional[int] = None,
+                 device="cuda"):
+        lib.load()
+        self.device = torch.device(device)
+        self.cam_list = list(cams)
+        self.cams = lib.cameras(self.cam_list)
+        self.V = len(self.cam_list)
+        self.n = int(n)
+        self.sh_degree = int(sh_degree)
+        self.K = (self.sh_degree + 1) ** 2
+        self.sh_format = lib.HM_SH_F16 if sh_f16 else lib.HM_SH_F32
+        self.opt = lib.options(tile=tile, batch=batch, mesh_cull=mesh_cull, bg=bg)
+        self.bg = tuple(float(x) for x in bg)
+        self.sizes = [(int(c.width), int(c.height)) for c in self.cam_list]
+        self.pix_off = np.concatenate([[0], np.cumsum([w * h for w, h in self.sizes])]).astype(np.int64)
+        self.npix = int(self.pix_off[-1])
+        self.ntiles = lib.hm_total_tiles(self.cams, self.opt)
+        if self.ntiles < 0:
+            raise lib.HmError(lib.last_error())
+        self.n_verts, self.n_faces = int(n_verts), int(n_faces)
+        self.has_mesh = self.n_faces > 0 or tex_shape is not None
+        self.tex_shape = tuple(tex_shape) if tex_shape is not None else None
+        d = self.device
+        f32, i32 = torch.float32, torch.int32
+        M = self.V * self.n
+        self.records = torch.empty(max(M, 1) * 12, dtype=f32, device=d)
+        self.ranges = torch.empty(2 * self.ntiles, dtype=i32, device=d)
+        self.n_pairs = torch.zeros(1, dtype=torch.int64, device=d)
+        self.n_items = torch.zeros(1, dtype=torch.int64, device=d)
+        self.status_word = torch.zeros(1, dtype=i32, device=d)
+        self.rgb = torch.empty(3 * self.npix, dtype=f32, device=d)
+        self.T = torch.empty(self.npix, dtype=f32, device=d)
+        self.n_contrib = torch.empty(self.npix, dtype=i32, device=d)
+        self.last_idx = torch.empty(self.npix, dtype=i32, device=d)
+        if self.has_mesh:
+            self.tri_id = torch.empty(self.npix, dtype=i32, device=d)
+            self.mesh_depth = torch.empty(self.npix, dtype=f32, device=d)
+            self.mesh_rgb = torch.empty(3 * self.npix, dtype=f32, device=d)
+            self.uv = torch.empty(2 * self.npix, dtype=f32, device=d)
+            self.tile_max = torch.empty(self.ntiles, dtype=f32, device=d)
+        else:
+            self.tri_id = self.mesh_depth = self.mesh_rgb = self.uv = self.tile_max = None
+        self._pair_cap = 0
+        self._item_cap = 0
+        self.set_pair_capacity(pair_capacity if pair_capacity else max(1024, 8 * M))
+        if self.has_mesh:
+            self.set_item_capacity(item_capacity if item_capacity else max(1024, 4 * self.V * self.n_faces))
+        self.bwd_ws = None
+
+    # -- capacities -------------------------------------------------------------
+    def set_pair_capacity(self, cap: int):
+        cap = int(min(max(cap, 1024), lib.HM_MAX_PAIRS))
+        self._pair_cap = cap
+        self.pair_vals = torch.empty(cap, dtype=torch.int32, device=self.device)
+        nb = lib.hm_bin_sort_workspace_size(self.cams, self.n, cap, self.opt)
+        self.bin_ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+
+    def set_item_capacity(self, cap: int):
+        cap = int(min(max(cap, 1024), lib.HM_MAX_PAIRS))
+        self._item_cap = cap
+        nb = lib.hm_rasterize_mesh_workspace_size(self.cams, self.n_verts, self.n_faces, cap, self.opt)
+        self.raster_ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+
+    @property
+    def pair_capacity(self) -> int:
+        return self._pair_cap
+
+    # -- stages -----------------------------------------------------------------
+    def rasterize_mesh(self, mesh: MeshInput):
+        s = _stream()
+        th, tw = mesh.texture.shape[:2]
+        lib.check(lib.hm_rasterize_mesh(self.cams, mesh.verts, mesh.uvs, self.n_verts, mesh.faces,
+                                        self.n_faces, mesh.texture, tw, th, mesh.tex_format,
+                                        self.opt, self.tri_id, self.mesh_depth, self.mesh_rgb,
+                                        self.uv, self.tile_max, self._item_cap, self.n_items,
+                                        self.status_word, self.raster_ws, self.raster_ws.numel(), s),
+                  "hm_rasterize_mesh")
+
+    def project(self, means, scales, quats, opacity, sh):
+        lib.check(lib.hm_project_gaussians(self.cams, self.n, means, scales, quats, opacity, sh,
+                                           self.sh_degree, self.sh_format, self.opt, self.records,
+                                           _stream()), "hm_project_gaussians")
+
+    def bin_sort(self):
+        tmax = self.tile_max if self.has_mesh else None
+        lib.check(lib.hm_bin_sort(self.cams, self.n, self.records, tmax, self.opt, self.pair_vals,
+                                  self._pair_cap, self.n_pairs, self.ranges, self.status_word,
+                                  self.bin_ws, self.bin_ws.numel(), _stream()), "hm_bin_sort")
+
+    def blend(self, eval_stats: Optional[torch.Tensor] = None):
+        md = self.mesh_depth if self.has_mesh else None
+        mr = self.mesh_rgb if self.has_mesh else None
+        lib.check(lib.hm_blend_forward(self.cams, self.n, self.records, self.pair_vals, self.ranges,
+                                       md, mr, self.opt, self.rgb, self.T, self.n_contrib,
+                                       self.last_idx, eval_stats, _stream()), "hm_blend_forward")
+
+    def count_evaluations(self):
+        """Re-run the blend of the last frame with the evaluation counters:
+        (alpha evaluations, list entries examined) -- synchronises."""
+        st = torch.zeros(2, dtype=torch.int64, device=self.device)
+        self.blend(st)
+        v = st.cpu().tolist()
+        return int(v[0]), int(v[1])
+
+    def forward(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None):
+        """All four stages, asynchronously on the current stream."""
+        self.status_word.zero_()
+        if self.has_mesh:
+            self.rasterize_mesh(mesh)
+        self.project(means, scales, quats, opacity, sh)
+        self.bin_sort()
+        self.blend()
+
+    def status(self):
+        """(status bits, pair count, mesh work items) -- synchronises."""
+        st, npairs, nitems = int(self.status_word.item()), int(self.n_pairs.item()), int(self.n_items.item())
+        return st, npairs, nitems
+
+    def render(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None,
+               max_retries: int = 3):
+        """forward() plus the capacity check; grows the buffers and re-runs
+        when a capacity was exceeded.  Raises on HM_DEV_TIMEOUT."""
+        for _ in range(max_retries + 1):
+            self.forward(means, scales, quats, opacity, sh, mesh)
+            st, npairs, nitems = self.status()
+            if st & lib.HM_DEV_TIMEOUT:
+                raise lib.HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
+            if not st & lib.HM_DEV_CAPACITY:
+                return self
+            if npairs > self._pair_cap:
+                self.set_pair_capacity(int(npairs * 1.25) + 1024)
+            if self.has_mesh and nitems > self._item_cap:
+                self.set_item_capacity(int(nitems * 1.25) + 1024)
+        raise lib.HmError("capacity retries exhausted")
+
+    def grad_buffers(self, tex_shape=None):
+        d = self.device
+        g = dict(means=torch.zeros(self.n, 3, device=d), scales=torch.zeros(self.n, 3, device=d),
+                 quats=torch.zeros(self.n, 4, device=d), opacity=torch.zeros(self.n, device=d),
+                 sh=torch.zeros(self.n, self.K, 3, device=d))
+        if tex_shape is not None:
+            g["texture"] = torch.zeros(tex_shape[0], tex_shape[1], 3, device=d)
+        return g
+
+    def backward(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT=None,
+                 mesh: Optional[MeshInput] = None, tex_grad: bool = False, out=None,
+                 stages: int = 0, zero: bool = True):
+        """Gradients of the last forward, accumulated into fresh zero tensors
+        (or into ``out``, a dict from ``grad_buffers``, zeroed first unless
+        ``zero`` is False).  ``stages``: HM_BWD_* bits to run (0 = all)."""
+        d = self.device
+        if self.bwd_ws is None:
+            self.bwd_ws = torch.empty(lib.hm_blend_backward_workspace_size(self.V, self.n),
+                                      dtype=torch.uint8, device=d)
+        want_tex = tex_grad and self.has_mesh
+        if out is None:
+            g = self.grad_buffers(mesh.texture.shape[:2] if want_tex else None)
+        else:
+            g = out
+            if zero:
+                for v in g.values():
+                    v.zero_()
+        d_tex = None
+        tw = th = 0
+        if want_tex:
+            th, tw = mesh.texture.shape[:2]
+            d_tex = g["texture"]
+        self.opt.bwd_stages = int(stages)
+        lib.check(lib.hm_blend_backward(
+            self.cams, self.n, means, scales, quats, opacity, sh, self.sh_degree, self.sh_format,
+            self.records, self.pair_vals, self.ranges,
+            self.mesh_depth if self.has_mesh else None, self.mesh_rgb if self.has_mesh else None,
+            self.uv if self.has_mesh else None, tw, th, self.opt, self.T, self.last_idx,
+            dL_drgb.contiguous(), None if dL_dT is None else dL_dT.contiguous(),
+            g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], d_tex,
+            self.bwd_ws, self.bwd_ws.numel(), _stream()), "hm_blend_backward")
+        return g
+
+    # -- views of the outputs -------------------------------------------------------
+    def image(self, k: int, which: str = "rgb") -> torch.Tensor:
+        w, h = self.sizes[k]
+        a, b = int(self.pix_off[k]), int(self.pix_off[k + 1])
+        if which == "rgb":
+            return self.rgb[3 * a:3 * b].view(3, h, w)
+        if which == "mesh_rgb":
+            return self.mesh_rgb[3 * a:3 * b].view(3, h, w)
+        if which == "uv":
+            return self.uv[2 * a:2 * b].view(2, h, w)
+        return getattr(self, which)[a:b].view(h, w)
+
+    def records_view(self) -> torch.Tensor:
+        return self.records[: self.V * self.n * 12].view(self.V * self.n, 12)
+
+
+class HybridRender(torch.autograd.Function):
+    """(means, scales, quats, opacity, sh[, texture]) -> (rgb, T) over all
+    cameras of ``renderer`` (flat, as ``Renderer.rgb`` / ``Renderer.T``).
+    The texture gets a gradient when it is float32 and requires grad."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, mesh: Optional[MeshInput], means, scales, quats, opacity,
+                sh, texture=None):
+        if mesh is not None and texture is not None:
+            mesh = MeshInput(mesh.verts, mesh.uvs, mesh.faces, texture)
+        means, scales, opacity = means.contiguous(), scales.contiguous(), opacity.contiguous()
+        quats, sh = quats.contiguous(), sh.contiguous()
+        renderer.render(means, scales, quats, opacity, sh, mesh)
+        ctx.renderer = renderer
+        ctx.mesh = mesh
+        ctx.tex_grad = texture is not None and texture.requires_grad
+        ctx.save_for_backward(means, scales, quats, opacity, sh)
+        return renderer.rgb.clone(), renderer.T.clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_T):
+        means, scales, quats, opacity, sh = ctx.saved_tensors
+        r: Renderer = ctx.renderer
+        g = r.backward(means, scales, quats, opacity, sh, g_rgb if g_rgb is not None else torch.zeros_like(r.rgb),
+                       g_T, mesh=ctx.mesh, tex_grad=ctx.tex_grad)
+        d_sh = g["sh"].to(sh.dtype) if sh.dtype != torch.float32 else g["sh"]
+        return (None, None, g["means"], g["scales"], g["quats"], g["opacity"], d_sh,
+                g.get("texture") if ctx.tex_grad else None)

@@ -1,0 +1,141 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and
+the oracle on the same seeded inputs, and compare them.
+
+Tolerances (derived in the design notes):
+* mesh tri_id, mesh depth, Gaussian depth keys, sorted pair lists, tile
+  ranges and per-pixel Gaussian counts are compared bit-exactly;
+* images and T within 1e-4 absolute per channel;
+* threshold decisions (3-sigma cut, alpha >= 1/255, T >= 1e-4) are taken in
+  FP32 on the GPU and FP64 in the oracle; a pixel whose oracle decisions lie
+  within a relative margin EPS of a threshold is "ambiguous": it is excluded
+  from the exact checks, checked for validity (count within the number of
+  ambiguous decisions, colour within the effect of those decisions), and
+  the fraction of such pixels is bounded.
+"""
+from __future__ import annotations
+
+from types import SimpleNamespace
+
+import numpy as np
+import torch
+
+from oracle import oracle as O
+from paper_2506_06988_b300 import lib
+from paper_2506_06988_b300.render import MeshInput, Renderer
+
+EPS = 2e-4
+IMG_TOL = 1e-4
+
+
+def gaussians_to_torch(g, device="cuda"):
+    t = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), device=device).to(dt)  # noqa: E731
+    sh = torch.as_tensor(np.ascontiguousarray(g.sh), device=device)
+    return dict(means=t(g.means), scales=t(g.scales), quats=t(g.quats), opacity=t(g.opacity), sh=sh)
+
+
+def make_renderer(scene, tile=(16, 16), batch=None, mesh_cull=True, views=None, **kw):
+    cams = scene.cameras if views is None else [scene.cameras[v] for v in views]
+    g = scene.gaussians
+    m = scene.mesh
+    return Renderer(cams, g.n, g.sh_degree, sh_f16=(np.asarray(g.sh).dtype == np.float16),
+                    n_verts=0 if m is None else len(m.verts), n_faces=0 if m is None else len(m.faces),
+                    tex_shape=None if m is None else m.texture.shape, tile=tile, batch=batch,
+                    mesh_cull=mesh_cull, bg=tuple(np.asarray(scene.bg, np.float64)), **kw)
+
+
+def gpu_render(scene, tile=(16, 16), batch=None, mesh_cull=True, views=None, **kw):
+    r = make_renderer(scene, tile, batch, mesh_cull, views, **kw)
+    P = gaussians_to_torch(scene.gaussians)
+    mesh = MeshInput.from_numpy(scene.mesh) if scene.mesh is not None else None
+    r.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh)
+    torch.cuda.synchronize()
+    return r, P, mesh
+
+
+def view_outputs(r: Renderer, k: int):
+    """numpy outputs of camera k (flat per pixel; rgb planar [3, npix])."""
+    w, h = r.sizes[k]
+    a, b = int(r.pix_off[k]), int(r.pix_off[k + 1])
+    out = SimpleNamespace(
+        rgb=r.rgb[3 * a:3 * b].view(3, -1).cpu().numpy().astype(np.float64),
+        T=r.T[a:b].cpu().numpy().astype(np.float64),
+        n_contrib=r.n_contrib[a:b].cpu().numpy(),
+        last_idx=r.last_idx[a:b].cpu().numpy())
+    if r.has_mesh:
+        out.tri_id = r.tri_id[a:b].cpu().numpy()
+        out.depth = r.mesh_depth[a:b].cpu().numpy()
+        out.mesh_rgb = r.mesh_rgb[3 * a:3 * b].view(3, -1).cpu().numpy().astype(np.float64)
+        out.uv = r.uv[2 * a:2 * b].view(2, -1).cpu().numpy().astype(np.float64)
+    return out
+
+
+def compare_blend(gout, orc, pix=None, eps=EPS, tol=IMG_TOL):
+    """Returns a dict of statistics; raises AssertionError on a failure."""
+    o = orc.out
+    if pix is None:
+        pix = np.arange(len(o.T))
+        g_rgb, g_T, g_n = gout.rgb, gout.T, gout.n_contrib
+    else:
+        g_rgb, g_T, g_n = gout.rgb[:, pix], gout.T[pix], gout.n_contrib[pix]
+    amb = o.margin < eps
+    ok = ~amb
+    d_rgb = np.abs(g_rgb - o.rgb).max(0)
+    d_T = np.abs(g_T - o.T)
+    n_bad = int((g_n[ok] != o.n_contrib[ok]).sum())
+    stats = dict(pixels=len(pix), ambiguous=int(amb.sum()), amb_frac=float(amb.mean()),
+                 max_rgb_err=float(d_rgb[ok].max()) if ok.any() else 0.0,
+                 max_T_err=float(d_T[ok].max()) if ok.any() else 0.0,
+                 count_mismatch=n_bad)
+    if n_bad:
+        bad = np.nonzero(ok & (g_n != o.n_contrib))[0]
+        stats["bad_margins"] = o.margin[bad][:10].tolist()
+    assert n_bad == 0, stats
+    assert stats["max_rgb_err"] <= tol, stats
+    assert stats["max_T_err"] <= tol, stats
+    if amb.any():
+        # the ambiguous pixels: a valid outcome of flipping ambiguous decisions
+        assert np.all(np.abs(g_n[amb].astype(np.int64) - o.n_contrib[amb]) <= o.n_amb[amb]), stats
+        assert d_rgb[amb].max() <= 0.05 * np.maximum(1, o.n_amb[amb]).max(), stats
+    return stats
+
+
+def oracle_view(scene, view, pix=None, mode="brute"):
+    return O.render(scene, view, pix=pix, mode=mode)
+
+
+def records_np(r: Renderer):
+    rec = r.records_view().cpu().numpy()
+    u32 = rec.view(np.uint32)
+    return SimpleNamespace(mean=rec[:, 0:2].astype(np.float64), conic=rec[:, [2, 3, 4]].astype(np.float64),
+                           opacity=rec[:, 5], depth=rec[:, 6], color=rec[:, 8:11].astype(np.float64),
+                           x0=u32[:, 7] & 0xFFFF, x1=u32[:, 7] >> 16, y0=u32[:, 11] & 0xFFFF,
+                           y1=u32[:, 11] >> 16)
+
+
+def expected_pairs(r: Renderer, rec, tile_max=None):
+    """Per global tile, the record indices a correct bin/sort must list:
+    records whose tile range covers the tile (and, with the cull, whose depth
+    is below the tile's farthest mesh depth), ordered by (depth, index)."""
+    V, n = r.V, r.n
+    lists = [[] for _ in range(r.ntiles)]
+    tw, th = r.opt.tile_w, r.opt.tile_h
+    tile_off = 0
+    for v in range(V):
+        w, h = r.sizes[v]
+        tx_n = (w + tw - 1) // tw
+        ty_n = (h + th - 1) // th
+        for i in range(n):
+            it = v * n + i
+            x0, x1, y0, y1 = int(rec.x0[it]), int(rec.x1[it]), int(rec.y0[it]), int(rec.y1[it])
+            if x0 > x1 or y0 > y1:
+                continue
+            for ty in range(y0, y1 + 1):
+                for tx in range(x0, x1 + 1):
+                    gt = tile_off + ty * tx_n + tx
+                    if tile_max is not None and not (rec.depth[it] < tile_max[gt]):
+                        continue
+                    lists[gt].append(it)
+        tile_off += tx_n * ty_n
+    for gt in range(r.ntiles):
+        lists[gt].sort(key=lambda it: (rec.depth[it], it))
+    return lists

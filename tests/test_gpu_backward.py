@@ -1,0 +1,131 @@
+"""GPU gradients (hm_blend_backward through the C ABI, and the autograd
+Function on top) against the FP64 gradient oracle (autograd through the
+plain restatement, itself pinned to finite differences of the C oracle).
+
+Relative error bound 1e-3: per gradient tensor, ||g_gpu - g_ref|| <= 1e-3
+||g_ref||, and per element |g_gpu - g_ref| <= 1e-3 |g_ref| + 1e-4 max|g_ref|
+(the floor absorbs FP32 atomic accumulation order on near-cancelling sums).
+Pixels whose forward decisions are ambiguous between FP32 and FP64 get a zero
+upstream gradient, so both sides differentiate the same discrete branch."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import torch_ref as TR
+from paper_2506_06988_b300 import scenes
+from paper_2506_06988_b300.render import HybridRender, MeshInput
+
+from gpu_util import EPS, gpu_render, gaussians_to_torch, make_renderer  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(name, g, ref, rel=1e-3, floor=1e-4):
+    g = np.asarray(g, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    nref = np.linalg.norm(ref)
+    assert nref > 0, name
+    norm_err = np.linalg.norm(g - ref) / nref
+    el = np.abs(g - ref) <= rel * np.abs(ref) + floor * np.abs(ref).max()
+    assert norm_err <= rel, (name, norm_err)
+    assert el.all(), (name, int((~el).sum()), float(np.abs(g - ref).max()))
+    return norm_err
+
+
+def _run(scene, tex_grad, seed=0):
+    cam = scene.cameras[0]
+    npx = cam.n_pixels
+    rng = np.random.default_rng(seed)
+    gI = rng.standard_normal((3, npx))
+    gT = rng.standard_normal(npx)
+    orc = O.render(scene)
+    amb = orc.out.margin < EPS
+    gI[:, amb] = 0.0
+    gT[amb] = 0.0
+    tex = O.texture_unit(scene.mesh.texture) if scene.mesh is not None else None
+    _, ref = TR.render_grad(scene, 0, gI, gT, tex=tex)
+    r, P, mesh = gpu_render(scene)
+    g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"],
+                   torch.as_tensor(gI.reshape(-1), dtype=torch.float32, device="cuda"),
+                   torch.as_tensor(gT, dtype=torch.float32, device="cuda"), mesh=mesh, tex_grad=tex_grad)
+    torch.cuda.synchronize()
+    errs = {}
+    for k in ("means", "scales", "quats", "opacity", "sh"):
+        errs[k] = _check(k, g[k].cpu().numpy(), ref[k])
+    if tex_grad:
+        # (a) against the oracle: norm-relative only -- the GPU's UVs are FP32
+        # (half an ulp of u is ~6e-5 texel at 2048 texels), which moves
+        # individual bilinear weights by that much
+        gt = g["texture"].cpu().numpy().astype(np.float64)
+        errs["texture"] = float(np.linalg.norm(gt - ref["texture"]) / np.linalg.norm(ref["texture"]))
+        assert errs["texture"] <= 1e-3, errs
+        # (b) the texel scatter itself, exactly: FP64 scatter of T * w * dL/dI
+        # from the GPU's own uv and T
+        uv = r.uv.view(2, -1).cpu().numpy().astype(np.float64)
+        T = r.T.cpu().numpy().astype(np.float64)
+        hit = np.isfinite(r.mesh_depth.cpu().numpy())
+        th, tw = scene.mesh.texture.shape[:2]
+        want = np.zeros((th, tw, 3))
+        s_ = uv[0] * np.float32(tw) - 0.5
+        t_ = uv[1] * np.float32(th) - 0.5
+        x0, y0 = np.floor(s_), np.floor(t_)
+        fx, fy = s_ - x0, t_ - y0
+        for dx, dy, w in ((0, 0, (1 - fx) * (1 - fy)), (1, 0, fx * (1 - fy)), (0, 1, (1 - fx) * fy), (1, 1, fx * fy)):
+            xi = np.clip(x0 + dx, 0, tw - 1).astype(np.int64)
+            yi = np.clip(y0 + dy, 0, th - 1).astype(np.int64)
+            for ch in range(3):
+                np.add.at(want[:, :, ch], (yi[hit], xi[hit]), (T * w * gI[ch])[hit])
+        _check("texture_scatter", gt, want, rel=1e-4, floor=1e-6)
+    return errs
+
+
+def test_backward_config0_hybrid_with_texture():
+    s = scenes.config0_scene(seed=0)
+    s.bg = np.array([0.2, 0.3, 0.4], np.float32)
+    print(_run(s, tex_grad=True))
+
+
+def test_backward_sh3_gaussian_only():
+    s = scenes.config0_scene(seed=2, n=800)
+    rng = np.random.default_rng(5)
+    s.gaussians.sh = rng.normal(0.0, 0.2, (s.gaussians.n, 16, 3)).astype(np.float32)
+    s.gaussians.sh_degree = 3
+    s.mesh = None
+    s.bg = np.array([0.5, 0.25, 0.1], np.float32)
+    print(_run(s, tex_grad=False, seed=1))
+
+
+def test_backward_room_sh3_hybrid():
+    s = scenes.room_scene(21, n_tris=3000, n_gauss=5000, resolutions=((128, 96),))
+    print(_run(s, tex_grad=True, seed=2))
+
+
+def test_autograd_function_matches_direct_backward():
+    """HybridRender (torch.autograd.Function) with activations in PyTorch:
+    gradients of an L1 loss equal the direct C-ABI backward chained through
+    exp/sigmoid by hand."""
+    s = scenes.config0_scene(seed=1)
+    s.mesh.texture = s.mesh.texture.astype(np.float32) / 255.0
+    r = make_renderer(s)
+    P = gaussians_to_torch(s.gaussians)
+    mesh = MeshInput.from_numpy(s.mesh)
+    log_s = torch.log(P["scales"]).requires_grad_()
+    logit = torch.logit(P["opacity"]).requires_grad_()
+    means = P["means"].clone().requires_grad_()
+    quats = P["quats"].clone().requires_grad_()
+    sh = P["sh"].clone().requires_grad_()
+    tex = mesh.texture.clone().requires_grad_()
+    target = torch.rand(3 * s.cameras[0].n_pixels, device="cuda")
+    rgb, T = HybridRender.apply(r, mesh, means, torch.exp(log_s), quats, torch.sigmoid(logit), sh, tex)
+    loss = (rgb - target).abs().mean()
+    loss.backward()
+    dI = torch.sign(rgb.detach() - target) / rgb.numel()
+    r.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], MeshInput(mesh.verts, mesh.uvs, mesh.faces, tex.detach()))
+    g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, None,
+                   mesh=MeshInput(mesh.verts, mesh.uvs, mesh.faces, tex.detach()), tex_grad=True)
+    torch.testing.assert_close(means.grad, g["means"], rtol=1e-5, atol=1e-9)
+    torch.testing.assert_close(log_s.grad, g["scales"] * P["scales"], rtol=1e-5, atol=1e-9)
+    op = P["opacity"]
+    torch.testing.assert_close(logit.grad, g["opacity"] * op * (1 - op), rtol=1e-5, atol=1e-9)
+    torch.testing.assert_close(tex.grad, g["texture"], rtol=1e-5, atol=1e-9)

@@ -1,0 +1,260 @@
+"""GPU parity of the forward path (called through the C ABI) against the
+CPU FP64 oracle on seeded inputs: mesh pass, projection, bin/sort, blend."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2506_06988_b300 import lib, scenes
+from paper_2506_06988_b300.render import MeshInput
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import (EPS, compare_blend, expected_pairs, gpu_render, oracle_view,  # noqa: E402
+                      records_np, view_outputs)
+
+
+def _small_room(seed=11, res=((160, 120),), n_gauss=6000, n_tris=3000, **kw):
+    return scenes.room_scene(seed, n_tris=n_tris, n_gauss=n_gauss, resolutions=res,
+                             focal_per_width=1100.0 / 1920.0, **kw)
+
+
+# ------------------------------------------------------------------- mesh --
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 8)])
+def test_mesh_raster_config0_bit_exact(tile):
+    s = scenes.config0_scene()
+    r, _, _ = gpu_render(s, tile=tile)
+    g = view_outputs(r, 0)
+    m = O.mesh_raster(s.cameras[0], s.mesh, bg=s.bg)
+    assert np.array_equal(g.tri_id, m.tri_id)
+    assert np.array_equal(g.depth, m.depth)
+    assert np.abs(g.mesh_rgb - m.rgb).max() < 1e-5
+    assert np.abs(g.uv - m.uv).max() < 1e-6
+
+
+def test_mesh_raster_room_multiview_ragged():
+    """Room mesh (grazing walls, pruned holes -> misses), two cameras of
+    different ragged sizes in one call; tile max depth per tile."""
+    s = _small_room(res=((173, 131), (96, 50)))
+    r, _, _ = gpu_render(s, tile=(16, 16))
+    tmax = r.tile_max.cpu().numpy()
+    toff = 0
+    for v, cam in enumerate(s.cameras):
+        g = view_outputs(r, v)
+        m = O.mesh_raster(cam, s.mesh, bg=s.bg)
+        assert np.array_equal(g.tri_id, m.tri_id)
+        assert np.array_equal(g.depth, m.depth)
+        hit = m.tri_id >= 0
+        assert 0.3 < hit.mean() < 1.0
+        assert np.abs(g.mesh_rgb - m.rgb).max() < 1e-4
+        W, H = cam.width, cam.height
+        tx_n, ty_n = (W + 15) // 16, (H + 15) // 16
+        D = m.depth.reshape(H, W)
+        for ty in range(ty_n):
+            for tx in range(tx_n):
+                blk = D[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
+                assert tmax[toff + ty * tx_n + tx] == blk.max()
+        toff += tx_n * ty_n
+
+
+def test_mesh_f32_texture_and_background():
+    s = scenes.micro_quad_only()
+    s.mesh.texture = (s.mesh.texture.astype(np.float32) / 255.0) ** 2
+    s.mesh.verts[:2, 2] = 6.0          # tilt: perspective-correct UVs matter
+    s.bg = np.array([0.2, 0.4, 0.6], np.float32)
+    r, _, _ = gpu_render(s)
+    g = view_outputs(r, 0)
+    m = O.mesh_raster(s.cameras[0], s.mesh, bg=s.bg)
+    assert np.array_equal(g.tri_id, m.tri_id)
+    assert np.array_equal(g.depth, m.depth)
+    assert np.abs(g.mesh_rgb - m.rgb).max() < 1e-5
+
+
+# ------------------------------------------------------------- projection --
+
+def test_projection_records_match_oracle():
+    s = _small_room(res=((160, 120), (200, 90)), n_gauss=4000)
+    r, _, _ = gpu_render(s)
+    rec = records_np(r)
+    n = s.gaussians.n
+    for v, cam in enumerate(s.cameras):
+        p = O.project(cam, s.gaussians)
+        sl = slice(v * n, (v + 1) * n)
+        assert np.array_equal(rec.depth[sl], p.depth)            # depth key bit-exact
+        vis = p.visible.astype(bool)
+        on = vis & (rec.x0[sl] <= rec.x1[sl])
+        m_err = np.abs(rec.mean[sl][on] - p.mean2d[on])
+        assert (m_err <= 4e-7 * np.abs(p.mean2d[on]) + 1e-5).all(), m_err.max()
+        scale = np.sqrt(np.abs(p.conic[on, 0] * p.conic[on, 2]))
+        c_err = np.abs(rec.conic[sl][on] - p.conic[on]) / scale[:, None]
+        assert c_err.max() < 1e-4, c_err.max()
+        assert np.abs(rec.color[sl][on] - p.color[on]).max() < 1e-5
+        assert np.array_equal(rec.opacity[sl], s.gaussians.opacity)
+        # tile rectangle covers the oracle's 3-sigma bounding box
+        hx = 3 * np.sqrt(p.cov2d[on, 0])
+        hy = 3 * np.sqrt(p.cov2d[on, 2])
+        xs0 = np.clip(np.ceil(p.mean2d[on, 0] - hx - 0.5), 0, cam.width - 1) // 16
+        xs1 = np.clip(np.floor(p.mean2d[on, 0] + hx - 0.5), 0, cam.width - 1) // 16
+        assert (rec.x0[sl][on] <= xs0).all() and (rec.x1[sl][on] >= xs1).all()
+        ys0 = np.clip(np.ceil(p.mean2d[on, 1] - hy - 0.5), 0, cam.height - 1) // 16
+        ys1 = np.clip(np.floor(p.mean2d[on, 1] + hy - 0.5), 0, cam.height - 1) // 16
+        assert (rec.y0[sl][on] <= ys0).all() and (rec.y1[sl][on] >= ys1).all()
+        # culled (behind the near plane) records carry an empty range
+        assert (rec.x0[sl][~vis] > rec.x1[sl][~vis]).all()
+
+
+# --------------------------------------------------------------- bin/sort --
+
+@pytest.mark.parametrize("cull", [True, False])
+def test_bin_sort_lists_exact(cull):
+    s = _small_room(res=((160, 120), (96, 64)), n_gauss=3000)
+    r, _, _ = gpu_render(s, mesh_cull=cull)
+    rec = records_np(r)
+    tmax = r.tile_max.cpu().numpy() if cull else None
+    want = expected_pairs(r, rec, tmax)
+    ranges = r.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    vals = r.pair_vals.cpu().numpy().astype(np.int64)
+    total = sum(len(l) for l in want)
+    assert int(r.n_pairs.item()) == total
+    for gt, lst in enumerate(want):
+        b, e = ranges[gt]
+        assert e - b == len(lst), gt
+        assert vals[b:e].tolist() == lst, gt
+
+
+def test_bin_sort_capacity_overflow_reports_need_then_recovers():
+    s = _small_room(n_gauss=3000)
+    r, P, mesh = gpu_render(s)
+    need = int(r.n_pairs.item())
+    small = type(r)(s.cameras, s.gaussians.n, s.gaussians.sh_degree, n_verts=len(s.mesh.verts),
+                    n_faces=len(s.mesh.faces), tex_shape=s.mesh.texture.shape, pair_capacity=1024)
+    small.forward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh)
+    st, npairs, _ = small.status()
+    assert need > 1024
+    assert st & lib.HM_DEV_CAPACITY and npairs == need
+    small.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh)
+    assert small.pair_capacity >= need
+    assert torch.equal(small.rgb, r.rgb)
+
+
+# ------------------------------------------------------------------ blend --
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 256), ((16, 16), 32), ((32, 8), 64),
+                                        ((8, 8), 64), ((8, 8), 32)])
+def test_hybrid_render_config0(tile, batch):
+    s = scenes.config0_scene()
+    r, _, _ = gpu_render(s, tile=tile, batch=batch)
+    st = compare_blend(view_outputs(r, 0), oracle_view(s, 0))
+    assert st["amb_frac"] < 0.01
+    print(st)
+
+
+def test_hybrid_render_is_tile_shape_invariant():
+    s = scenes.config0_scene(seed=4)
+    outs = []
+    for tile in ((16, 16), (32, 8), (8, 8)):
+        r, _, _ = gpu_render(s, tile=tile)
+        outs.append(view_outputs(r, 0))
+    for o in outs[1:]:
+        assert np.array_equal(o.n_contrib, outs[0].n_contrib)
+        assert np.abs(o.rgb - outs[0].rgb).max() < 1e-6
+
+
+def test_mesh_cull_does_not_change_the_image():
+    s = _small_room(n_gauss=8000)
+    a, _, _ = gpu_render(s, mesh_cull=True)
+    b, _, _ = gpu_render(s, mesh_cull=False)
+    assert int(a.n_pairs.item()) < int(b.n_pairs.item())
+    assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T, b.T) and torch.equal(a.n_contrib, b.n_contrib)
+
+
+def test_hybrid_render_room_multiview():
+    s = _small_room(seed=3, res=((160, 120), (123, 77), (64, 200)), n_gauss=20000)
+    s.bg = np.array([0.1, 0.2, 0.3], np.float32)
+    r, _, _ = gpu_render(s)
+    for v in range(3):
+        st = compare_blend(view_outputs(r, v), oracle_view(s, v, mode="grid"))
+        assert st["amb_frac"] < 0.01, st
+        print(v, st)
+
+
+def test_gaussian_only_scene_no_mesh():
+    s = _small_room(seed=5, with_mesh=False, n_gauss=20000)
+    s.bg = np.array([0.3, 0.3, 0.3], np.float32)
+    r, _, _ = gpu_render(s)
+    st = compare_blend(view_outputs(r, 0), oracle_view(s, 0, mode="grid"))
+    assert st["amb_frac"] < 0.01
+
+
+def test_sh_fp16_storage():
+    s = _small_room(seed=6, n_gauss=10000, sh_f16=True)
+    r, _, _ = gpu_render(s)
+    st = compare_blend(view_outputs(r, 0), oracle_view(s, 0, mode="grid"))
+    assert st["amb_frac"] < 0.01
+
+
+# ------------------------------------------------------------- edge cases --
+
+def test_no_gaussians_gives_the_mesh_image():
+    s = scenes.micro_quad_only()
+    r, _, _ = gpu_render(s)
+    g = view_outputs(r, 0)
+    m = O.mesh_raster(s.cameras[0], s.mesh, bg=s.bg)
+    assert np.abs(g.rgb - m.rgb).max() < 1e-5
+    assert np.all(g.T == 1.0) and np.all(g.n_contrib == 0)
+
+
+def test_lone_gaussian_peaks_at_opacity_on_gpu():
+    s = scenes.micro_lone_gaussian(opacity=0.6)
+    s.bg = np.array([0.1, 0.2, 0.3], np.float32)
+    r, _, _ = gpu_render(s)
+    g = view_outputs(r, 0)
+    q = 12 * 32 + 10
+    o = float(np.float32(0.6))
+    c = 0.5 + 0.28209479177387814 * s.gaussians.sh[0, 0].astype(np.float64)
+    assert np.abs(g.rgb[:, q] - (o * c + (1 - o) * s.bg)).max() < 1e-6
+    assert abs(g.T[q] - (1 - o)) < 1e-6 and g.n_contrib[q] == 1
+
+
+def test_all_gaussians_behind_camera_and_tiny_images():
+    s = scenes.config0_scene()
+    s.gaussians.means[:, 2] = -s.gaussians.means[:, 2]
+    r, _, _ = gpu_render(s)
+    assert int(r.n_pairs.item()) == 0
+    g = view_outputs(r, 0)
+    m = O.mesh_raster(s.cameras[0], s.mesh, bg=s.bg)
+    assert np.abs(g.rgb - m.rgb).max() < 1e-5
+    s2 = scenes.config0_scene()
+    s2.cameras = [scenes.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 1.0, 1.0, 0.5, 0.5, 1, 1),
+                  scenes.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 30.0, 30.0, 18.5, 11.5, 37, 23)]
+    r2, _, _ = gpu_render(s2)
+    for v in range(2):
+        compare_blend(view_outputs(r2, v), oracle_view(s2, v))
+
+
+def test_huge_gaussian_covering_every_tile():
+    s = scenes.config0_scene(n=50)
+    s.gaussians.scales[0] = [2.0, 2.0, 0.01]
+    s.gaussians.means[0] = [0.0, 0.0, 2.0]
+    r, _, _ = gpu_render(s)
+    compare_blend(view_outputs(r, 0), oracle_view(s, 0))
+
+
+# ----------------------------------------------- full size, sampled pixels --
+
+def test_config1_full_size_sampled_pixels():
+    """The bench workload (1920x1080, 300k Gaussians, 50k-face room, 8
+    poses) in the bench's launch configuration; the oracle evaluates 150
+    random pixels per view of 3 views one by one (brute force)."""
+    s = scenes.config1_scene()
+    r, _, _ = gpu_render(s, tile=(16, 16))
+    rng = np.random.default_rng(0)
+    for v in (0, 3, 7):
+        pix = np.sort(rng.choice(s.cameras[v].n_pixels, 150, replace=False))
+        g = view_outputs(r, v)
+        m = O.mesh_raster(s.cameras[v], s.mesh, bg=s.bg, pix=pix)
+        assert np.array_equal(g.tri_id[pix], m.tri_id)
+        assert np.array_equal(g.depth[pix], m.depth)
+        st = compare_blend(g, oracle_view(s, v, pix=pix), pix=pix)
+        print(v, st)
