@@ -86,6 +86,8 @@ typedef struct hm_options {
     float near_mesh;         /* faces with a vertex at view z <= this are culled (0.01) */
     float bg[3];             /* I_bg */
     int32_t bwd_stages;      /* hm_blend_backward parts to run (HM_BWD_* bits; 0 = all) */
+    int32_t ellipse_cull;    /* 1: bin a Gaussian only into tiles whose pixel-centre
+                                rectangle its 3-sigma ellipse reaches (result-preserving) */
 } hm_options;
 
 /* hm_blend_backward parts.  HM_BWD_PROJECT consumes the per-record partials
@@ -96,7 +98,8 @@ typedef struct hm_options {
 #define HM_BWD_PROJECT 4       /* partials -> Gaussian parameter gradients */
 
 /* Fill `opt` with the defaults: 16x16 tiles, batch 256, mesh_cull 1,
- * near planes 0.2 / 0.01, black background, all backward parts. */
+ * ellipse_cull 1, near planes 0.2 / 0.01, black background, all backward
+ * parts. */
 void hm_default_options(hm_options *opt);
 
 /* Thread-local text of the last host-side error. */
@@ -108,9 +111,10 @@ const char *hm_last_error(void);
  * Per pixel: the nearest covering triangle (two-sided; vertices projected in
  * FP64, snapped to 1/256 px, exact integer edge functions, top-left fill
  * rule; faces with a vertex at z <= near_mesh or beyond +-2^21 px culled),
- * its view depth z = W / sum_k(w_k / z_k) evaluated in FP64 with a fixed
- * operation order and rounded once to FP32 (nearest FP32 depth wins, ties to
- * the lower face index), perspective-correct UVs and a bilinear,
+ * its view depth z = fp32(W) / fp32(S), S = sum_k(w_k / z_k) evaluated in
+ * FP64 with a fixed operation order, the division in IEEE FP32 (nearest FP32
+ * depth wins, ties to the lower face index), perspective-correct UVs and a
+ * bilinear,
  * clamp-to-edge texture fetch (texel centres at half-integers, row 0 at v=0).
  *
  *  verts [n_verts][3], uvs [n_verts][2] float32; faces [n_faces][3] int32.
@@ -159,7 +163,8 @@ hm_status hm_project_gaussians(const hm_camera *cams, int32_t n_views, int32_t n
  * number of Gaussians).  Emits one (tile, depth) key per (record, tile) pair
  * whose tile the record's rectangle covers (minus pairs at or behind the
  * tile's farthest mesh depth when opt->mesh_cull and tile_max_depth are
- * given), and sorts them by (tile, FP32 depth, Gaussian index) with an LSD
+ * given, and, with opt->ellipse_cull, tiles whose pixel centres all lie
+ * outside the 3-sigma ellipse), and sorts them by (tile, FP32 depth, Gaussian index) with an LSD
  * device radix sort.  Outputs: pair_vals[capacity] uint32 record indices in
  * sorted order, *n_pairs_out (device int64) the pair count, tile_ranges
  * [total_tiles][2] uint32 [begin, end) into pair_vals.  If the count exceeds

@@ -30,9 +30,12 @@
  *   - mesh coverage: vertices projected in FP64, snapped to 1/256 px,
  *     exact integer edge functions with the top-left fill rule, two-sided;
  *     nearest FP32 view depth wins, ties to the lower triangle index;
- *     depth z = W / sum_k(b_k / z_k) in FP64 with a fixed operation order,
- *     rounded once to FP32; perspective-correct UVs; bilinear clamp-to-edge
- *     texture fetch with texel centres at half-integers, row 0 at v = 0.
+ *     depth z = W / S with S = sum_k(b_k / z_k) evaluated in FP64 with a
+ *     fixed operation order and the quotient taken as the IEEE FP32
+ *     division fp32(W) / fp32(S) -- the nearest-face decision is an argmin,
+ *     taken in the FP32 precision the GPU decides it in; perspective-correct
+ *     UVs; bilinear clamp-to-edge texture fetch with texel centres at
+ *     half-integers, row 0 at v = 0.
  *   - Gaussian depth key: z = R_2 . mean + t_2 evaluated in FP64 as
  *     fma(R20, x, fma(R21, y, fma(R22, z, t2))), rounded once to FP32.
  *
@@ -130,10 +133,13 @@ static int face_covers(const face_setup *s, int64_t px, int64_t py, int64_t w[3]
     return 1;
 }
 
-static double face_depth64(const face_setup *s, const int64_t w[3], double *S_out) {
+/* view depth at a covered centre: S in FP64 (fixed order), then the FP32
+ * quotient of the FP32-rounded W and S (both IEEE round-to-nearest) */
+static float face_depth(const face_setup *s, const int64_t w[3], double *S_out) {
     double S = fma((double)w[2], s->iz[2], fma((double)w[1], s->iz[1], (double)w[0] * s->iz[0]));
     *S_out = S;
-    return (double)s->area2 / S;
+    float Wf = (float)s->area2, Sf = (float)S;
+    return Wf / Sf;
 }
 
 static double texel(const double *tex, int tw, int th, int x, int y, int ch) {
@@ -188,7 +194,7 @@ void or_mesh_raster(const double *cam, int W, int H, const double *verts, const 
             int64_t w[3];
             if (!face_covers(&fs[f], px, py, w)) continue;
             double S;
-            float D = (float)face_depth64(&fs[f], w, &S);
+            float D = face_depth(&fs[f], w, &S);
             if (D < bestD) { bestD = D; best = f; bestS = S; bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2]; }
         }
         tri_id[q] = best;

@@ -25,16 +25,43 @@ __device__ __forceinline__ bool tile_kept(const float *tmax, int gt, float depth
     return tmax == nullptr || depth < tmax[gt];
 }
 
+// d^2 along one edge of the rectangle: the edge's coordinate is fixed at e,
+// the other coordinate ranges over [lo, hi]; the 1-D quadratic's minimiser
+// is clamped into the range
+__device__ __forceinline__ float edge_min(float p, float q, float r, float e, float lo, float hi) {
+    // d^2 = p e^2 + 2 q e f + r f^2 over f in [lo, hi]
+    const float f = fminf(hi, fmaxf(lo, -q * e / r));
+    return fmaf(p * e, e, fmaf(2.f * q * e, f, r * f * f));
+}
+
+// Does the 3-sigma ellipse (conic a,b,c at mean m) reach the rectangle of
+// the tile's in-image pixel centres?  The minimum of the convex quadratic
+// d^2 over the rectangle is 0 if the mean is inside, else it lies on the
+// boundary; 9 is inflated by 0.2% so the test stays a superset of the
+// blend's FP32 per-pixel test.
+__device__ __forceinline__ bool ellipse_hits(const ViewDev &V, int TW, int TH, int tx, int ty,
+                                             float mx, float my, float a, float b, float c) {
+    const float x0 = (float)(tx * TW) + 0.5f - mx;
+    const float x1 = (float)(min((tx + 1) * TW, V.W) - 1) + 0.5f - mx;
+    const float y0 = (float)(ty * TH) + 0.5f - my;
+    const float y1 = (float)(min((ty + 1) * TH, V.H) - 1) + 0.5f - my;
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+    float m = fminf(edge_min(a, b, c, x0, y0, y1), edge_min(a, b, c, x1, y0, y1));
+    m = fminf(m, fminf(edge_min(c, b, a, y0, x0, x1), edge_min(c, b, a, y1, x0, x1)));
+    return m <= 9.0f * 1.002f;
+}
+
 // per record: number of kept tiles, and the depth-sort key
 __global__ void __launch_bounds__(256)
 bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec,
-                 const float *__restrict__ tmax, uint32_t *__restrict__ cnt,
+                 const float *__restrict__ tmax, int ellipse, uint32_t *__restrict__ cnt,
                  uint32_t *__restrict__ dkey) {
     const long long m = (long long)vt.n_views * n;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
         const int v = (int)(it / n);
         const ViewDev &V = vt.v[v];
+        const float4 a = rec[it].a;
         const float4 b = rec[it].b;
         const float4 c = rec[it].c;
         int x0, x1, y0, y1;
@@ -42,12 +69,14 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec,
         unpack_range(__float_as_uint(c.w), y0, y1);
         uint32_t k = 0;
         if (x0 <= x1 && y0 <= y1) {
-            if (tmax == nullptr) {
+            if (tmax == nullptr && !ellipse) {
                 k = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
             } else {
                 for (int ty = y0; ty <= y1; ++ty) {
                     const int row = V.tile_off + ty * V.tiles_x;
-                    for (int tx = x0; tx <= x1; ++tx) k += tile_kept(tmax, row + tx, b.z);
+                    for (int tx = x0; tx <= x1; ++tx)
+                        k += tile_kept(tmax, row + tx, b.z) &&
+                             (!ellipse || ellipse_hits(V, vt.tile_w, vt.tile_h, tx, ty, a.x, a.y, a.z, a.w, b.x));
                 }
             }
         }
@@ -59,7 +88,7 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec,
 // per depth-sorted record: write its (tile, record) pairs at its scan offset
 __global__ void __launch_bounds__(256)
 bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec,
-                const float *__restrict__ tmax, const uint32_t *__restrict__ sorted_items,
+                const float *__restrict__ tmax, int ellipse, const uint32_t *__restrict__ sorted_items,
                 const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
                 long long capacity, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
     const long long m = (long long)vt.n_views * n;
@@ -72,6 +101,7 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec,
         if (o + k > capacity) continue;          // capacity exceeded: flagged by the scan
         const int v = (int)(it / (uint32_t)n);
         const ViewDev &V = vt.v[v];
+        const float4 a = rec[it].a;
         const float4 b = rec[it].b;
         const float4 c = rec[it].c;
         int x0, x1, y0, y1;
@@ -81,6 +111,7 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec,
             const int row = V.tile_off + ty * V.tiles_x;
             for (int tx = x0; tx <= x1; ++tx) {
                 if (!tile_kept(tmax, row + tx, b.z)) continue;
+                if (ellipse && !ellipse_hits(V, vt.tile_w, vt.tile_h, tx, ty, a.x, a.y, a.z, a.w, b.x)) continue;
                 pkey[o] = (uint32_t)(row + tx);
                 pval[o] = it;
                 ++o;
@@ -197,7 +228,7 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     if (m == 0) return cuda_status(cudaMemsetAsync(n_pairs_out, 0, sizeof(long long), s));
 
     // 1. counts and depth keys
-    bin_count_kernel<<<grid_for(m, 256), 256, 0, s>>>(vt, n, rec, tmax, b.cnt, b.dkey0);
+    bin_count_kernel<<<grid_for(m, 256), 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.cnt, b.dkey0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 2. depth sort of the records (4 digit passes; result back in dkey0/ditem0)
     if ((e = launch_fill_i64(b.n_items, m, s)) != cudaSuccess) return cuda_status(e);
@@ -212,7 +243,7 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     const int passes = tile_key_passes(vt.total_tiles);
     uint32_t *v0 = (passes & 1) ? b.pval_tmp : pair_vals;
     uint32_t *v1 = (passes & 1) ? pair_vals : b.pval_tmp;
-    bin_emit_kernel<<<grid_for(m, 256), 256, 0, s>>>(vt, n, rec, tmax, b.ditem0, b.cnt, b.offs,
+    bin_emit_kernel<<<grid_for(m, 256), 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.ditem0, b.cnt, b.offs,
                                                       capacity, b.pkey0, v0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 5. stable sort of the pairs by tile

@@ -30,6 +30,32 @@ namespace {
 
 constexpr int kG = 9;   // dmx, dmy, dconic_xx, dconic_xy, dconic_yy, dopacity, dr, dg, db
 
+// Warp sum of 8 per-lane values by recursive halving: at each of the first
+// three levels a lane keeps half of its values and sends the other half to
+// its partner, so 4 + 2 + 1 + 2 shuffles (instead of 8 x 5) leave the sum of
+// value (lane >> 2) in every lane with lane % 4 == 0.
+__device__ __forceinline__ float warp_sum8(const float *v, int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4];
+        const float keep = b4 ? v[i + 4] : v[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? w[i] : w[i + 2];
+        const float keep = b3 ? w[i + 2] : w[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    return y;
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH)
 blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
@@ -125,19 +151,13 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
                 }
             }
             if (__any_sync(0xffffffffu, active)) {
+                float *dst = g2d + (size_t)s_item[k] * kG;
+                const float y = warp_sum8(g, lane);
+                float z = g[8];
 #pragma unroll
-                for (int q = 0; q < kG; ++q) {
-                    float x = g[q];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    g[q] = x;
-                }
-                if (lane == 0) {
-                    float *dst = g2d + (size_t)s_item[k] * kG;
-#pragma unroll
-                    for (int q = 0; q < kG; ++q)
-                        if (g[q] != 0.f) atomicAdd(dst + q, g[q]);
-                }
+                for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+                if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
+                if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
             }
         }
         hi = lo;
@@ -171,10 +191,17 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         for (int k = 0; k < 4; ++k) {
             if (w[k] == 0.f) continue;
             const int x = min(max(xs[k], 0), tw - 1), y = min(max(ys[k], 0), th - 1);
-            float *d = d_tex + ((size_t)y * tw + x) * 3;
-            atomicAdd(d, w[k] * g0);
-            atomicAdd(d + 1, w[k] * g1);
-            atomicAdd(d + 2, w[k] * g2);
+            const size_t tix = (size_t)y * tw + x;
+            float *d = d_tex + tix * 3;
+            // texel t starts at float 3t: (r,g) is 8-byte aligned for even t,
+            // (g,b) for odd t -- one vector and one scalar reduction per tap
+            if ((tix & 1) == 0) {
+                atomicAdd(reinterpret_cast<float2 *>(d), make_float2(w[k] * g0, w[k] * g1));
+                atomicAdd(d + 2, w[k] * g2);
+            } else {
+                atomicAdd(d, w[k] * g0);
+                atomicAdd(reinterpret_cast<float2 *>(d + 1), make_float2(w[k] * g1, w[k] * g2));
+            }
         }
     }
 }
@@ -449,6 +476,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
         return fail(HM_ERR_INVALID_ARG, "null pointer");
     if (d_tex && (!mesh_depth || !mesh_uv || tex_w <= 0 || tex_h <= 0))
         return fail(HM_ERR_INVALID_ARG, "texture gradient needs mesh_depth, mesh_uv and the texture size");
+    if ((uintptr_t)d_tex & 7) return fail(HM_ERR_INVALID_ARG, "d_tex must be 8-byte aligned");
     if (((uintptr_t)records & 15) || ((uintptr_t)quats & 15))
         return fail(HM_ERR_INVALID_ARG, "records and quats must be 16-byte aligned");
     const size_t need = hm_blend_backward_workspace_size(n_views, n);

@@ -88,6 +88,7 @@ extern "C" void hm_default_options(hm_options *opt) {
     opt->near_gauss = 0.2f;
     opt->near_mesh = 0.01f;
     opt->bwd_stages = 0;
+    opt->ellipse_cull = 1;
 }
 
 extern "C" const char *hm_last_error(void) { return g_err; }

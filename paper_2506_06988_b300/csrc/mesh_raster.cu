@@ -7,10 +7,11 @@
 //                 1/256 px, 1/z;
 //   face pass     orientation, bounding box, tiles touched (count);
 //   scan + emit   one (face, tile) work item per touched tile;
-//   coverage      one warp per item: exact int64 edge functions with the
-//                 top-left rule at the tile's pixel centres; the FP64 depth
-//                 W / sum_k(w_k / z_k), rounded once to FP32, is packed with
-//                 the face index into a 64-bit key and merged with
+//   coverage      one warp per item: exact int64 edge functions (stepped
+//                 incrementally down each lane's column) with the top-left
+//                 rule at the tile's pixel centres; the depth
+//                 fp32(W) / fp32(S), S = sum_k(w_k / z_k) in FP64, is packed
+//                 with the face index into a 64-bit key and merged with
 //                 atomicMin into a per-pixel visibility word -- the minimum
 //                 is (nearest FP32 depth, lowest face index) whatever the
 //                 order the items run in;
@@ -34,7 +35,7 @@ struct FaceSetup {
     long long area2;         // |signed double area| (1/256 px)^2
     int flip;                // signed area negative: traverse 0 -> 2 -> 1
     int tx0, tx1, ty0, ty1;  // touched tiles (empty: tx0 > tx1)
-    int pad;
+    float Wf;                // fp32(area2)
     double iz[3];            // 1 / view z per vertex
 };
 
@@ -84,7 +85,7 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
         const ViewDev &V = vt.v[v];
         FaceSetup s;
         s.tx0 = 1; s.tx1 = 0; s.ty0 = 1; s.ty1 = 0;
-        s.flip = 0; s.area2 = 0; s.pad = 0;
+        s.flip = 0; s.area2 = 0; s.Wf = 0.f;
         bool ok = true;
         for (int k = 0; k < 3; ++k) {
             const int vi = faces[3 * f + k];
@@ -101,6 +102,7 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
             if (a2 != 0) {
                 s.flip = a2 < 0;
                 s.area2 = a2 < 0 ? -a2 : a2;
+                s.Wf = __ll2float_rn(s.area2);
                 const long long mnx = min(s.x[0], min(s.x[1], s.x[2])), mxx = max(s.x[0], max(s.x[1], s.x[2]));
                 const long long mny = min(s.y[0], min(s.y[1], s.y[2])), mxy = max(s.y[0], max(s.y[1], s.y[2]));
                 // pixel centres 256 x + 128 inside [mn, mx]
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(256)
 mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
                   const unsigned long long *__restrict__ items, const long long *n_items,
                   unsigned long long *__restrict__ vis) {
+    // a lane owns one column of the tile: pixels (x, y0 + k*YS), k < NP
+    constexpr int NP = TW * TH / 32, YS = 32 / TW;
     const long long n = *n_items;
     const int lane = threadIdx.x & 31;
     const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -177,17 +181,42 @@ mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         const unsigned f = (unsigned)(vf - (long long)v * nf);
         const ViewDev &V = vt.v[v];
         const FaceSetup s = setup[vf];
-        const double area = (double)s.area2;
+        const int px = tx * TW + (lane % TW), py0 = ty * TH + (lane / TW);
+        if (px >= V.W) continue;
+        const int b = s.flip ? 2 : 1, c = s.flip ? 1 : 2;   // oriented order 0, b, c
+        const long long PX = (long long)px * 256 + 128, PY = (long long)py0 * 256 + 128;
+        // oriented edges e0: 0->b, e1: b->c, e2: c->0 (E > 0 inside)
+        const long long ax[3] = {s.x[0], s.x[b], s.x[c]}, ay[3] = {s.y[0], s.y[b], s.y[c]};
+        const long long bx[3] = {s.x[b], s.x[c], s.x[0]}, by[3] = {s.y[b], s.y[c], s.y[0]};
+        long long E[3], inc[3];
+        bool tl[3];
 #pragma unroll
-        for (int p = lane; p < TW * TH; p += 32) {
-            const int px = tx * TW + (p % TW), py = ty * TH + (p / TW);
-            if (px >= V.W || py >= V.H) continue;
-            long long wgt[3];
-            if (!face_cover(s, (long long)px * 256 + 128, (long long)py * 256 + 128, wgt)) continue;
-            const double S = fma((double)wgt[2], s.iz[2], fma((double)wgt[1], s.iz[1], (double)wgt[0] * s.iz[0]));
-            const float D = __double2float_rn(area / S);
-            const unsigned long long key = ((unsigned long long)__float_as_uint(D) << 32) | f;
-            atomicMin(&vis[V.pix_off + (long long)py * V.W + px], key);
+        for (int e = 0; e < 3; ++e) {
+            const long long dx = bx[e] - ax[e], dy = by[e] - ay[e];
+            E[e] = dx * (PY - ay[e]) - dy * (PX - ax[e]);
+            inc[e] = dx * (256 * YS);
+            tl[e] = dy < 0 || (dy == 0 && dx > 0);
+        }
+        const unsigned long long fkey = f;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int py = py0 + k * YS;
+            if (py >= V.H) break;
+            const bool in = (E[0] > 0 || (E[0] == 0 && tl[0])) && (E[1] > 0 || (E[1] == 0 && tl[1])) &&
+                            (E[2] > 0 || (E[2] == 0 && tl[2]));
+            if (in) {
+                // weight of a vertex = edge function of the opposite edge
+                long long wgt[3];
+                wgt[0] = E[1];
+                wgt[b] = E[2];
+                wgt[c] = E[0];
+                const double S = fma((double)wgt[2], s.iz[2], fma((double)wgt[1], s.iz[1], (double)wgt[0] * s.iz[0]));
+                const float D = __fdiv_rn(s.Wf, __double2float_rn(S));
+                atomicMin(&vis[V.pix_off + (long long)py * V.W + px],
+                          ((unsigned long long)__float_as_uint(D) << 32) | fkey);
+            }
+#pragma unroll
+            for (int e = 0; e < 3; ++e) E[e] += inc[e];
         }
     }
 }

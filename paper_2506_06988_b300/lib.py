@@ -49,7 +49,7 @@ class HmCamera(ctypes.Structure):
 class HmOptions(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32),
                 ("mesh_cull", c_int32), ("near_gauss", c_float), ("near_mesh", c_float),
-                ("bg", c_float * 3), ("bwd_stages", c_int32)]
+                ("bg", c_float * 3), ("bwd_stages", c_int32), ("ellipse_cull", c_int32)]
 
 
 class HmError(RuntimeError):
@@ -124,12 +124,13 @@ def cameras(cams) -> ctypes.Array:
 
 
 def options(tile=(16, 16), batch=None, mesh_cull=True, bg=(0.0, 0.0, 0.0), near_gauss=0.2,
-            near_mesh=0.01) -> HmOptions:
+            near_mesh=0.01, ellipse_cull=True) -> HmOptions:
     o = HmOptions()
     load().hm_default_options(ctypes.byref(o))
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     o.batch = int(batch) if batch is not None else int(tile[0] * tile[1])
     o.mesh_cull = int(bool(mesh_cull))
+    o.ellipse_cull = int(bool(ellipse_cull))
     o.near_gauss, o.near_mesh = float(near_gauss), float(near_mesh)
     o.bg[:] = [float(x) for x in bg]
     return o

@@ -66,7 +66,7 @@ class Renderer:
                  n_verts: int = 0, n_faces: int = 0, tex_shape=None, tile=(16, 16),
                  batch: Optional[int] = None, mesh_cull: bool = True, bg=(0.0, 0.0, 0.0),
                  pair_capacity: Optional[int] = None, item_capacity: Optional[int] = None,
-                 device="cuda"):
+                 ellipse_cull: bool = True, device="cuda"):
         lib.load()
         self.device = torch.device(device)
         self.cam_list = list(cams)
@@ -76,7 +76,8 @@ class Renderer:
         self.sh_degree = int(sh_degree)
         self.K = (self.sh_degree + 1) ** 2
         self.sh_format = lib.HM_SH_F16 if sh_f16 else lib.HM_SH_F32
-        self.opt = lib.options(tile=tile, batch=batch, mesh_cull=mesh_cull, bg=bg)
+        self.opt = lib.options(tile=tile, batch=batch, mesh_cull=mesh_cull, bg=bg,
+                               ellipse_cull=ellipse_cull)
         self.bg = tuple(float(x) for x in bg)
         self.sizes = [(int(c.width), int(c.height)) for c in self.cam_list]
         self.pix_off = np.concatenate([[0], np.cumsum([w * h for w, h in self.sizes])]).astype(np.int64)
