@@ -111,10 +111,11 @@ const char *hm_last_error(void);
  * Per pixel: the nearest covering triangle (two-sided; vertices projected in
  * FP64, snapped to 1/256 px, exact integer edge functions, top-left fill
  * rule; faces with a vertex at z <= near_mesh or beyond +-2^21 px culled),
- * its view depth z = fp32(W) / fp32(S), S = sum_k(w_k / z_k) evaluated in
- * FP64 with a fixed operation order, the division in IEEE FP32 (nearest FP32
- * depth wins, ties to the lower face index), perspective-correct UVs and a
- * bilinear,
+ * its view depth z = 1 / fma(a, U, fma(b, V, 1/z0)) in FP32, where 1/z is
+ * affine in screen space, (U,V) is the pixel centre minus the snapped vertex
+ * 0 in pixels and a, b, 1/z0 are the face's coefficients computed in FP64
+ * and rounded once to FP32 (nearest FP32 depth wins, ties to the lower face
+ * index), perspective-correct UVs and a bilinear,
  * clamp-to-edge texture fetch (texel centres at half-integers, row 0 at v=0).
  *
  *  verts [n_verts][3], uvs [n_verts][2] float32; faces [n_faces][3] int32.

@@ -30,12 +30,14 @@
  *   - mesh coverage: vertices projected in FP64, snapped to 1/256 px,
  *     exact integer edge functions with the top-left fill rule, two-sided;
  *     nearest FP32 view depth wins, ties to the lower triangle index;
- *     depth z = W / S with S = sum_k(b_k / z_k) evaluated in FP64 with a
- *     fixed operation order and the quotient taken as the IEEE FP32
- *     division fp32(W) / fp32(S) -- the nearest-face decision is an argmin,
- *     taken in the FP32 precision the GPU decides it in; perspective-correct
- *     UVs; bilinear clamp-to-edge texture fetch with texel centres at
- *     half-integers, row 0 at v = 0.
+ *     depth: 1/z is affine in screen space, 1/z = 1/z0 + a U + b V with
+ *     (U,V) the pixel centre minus the snapped vertex 0 in pixels; a, b
+ *     and 1/z0 are computed per face in FP64 and rounded once to FP32, and
+ *     the pixel's depth is the FP32 reciprocal of fma(a, U, fma(b, V, 1/z0))
+ *     -- the nearest-face decision is an argmin, taken in the FP32
+ *     precision the GPU decides it in; perspective-correct UVs; bilinear
+ *     clamp-to-edge texture fetch with texel centres at half-integers, row 0
+ *     at v = 0.
  *   - Gaussian depth key: z = R_2 . mean + t_2 evaluated in FP64 as
  *     fma(R20, x, fma(R21, y, fma(R22, z, t2))), rounded once to FP32.
  *
@@ -79,6 +81,7 @@ typedef struct {
     double iz[3];         /* 1 / view z per vertex */
     int ord[3];           /* vertex order with positive signed area */
     int64_t area2;        /* |signed double area| in (1/256 px)^2 */
+    float iz0f, af, bf;   /* 1/z = iz0 + a U + b V (per pixel of offset from vertex 0) */
 } face_setup;
 
 #define OR_SNAP 256.0
@@ -100,10 +103,22 @@ static void setup_face(const double *c, const double *verts, const int *f, doubl
         s->Y[k] = llrint(sy * OR_SNAP);
         s->iz[k] = 1.0 / Z;
     }
-    int64_t a2 = (s->X[1] - s->X[0]) * (s->Y[2] - s->Y[0]) - (s->Y[1] - s->Y[0]) * (s->X[2] - s->X[0]);
+    int64_t e1x = s->X[1] - s->X[0], e1y = s->Y[1] - s->Y[0];
+    int64_t e2x = s->X[2] - s->X[0], e2y = s->Y[2] - s->Y[0];
+    int64_t a2 = e1x * e2y - e1y * e2x;
     if (a2 == 0) return;
     if (a2 > 0) { s->ord[0] = 0; s->ord[1] = 1; s->ord[2] = 2; s->area2 = a2; }
     else        { s->ord[0] = 0; s->ord[1] = 2; s->ord[2] = 1; s->area2 = -a2; }
+    /* screen-space barycentrics l1 = (dx e2y - dy e2x) / D, l2 = (e1x dy - e1y dx) / D
+     * for the offset (dx, dy) from vertex 0 (Cramer's rule, D = signed area2), so
+     * 1/z = iz0 + (iz1 - iz0) l1 + (iz2 - iz0) l2 = iz0 + a dx + b dy; per pixel of
+     * offset the coefficients carry a factor 256 */
+    double d1 = s->iz[1] - s->iz[0], d2 = s->iz[2] - s->iz[0];
+    double na = fma(d1, (double)e2y, -(d2 * (double)e1y));
+    double nb = fma(d2, (double)e1x, -(d1 * (double)e2x));
+    s->af = (float)((na * 256.0) / (double)a2);
+    s->bf = (float)((nb * 256.0) / (double)a2);
+    s->iz0f = (float)s->iz[0];
     s->valid = 1;
 }
 
@@ -133,13 +148,20 @@ static int face_covers(const face_setup *s, int64_t px, int64_t py, int64_t w[3]
     return 1;
 }
 
-/* view depth at a covered centre: S in FP64 (fixed order), then the FP32
- * quotient of the FP32-rounded W and S (both IEEE round-to-nearest) */
-static float face_depth(const face_setup *s, const int64_t w[3], double *S_out) {
-    double S = fma((double)w[2], s->iz[2], fma((double)w[1], s->iz[1], (double)w[0] * s->iz[0]));
-    *S_out = S;
-    float Wf = (float)s->area2, Sf = (float)S;
-    return Wf / Sf;
+/* view depth at the covered centre (px, py) (1/256 px): the FP32 reciprocal
+ * of the affine 1/z evaluated in FP32 at the pixel offset from vertex 0 */
+static float face_depth(const face_setup *s, int64_t px, int64_t py) {
+    float U = (float)(int32_t)(px - s->X[0]) * 0.00390625f;
+    float V = (float)(int32_t)(py - s->Y[0]) * 0.00390625f;
+    float invz = fmaf(s->af, U, fmaf(s->bf, V, s->iz0f));
+    return 1.0f / invz;
+}
+
+/* perspective-correct barycentrics (FP64) of a covered centre */
+static double face_bary(const face_setup *s, const int64_t w[3], double b[3]) {
+    double S = (double)w[0] * s->iz[0] + (double)w[1] * s->iz[1] + (double)w[2] * s->iz[2];
+    for (int k = 0; k < 3; k++) b[k] = (double)w[k] * s->iz[k] / S;
+    return S;
 }
 
 static double texel(const double *tex, int tw, int th, int x, int y, int ch) {
@@ -187,15 +209,13 @@ void or_mesh_raster(const double *cam, int W, int H, const double *verts, const 
         int64_t px = (int64_t)x * 256 + 128, py = (int64_t)y * 256 + 128;
         int best = -1;
         float bestD = INFINITY;
-        double bestS = 0;
         int64_t bw[3] = {0, 0, 0};
         for (int f = 0; f < nf; f++) {
             if (!fs[f].valid) continue;
             int64_t w[3];
             if (!face_covers(&fs[f], px, py, w)) continue;
-            double S;
-            float D = face_depth(&fs[f], w, &S);
-            if (D < bestD) { bestD = D; best = f; bestS = S; bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2]; }
+            float D = face_depth(&fs[f], px, py);
+            if (D < bestD) { bestD = D; best = f; bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2]; }
         }
         tri_id[q] = best;
         depth[q] = best >= 0 ? bestD : INFINITY;
@@ -207,8 +227,8 @@ void or_mesh_raster(const double *cam, int W, int H, const double *verts, const 
         }
         const int *f = faces + 3 * (int64_t)best;
         double b[3], u = 0, v = 0;
+        face_bary(&fs[best], bw, b);
         for (int k = 0; k < 3; k++) {
-            b[k] = (double)bw[k] * fs[best].iz[k] / bestS;
             u += b[k] * uvs[2 * (int64_t)f[k]];
             v += b[k] * uvs[2 * (int64_t)f[k] + 1];
         }

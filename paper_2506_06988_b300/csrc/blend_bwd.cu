@@ -3,7 +3,8 @@
 // parameters and the texels (the texture map is optimisable, Sec. 3.4).
 //
 // Three kernels:
-//  * blend_bwd: per tile, per pixel, the blended Gaussians are replayed back
+//  * blend_bwd: per tile, per pixel (two pixels of a column per thread, as in
+//    the forward, in packed FP32x2), the blended Gaussians are replayed back
 //    to front from the pixel's last blended list position.  With
 //    B = (colour behind Gaussian i) / T_{i+1}, running from B = back:
 //        dI/dc_i     = alpha_i T_i
@@ -14,7 +15,8 @@
 //    opacity, colour) are summed over the warp with shuffles and added to
 //    per-record accumulators with one atomic per value per warp.
 //  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
-//    triangle (the mesh colour enters I_h weighted by T).
+//    triangle (the mesh colour enters I_h weighted by T), summed per screen
+//    tile in shared memory before the global reductions.
 //  * project_bwd: one thread per Gaussian chains the per-record partials
 //    through the conic inverse, Sigma' = V V^T, V = (J W)(R S), the clamped
 //    Jacobian, the projection of the mean, the quaternion normalisation and
@@ -57,13 +59,13 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH)
+__global__ void __launch_bounds__(TW *TH / 2, 6)
 blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
                  const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_rgb, float bg0,
                  float bg1, float bg2, const float *__restrict__ out_T,
                  const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
                  const float *__restrict__ dL_dT, float *__restrict__ g2d) {
-    constexpr int NT = TW * TH;
+    constexpr int NT = TW * TH, NTH = NT / 2;
     __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
     __shared__ uint32_t s_item[NT];
     __shared__ uint32_t s_hi;
@@ -73,136 +75,218 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x, lane = t & 31;
-    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
-    const bool inside = px < V.W && py < V.H;
+    // two pixels of one column, rows ya and ya + TH/2 (as in the forward)
+    const int px = tx * TW + (t % TW), pya = ty * TH + (t / TW), pyb = pya + TH / 2;
+    const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
     const long long npx = (long long)V.W * V.H;
-    const long long lp = (long long)py * V.W + px;
-    const long long gp = V.pix_off + lp;
-    float Tf = 1.f, gI0 = 0.f, gI1 = 0.f, gI2 = 0.f, gT = 0.f;
-    float B0 = bg0, B1 = bg1, B2 = bg2;
-    uint32_t my_last = 0;
-    if (inside) {
-        Tf = out_T[gp];
-        my_last = last_idx[gp];
-        const float *g = dL_drgb + 3 * V.pix_off + lp;
-        gI0 = g[0]; gI1 = g[npx]; gI2 = g[2 * npx];
-        if (dL_dT) gT = dL_dT[gp];
-        if (mesh_rgb) {
-            const float *m = mesh_rgb + 3 * V.pix_off + lp;
-            B0 = m[0]; B1 = m[npx]; B2 = m[2 * npx];
-        }
+    const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
+    float2 Tf = make_float2(1.f, 1.f), gI0 = make_float2(0.f, 0.f), gI1 = gI0, gI2 = gI0, gT = gI0;
+    float2 B0 = make_float2(bg0, bg0), B1 = make_float2(bg1, bg1), B2 = make_float2(bg2, bg2);
+    uint32_t last_a = 0, last_b = 0;
+    const float *gI = dL_drgb + 3 * V.pix_off;
+    const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
+    if (in_a) {
+        Tf.x = out_T[V.pix_off + lpa];
+        last_a = last_idx[V.pix_off + lpa];
+        gI0.x = gI[lpa]; gI1.x = gI[npx + lpa]; gI2.x = gI[2 * npx + lpa];
+        if (dL_dT) gT.x = dL_dT[V.pix_off + lpa];
+        if (mr) { B0.x = mr[lpa]; B1.x = mr[npx + lpa]; B2.x = mr[2 * npx + lpa]; }
+    }
+    if (in_b) {
+        Tf.y = out_T[V.pix_off + lpb];
+        last_b = last_idx[V.pix_off + lpb];
+        gI0.y = gI[lpb]; gI1.y = gI[npx + lpb]; gI2.y = gI[2 * npx + lpb];
+        if (dL_dT) gT.y = dL_dT[V.pix_off + lpb];
+        if (mr) { B0.y = mr[lpb]; B1.y = mr[npx + lpb]; B2.y = mr[2 * npx + lpb]; }
     }
     const uint32_t begin = ranges[2 * gt];
     if (t == 0) s_hi = 0;
     __syncthreads();
-    if (my_last > 0) atomicMax(&s_hi, my_last);
+    const uint32_t my_hi = max(last_a, last_b);
+    if (my_hi > 0) atomicMax(&s_hi, my_hi);
     __syncthreads();
     const uint32_t hi_all = s_hi;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    float T = Tf;
-    const float gTT = gT * Tf;
+    const float fpx = (float)px + 0.5f;
+    const float2 fpy = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
+    float2 T = Tf;
+    const float2 gTT = __fmul2_rn(gT, Tf);
     for (uint32_t hi = hi_all; hi > begin;) {
         const uint32_t lo = hi - begin > (uint32_t)NT ? hi - NT : begin;
         const int nb = (int)(hi - lo);
         __syncthreads();
-        if (t < nb) {
-            const uint32_t it = vals[lo + t];
-            s_item[t] = it;
-            stage_record(rec[it], s_a[t], s_b[t], s_c[t]);
+        for (int i = t; i < nb; i += NTH) {
+            const uint32_t it = vals[lo + i];
+            s_item[i] = it;
+            stage_record(rec[it], s_a[i], s_b[i], s_c[i]);
         }
         __syncthreads();
         for (int k = nb - 1; k >= 0; --k) {
             const uint32_t j = lo + k;
+            bool ea = j < last_a, eb = j < last_b;
+            if (!__any_sync(0xffffffffu, ea || eb)) continue;
             float g[kG];
+            const float4 A = s_a[k], Bs = s_b[k], c = s_c[k];
+            float dx;
+            float2 dy;
+            const float2 q = eval_q2(A, Bs, fpx, fpy, dx, dy);
+            ea = ea && q.x >= kQ3;
+            eb = eb && q.y >= kQ3;
+            float2 G, araw;
+            const float2 al = eval_alpha2(Bs.y, q, G, araw);
+            ea = ea && al.x >= kAlphaMin;                  // the forward blended it
+            eb = eb && al.y >= kAlphaMin;
+            const float2 ae = make_float2(ea ? al.x : 0.f, eb ? al.y : 0.f);
+            const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
+            const float2 r = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+            const float2 Ti = make_float2(ea ? T.x * r.x : T.x, eb ? T.y * r.y : T.y);
+            // colour: dI/dc = alpha T_i
+            const float2 wgt = __fmul2_rn(ae, Ti);
+            float2 p = __fmul2_rn(wgt, gI0);
+            g[6] = p.x + p.y;
+            p = __fmul2_rn(wgt, gI1);
+            g[7] = p.x + p.y;
+            p = __fmul2_rn(wgt, gI2);
+            g[8] = p.x + p.y;
+            // dL/dalpha = T_i (gI . (c - B)) - dL/dT T_final / (1 - alpha)
+            float2 sdot = __fmul2_rn(gI0, __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0.x, -B0.y)));
+            sdot = __ffma2_rn(gI1, __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1.x, -B1.y)), sdot);
+            sdot = __ffma2_rn(gI2, __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2.x, -B2.y)), sdot);
+            float2 dLda = __ffma2_rn(make_float2(-gTT.x, -gTT.y), r, __fmul2_rn(Ti, sdot));
+            dLda = make_float2(ea ? dLda.x : 0.f, eb ? dLda.y : 0.f);
+            // through alpha = o 2^q when not clamped at 0.99
+            const float2 dLa_u = make_float2(araw.x < kAlphaMax ? dLda.x : 0.f, araw.y < kAlphaMax ? dLda.y : 0.f);
+            const float2 gq = __fmul2_rn(__fmul2_rn(dLa_u, araw), make_float2(kLn2, kLn2));   // dL/dq
+            const float azdx2 = 2.f * A.z * dx, awdx = A.w * dx;
+            p = __fmul2_rn(gq, __ffma2_rn(make_float2(A.w, A.w), dy, make_float2(azdx2, azdx2)));
+            g[0] = -(p.x + p.y);                                          // dq/dmx = -(2K a dx + 2K b dy)
+            p = __fmul2_rn(gq, __ffma2_rn(make_float2(2.f * Bs.x, 2.f * Bs.x), dy, make_float2(awdx, awdx)));
+            g[1] = -(p.x + p.y);                                          // dq/dmy = -(2K b dx + 2K c dy)
+            const float sgq = gq.x + gq.y;
+            const float2 gqdy = __fmul2_rn(gq, dy);
+            const float sgqdy = gqdy.x + gqdy.y;
+            const float2 gqdy2 = __fmul2_rn(gqdy, dy);
+            g[2] = kNegHalfLog2e * dx * dx * sgq;                         // dq/dconic_xx = K dx^2
+            g[3] = 2.f * kNegHalfLog2e * dx * sgqdy;                      // dq/dconic_xy = 2K dx dy
+            g[4] = kNegHalfLog2e * (gqdy2.x + gqdy2.y);                   // dq/dconic_yy = K dy^2
+            p = __fmul2_rn(dLa_u, G);
+            g[5] = p.x + p.y;                                             // dalpha/do = G
+            // colour behind the previous Gaussian (normalised), then T_i
+            B0 = __ffma2_rn(ae, make_float2(c.x, c.x), __fmul2_rn(om, B0));
+            B1 = __ffma2_rn(ae, make_float2(c.y, c.y), __fmul2_rn(om, B1));
+            B2 = __ffma2_rn(ae, make_float2(c.z, c.z), __fmul2_rn(om, B2));
+            T = Ti;
+            float *dst = g2d + (size_t)s_item[k] * kG;
+            const float y = warp_sum8(g, lane);
+            float z = g[8];
 #pragma unroll
-            for (int q = 0; q < kG; ++q) g[q] = 0.f;
-            bool active = false;
-            if (j < my_last) {
-                const float4 A = s_a[k], Bs = s_b[k], c = s_c[k];
-                float dx, dy;
-                const float q = eval_q(A, Bs, fpx, fpy, dx, dy);
-                if (q >= kQ3) {
-                    const float G = ex2_approx(q);
-                    const float araw = __fmul_rn(Bs.y, G);
-                    const float alpha = fminf(kAlphaMax, araw);
-                    if (alpha >= kAlphaMin) {
-                        active = true;
-                        const float om = 1.f - alpha;
-                        const float Ti = T / om;
-                        const float wgt = alpha * Ti;
-                        g[6] = wgt * gI0;
-                        g[7] = wgt * gI1;
-                        g[8] = wgt * gI2;
-                        float dLda = Ti * (gI0 * (c.x - B0) + gI1 * (c.y - B1) + gI2 * (c.z - B2)) - gTT / om;
-                        if (araw < kAlphaMax) {
-                            const float gq = dLda * araw * kLn2;     // d alpha / d q = o G ln 2
-                            g[0] = -gq * (2.f * A.z * dx + A.w * dy);
-                            g[1] = -gq * (A.w * dx + 2.f * Bs.x * dy);
-                            g[2] = gq * kNegHalfLog2e * dx * dx;
-                            g[3] = gq * 2.f * kNegHalfLog2e * dx * dy;
-                            g[4] = gq * kNegHalfLog2e * dy * dy;
-                            g[5] = dLda * G;
-                        }
-                        B0 = fmaf(alpha, c.x, om * B0);
-                        B1 = fmaf(alpha, c.y, om * B1);
-                        B2 = fmaf(alpha, c.z, om * B2);
-                        T = Ti;
-                    }
-                }
-            }
-            if (__any_sync(0xffffffffu, active)) {
-                float *dst = g2d + (size_t)s_item[k] * kG;
-                const float y = warp_sum8(g, lane);
-                float z = g[8];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-                if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
-                if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
-            }
+            for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+            if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
+            if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
         }
         hi = lo;
     }
 }
 
-template <bool F32TEX>
-__global__ void __launch_bounds__(256)
+// add (r,g,b) to texel t of a [.][.][3] float array: texel t starts at float
+// 3t, so (r,g) is 8-byte aligned for even t and (g,b) for odd t -- one
+// vector and one scalar reduction
+__device__ __forceinline__ void red_texel(float *d_tex, size_t t, float r, float g, float b) {
+    float *d = d_tex + t * 3;
+    if ((t & 1) == 0) {
+        atomicAdd(reinterpret_cast<float2 *>(d), make_float2(r, g));
+        atomicAdd(d + 2, b);
+    } else {
+        atomicAdd(d, r);
+        atomicAdd(reinterpret_cast<float2 *>(d + 1), make_float2(g, b));
+    }
+}
+
+// One CTA per screen tile.  Each pixel with a triangle contributes
+// T * w_k * dL/dI_h to the 4 texels of its bilinear footprint.  The tile's
+// taps fall in a small texel box when the tile lies on one chart: they are
+// summed in shared memory and every touched texel is flushed with one
+// global reduction; a tile whose box exceeds kTexCap texels (it straddles
+// charts) reduces straight to global memory.
+constexpr int kTexCap = 1024;
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH)
 texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const float *__restrict__ uv,
                    const float *__restrict__ out_T, const float *__restrict__ dL_drgb, int tw, int th,
                    float *__restrict__ d_tex) {
-    const long long total = vt.total_pixels;
-    for (long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x; gp < total;
-         gp += (long long)gridDim.x * blockDim.x) {
-        if (!(mesh_depth[gp] < INFINITY)) continue;
-        const int v = view_of_pixel(vt, gp);
-        const ViewDev &V = vt.v[v];
-        const long long npx = (long long)V.W * V.H;
-        const long long lp = gp - V.pix_off;
+    constexpr int NT = TW * TH;
+    __shared__ float s_acc[kTexCap * 3];
+    __shared__ int s_box[4];
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(vt, gt);
+    const ViewDev &V = vt.v[v];
+    const int local = gt - V.tile_off;
+    const int t = threadIdx.x;
+    const int px = (local % V.tiles_x) * TW + (t % TW), py = (local / V.tiles_x) * TH + (t / TW);
+    const bool inside = px < V.W && py < V.H;
+    const long long npx = (long long)V.W * V.H;
+    const long long lp = (long long)py * V.W + px;
+    const long long gp = V.pix_off + lp;
+    bool act = inside && mesh_depth[gp] < INFINITY;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, fx = 0.f, fy = 0.f;
+    int ix = 0, iy = 0;
+    if (act) {
         const float T = out_T[gp];
         const float *g = dL_drgb + 3 * V.pix_off + lp;
-        const float g0 = T * g[0], g1 = T * g[npx], g2 = T * g[2 * npx];
+        g0 = T * g[0]; g1 = T * g[npx]; g2 = T * g[2 * npx];
         const float *u = uv + 2 * V.pix_off + lp;
         const float ss = u[0] * (float)tw - 0.5f, tt = u[npx] * (float)th - 0.5f;
         const float x0 = floorf(ss), y0 = floorf(tt);
-        const float fx = ss - x0, fy = tt - y0;
-        const int ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f), iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
-        const float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
-        const int xs[4] = {ix, ix + 1, ix, ix + 1}, ys[4] = {iy, iy, iy + 1, iy + 1};
+        fx = ss - x0; fy = tt - y0;
+        ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f);
+        iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
+    }
+    const int xa = min(max(ix, 0), tw - 1), xb = min(max(ix + 1, 0), tw - 1);
+    const int ya = min(max(iy, 0), th - 1), yb = min(max(iy + 1, 0), th - 1);
+    if (t == 0) { s_box[0] = 0x7fffffff; s_box[1] = -1; s_box[2] = 0x7fffffff; s_box[3] = -1; }
+    __syncthreads();
+    {   // texel box of the tile's taps: warp reductions, then one shared atomic per warp
+        const int mx0 = __reduce_min_sync(0xffffffffu, act ? xa : 0x7fffffff);
+        const int mx1 = __reduce_max_sync(0xffffffffu, act ? xb : -1);
+        const int my0 = __reduce_min_sync(0xffffffffu, act ? ya : 0x7fffffff);
+        const int my1 = __reduce_max_sync(0xffffffffu, act ? yb : -1);
+        if ((t & 31) == 0 && mx1 >= 0) {
+            atomicMin(&s_box[0], mx0); atomicMax(&s_box[1], mx1);
+            atomicMin(&s_box[2], my0); atomicMax(&s_box[3], my1);
+        }
+    }
+    __syncthreads();
+    const int bx0 = s_box[0], by0 = s_box[2];
+    if (s_box[1] < 0) return;                               // no pixel of the tile has a triangle
+    const int bw = s_box[1] - bx0 + 1, bh = s_box[3] - by0 + 1;
+    const float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+    const int xs[4] = {xa, xb, xa, xb}, ys[4] = {ya, ya, yb, yb};
+    if ((long long)bw * bh > kTexCap) {
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (w[k] != 0.f) red_texel(d_tex, (size_t)ys[k] * tw + xs[k], w[k] * g0, w[k] * g1, w[k] * g2);
+        }
+        return;
+    }
+    const int ncell = bw * bh;
+    for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0.f;
+    __syncthreads();
+    if (act) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (w[k] == 0.f) continue;
-            const int x = min(max(xs[k], 0), tw - 1), y = min(max(ys[k], 0), th - 1);
-            const size_t tix = (size_t)y * tw + x;
-            float *d = d_tex + tix * 3;
-            // texel t starts at float 3t: (r,g) is 8-byte aligned for even t,
-            // (g,b) for odd t -- one vector and one scalar reduction per tap
-            if ((tix & 1) == 0) {
-                atomicAdd(reinterpret_cast<float2 *>(d), make_float2(w[k] * g0, w[k] * g1));
-                atomicAdd(d + 2, w[k] * g2);
-            } else {
-                atomicAdd(d, w[k] * g0);
-                atomicAdd(reinterpret_cast<float2 *>(d + 1), make_float2(w[k] * g1, w[k] * g2));
-            }
+            float *a = s_acc + 3 * ((ys[k] - by0) * bw + (xs[k] - bx0));
+            atomicAdd(a, w[k] * g0);
+            atomicAdd(a + 1, w[k] * g1);
+            atomicAdd(a + 2, w[k] * g2);
         }
+    }
+    __syncthreads();
+    for (int i = t; i < ncell; i += NT) {
+        const float r = s_acc[3 * i], gg = s_acc[3 * i + 1], b = s_acc[3 * i + 2];
+        if (r != 0.f || gg != 0.f || b != 0.f)
+            red_texel(d_tex, (size_t)(by0 + i / bw) * tw + (bx0 + i % bw), r, gg, b);
     }
 }
 
@@ -486,12 +570,13 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     const float *bg = opt->bg;
     const int stages = opt->bwd_stages ? opt->bwd_stages : (HM_BWD_TEXTURE | HM_BWD_BLEND | HM_BWD_PROJECT);
     if (d_tex && (stages & HM_BWD_TEXTURE)) {
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        long long g = (vt.total_pixels + 255) / 256;
-        if (g > (long long)sms * 16) g = (long long)sms * 16;
-        texture_bwd_kernel<false><<<(unsigned)g, 256, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, tex_w, tex_h, d_tex);
+        dim3 tg(vt.total_tiles);
+#define HM_TBWD(TW, TH) \
+    texture_bwd_kernel<TW, TH><<<tg, TW * TH, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, tex_w, tex_h, d_tex)
+        if (opt->tile_w == 16) HM_TBWD(16, 16);
+        else if (opt->tile_w == 32) HM_TBWD(32, 8);
+        else HM_TBWD(8, 8);
+#undef HM_TBWD
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (n == 0) return HM_OK;
@@ -502,7 +587,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     e = cudaMemsetAsync(g2d, 0, sizeof(float) * kG * (size_t)n_views * n, s);
     if (e != cudaSuccess) return cuda_status(e);
 #define HM_BBWD(TW, TH)                                                                          \
-    blend_bwd_kernel<TW, TH><<<grid, TW * TH, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_rgb, \
+    blend_bwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_rgb, \
                                                       bg[0], bg[1], bg[2], out_T, last_idx,      \
                                                       dL_drgb, dL_dT, g2d)
     if (opt->tile_w == 16) HM_BBWD(16, 16);

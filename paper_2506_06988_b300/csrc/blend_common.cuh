@@ -38,4 +38,30 @@ __device__ __forceinline__ float eval_q(const float4 &A, const float4 &B, float 
     return __fmaf_rn(dx, __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy)), __fmul_rn(__fmul_rn(B.x, dy), dy));
 }
 
+// q = K d^2 at two pixel centres of one column, (fpx, fpy.x) and (fpx, fpy.y),
+// in packed FP32x2: dx is shared, K a dx^2 and 2K b dx once per Gaussian,
+// then q = K a dx^2 + dy (2K b dx + K c dy) for both pixels.
+__device__ __forceinline__ float2 eval_q2(const float4 &A, const float4 &B, float fpx, float2 fpy,
+                                          float &dx, float2 &dy) {
+    dx = __fsub_rn(fpx, A.x);
+    dy = __fadd2_rn(fpy, make_float2(-A.y, -A.y));
+    const float adx = __fmul_rn(__fmul_rn(A.z, dx), dx);
+    const float bdx = __fmul_rn(A.w, dx);
+    const float2 t = __ffma2_rn(make_float2(B.x, B.x), dy, make_float2(bdx, bdx));
+    return __ffma2_rn(dy, t, make_float2(adx, adx));
+}
+
+// alpha = min(0.99, o 2^q) for both pixels; G = 2^q, araw = o G
+__device__ __forceinline__ float2 eval_alpha2(float o, float2 q, float2 &G, float2 &araw) {
+    G = make_float2(ex2_approx(q.x), ex2_approx(q.y));
+    araw = __fmul2_rn(make_float2(o, o), G);
+    return make_float2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 }  // namespace hm

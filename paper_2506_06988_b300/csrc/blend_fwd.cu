@@ -1,9 +1,11 @@
 // blend_fwd.cu -- hybrid front-to-back blending (Eq. 2 with the mesh cut-off
 // and composite of Sec. 3.4).
 //
-// One CTA per screen tile, one thread per pixel.  The tile's depth-sorted
-// list is consumed in batches: each batch's records are gathered once into
-// shared memory and then evaluated by every pixel of the tile.  A pixel
+// One CTA per screen tile; a thread owns two pixels of one column (rows y and
+// y + TH/2), so the staged record, dx and the loop are shared by the pair and
+// the pair's arithmetic runs in packed FP32x2 (Blackwell FFMA2/FMUL2).  The
+// tile's depth-sorted list is consumed in batches: each batch's records are
+// gathered once into shared memory and then evaluated by every pixel.  A pixel
 // stops at the first Gaussian at or behind its mesh depth (the list is
 // depth-ordered, so all later ones are behind too) or when T would fall below
 // 1e-4; the CTA leaves the list as soon as every pixel has stopped
@@ -11,7 +13,8 @@
 // per-pixel work.
 //
 // Per evaluated (pixel, Gaussian): q = -log2(e)/2 * d^2 from the pre-scaled
-// conic (5 FP32 ops), one ex2, the alpha/T updates and three FMAs of colour.
+// conic, one ex2, the alpha/T updates and three FMAs of colour; updates are
+// masked (alpha 0 for a pixel that does not blend) instead of branched.
 #include "blend_common.cuh"
 #include "hm_host.h"
 
@@ -20,14 +23,14 @@ namespace hm {
 namespace {
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH)
+__global__ void __launch_bounds__(TW *TH / 2, 8)
 blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
                  const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_depth,
                  const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2, int batch,
                  float *__restrict__ out_rgb, float *__restrict__ out_T,
                  uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ last_idx,
                  unsigned long long *__restrict__ eval_stats) {
-    constexpr int NT = TW * TH;
+    constexpr int NT = TW * TH, NTH = NT / 2;
     __shared__ float4 s_a[NT];   // mean x, mean y, K*conic_xx, 2K*conic_xy
     __shared__ float4 s_b[NT];   // K*conic_yy, opacity, depth, -
     __shared__ float4 s_c[NT];   // r, g, b, -
@@ -37,68 +40,83 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x;
-    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
-    const bool inside = px < V.W && py < V.H;
+    // a thread owns two pixels of one column: rows ya and ya + TH/2
+    const int px = tx * TW + (t % TW), pya = ty * TH + (t / TW), pyb = pya + TH / 2;
+    const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
     const long long npx = (long long)V.W * V.H;
-    const long long lp = (long long)py * V.W + px;
-    const long long gp = V.pix_off + lp;
-    float Dm = INFINITY;
-    float back0 = bg0, back1 = bg1, back2 = bg2;
-    if (inside) {
-        if (mesh_depth) Dm = mesh_depth[gp];
-        if (mesh_rgb) {
-            const float *m = mesh_rgb + 3 * V.pix_off + lp;
-            back0 = m[0];
-            back1 = m[npx];
-            back2 = m[2 * npx];
-        }
+    const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
+    float Dm_a = INFINITY, Dm_b = INFINITY;
+    if (mesh_depth) {
+        if (in_a) Dm_a = mesh_depth[V.pix_off + lpa];
+        if (in_b) Dm_b = mesh_depth[V.pix_off + lpb];
     }
     const uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    bool done = !inside;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t cnt = 0, last = 0, n_eval = 0, n_exam = 0;
+    const float fpx = (float)px + 0.5f;
+    const float2 fpy = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
+    bool done_a = !in_a, done_b = !in_b;
+    float2 T = make_float2(1.f, 1.f);
+    float2 C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
+    uint32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0, n_eval = 0, n_exam = 0;
     for (uint32_t b0 = begin; b0 < end; b0 += batch) {
-        if (__syncthreads_count(done) == NT) break;
-        const uint32_t j = b0 + t;
-        if (t < batch && j < end) {
-            stage_record(rec[vals[j]], s_a[t], s_b[t], s_c[t]);
+        if (__syncthreads_count(done_a && done_b) == NTH) break;
+        for (int i = t; i < batch; i += NTH) {
+            const uint32_t j = b0 + i;
+            if (j < end) stage_record(rec[vals[j]], s_a[i], s_b[i], s_c[i]);
         }
         __syncthreads();
-        if (!done) {
-            const int nb = (int)min((uint32_t)batch, end - b0);
-            for (int k = 0; k < nb; ++k) {
-                const float4 A = s_a[k];
-                const float4 B = s_b[k];
-                if (B.z >= Dm) { done = true; break; }        // at or behind the mesh
-                float dx, dy;
-                const float q = eval_q(A, B, fpx, fpy, dx, dy);
-                if (eval_stats) ++n_exam;
-                if (q < kQ3) continue;                          // outside the 3-sigma ellipse
-                if (eval_stats) ++n_eval;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(B.y, ex2_approx(q)));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < kTMin) { done = true; break; }
-                const float w = alpha * T;
-                const float4 c = s_c[k];
-                C0 = fmaf(w, c.x, C0);
-                C1 = fmaf(w, c.y, C1);
-                C2 = fmaf(w, c.z, C2);
-                T = Tn;
-                ++cnt;
-                last = b0 + k + 1;
-            }
+        if (done_a && done_b) continue;
+        const int nb = (int)min((uint32_t)batch, end - b0);
+        for (int k = 0; k < nb; ++k) {
+            const float4 A = s_a[k];
+            const float4 B = s_b[k];
+            // at or behind the mesh: this and every later Gaussian is cut
+            done_a |= B.z >= Dm_a;
+            done_b |= B.z >= Dm_b;
+            if (done_a && done_b) break;
+            float dx;
+            float2 dy;
+            const float2 q = eval_q2(A, B, fpx, fpy, dx, dy);
+            bool ea = !done_a && q.x >= kQ3, eb = !done_b && q.y >= kQ3;   // inside the 3-sigma ellipse
+            if (eval_stats) n_exam += !done_a + !done_b, n_eval += ea + eb;
+            if (!(ea || eb)) continue;
+            float2 G, araw;
+            const float2 al = eval_alpha2(B.y, q, G, araw);
+            ea = ea && al.x >= kAlphaMin;
+            eb = eb && al.y >= kAlphaMin;
+            const float2 Tn = __ffma2_rn(make_float2(-T.x, -T.y), al, T);   // T (1 - alpha)
+            // stop before a Gaussian that would take T below 1e-4
+            if (ea && Tn.x < kTMin) { done_a = true; ea = false; }
+            if (eb && Tn.y < kTMin) { done_b = true; eb = false; }
+            const float2 ae = make_float2(ea ? al.x : 0.f, eb ? al.y : 0.f);
+            const float2 w = __fmul2_rn(ae, T);
+            const float4 c = s_c[k];
+            C0 = __ffma2_rn(w, make_float2(c.x, c.x), C0);
+            C1 = __ffma2_rn(w, make_float2(c.y, c.y), C1);
+            C2 = __ffma2_rn(w, make_float2(c.z, c.z), C2);
+            T = make_float2(ea ? Tn.x : T.x, eb ? Tn.y : T.y);
+            cnt_a += ea;
+            cnt_b += eb;
+            if (ea) last_a = b0 + k + 1;
+            if (eb) last_b = b0 + k + 1;
         }
     }
-    if (inside) {
-        float *o = out_rgb + 3 * V.pix_off + lp;
-        o[0] = fmaf(T, back0, C0);
-        o[npx] = fmaf(T, back1, C1);
-        o[2 * npx] = fmaf(T, back2, C2);
-        out_T[gp] = T;
-        n_contrib[gp] = cnt;
-        if (last_idx) last_idx[gp] = last;
+    const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
+    float *o = out_rgb + 3 * V.pix_off;
+    if (in_a) {
+        o[lpa] = fmaf(T.x, mr ? mr[lpa] : bg0, C0.x);
+        o[npx + lpa] = fmaf(T.x, mr ? mr[npx + lpa] : bg1, C1.x);
+        o[2 * npx + lpa] = fmaf(T.x, mr ? mr[2 * npx + lpa] : bg2, C2.x);
+        out_T[V.pix_off + lpa] = T.x;
+        n_contrib[V.pix_off + lpa] = cnt_a;
+        if (last_idx) last_idx[V.pix_off + lpa] = last_a;
+    }
+    if (in_b) {
+        o[lpb] = fmaf(T.y, mr ? mr[lpb] : bg0, C0.y);
+        o[npx + lpb] = fmaf(T.y, mr ? mr[npx + lpb] : bg1, C1.y);
+        o[2 * npx + lpb] = fmaf(T.y, mr ? mr[2 * npx + lpb] : bg2, C2.y);
+        out_T[V.pix_off + lpb] = T.y;
+        n_contrib[V.pix_off + lpb] = cnt_b;
+        if (last_idx) last_idx[V.pix_off + lpb] = last_b;
     }
     if (eval_stats) {
         unsigned long long e = n_eval, x = n_exam;
@@ -141,7 +159,7 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
     dim3 grid(vt.total_tiles);
     const float *bg = opt->bg;
 #define HM_BLEND(TW, TH)                                                                        \
-    blend_fwd_kernel<TW, TH><<<grid, TW * TH, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_depth, \
+    blend_fwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_depth, \
                                                       mesh_rgb, bg[0], bg[1], bg[2], opt->batch,   \
                                                       out_rgb, out_T, n_contrib, last_idx, eval_stats)
     if (opt->tile_w == 16) HM_BLEND(16, 16);

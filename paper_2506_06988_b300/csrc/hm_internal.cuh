@@ -120,9 +120,10 @@ inline long long scan_tiles(long long n) { return (n + kScanTile - 1) / kScanTil
 
 // out[i] = sum_{j<i} in[idx ? idx[j] : j] (uint32, exclusive); *total (int64)
 // = the full sum; if capacity >= 0 and the sum exceeds it, HM_DEV_CAPACITY.
+// The element count is n, or *n_dev (<= n) when n_dev is given.
 cudaError_t launch_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, long long n,
                         long long *total, long long capacity, int32_t *d_status, ScanWs ws,
-                        cudaStream_t s);
+                        cudaStream_t s, const long long *n_dev = nullptr);
 
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;

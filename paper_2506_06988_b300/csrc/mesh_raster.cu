@@ -9,12 +9,12 @@
 //   scan + emit   one (face, tile) work item per touched tile;
 //   coverage      one warp per item: exact int64 edge functions (stepped
 //                 incrementally down each lane's column) with the top-left
-//                 rule at the tile's pixel centres; the depth
-//                 fp32(W) / fp32(S), S = sum_k(w_k / z_k) in FP64, is packed
-//                 with the face index into a 64-bit key and merged with
-//                 atomicMin into a per-pixel visibility word -- the minimum
-//                 is (nearest FP32 depth, lowest face index) whatever the
-//                 order the items run in;
+//                 rule at the tile's pixel centres; the depth is the FP32
+//                 reciprocal of the face's affine 1/z (coefficients from the
+//                 face pass), packed with the face index into a 64-bit key
+//                 and merged with atomicMin into a per-pixel visibility
+//                 word -- the minimum is (nearest FP32 depth, lowest face
+//                 index) whatever the order the items run in;
 //   resolve       one CTA per tile: perspective-correct UVs, bilinear
 //                 clamp-to-edge texel fetch, outputs, per-tile farthest mesh
 //                 depth (for the Gaussian pair cull).
@@ -35,8 +35,9 @@ struct FaceSetup {
     long long area2;         // |signed double area| (1/256 px)^2
     int flip;                // signed area negative: traverse 0 -> 2 -> 1
     int tx0, tx1, ty0, ty1;  // touched tiles (empty: tx0 > tx1)
-    float Wf;                // fp32(area2)
-    double iz[3];            // 1 / view z per vertex
+    float iz0f, af, bf;      // 1/z = iz0 + a U + b V, (U,V) = centre - vertex 0 in pixels
+    float izf[3];            // 1 / view z per vertex (FP32)
+    float rD;                // 1 / signed double area
 };
 
 __global__ void __launch_bounds__(256)
@@ -85,24 +86,39 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
         const ViewDev &V = vt.v[v];
         FaceSetup s;
         s.tx0 = 1; s.tx1 = 0; s.ty0 = 1; s.ty1 = 0;
-        s.flip = 0; s.area2 = 0; s.Wf = 0.f;
+        s.flip = 0; s.area2 = 0;
+        s.iz0f = s.af = s.bf = s.rD = 0.f;
+        double izd[3];
         bool ok = true;
         for (int k = 0; k < 3; ++k) {
             const int vi = faces[3 * f + k];
-            if (vi < 0 || vi >= nv) { ok = false; s.x[k] = s.y[k] = 0; s.iz[k] = 0; continue; }
+            s.izf[k] = 0.f;
+            izd[k] = 0.0;
+            if (vi < 0 || vi >= nv) { ok = false; s.x[k] = s.y[k] = 0; continue; }
             const int2 p = sxy[(long long)v * nv + vi];
             s.x[k] = p.x; s.y[k] = p.y;
-            s.iz[k] = iz[(long long)v * nv + vi];
+            izd[k] = iz[(long long)v * nv + vi];
+            s.izf[k] = __double2float_rn(izd[k]);
             if (p.x == kInvalid) ok = false;
         }
         uint32_t c = 0;
         if (ok) {
-            const long long a2 = (long long)(s.x[1] - s.x[0]) * (s.y[2] - s.y[0]) -
-                                 (long long)(s.y[1] - s.y[0]) * (s.x[2] - s.x[0]);
+            const long long e1x = (long long)s.x[1] - s.x[0], e1y = (long long)s.y[1] - s.y[0];
+            const long long e2x = (long long)s.x[2] - s.x[0], e2y = (long long)s.y[2] - s.y[0];
+            const long long a2 = e1x * e2y - e1y * e2x;
             if (a2 != 0) {
                 s.flip = a2 < 0;
                 s.area2 = a2 < 0 ? -a2 : a2;
-                s.Wf = __ll2float_rn(s.area2);
+                // screen-space barycentrics of the offset (dx,dy) from vertex 0 (Cramer):
+                // l1 = (dx e2y - dy e2x)/D, l2 = (e1x dy - e1y dx)/D, so
+                // 1/z = iz0 + (iz1-iz0) l1 + (iz2-iz0) l2 = iz0 + a dx + b dy
+                const double d1 = izd[1] - izd[0], d2 = izd[2] - izd[0];
+                const double na = fma(d1, (double)e2y, -(d2 * (double)e1y));
+                const double nb = fma(d2, (double)e1x, -(d1 * (double)e2x));
+                s.af = __double2float_rn((na * 256.0) / (double)a2);
+                s.bf = __double2float_rn((nb * 256.0) / (double)a2);
+                s.iz0f = __double2float_rn(izd[0]);
+                s.rD = __double2float_rn(1.0 / (double)a2);
                 const long long mnx = min(s.x[0], min(s.x[1], s.x[2])), mxx = max(s.x[0], max(s.x[1], s.x[2]));
                 const long long mny = min(s.y[0], min(s.y[1], s.y[2])), mxy = max(s.y[0], max(s.y[1], s.y[2]));
                 // pixel centres 256 x + 128 inside [mn, mx]
@@ -148,20 +164,6 @@ __device__ __forceinline__ bool edge_in(long long ax, long long ay, long long bx
     return E > 0 || (E == 0 && (dy < 0 || (dy == 0 && dx > 0)));
 }
 
-// barycentric numerators w[k] (face vertex order) if the centre is covered
-__device__ __forceinline__ bool face_cover(const FaceSetup &s, long long px, long long py,
-                                           long long w[3]) {
-    const int b = s.flip ? 2 : 1, c = s.flip ? 1 : 2;   // oriented order 0, b, c
-    long long e0b, ebc, ec0;
-    if (!edge_in(s.x[0], s.y[0], s.x[b], s.y[b], px, py, e0b)) return false;
-    if (!edge_in(s.x[b], s.y[b], s.x[c], s.y[c], px, py, ebc)) return false;
-    if (!edge_in(s.x[c], s.y[c], s.x[0], s.y[0], px, py, ec0)) return false;
-    w[0] = ebc;   // weight of a vertex: edge function of the opposite edge
-    w[b] = ec0;
-    w[c] = e0b;
-    return true;
-}
-
 template <int TW, int TH>
 __global__ void __launch_bounds__(256)
 mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
@@ -198,6 +200,8 @@ mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             tl[e] = dy < 0 || (dy == 0 && dx > 0);
         }
         const unsigned long long fkey = f;
+        // depth: 1 / fma(a, U, fma(b, V, 1/z0)) at the offset from vertex 0, in pixels
+        const float U = __fmul_rn(__int2float_rn((int)(PX - s.x[0])), 0.00390625f);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             const int py = py0 + k * YS;
@@ -205,13 +209,8 @@ mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             const bool in = (E[0] > 0 || (E[0] == 0 && tl[0])) && (E[1] > 0 || (E[1] == 0 && tl[1])) &&
                             (E[2] > 0 || (E[2] == 0 && tl[2]));
             if (in) {
-                // weight of a vertex = edge function of the opposite edge
-                long long wgt[3];
-                wgt[0] = E[1];
-                wgt[b] = E[2];
-                wgt[c] = E[0];
-                const double S = fma((double)wgt[2], s.iz[2], fma((double)wgt[1], s.iz[1], (double)wgt[0] * s.iz[0]));
-                const float D = __fdiv_rn(s.Wf, __double2float_rn(S));
+                const float Vv = __fmul_rn(__int2float_rn((int)((long long)py * 256 + 128 - s.y[0])), 0.00390625f);
+                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
                 atomicMin(&vis[V.pix_off + (long long)py * V.W + px],
                           ((unsigned long long)__float_as_uint(D) << 32) | fkey);
             }
@@ -261,21 +260,20 @@ mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             id = (int)(unsigned)(key & 0xFFFFFFFFu);
             D = __uint_as_float((unsigned)(key >> 32));
             const FaceSetup s = setup[(long long)v * nf + id];
-            long long wgt[3];
-            face_cover(s, (long long)px * 256 + 128, (long long)py * 256 + 128, wgt);
-            float b[3], sum = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                b[k] = (float)wgt[k] * (float)s.iz[k];
-                sum += b[k];
-            }
-            const float rs = 1.f / sum;
+            // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
+            // screen-space ones of the offset from vertex 0 (Cramer's rule)
+            const float dx = (float)((long long)px * 256 + 128 - s.x[0]);
+            const float dy = (float)((long long)py * 256 + 128 - s.y[0]);
+            const float e1x = (float)(s.x[1] - s.x[0]), e1y = (float)(s.y[1] - s.y[0]);
+            const float e2x = (float)(s.x[2] - s.x[0]), e2y = (float)(s.y[2] - s.y[0]);
+            const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
+            const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
+            const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;
             // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
             // for small faces, so uv keeps close to FP32 rounding of its value
             const int v0i = faces[3 * (long long)id], v1i = faces[3 * (long long)id + 1],
                       v2i = faces[3 * (long long)id + 2];
             const float u0 = __ldg(uvs + 2 * (long long)v0i), w0 = __ldg(uvs + 2 * (long long)v0i + 1);
-            const float b1 = b[1] * rs, b2 = b[2] * rs;
             u = u0 + fmaf(b1, __ldg(uvs + 2 * (long long)v1i) - u0, b2 * (__ldg(uvs + 2 * (long long)v2i) - u0));
             w = w0 + fmaf(b1, __ldg(uvs + 2 * (long long)v1i + 1) - w0, b2 * (__ldg(uvs + 2 * (long long)v2i + 1) - w0));
             const float ss = u * (float)tw - 0.5f, tt = w * (float)th - 0.5f;

@@ -18,17 +18,24 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
 __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ idx,
-            uint32_t *__restrict__ out, long long n, long long *total, long long capacity,
-            int32_t *d_status, unsigned long long *tstat, unsigned int *ticket) {
+            uint32_t *__restrict__ out, long long n_host, const long long *n_dev, long long *total,
+            long long capacity, int32_t *d_status, unsigned long long *tstat, unsigned int *ticket) {
     __shared__ uint32_t s_buf[kScanTile];
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_prefix;
     __shared__ unsigned int s_tile;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long n = n_dev ? *n_dev : n_host;
     if (t == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
     const long long tile = s_tile;
     const long long base = tile * kScanTile;
+    if (base >= n) {
+        // beyond the element count (count held on the device): nothing to do;
+        // an empty input still reports a zero total
+        if (t == 0 && tile == 0 && total) *total = 0;
+        return;
+    }
 
     // striped (coalesced) load into shared memory
 #pragma unroll
@@ -125,7 +132,7 @@ cudaError_t launch_fill_i64(long long *p, long long v, cudaStream_t s) {
 
 cudaError_t launch_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, long long n,
                         long long *total, long long capacity, int32_t *d_status, ScanWs ws,
-                        cudaStream_t s) {
+                        cudaStream_t s, const long long *n_dev) {
     long long tiles = scan_tiles(n);
     cudaError_t e = cudaMemsetAsync(ws.ticket, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
@@ -135,8 +142,8 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, 
     }
     e = cudaMemsetAsync(ws.tile_status, 0, sizeof(unsigned long long) * tiles, s);
     if (e != cudaSuccess) return e;
-    scan_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, idx, out, n, total, capacity, d_status,
-                                                         ws.tile_status, ws.ticket);
+    scan_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, idx, out, n, n_dev, total, capacity,
+                                                         d_status, ws.tile_status, ws.ticket);
     return cudaGetLastError();
 }
 
