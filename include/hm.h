@@ -227,6 +227,38 @@ hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, c
                             float *d_means, float *d_scales, float *d_quats, float *d_opacity,
                             float *d_sh, float *d_tex, void *ws, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* hm_blend_backward_noalloc -- hm_blend_backward for callers that cannot
+ * allocate device memory: code running inside a CUDA stream capture, a
+ * host whose allocator is owned by someone else (a plug-in, an embedded
+ * runtime), or a real-time loop that must not allocate.  The paper has no
+ * counterpart; it is a convenience of this library.
+ *
+ * Same arguments and results as hm_blend_backward, without ws/ws_bytes: the
+ * scratch is a library-owned static device array of HM_BWD_NOALLOC_BYTES
+ * bytes (16 MiB), which every GPU that loads the library holds until the
+ * process exits.  Problems needing more (9 floats per record: n_views * n
+ * above 466,026) are rejected with HM_ERR_INVALID_ARG and a message.  The
+ * first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array, which keeps the last call's contents (the call
+ * clears what it needs): calls that overlap on the GPU -- on two streams, or
+ * a HM_BWD_PROJECT-only call after another call's HM_BWD_BLEND -- race and
+ * give wrong gradients.  No allocation happens in this call. */
+#define HM_BWD_NOALLOC_BYTES (16u << 20)
+hm_status hm_blend_backward_noalloc(const hm_camera *cams, int32_t n_views, int32_t n,
+                                    const float *means, const float *scales, const float *quats,
+                                    const float *opacity, const void *sh, int32_t sh_degree,
+                                    int32_t sh_format, const void *records,
+                                    const uint32_t *pair_vals, const uint32_t *tile_ranges,
+                                    const float *mesh_depth, const float *mesh_rgb,
+                                    const float *mesh_uv, int32_t tex_w, int32_t tex_h,
+                                    const hm_options *opt, const float *out_T,
+                                    const uint32_t *last_idx, const float *dL_drgb,
+                                    const float *dL_dT, float *d_means, float *d_scales,
+                                    float *d_quats, float *d_opacity, float *d_sh, float *d_tex,
+                                    void *stream);
+
 /* Number of tiles of all cameras for the tile shape in `opt`. */
 int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options *opt);
 

@@ -22,6 +22,8 @@
 //    Jacobian, the projection of the mean, the quaternion normalisation and
 //    the SH colour (including its dependence on the mean through the view
 //    direction), summing over cameras without atomics.
+#include <mutex>
+
 #include "blend_common.cuh"
 #include "hm_host.h"
 #include "sh.cuh"
@@ -605,4 +607,61 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
         default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
     }
     return cuda_status(e);
+}
+
+// ---------------------------------------------------------------------------
+// hm_blend_backward_noalloc: the same pass with its scratch in a static device
+// array, for callers that cannot allocate (see hm.h).
+// ---------------------------------------------------------------------------
+namespace hm {
+namespace {
+
+static __device__ __align__(256) unsigned char g_bwd_noalloc_scratch[HM_BWD_NOALLOC_BYTES];
+
+// device address of the array per device, looked up once with that device current
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {};
+
+hm_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return fail(HM_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_bwd_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HM_OK;
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_blend_backward_noalloc(
+    const hm_camera *cams, int32_t n_views, int32_t n, const float *means, const float *scales,
+    const float *quats, const float *opacity, const void *sh, int32_t sh_degree, int32_t sh_format,
+    const void *records, const uint32_t *pair_vals, const uint32_t *tile_ranges,
+    const float *mesh_depth, const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
+    int32_t tex_h, const hm_options *opt, const float *out_T, const uint32_t *last_idx,
+    const float *dL_drgb, const float *dL_dT, float *d_means, float *d_scales, float *d_quats,
+    float *d_opacity, float *d_sh, float *d_tex, void *stream) {
+    if (n_views < 1 || n < 0) return fail(HM_ERR_INVALID_ARG, "bad n_views or n");
+    const size_t need = hm_blend_backward_workspace_size(n_views, n);
+    if (need > HM_BWD_NOALLOC_BYTES)
+        return fail(HM_ERR_INVALID_ARG,
+                    "n_views * n = %lld needs %zu bytes of scratch, above the %u-byte static array "
+                    "of hm_blend_backward_noalloc; use hm_blend_backward with a workspace",
+                    (long long)n_views * n, need, (unsigned)HM_BWD_NOALLOC_BYTES);
+    void *ws = nullptr;
+    const hm_status st = noalloc_scratch(&ws);
+    if (st != HM_OK) return st;
+    return hm_blend_backward(cams, n_views, n, means, scales, quats, opacity, sh, sh_degree,
+                             sh_format, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb,
+                             mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means,
+                             d_scales, d_quats, d_opacity, d_sh, d_tex, ws, HM_BWD_NOALLOC_BYTES,
+                             stream);
 }

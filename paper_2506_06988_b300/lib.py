@@ -30,6 +30,7 @@ HM_SH_F16 = 1
 HM_BWD_TEXTURE = 1
 HM_BWD_BLEND = 2
 HM_BWD_PROJECT = 4
+HM_BWD_NOALLOC_BYTES = 16 << 20
 
 EXPORTS = [
     "hm_default_options", "hm_last_error", "hm_total_tiles",
@@ -37,7 +38,7 @@ EXPORTS = [
     "hm_project_gaussians",
     "hm_bin_sort_workspace_size", "hm_bin_sort",
     "hm_blend_forward",
-    "hm_blend_backward_workspace_size", "hm_blend_backward",
+    "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
 ]
 
 
@@ -85,6 +86,11 @@ _SIGS = {
                                     _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_size_t, c_void_p]),
+    "hm_blend_backward_noalloc": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                            _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 
@@ -206,3 +212,19 @@ def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_
                                     _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
                                     _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacity),
                                     _ptr(d_sh), _ptr(d_tex), _ptr(ws), ws_bytes, stream)
+
+
+def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format,
+                              records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w,
+                              tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats,
+                              d_opacity, d_sh, d_tex, stream):
+    """hm_blend_backward without a workspace argument: the scratch is the
+    library's static 16 MiB device array (for callers that cannot allocate)."""
+    return load().hm_blend_backward_noalloc(cams, len(cams), n, _ptr(means), _ptr(scales),
+                                            _ptr(quats), _ptr(opacity), _ptr(sh), sh_degree,
+                                            sh_format, _ptr(records), _ptr(pair_vals),
+                                            _ptr(tile_ranges), _ptr(mesh_depth), _ptr(mesh_rgb),
+                                            _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
+                                            _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
+                                            _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
+                                            _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex), stream)
