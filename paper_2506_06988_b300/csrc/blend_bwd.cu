@@ -16,7 +16,7 @@
 //    per-record accumulators with one atomic per value per warp.
 //  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
 //    triangle (the mesh colour enters I_h weighted by T), summed per screen
-//    tile in shared memory before the global reductions.
+//    tile in shared memory (fixed point) before the global reductions.
 //  * project_bwd: one thread per Gaussian chains the per-record partials
 //    through the conic inverse, Sigma' = V V^T, V = (J W)(R S), the clamped
 //    Jacobian, the projection of the mean, the quaternion normalisation and
@@ -206,9 +206,9 @@ __device__ __forceinline__ void red_texel(float *d_tex, size_t t, float r, float
 // One CTA per screen tile.  Each pixel with a triangle contributes
 // T * w_k * dL/dI_h to the 4 texels of its bilinear footprint.  The tile's
 // taps fall in a small texel box when the tile lies on one chart: they are
-// summed in shared memory and every touched texel is flushed with one
-// global reduction; a tile whose box exceeds kTexCap texels (it straddles
-// charts) reduces straight to global memory.
+// summed in shared memory (int32 fixed point) and every touched texel is
+// flushed with one global reduction; a tile whose box exceeds kTexCap texels
+// (it straddles charts) reduces straight to global memory.
 constexpr int kTexCap = 1024;
 
 template <int TW, int TH>
@@ -217,8 +217,9 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
                    const float *__restrict__ out_T, const float *__restrict__ dL_drgb, int tw, int th,
                    float *__restrict__ d_tex) {
     constexpr int NT = TW * TH;
-    __shared__ float s_acc[kTexCap * 3];
+    __shared__ int s_acc[kTexCap * 3];
     __shared__ int s_box[4];
+    __shared__ int s_max[3];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -245,21 +246,28 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     }
     const int xa = min(max(ix, 0), tw - 1), xb = min(max(ix + 1, 0), tw - 1);
     const int ya = min(max(iy, 0), th - 1), yb = min(max(iy + 1, 0), th - 1);
-    if (t == 0) { s_box[0] = 0x7fffffff; s_box[1] = -1; s_box[2] = 0x7fffffff; s_box[3] = -1; }
+    if (t == 0) {
+        s_box[0] = 0x7fffffff; s_box[1] = -1; s_box[2] = 0x7fffffff; s_box[3] = -1;
+        s_max[0] = s_max[1] = s_max[2] = 0;
+    }
     __syncthreads();
-    {   // texel box of the tile's taps: warp reductions, then one shared atomic per warp
+    {
         const int mx0 = __reduce_min_sync(0xffffffffu, act ? xa : 0x7fffffff);
         const int mx1 = __reduce_max_sync(0xffffffffu, act ? xb : -1);
         const int my0 = __reduce_min_sync(0xffffffffu, act ? ya : 0x7fffffff);
         const int my1 = __reduce_max_sync(0xffffffffu, act ? yb : -1);
+        const int m0 = __reduce_max_sync(0xffffffffu, __float_as_int(fabsf(g0)));
+        const int m1 = __reduce_max_sync(0xffffffffu, __float_as_int(fabsf(g1)));
+        const int m2 = __reduce_max_sync(0xffffffffu, __float_as_int(fabsf(g2)));
         if ((t & 31) == 0 && mx1 >= 0) {
             atomicMin(&s_box[0], mx0); atomicMax(&s_box[1], mx1);
             atomicMin(&s_box[2], my0); atomicMax(&s_box[3], my1);
+            atomicMax(&s_max[0], m0); atomicMax(&s_max[1], m1); atomicMax(&s_max[2], m2);
         }
     }
     __syncthreads();
     const int bx0 = s_box[0], by0 = s_box[2];
-    if (s_box[1] < 0) return;                               // no pixel of the tile has a triangle
+    if (s_box[1] < 0) return;
     const int bw = s_box[1] - bx0 + 1, bh = s_box[3] - by0 + 1;
     const float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
     const int xs[4] = {xa, xb, xa, xb}, ys[4] = {ya, ya, yb, yb};
@@ -271,24 +279,38 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         }
         return;
     }
+    // Fixed point per channel: the tile's largest |T dL/dI| maps to
+    // [2^21, 2^22).  A pixel's taps have weights summing to 1, so a texel
+    // receives at most the tile's 256 pixels' worth: |sum| < 2^30 + 512 (one
+    // rounding per tap) fits int32.  Integer shared atomics are native and
+    // the sum is exact; each tap is rounded to 2^-22 of the tile maximum.
+    float sc[3], isc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int e = ((s_max[c] >> 23) & 0xff) - 127;
+        const int se = min(max(21 - e, -126), 127);
+        sc[c] = __int_as_float((se + 127) << 23);
+        isc[c] = __int_as_float((127 - se) << 23);
+    }
     const int ncell = bw * bh;
-    for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0.f;
+    for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0;
     __syncthreads();
     if (act) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (w[k] == 0.f) continue;
-            float *a = s_acc + 3 * ((ys[k] - by0) * bw + (xs[k] - bx0));
-            atomicAdd(a, w[k] * g0);
-            atomicAdd(a + 1, w[k] * g1);
-            atomicAdd(a + 2, w[k] * g2);
+            int *a = s_acc + 3 * ((ys[k] - by0) * bw + (xs[k] - bx0));
+            atomicAdd(a, __float2int_rn(w[k] * g0 * sc[0]));
+            atomicAdd(a + 1, __float2int_rn(w[k] * g1 * sc[1]));
+            atomicAdd(a + 2, __float2int_rn(w[k] * g2 * sc[2]));
         }
     }
     __syncthreads();
     for (int i = t; i < ncell; i += NT) {
-        const float r = s_acc[3 * i], gg = s_acc[3 * i + 1], b = s_acc[3 * i + 2];
-        if (r != 0.f || gg != 0.f || b != 0.f)
-            red_texel(d_tex, (size_t)(by0 + i / bw) * tw + (bx0 + i % bw), r, gg, b);
+        const int r = s_acc[3 * i], gg = s_acc[3 * i + 1], b = s_acc[3 * i + 2];
+        if (r != 0 || gg != 0 || b != 0)
+            red_texel(d_tex, (size_t)(by0 + i / bw) * tw + (bx0 + i % bw), (float)r * isc[0],
+                      (float)gg * isc[1], (float)b * isc[2]);
     }
 }
 

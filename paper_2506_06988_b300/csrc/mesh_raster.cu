@@ -155,15 +155,6 @@ mesh_emit_kernel(long long m, const FaceSetup *__restrict__ setup, const uint32_
     }
 }
 
-// edge a->b of a positively oriented triangle (y down): inside E > 0; a
-// centre exactly on an edge belongs to it iff the edge is top or left
-__device__ __forceinline__ bool edge_in(long long ax, long long ay, long long bx, long long by,
-                                        long long px, long long py, long long &E) {
-    const long long dx = bx - ax, dy = by - ay;
-    E = dx * (py - ay) - dy * (px - ax);
-    return E > 0 || (E == 0 && (dy < 0 || (dy == 0 && dx > 0)));
-}
-
 template <int TW, int TH>
 __global__ void __launch_bounds__(256)
 mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
@@ -262,10 +253,11 @@ mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             const FaceSetup s = setup[(long long)v * nf + id];
             // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
             // screen-space ones of the offset from vertex 0 (Cramer's rule)
-            const float dx = (float)((long long)px * 256 + 128 - s.x[0]);
-            const float dy = (float)((long long)py * 256 + 128 - s.y[0]);
-            const float e1x = (float)(s.x[1] - s.x[0]), e1y = (float)(s.y[1] - s.y[0]);
-            const float e2x = (float)(s.x[2] - s.x[0]), e2y = (float)(s.y[2] - s.y[0]);
+            // (snapped coordinates stay within +-2^29, so the differences fit int32)
+            const float dx = __int2float_rn(px * 256 + 128 - s.x[0]);
+            const float dy = __int2float_rn(py * 256 + 128 - s.y[0]);
+            const float e1x = __int2float_rn(s.x[1] - s.x[0]), e1y = __int2float_rn(s.y[1] - s.y[0]);
+            const float e2x = __int2float_rn(s.x[2] - s.x[0]), e2y = __int2float_rn(s.y[2] - s.y[0]);
             const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
             const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
             const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;

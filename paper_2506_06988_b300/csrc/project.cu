@@ -7,13 +7,13 @@
 // number of views; the view-independent factor M = R(q) S is formed once.
 //
 // Numerics.
-//  * The view-space point is evaluated in FP64 with the fixed FMA order
-//    fma(R_k0, x, fma(R_k1, y, fma(R_k2, z, t_k))); the depth key is that z
-//    rounded once to FP32, bit-identical to the definition the sort and the
-//    mesh cut-off rely on.
-//  * x/z and y/z are formed in FP32 from the FP64 values split into
-//    float-float pairs plus one residual correction, so the projected mean
-//    carries close to FP32 rounding only.
+//  * The depth key is fp32(fma(R20, x, fma(R21, y, fma(R22, z, t2)))) in
+//    FP64, bit-identical to the definition the sort and the mesh cut-off
+//    rely on (4 FP64 operations per camera and Gaussian -- the FP64 pipe is
+//    1/64 of the FP32 rate on B300).
+//  * The view-space point used for the projection is a float-float
+//    (TwoProduct/TwoSum) evaluation in FP32, and x/z, y/z take one residual
+//    correction, so the projected mean carries close to FP32 rounding only.
 //  * Sigma' is formed as V V^T with V = (J W)(R S) (2x3).  det(Sigma' + 0.3 I)
 //    = |V0 x V1|^2 + 0.3 (|V0|^2 + |V1|^2) + 0.09 (Lagrange's identity) is a
 //    sum of non-negative terms, with the cross product from FMA-based
@@ -52,12 +52,31 @@ __device__ __forceinline__ float dot3_c(const float *u, const float *v) {
     return s + c;
 }
 
-// accurate FP32 x/z from FP64 x and z
-__device__ __forceinline__ float ratio_ff(double x, float zf, float zl, float rz) {
-    float xf = __double2float_rn(x);
-    float xl = __double2float_rn(x - (double)xf);
-    float q0 = xf * rz;
-    float e = fmaf(-q0, zf, xf);
+// r0 x + r1 y + r2 z + t as an unevaluated float-float sum (hi, lo):
+// TwoProduct (FMA) for each product and TwoSum for each addition, so the
+// pair carries the value to ~2^-46 relative -- no FP64 needed
+__device__ __forceinline__ void dot3t_ff(const float *r, float t, float x, float y, float z,
+                                         float &hi, float &lo) {
+    const float v[3] = {x, y, z};
+    float s = t, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float p = r[k] * v[k];
+        const float pe = fmaf(r[k], v[k], -p);
+        const float u = s + p;
+        const float bb = u - s;
+        const float se = (s - (u - bb)) + (p - bb);
+        s = u;
+        c += pe + se;
+    }
+    hi = s + c;
+    lo = c - (hi - s);
+}
+
+// accurate FP32 (xh + xl) / (zh + zl), rz = 1/zh
+__device__ __forceinline__ float ratio_ff(float xh, float xl, float zh, float zl, float rz) {
+    const float q0 = xh * rz;
+    float e = fmaf(-q0, zh, xh);
     e += xl - q0 * zl;
     return fmaf(e, rz, q0);
 }
@@ -114,12 +133,13 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
         r.b = make_float4(0.f, op, zf, __uint_as_float(kEmptyRange));
         r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(kEmptyRange));
         if (zf > near_z) {
-            const double tx = fma((double)V.R[0], dx, fma((double)V.R[1], dy, fma((double)V.R[2], dz, (double)V.t[0])));
-            const double ty = fma((double)V.R[3], dx, fma((double)V.R[4], dy, fma((double)V.R[5], dz, (double)V.t[1])));
-            const float zl = __double2float_rn(tz - (double)zf);
-            const float rz = __frcp_rn(zf);
-            const float qx = ratio_ff(tx, zf, zl, rz);
-            const float qy = ratio_ff(ty, zf, zl, rz);
+            float xh, xl, yh, yl, zh, zl;
+            dot3t_ff(&V.R[0], V.t[0], mx, my, mz, xh, xl);
+            dot3t_ff(&V.R[3], V.t[1], mx, my, mz, yh, yl);
+            dot3t_ff(&V.R[6], V.t[2], mx, my, mz, zh, zl);
+            const float rz = __frcp_rn(zh);
+            const float qx = ratio_ff(xh, xl, zh, zl, rz);
+            const float qy = ratio_ff(yh, yl, zh, zl, rz);
             const float u = fmaf(V.fx, qx, V.cx);
             const float w = fmaf(V.fy, qy, V.cy);
             // affine Jacobian with the 1.3 x half-FOV clamp
