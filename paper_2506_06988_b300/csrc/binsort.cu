@@ -97,9 +97,11 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const floa
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
-         base += nw * 32) {
-        const long long it = base + lane;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // lane l of warp w takes element w + nw (l + 32 k): a warp's records are
+    // spread over the whole range, so large ones do not pile up in one warp
+    for (long long base = w0; base < m; base += nw * 32) {
+        const long long it = base + (long long)lane * nw;
         const bool valid = it < m;
         BinRec r;
         int nt = 0;
@@ -160,9 +162,11 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < m;
-         base += nw * 32) {
-        const long long j = base + lane;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // strided as in the count: the depth order puts the large near-camera
+    // records together, and a warp walks its large records one at a time
+    for (long long base = w0; base < m; base += nw * 32) {
+        const long long j = base + (long long)lane * nw;
         bool valid = j < m;
         uint32_t it = 0, k = 0;
         long long o = 0;

@@ -77,8 +77,8 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x, lane = t & 31;
-    // two pixels of one column, rows ya and ya + TH/2 (as in the forward)
-    const int px = tx * TW + (t % TW), pya = ty * TH + (t / TW), pyb = pya + TH / 2;
+    int px, pya, pyb;
+    pixel_pair<TW>(t, tx * TW, ty * TH, px, pya, pyb);
     const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
     const long long npx = (long long)V.W * V.H;
     const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
@@ -137,6 +137,9 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             const float2 al = eval_alpha2(Bs.y, q, G, araw);
             ea = ea && al.x >= kAlphaMin;                  // the forward blended it
             eb = eb && al.y >= kAlphaMin;
+            // entries the forward blended at none of the warp's pixels need no
+            // gradient math and no reduction
+            if (!__any_sync(0xffffffffu, ea || eb)) continue;
             const float2 ae = make_float2(ea ? al.x : 0.f, eb ? al.y : 0.f);
             const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
             const float2 r = make_float2(rcp_approx(om.x), rcp_approx(om.y));
@@ -324,7 +327,7 @@ __device__ __forceinline__ float ratio_ff(double x, float zf, float zl, float rz
 }
 
 template <int DEG, bool F16>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
                    const float *__restrict__ scales, const float *__restrict__ quats,
                    const float *__restrict__ opac, const void *__restrict__ sh_raw, float near_z,

@@ -38,6 +38,18 @@ __device__ __forceinline__ float eval_q(const float4 &A, const float4 &B, float 
     return __fmaf_rn(dx, __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy)), __fmul_rn(__fmul_rn(B.x, dy), dy));
 }
 
+// The two pixels thread t owns: each warp covers a compact 8x8 block of the
+// tile (lane l at column l % 8, rows l / 8 and l / 8 + 4), so a small
+// Gaussian activates few warps.  Requires TW % 8 == 0 and TH % 8 == 0.
+template <int TW>
+__device__ __forceinline__ void pixel_pair(int t, int x0, int y0, int &px, int &pya, int &pyb) {
+    constexpr int WX = TW / 8;                  // warps across the tile
+    const int w = t >> 5, l = t & 31;
+    px = x0 + (w % WX) * 8 + (l & 7);
+    pya = y0 + (w / WX) * 8 + (l >> 3);
+    pyb = pya + 4;
+}
+
 // q = K d^2 at two pixel centres of one column, (fpx, fpy.x) and (fpx, fpy.y),
 // in packed FP32x2: dx is shared, K a dx^2 and 2K b dx once per Gaussian,
 // then q = K a dx^2 + dy (2K b dx + K c dy) for both pixels.

@@ -40,8 +40,8 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x;
-    // a thread owns two pixels of one column: rows ya and ya + TH/2
-    const int px = tx * TW + (t % TW), pya = ty * TH + (t / TW), pyb = pya + TH / 2;
+    int px, pya, pyb;
+    pixel_pair<TW>(t, tx * TW, ty * TH, px, pya, pyb);
     const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
     const long long npx = (long long)V.W * V.H;
     const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;

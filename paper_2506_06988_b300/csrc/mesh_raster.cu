@@ -38,6 +38,7 @@ struct FaceSetup {
     float iz0f, af, bf;      // 1/z = iz0 + a U + b V, (U,V) = centre - vertex 0 in pixels
     float izf[3];            // 1 / view z per vertex (FP32)
     float rD;                // 1 / signed double area
+    float u0, v0, du1, dv1, du2, dv2;   // uv0 and uv_k - uv0
 };
 
 __global__ void __launch_bounds__(256)
@@ -76,8 +77,9 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {
 
 __global__ void __launch_bounds__(256)
 mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces,
-                 const int2 *__restrict__ sxy, const double *__restrict__ iz,
-                 FaceSetup *__restrict__ setup, uint32_t *__restrict__ cnt) {
+                 const float *__restrict__ uvs, const int2 *__restrict__ sxy,
+                 const double *__restrict__ iz, FaceSetup *__restrict__ setup,
+                 uint32_t *__restrict__ cnt) {
     const long long m = (long long)vt.n_views * nf;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
@@ -89,18 +91,24 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
         s.flip = 0; s.area2 = 0;
         s.iz0f = s.af = s.bf = s.rD = 0.f;
         double izd[3];
+        float fu[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f};
         bool ok = true;
         for (int k = 0; k < 3; ++k) {
             const int vi = faces[3 * f + k];
             s.izf[k] = 0.f;
             izd[k] = 0.0;
             if (vi < 0 || vi >= nv) { ok = false; s.x[k] = s.y[k] = 0; continue; }
+            fu[k] = uvs[2 * (long long)vi];
+            fv[k] = uvs[2 * (long long)vi + 1];
             const int2 p = sxy[(long long)v * nv + vi];
             s.x[k] = p.x; s.y[k] = p.y;
             izd[k] = iz[(long long)v * nv + vi];
             s.izf[k] = __double2float_rn(izd[k]);
             if (p.x == kInvalid) ok = false;
         }
+        s.u0 = fu[0]; s.v0 = fv[0];
+        s.du1 = fu[1] - fu[0]; s.dv1 = fv[1] - fv[0];
+        s.du2 = fu[2] - fu[0]; s.dv2 = fv[2] - fv[0];
         uint32_t c = 0;
         if (ok) {
             const long long e1x = (long long)s.x[1] - s.x[0], e1y = (long long)s.y[1] - s.y[0];
@@ -263,11 +271,8 @@ mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;
             // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
             // for small faces, so uv keeps close to FP32 rounding of its value
-            const int v0i = faces[3 * (long long)id], v1i = faces[3 * (long long)id + 1],
-                      v2i = faces[3 * (long long)id + 2];
-            const float u0 = __ldg(uvs + 2 * (long long)v0i), w0 = __ldg(uvs + 2 * (long long)v0i + 1);
-            u = u0 + fmaf(b1, __ldg(uvs + 2 * (long long)v1i) - u0, b2 * (__ldg(uvs + 2 * (long long)v2i) - u0));
-            w = w0 + fmaf(b1, __ldg(uvs + 2 * (long long)v1i + 1) - w0, b2 * (__ldg(uvs + 2 * (long long)v2i + 1) - w0));
+            u = s.u0 + fmaf(b1, s.du1, b2 * s.du2);
+            w = s.v0 + fmaf(b1, s.dv1, b2 * s.dv2);
             const float ss = u * (float)tw - 0.5f, tt = w * (float)th - 0.5f;
             const float x0 = floorf(ss), y0 = floorf(tt);
             const float fx = ss - x0, fy = tt - y0;
@@ -394,7 +399,7 @@ extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, c
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (mf > 0) {
-        mesh_face_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_verts, n_faces, faces, r.sxy, r.iz, r.setup, r.cnt);
+        mesh_face_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_verts, n_faces, faces, uvs, r.sxy, r.iz, r.setup, r.cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     e = launch_scan(r.cnt, nullptr, r.offs, mf, (long long *)n_items_out, item_capacity, d_status, r.scan, s);
