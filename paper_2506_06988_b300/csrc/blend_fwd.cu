@@ -22,7 +22,7 @@ namespace hm {
 
 namespace {
 
-template <int TW, int TH>
+template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / 2, 8)
 blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
                  const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_depth,
@@ -77,7 +77,7 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             float2 dy;
             const float2 q = eval_q2(A, B, fpx, fpy, dx, dy);
             bool ea = !done_a && q.x >= kQ3, eb = !done_b && q.y >= kQ3;   // inside the 3-sigma ellipse
-            if (eval_stats) n_exam += !done_a + !done_b, n_eval += ea + eb;
+            if (COUNT) n_exam += !done_a + !done_b, n_eval += ea + eb;
             if (!(ea || eb)) continue;
             float2 G, araw;
             const float2 al = eval_alpha2(B.y, q, G, araw);
@@ -93,7 +93,7 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             C0 = __ffma2_rn(w, make_float2(c.x, c.x), C0);
             C1 = __ffma2_rn(w, make_float2(c.y, c.y), C1);
             C2 = __ffma2_rn(w, make_float2(c.z, c.z), C2);
-            T = make_float2(ea ? Tn.x : T.x, eb ? Tn.y : T.y);
+            T = __ffma2_rn(make_float2(-T.x, -T.y), ae, T);     // Tn where blended, T where ae = 0
             cnt_a += ea;
             cnt_b += eb;
             if (ea) last_a = b0 + k + 1;
@@ -118,7 +118,7 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
         n_contrib[V.pix_off + lpb] = cnt_b;
         if (last_idx) last_idx[V.pix_off + lpb] = last_b;
     }
-    if (eval_stats) {
+    if (COUNT) {
         unsigned long long e = n_eval, x = n_exam;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -158,10 +158,17 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
     const Record *rec = reinterpret_cast<const Record *>(records);
     dim3 grid(vt.total_tiles);
     const float *bg = opt->bg;
-#define HM_BLEND(TW, TH)                                                                        \
-    blend_fwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_depth, \
-                                                      mesh_rgb, bg[0], bg[1], bg[2], opt->batch,   \
-                                                      out_rgb, out_T, n_contrib, last_idx, eval_stats)
+#define HM_BLEND(TW, TH)                                                                              \
+    do {                                                                                              \
+        if (eval_stats)                                                                               \
+            blend_fwd_kernel<TW, TH, true><<<grid, TW * TH / 2, 0, s>>>(                              \
+                vt, rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2], opt->batch, \
+                out_rgb, out_T, n_contrib, last_idx, eval_stats);                                     \
+        else                                                                                          \
+            blend_fwd_kernel<TW, TH, false><<<grid, TW * TH / 2, 0, s>>>(                             \
+                vt, rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2], opt->batch, \
+                out_rgb, out_T, n_contrib, last_idx, nullptr);                                        \
+    } while (0)
     if (opt->tile_w == 16) HM_BLEND(16, 16);
     else if (opt->tile_w == 32) HM_BLEND(32, 8);
     else HM_BLEND(8, 8);
