@@ -66,7 +66,7 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
                  const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_rgb, float bg0,
                  float bg1, float bg2, const float *__restrict__ out_T,
                  const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
-                 const float *__restrict__ dL_dT, float *__restrict__ g2d) {
+                 const float *__restrict__ dL_dT, int batch, float *__restrict__ g2d) {
     constexpr int NT = TW * TH, NTH = NT / 2;
     __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
     __shared__ uint32_t s_item[NT];
@@ -113,7 +113,7 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
     float2 T = Tf;
     const float2 gTT = __fmul2_rn(gT, Tf);
     for (uint32_t hi = hi_all; hi > begin;) {
-        const uint32_t lo = hi - begin > (uint32_t)NT ? hi - NT : begin;
+        const uint32_t lo = hi - begin > (uint32_t)batch ? hi - batch : begin;
         const int nb = (int)(hi - lo);
         __syncthreads();
         for (int i = t; i < nb; i += NTH) {
@@ -581,6 +581,8 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
     if (sh_degree < 0 || sh_degree > 3) return fail(HM_ERR_INVALID_ARG, "sh_degree must be 0..3");
     if (sh_format != HM_SH_F32 && sh_format != HM_SH_F16) return fail(HM_ERR_INVALID_ARG, "sh_format");
+    if (opt->batch < 1 || opt->batch > opt->tile_w * opt->tile_h)
+        return fail(HM_ERR_INVALID_ARG, "batch must be in 1..%d for this tile shape", opt->tile_w * opt->tile_h);
     if (!tile_ranges || !out_T || !last_idx || !dL_drgb) return fail(HM_ERR_INVALID_ARG, "null pointer");
     if (n > 0 && (!means || !scales || !quats || !opacity || !sh || !records || !pair_vals ||
                   !d_means || !d_scales || !d_quats || !d_opacity || !d_sh))
@@ -616,7 +618,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
 #define HM_BBWD(TW, TH)                                                                          \
     blend_bwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_rgb, \
                                                       bg[0], bg[1], bg[2], out_T, last_idx,      \
-                                                      dL_drgb, dL_dT, g2d)
+                                                      dL_drgb, dL_dT, opt->batch, g2d)
     if (opt->tile_w == 16) HM_BBWD(16, 16);
     else if (opt->tile_w == 32) HM_BBWD(32, 8);
     else HM_BBWD(8, 8);

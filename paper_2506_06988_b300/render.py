@@ -27,7 +27,7 @@ import torch
 
 from . import lib
 
-__all__ = ["MeshInput", "Renderer", "HybridRender"]
+__all__ = ["MeshInput", "Renderer", "HybridRender", "GraphStep"]
 
 
 @dataclass
@@ -288,3 +288,64 @@ class HybridRender(torch.autograd.Function):
         d_sh = g["sh"].to(sh.dtype) if sh.dtype != torch.float32 else g["sh"]
         return (None, None, g["means"], g["scales"], g["quats"], g["opacity"], d_sh,
                 g.get("texture") if ctx.tex_grad else None)
+
+
+class GraphStep:
+    """One frame of a ``Renderer`` -- the forward stages and, when an upstream
+    gradient is given, the backward pass into ``grads`` -- captured once in a
+    CUDA graph and replayed with one launch call.
+
+    A replay re-reads the current contents of the parameter tensors, the mesh
+    and the upstream gradients, so callers update those in place between
+    replays (the renderer's outputs and ``grads`` are overwritten each time).
+    The capture follows an eager frame that settles the pair and work-item
+    capacities; ``replay(check=True)`` synchronises, and on a capacity
+    overflow grows the buffers eagerly and captures again.
+    """
+
+    def __init__(self, renderer: Renderer, params, mesh: Optional[MeshInput] = None,
+                 dL_drgb: Optional[torch.Tensor] = None, dL_dT: Optional[torch.Tensor] = None,
+                 grads=None, tex_grad: bool = False):
+        self.r = renderer
+        self.params = tuple(params)
+        self.mesh = mesh
+        self.dI, self.dT = dL_drgb, dL_dT
+        self.tex_grad = bool(tex_grad and renderer.has_mesh)
+        self.grads = grads
+        if self.dI is not None and self.grads is None:
+            self.grads = renderer.grad_buffers(mesh.texture.shape[:2] if self.tex_grad else None)
+        self.graph = None
+        self.capture()
+
+    def _body(self):
+        r = self.r
+        r.forward(*self.params, self.mesh)
+        if self.dI is not None:
+            r.backward(*self.params, self.dI, self.dT, mesh=self.mesh, tex_grad=self.tex_grad,
+                       out=self.grads, zero=True)
+
+    def capture(self):
+        r = self.r
+        r.render(*self.params, self.mesh)                 # settles the capacities
+        side = torch.cuda.Stream(device=r.device)
+        side.wait_stream(torch.cuda.current_stream(r.device))
+        with torch.cuda.stream(side):                    # lazy workspaces, first-call set-up
+            self._body()
+        torch.cuda.current_stream(r.device).wait_stream(side)
+        torch.cuda.synchronize(r.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._body()
+        self.graph = g
+        return self
+
+    def replay(self, check: bool = False):
+        self.graph.replay()
+        if check:
+            st, npairs, nitems = self.r.status()
+            if st & lib.HM_DEV_TIMEOUT:
+                raise lib.HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
+            if st & lib.HM_DEV_CAPACITY:
+                self.capture()                            # grows the buffers, then re-captures
+                self.graph.replay()
+        return self

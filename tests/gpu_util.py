@@ -27,6 +27,21 @@ EPS = 2e-4
 IMG_TOL = 1e-4
 
 
+def check_grad(name, g, ref, rel=1e-3, floor=1e-4):
+    """GPU gradient vs the FP64 oracle: ||g - ref|| <= rel ||ref|| and per
+    element |g - ref| <= rel |ref| + floor max|ref| (the floor absorbs FP32
+    atomic accumulation order on near-cancelling sums)."""
+    g = np.asarray(g, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    nref = np.linalg.norm(ref)
+    assert nref > 0, name
+    norm_err = np.linalg.norm(g - ref) / nref
+    el = np.abs(g - ref) <= rel * np.abs(ref) + floor * np.abs(ref).max()
+    assert norm_err <= rel, (name, norm_err)
+    assert el.all(), (name, int((~el).sum()), float(np.abs(g - ref).max()))
+    return norm_err
+
+
 def gaussians_to_torch(g, device="cuda"):
     t = lambda a, dt=torch.float32: torch.as_tensor(np.ascontiguousarray(a), device=device).to(dt)  # noqa: E731
     sh = torch.as_tensor(np.ascontiguousarray(g.sh), device=device)

@@ -16,21 +16,13 @@ from oracle import torch_ref as TR
 from paper_2506_06988_b300 import scenes
 from paper_2506_06988_b300.render import HybridRender, MeshInput
 
-from gpu_util import EPS, gpu_render, gaussians_to_torch, make_renderer  # noqa: E402
+from gpu_util import EPS, check_grad, gpu_render, gaussians_to_torch, make_renderer  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
 
 def _check(name, g, ref, rel=1e-3, floor=1e-4):
-    g = np.asarray(g, np.float64).reshape(-1)
-    ref = np.asarray(ref, np.float64).reshape(-1)
-    nref = np.linalg.norm(ref)
-    assert nref > 0, name
-    norm_err = np.linalg.norm(g - ref) / nref
-    el = np.abs(g - ref) <= rel * np.abs(ref) + floor * np.abs(ref).max()
-    assert norm_err <= rel, (name, norm_err)
-    assert el.all(), (name, int((~el).sum()), float(np.abs(g - ref).max()))
-    return norm_err
+    return check_grad(name, g, ref, rel, floor)
 
 
 def _run(scene, tex_grad, seed=0):

@@ -1,0 +1,132 @@
+"""Batched views of uneven resolution, CUDA-graph frames and the autotuner.
+
+* A frame captured in a CUDA graph (GraphStep) gives exactly the eager
+  frame's images and counts, and its gradients up to the order of FP32
+  atomic additions; a replay reads the parameters' current contents.
+* The autotuner times every valid (tile, batch) pair; the image it leads to
+  is bit-identical to the default configuration's (per-pixel candidate sets
+  and their order do not depend on the tile or the staging batch).
+* Gradients of a batched render of several cameras of different sizes with
+  FP16 SH storage equal the sum over cameras of the FP64 gradient oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import torch_ref as TR
+from paper_2506_06988_b300 import autotune, scenes
+from paper_2506_06988_b300.render import GraphStep, MeshInput
+
+from gpu_util import EPS, check_grad, gaussians_to_torch, gpu_render, make_renderer  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+RES = ((160, 120), (96, 64), (200, 104))
+
+
+def _room(seed=31, res=RES, n_gauss=4000, n_tris=2500, sh_f16=True):
+    return scenes.room_scene(seed, n_tris=n_tris, n_gauss=n_gauss, resolutions=res, sh_f16=sh_f16,
+                             focal_per_width=1100.0 / 1920.0)
+
+
+def _params(P):
+    return (P["means"], P["scales"], P["quats"], P["opacity"], P["sh"])
+
+
+def _grads_close(a, b):
+    for k in b:
+        tol = 1e-5 * float(b[k].abs().max()) + 1e-12
+        assert torch.allclose(a[k], b[k], rtol=1e-5, atol=tol), k
+
+
+def test_graph_step_matches_eager_frame():
+    s = _room()
+    r, P, mesh = gpu_render(s)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    dI = torch.randn(3 * r.npix, device="cuda", generator=gen)
+    ref_g = r.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True)
+    ref = {k: getattr(r, k).clone() for k in ("rgb", "T", "n_contrib", "last_idx")}
+    gs = GraphStep(r, _params(P), mesh, dL_drgb=dI, tex_grad=True)
+    for _ in range(2):
+        for k in ref:
+            getattr(r, k).fill_(-1)
+        gs.replay(check=True)
+        torch.cuda.synchronize()
+        for k, v in ref.items():
+            assert torch.equal(getattr(r, k), v), k
+        _grads_close(gs.grads, ref_g)
+
+
+def test_graph_step_reads_current_parameters():
+    s = _room(seed=32)
+    r, P, mesh = gpu_render(s)
+    gs = GraphStep(r, _params(P), mesh)
+    P["means"][::3] += 0.02                      # in place: the graph sees the new values
+    P["opacity"].mul_(0.9)
+    gs.replay(check=True)
+    torch.cuda.synchronize()
+    got = (r.rgb.clone(), r.T.clone(), r.n_contrib.clone())
+    r2, _, _ = gpu_render(s)
+    r2.render(*_params(P), mesh)
+    torch.cuda.synchronize()
+    assert torch.equal(got[0], r2.rgb)
+    assert torch.equal(got[1], r2.T)
+    assert torch.equal(got[2], r2.n_contrib)
+
+
+def test_autotune_covers_the_grid_and_does_not_change_the_image():
+    s = _room(seed=33, res=((160, 120), (96, 64)))
+    g = s.gaussians
+    P = gaussians_to_torch(g)
+    mesh = MeshInput.from_numpy(s.mesh)
+    kw = dict(sh_f16=True, n_verts=len(s.mesh.verts), n_faces=len(s.mesh.faces),
+              tex_shape=s.mesh.texture.shape, bg=tuple(np.asarray(s.bg, np.float64)))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    npix = sum(c.width * c.height for c in s.cameras)
+    dI = torch.randn(3 * npix, device="cuda", generator=gen)
+    res = autotune.tune(s.cameras, g.n, g.sh_degree, _params(P), mesh, dL_drgb=dI, tex_grad=True,
+                        warmup=1, iters=2, **kw)
+    combos = {(t, b) for t, b, _ in res.table}
+    want = {((16, 16), b) for b in (32, 64, 128, 256)} | {((32, 8), b) for b in (32, 64, 128, 256)} \
+        | {((8, 8), b) for b in (32, 64)}
+    assert combos == want
+    assert all(np.isfinite(ms) and ms > 0 for _, _, ms in res.table)
+    assert (res.tile, res.batch) in combos
+    ref, _, _ = gpu_render(s)
+    r = res.renderer
+    r.render(*_params(P), mesh)
+    torch.cuda.synchronize()
+    assert torch.equal(r.rgb, ref.rgb)
+    assert torch.equal(r.T, ref.T)
+    assert torch.equal(r.n_contrib, ref.n_contrib)
+
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 32), ((32, 8), 128), ((8, 8), 64)])
+def test_batched_uneven_fp16_backward_matches_oracle(tile, batch):
+    s = _room(seed=34)
+    rng = np.random.default_rng(7)
+    gI_views, gT_views = [], []
+    ref = None
+    for v, cam in enumerate(s.cameras):
+        npx = cam.n_pixels
+        gI = rng.standard_normal((3, npx))
+        gT = rng.standard_normal(npx)
+        amb = O.render(s, view=v).out.margin < EPS
+        gI[:, amb] = 0.0
+        gT[amb] = 0.0
+        _, gv = TR.render_grad(s, v, gI, gT)
+        ref = gv if ref is None else {k: ref[k] + gv[k] for k in ref}
+        gI_views.append(gI)
+        gT_views.append(gT)
+    r, P, mesh = gpu_render(s, tile=tile, batch=batch)
+    dI = torch.as_tensor(np.concatenate([g.reshape(-1) for g in gI_views]), dtype=torch.float32, device="cuda")
+    dT = torch.as_tensor(np.concatenate(gT_views), dtype=torch.float32, device="cuda")
+    g = r.backward(*_params(P), dI, dT, mesh=mesh, tex_grad=True)
+    torch.cuda.synchronize()
+    for k in ("means", "scales", "quats", "opacity", "sh"):
+        check_grad(k, g[k].cpu().numpy(), ref[k])
+    gt = g["texture"].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gt - ref["texture"]) <= 1e-3 * np.linalg.norm(ref["texture"])
