@@ -47,18 +47,15 @@ FLOPS_PER_EVAL_BWD = 70
 # sources hash to the recorded value, i.e. while the kernel is the one that
 # was measured (profiles/*_room1080p_8views.md hold the captures)
 KERNEL_SOURCES = {
-    "blend_forward": ("blend_fwd.cu", "blend_common.cuh", "hm_internal.cuh"),
-    "blend_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh"),
-    "texture_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh"),
-    "project_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh", "sh.cuh"),
+    "blend_forward": ("blend_fwd.cu", "blend_common.cuh", "hm_internal.cuh", "tma.cuh"),
+    "blend_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh", "tma.cuh"),
+    "texture_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh", "tma.cuh"),
+    "project_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh", "sh.cuh", "tma.cuh"),
     "project": ("project.cu", "sh.cuh", "hm_internal.cuh"),
 }
 NCU_TRAFFIC = {
-    "blend_forward": (654_763_776, "484e75abc162ae1b"),
-    "blend_backward": (566_742_784, "76f3de9a04ea931c"),
-    "texture_backward": (497_151_232, "76f3de9a04ea931c"),
-    "project_backward": (298_739_712, "809fee2243d9b757"),
-    "project": (128_780_544, "df7152b8776508d2"),
+    "blend_forward": (654_741_760, "a6abda8acbf15397"),
+    "blend_backward": (566_785_280, "e21bb9e258335d56"),
 }
 
 

@@ -55,7 +55,11 @@ typedef int32_t hm_status;
 
 /* device status bits (OR-ed into *d_status) */
 #define HM_DEV_CAPACITY 1      /* more (Gaussian,tile) or (face,tile) pairs than capacity */
-#define HM_DEV_TIMEOUT 2       /* a bounded inter-CTA wait gave up; outputs are invalid */
+#define HM_DEV_TIMEOUT 2       /* a bounded wait (inter-CTA look-back, or a bulk copy's
+                                  barrier) gave up; outputs are invalid */
+#define HM_DEV_BAD_INDEX 4     /* a pair list held a record index >= n_views*n (a list
+                                  left invalid by an earlier error); record 0 was read
+                                  in its place and the outputs are invalid */
 
 #define HM_MAX_VIEWS 32        /* cameras per call */
 #define HM_MAX_PAIRS 0x3FFFFFFF /* pair capacities must stay below 2^30 */
@@ -196,12 +200,15 @@ hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t n, const v
  *  eval_stats (device uint64[2], may be NULL): when given, [0] += the number
  *  of (pixel, Gaussian) pairs whose alpha was evaluated (inside the 3-sigma
  *  ellipse, before the pixel stopped) and [1] += the list entries examined.
+ *  d_status (device int32, may be NULL): HM_DEV_TIMEOUT / HM_DEV_BAD_INDEX.
+ *  Records are staged into shared memory by bulk asynchronous copies (TMA),
+ *  opt->batch list entries per round, double buffered.
  */
 hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, const void *records,
                            const uint32_t *pair_vals, const uint32_t *tile_ranges,
                            const float *mesh_depth, const float *mesh_rgb, const hm_options *opt,
                            float *out_rgb, float *out_T, uint32_t *n_contrib, uint32_t *last_idx,
-                           unsigned long long *eval_stats, void *stream);
+                           unsigned long long *eval_stats, int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* hm_blend_backward -- gradients of a loss L through hm_blend_forward and
@@ -216,6 +223,7 @@ hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, co
  *  Outputs, ACCUMULATED into caller-zeroed buffers: d_means [n][3],
  *  d_scales [n][3], d_quats [n][4], d_opacity [n], d_sh [n][K][3] float32
  *  (also for F16 SH storage), d_tex [tex_h][tex_w][3] float32 (may be NULL).
+ *  d_status (device int32, may be NULL): as for hm_blend_forward.
  */
 size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n);
 hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, const float *means,
@@ -227,7 +235,8 @@ hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, c
                             int32_t tex_h, const hm_options *opt, const float *out_T,
                             const uint32_t *last_idx, const float *dL_drgb, const float *dL_dT,
                             float *d_means, float *d_scales, float *d_quats, float *d_opacity,
-                            float *d_sh, float *d_tex, void *ws, size_t ws_bytes, void *stream);
+                            float *d_sh, float *d_tex, int32_t *d_status, void *ws, size_t ws_bytes,
+                            void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* hm_blend_backward_noalloc -- hm_blend_backward for callers that cannot
@@ -259,7 +268,7 @@ hm_status hm_blend_backward_noalloc(const hm_camera *cams, int32_t n_views, int3
                                     const uint32_t *last_idx, const float *dL_drgb,
                                     const float *dL_dT, float *d_means, float *d_scales,
                                     float *d_quats, float *d_opacity, float *d_sh, float *d_tex,
-                                    void *stream);
+                                    int32_t *d_status, void *stream);
 
 /* Number of tiles of all cameras for the tile shape in `opt`. */
 int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options *opt);

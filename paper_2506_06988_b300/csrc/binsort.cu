@@ -39,8 +39,13 @@ struct BinRec {
 __device__ __forceinline__ BinRec load_bin_rec(const Record *rec, long long it, int n) {
     BinRec r;
     const float4 A = rec[it].a, B = rec[it].b, C = rec[it].c;
-    r.mx = A.x; r.my = A.y; r.a = A.z; r.b = A.w; r.c = B.x;
-    r.ra = 1.f / A.z; r.rc = 1.f / B.x;
+    // undo the record's K scaling (one rounding each, far inside the
+    // ellipse test's 0.2% slack)
+    r.mx = A.x; r.my = A.y;
+    r.a = A.z * (1.f / kConicScale);
+    r.b = A.w * (0.5f / kConicScale);
+    r.c = B.x * (1.f / kConicScale);
+    r.ra = 1.f / r.a; r.rc = 1.f / r.c;
     r.depth = B.z;
     unpack_range(__float_as_uint(B.w), r.x0, r.x1);
     unpack_range(__float_as_uint(C.w), r.y0, r.y1);

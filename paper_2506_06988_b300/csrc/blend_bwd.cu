@@ -27,6 +27,7 @@
 #include "blend_common.cuh"
 #include "hm_host.h"
 #include "sh.cuh"
+#include "tma.cuh"
 
 namespace hm {
 
@@ -62,14 +63,16 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH / 2, 6)
-blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
-                 const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_rgb, float bg0,
-                 float bg1, float bg2, const float *__restrict__ out_T,
-                 const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
-                 const float *__restrict__ dL_dT, int batch, float *__restrict__ g2d) {
+blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
+                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+                 const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2,
+                 const float *__restrict__ out_T, const uint32_t *__restrict__ last_idx,
+                 const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, int batch,
+                 float *__restrict__ g2d, int32_t *__restrict__ d_status) {
     constexpr int NT = TW * TH, NTH = NT / 2;
-    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-    __shared__ uint32_t s_item[NT];
+    __shared__ Record s_rec[2][NT];
+    __shared__ uint32_t s_item[2][NT];
+    __shared__ uint64_t s_bar[2];
     __shared__ uint32_t s_hi;
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
@@ -102,32 +105,85 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
         if (mr) { B0.y = mr[lpb]; B1.y = mr[npx + lpb]; B2.y = mr[2 * npx + lpb]; }
     }
     const uint32_t begin = ranges[2 * gt];
-    if (t == 0) s_hi = 0;
+    if (t == 0) {
+        s_hi = 0;
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
     __syncthreads();
     const uint32_t my_hi = max(last_a, last_b);
     if (my_hi > 0) atomicMax(&s_hi, my_hi);
     __syncthreads();
     const uint32_t hi_all = s_hi;
+    // rounds walk the list back to front: round r covers [lo_r, hi_r) with
+    // hi_r = hi_all - r batch, lo_r = max(begin, hi_r - batch)
+    const uint32_t n_rounds = hi_all > begin ? (hi_all - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
+    uint32_t nxt0 = 0, nxt1 = 0;
+    auto round_lo = [&](uint32_t r, uint32_t &lo, uint32_t &nb) {
+        const uint32_t hi = hi_all - r * (uint32_t)batch;
+        lo = hi - begin > (uint32_t)batch ? hi - (uint32_t)batch : begin;
+        nb = hi - lo;
+    };
+    auto load_idx = [&](uint32_t r) {
+        uint32_t lo, nb;
+        round_lo(r, lo, nb);
+        if ((uint32_t)t < nb) nxt0 = vals[lo + t];
+        if ((uint32_t)(t + NTH) < nb) nxt1 = vals[lo + t + NTH];
+    };
+    auto issue = [&](uint32_t r) {
+        const int buf = r & 1;
+        uint32_t lo, nb;
+        round_lo(r, lo, nb);
+        if (t == 0) mbar_arrive_expect_tx(&s_bar[buf], nb * (uint32_t)sizeof(Record));
+        if ((uint32_t)t < nb) {
+            uint32_t it = nxt0;
+            if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
+            s_item[buf][t] = it;
+            bulk_g2s(&s_rec[buf][t], rec + it, sizeof(Record), &s_bar[buf]);
+        }
+        if ((uint32_t)(t + NTH) < nb) {
+            uint32_t it = nxt1;
+            if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
+            s_item[buf][t + NTH] = it;
+            bulk_g2s(&s_rec[buf][t + NTH], rec + it, sizeof(Record), &s_bar[buf]);
+        }
+    };
+    if (n_rounds > 0) {
+        load_idx(0);
+        issue(0);
+    }
+    if (n_rounds > 1) load_idx(1);
     const float fpx = (float)px + 0.5f;
     const float2 fpy = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
     float2 T = Tf;
     const float2 gTT = __fmul2_rn(gT, Tf);
-    for (uint32_t hi = hi_all; hi > begin;) {
-        const uint32_t lo = hi - begin > (uint32_t)batch ? hi - batch : begin;
-        const int nb = (int)(hi - lo);
+    bool ok = true;
+    for (uint32_t r = 0; r < n_rounds; ++r) {
+        // ends every thread's use of round r - 1, whose buffers round r + 1
+        // refills, and publishes round r's record indices
         __syncthreads();
-        for (int i = t; i < nb; i += NTH) {
-            const uint32_t it = vals[lo + i];
-            s_item[i] = it;
-            stage_record(rec[it], s_a[i], s_b[i], s_c[i]);
+        if (r + 1 < n_rounds) {
+            issue(r + 1);
+            if (r + 2 < n_rounds) load_idx(r + 2);
         }
-        __syncthreads();
+        const int buf = r & 1;
+        if (!mbar_wait(&s_bar[buf], (r >> 1) & 1)) {
+            set_status(d_status, HM_DEV_TIMEOUT);
+            ok = false;
+        }
+        ok = __all_sync(0xffffffffu, ok);   // the replay below uses warp shuffles
+        uint32_t lo, nb_u;
+        round_lo(r, lo, nb_u);
+        const int nb = ok ? (int)nb_u : 0;
+        const Record *sr = s_rec[buf];
+        const uint32_t *si = s_item[buf];
         for (int k = nb - 1; k >= 0; --k) {
             const uint32_t j = lo + k;
             bool ea = j < last_a, eb = j < last_b;
             if (!__any_sync(0xffffffffu, ea || eb)) continue;
             float g[kG];
-            const float4 A = s_a[k], Bs = s_b[k], c = s_c[k];
+            const float4 A = sr[k].a, Bs = sr[k].b, c = sr[k].c;
             float dx;
             float2 dy;
             const float2 q = eval_q2(A, Bs, fpx, fpy, dx, dy);
@@ -180,7 +236,7 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             B1 = __ffma2_rn(ae, make_float2(c.y, c.y), __fmul2_rn(om, B1));
             B2 = __ffma2_rn(ae, make_float2(c.z, c.z), __fmul2_rn(om, B2));
             T = Ti;
-            float *dst = g2d + (size_t)s_item[k] * kG;
+            float *dst = g2d + (size_t)si[k] * kG;
             const float y = warp_sum8(g, lane);
             float z = g[8];
 #pragma unroll
@@ -188,7 +244,11 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
             if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
         }
-        hi = lo;
+    }
+    // after a timed-out wait, the copies still in flight must land before
+    // the CTA's shared memory is released (every round was waited for)
+    if (!ok && t == 0) {
+        for (uint32_t r = n_rounds >= 2 ? n_rounds - 2 : 0; r < n_rounds; ++r) mbar_wait(&s_bar[r & 1], (r >> 1) & 1);
     }
 }
 
@@ -575,7 +635,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
                                        const uint32_t *last_idx, const float *dL_drgb,
                                        const float *dL_dT, float *d_means, float *d_scales,
                                        float *d_quats, float *d_opacity, float *d_sh, float *d_tex,
-                                       void *ws, size_t ws_bytes, void *stream) {
+                                       int32_t *d_status, void *ws, size_t ws_bytes, void *stream) {
     ViewTable vt;
     if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
@@ -615,10 +675,12 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (stages & HM_BWD_BLEND) {
     e = cudaMemsetAsync(g2d, 0, sizeof(float) * kG * (size_t)n_views * n, s);
     if (e != cudaSuccess) return cuda_status(e);
+    const uint32_t n_rec = (uint32_t)((long long)n_views * n);
 #define HM_BBWD(TW, TH)                                                                          \
-    blend_bwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, pair_vals, tile_ranges, mesh_rgb, \
-                                                      bg[0], bg[1], bg[2], out_T, last_idx,      \
-                                                      dL_drgb, dL_dT, opt->batch, g2d)
+    blend_bwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, n_rec, pair_vals, tile_ranges,  \
+                                                      mesh_rgb, bg[0], bg[1], bg[2], out_T,      \
+                                                      last_idx, dL_drgb, dL_dT, opt->batch, g2d, \
+                                                      d_status)
     if (opt->tile_w == 16) HM_BBWD(16, 16);
     else if (opt->tile_w == 32) HM_BBWD(32, 8);
     else HM_BBWD(8, 8);
@@ -675,7 +737,7 @@ extern "C" hm_status hm_blend_backward_noalloc(
     const float *mesh_depth, const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
     int32_t tex_h, const hm_options *opt, const float *out_T, const uint32_t *last_idx,
     const float *dL_drgb, const float *dL_dT, float *d_means, float *d_scales, float *d_quats,
-    float *d_opacity, float *d_sh, float *d_tex, void *stream) {
+    float *d_opacity, float *d_sh, float *d_tex, int32_t *d_status, void *stream) {
     if (n_views < 1 || n < 0) return fail(HM_ERR_INVALID_ARG, "bad n_views or n");
     const size_t need = hm_blend_backward_workspace_size(n_views, n);
     if (need > HM_BWD_NOALLOC_BYTES)
@@ -689,6 +751,6 @@ extern "C" hm_status hm_blend_backward_noalloc(
     return hm_blend_backward(cams, n_views, n, means, scales, quats, opacity, sh, sh_degree,
                              sh_format, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb,
                              mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means,
-                             d_scales, d_quats, d_opacity, d_sh, d_tex, ws, HM_BWD_NOALLOC_BYTES,
-                             stream);
+                             d_scales, d_quats, d_opacity, d_sh, d_tex, d_status, ws,
+                             HM_BWD_NOALLOC_BYTES, stream);
 }

@@ -2,21 +2,26 @@
 // and composite of Sec. 3.4).
 //
 // One CTA per screen tile; a thread owns two pixels of one column (rows y and
-// y + TH/2), so the staged record, dx and the loop are shared by the pair and
-// the pair's arithmetic runs in packed FP32x2 (Blackwell FFMA2/FMUL2).  The
-// tile's depth-sorted list is consumed in batches: each batch's records are
-// gathered once into shared memory and then evaluated by every pixel.  A pixel
-// stops at the first Gaussian at or behind its mesh depth (the list is
-// depth-ordered, so all later ones are behind too) or when T would fall below
-// 1e-4; the CTA leaves the list as soon as every pixel has stopped
-// (__syncthreads_count vote), which is where the opaque mesh shortens the
-// per-pixel work.
+// y + 4 of its warp's 8x8 block), so the staged record, dx and the loop are
+// shared by the pair and the pair's arithmetic runs in packed FP32x2
+// (Blackwell FFMA2/FMUL2).  The tile's depth-sorted list is consumed in
+// rounds of `batch` entries.  Each round's 48-byte records are fetched into
+// shared memory by bulk asynchronous copies (cp.async.bulk, the TMA unit),
+// one per entry, completing on the round's mbarrier; rounds are double
+// buffered, so round r+1 is in flight while round r is evaluated, and the
+// record indices of round r+2 are loaded meanwhile.  A pixel stops at the
+// first Gaussian at or behind its mesh depth (the list is depth-ordered, so
+// all later ones are behind too) or when T would fall below 1e-4; the CTA
+// leaves the list as soon as every pixel has stopped (__syncthreads_count
+// vote), which is where the opaque mesh shortens the per-pixel work.
 //
-// Per evaluated (pixel, Gaussian): q = -log2(e)/2 * d^2 from the pre-scaled
-// conic, one ex2, the alpha/T updates and three FMAs of colour; updates are
-// masked (alpha 0 for a pixel that does not blend) instead of branched.
+// Per evaluated (pixel, Gaussian): q = -log2(e)/2 * d^2 from the record's
+// pre-scaled conic, one ex2, the alpha/T updates and three FMAs of colour;
+// updates are masked (alpha 0 for a pixel that does not blend) instead of
+// branched.
 #include "blend_common.cuh"
 #include "hm_host.h"
+#include "tma.cuh"
 
 namespace hm {
 
@@ -24,16 +29,16 @@ namespace {
 
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / 2, 8)
-blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *__restrict__ vals,
-                 const uint32_t *__restrict__ ranges, const float *__restrict__ mesh_depth,
-                 const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2, int batch,
-                 float *__restrict__ out_rgb, float *__restrict__ out_T,
-                 uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ last_idx,
-                 unsigned long long *__restrict__ eval_stats) {
+blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
+                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+                 const float *__restrict__ mesh_depth, const float *__restrict__ mesh_rgb, float bg0,
+                 float bg1, float bg2, int batch, float *__restrict__ out_rgb,
+                 float *__restrict__ out_T, uint32_t *__restrict__ n_contrib,
+                 uint32_t *__restrict__ last_idx, unsigned long long *__restrict__ eval_stats,
+                 int32_t *__restrict__ d_status) {
     constexpr int NT = TW * TH, NTH = NT / 2;
-    __shared__ float4 s_a[NT];   // mean x, mean y, K*conic_xx, 2K*conic_xy
-    __shared__ float4 s_b[NT];   // K*conic_yy, opacity, depth, -
-    __shared__ float4 s_c[NT];   // r, g, b, -
+    __shared__ Record s_rec[2][NT];
+    __shared__ uint64_t s_bar[2];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -45,30 +50,76 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
     const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
     const long long npx = (long long)V.W * V.H;
     const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
+    const uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
+    const uint32_t n_rounds = end > begin ? (end - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
+    if (t == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
+    // record indices of the next round to issue (entries t and t + NTH)
+    uint32_t nxt0 = 0, nxt1 = 0;
+    auto load_idx = [&](uint32_t r) {
+        const uint32_t b0 = begin + r * (uint32_t)batch;
+        const uint32_t nb = min((uint32_t)batch, end - b0);
+        if ((uint32_t)t < nb) nxt0 = vals[b0 + t];
+        if ((uint32_t)(t + NTH) < nb) nxt1 = vals[b0 + t + NTH];
+    };
+    auto issue = [&](uint32_t r) {
+        const int buf = r & 1;
+        const uint32_t b0 = begin + r * (uint32_t)batch;
+        const uint32_t nb = min((uint32_t)batch, end - b0);
+        if (t == 0) mbar_arrive_expect_tx(&s_bar[buf], nb * (uint32_t)sizeof(Record));
+        if ((uint32_t)t < nb) {
+            uint32_t it = nxt0;
+            if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
+            bulk_g2s(&s_rec[buf][t], rec + it, sizeof(Record), &s_bar[buf]);
+        }
+        if ((uint32_t)(t + NTH) < nb) {
+            uint32_t it = nxt1;
+            if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
+            bulk_g2s(&s_rec[buf][t + NTH], rec + it, sizeof(Record), &s_bar[buf]);
+        }
+    };
+    if (n_rounds > 0) load_idx(0);
+    __syncthreads();                                 // barriers initialised
+    if (n_rounds > 0) issue(0);
+    if (n_rounds > 1) load_idx(1);
+
     float Dm_a = INFINITY, Dm_b = INFINITY;
     if (mesh_depth) {
         if (in_a) Dm_a = mesh_depth[V.pix_off + lpa];
         if (in_b) Dm_b = mesh_depth[V.pix_off + lpb];
     }
-    const uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
     const float fpx = (float)px + 0.5f;
     const float2 fpy = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
     bool done_a = !in_a, done_b = !in_b;
     float2 T = make_float2(1.f, 1.f);
     float2 C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
     uint32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0, n_eval = 0, n_exam = 0;
-    for (uint32_t b0 = begin; b0 < end; b0 += batch) {
+    uint32_t issued = n_rounds > 0 ? 1u : 0u, consumed = 0;
+    for (uint32_t r = 0; r < n_rounds; ++r) {
+        // every pixel has stopped: leave the list.  The barrier also ends
+        // every thread's reads of round r - 1, whose buffer round r + 1 refills.
         if (__syncthreads_count(done_a && done_b) == NTH) break;
-        for (int i = t; i < batch; i += NTH) {
-            const uint32_t j = b0 + i;
-            if (j < end) stage_record(rec[vals[j]], s_a[i], s_b[i], s_c[i]);
+        if (r + 1 < n_rounds) {
+            issue(r + 1);
+            ++issued;
+            if (r + 2 < n_rounds) load_idx(r + 2);
         }
-        __syncthreads();
+        const int buf = r & 1;
+        if (!mbar_wait(&s_bar[buf], (r >> 1) & 1)) {
+            set_status(d_status, HM_DEV_TIMEOUT);
+            done_a = done_b = true;
+        }
+        consumed = r + 1;
         if (done_a && done_b) continue;
+        const uint32_t b0 = begin + r * (uint32_t)batch;
         const int nb = (int)min((uint32_t)batch, end - b0);
+        const Record *sr = s_rec[buf];
         for (int k = 0; k < nb; ++k) {
-            const float4 A = s_a[k];
-            const float4 B = s_b[k];
+            const float4 A = sr[k].a;
+            const float4 B = sr[k].b;
             // at or behind the mesh: this and every later Gaussian is cut
             done_a |= B.z >= Dm_a;
             done_b |= B.z >= Dm_b;
@@ -89,7 +140,7 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             if (eb && Tn.y < kTMin) { done_b = true; eb = false; }
             const float2 ae = make_float2(ea ? al.x : 0.f, eb ? al.y : 0.f);
             const float2 w = __fmul2_rn(ae, T);
-            const float4 c = s_c[k];
+            const float4 c = sr[k].c;
             C0 = __ffma2_rn(w, make_float2(c.x, c.x), C0);
             C1 = __ffma2_rn(w, make_float2(c.y, c.y), C1);
             C2 = __ffma2_rn(w, make_float2(c.z, c.z), C2);
@@ -99,6 +150,12 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, const uint32_t *_
             if (ea) last_a = b0 + k + 1;
             if (eb) last_b = b0 + k + 1;
         }
+    }
+    // a round issued but never consumed (early exit) must land before the
+    // CTA's shared memory is released
+    if (t == 0) {
+        for (uint32_t r = consumed; r < issued; ++r)
+            if (!mbar_wait(&s_bar[r & 1], (r >> 1) & 1)) set_status(d_status, HM_DEV_TIMEOUT);
     }
     const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
     float *o = out_rgb + 3 * V.pix_off;
@@ -144,7 +201,7 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
                                       const float *mesh_rgb, const hm_options *opt,
                                       float *out_rgb, float *out_T, uint32_t *n_contrib,
                                       uint32_t *last_idx, unsigned long long *eval_stats,
-                                      void *stream) {
+                                      int32_t *d_status, void *stream) {
     ViewTable vt;
     if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
@@ -162,13 +219,14 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
     do {                                                                                              \
         if (eval_stats)                                                                               \
             blend_fwd_kernel<TW, TH, true><<<grid, TW * TH / 2, 0, s>>>(                              \
-                vt, rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2], opt->batch, \
-                out_rgb, out_T, n_contrib, last_idx, eval_stats);                                     \
+                vt, rec, n_rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2],     \
+                opt->batch, out_rgb, out_T, n_contrib, last_idx, eval_stats, d_status);               \
         else                                                                                          \
             blend_fwd_kernel<TW, TH, false><<<grid, TW * TH / 2, 0, s>>>(                             \
-                vt, rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2], opt->batch, \
-                out_rgb, out_T, n_contrib, last_idx, nullptr);                                        \
+                vt, rec, n_rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2],     \
+                opt->batch, out_rgb, out_T, n_contrib, last_idx, nullptr, d_status);                  \
     } while (0)
+    const uint32_t n_rec = (uint32_t)((long long)n_views * n);
     if (opt->tile_w == 16) HM_BLEND(16, 16);
     else if (opt->tile_w == 32) HM_BLEND(32, 8);
     else HM_BLEND(8, 8);

@@ -47,11 +47,15 @@ __device__ __forceinline__ int view_of_pixel(const ViewTable &vt, long long gp) 
 
 // ---------------------------------------------------------------------------
 // projected Gaussian record (48 bytes)
-//   a = {mean_x, mean_y, conic_xx, conic_xy}
-//   b = {conic_yy, opacity, depth, tile x-range (u16 x0 | u16 x1 << 16)}
+//   a = {mean_x, mean_y, K conic_xx, 2K conic_xy}
+//   b = {K conic_yy, opacity, depth, tile x-range (u16 x0 | u16 x1 << 16)}
 //   c = {r, g, b, tile y-range (u16 y0 | u16 y1 << 16)}
-// An empty range has x0 > x1.
+// with K = -log2(e)/2, so that the blend's exponent is q = K d^2 and
+// exp(-d^2/2) = 2^q with no per-pixel scaling; the blend kernels copy
+// records into shared memory unchanged.  An empty range has x0 > x1.
 // ---------------------------------------------------------------------------
+constexpr float kConicScale = -0.72134752044448170f;   // K = -log2(e)/2
+
 struct __align__(16) Record {
     float4 a, b, c;
 };

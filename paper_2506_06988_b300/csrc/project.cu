@@ -199,8 +199,9 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
                 for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
                 col[ch] = fmaxf(acc, 0.f);
             }
-            r.a = make_float4(u, w, c * rd, -B * rd);
-            r.b = make_float4(a * rd, op, zf, __uint_as_float(xr));
+            // conic (c, -B, a) / det, pre-multiplied by K (and 2K for xy)
+            r.a = make_float4(u, w, __fmul_rn(kConicScale, c * rd), __fmul_rn(2.f * kConicScale, -B * rd));
+            r.b = make_float4(__fmul_rn(kConicScale, a * rd), op, zf, __uint_as_float(xr));
             r.c = make_float4(col[0], col[1], col[2], __uint_as_float(yr));
         }
         Record *o = out + (size_t)v * n + i;

@@ -21,6 +21,7 @@ HM_ERR_CUDA = 2
 HM_ERR_WORKSPACE = 3
 HM_DEV_CAPACITY = 1
 HM_DEV_TIMEOUT = 2
+HM_DEV_BAD_INDEX = 4
 HM_MAX_VIEWS = 32
 HM_MAX_PAIRS = 0x3FFFFFFF
 HM_TEX_RGB8 = 0
@@ -78,19 +79,20 @@ _SIGS = {
                               c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_blend_forward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p,
-                                   c_void_p, c_void_p]),
+                                   c_void_p, c_void_p, c_void_p]),
     "hm_blend_backward_workspace_size": (c_size_t, [c_int32, c_int32]),
     "hm_blend_backward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                     _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                    c_size_t, c_void_p]),
+                                    c_void_p, c_size_t, c_void_p]),
     "hm_blend_backward_noalloc": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                             _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                            c_void_p]),
 }
 
 
@@ -190,11 +192,11 @@ def hm_bin_sort(cams, n, records, tile_max_depth, opt, pair_vals, capacity, n_pa
 
 
 def hm_blend_forward(cams, n, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, opt, out_rgb,
-                     out_T, n_contrib, last_idx, eval_stats, stream):
+                     out_T, n_contrib, last_idx, eval_stats, d_status, stream):
     return load().hm_blend_forward(cams, len(cams), n, _ptr(records), _ptr(pair_vals),
                                    _ptr(tile_ranges), _ptr(mesh_depth), _ptr(mesh_rgb),
                                    ctypes.byref(opt), _ptr(out_rgb), _ptr(out_T), _ptr(n_contrib),
-                                   _ptr(last_idx), _ptr(eval_stats), stream)
+                                   _ptr(last_idx), _ptr(eval_stats), _ptr(d_status), stream)
 
 
 def hm_blend_backward_workspace_size(n_views, n) -> int:
@@ -204,20 +206,21 @@ def hm_blend_backward_workspace_size(n_views, n) -> int:
 def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format, records,
                       pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w, tex_h, opt,
                       out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats, d_opacity, d_sh,
-                      d_tex, ws, ws_bytes, stream):
+                      d_tex, d_status, ws, ws_bytes, stream):
     return load().hm_blend_backward(cams, len(cams), n, _ptr(means), _ptr(scales), _ptr(quats),
                                     _ptr(opacity), _ptr(sh), sh_degree, sh_format, _ptr(records),
                                     _ptr(pair_vals), _ptr(tile_ranges), _ptr(mesh_depth),
                                     _ptr(mesh_rgb), _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
                                     _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
                                     _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacity),
-                                    _ptr(d_sh), _ptr(d_tex), _ptr(ws), ws_bytes, stream)
+                                    _ptr(d_sh), _ptr(d_tex), _ptr(d_status), _ptr(ws), ws_bytes,
+                                    stream)
 
 
 def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format,
                               records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w,
                               tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats,
-                              d_opacity, d_sh, d_tex, stream):
+                              d_opacity, d_sh, d_tex, d_status, stream):
     """hm_blend_backward without a workspace argument: the scratch is the
     library's static 16 MiB device array (for callers that cannot allocate)."""
     return load().hm_blend_backward_noalloc(cams, len(cams), n, _ptr(means), _ptr(scales),
@@ -227,4 +230,5 @@ def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_deg
                                             _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
                                             _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
                                             _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
-                                            _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex), stream)
+                                            _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex),
+                                            _ptr(d_status), stream)

@@ -160,7 +160,8 @@ class Renderer:
         mr = self.mesh_rgb if self.has_mesh else None
         lib.check(lib.hm_blend_forward(self.cams, self.n, self.records, self.pair_vals, self.ranges,
                                        md, mr, self.opt, self.rgb, self.T, self.n_contrib,
-                                       self.last_idx, eval_stats, _stream()), "hm_blend_forward")
+                                       self.last_idx, eval_stats, self.status_word, _stream()),
+                  "hm_blend_forward")
 
     def count_evaluations(self):
         """Re-run the blend of the last frame with the evaluation counters:
@@ -240,7 +241,7 @@ class Renderer:
             self.mesh_depth if self.has_mesh else None, self.mesh_rgb if self.has_mesh else None,
             self.uv if self.has_mesh else None, tw, th, self.opt, self.T, self.last_idx,
             dL_drgb.contiguous(), None if dL_dT is None else dL_dT.contiguous(),
-            g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], d_tex,
+            g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], d_tex, self.status_word,
             self.bwd_ws, self.bwd_ws.numel(), _stream()), "hm_blend_backward")
         return g
 

@@ -118,10 +118,15 @@ def oracle_view(scene, view, pix=None, mode="brute"):
     return O.render(scene, view, pix=pix, mode=mode)
 
 
+# the records hold the conic pre-multiplied by K = -log2(e)/2 (xy by 2K)
+K_CONIC = np.float64(np.float32(-0.72134752044448170))
+
+
 def records_np(r: Renderer):
     rec = r.records_view().cpu().numpy()
     u32 = rec.view(np.uint32)
-    return SimpleNamespace(mean=rec[:, 0:2].astype(np.float64), conic=rec[:, [2, 3, 4]].astype(np.float64),
+    conic = rec[:, [2, 3, 4]].astype(np.float64) / np.array([K_CONIC, 2 * K_CONIC, K_CONIC])
+    return SimpleNamespace(mean=rec[:, 0:2].astype(np.float64), conic=conic,
                            opacity=rec[:, 5], depth=rec[:, 6], color=rec[:, 8:11].astype(np.float64),
                            x0=u32[:, 7] & 0xFFFF, x1=u32[:, 7] >> 16, y0=u32[:, 11] & 0xFFFF,
                            y1=u32[:, 11] >> 16)

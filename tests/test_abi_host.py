@@ -83,10 +83,10 @@ def test_invalid_arguments_are_rejected_on_the_host(hm):
     # batch larger than the tile
     ob = lib.options(tile=(8, 8))
     ob.batch = 128
-    st = lib.hm_blend_forward(cams, 1, 0, 0, 8, 0, 0, ob, 8, 8, 8, 0, None, 0)
+    st = lib.hm_blend_forward(cams, 1, 0, 0, 8, 0, 0, ob, 8, 8, 8, 0, None, None, 0)
     assert st == lib.HM_ERR_INVALID_ARG and "batch" in lib.last_error()
     # misaligned records
-    st = lib.hm_blend_forward(cams, 10, 4, 8, 8, 0, 0, o, 8, 8, 8, 0, None, 0)
+    st = lib.hm_blend_forward(cams, 10, 4, 8, 8, 0, 0, o, 8, 8, 8, 0, None, None, 0)
     assert st == lib.HM_ERR_INVALID_ARG and "aligned" in lib.last_error()
     # workspace too small
     st = lib.hm_bin_sort(cams, 10, 16, None, o, 16, 1000, 16, 16, 0, 16, 8, 0)

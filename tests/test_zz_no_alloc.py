@@ -32,7 +32,7 @@ def _grads_noalloc(r, P, mesh, dI, dT):
         r.cams, r.n, P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], r.sh_degree,
         r.sh_format, r.records, r.pair_vals, r.ranges, r.mesh_depth, r.mesh_rgb, r.uv, tw, th,
         r.opt, r.T, r.last_idx, dI, dT, g["means"], g["scales"], g["quats"], g["opacity"], g["sh"],
-        g["texture"], torch.cuda.current_stream().cuda_stream)
+        g["texture"], r.status_word, torch.cuda.current_stream().cuda_stream)
     lib.check(st, "hm_blend_backward_noalloc")
     return g
 
@@ -67,6 +67,6 @@ def test_noalloc_rejects_problems_above_its_static_scratch():
     n_max = (lib.HM_BWD_NOALLOC_BYTES - 256) // (9 * 4)
     st = lib.hm_blend_backward_noalloc(cams, n_max + 1, 16, 16, 16, 16, 16, 0, lib.HM_SH_F32, 16, 16,
                                        16, None, None, None, 0, 0, o, 16, 16, 16, None, 16, 16, 16, 16,
-                                       16, None, 0)
+                                       16, None, None, 0)
     assert st == lib.HM_ERR_INVALID_ARG
     assert "static array" in lib.last_error()
