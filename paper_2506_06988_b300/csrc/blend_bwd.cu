@@ -11,13 +11,15 @@
 //        dI/dalpha_i = T_i (c_i - B),  dT_final/dalpha_i = -T_final/(1-alpha_i)
 //        B <- alpha_i c_i + (1 - alpha_i) B,  T_i = T_{i+1} / (1 - alpha_i).
 //    Decisions are re-evaluated with the forward's exact arithmetic
-//    (blend_common.cuh).  Per Gaussian the 9 partials (mean2d, conic,
+//    (blend_common.cuh).  Per Gaussian the 9 partials (five pixel-space
+//    moments of dL/dq from which the mean2d and conic gradients follow,
 //    opacity, colour) are summed over the warp with shuffles and added to
 //    per-record accumulators with one atomic per value per warp.
 //  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
 //    triangle (the mesh colour enters I_h weighted by T), summed per screen
 //    tile in shared memory (fixed point) before the global reductions.
-//  * project_bwd: one thread per Gaussian chains the per-record partials
+//  * project_bwd: one thread per Gaussian turns each view's moments into
+//    dL/dmean2d and dL/dconic with the view's conic and chains them
 //    through the conic inverse, Sigma' = V V^T, V = (J W)(R S), the clamped
 //    Jacobian, the projection of the mean, the quaternion normalisation and
 //    the SH colour (including its dependence on the mean through the view
@@ -33,7 +35,11 @@ namespace hm {
 
 namespace {
 
-constexpr int kG = 9;   // dmx, dmy, dconic_xx, dconic_xy, dconic_yy, dopacity, dr, dg, db
+// per-record partials left by the blend replay: the moments of dL/dq over the
+// record's pixels (sum gq dx, sum gq dy, sum gq dx^2, sum gq dx dy,
+// sum gq dy^2; q = K d^2, (dx, dy) = pixel centre - mean), dL/dopacity and
+// dL/dcolour (r, g, b)
+constexpr int kG = 9;
 
 // Warp sum of 8 per-lane values by recursive halving: at each of the first
 // three levels a lane keeps half of its values and sends the other half to
@@ -217,18 +223,17 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             // through alpha = o 2^q when not clamped at 0.99
             const float2 dLa_u = make_float2(araw.x < kAlphaMax ? dLda.x : 0.f, araw.y < kAlphaMax ? dLda.y : 0.f);
             const float2 gq = __fmul2_rn(__fmul2_rn(dLa_u, araw), make_float2(kLn2, kLn2));   // dL/dq
-            const float azdx2 = 2.f * A.z * dx, awdx = A.w * dx;
-            p = __fmul2_rn(gq, __ffma2_rn(make_float2(A.w, A.w), dy, make_float2(azdx2, azdx2)));
-            g[0] = -(p.x + p.y);                                          // dq/dmx = -(2K a dx + 2K b dy)
-            p = __fmul2_rn(gq, __ffma2_rn(make_float2(2.f * Bs.x, 2.f * Bs.x), dy, make_float2(awdx, awdx)));
-            g[1] = -(p.x + p.y);                                          // dq/dmy = -(2K b dx + 2K c dy)
+            // the pixel-space moments of dL/dq (the mean and conic gradients
+            // follow per record from them: dq/dmean = -2K conic (dx, dy),
+            // dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared by the pair
             const float sgq = gq.x + gq.y;
             const float2 gqdy = __fmul2_rn(gq, dy);
-            const float sgqdy = gqdy.x + gqdy.y;
             const float2 gqdy2 = __fmul2_rn(gqdy, dy);
-            g[2] = kNegHalfLog2e * dx * dx * sgq;                         // dq/dconic_xx = K dx^2
-            g[3] = 2.f * kNegHalfLog2e * dx * sgqdy;                      // dq/dconic_xy = 2K dx dy
-            g[4] = kNegHalfLog2e * (gqdy2.x + gqdy2.y);                   // dq/dconic_yy = K dy^2
+            g[0] = dx * sgq;                                              // sum gq dx
+            g[1] = gqdy.x + gqdy.y;                                       // sum gq dy
+            g[2] = dx * g[0];                                             // sum gq dx^2
+            g[3] = dx * g[1];                                             // sum gq dx dy
+            g[4] = gqdy2.x + gqdy2.y;                                     // sum gq dy^2
             p = __fmul2_rn(dLa_u, G);
             g[5] = p.x + p.y;                                             // dalpha/do = G
             // colour behind the previous Gaussian (normalised), then T_i
@@ -395,8 +400,13 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
                    float *__restrict__ d_scales, float *__restrict__ d_quats,
                    float *__restrict__ d_opac, float *__restrict__ d_sh) {
     constexpr int K = (DEG + 1) * (DEG + 1);
+    // SH gradient accumulators, one private column per thread (conflict-free
+    // [k][c][thread] layout): keeps 3K values out of the register file
+    __shared__ float s_gsh[K * 3][128];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    float(*gsh)[128] = s_gsh;
+    const int tl = threadIdx.x;
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
     const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
     const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
@@ -411,25 +421,15 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int k = 0; k < 3; ++k) M[a][k] = R[a][k] * s[k];
-    float sh[K][3];
-    if (F16) {
-        const __half *h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sh[k][c] = __half2float(h[3 * k + c]);
-    } else {
-        const float *f = reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sh[k][c] = __ldg(f + 3 * k + c);
-    }
+    // SH coefficients are re-read (L1-resident after the first view) where
+    // they are used instead of being held across the view loop
+    const __half *sh_h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
+    const float *sh_f = reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3;
+    auto ld_sh = [&](int j) -> float { return F16 ? __half2float(sh_h[j]) : __ldg(sh_f + j); };
     float gmean[3] = {0.f, 0.f, 0.f};
     float gM[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float gsh[K][3];
 #pragma unroll
-    for (int k = 0; k < K; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.f;
+    for (int k = 0; k < K * 3; ++k) gsh[k][tl] = 0.f;
     float gop = 0.f;
     const double dxw = mx, dyw = my, dzw = mz;
     for (int v = 0; v < vt.n_views; ++v) {
@@ -474,8 +474,14 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
                     cz_ = V0[0] * V1[1] - V0[1] * V1[0];
         const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + 0.3f * (a + c - 0.6f) + 0.09f;
         const float rd2 = 1.f / (det * det);
+        // the blend's moments S of dL/dq (q = K d^2): dL/dmean2d = -2K conic S_(dx,dy),
+        // dL/dconic = K (S_dx2, 2 S_dxdy, S_dy2)
+        const float rdet = 1.f / det;
+        const float cxx = c * rdet, cxy = -b * rdet, cyy = a * rdet;
+        const float gmx = -2.f * kConicScale * (cxx * g[0] + cxy * g[1]);
+        const float gmy = -2.f * kConicScale * (cxy * g[0] + cyy * g[1]);
         // conic (c/det, -b/det, a/det) -> Sigma' entries
-        const float gA = g[2], gB = g[3], gC = g[4];
+        const float gA = kConicScale * g[2], gB = 2.f * kConicScale * g[3], gC = kConicScale * g[4];
         const float ga = (-c * c * gA + b * c * gB - b * b * gC) * rd2;
         const float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * rd2;
         const float gc = (-b * b * gA + a * b * gB - a * a * gC) * rd2;
@@ -519,9 +525,9 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
             gtz += gJ12 * V.fy * ry * rz2;
         }
         // mean2d = (fx x/z + cx, fy y/z + cy)
-        gtx += g[0] * V.fx * rz;
-        gty += g[1] * V.fy * rz;
-        gtz += -(g[0] * V.fx * rx + g[1] * V.fy * ry) * rz;
+        gtx += gmx * V.fx * rz;
+        gty += gmy * V.fy * rz;
+        gtz += -(gmx * V.fx * rx + gmy * V.fy * ry) * rz;
         // t = W mean + t_cam
 #pragma unroll
         for (int k = 0; k < 3; ++k) gmean[k] += V.R[k] * gtx + V.R[3 + k] * gty + V.R[6 + k] * gtz;
@@ -537,22 +543,18 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
         for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.5f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
+            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], ld_sh(3 * k + ch), acc);
             if (acc < 0.f) gcol[ch] = 0.f;   // clamped at 0: no gradient
 #pragma unroll
-            for (int k = 0; k < K; ++k) gsh[k][ch] += Y[k] * gcol[ch];
+            for (int k = 0; k < K; ++k) gsh[3 * k + ch][tl] += Y[k] * gcol[ch];
         }
         if (DEG > 0) {
-            float GY[K][3];
-            sh_basis_grad<DEG>(d0, d1, d2, GY);
-            float gd[3] = {0.f, 0.f, 0.f};
+            float wk[K];
 #pragma unroll
-            for (int k = 1; k < K; ++k) {
-                const float w = sh[k][0] * gcol[0] + sh[k][1] * gcol[1] + sh[k][2] * gcol[2];
-                gd[0] += w * GY[k][0];
-                gd[1] += w * GY[k][1];
-                gd[2] += w * GY[k][2];
-            }
+            for (int k = 0; k < K; ++k)
+                wk[k] = ld_sh(3 * k) * gcol[0] + ld_sh(3 * k + 1) * gcol[1] + ld_sh(3 * k + 2) * gcol[2];
+            float gd[3];
+            sh_grad_dot<DEG>(d0, d1, d2, wk, gd[0], gd[1], gd[2]);
             const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
             gmean[0] += (gd[0] - dd * d0) * dinv;
             gmean[1] += (gd[1] - dd * d1) * dinv;
@@ -597,7 +599,7 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[k][c];
+        for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[3 * k + c][tl];
 }
 
 template <int DEG>

@@ -81,4 +81,53 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float (
     }
 }
 
+// sum_k w[k] dY_k/d(x,y,z): the Cartesian gradient of the weighted sum of
+// the polynomials above (the same derivatives as sh_basis_grad, accumulated
+// term by term so that no K x 3 table is held)
+template <int DEG>
+__device__ __forceinline__ void sh_grad_dot(float x, float y, float z, const float *w, float &gx,
+                                            float &gy, float &gz) {
+    gx = gy = gz = 0.f;
+    if (DEG >= 1) {
+        gx = -kSH1 * w[3];
+        gy = -kSH1 * w[1];
+        gz = kSH1 * w[2];
+    }
+    if (DEG >= 2) {
+        gx += kSH2a * (w[4] * y - w[7] * z) + 2.f * x * (kSH2e * w[8] - kSH2c * w[6]);
+        gy += kSH2a * (w[4] * x - w[5] * z) - 2.f * y * (kSH2c * w[6] + kSH2e * w[8]);
+        gz += 4.f * kSH2c * w[6] * z - kSH2a * (w[5] * y + w[7] * x);
+        if (DEG >= 3) {
+            const float xx = x * x, yy = y * y, zz = z * z;
+            const float xy = x * y, xz = x * z, yz = y * z;
+            // Y9 = -a y (3xx - yy)
+            gx += w[9] * (-6.f * kSH3a * xy);
+            gy += w[9] * (-3.f * kSH3a * (xx - yy));
+            // Y10 = b x y z
+            gx += w[10] * (kSH3b * yz);
+            gy += w[10] * (kSH3b * xz);
+            gz += w[10] * (kSH3b * xy);
+            // Y11 = -c y (4zz - xx - yy)
+            gx += w[11] * (2.f * kSH3c * xy);
+            gy += w[11] * (-kSH3c * (4.f * zz - xx - 3.f * yy));
+            gz += w[11] * (-8.f * kSH3c * yz);
+            // Y12 = d z (2zz - 3xx - 3yy)
+            gx += w[12] * (-6.f * kSH3d * xz);
+            gy += w[12] * (-6.f * kSH3d * yz);
+            gz += w[12] * (kSH3d * (6.f * zz - 3.f * xx - 3.f * yy));
+            // Y13 = -c x (4zz - xx - yy)
+            gx += w[13] * (-kSH3c * (4.f * zz - 3.f * xx - yy));
+            gy += w[13] * (2.f * kSH3c * xy);
+            gz += w[13] * (-8.f * kSH3c * xz);
+            // Y14 = e z (xx - yy)
+            gx += w[14] * (2.f * kSH3e * xz);
+            gy += w[14] * (-2.f * kSH3e * yz);
+            gz += w[14] * (kSH3e * (xx - yy));
+            // Y15 = -a x (xx - 3yy)
+            gx += w[15] * (-3.f * kSH3a * (xx - yy));
+            gy += w[15] * (6.f * kSH3a * xy);
+        }
+    }
+}
+
 }  // namespace hm
