@@ -27,7 +27,7 @@ import torch
 
 from . import lib
 
-__all__ = ["MeshInput", "Renderer", "HybridRender", "GraphStep"]
+__all__ = ["MeshInput", "Renderer", "ChunkedRenderer", "HybridRender", "GraphStep"]
 
 
 @dataclass
@@ -66,7 +66,7 @@ class Renderer:
                  n_verts: int = 0, n_faces: int = 0, tex_shape=None, tile=(16, 16),
                  batch: Optional[int] = None, mesh_cull: bool = True, bg=(0.0, 0.0, 0.0),
                  pair_capacity: Optional[int] = None, item_capacity: Optional[int] = None,
-                 ellipse_cull: bool = True, device="cuda"):
+                 ellipse_cull: bool = True, pixel_buffers: Optional[dict] = None, device="cuda"):
         lib.load()
         self.device = torch.device(device)
         self.cam_list = list(cams)
@@ -96,24 +96,63 @@ class Renderer:
         self.n_pairs = torch.zeros(1, dtype=torch.int64, device=d)
         self.n_items = torch.zeros(1, dtype=torch.int64, device=d)
         self.status_word = torch.zeros(1, dtype=i32, device=d)
-        self.rgb = torch.empty(3 * self.npix, dtype=f32, device=d)
-        self.T = torch.empty(self.npix, dtype=f32, device=d)
-        self.n_contrib = torch.empty(self.npix, dtype=i32, device=d)
-        self.last_idx = torch.empty(self.npix, dtype=i32, device=d)
-        if self.has_mesh:
-            self.tri_id = torch.empty(self.npix, dtype=i32, device=d)
-            self.mesh_depth = torch.empty(self.npix, dtype=f32, device=d)
-            self.mesh_rgb = torch.empty(3 * self.npix, dtype=f32, device=d)
-            self.uv = torch.empty(2 * self.npix, dtype=f32, device=d)
-            self.tile_max = torch.empty(self.ntiles, dtype=f32, device=d)
+        if pixel_buffers is not None:
+            self.use_pixel_buffers(pixel_buffers)
         else:
-            self.tri_id = self.mesh_depth = self.mesh_rgb = self.uv = self.tile_max = None
+            self.rgb = torch.empty(3 * self.npix, dtype=f32, device=d)
+            self.T = torch.empty(self.npix, dtype=f32, device=d)
+            self.n_contrib = torch.empty(self.npix, dtype=i32, device=d)
+            self.last_idx = torch.empty(self.npix, dtype=i32, device=d)
+            if self.has_mesh:
+                self.tri_id = torch.empty(self.npix, dtype=i32, device=d)
+                self.mesh_depth = torch.empty(self.npix, dtype=f32, device=d)
+                self.mesh_rgb = torch.empty(3 * self.npix, dtype=f32, device=d)
+                self.uv = torch.empty(2 * self.npix, dtype=f32, device=d)
+                self.tile_max = torch.empty(self.ntiles, dtype=f32, device=d)
+            else:
+                self.tri_id = self.mesh_depth = self.mesh_rgb = self.uv = self.tile_max = None
         self._pair_cap = 0
         self._item_cap = 0
         self.set_pair_capacity(pair_capacity if pair_capacity else max(1024, 8 * M))
         if self.has_mesh:
             self.set_item_capacity(item_capacity if item_capacity else max(1024, 4 * self.V * self.n_faces))
         self.bwd_ws = None
+
+    # per-pixel (and per-tile) storage: (name, elements per pixel or per tile, dtype)
+    PIXEL_FIELDS = (("rgb", 3, torch.float32), ("T", 1, torch.float32), ("n_contrib", 1, torch.int32),
+                    ("last_idx", 1, torch.int32))
+    MESH_FIELDS = (("tri_id", 1, torch.int32), ("mesh_depth", 1, torch.float32),
+                   ("mesh_rgb", 3, torch.float32), ("uv", 2, torch.float32))
+
+    def use_pixel_buffers(self, bufs: dict):
+        """Write the per-pixel outputs (and the per-tile farthest mesh depth)
+        into caller tensors -- e.g. slices of larger arrays shared by several
+        renderers -- instead of the renderer's own: keys as ``PIXEL_FIELDS``,
+        ``MESH_FIELDS`` and ``tile_max``, flat, sized for these cameras."""
+        fields = self.PIXEL_FIELDS + (self.MESH_FIELDS if self.has_mesh else ())
+        for name, per, dt in fields:
+            t = bufs[name]
+            if t.dtype != dt or t.numel() != per * self.npix or not t.is_contiguous():
+                raise ValueError(f"pixel buffer {name}: need {per * self.npix} contiguous {dt}")
+            setattr(self, name, t)
+        if self.has_mesh:
+            t = bufs["tile_max"]
+            if t.dtype != torch.float32 or t.numel() != self.ntiles:
+                raise ValueError(f"tile_max: need {self.ntiles} float32")
+            self.tile_max = t
+        else:
+            self.tri_id = self.mesh_depth = self.mesh_rgb = self.uv = self.tile_max = None
+
+    def retarget(self, cams, bufs: dict):
+        """Render another set of cameras of the same sizes (in order) with
+        the same scratch (records, pair lists, workspaces)."""
+        cams = list(cams)
+        sizes = [(int(c.width), int(c.height)) for c in cams]
+        if sizes != self.sizes:
+            raise ValueError("retarget needs cameras of the same sizes")
+        self.cam_list = cams
+        self.cams = lib.cameras(cams)
+        self.use_pixel_buffers(bufs)
 
     # -- capacities -------------------------------------------------------------
     def set_pair_capacity(self, cap: int):
@@ -350,3 +389,112 @@ class GraphStep:
                 self.capture()                            # grows the buffers, then re-captures
                 self.graph.replay()
         return self
+
+
+class ChunkedRenderer:
+    """Many cameras rendered ``chunk`` at a time through one renderer's
+    scratch: records, sorted per-tile lists and workspaces exist for one
+    chunk only.  The per-pixel outputs of every camera are kept (they are the
+    backward pass's inputs); the backward pass re-projects each chunk and
+    recomputes its sorted lists instead of storing them -- bit-identical
+    lists, since the projection and the sort are deterministic.
+
+    Chunks of different camera sizes get a renderer each (one per distinct
+    size pattern).
+    """
+
+    def __init__(self, cams, n: int, sh_degree: int, *, chunk: int, device="cuda", **kw):
+        self.cam_list = list(cams)
+        self.V = len(self.cam_list)
+        self.chunk = max(1, int(chunk))
+        self.n, self.sh_degree = int(n), int(sh_degree)
+        self.K = (self.sh_degree + 1) ** 2
+        self.kw = dict(kw)
+        self.device = torch.device(device)
+        self.sizes = [(int(c.width), int(c.height)) for c in self.cam_list]
+        self.pix_off = np.concatenate([[0], np.cumsum([w * h for w, h in self.sizes])]).astype(np.int64)
+        self.npix = int(self.pix_off[-1])
+        tw, th = kw.get("tile", (16, 16))
+        tiles = [((w + tw - 1) // tw) * ((h + th - 1) // th) for w, h in self.sizes]
+        self.tile_off = np.concatenate([[0], np.cumsum(tiles)]).astype(np.int64)
+        self.has_mesh = kw.get("n_faces", 0) > 0 or kw.get("tex_shape") is not None
+        d = self.device
+        fields = Renderer.PIXEL_FIELDS + (Renderer.MESH_FIELDS if self.has_mesh else ())
+        for name, per, dt in fields:
+            setattr(self, name, torch.empty(per * self.npix, dtype=dt, device=d))
+        self.tile_max = torch.empty(int(self.tile_off[-1]), dtype=torch.float32, device=d) if self.has_mesh else None
+        self.chunks = [list(range(i, min(i + self.chunk, self.V))) for i in range(0, self.V, self.chunk)]
+        self._renderers = {}
+
+    def _bufs(self, idx):
+        a, b = int(self.pix_off[idx[0]]), int(self.pix_off[idx[-1] + 1])
+        out = {}
+        fields = Renderer.PIXEL_FIELDS + (Renderer.MESH_FIELDS if self.has_mesh else ())
+        for name, per, _ in fields:
+            out[name] = getattr(self, name)[per * a:per * b]
+        if self.has_mesh:
+            out["tile_max"] = self.tile_max[int(self.tile_off[idx[0]]):int(self.tile_off[idx[-1] + 1])]
+        return out
+
+    def renderer(self, ci: int) -> Renderer:
+        """The renderer set up for chunk ``ci`` (cameras and output slices)."""
+        idx = self.chunks[ci]
+        cams = [self.cam_list[k] for k in idx]
+        key = tuple(self.sizes[k] for k in idx)
+        r = self._renderers.get(key)
+        if r is None:
+            r = Renderer(cams, self.n, self.sh_degree, pixel_buffers=self._bufs(idx), device=self.device,
+                         **self.kw)
+            self._renderers[key] = r
+        else:
+            r.retarget(cams, self._bufs(idx))
+        return r
+
+    def render(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None):
+        """Forward pass of every chunk (capacity checks synchronise per chunk)."""
+        for ci in range(len(self.chunks)):
+            self.renderer(ci).render(means, scales, quats, opacity, sh, mesh)
+        return self
+
+    def forward(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None):
+        """Forward pass of every chunk, asynchronously (capacities as settled
+        by an earlier ``render``)."""
+        for ci in range(len(self.chunks)):
+            self.renderer(ci).forward(means, scales, quats, opacity, sh, mesh)
+        return self
+
+    def status(self):
+        """OR of the chunk renderers' status bits -- synchronises."""
+        st = 0
+        for r in self._renderers.values():
+            st |= r.status()[0]
+        return st
+
+    def grad_buffers(self, tex_shape=None):
+        d = self.device
+        g = dict(means=torch.zeros(self.n, 3, device=d), scales=torch.zeros(self.n, 3, device=d),
+                 quats=torch.zeros(self.n, 4, device=d), opacity=torch.zeros(self.n, device=d),
+                 sh=torch.zeros(self.n, self.K, 3, device=d))
+        if tex_shape is not None:
+            g["texture"] = torch.zeros(tex_shape[0], tex_shape[1], 3, device=d)
+        return g
+
+    def backward(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT=None,
+                 mesh: Optional[MeshInput] = None, tex_grad: bool = False, out=None, zero: bool = True):
+        """Gradients of the last forward: per chunk, re-project and re-sort
+        (the lists are recomputed, not stored), then the backward kernels,
+        accumulating into one set of gradient buffers."""
+        want_tex = tex_grad and self.has_mesh
+        g = out if out is not None else self.grad_buffers(mesh.texture.shape[:2] if want_tex else None)
+        if out is not None and zero:
+            for v in g.values():
+                v.zero_()
+        for ci, idx in enumerate(self.chunks):
+            r = self.renderer(ci)
+            a, b = int(self.pix_off[idx[0]]), int(self.pix_off[idx[-1] + 1])
+            r.project(means, scales, quats, opacity, sh)
+            r.bin_sort()
+            r.backward(means, scales, quats, opacity, sh, dL_drgb[3 * a:3 * b],
+                       None if dL_dT is None else dL_dT[a:b], mesh=mesh, tex_grad=want_tex, out=g,
+                       zero=False)
+        return g

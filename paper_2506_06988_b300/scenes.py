@@ -451,12 +451,13 @@ def config2_scene(seed: int = 2) -> Scene:
 
 def config2_target_params(scene: Scene, seed: int = 20) -> Gaussians:
     """Perturbed parameters whose rendering is the L1 target of config 2:
-    means + N(0,0.01), SH DC (colour) coefficients + N(0,0.05)."""
+    means + N(0,0.01); view-independent colours + N(0,0.05), i.e. the SH DC
+    coefficients + N(0,0.05)/C0 (the colour is 0.5 + C0 * DC + ...)."""
     r1, r2 = _rngs(seed, 2)
     g = scene.gaussians.copy()
     g.means = (g.means + r1.normal(0.0, 0.01, g.means.shape)).astype(np.float32)
     sh = g.sh.astype(np.float32)
-    sh[:, 0, :] += r2.normal(0.0, 0.05, sh[:, 0, :].shape)
+    sh[:, 0, :] += r2.normal(0.0, 0.05, sh[:, 0, :].shape) / 0.28209479177387814
     g.sh = sh.astype(g.sh.dtype)
     return g
 

@@ -10,7 +10,7 @@ from paper_2506_06988_b300.render import MeshInput
 
 pytestmark = pytest.mark.gpu
 
-from gpu_util import (EPS, compare_blend, expected_pairs, gpu_render, oracle_view,  # noqa: E402
+from gpu_util import (EPS, compare_blend, expected_pairs, gaussians_to_torch, gpu_render, oracle_view,  # noqa: E402
                       records_np, view_outputs)
 
 
@@ -297,4 +297,30 @@ def test_config1_full_size_sampled_pixels():
         assert np.array_equal(g.tri_id[pix], m.tri_id)
         assert np.array_equal(g.depth[pix], m.depth)
         st = compare_blend(g, oracle_view(s, v, pix=pix), pix=pix)
+        print(v, st)
+
+
+def test_config4_full_size_sampled_pixels_chunked():
+    """The large workload (4 connected rooms, ~1M faces with 15% pruned, 3M
+    Gaussians, 8 views at 3840x2160) through the chunked renderer (two views
+    at a time, the launch configuration the bench times); the oracle
+    evaluates 100 random pixels of two views one by one."""
+    from paper_2506_06988_b300.render import ChunkedRenderer
+    s = scenes.config4_scene()
+    g = s.gaussians
+    P = gaussians_to_torch(g)
+    mesh = MeshInput.from_numpy(s.mesh)
+    cr = ChunkedRenderer(s.cameras, g.n, g.sh_degree, chunk=2, n_verts=len(s.mesh.verts),
+                         n_faces=len(s.mesh.faces), tex_shape=s.mesh.texture.shape,
+                         bg=tuple(np.asarray(s.bg, np.float64)))
+    cr.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    for v in (0, 5):
+        pix = np.sort(rng.choice(s.cameras[v].n_pixels, 100, replace=False))
+        gv = view_outputs(cr, v)
+        m = O.mesh_raster(s.cameras[v], s.mesh, bg=s.bg, pix=pix)
+        assert np.array_equal(gv.tri_id[pix], m.tri_id)
+        assert np.array_equal(gv.depth[pix], m.depth)
+        st = compare_blend(gv, oracle_view(s, v, pix=pix), pix=pix)
         print(v, st)
