@@ -428,6 +428,9 @@ def run_ours(args):
         "roofline": roof, "kernels": per_kernel, "stage_roofline_hbm": stage_roof,
         "blend_units": {"evaluated_pairs": n_eval, "examined_pairs": n_exam, "blended_pairs": n_blended},
         "peak_kind": peak_kind,
+        "paper_context": {"hardware": "one V100", "hybrid_fps_mean": {"Deep Blending": 498, "ScanNet++": 231},
+                          "what": "forward only, the CUDA rasteriser routine, trained models of real "
+                                  "captures at an unstated resolution (Tab. 1); not this workload"},
         "clocks": gclk.summary(),
         "clocks_eager": clocks,
         "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
