@@ -441,7 +441,7 @@ def run_ours(args):
     if not args.no_cpu_baseline and rank == 0:
         from oracle import oracle as O
         t0 = time.perf_counter()
-        fwd_s, fb_s, info = cpu_oracle_sample(scene)
+        fwd_s, fb_s, info = cpu_oracle_sample(scene, rows=128, crop=44)
         line["cpu_baseline"] = {"value": 1.0 / fb_s, "unit": UNIT, "cores": O.num_threads(),
                                 "kind": "oracle", "forward_frames_per_s": 1.0 / fwd_s,
                                 "sample": f"one 1080p view: oracle forward over {info['rows']} rows "
