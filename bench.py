@@ -73,7 +73,7 @@ def _traffic(stage, views, tile):
     return nbytes if h.hexdigest()[:16] == digest else None
 
 
-KERNELS_PER_STEP = {"rasterize_mesh": 7, "project": 1, "bin_sort": 14, "blend_forward": 1,
+KERNELS_PER_STEP = {"rasterize_mesh": 7, "project": 1, "bin_sort": 6, "blend_forward": 1,
                     "texture_backward": 1, "blend_backward": 1, "project_backward": 1}
 
 
@@ -392,7 +392,10 @@ def run_ours(args):
                            if roof["bound"] == "alu" else f"HBM copy bandwidth, {peak_kind}")
     if roof["bound"] == "alu" and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = roof["achieved"] / (nsm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
-    sort_bytes = M * (4 * 2 * 4 * 2 + 8) + npairs * (8 + 2 * 2 * 8 + 8)
+    # count (record read, mask write), emit (mask + record read), per pair the
+    # 8-B key written and read back and the 4-B index written, per tile the
+    # counts, offsets and ranges
+    sort_bytes = M * (48 + 4) * 2 + npairs * (8 + 8 + 4) + r.ntiles * 16
     stage_roof = {"bin_sort": {"bytes": sort_bytes, "GB/s": sort_bytes / (stage_ms["bin_sort"] * 1e-3) / 1e9}}
     stage_roof["bin_sort"]["frac_of_hbm"] = stage_roof["bin_sort"]["GB/s"] / hbm
 

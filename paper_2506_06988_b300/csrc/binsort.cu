@@ -1,15 +1,23 @@
-// binsort.cu -- tile binning and the (tile, depth) sort of (Gaussian, tile)
+// binsort.cu -- tile binning and the per-tile depth sort of (Gaussian, tile)
 // pairs (the "tile-wise sorting" of the splatting rasteriser, Sec. 1).
 //
-// The sort is an LSD radix sort of the key (tile << 32 | depth bits), done
-// in two stages:
-//  1. the four depth digits are sorted on the un-duplicated records (every
-//     copy of a record carries the same depth, so sorting before duplication
-//     gives the same order and touches V*N elements instead of P pairs);
-//  2. pairs are emitted in that depth order and the tile digits are sorted
-//     stably on the P pairs.
-// Equal depths keep the record order (camera, then Gaussian index), so each
-// tile's list is ordered by (FP32 depth, Gaussian index).
+// Each tile's list must be ordered by (FP32 depth, Gaussian index).  The
+// pairs are bucketed by tile first and each tile's bucket is then sorted on
+// its own (a segmented sort), instead of a global radix sort on a
+// (tile, depth) key:
+//  1. count: per record, the tiles it keeps (mesh cull, ellipse test) -- a
+//     bit mask for small rectangles -- and per tile the number of records
+//     that keep it (atomic counts);
+//  2. scan of the per-tile counts: each tile's [begin, end) in the output,
+//     the pair count and the capacity check;
+//  3. emit: every kept (record, tile) writes the 64-bit key
+//     (depth bits << 32 | record index) into its tile's bucket at an
+//     atomically taken slot (bucket order is arbitrary at this point);
+//  4. sort each bucket by that key -- a warp per tile in registers (bitonic)
+//     for up to 128 pairs, a CTA in shared memory (radix) for up to 4096,
+//     chunk sorts plus merge passes beyond -- and write the record indices.
+// Positive FP32 depths order like their bit patterns, and all records of a
+// tile belong to one camera, so the key order is (depth, Gaussian index).
 //
 // Pairs are culled where the tile's farthest mesh depth is at or in front of
 // the Gaussian (depth >= tile_max_depth): every pixel of the tile then stops
@@ -92,21 +100,22 @@ __device__ __forceinline__ bool keep_tile(const ViewTable &vt, const float *tmax
 
 // records with more tiles than this are binned by the whole warp
 constexpr int kSmallRect = 8;
+// record whose kept tiles are recomputed at emission (large rectangle)
+constexpr uint32_t kMaskRecompute = 0x80000000u;
 
-// per record: number of kept tiles and a visibility flag.  Small rectangles
-// are walked by their own thread; large ones by the whole warp, one record
-// at a time, lanes over tiles.
+// Per record: the kept tiles of a small rectangle as a bit mask (bit
+// (ty - y0) * nx + (tx - x0)), kMaskRecompute for a large one, 0 for none;
+// per tile: atomic count of the records that keep it.  Small rectangles are
+// walked by their own thread; large ones by the whole warp, one record at a
+// time, lanes over tiles.
 __global__ void __launch_bounds__(256)
 bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                 int ellipse, uint32_t *__restrict__ cnt, uint32_t *__restrict__ flag) {
+                 int ellipse, uint32_t *__restrict__ kmask, uint32_t *__restrict__ tile_cnt) {
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    // lane l of warp w takes element w + nw (l + 32 k): a warp's records are
-    // spread over the whole range, so large ones do not pile up in one warp
-    for (long long base = w0; base < m; base += nw * 32) {
-        const long long it = base + (long long)lane * nw;
+    // one record per thread, consecutive records in a warp (coalesced loads)
+    {
+        const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         const bool valid = it < m;
         BinRec r;
         int nt = 0;
@@ -116,170 +125,496 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const floa
         } else {
             r = BinRec{};
         }
-        uint32_t k = 0;
+        uint32_t mask = 0;
         if (nt > 0 && nt <= kSmallRect) {
+            const ViewDev &V = vt.v[r.v];
+            int b = 0;
             for (int ty = r.y0; ty <= r.y1; ++ty)
-                for (int tx = r.x0; tx <= r.x1; ++tx) k += keep_tile(vt, tmax, ellipse, r, tx, ty);
+                for (int tx = r.x0; tx <= r.x1; ++tx, ++b)
+                    if (keep_tile(vt, tmax, ellipse, r, tx, ty)) {
+                        mask |= 1u << b;
+                        atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
+                    }
         }
         unsigned big = __ballot_sync(0xffffffffu, nt > kSmallRect);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const BinRec q = shfl_rec(r, src);
-            const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
-            uint32_t c = 0;
-            for (int t0 = 0; t0 < ntot; t0 += 32) {
-                const int t = t0 + lane;
-                const bool kept = t < ntot && keep_tile(vt, tmax, ellipse, q, q.x0 + t % nx, q.y0 + t / nx);
-                c += __popc(__ballot_sync(0xffffffffu, kept));
-            }
-            if (lane == src) k = c;
-        }
-        if (valid) {
-            cnt[it] = k;
-            flag[it] = k != 0;
-        }
-    }
-}
-
-// visible records, compacted in record order: depth-sort keys and record ids
-__global__ void __launch_bounds__(256)
-bin_compact_kernel(long long m, const Record *__restrict__ rec, const uint32_t *__restrict__ cnt,
-                   const uint32_t *__restrict__ pos, uint32_t *__restrict__ dkey,
-                   uint32_t *__restrict__ ditem) {
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
-         it += (long long)gridDim.x * blockDim.x) {
-        if (cnt[it] == 0) continue;
-        const uint32_t o = pos[it];
-        dkey[o] = __float_as_uint(rec[it].b.z);
-        ditem[o] = (uint32_t)it;
-    }
-}
-
-// per depth-sorted visible record: write its kept (tile, record) pairs at its
-// scan offset; same small/large split as the count
-__global__ void __launch_bounds__(256)
-bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                int ellipse, const uint32_t *__restrict__ sorted_items, const long long *n_vis,
-                const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
-                long long capacity, uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
-    const long long m = *n_vis;
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    // strided as in the count: the depth order puts the large near-camera
-    // records together, and a warp walks its large records one at a time
-    for (long long base = w0; base < m; base += nw * 32) {
-        const long long j = base + (long long)lane * nw;
-        bool valid = j < m;
-        uint32_t it = 0, k = 0;
-        long long o = 0;
-        BinRec r = BinRec{};
-        int nt = 0;
-        if (valid) {
-            it = sorted_items[j];
-            k = cnt[it];
-            o = offs[j];
-            valid = k > 0 && o + k <= capacity;      // capacity exceeded: flagged by the scan
-            if (valid) {
-                r = load_bin_rec(rec, it, n);
-                nt = rec_tiles(r);
-            }
-        }
-        if (valid && nt <= kSmallRect) {
-            const ViewDev &V = vt.v[r.v];
-            for (int ty = r.y0; ty <= r.y1; ++ty)
-                for (int tx = r.x0; tx <= r.x1; ++tx) {
-                    if (!keep_tile(vt, tmax, ellipse, r, tx, ty)) continue;
-                    pkey[o] = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
-                    pval[o] = it;
-                    ++o;
-                }
-        }
-        unsigned big = __ballot_sync(0xffffffffu, valid && nt > kSmallRect);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const BinRec q = shfl_rec(r, src);
-            const uint32_t qit = __shfl_sync(0xffffffffu, it, src);
-            long long qo = __shfl_sync(0xffffffffu, o, src);
             const ViewDev &V = vt.v[q.v];
             const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
             for (int t0 = 0; t0 < ntot; t0 += 32) {
                 const int t = t0 + lane;
                 const int tx = q.x0 + t % nx, ty = q.y0 + t / nx;
-                const bool kept = t < ntot && keep_tile(vt, tmax, ellipse, q, tx, ty);
-                const unsigned km = __ballot_sync(0xffffffffu, kept);
-                if (kept) {
-                    const long long at = qo + __popc(km & lt);
-                    pkey[at] = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
-                    pval[at] = qit;
-                }
-                qo += __popc(km);
+                if (t < ntot && keep_tile(vt, tmax, ellipse, q, tx, ty))
+                    atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
             }
+            if (lane == src) mask = kMaskRecompute;
         }
+        if (valid) kmask[it] = mask;
     }
 }
 
-// pairs to sort: all of them, or none when the capacity was exceeded (the
-// emitted array then has unwritten slots; the caller re-runs with more room)
+// pairs to sort: all of them, or none when the capacity was exceeded
 __global__ void clamp_count_kernel(const long long *total, long long capacity, long long *n_out) {
     long long t = *total;
     *n_out = t <= capacity ? t : 0;
 }
 
-// [begin, end) of each tile's run in the sorted keys
+__device__ __forceinline__ unsigned long long pair_key(const BinRec &r, long long it) {
+    return ((unsigned long long)__float_as_uint(r.depth) << 32) | (unsigned long long)(uint32_t)it;
+}
+
+// every kept (record, tile): its key into the tile's bucket, at a slot
+// taken from the tile's cursor (initialised to the bucket's start); nothing
+// is written when the capacity was exceeded
 __global__ void __launch_bounds__(256)
-tile_ranges_kernel(const uint32_t *__restrict__ keys, const long long *n_dev,
-                   uint32_t n_tiles, uint32_t *__restrict__ ranges) {
-    const long long n = *n_dev;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        if (k >= n_tiles) continue;
-        if (i == 0 || keys[i - 1] != k) ranges[2 * (size_t)k] = (uint32_t)i;
-        if (i == n - 1 || keys[i + 1] != k) ranges[2 * (size_t)k + 1] = (uint32_t)(i + 1);
+bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
+                int ellipse, const uint32_t *__restrict__ kmask, uint32_t *__restrict__ cursor,
+                const long long *n_sort, unsigned long long *__restrict__ keys) {
+    if (*n_sort == 0) return;
+    const long long m = (long long)vt.n_views * n;
+    const int lane = threadIdx.x & 31;
+    {
+        const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const uint32_t mask = it < m ? kmask[it] : 0u;
+        BinRec r = BinRec{};
+        if (mask) r = load_bin_rec(rec, it, n);
+        if (mask && mask != kMaskRecompute) {
+            const ViewDev &V = vt.v[r.v];
+            const unsigned long long key = pair_key(r, it);
+            const int nx = r.x1 - r.x0 + 1;
+            const uint32_t g0 = V.tile_off + r.y0 * V.tiles_x + r.x0;
+            // all slots first (independent atomics in flight together), then the stores
+            uint32_t pos[kSmallRect];
+#pragma unroll
+            for (int b = 0; b < kSmallRect; ++b)
+                if (mask & (1u << b)) pos[b] = atomicAdd(&cursor[g0 + (b / nx) * V.tiles_x + b % nx], 1u);
+#pragma unroll
+            for (int b = 0; b < kSmallRect; ++b)
+                if (mask & (1u << b)) keys[pos[b]] = key;
+        }
+        unsigned big = __ballot_sync(0xffffffffu, mask == kMaskRecompute);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const BinRec q = shfl_rec(r, src);
+            const long long qit = __shfl_sync(0xffffffffu, it, src);
+            const unsigned long long key = pair_key(q, qit);
+            const ViewDev &V = vt.v[q.v];
+            const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
+            for (int t0 = 0; t0 < ntot; t0 += 32) {
+                const int t = t0 + lane;
+                const int tx = q.x0 + t % nx, ty = q.y0 + t / nx;
+                if (t < ntot && keep_tile(vt, tmax, ellipse, q, tx, ty))
+                    keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] = key;
+            }
+        }
     }
 }
 
-int tile_key_passes(int total_tiles) {
-    int bits = 1;
-    while ((1ll << bits) < (long long)total_tiles) ++bits;
-    return (bits + 7) / 8;
+// ---------------------------------------------------------------------------
+// segmented sort of the tile buckets
+// ---------------------------------------------------------------------------
+constexpr int kWarpSeg = 128;      // bucket sizes sorted by one warp in registers
+constexpr int kMidSeg = 1024;      // ... by a 128-thread CTA in shared memory (radix)
+constexpr int kSegMax = 4096;      // ... by a 256-thread CTA in shared memory (radix)
+constexpr int kSegThreads = 256;
+
+// compare-exchange of a (low, high) element pair for an ascending (asc) or
+// descending bitonic stage: afterwards lo holds the min if asc, else the max
+__device__ __forceinline__ void cmp_swap(unsigned long long &lo, unsigned long long &hi, bool asc) {
+    const bool sw = (lo > hi) == asc;
+    const unsigned long long a = lo, b = hi;
+    lo = sw ? b : a;
+    hi = sw ? a : b;
+}
+
+// in-lane compare-exchange stage of warp_bitonic: slots sl and sl ^ JS of
+// each lane (partner distance 32 JS elements)
+template <int E, int JS>
+__device__ __forceinline__ void lane_stage(unsigned long long (&v)[E], int lane, int k) {
+#pragma unroll
+    for (int sl = 0; sl < E; ++sl)
+        if (!(sl & JS)) cmp_swap(v[sl], v[sl | JS], ((lane + 32 * sl) & k) == 0);
+}
+
+// Bitonic sort of the 32 E keys of a warp held in registers: element
+// e = lane + 32 s sits in lane e % 32, slot s.  Stages whose partner
+// distance j is >= 32 pair two slots of the same lane; shorter ones pair the
+// same slot of lanes lane and lane ^ j (one shuffle per slot).  The stage
+// loops run at run time (only the slot loop is unrolled), which keeps the
+// code small enough for the instruction cache.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E], int lane) {
+    constexpr int N = 32 * E;
+#pragma unroll 1
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll 1
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int js = j >> 5;
+                if (E > 1 && js == 1) lane_stage<E, 1>(v, lane, k);
+                if (E > 2 && js == 2) lane_stage<E, (E > 2 ? 2 : 1)>(v, lane, k);
+                if (E > 4 && js == 4) lane_stage<E, (E > 4 ? 4 : 1)>(v, lane, k);
+                if (E > 8 && js == 8) lane_stage<E, (E > 8 ? 8 : 1)>(v, lane, k);
+                if (E > 16 && js == 16) lane_stage<E, (E > 16 ? 16 : 1)>(v, lane, k);
+            } else {
+                const bool low = (lane & j) == 0;
+#pragma unroll
+                for (int sl = 0; sl < E; ++sl) {
+                    const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[sl], j);
+                    // the lower element keeps the min in an ascending block
+                    const bool take_min = low == (((lane + 32 * sl) & k) == 0);
+                    v[sl] = take_min ? (p < v[sl] ? p : v[sl]) : (p > v[sl] ? p : v[sl]);
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_bucket(const unsigned long long *__restrict__ keys,
+                                                 uint32_t *__restrict__ vals, uint32_t off, uint32_t cnt,
+                                                 int lane) {
+    unsigned long long v[E];
+#pragma unroll
+    for (int sl = 0; sl < E; ++sl) {
+        const uint32_t e = lane + 32 * sl;
+        v[sl] = e < cnt ? keys[off + e] : ~0ull;
+    }
+    warp_bitonic<E>(v, lane);
+#pragma unroll
+    for (int sl = 0; sl < E; ++sl) {
+        const uint32_t e = lane + 32 * sl;
+        if (e < cnt) vals[off + e] = (uint32_t)v[sl];
+    }
+}
+
+// Warp per tile (grid-stride): writes the tile's range; buckets of up to 128
+// keys are sorted in registers (the smallest power-of-two slot count that
+// holds them); larger buckets go to the mid-size (up to 4096 keys, radix
+// sorted by a CTA) or the large list.  Nothing when the capacity was
+// exceeded (ranges stay empty).
+__global__ void __launch_bounds__(256)
+seg_sort_small_kernel(uint32_t n_tiles, const uint32_t *__restrict__ tile_off,
+                      const uint32_t *__restrict__ tile_cnt, const long long *n_sort,
+                      const unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals,
+                      uint32_t *__restrict__ ranges, uint32_t *__restrict__ mid_list,
+                      unsigned int *__restrict__ mid_count, uint32_t *__restrict__ big_list,
+                      unsigned int *__restrict__ big_count) {
+    if (*n_sort == 0) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t gt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < n_tiles; gt += nw) {
+        const uint32_t off = tile_off[gt], cnt = tile_cnt[gt];
+        if (lane == 0) {
+            ranges[2 * (size_t)gt] = off;
+            ranges[2 * (size_t)gt + 1] = off + cnt;
+        }
+        if (cnt == 0) continue;
+        if (cnt == 1) {
+            if (lane == 0) vals[off] = (uint32_t)keys[off];
+        } else if (cnt <= 32) {
+            warp_sort_bucket<1>(keys, vals, off, cnt, lane);
+        } else if (cnt <= 64) {
+            warp_sort_bucket<2>(keys, vals, off, cnt, lane);
+        } else if (cnt <= (uint32_t)kWarpSeg) {
+            warp_sort_bucket<4>(keys, vals, off, cnt, lane);
+        } else if (lane == 0) {
+            if (cnt <= (uint32_t)kMidSeg) mid_list[atomicAdd(mid_count, 1u)] = gt;
+            else big_list[atomicAdd(big_count, 1u)] = gt;
+        }
+    }
+}
+
+// ---- CTA radix sort of one bucket of up to kSegMax keys in shared memory.
+// The sort key is the depth (the high word of the 64-bit pair key) with the
+// record index as payload: 4 stable LSD passes of 8 bits, skipping passes in
+// which every key has the same digit.  A pass ranks the keys warp by warp
+// (match.any gives each key its rank among equal digits in input order),
+// turns the per-warp digit counts into offsets and scatters -- stable, so
+// equal depths keep their input order, which the emission left arbitrary:
+// a final fix-up sorts each run of equal depths by record index, which
+// makes the result the (depth, index) order.
+template <int THREADS, int CAP>
+struct RadixSmem {
+    static constexpr int kWarps = THREADS / 32;
+    uint32_t k[2][CAP];
+    uint32_t v[2][CAP];
+    uint32_t whist[kWarps][257];   // per-warp digit counts, then offsets
+    uint32_t dstart[256];          // bucket-local start of each digit
+    uint32_t wsum[kWarps];
+    uint32_t kand, kor;
+};
+
+template <int THREADS, int CAP>
+__device__ void radix_pass(RadixSmem<THREADS, CAP> &S, int src, int n, int shift) {
+    constexpr int kWarps = THREADS / 32, kItems = CAP / THREADS;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (int i = t; i < kWarps * 257; i += THREADS) (&S.whist[0][0])[i] = 0;
+    __syncthreads();
+    // warp w ranks the contiguous chunk [w C, (w + 1) C), items in input order
+    const int per = (n + THREADS - 1) / THREADS;     // items per lane
+    const int C = 32 * per;
+    uint32_t key[kItems], val[kItems], rank[kItems];
+    int dig[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        if (j >= per) break;
+        const int e = w * C + j * 32 + lane;
+        const bool valid = e < n;
+        key[j] = valid ? S.k[src][e] : 0u;
+        val[j] = valid ? S.v[src][e] : 0u;
+        const int d = valid ? (int)((key[j] >> shift) & 255u) : 256;
+        dig[j] = d;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = S.whist[w][d];
+        __syncwarp();
+        if ((peers & lt) == 0) S.whist[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[j] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // digit d (threads take digits t, t + THREADS, ...): offsets of the warps
+    // within the digit and the digit total; then an exclusive scan over the
+    // 256 digits
+    for (int d = t; d < 256; d += THREADS) {
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t c = S.whist[ww][d];
+            S.whist[ww][d] = cnt;
+            cnt += c;
+        }
+        S.dstart[d] = cnt;
+    }
+    __syncthreads();
+    if (w == 0) {
+        // 256 totals, 8 per lane: serial within the lane, shuffle scan across
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            c[q] = S.dstart[lane * 8 + q];
+            sum += c[q];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            S.dstart[lane * 8 + q] = run;
+            run += c[q];
+        }
+    }
+    __syncthreads();
+    const int dst = src ^ 1;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        if (j >= per) break;
+        const int d = dig[j];
+        if (d < 256) {
+            const uint32_t pos = S.dstart[d] + S.whist[w][d] + rank[j];
+            S.k[dst][pos] = key[j];
+            S.v[dst][pos] = val[j];
+        }
+    }
+    __syncthreads();
+}
+
+// CTA per bucket of at most CAP keys (grid-stride over its list).
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS)
+seg_sort_radix_kernel(const uint32_t *__restrict__ list, const unsigned int *list_count,
+                      const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ tile_cnt,
+                      const unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RadixSmem<THREADS, CAP> &S = *reinterpret_cast<RadixSmem<THREADS, CAP> *>(smem_raw);
+    const int t = threadIdx.x;
+    const unsigned int nl = *list_count;
+    for (unsigned int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const uint32_t gt = list[li];
+        const uint32_t off = tile_off[gt];
+        const int n = (int)tile_cnt[gt];
+        if (n > CAP) continue;                       // a larger bucket: the merge path's
+        if (t == 0) {
+            S.kand = 0xFFFFFFFFu;
+            S.kor = 0u;
+        }
+        __syncthreads();
+        uint32_t ka = 0xFFFFFFFFu, ko = 0u;
+        for (int i = t; i < n; i += THREADS) {
+            const unsigned long long kv = keys[off + i];
+            const uint32_t k = (uint32_t)(kv >> 32);
+            S.k[0][i] = k;
+            S.v[0][i] = (uint32_t)kv;
+            ka &= k;
+            ko |= k;
+        }
+        atomicAnd(&S.kand, ka);
+        atomicOr(&S.kor, ko);
+        __syncthreads();
+        const uint32_t differ = S.kand ^ S.kor;     // bits that are not the same in every key
+        int src = 0;
+        for (int pass = 0; pass < 4; ++pass) {
+            if (((differ >> (8 * pass)) & 255u) == 0) continue;   // one digit value: identity pass
+            radix_pass<THREADS, CAP>(S, src, n, 8 * pass);
+            src ^= 1;
+        }
+        // runs of equal depth: order by record index (a thread per run start)
+        for (int i = t; i < n; i += THREADS) {
+            const uint32_t k = S.k[src][i];
+            if (i > 0 && S.k[src][i - 1] == k) continue;          // not a run start
+            int e = i + 1;
+            while (e < n && S.k[src][e] == k) ++e;
+            for (int a = i + 1; a < e; ++a) {                     // insertion sort of the run
+                const uint32_t x = S.v[src][a];
+                int b = a - 1;
+                while (b >= i && S.v[src][b] > x) {
+                    S.v[src][b + 1] = S.v[src][b];
+                    --b;
+                }
+                S.v[src][b + 1] = x;
+            }
+        }
+        __syncthreads();
+        for (int i = t; i < n; i += THREADS) vals[off + i] = S.v[src][i];
+        __syncthreads();
+    }
+}
+
+template <int THREADS, int CAP>
+cudaError_t launch_radix_buckets(const uint32_t *list, const unsigned int *count, const uint32_t *tile_off,
+                                 const uint32_t *tile_cnt, const unsigned long long *keys, uint32_t *vals,
+                                 int grid, cudaStream_t s) {
+    static bool attr = false;
+    const int smem = (int)sizeof(RadixSmem<THREADS, CAP>);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(seg_sort_radix_kernel<THREADS, CAP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    seg_sort_radix_kernel<THREADS, CAP><<<grid, THREADS, smem, s>>>(list, count, tile_off, tile_cnt, keys, vals);
+    return cudaGetLastError();
+}
+
+// bitonic sort of s[0, P) (P a power of two <= kSegMax) by the CTA
+__device__ void block_bitonic(unsigned long long *s, int P) {
+    const int t = threadIdx.x;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < P / 2; i += kSegThreads) {
+                const int e = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                unsigned long long a = s[e], b = s[e | j];
+                cmp_swap(a, b, (e & k) == 0);
+                s[e] = a;
+                s[e | j] = b;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// number of elements of a[0, na) that precede the merge-path diagonal d of
+// the merge of a and b (stable: on equal keys a first; keys here are unique)
+__device__ __forceinline__ long long merge_split(const unsigned long long *a, long long na,
+                                                 const unsigned long long *b, long long nb, long long d) {
+    long long lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (a[mid] <= b[d - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// CTA per bucket above kSegMax keys (grid-stride over the list of buckets
+// above kMidSeg, skipping those the radix CTA takes): bitonic sorts of
+// kSegMax chunks in shared memory, then merge passes doubling the run
+// length, ping-ponging between the bucket and the same range of `scratch`;
+// the record indices of the final run are written to vals.
+__global__ void __launch_bounds__(kSegThreads)
+seg_sort_large_kernel(const uint32_t *__restrict__ large_list, const unsigned int *large_count,
+                      const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ tile_cnt,
+                      unsigned long long *__restrict__ keys, unsigned long long *__restrict__ scratch,
+                      uint32_t *__restrict__ vals) {
+    __shared__ unsigned long long s[kSegMax];
+    const int t = threadIdx.x;
+    const unsigned int nl = *large_count;
+    for (unsigned int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const uint32_t gt = large_list[li];
+        const long long off = tile_off[gt], n = tile_cnt[gt];
+        if (n <= kSegMax) continue;                  // sorted by the radix CTA
+        unsigned long long *src = keys + off, *dst = scratch + off;
+        for (long long c0 = 0; c0 < n; c0 += kSegMax) {
+            const int cn = (int)min((long long)kSegMax, n - c0);
+            int P = 1;
+            while (P < cn) P <<= 1;
+            for (int i = t; i < P; i += kSegThreads) s[i] = i < cn ? src[c0 + i] : ~0ull;
+            __syncthreads();
+            block_bitonic(s, P);
+            if (n <= kSegMax) {
+                for (int i = t; i < cn; i += kSegThreads) vals[off + i] = (uint32_t)s[i];
+            } else {
+                for (int i = t; i < cn; i += kSegThreads) src[c0 + i] = s[i];
+            }
+            __syncthreads();
+        }
+        if (n <= kSegMax) continue;
+        // merge passes: runs of length L in src -> runs of 2L in dst
+        for (long long L = kSegMax; L < n; L <<= 1) {
+            const bool last = 2 * L >= n;
+            for (long long a0 = 0; a0 < n; a0 += 2 * L) {
+                const long long na = min(L, n - a0), nb = min(L, max(0ll, n - a0 - L));
+                const unsigned long long *A = src + a0, *B = src + a0 + na;
+                const long long tot = na + nb;
+                const long long per = (tot + kSegThreads - 1) / kSegThreads;
+                const long long d0 = min(tot, per * t), d1 = min(tot, per * (t + 1));
+                long long ia = merge_split(A, na, B, nb, d0), ib = d0 - ia;
+                for (long long d = d0; d < d1; ++d) {
+                    const bool fa = ib >= nb || (ia < na && A[ia] <= B[ib]);
+                    const unsigned long long v = fa ? A[ia++] : B[ib++];
+                    if (last) vals[off + a0 + d] = (uint32_t)v;
+                    else dst[a0 + d] = v;
+                }
+            }
+            __syncthreads();
+            unsigned long long *tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+    }
 }
 
 struct BinWs {
-    uint32_t *cnt, *flag, *vpos, *dkey0, *dkey1, *ditem0, *ditem1, *offs;
-    uint32_t *pkey0, *pkey1, *pval_tmp;
-    long long *n_vis, *n_sort;
+    uint32_t *kmask, *tile_cnt, *tile_off, *tile_fill, *mid_list, *big_list;
+    unsigned long long *keys, *scratch;
+    unsigned int *counts;   // [0] mid-size buckets (<= kMidSeg), [1] larger buckets
+    long long *n_sort;
     ScanWs scan;
-    SortWs sort;
 };
 
-BinWs carve(void *ws, long long m, long long cap, size_t *bytes) {
+BinWs carve(void *ws, long long m, long long cap, long long tiles, size_t *bytes) {
     WsCarver c(ws);
     BinWs b;
-    b.cnt = c.take<uint32_t>(m);
-    b.flag = c.take<uint32_t>(m);
-    b.vpos = c.take<uint32_t>(m);
-    b.dkey0 = c.take<uint32_t>(m);
-    b.dkey1 = c.take<uint32_t>(m);
-    b.ditem0 = c.take<uint32_t>(m);
-    b.ditem1 = c.take<uint32_t>(m);
-    b.offs = c.take<uint32_t>(m);
-    b.pkey0 = c.take<uint32_t>(cap);
-    b.pkey1 = c.take<uint32_t>(cap);
-    b.pval_tmp = c.take<uint32_t>(cap);
-    b.n_vis = c.take<long long>(1);
+    b.kmask = c.take<uint32_t>(m);
+    b.tile_cnt = c.take<uint32_t>(tiles);
+    b.tile_off = c.take<uint32_t>(tiles);
+    b.tile_fill = c.take<uint32_t>(tiles);
+    b.mid_list = c.take<uint32_t>(tiles);
+    b.big_list = c.take<uint32_t>(tiles);
+    b.keys = c.take<unsigned long long>(cap);
+    b.scratch = c.take<unsigned long long>(cap);
+    b.counts = c.take<unsigned int>(2);
     b.n_sort = c.take<long long>(1);
-    b.scan.tile_status = c.take<unsigned long long>(scan_tiles(m) + 1);
+    b.scan.tile_status = c.take<unsigned long long>(scan_tiles(tiles) + 1);
     b.scan.ticket = c.take<unsigned int>(1);
-    long long mt = sort_tiles(m > cap ? m : cap) + 1;
-    b.sort.max_tiles = mt;
-    b.sort.hist = c.take<uint32_t>(4 * 256);
-    b.sort.lookback = c.take<uint32_t>((size_t)4 * 256 * mt);
-    b.sort.ticket = c.take<unsigned int>(4);
     *bytes = c.off + 256;
     return b;
 }
@@ -302,7 +637,7 @@ extern "C" size_t hm_bin_sort_workspace_size(const hm_camera *cams, int32_t n_vi
     ViewTable vt;
     if (!build_view_table(cams, n_views, opt, &vt) || n < 0 || capacity < 0) return 0;
     size_t bytes = 0;
-    carve(nullptr, (long long)n_views * n, capacity, &bytes);
+    carve(nullptr, (long long)n_views * n, capacity, vt.total_tiles, &bytes);
     return bytes;
 }
 
@@ -320,48 +655,49 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
         return fail(HM_ERR_INVALID_ARG, "null pointer");
     if ((uintptr_t)records & 15) return fail(HM_ERR_INVALID_ARG, "records must be 16-byte aligned");
     const long long m = (long long)n_views * n;
+    const long long T = vt.total_tiles;
     size_t need = 0;
-    carve(nullptr, m, capacity, &need);
+    carve(nullptr, m, capacity, T, &need);
     if (!ws || ws_bytes < need) return fail(HM_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, need);
     cudaStream_t s = (cudaStream_t)stream;
-    BinWs b = carve(ws, m, capacity, &need);
+    BinWs b = carve(ws, m, capacity, T, &need);
     const Record *rec = reinterpret_cast<const Record *>(records);
     const float *tmax = opt->mesh_cull ? tile_max_depth : nullptr;
-    cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)vt.total_tiles, s);
+    cudaError_t e = cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)T, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (m == 0) return cuda_status(cudaMemsetAsync(n_pairs_out, 0, sizeof(long long), s));
+    if ((e = cudaMemsetAsync(b.tile_cnt, 0, sizeof(uint32_t) * (size_t)T, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b.counts, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess)
+        return cuda_status(e);
 
-    // 1. kept-tile counts per record
-    bin_count_kernel<<<grid_for(m, 256), 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.cnt, b.flag);
+    // 1. kept tiles per record, records per tile
+    const unsigned rgrid = (unsigned)((m + 255) / 256);
+    bin_count_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.kmask, b.tile_cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    // 2. compact the visible records (count > 0) and sort them by depth
-    //    (4 digit passes; the result lands back in dkey0/ditem0)
-    e = launch_scan(b.flag, nullptr, b.vpos, m, b.n_vis, -1, d_status, b.scan, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    bin_compact_kernel<<<grid_for(m, 256), 256, 0, s>>>(m, rec, b.cnt, b.vpos, b.dkey0, b.ditem0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    e = launch_radix_sort(b.dkey0, b.ditem0, b.dkey1, b.ditem1, b.n_vis, m, 4, false, d_status,
-                          b.sort, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    // 3. pair offsets in depth order; pair count and capacity check
-    e = launch_scan(b.cnt, b.ditem0, b.offs, m, (long long *)n_pairs_out, capacity, d_status, b.scan, s,
-                    b.n_vis);
+    // 2. tile offsets, pair count and capacity check
+    e = launch_scan(b.tile_cnt, nullptr, b.tile_off, T, (long long *)n_pairs_out, capacity, d_status, b.scan, s);
     if (e != cudaSuccess) return cuda_status(e);
     clamp_count_kernel<<<1, 1, 0, s>>>((const long long *)n_pairs_out, capacity, b.n_sort);
-    // 4. emit (tile, record) pairs; the final radix pass must land in pair_vals
-    const int passes = tile_key_passes(vt.total_tiles);
-    uint32_t *v0 = (passes & 1) ? b.pval_tmp : pair_vals;
-    uint32_t *v1 = (passes & 1) ? pair_vals : b.pval_tmp;
-    bin_emit_kernel<<<grid_for(m, 256), 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.ditem0, b.n_vis,
-                                                      b.cnt, b.offs, capacity, b.pkey0, v0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    // 5. stable sort of the pairs by tile
-    e = launch_radix_sort(b.pkey0, v0, b.pkey1, v1, b.n_sort, capacity, passes, false, d_status,
-                          b.sort, s);
+    // 3. keys into the tile buckets (cursors start at the bucket starts)
+    e = cudaMemcpyAsync(b.tile_fill, b.tile_off, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    const uint32_t *kfinal = (passes & 1) ? b.pkey1 : b.pkey0;
-    // 6. tile ranges
-    tile_ranges_kernel<<<grid_for(capacity, 256), 256, 0, s>>>(kfinal, b.n_sort, (uint32_t)vt.total_tiles,
-                                                                 tile_ranges);
+    bin_emit_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.kmask, b.tile_fill, b.n_sort,
+                                          b.keys);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    // 4. sort every bucket; tile ranges
+    seg_sort_small_kernel<<<grid_for(T * 32, 256), 256, 0, s>>>((uint32_t)T, b.tile_off, b.tile_cnt, b.n_sort,
+                                                                 b.keys, pair_vals, tile_ranges, b.mid_list,
+                                                                 b.counts, b.big_list, b.counts + 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    e = launch_radix_buckets<128, kMidSeg>(b.mid_list, b.counts, b.tile_off, b.tile_cnt, b.keys, pair_vals,
+                                          148 * 10, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    // buckets above kMidSeg: the 4096-key radix CTA, and beyond that chunk
+    // sorts and merges (each kernel skips the sizes it does not take)
+    e = launch_radix_buckets<256, kSegMax>(b.big_list, b.counts + 1, b.tile_off, b.tile_cnt, b.keys, pair_vals,
+                                          148 * 2, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    seg_sort_large_kernel<<<148 * 2, kSegThreads, 0, s>>>(b.big_list, b.counts + 1, b.tile_off, b.tile_cnt,
+                                                          b.keys, b.scratch, pair_vals);
     return cuda_status(cudaGetLastError());
 }

@@ -129,25 +129,6 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, 
                         long long *total, long long capacity, int32_t *d_status, ScanWs ws,
                         cudaStream_t s, const long long *n_dev = nullptr);
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
-struct SortWs {
-    uint32_t *hist;        // [4][256]
-    uint32_t *lookback;    // [4][max_tiles][256]
-    unsigned int *ticket;  // [4]
-    long long max_tiles;
-};
-inline long long sort_tiles(long long n) { return (n + kSortTile - 1) / kSortTile; }
-// Stable LSD radix sort of (key, value) uint32 pairs on key bits
-// [0, 8*passes); the count is *n_dev (<= n_max).  Ping-pongs between
-// (k0,v0) and (k1,v1); with an even number of passes the result ends in
-// (k0,v0), otherwise in (k1,v1).  identity_vals: the input values are the
-// input positions (v0 is not read, only written).
-cudaError_t launch_radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
-                              const long long *n_dev, long long n_max, int passes,
-                              bool identity_vals, int32_t *d_status, SortWs ws, cudaStream_t s);
-
 cudaError_t launch_fill_i64(long long *p, long long v, cudaStream_t s);
 
 }  // namespace hm

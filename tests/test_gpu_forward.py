@@ -113,8 +113,8 @@ def test_projection_records_match_oracle():
 def test_bin_sort_lists_exact(cull):
     """Rectangle binning (ellipse test off): every list is exactly the
     records whose tile range covers the tile (minus the mesh cull), in
-    (depth, index) order -- an exact check of scan, emit, both radix sorts
-    and the ranges."""
+    (depth, index) order -- an exact check of the counts, the tile scan, the
+    emission, the per-tile sort and the ranges."""
     s = _small_room(res=((160, 120), (96, 64)), n_gauss=3000)
     r, _, _ = gpu_render(s, mesh_cull=cull, ellipse_cull=False)
     rec = records_np(r)
@@ -128,6 +128,32 @@ def test_bin_sort_lists_exact(cull):
         b, e = ranges[gt]
         assert e - b == len(lst), gt
         assert vals[b:e].tolist() == lst, gt
+
+
+def test_bin_sort_dense_tiles_exact():
+    """12,000 Gaussians crowded onto the 4 central tiles of a 64x64 view (no
+    mesh, ellipse test off): buckets of several thousand pairs exercise the
+    CTA and the chunk-sort-and-merge paths of the segmented sort; every list
+    must still be exactly the covering records in (depth, index) order."""
+    rng = np.random.default_rng(21)
+    n = 12000
+    z = rng.uniform(1.5, 3.0, n)
+    means = np.stack([rng.uniform(-0.08, 0.08, n) * z, rng.uniform(-0.08, 0.08, n) * z, z], 1)
+    g = scenes.Gaussians(means.astype(np.float32), np.exp(rng.normal(-4.0, 0.3, (n, 3))).astype(np.float32),
+                         scenes._unit_quats(rng, n), scenes._sigmoid(rng.normal(0.0, 1.0, n)).astype(np.float32),
+                         rng.uniform(0.0, 1.0, (n, 1, 3)).astype(np.float32), 0)
+    cam = scenes.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 64.0, 64.0, 32.0, 32.0, 64, 64)
+    s = scenes.Scene("dense", 21, g, None, [cam], np.zeros(3, np.float32))
+    r, _, _ = gpu_render(s, ellipse_cull=False)
+    rec = records_np(r)
+    want = expected_pairs(r, rec)
+    assert max(len(l) for l in want) > 4096
+    ranges = r.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    vals = r.pair_vals.cpu().numpy().astype(np.int64)
+    assert int(r.n_pairs.item()) == sum(len(l) for l in want)
+    for gt, lst in enumerate(want):
+        b, e = ranges[gt]
+        assert vals[b:e].tolist() == lst, (gt, len(lst))
 
 
 def test_bin_sort_ellipse_cull_lists():
