@@ -14,7 +14,7 @@
 //     (depth bits << 32 | record index) into its tile's bucket at an
 //     atomically taken slot (bucket order is arbitrary at this point);
 //  4. sort each bucket by that key -- a warp per tile in registers (bitonic)
-//     for up to 128 pairs, a CTA in shared memory (radix) for up to 4096,
+//     for up to 256 pairs, a CTA in shared memory (radix) for up to 4096,
 //     chunk sorts plus merge passes beyond -- and write the record indices.
 // Positive FP32 depths order like their bit patterns, and all records of a
 // tile belong to one camera, so the key order is (depth, Gaussian index).
@@ -103,14 +103,17 @@ constexpr int kSmallRect = 8;
 // record whose kept tiles are recomputed at emission (large rectangle)
 constexpr uint32_t kMaskRecompute = 0x80000000u;
 
-// Per record: the kept tiles of a small rectangle as a bit mask (bit
-// (ty - y0) * nx + (tx - x0)), kMaskRecompute for a large one, 0 for none;
-// per tile: atomic count of the records that keep it.  Small rectangles are
-// walked by their own thread; large ones by the whole warp, one record at a
-// time, lanes over tiles.
+// Per record, what the emission needs (16 B, so that it does not re-read the
+// 48-B record): {mask, depth bits, first tile's global id, nx | tiles_x << 16}
+// with mask = the kept tiles of a small rectangle as bits (bit
+// (ty - y0) * nx + (tx - x0)), kMaskRecompute for a large rectangle (the
+// emission recomputes from the record), 0 for none.  Per tile: atomic count
+// of the records that keep it.  Small rectangles are walked by their own
+// thread; large ones by the whole warp, one record at a time, lanes over
+// tiles.
 __global__ void __launch_bounds__(256)
 bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                 int ellipse, uint32_t *__restrict__ kmask, uint32_t *__restrict__ tile_cnt) {
+                 int ellipse, uint4 *__restrict__ desc, uint32_t *__restrict__ tile_cnt) {
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
     // one record per thread, consecutive records in a warp (coalesced loads)
@@ -125,9 +128,11 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const floa
         } else {
             r = BinRec{};
         }
-        uint32_t mask = 0;
+        uint32_t mask = 0, g0 = 0, geo = 0;
         if (nt > 0 && nt <= kSmallRect) {
             const ViewDev &V = vt.v[r.v];
+            g0 = V.tile_off + r.y0 * V.tiles_x + r.x0;
+            geo = (uint32_t)(r.x1 - r.x0 + 1) | ((uint32_t)V.tiles_x << 16);
             int b = 0;
             for (int ty = r.y0; ty <= r.y1; ++ty)
                 for (int tx = r.x0; tx <= r.x1; ++tx, ++b)
@@ -151,7 +156,7 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const floa
             }
             if (lane == src) mask = kMaskRecompute;
         }
-        if (valid) kmask[it] = mask;
+        if (valid) desc[it] = make_uint4(mask, __float_as_uint(r.depth), g0, geo);
     }
 }
 
@@ -170,30 +175,29 @@ __device__ __forceinline__ unsigned long long pair_key(const BinRec &r, long lon
 // is written when the capacity was exceeded
 __global__ void __launch_bounds__(256)
 bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                int ellipse, const uint32_t *__restrict__ kmask, uint32_t *__restrict__ cursor,
+                int ellipse, const uint4 *__restrict__ desc, uint32_t *__restrict__ cursor,
                 const long long *n_sort, unsigned long long *__restrict__ keys) {
     if (*n_sort == 0) return;
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
     {
         const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const uint32_t mask = it < m ? kmask[it] : 0u;
-        BinRec r = BinRec{};
-        if (mask) r = load_bin_rec(rec, it, n);
+        const uint4 dsc = it < m ? desc[it] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t mask = dsc.x;
         if (mask && mask != kMaskRecompute) {
-            const ViewDev &V = vt.v[r.v];
-            const unsigned long long key = pair_key(r, it);
-            const int nx = r.x1 - r.x0 + 1;
-            const uint32_t g0 = V.tile_off + r.y0 * V.tiles_x + r.x0;
+            const unsigned long long key = ((unsigned long long)dsc.y << 32) | (uint32_t)it;
+            const int nx = (int)(dsc.w & 0xFFFFu), tiles_x = (int)(dsc.w >> 16);
             // all slots first (independent atomics in flight together), then the stores
             uint32_t pos[kSmallRect];
 #pragma unroll
             for (int b = 0; b < kSmallRect; ++b)
-                if (mask & (1u << b)) pos[b] = atomicAdd(&cursor[g0 + (b / nx) * V.tiles_x + b % nx], 1u);
+                if (mask & (1u << b)) pos[b] = atomicAdd(&cursor[dsc.z + (b / nx) * tiles_x + b % nx], 1u);
 #pragma unroll
             for (int b = 0; b < kSmallRect; ++b)
                 if (mask & (1u << b)) keys[pos[b]] = key;
         }
+        BinRec r = BinRec{};
+        if (mask == kMaskRecompute) r = load_bin_rec(rec, it, n);
         unsigned big = __ballot_sync(0xffffffffu, mask == kMaskRecompute);
         while (big) {
             const int src = __ffs(big) - 1;
@@ -216,7 +220,7 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
 // ---------------------------------------------------------------------------
 // segmented sort of the tile buckets
 // ---------------------------------------------------------------------------
-constexpr int kWarpSeg = 128;      // bucket sizes sorted by one warp in registers
+constexpr int kWarpSeg = 256;      // bucket sizes sorted by one warp in registers
 constexpr int kMidSeg = 1024;      // ... by a 128-thread CTA in shared memory (radix)
 constexpr int kSegMax = 4096;      // ... by a 256-thread CTA in shared memory (radix)
 constexpr int kSegThreads = 256;
@@ -291,7 +295,7 @@ __device__ __forceinline__ void warp_sort_bucket(const unsigned long long *__res
     }
 }
 
-// Warp per tile (grid-stride): writes the tile's range; buckets of up to 128
+// Warp per tile (grid-stride): writes the tile's range; buckets of up to 256
 // keys are sorted in registers (the smallest power-of-two slot count that
 // holds them); larger buckets go to the mid-size (up to 4096 keys, radix
 // sorted by a CTA) or the large list.  Nothing when the capacity was
@@ -319,8 +323,10 @@ seg_sort_small_kernel(uint32_t n_tiles, const uint32_t *__restrict__ tile_off,
             warp_sort_bucket<1>(keys, vals, off, cnt, lane);
         } else if (cnt <= 64) {
             warp_sort_bucket<2>(keys, vals, off, cnt, lane);
-        } else if (cnt <= (uint32_t)kWarpSeg) {
+        } else if (cnt <= 128) {
             warp_sort_bucket<4>(keys, vals, off, cnt, lane);
+        } else if (cnt <= (uint32_t)kWarpSeg) {
+            warp_sort_bucket<8>(keys, vals, off, cnt, lane);
         } else if (lane == 0) {
             if (cnt <= (uint32_t)kMidSeg) mid_list[atomicAdd(mid_count, 1u)] = gt;
             else big_list[atomicAdd(big_count, 1u)] = gt;
@@ -593,7 +599,8 @@ seg_sort_large_kernel(const uint32_t *__restrict__ large_list, const unsigned in
 }
 
 struct BinWs {
-    uint32_t *kmask, *tile_cnt, *tile_off, *tile_fill, *mid_list, *big_list;
+    uint4 *desc;
+    uint32_t *tile_cnt, *tile_off, *tile_fill, *mid_list, *big_list;
     unsigned long long *keys, *scratch;
     unsigned int *counts;   // [0] mid-size buckets (<= kMidSeg), [1] larger buckets
     long long *n_sort;
@@ -603,7 +610,7 @@ struct BinWs {
 BinWs carve(void *ws, long long m, long long cap, long long tiles, size_t *bytes) {
     WsCarver c(ws);
     BinWs b;
-    b.kmask = c.take<uint32_t>(m);
+    b.desc = c.take<uint4>(m);
     b.tile_cnt = c.take<uint32_t>(tiles);
     b.tile_off = c.take<uint32_t>(tiles);
     b.tile_fill = c.take<uint32_t>(tiles);
@@ -672,7 +679,7 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
 
     // 1. kept tiles per record, records per tile
     const unsigned rgrid = (unsigned)((m + 255) / 256);
-    bin_count_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.kmask, b.tile_cnt);
+    bin_count_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.desc, b.tile_cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 2. tile offsets, pair count and capacity check
     e = launch_scan(b.tile_cnt, nullptr, b.tile_off, T, (long long *)n_pairs_out, capacity, d_status, b.scan, s);
@@ -681,7 +688,7 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     // 3. keys into the tile buckets (cursors start at the bucket starts)
     e = cudaMemcpyAsync(b.tile_fill, b.tile_off, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    bin_emit_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.kmask, b.tile_fill, b.n_sort,
+    bin_emit_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.desc, b.tile_fill, b.n_sort,
                                           b.keys);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 4. sort every bucket; tile ranges
