@@ -189,14 +189,16 @@ mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         // oriented edges e0: 0->b, e1: b->c, e2: c->0 (E > 0 inside)
         const long long ax[3] = {s.x[0], s.x[b], s.x[c]}, ay[3] = {s.y[0], s.y[b], s.y[c]};
         const long long bx[3] = {s.x[b], s.x[c], s.x[0]}, by[3] = {s.y[b], s.y[c], s.y[0]};
+        // E' = E - (edge is not top-left): the pixel is covered by the edge iff
+        // E > 0, or E == 0 on a top or left edge, i.e. iff E' >= 0 -- the sign
+        // bit of E', the sign of its high word
         long long E[3], inc[3];
-        bool tl[3];
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
             const long long dx = bx[e] - ax[e], dy = by[e] - ay[e];
-            E[e] = dx * (PY - ay[e]) - dy * (PX - ax[e]);
+            const bool tl = dy < 0 || (dy == 0 && dx > 0);
+            E[e] = dx * (PY - ay[e]) - dy * (PX - ax[e]) - (tl ? 0 : 1);
             inc[e] = dx * (256 * YS);
-            tl[e] = dy < 0 || (dy == 0 && dx > 0);
         }
         const unsigned long long fkey = f;
         // depth: 1 / fma(a, U, fma(b, V, 1/z0)) at the offset from vertex 0, in pixels
@@ -205,8 +207,7 @@ mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         for (int k = 0; k < NP; ++k) {
             const int py = py0 + k * YS;
             if (py >= V.H) break;
-            const bool in = (E[0] > 0 || (E[0] == 0 && tl[0])) && (E[1] > 0 || (E[1] == 0 && tl[1])) &&
-                            (E[2] > 0 || (E[2] == 0 && tl[2]));
+            const bool in = ((int)(E[0] >> 32) | (int)(E[1] >> 32) | (int)(E[2] >> 32)) >= 0;
             if (in) {
                 const float Vv = __fmul_rn(__int2float_rn((int)((long long)py * 256 + 128 - s.y[0])), 0.00390625f);
                 const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
@@ -219,93 +220,146 @@ mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     }
 }
 
+// texture coordinates and bilinear weights of a covered pixel centre
+struct TexTap {
+    float u, w;          // perspective-correct UV
+    int x0, x1, y0, y1;  // clamped texel columns and rows
+    float w00, w10, w01, w11;
+};
+
+__device__ __forceinline__ TexTap tex_tap(const FaceSetup &s, int px, int py, float D, int tw, int th) {
+    TexTap r;
+    // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
+    // screen-space ones of the offset from vertex 0 (Cramer's rule)
+    // (snapped coordinates stay within +-2^29, so the differences fit int32)
+    const float dx = __int2float_rn(px * 256 + 128 - s.x[0]);
+    const float dy = __int2float_rn(py * 256 + 128 - s.y[0]);
+    const float e1x = __int2float_rn(s.x[1] - s.x[0]), e1y = __int2float_rn(s.y[1] - s.y[0]);
+    const float e2x = __int2float_rn(s.x[2] - s.x[0]), e2y = __int2float_rn(s.y[2] - s.y[0]);
+    const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
+    const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
+    const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;
+    // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
+    // for small faces, so uv keeps close to FP32 rounding of its value
+    r.u = s.u0 + fmaf(b1, s.du1, b2 * s.du2);
+    r.w = s.v0 + fmaf(b1, s.dv1, b2 * s.dv2);
+    const float ss = r.u * (float)tw - 0.5f, tt = r.w * (float)th - 0.5f;
+    const float xf = floorf(ss), yf = floorf(tt);
+    const float fx = ss - xf, fy = tt - yf;
+    const int ix = (int)fmaxf(fminf(xf, 1e8f), -1e8f), iy = (int)fmaxf(fminf(yf, 1e8f), -1e8f);
+    // clamp-to-edge addressing
+    r.x0 = min(max(ix, 0), tw - 1);
+    r.x1 = min(max(ix + 1, 0), tw - 1);
+    r.y0 = min(max(iy, 0), th - 1);
+    r.y1 = min(max(iy + 1, 0), th - 1);
+    r.w00 = (1.f - fx) * (1.f - fy);
+    r.w10 = fx * (1.f - fy);
+    r.w01 = (1.f - fx) * fy;
+    r.w11 = fx * fy;
+    return r;
+}
+
 template <bool F32TEX>
-__device__ __forceinline__ float texel(const void *tex, int tw, int th, int x, int y, int ch) {
-    x = min(max(x, 0), tw - 1);
-    y = min(max(y, 0), th - 1);
-    const size_t o = ((size_t)y * tw + x) * 3 + ch;
+__device__ __forceinline__ float texel_at(const void *tex, size_t o) {
     if (F32TEX) return __ldg(reinterpret_cast<const float *>(tex) + o);
     return (float)__ldg(reinterpret_cast<const unsigned char *>(tex) + o) * (1.0f / 255.0f);
 }
 
+template <bool F32TEX>
+__device__ __forceinline__ void bilinear(const void *tex, int tw, const TexTap &a, float &c0, float &c1,
+                                         float &c2) {
+    const size_t o00 = ((size_t)a.y0 * tw + a.x0) * 3, o10 = ((size_t)a.y0 * tw + a.x1) * 3;
+    const size_t o01 = ((size_t)a.y1 * tw + a.x0) * 3, o11 = ((size_t)a.y1 * tw + a.x1) * 3;
+    float cc[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        cc[ch] = a.w00 * texel_at<F32TEX>(tex, o00 + ch) + a.w10 * texel_at<F32TEX>(tex, o10 + ch) +
+                 a.w01 * texel_at<F32TEX>(tex, o01 + ch) + a.w11 * texel_at<F32TEX>(tex, o11 + ch);
+    c0 = cc[0];
+    c1 = cc[1];
+    c2 = cc[2];
+}
+
+// One CTA per screen tile; a thread resolves two pixels of one column (rows
+// y and y + TH/2), their loads issued together (visibility words, then face
+// set-ups, then texels) so that two dependent load chains are in flight.
 template <int TW, int TH, bool F32TEX>
-__global__ void __launch_bounds__(TW *TH)
+__global__ void __launch_bounds__(TW *TH / 2)
 mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
                     const int32_t *__restrict__ faces, const float *__restrict__ uvs,
                     const void *__restrict__ tex, int tw, int th, float bg0, float bg1, float bg2,
                     const unsigned long long *__restrict__ vis, int32_t *__restrict__ tri_id,
                     float *__restrict__ depth, float *__restrict__ rgb, float *__restrict__ uv_out,
                     float *__restrict__ tile_max) {
-    __shared__ float s_max[TW * TH / 32];
+    constexpr int NT = TW * TH / 2;
+    __shared__ float s_max[NT / 32];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x;
-    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
-    const bool inside = px < V.W && py < V.H;
-    float D = -INFINITY;   // neutral for the max over in-image pixels
-    if (inside) {
-        const long long npx = (long long)V.W * V.H;
-        const long long lp = (long long)py * V.W + px;
-        const long long gp = V.pix_off + lp;
-        const unsigned long long key = vis[gp];
-        int id = -1;
-        float c0 = bg0, c1 = bg1, c2 = bg2, u = 0.f, w = 0.f;
-        if (key == ~0ull) {
-            D = INFINITY;
-        } else {
-            id = (int)(unsigned)(key & 0xFFFFFFFFu);
-            D = __uint_as_float((unsigned)(key >> 32));
-            const FaceSetup s = setup[(long long)v * nf + id];
-            // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
-            // screen-space ones of the offset from vertex 0 (Cramer's rule)
-            // (snapped coordinates stay within +-2^29, so the differences fit int32)
-            const float dx = __int2float_rn(px * 256 + 128 - s.x[0]);
-            const float dy = __int2float_rn(py * 256 + 128 - s.y[0]);
-            const float e1x = __int2float_rn(s.x[1] - s.x[0]), e1y = __int2float_rn(s.y[1] - s.y[0]);
-            const float e2x = __int2float_rn(s.x[2] - s.x[0]), e2y = __int2float_rn(s.y[2] - s.y[0]);
-            const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
-            const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
-            const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;
-            // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
-            // for small faces, so uv keeps close to FP32 rounding of its value
-            u = s.u0 + fmaf(b1, s.du1, b2 * s.du2);
-            w = s.v0 + fmaf(b1, s.dv1, b2 * s.dv2);
-            const float ss = u * (float)tw - 0.5f, tt = w * (float)th - 0.5f;
-            const float x0 = floorf(ss), y0 = floorf(tt);
-            const float fx = ss - x0, fy = tt - y0;
-            const int ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f), iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
-            const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy);
-            const float w01 = (1.f - fx) * fy, w11 = fx * fy;
-            float cc[3];
+    const int px = tx * TW + (t % TW);
+    const int py[2] = {ty * TH + (t / TW), ty * TH + (t / TW) + TH / 2};
+    const long long npx = (long long)V.W * V.H;
+    bool in[2];
+    long long lp[2];
+    unsigned long long key[2];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
-                cc[ch] = w00 * texel<F32TEX>(tex, tw, th, ix, iy, ch) + w10 * texel<F32TEX>(tex, tw, th, ix + 1, iy, ch) +
-                         w01 * texel<F32TEX>(tex, tw, th, ix, iy + 1, ch) + w11 * texel<F32TEX>(tex, tw, th, ix + 1, iy + 1, ch);
-            c0 = cc[0]; c1 = cc[1]; c2 = cc[2];
-        }
-        if (tri_id) tri_id[gp] = id;
-        if (depth) depth[gp] = D;
+    for (int q = 0; q < 2; ++q) {
+        in[q] = px < V.W && py[q] < V.H;
+        lp[q] = (long long)py[q] * V.W + px;
+        key[q] = in[q] ? vis[V.pix_off + lp[q]] : ~0ull;
+    }
+    bool hit[2];
+    FaceSetup fs[2];
+    float D[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        hit[q] = key[q] != ~0ull;
+        D[q] = hit[q] ? __uint_as_float((unsigned)(key[q] >> 32)) : INFINITY;
+        if (hit[q]) fs[q] = setup[(long long)v * nf + (unsigned)(key[q] & 0xFFFFFFFFu)];
+    }
+    TexTap tap[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        if (hit[q]) tap[q] = tex_tap(fs[q], px, py[q], D[q], tw, th);
+    float c[2][3];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        c[q][0] = bg0;
+        c[q][1] = bg1;
+        c[q][2] = bg2;
+        if (hit[q]) bilinear<F32TEX>(tex, tw, tap[q], c[q][0], c[q][1], c[q][2]);
+    }
+    float m = -INFINITY;   // neutral for the max over in-image pixels
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (!in[q]) continue;
+        m = fmaxf(m, D[q]);
+        const long long gp = V.pix_off + lp[q];
+        if (tri_id) tri_id[gp] = hit[q] ? (int)(unsigned)(key[q] & 0xFFFFFFFFu) : -1;
+        if (depth) depth[gp] = D[q];
         if (rgb) {
-            float *o = rgb + 3 * V.pix_off + lp;
-            o[0] = c0; o[npx] = c1; o[2 * npx] = c2;
+            float *o = rgb + 3 * V.pix_off + lp[q];
+            o[0] = c[q][0];
+            o[npx] = c[q][1];
+            o[2 * npx] = c[q][2];
         }
         if (uv_out) {
-            float *o = uv_out + 2 * V.pix_off + lp;
-            o[0] = u; o[npx] = w;
+            float *o = uv_out + 2 * V.pix_off + lp[q];
+            o[0] = hit[q] ? tap[q].u : 0.f;
+            o[npx] = hit[q] ? tap[q].w : 0.f;
         }
     }
     // farthest mesh depth of the tile (+inf if any in-image pixel misses)
-    float m = D;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((t & 31) == 0) s_max[t >> 5] = m;
     __syncthreads();
     if (t == 0) {
         float r = s_max[0];
-        for (int k = 1; k < TW * TH / 32; ++k) r = fmaxf(r, s_max[k]);
+        for (int k = 1; k < NT / 32; ++k) r = fmaxf(r, s_max[k]);
         if (tile_max) tile_max[gt] = r;
     }
 }
@@ -424,11 +478,11 @@ extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, c
         mesh_cover_kernel<TW, TH><<<(unsigned)cgrid, 256, 0, s>>>(vt, n_faces, r.setup, r.items,       \
                                                                  r.n_clamped, r.vis);                  \
         if (f32)                                                                                        \
-            mesh_resolve_kernel<TW, TH, true><<<tgrid, TW * TH, 0, s>>>(                                \
+            mesh_resolve_kernel<TW, TH, true><<<tgrid, TW * TH / 2, 0, s>>>(                                \
                 vt, n_faces, r.setup, faces, uvs, tex, tex_w, tex_h, bg[0], bg[1], bg[2], r.vis,       \
                 tri_id, depth, rgb, uv, tile_max_depth);                                                \
         else                                                                                            \
-            mesh_resolve_kernel<TW, TH, false><<<tgrid, TW * TH, 0, s>>>(                               \
+            mesh_resolve_kernel<TW, TH, false><<<tgrid, TW * TH / 2, 0, s>>>(                               \
                 vt, n_faces, r.setup, faces, uvs, tex, tex_w, tex_h, bg[0], bg[1], bg[2], r.vis,       \
                 tri_id, depth, rgb, uv, tile_max_depth);                                                \
     } while (0)
