@@ -5,19 +5,22 @@
 // Pipeline (all cameras of a call at once):
 //   vertex pass   FP64 view transform (fixed FMA order), projection, snap to
 //                 1/256 px, 1/z;
-//   face pass     orientation, bounding box, tiles touched (count);
-//   scan + emit   one (face, tile) work item per touched tile;
-//   coverage      one warp per item: exact int64 edge functions (stepped
-//                 incrementally down each lane's column) with the top-left
-//                 rule at the tile's pixel centres; the depth is the FP32
-//                 reciprocal of the face's affine 1/z (coefficients from the
-//                 face pass), packed with the face index into a 64-bit key
-//                 and merged with atomicMin into a per-pixel visibility
-//                 word -- the minimum is (nearest FP32 depth, lowest face
-//                 index) whatever the order the items run in;
-//   resolve       one CTA per tile: perspective-correct UVs, bilinear
-//                 clamp-to-edge texel fetch, outputs, per-tile farthest mesh
-//                 depth (for the Gaussian pair cull).
+//   face pass     orientation, bounding box, the tiles it touches (atomic
+//                 per-tile face counts);
+//   scan + emit   per-tile offsets; each face's index into the bucket of
+//                 every tile it touches (atomic slots: the order within a
+//                 bucket does not matter);
+//   tile pass     one CTA per tile, a thread per two pixels of a column:
+//                 for every face of the tile's bucket, exact int64 edge
+//                 functions with the top-left rule at the pixel centres; the
+//                 depth is the FP32 reciprocal of the face's affine 1/z,
+//                 packed with the face index into a 64-bit key whose minimum
+//                 over the faces is (nearest FP32 depth, lowest face index)
+//                 whatever the bucket order; then the resolve: perspective-
+//                 correct UVs, bilinear clamp-to-edge texel fetch, outputs
+//                 and the tile's farthest mesh depth (for the Gaussian pair
+//                 cull).  No per-pixel visibility buffer and no global
+//                 atomics on pixels.
 #include <limits.h>
 
 #include "hm_host.h"
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(256)
 mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces,
                  const float *__restrict__ uvs, const int2 *__restrict__ sxy,
                  const double *__restrict__ iz, FaceSetup *__restrict__ setup,
-                 uint32_t *__restrict__ cnt) {
+                 uint32_t *__restrict__ tile_fcnt) {
     const long long m = (long long)vt.n_views * nf;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
@@ -109,7 +112,6 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
         s.u0 = fu[0]; s.v0 = fv[0];
         s.du1 = fu[1] - fu[0]; s.dv1 = fv[1] - fv[0];
         s.du2 = fu[2] - fu[0]; s.dv2 = fv[2] - fv[0];
-        uint32_t c = 0;
         if (ok) {
             const long long e1x = (long long)s.x[1] - s.x[0], e1y = (long long)s.y[1] - s.y[0];
             const long long e2x = (long long)s.x[2] - s.x[0], e2y = (long long)s.y[2] - s.y[0];
@@ -137,85 +139,40 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
                 if (x0 <= x1 && y0 <= y1) {
                     s.tx0 = (int)(x0 / vt.tile_w); s.tx1 = (int)(x1 / vt.tile_w);
                     s.ty0 = (int)(y0 / vt.tile_h); s.ty1 = (int)(y1 / vt.tile_h);
-                    c = (uint32_t)((s.tx1 - s.tx0 + 1) * (s.ty1 - s.ty0 + 1));
+                    for (int ty = s.ty0; ty <= s.ty1; ++ty)
+                        for (int tx = s.tx0; tx <= s.tx1; ++tx)
+                            atomicAdd(&tile_fcnt[V.tile_off + ty * V.tiles_x + tx], 1u);
                 }
             }
         }
         setup[it] = s;
-        cnt[it] = c;
     }
 }
 
+// each face's index into the bucket of every tile it touches; nothing when
+// the item capacity was exceeded (*n_items == 0)
 __global__ void __launch_bounds__(256)
-mesh_emit_kernel(long long m, const FaceSetup *__restrict__ setup, const uint32_t *__restrict__ cnt,
-                 const uint32_t *__restrict__ offs, long long capacity,
-                 unsigned long long *__restrict__ items) {
+mesh_emit_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup, const long long *n_items,
+                 uint32_t *__restrict__ cursor, uint32_t *__restrict__ items) {
+    if (*n_items == 0) return;
+    const long long m = (long long)vt.n_views * nf;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
-        const uint32_t c = cnt[it];
-        if (c == 0) continue;
-        long long o = offs[it];
-        if (o + c > capacity) continue;
         const FaceSetup &s = setup[it];
-        for (int ty = s.ty0; ty <= s.ty1; ++ty)
-            for (int tx = s.tx0; tx <= s.tx1; ++tx)
-                items[o++] = ((unsigned long long)it << 32) | ((unsigned)ty << 16) | (unsigned)tx;
-    }
-}
-
-template <int TW, int TH>
-__global__ void __launch_bounds__(256)
-mesh_cover_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
-                  const unsigned long long *__restrict__ items, const long long *n_items,
-                  unsigned long long *__restrict__ vis) {
-    // a lane owns one column of the tile: pixels (x, y0 + k*YS), k < NP
-    constexpr int NP = TW * TH / 32, YS = 32 / TW;
-    const long long n = *n_items;
-    const int lane = threadIdx.x & 31;
-    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long w = warp0; w < n; w += nwarps) {
-        const unsigned long long item = items[w];
-        const long long vf = (long long)(item >> 32);
-        const int tx = (int)(item & 0xFFFFu), ty = (int)((item >> 16) & 0xFFFFu);
-        const int v = (int)(vf / nf);
-        const unsigned f = (unsigned)(vf - (long long)v * nf);
-        const ViewDev &V = vt.v[v];
-        const FaceSetup s = setup[vf];
-        const int px = tx * TW + (lane % TW), py0 = ty * TH + (lane / TW);
-        if (px >= V.W) continue;
-        const int b = s.flip ? 2 : 1, c = s.flip ? 1 : 2;   // oriented order 0, b, c
-        const long long PX = (long long)px * 256 + 128, PY = (long long)py0 * 256 + 128;
-        // oriented edges e0: 0->b, e1: b->c, e2: c->0 (E > 0 inside)
-        const long long ax[3] = {s.x[0], s.x[b], s.x[c]}, ay[3] = {s.y[0], s.y[b], s.y[c]};
-        const long long bx[3] = {s.x[b], s.x[c], s.x[0]}, by[3] = {s.y[b], s.y[c], s.y[0]};
-        // E' = E - (edge is not top-left): the pixel is covered by the edge iff
-        // E > 0, or E == 0 on a top or left edge, i.e. iff E' >= 0 -- the sign
-        // bit of E', the sign of its high word
-        long long E[3], inc[3];
+        if (s.tx0 > s.tx1) continue;
+        const ViewDev &V = vt.v[(int)(it / nf)];
+        const int nx = s.tx1 - s.tx0 + 1, nt = nx * (s.ty1 - s.ty0 + 1);
+        const uint32_t g0 = V.tile_off + s.ty0 * V.tiles_x + s.tx0;
+        // slots four at a time (independent atomics in flight together), then the stores
+        for (int b0 = 0; b0 < nt; b0 += 4) {
+            uint32_t pos[4];
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const long long dx = bx[e] - ax[e], dy = by[e] - ay[e];
-            const bool tl = dy < 0 || (dy == 0 && dx > 0);
-            E[e] = dx * (PY - ay[e]) - dy * (PX - ax[e]) - (tl ? 0 : 1);
-            inc[e] = dx * (256 * YS);
-        }
-        const unsigned long long fkey = f;
-        // depth: 1 / fma(a, U, fma(b, V, 1/z0)) at the offset from vertex 0, in pixels
-        const float U = __fmul_rn(__int2float_rn((int)(PX - s.x[0])), 0.00390625f);
+            for (int q = 0; q < 4; ++q)
+                if (b0 + q < nt)
+                    pos[q] = atomicAdd(&cursor[g0 + ((b0 + q) / nx) * V.tiles_x + (b0 + q) % nx], 1u);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const int py = py0 + k * YS;
-            if (py >= V.H) break;
-            const bool in = ((int)(E[0] >> 32) | (int)(E[1] >> 32) | (int)(E[2] >> 32)) >= 0;
-            if (in) {
-                const float Vv = __fmul_rn(__int2float_rn((int)((long long)py * 256 + 128 - s.y[0])), 0.00390625f);
-                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
-                atomicMin(&vis[V.pix_off + (long long)py * V.W + px],
-                          ((unsigned long long)__float_as_uint(D) << 32) | fkey);
-            }
-#pragma unroll
-            for (int e = 0; e < 3; ++e) E[e] += inc[e];
+            for (int q = 0; q < 4; ++q)
+                if (b0 + q < nt) items[pos[q]] = (uint32_t)it;
         }
     }
 }
@@ -280,19 +237,29 @@ __device__ __forceinline__ void bilinear(const void *tex, int tw, const TexTap &
     c2 = cc[2];
 }
 
-// One CTA per screen tile; a thread resolves two pixels of one column (rows
-// y and y + TH/2), their loads issued together (visibility words, then face
-// set-ups, then texels) so that two dependent load chains are in flight.
+// what the coverage test needs of a face: snapped vertices in positive
+// orientation (0, b, c), the 1/z plane and the face index within its view
+struct CoverFace {
+    int x[3], y[3];
+    float af, bf, iz0f;
+    uint32_t f;
+};
+
+// One CTA per screen tile; a thread owns two pixels of one column (rows y
+// and y + TH/2): it finds their nearest faces among the tile's bucket, then
+// resolves both, their loads issued together (face set-ups, then texels) so
+// that two dependent load chains are in flight.
 template <int TW, int TH, bool F32TEX>
 __global__ void __launch_bounds__(TW *TH / 2)
-mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
-                    const int32_t *__restrict__ faces, const float *__restrict__ uvs,
-                    const void *__restrict__ tex, int tw, int th, float bg0, float bg1, float bg2,
-                    const unsigned long long *__restrict__ vis, int32_t *__restrict__ tri_id,
-                    float *__restrict__ depth, float *__restrict__ rgb, float *__restrict__ uv_out,
-                    float *__restrict__ tile_max) {
+mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
+                 const uint32_t *__restrict__ tile_foff, const uint32_t *__restrict__ tile_fcnt,
+                 const long long *n_items, const uint32_t *__restrict__ items,
+                 const void *__restrict__ tex, int tw, int th, float bg0, float bg1, float bg2,
+                 int32_t *__restrict__ tri_id, float *__restrict__ depth, float *__restrict__ rgb,
+                 float *__restrict__ uv_out, float *__restrict__ tile_max) {
     constexpr int NT = TW * TH / 2;
     __shared__ float s_max[NT / 32];
+    __shared__ CoverFace s_face[NT];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -304,12 +271,63 @@ mesh_resolve_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     const long long npx = (long long)V.W * V.H;
     bool in[2];
     long long lp[2];
-    unsigned long long key[2];
+    unsigned long long key[2] = {~0ull, ~0ull};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         in[q] = px < V.W && py[q] < V.H;
         lp[q] = (long long)py[q] * V.W + px;
-        key[q] = in[q] ? vis[V.pix_off + lp[q]] : ~0ull;
+    }
+    // coverage: every face of the bucket against both pixel centres.  The
+    // faces' edge and depth data are staged in shared memory NT at a time
+    // (one face per thread, loads in parallel), then every thread walks them.
+    const uint32_t fc = *n_items > 0 ? tile_fcnt[gt] : 0u, f0 = tile_foff[gt];
+    const int PX = px * 256 + 128, PY = py[0] * 256 + 128;
+    for (uint32_t r0 = 0; r0 < fc; r0 += NT) {
+        const int nb = (int)min((uint32_t)NT, fc - r0);
+        __syncthreads();                             // the previous round's faces are consumed
+        if (t < nb) {
+            const uint32_t vf = items[f0 + r0 + t];
+            const FaceSetup &g = setup[vf];
+            const int b = g.flip ? 2 : 1, c = g.flip ? 1 : 2;   // oriented order 0, b, c
+            CoverFace cf;
+            cf.x[0] = g.x[0]; cf.x[1] = g.x[b]; cf.x[2] = g.x[c];
+            cf.y[0] = g.y[0]; cf.y[1] = g.y[b]; cf.y[2] = g.y[c];
+            cf.af = g.af; cf.bf = g.bf; cf.iz0f = g.iz0f;
+            cf.f = vf - (unsigned)v * (unsigned)nf;
+            s_face[t] = cf;
+        }
+        __syncthreads();
+        for (int k = 0; k < nb; ++k) {
+            const CoverFace &s = s_face[k];
+            const int ax[3] = {s.x[0], s.x[1], s.x[2]}, ay[3] = {s.y[0], s.y[1], s.y[2]};
+            const int bx[3] = {s.x[1], s.x[2], s.x[0]}, by[3] = {s.y[1], s.y[2], s.y[0]};
+            // E' = E - (edge is not top-left): covered by the edge iff E > 0, or
+            // E == 0 on a top or left edge, i.e. iff E' >= 0 (the sign of the
+            // high word); snapped coordinates lie within +-2^29, so the
+            // differences and the pixel offsets fit int32, their products int64
+            int hi0 = 0, hi1 = 0;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const int dx = bx[e] - ax[e], dy = by[e] - ay[e];
+                const bool tl = dy < 0 || (dy == 0 && dx > 0);
+                const long long E0 = (long long)dx * (PY - ay[e]) - (long long)dy * (PX - ax[e]) - (tl ? 0 : 1);
+                const long long E1 = E0 + (long long)dx * (256 * (TH / 2));
+                hi0 |= (int)(E0 >> 32);
+                hi1 |= (int)(E1 >> 32);
+            }
+            const float U = __fmul_rn(__int2float_rn(PX - s.x[0]), 0.00390625f);
+            const unsigned long long fkey = s.f;
+            if (hi0 >= 0 && in[0]) {
+                const float Vv = __fmul_rn(__int2float_rn(PY - s.y[0]), 0.00390625f);
+                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
+                key[0] = min(key[0], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
+            }
+            if (hi1 >= 0 && in[1]) {
+                const float Vv = __fmul_rn(__int2float_rn(PY + 256 * (TH / 2) - s.y[0]), 0.00390625f);
+                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
+                key[1] = min(key[1], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
+            }
+        }
     }
     bool hit[2];
     FaceSetup fs[2];
@@ -368,24 +386,23 @@ struct RasterWs {
     int2 *sxy;
     double *iz;
     FaceSetup *setup;
-    uint32_t *cnt, *offs;
-    unsigned long long *items, *vis;
+    uint32_t *tile_fcnt, *tile_foff, *cursor, *items;
     long long *n_clamped;
     ScanWs scan;
 };
 
-RasterWs carve(void *ws, long long mv, long long mf, long long cap, long long npix, size_t *bytes) {
+RasterWs carve(void *ws, long long mv, long long mf, long long cap, long long tiles, size_t *bytes) {
     WsCarver c(ws);
     RasterWs r;
     r.sxy = c.take<int2>(mv);
     r.iz = c.take<double>(mv);
     r.setup = c.take<FaceSetup>(mf);
-    r.cnt = c.take<uint32_t>(mf);
-    r.offs = c.take<uint32_t>(mf);
-    r.items = c.take<unsigned long long>(cap);
-    r.vis = c.take<unsigned long long>(npix);
+    r.tile_fcnt = c.take<uint32_t>(tiles);
+    r.tile_foff = c.take<uint32_t>(tiles);
+    r.cursor = c.take<uint32_t>(tiles);
+    r.items = c.take<uint32_t>(cap);
     r.n_clamped = c.take<long long>(1);
-    r.scan.tile_status = c.take<unsigned long long>(scan_tiles(mf) + 1);
+    r.scan.tile_status = c.take<unsigned long long>(scan_tiles(tiles) + 1);
     r.scan.ticket = c.take<unsigned int>(1);
     *bytes = c.off + 256;
     return r;
@@ -418,7 +435,7 @@ extern "C" size_t hm_rasterize_mesh_workspace_size(const hm_camera *cams, int32_
         return 0;
     size_t bytes = 0;
     carve(nullptr, (long long)n_views * n_verts, (long long)n_views * n_faces, item_capacity,
-          vt.total_pixels, &bytes);
+          vt.total_tiles, &bytes);
     return bytes;
 }
 
@@ -442,49 +459,47 @@ extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, c
         (n_faces > 0 && (!verts || !uvs || !faces)))
         return fail(HM_ERR_INVALID_ARG, "null pointer");
     const long long mv = (long long)n_views * n_verts, mf = (long long)n_views * n_faces;
+    const long long T = vt.total_tiles;
     size_t need = 0;
-    carve(nullptr, mv, mf, item_capacity, vt.total_pixels, &need);
+    carve(nullptr, mv, mf, item_capacity, T, &need);
     if (!ws || ws_bytes < need) return fail(HM_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws_bytes, need);
     cudaStream_t s = (cudaStream_t)stream;
-    RasterWs r = carve(ws, mv, mf, item_capacity, vt.total_pixels, &need);
-    cudaError_t e;
+    RasterWs r = carve(ws, mv, mf, item_capacity, T, &need);
+    cudaError_t e = cudaMemsetAsync(r.tile_fcnt, 0, sizeof(uint32_t) * (size_t)T, s);
+    if (e != cudaSuccess) return cuda_status(e);
     if (mv > 0) {
         mesh_vertex_kernel<<<grid_for(mv, 256), 256, 0, s>>>(vt, n_verts, verts, (double)opt->near_mesh, r.sxy, r.iz);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (mf > 0) {
-        mesh_face_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_verts, n_faces, faces, uvs, r.sxy, r.iz, r.setup, r.cnt);
+        mesh_face_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_verts, n_faces, faces, uvs, r.sxy, r.iz, r.setup,
+                                                           r.tile_fcnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
-    e = launch_scan(r.cnt, nullptr, r.offs, mf, (long long *)n_items_out, item_capacity, d_status, r.scan, s);
+    // per-tile bucket offsets, the item count and the capacity check
+    e = launch_scan(r.tile_fcnt, nullptr, r.tile_foff, T, (long long *)n_items_out, item_capacity, d_status,
+                    r.scan, s);
     if (e != cudaSuccess) return cuda_status(e);
     clamp_items_kernel<<<1, 1, 0, s>>>((const long long *)n_items_out, item_capacity, r.n_clamped);
     if (mf > 0) {
-        mesh_emit_kernel<<<grid_for(mf, 256), 256, 0, s>>>(mf, r.setup, r.cnt, r.offs, item_capacity, r.items);
+        e = cudaMemcpyAsync(r.cursor, r.tile_foff, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_status(e);
+        mesh_emit_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_faces, r.setup, r.n_clamped, r.cursor, r.items);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
-    e = cudaMemsetAsync(r.vis, 0xFF, sizeof(unsigned long long) * (size_t)vt.total_pixels, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long cgrid = item_capacity > 0 ? (item_capacity + 7) / 8 : 1;
-    if (cgrid > (long long)sms * 8) cgrid = (long long)sms * 8;
     const float *bg = opt->bg;
     const bool f32 = tex_format == HM_TEX_RGBF32;
     dim3 tgrid(vt.total_tiles);
 #define HM_RASTER(TW, TH)                                                                               \
     do {                                                                                                \
-        mesh_cover_kernel<TW, TH><<<(unsigned)cgrid, 256, 0, s>>>(vt, n_faces, r.setup, r.items,       \
-                                                                 r.n_clamped, r.vis);                  \
         if (f32)                                                                                        \
-            mesh_resolve_kernel<TW, TH, true><<<tgrid, TW * TH / 2, 0, s>>>(                                \
-                vt, n_faces, r.setup, faces, uvs, tex, tex_w, tex_h, bg[0], bg[1], bg[2], r.vis,       \
-                tri_id, depth, rgb, uv, tile_max_depth);                                                \
+            mesh_tile_kernel<TW, TH, true><<<tgrid, TW * TH / 2, 0, s>>>(                               \
+                vt, n_faces, r.setup, r.tile_foff, r.tile_fcnt, r.n_clamped, r.items, tex, tex_w, tex_h,   \
+                bg[0], bg[1], bg[2], tri_id, depth, rgb, uv, tile_max_depth);                           \
         else                                                                                            \
-            mesh_resolve_kernel<TW, TH, false><<<tgrid, TW * TH / 2, 0, s>>>(                               \
-                vt, n_faces, r.setup, faces, uvs, tex, tex_w, tex_h, bg[0], bg[1], bg[2], r.vis,       \
-                tri_id, depth, rgb, uv, tile_max_depth);                                                \
+            mesh_tile_kernel<TW, TH, false><<<tgrid, TW * TH / 2, 0, s>>>(                              \
+                vt, n_faces, r.setup, r.tile_foff, r.tile_fcnt, r.n_clamped, r.items, tex, tex_w, tex_h,   \
+                bg[0], bg[1], bg[2], tri_id, depth, rgb, uv, tile_max_depth);                           \
     } while (0)
     if (opt->tile_w == 16) HM_RASTER(16, 16);
     else if (opt->tile_w == 32) HM_RASTER(32, 8);
