@@ -216,31 +216,52 @@ __device__ __forceinline__ TexTap tex_tap(const FaceSetup &s, int px, int py, fl
     return r;
 }
 
-template <bool F32TEX>
-__device__ __forceinline__ float texel_at(const void *tex, size_t o) {
-    if (F32TEX) return __ldg(reinterpret_cast<const float *>(tex) + o);
-    return (float)__ldg(reinterpret_cast<const unsigned char *>(tex) + o) * (1.0f / 255.0f);
-}
-
+// bilinear clamp-to-edge fetch: the four texels' channels are read at
+// immediate offsets from per-texel base pointers; RGB8 sums the weighted
+// bytes and scales by 1/255 once per channel
 template <bool F32TEX>
 __device__ __forceinline__ void bilinear(const void *tex, int tw, const TexTap &a, float &c0, float &c1,
                                          float &c2) {
-    const size_t o00 = ((size_t)a.y0 * tw + a.x0) * 3, o10 = ((size_t)a.y0 * tw + a.x1) * 3;
-    const size_t o01 = ((size_t)a.y1 * tw + a.x0) * 3, o11 = ((size_t)a.y1 * tw + a.x1) * 3;
+    const size_t r0 = (size_t)a.y0 * (size_t)tw * 3, r1 = (size_t)a.y1 * (size_t)tw * 3;
+    const int x0 = a.x0 * 3, x1 = a.x1 * 3;
     float cc[3];
+    if (F32TEX) {
+        const float *T = reinterpret_cast<const float *>(tex);
+        const float *p00 = T + r0 + x0, *p10 = T + r0 + x1, *p01 = T + r1 + x0, *p11 = T + r1 + x1;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-        cc[ch] = a.w00 * texel_at<F32TEX>(tex, o00 + ch) + a.w10 * texel_at<F32TEX>(tex, o10 + ch) +
-                 a.w01 * texel_at<F32TEX>(tex, o01 + ch) + a.w11 * texel_at<F32TEX>(tex, o11 + ch);
+        for (int ch = 0; ch < 3; ++ch)
+            cc[ch] = a.w00 * __ldg(p00 + ch) + a.w10 * __ldg(p10 + ch) + a.w01 * __ldg(p01 + ch) +
+                     a.w11 * __ldg(p11 + ch);
+    } else {
+        const unsigned char *T = reinterpret_cast<const unsigned char *>(tex);
+        const unsigned char *p00 = T + r0 + x0, *p10 = T + r0 + x1, *p01 = T + r1 + x0, *p11 = T + r1 + x1;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+            cc[ch] = (a.w00 * (float)__ldg(p00 + ch) + a.w10 * (float)__ldg(p10 + ch) +
+                      a.w01 * (float)__ldg(p01 + ch) + a.w11 * (float)__ldg(p11 + ch)) * (1.0f / 255.0f);
+    }
     c0 = cc[0];
     c1 = cc[1];
     c2 = cc[2];
 }
 
-// what the coverage test needs of a face: snapped vertices in positive
-// orientation (0, b, c), the 1/z plane and the face index within its view
+// What the coverage test of a tile needs of a face, prepared once per
+// (tile, face).  Edge k of the positively oriented face has the exact
+// integer function E_k(P) = dx_k (PY - ay_k) - dy_k (PX - ax_k) (1/256 px
+// units), biased by -1 on edges that are not top or left, so that a pixel
+// centre is covered by the edge iff E_k >= 0.  With P = O + (DX, DY), O the
+// tile's first pixel centre, E_k(P) = E_k(O) + (dx_k DY - dy_k DX).  When
+// every |dx|, |dy| < 2^17 (edges under 512 px), the offset term is below
+// 2^30 in magnitude for any pixel of the tile, so E_k(P) >= 0 reduces to the
+// int32 test (dx_k DY - dy_k DX) >= thr_k with thr_k = -E_k(O) clamped to
+// int32 (if |E_k(O)| >= 2^31 its sign decides alone, and the clamp keeps
+// that).  Larger faces take the exact int64 evaluation.
 struct CoverFace {
-    int x[3], y[3];
+    int dx[3], dy[3];   // edge vectors
+    int thr[3];         // small faces: int32 thresholds
+    long long e0[3];    // E_k(O), exact
+    int small;          // the int32 test applies
+    int x0, y0;         // snapped vertex 0 (depth plane origin)
     float af, bf, iz0f;
     uint32_t f;
 };
@@ -282,6 +303,7 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     // (one face per thread, loads in parallel), then every thread walks them.
     const uint32_t fc = *n_items > 0 ? tile_fcnt[gt] : 0u, f0 = tile_foff[gt];
     const int PX = px * 256 + 128, PY = py[0] * 256 + 128;
+    const int DX = (t % TW) * 256, DY = (t / TW) * 256;   // offset from the tile's first pixel centre
     for (uint32_t r0 = 0; r0 < fc; r0 += NT) {
         const int nb = (int)min((uint32_t)NT, fc - r0);
         __syncthreads();                             // the previous round's faces are consumed
@@ -289,9 +311,26 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             const uint32_t vf = items[f0 + r0 + t];
             const FaceSetup &g = setup[vf];
             const int b = g.flip ? 2 : 1, c = g.flip ? 1 : 2;   // oriented order 0, b, c
+            const int ax[3] = {g.x[0], g.x[b], g.x[c]}, ay[3] = {g.y[0], g.y[b], g.y[c]};
+            const int bx[3] = {g.x[b], g.x[c], g.x[0]}, by[3] = {g.y[b], g.y[c], g.y[0]};
+            // snapped coordinates lie within +-2^29: differences fit int32
+            const int OX = tx * TW * 256 + 128, OY = ty * TH * 256 + 128;
             CoverFace cf;
-            cf.x[0] = g.x[0]; cf.x[1] = g.x[b]; cf.x[2] = g.x[c];
-            cf.y[0] = g.y[0]; cf.y[1] = g.y[b]; cf.y[2] = g.y[c];
+            bool small = true;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const int dx = bx[e] - ax[e], dy = by[e] - ay[e];
+                const bool tl = dy < 0 || (dy == 0 && dx > 0);
+                const long long E = (long long)dx * (OY - ay[e]) - (long long)dy * (OX - ax[e]) - (tl ? 0 : 1);
+                cf.dx[e] = dx;
+                cf.dy[e] = dy;
+                cf.e0[e] = E;
+                cf.thr[e] = (int)max(-2147483647ll, min(2147483647ll, -E));
+                small = small && abs(dx) < (1 << 17) && abs(dy) < (1 << 17);
+            }
+            cf.small = small;
+            cf.x0 = g.x[0];
+            cf.y0 = g.y[0];
             cf.af = g.af; cf.bf = g.bf; cf.iz0f = g.iz0f;
             cf.f = vf - (unsigned)v * (unsigned)nf;
             s_face[t] = cf;
@@ -299,31 +338,32 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         __syncthreads();
         for (int k = 0; k < nb; ++k) {
             const CoverFace &s = s_face[k];
-            const int ax[3] = {s.x[0], s.x[1], s.x[2]}, ay[3] = {s.y[0], s.y[1], s.y[2]};
-            const int bx[3] = {s.x[1], s.x[2], s.x[0]}, by[3] = {s.y[1], s.y[2], s.y[0]};
-            // E' = E - (edge is not top-left): covered by the edge iff E > 0, or
-            // E == 0 on a top or left edge, i.e. iff E' >= 0 (the sign of the
-            // high word); snapped coordinates lie within +-2^29, so the
-            // differences and the pixel offsets fit int32, their products int64
-            int hi0 = 0, hi1 = 0;
+            bool cov0 = true, cov1 = true;
+            if (s.small) {
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const int dx = bx[e] - ax[e], dy = by[e] - ay[e];
-                const bool tl = dy < 0 || (dy == 0 && dx > 0);
-                const long long E0 = (long long)dx * (PY - ay[e]) - (long long)dy * (PX - ax[e]) - (tl ? 0 : 1);
-                const long long E1 = E0 + (long long)dx * (256 * (TH / 2));
-                hi0 |= (int)(E0 >> 32);
-                hi1 |= (int)(E1 >> 32);
+                for (int e = 0; e < 3; ++e) {
+                    const int d0 = s.dx[e] * DY - s.dy[e] * DX;
+                    cov0 = cov0 && d0 >= s.thr[e];
+                    cov1 = cov1 && d0 + s.dx[e] * (256 * (TH / 2)) >= s.thr[e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const long long E0 = s.e0[e] + (long long)s.dx[e] * DY - (long long)s.dy[e] * DX;
+                    const long long E1 = E0 + (long long)s.dx[e] * (256 * (TH / 2));
+                    cov0 = cov0 && E0 >= 0;
+                    cov1 = cov1 && E1 >= 0;
+                }
             }
-            const float U = __fmul_rn(__int2float_rn(PX - s.x[0]), 0.00390625f);
+            const float U = __fmul_rn(__int2float_rn(PX - s.x0), 0.00390625f);
             const unsigned long long fkey = s.f;
-            if (hi0 >= 0 && in[0]) {
-                const float Vv = __fmul_rn(__int2float_rn(PY - s.y[0]), 0.00390625f);
+            if (cov0 && in[0]) {
+                const float Vv = __fmul_rn(__int2float_rn(PY - s.y0), 0.00390625f);
                 const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
                 key[0] = min(key[0], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
             }
-            if (hi1 >= 0 && in[1]) {
-                const float Vv = __fmul_rn(__int2float_rn(PY + 256 * (TH / 2) - s.y[0]), 0.00390625f);
+            if (cov1 && in[1]) {
+                const float Vv = __fmul_rn(__int2float_rn(PY + 256 * (TH / 2) - s.y0), 0.00390625f);
                 const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
                 key[1] = min(key[1], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
             }
