@@ -117,6 +117,8 @@ class Renderer:
         if self.has_mesh:
             self.set_item_capacity(item_capacity if item_capacity else max(1024, 4 * self.V * self.n_faces))
         self.bwd_ws = None
+        self.overlap = True
+        self._side = None
 
     # per-pixel (and per-tile) storage: (name, elements per pixel or per tile, dtype)
     PIXEL_FIELDS = (("rgb", 3, torch.float32), ("T", 1, torch.float32), ("n_contrib", 1, torch.int32),
@@ -210,12 +212,31 @@ class Renderer:
         v = st.cpu().tolist()
         return int(v[0]), int(v[1])
 
-    def forward(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None):
-        """All four stages, asynchronously on the current stream."""
+    def _side_stream(self) -> torch.cuda.Stream:
+        if self._side is None:
+            self._side = torch.cuda.Stream(device=self.device)
+        return self._side
+
+    def forward(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None,
+                overlap: Optional[bool] = None):
+        """All four stages, asynchronously on the current stream.  With
+        ``overlap`` (default ``self.overlap``) the mesh pass runs on a side
+        stream concurrently with the projection (they are independent; the
+        binning needs both) and joins the current stream before the binning
+        -- inside a graph capture this becomes a fork and a join."""
         self.status_word.zero_()
-        if self.has_mesh:
-            self.rasterize_mesh(mesh)
-        self.project(means, scales, quats, opacity, sh)
+        if self.has_mesh and (self.overlap if overlap is None else overlap):
+            main = torch.cuda.current_stream(self.device)
+            side = self._side_stream()
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                self.rasterize_mesh(mesh)
+            self.project(means, scales, quats, opacity, sh)
+            main.wait_stream(side)
+        else:
+            if self.has_mesh:
+                self.rasterize_mesh(mesh)
+            self.project(means, scales, quats, opacity, sh)
         self.bin_sort()
         self.blend()
 
@@ -252,15 +273,32 @@ class Renderer:
 
     def backward(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT=None,
                  mesh: Optional[MeshInput] = None, tex_grad: bool = False, out=None,
-                 stages: int = 0, zero: bool = True):
+                 stages: int = 0, zero: bool = True, overlap: Optional[bool] = None):
         """Gradients of the last forward, accumulated into fresh zero tensors
         (or into ``out``, a dict from ``grad_buffers``, zeroed first unless
-        ``zero`` is False).  ``stages``: HM_BWD_* bits to run (0 = all)."""
-        d = self.device
-        if self.bwd_ws is None:
-            self.bwd_ws = torch.empty(lib.hm_blend_backward_workspace_size(self.V, self.n),
-                                      dtype=torch.uint8, device=d)
+        ``zero`` is False).  ``stages``: HM_BWD_* bits to run (0 = all).
+        With ``overlap`` (default ``self.overlap``) the texel gradients run on
+        a side stream concurrently with the blend and projection gradients
+        (they share no output) and join the current stream at the end."""
         want_tex = tex_grad and self.has_mesh
+        if (self.overlap if overlap is None else overlap) and want_tex and stages == 0:
+            g = out if out is not None else self.grad_buffers(mesh.texture.shape[:2])
+            if out is not None and zero:
+                for k, v in g.items():
+                    if k != "texture":
+                        v.zero_()
+            main = torch.cuda.current_stream(self.device)
+            side = self._side_stream()
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                if out is not None and zero:
+                    g["texture"].zero_()
+                self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
+                                    lib.HM_BWD_TEXTURE)
+            self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
+                                lib.HM_BWD_BLEND | lib.HM_BWD_PROJECT)
+            main.wait_stream(side)
+            return g
         if out is None:
             g = self.grad_buffers(mesh.texture.shape[:2] if want_tex else None)
         else:
@@ -268,9 +306,19 @@ class Renderer:
             if zero:
                 for v in g.values():
                     v.zero_()
+        self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh if want_tex else None,
+                            g, stages)
+        return g
+
+    def _backward_call(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g, stages):
+        """One hm_blend_backward call on the current stream (texel gradients
+        when ``mesh`` is given and ``g`` holds a texture buffer)."""
+        if self.bwd_ws is None:
+            self.bwd_ws = torch.empty(lib.hm_blend_backward_workspace_size(self.V, self.n),
+                                      dtype=torch.uint8, device=self.device)
         d_tex = None
         tw = th = 0
-        if want_tex:
+        if mesh is not None and self.has_mesh and "texture" in g:
             th, tw = mesh.texture.shape[:2]
             d_tex = g["texture"]
         self.opt.bwd_stages = int(stages)
@@ -282,7 +330,6 @@ class Renderer:
             dL_drgb.contiguous(), None if dL_dT is None else dL_dT.contiguous(),
             g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], d_tex, self.status_word,
             self.bwd_ws, self.bwd_ws.numel(), _stream()), "hm_blend_backward")
-        return g
 
     # -- views of the outputs -------------------------------------------------------
     def image(self, k: int, which: str = "rgb") -> torch.Tensor:

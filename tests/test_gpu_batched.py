@@ -160,3 +160,23 @@ def test_chunked_renderer_recomputes_lists_and_matches_the_batched_renderer():
     got = cr.backward(*_params(P), dI, dT, mesh=mesh, tex_grad=True)
     assert cr.status() == 0
     _grads_close(got, ref_g)
+
+
+def test_stream_overlap_gives_the_sequential_results():
+    """The mesh pass beside the projection, and the texel gradients beside
+    the blend and projection gradients, on a side stream: the same images
+    (bit-exact) and gradients (up to atomic order) as one stream."""
+    s = _room(seed=36)
+    r, P, mesh = gpu_render(s)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(6)
+    dI = torch.randn(3 * r.npix, device="cuda", generator=gen)
+    r.forward(*_params(P), mesh, overlap=False)
+    seq = {k: getattr(r, k).clone() for k in ("rgb", "T", "n_contrib", "mesh_depth", "tri_id")}
+    g_seq = r.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True, overlap=False)
+    r.forward(*_params(P), mesh, overlap=True)
+    g_ovl = r.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True, overlap=True)
+    torch.cuda.synchronize()
+    for k, v in seq.items():
+        assert torch.equal(getattr(r, k), v), k
+    _grads_close(g_ovl, g_seq)
