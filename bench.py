@@ -73,7 +73,7 @@ def _traffic(stage, views, tile):
     return nbytes if h.hexdigest()[:16] == digest else None
 
 
-KERNELS_PER_STEP = {"rasterize_mesh": 6, "project": 1, "bin_sort": 6, "blend_forward": 1,
+KERNELS_PER_STEP = {"rasterize_mesh": 6, "project": 1, "bin_sort": 8, "blend_forward": 1,
                     "texture_backward": 1, "blend_backward": 1, "project_backward": 1}
 
 

@@ -14,8 +14,9 @@
 //     (depth bits << 32 | record index) into its tile's bucket at an
 //     atomically taken slot (bucket order is arbitrary at this point);
 //  4. sort each bucket by that key -- a warp per tile in registers (bitonic)
-//     for up to 256 pairs, a CTA in shared memory (radix) for up to 4096,
-//     chunk sorts plus merge passes beyond -- and write the record indices.
+//     for up to 256 pairs, a CTA in shared memory (radix) for up to 4096, a
+//     CTA with radix passes through global memory beyond -- and write the
+//     record indices.
 // Positive FP32 depths order like their bit patterns, and all records of a
 // tile belong to one camera, so the key order is (depth, Gaussian index).
 //
@@ -40,8 +41,8 @@ __device__ __forceinline__ float edge_min(float p, float q, float r, float rr, f
 
 // A projected record as the binning needs it.
 struct BinRec {
-    float mx, my, a, b, c, ra, rc, depth;   // mean, conic, 1/conic_xx, 1/conic_yy, depth key
-    int x0, x1, y0, y1, v;                  // tile rectangle, camera
+    float mx, my, a, b, c, depth;   // mean, conic, depth key
+    int x0, x1, y0, y1, v;          // tile rectangle, camera
 };
 
 __device__ __forceinline__ BinRec load_bin_rec(const Record *rec, long long it, int n) {
@@ -53,11 +54,10 @@ __device__ __forceinline__ BinRec load_bin_rec(const Record *rec, long long it, 
     r.a = A.z * (1.f / kConicScale);
     r.b = A.w * (0.5f / kConicScale);
     r.c = B.x * (1.f / kConicScale);
-    r.ra = 1.f / r.a; r.rc = 1.f / r.c;
     r.depth = B.z;
     unpack_range(__float_as_uint(B.w), r.x0, r.x1);
     unpack_range(__float_as_uint(C.w), r.y0, r.y1);
-    r.v = (int)(it / n);
+    r.v = (int)((uint32_t)it / (uint32_t)n);   // record indices stay below 2^31
     return r;
 }
 
@@ -69,22 +69,22 @@ __device__ __forceinline__ BinRec shfl_rec(const BinRec &r, int src) {
     BinRec o;
     o.mx = __shfl_sync(0xffffffffu, r.mx, src); o.my = __shfl_sync(0xffffffffu, r.my, src);
     o.a = __shfl_sync(0xffffffffu, r.a, src); o.b = __shfl_sync(0xffffffffu, r.b, src);
-    o.c = __shfl_sync(0xffffffffu, r.c, src); o.ra = __shfl_sync(0xffffffffu, r.ra, src);
-    o.rc = __shfl_sync(0xffffffffu, r.rc, src); o.depth = __shfl_sync(0xffffffffu, r.depth, src);
+    o.c = __shfl_sync(0xffffffffu, r.c, src); o.depth = __shfl_sync(0xffffffffu, r.depth, src);
     o.x0 = __shfl_sync(0xffffffffu, r.x0, src); o.x1 = __shfl_sync(0xffffffffu, r.x1, src);
     o.y0 = __shfl_sync(0xffffffffu, r.y0, src); o.y1 = __shfl_sync(0xffffffffu, r.y1, src);
     o.v = __shfl_sync(0xffffffffu, r.v, src);
     return o;
 }
 
-// Is the pair (record, tile) kept?  Mesh cull: the tile's farthest mesh depth
+
+// Is the pair (record, tile) kept (ra, rc = 1 / conic_xx, 1 / conic_yy)?  Mesh cull: the tile's farthest mesh depth
 // must lie behind the record (Sec. 3.4 blends only D_gs < D_m).  Ellipse
 // test: the 3-sigma ellipse must reach the rectangle of the tile's in-image
 // pixel centres -- the minimum of the convex d^2 over the rectangle is 0 with
 // the mean inside, else on an edge; 9 is inflated by 0.2% so the test stays
 // a superset of the blend's FP32 per-pixel test.
 __device__ __forceinline__ bool keep_tile(const ViewTable &vt, const float *tmax, int ellipse,
-                                          const BinRec &r, int tx, int ty) {
+                                          const BinRec &r, float ra, float rc, int tx, int ty) {
     const ViewDev &V = vt.v[r.v];
     if (tmax != nullptr && !(r.depth < tmax[V.tile_off + ty * V.tiles_x + tx])) return false;
     if (!ellipse) return true;
@@ -93,9 +93,51 @@ __device__ __forceinline__ bool keep_tile(const ViewTable &vt, const float *tmax
     const float y0 = (float)(ty * vt.tile_h) + 0.5f - r.my;
     const float y1 = (float)(min((ty + 1) * vt.tile_h, V.H) - 1) + 0.5f - r.my;
     if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
-    float m = fminf(edge_min(r.a, r.b, r.c, r.rc, x0, y0, y1), edge_min(r.a, r.b, r.c, r.rc, x1, y0, y1));
-    m = fminf(m, fminf(edge_min(r.c, r.b, r.a, r.ra, y0, x0, x1), edge_min(r.c, r.b, r.a, r.ra, y1, x0, x1)));
+    float m = fminf(edge_min(r.a, r.b, r.c, rc, x0, y0, y1), edge_min(r.a, r.b, r.c, rc, x1, y0, y1));
+    m = fminf(m, fminf(edge_min(r.c, r.b, r.a, ra, y0, x0, x1), edge_min(r.c, r.b, r.a, ra, y1, x0, x1)));
     return m <= 9.0f * 1.002f;
+}
+
+// Tiles of row ty that the (0.2%-inflated) 3-sigma ellipse reaches, as the
+// column range [lo, hi] clipped to the record's rectangle (lo > hi: none).
+// The ellipse meets a tile's rectangle of pixel centres iff its slice by
+// the tile row's band of pixel-centre rows, projected on x, meets the tile's
+// column range: an exact, per-row alternative to keep_tile's per-tile
+// test.  With the conic (a, b, c), det = ac - b^2 (a compensated difference
+// of products: thin ellipses cancel), R = 9 * 1.002, the slice at dy spans
+// dx in (-b dy -+ sqrt(a R - det dy^2)) / a; its leftmost point over the
+// band is the ellipse's own leftmost point (dx = -xe, dy = b xe / c, with
+// xe = sqrt(R c / det)) when that lies in the band, else an end of the band
+// (the left boundary is convex in dy), and symmetrically on the right.
+__device__ __forceinline__ void row_span(const ViewTable &vt, const ViewDev &V, const BinRec &r, int ty,
+                                         int &lo, int &hi) {
+    constexpr float R = 9.0f * 1.002f;
+    lo = r.x0;
+    hi = r.x1;
+    const float bb = r.b * r.b;
+    const float det = __fmaf_rn(r.a, r.c, -bb) + __fmaf_rn(-r.b, r.b, bb);
+    if (!(det > 0.f)) return;                    // degenerate: the whole rectangle row
+    const float ye = sqrtf(R * r.a / det), xe = sqrtf(R * r.c / det);
+    float s0 = (float)(ty * vt.tile_h) + 0.5f - r.my;
+    float s1 = (float)(min((ty + 1) * vt.tile_h, V.H) - 1) + 0.5f - r.my;
+    s0 = fmaxf(s0, -ye);
+    s1 = fminf(s1, ye);
+    if (s0 > s1) {
+        lo = 1;
+        hi = 0;
+        return;
+    }
+    const float ra = 1.f / r.a;
+    const float sq0 = sqrtf(fmaxf(0.f, r.a * R - det * s0 * s0));
+    const float sq1 = sqrtf(fmaxf(0.f, r.a * R - det * s1 * s1));
+    const float yl = r.b * xe / r.c, yr = -yl;
+    const float xmin = (yl >= s0 && yl <= s1) ? -xe : fminf((-r.b * s0 - sq0) * ra, (-r.b * s1 - sq1) * ra);
+    const float xmax = (yr >= s0 && yr <= s1) ? xe : fmaxf((-r.b * s0 + sq0) * ra, (-r.b * s1 + sq1) * ra);
+    // tile tx spans pixel centres [tx TW + 1/2, (tx + 1) TW - 1/2] (clipped to
+    // the image at the last column of tiles)
+    const float u0 = r.mx + xmin, u1 = r.mx + xmax;
+    lo = max(lo, (int)ceilf((u0 + 0.5f) / (float)vt.tile_w) - 1);
+    hi = min(hi, (int)floorf((u1 - 0.5f) / (float)vt.tile_w));
 }
 
 // records with more tiles than this are binned by the whole warp
@@ -106,58 +148,75 @@ constexpr uint32_t kMaskRecompute = 0x80000000u;
 // Per record, what the emission needs (16 B, so that it does not re-read the
 // 48-B record): {mask, depth bits, first tile's global id, nx | tiles_x << 16}
 // with mask = the kept tiles of a small rectangle as bits (bit
-// (ty - y0) * nx + (tx - x0)), kMaskRecompute for a large rectangle (the
-// emission recomputes from the record), 0 for none.  Per tile: atomic count
-// of the records that keep it.  Small rectangles are walked by their own
-// thread; large ones by the whole warp, one record at a time, lanes over
-// tiles.
+// (ty - y0) * nx + (tx - x0)), kMaskRecompute for a large rectangle, 0 for
+// none.  Per tile: atomic count of the records that keep it.  Small
+// rectangles are walked by their own thread (the ellipse's tile columns per
+// tile row from row_span); large ones by the whole warp, one record at a
+// time, lanes over tiles.
 __global__ void __launch_bounds__(256)
 bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
                  int ellipse, uint4 *__restrict__ desc, uint32_t *__restrict__ tile_cnt) {
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
     // one record per thread, consecutive records in a warp (coalesced loads)
-    {
-        const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const bool valid = it < m;
-        BinRec r;
-        int nt = 0;
-        if (valid) {
-            r = load_bin_rec(rec, it, n);
-            nt = rec_tiles(r);
-        } else {
-            r = BinRec{};
-        }
-        uint32_t mask = 0, g0 = 0, geo = 0;
-        if (nt > 0 && nt <= kSmallRect) {
-            const ViewDev &V = vt.v[r.v];
-            g0 = V.tile_off + r.y0 * V.tiles_x + r.x0;
-            geo = (uint32_t)(r.x1 - r.x0 + 1) | ((uint32_t)V.tiles_x << 16);
-            int b = 0;
-            for (int ty = r.y0; ty <= r.y1; ++ty)
-                for (int tx = r.x0; tx <= r.x1; ++tx, ++b)
-                    if (keep_tile(vt, tmax, ellipse, r, tx, ty)) {
-                        mask |= 1u << b;
-                        atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
-                    }
-        }
-        unsigned big = __ballot_sync(0xffffffffu, nt > kSmallRect);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const BinRec q = shfl_rec(r, src);
-            const ViewDev &V = vt.v[q.v];
-            const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
-            for (int t0 = 0; t0 < ntot; t0 += 32) {
-                const int t = t0 + lane;
-                const int tx = q.x0 + t % nx, ty = q.y0 + t / nx;
-                if (t < ntot && keep_tile(vt, tmax, ellipse, q, tx, ty))
-                    atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
-            }
-            if (lane == src) mask = kMaskRecompute;
-        }
-        if (valid) desc[it] = make_uint4(mask, __float_as_uint(r.depth), g0, geo);
+    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = it < m;
+    BinRec r;
+    int nt = 0;
+    if (valid) {
+        r = load_bin_rec(rec, it, n);
+        nt = rec_tiles(r);
+    } else {
+        r = BinRec{};
     }
+    uint32_t mask = 0, g0 = 0, geo = 0;
+    if (nt > 0 && nt <= kSmallRect) {
+        const ViewDev &V = vt.v[r.v];
+        g0 = V.tile_off + r.y0 * V.tiles_x + r.x0;
+        geo = (uint32_t)(r.x1 - r.x0 + 1) | ((uint32_t)V.tiles_x << 16);
+        const int nx = r.x1 - r.x0 + 1;
+        for (int ty = r.y0; ty <= r.y1; ++ty) {
+            int lo = r.x0, hi = r.x1;
+            if (ellipse) row_span(vt, V, r, ty, lo, hi);
+            for (int tx = lo; tx <= hi; ++tx)
+                if (tmax == nullptr || r.depth < tmax[V.tile_off + ty * V.tiles_x + tx])
+                    mask |= 1u << ((ty - r.y0) * nx + (tx - r.x0));
+        }
+    }
+    // per-tile counts, one atomic per distinct tile and round across the warp
+    // (consecutive records often share tiles; hot tiles take thousands)
+    {
+        const int nx = (int)(geo & 0xFFFFu), tiles_x = (int)(geo >> 16);
+        uint32_t bits = mask;
+        while (__any_sync(0xffffffffu, bits != 0)) {
+            uint32_t gt = 0xFFFFFFFFu;
+            if (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                gt = g0 + (b / nx) * tiles_x + b % nx;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, gt);
+            if (gt != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&tile_cnt[gt], (unsigned)__popc(peers));
+        }
+    }
+    // large rectangles: the whole warp, one record at a time, lanes over tiles
+    unsigned big = __ballot_sync(0xffffffffu, nt > kSmallRect);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const BinRec q = shfl_rec(r, src);
+        const float ra = 1.f / q.a, rc = 1.f / q.c;
+        const ViewDev &V = vt.v[q.v];
+        const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
+        for (int t0 = 0; t0 < ntot; t0 += 32) {
+            const int t = t0 + lane;
+            const int tx = q.x0 + t % nx, ty = q.y0 + t / nx;
+            if (t < ntot && keep_tile(vt, tmax, ellipse, q, ra, rc, tx, ty))
+                atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
+        }
+        if (lane == src) mask = kMaskRecompute;
+    }
+    if (valid) desc[it] = make_uint4(mask, __float_as_uint(r.depth), g0, geo);
 }
 
 // pairs to sort: all of them, or none when the capacity was exceeded
@@ -166,13 +225,9 @@ __global__ void clamp_count_kernel(const long long *total, long long capacity, l
     *n_out = t <= capacity ? t : 0;
 }
 
-__device__ __forceinline__ unsigned long long pair_key(const BinRec &r, long long it) {
-    return ((unsigned long long)__float_as_uint(r.depth) << 32) | (unsigned long long)(uint32_t)it;
-}
-
-// every kept (record, tile): its key into the tile's bucket, at a slot
-// taken from the tile's cursor (initialised to the bucket's start); nothing
-// is written when the capacity was exceeded
+// every kept (record, tile) of a small rectangle: its key into the tile's
+// bucket, at a slot taken from the tile's cursor (initialised to the
+// bucket's start); nothing is written when the capacity was exceeded
 __global__ void __launch_bounds__(256)
 bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
                 int ellipse, const uint4 *__restrict__ desc, uint32_t *__restrict__ cursor,
@@ -180,39 +235,58 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
     if (*n_sort == 0) return;
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
-    {
-        const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        const uint4 dsc = it < m ? desc[it] : make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t mask = dsc.x;
-        if (mask && mask != kMaskRecompute) {
-            const unsigned long long key = ((unsigned long long)dsc.y << 32) | (uint32_t)it;
-            const int nx = (int)(dsc.w & 0xFFFFu), tiles_x = (int)(dsc.w >> 16);
-            // all slots first (independent atomics in flight together), then the stores
-            uint32_t pos[kSmallRect];
+    const uint32_t lt = lanemask_lt();
+    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 dsc = it < m ? desc[it] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t mask = dsc.x;
+    const unsigned long long key = ((unsigned long long)dsc.y << 32) | (uint32_t)it;
+    const int nx = (int)(dsc.w & 0xFFFFu), tiles_x = (int)(dsc.w >> 16);
+    // round r offers each lane's r-th kept tile; the lanes that offer the
+    // same tile share one atomic and a block of slots.  Rounds go in groups
+    // of kRounds whose atomics are all issued before any result is used, so
+    // their latencies overlap.
+    constexpr int kRounds = 8;
+    uint32_t bits = mask != kMaskRecompute ? mask : 0u;
+    while (__any_sync(0xffffffffu, bits != 0)) {
+        uint32_t gts[kRounds], base[kRounds];
+        unsigned peers[kRounds];
 #pragma unroll
-            for (int b = 0; b < kSmallRect; ++b)
-                if (mask & (1u << b)) pos[b] = atomicAdd(&cursor[dsc.z + (b / nx) * tiles_x + b % nx], 1u);
-#pragma unroll
-            for (int b = 0; b < kSmallRect; ++b)
-                if (mask & (1u << b)) keys[pos[b]] = key;
-        }
-        BinRec r = BinRec{};
-        if (mask == kMaskRecompute) r = load_bin_rec(rec, it, n);
-        unsigned big = __ballot_sync(0xffffffffu, mask == kMaskRecompute);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const BinRec q = shfl_rec(r, src);
-            const long long qit = __shfl_sync(0xffffffffu, it, src);
-            const unsigned long long key = pair_key(q, qit);
-            const ViewDev &V = vt.v[q.v];
-            const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
-            for (int t0 = 0; t0 < ntot; t0 += 32) {
-                const int t = t0 + lane;
-                const int tx = q.x0 + t % nx, ty = q.y0 + t / nx;
-                if (t < ntot && keep_tile(vt, tmax, ellipse, q, tx, ty))
-                    keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] = key;
+        for (int r = 0; r < kRounds; ++r) {
+            uint32_t gt = 0xFFFFFFFFu;
+            if (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                gt = dsc.z + (b / nx) * tiles_x + b % nx;
             }
+            gts[r] = gt;
+            peers[r] = __match_any_sync(0xffffffffu, gt);
+            base[r] = 0;
+            if (gt != 0xFFFFFFFFu && lane == __ffs(peers[r]) - 1)
+                base[r] = atomicAdd(&cursor[gt], (unsigned)__popc(peers[r]));
+        }
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const uint32_t b0 = __shfl_sync(0xffffffffu, base[r], __ffs(peers[r]) - 1);
+            if (gts[r] != 0xFFFFFFFFu) keys[b0 + __popc(peers[r] & lt)] = key;
+        }
+    }
+    // large rectangles: the whole warp, one record at a time, lanes over tiles
+    BinRec r = BinRec{};
+    if (mask == kMaskRecompute) r = load_bin_rec(rec, it, n);
+    unsigned big = __ballot_sync(0xffffffffu, mask == kMaskRecompute);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const BinRec q = shfl_rec(r, src);
+        const unsigned long long qkey = __shfl_sync(0xffffffffu, key, src);
+        const float ra = 1.f / q.a, rc = 1.f / q.c;
+        const ViewDev &V = vt.v[q.v];
+        const int qnx = q.x1 - q.x0 + 1, ntot = qnx * (q.y1 - q.y0 + 1);
+        for (int t0 = 0; t0 < ntot; t0 += 32) {
+            const int t = t0 + lane;
+            const int tx = q.x0 + t % qnx, ty = q.y0 + t / qnx;
+            if (t < ntot && keep_tile(vt, tmax, ellipse, q, ra, rc, tx, ty))
+                keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] = qkey;
         }
     }
 }
@@ -223,7 +297,6 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
 constexpr int kWarpSeg = 256;      // bucket sizes sorted by one warp in registers
 constexpr int kMidSeg = 1024;      // ... by a 128-thread CTA in shared memory (radix)
 constexpr int kSegMax = 4096;      // ... by a 256-thread CTA in shared memory (radix)
-constexpr int kSegThreads = 256;
 
 // compare-exchange of a (low, high) element pair for an ascending (asc) or
 // descending bitonic stage: afterwards lo holds the min if asc, else the max
@@ -510,91 +583,189 @@ cudaError_t launch_radix_buckets(const uint32_t *list, const unsigned int *count
     return cudaGetLastError();
 }
 
-// bitonic sort of s[0, P) (P a power of two <= kSegMax) by the CTA
-__device__ void block_bitonic(unsigned long long *s, int P) {
-    const int t = threadIdx.x;
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = t; i < P / 2; i += kSegThreads) {
-                const int e = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-                unsigned long long a = s[e], b = s[e | j];
-                cmp_swap(a, b, (e & k) == 0);
-                s[e] = a;
-                s[e | j] = b;
-            }
-            __syncthreads();
+// ---- buckets above kSegMax keys: one CTA, LSD radix passes through global
+// memory in chunks of kSegMax.  The depth keys are split from the record
+// indices into two uint32 arrays (ping-pong between the bucket's range of
+// `scratch` and of the key array itself).  One read counts every pass's
+// digits; a pass then walks the chunks in order, ranks each chunk in shared
+// memory exactly as radix_pass does (stable), and scatters it to
+// digit start + count of the digit in earlier chunks + rank, which keeps the
+// pass stable across chunks.  Runs of equal depth are then ordered by
+// record index as in the in-shared-memory sort.
+template <int THREADS, int CAP>
+struct HugeSmem {
+    RadixSmem<THREADS, CAP> r;
+    uint32_t hist[4][256];
+    uint32_t base[256];
+    uint32_t run[256];
+};
+
+template <int THREADS, int CAP>
+__device__ void huge_chunk_pass(HugeSmem<THREADS, CAP> &H, const uint32_t *ks, const uint32_t *vs,
+                                uint32_t *kd, uint32_t *vd, int n0, int n, int shift) {
+    constexpr int kWarps = THREADS / 32, kItems = CAP / THREADS;
+    RadixSmem<THREADS, CAP> &S = H.r;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (int i = t; i < n; i += THREADS) {
+        S.k[0][i] = ks[n0 + i];
+        S.v[0][i] = vs[n0 + i];
+    }
+    for (int i = t; i < kWarps * 257; i += THREADS) (&S.whist[0][0])[i] = 0;
+    __syncthreads();
+    const int per = (n + THREADS - 1) / THREADS;
+    const int C = 32 * per;
+    uint32_t key[kItems], val[kItems], rank[kItems];
+    int dig[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        if (j >= per) break;
+        const int e = w * C + j * 32 + lane;
+        const bool valid = e < n;
+        key[j] = valid ? S.k[0][e] : 0u;
+        val[j] = valid ? S.v[0][e] : 0u;
+        const int d = valid ? (int)((key[j] >> shift) & 255u) : 256;
+        dig[j] = d;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = S.whist[w][d];
+        __syncwarp();
+        if ((peers & lt) == 0) S.whist[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[j] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit: the warps' offsets within the chunk's digit, chunk total
+    for (int d = t; d < 256; d += THREADS) {
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t c = S.whist[ww][d];
+            S.whist[ww][d] = cnt;
+            cnt += c;
+        }
+        S.dstart[d] = cnt;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        if (j >= per) break;
+        const int d = dig[j];
+        if (d < 256) {
+            const uint32_t pos = H.base[d] + H.run[d] + S.whist[w][d] + rank[j];
+            kd[pos] = key[j];
+            vd[pos] = val[j];
         }
     }
+    __syncthreads();
+    for (int d = t; d < 256; d += THREADS) H.run[d] += S.dstart[d];
+    __syncthreads();
 }
 
-// number of elements of a[0, na) that precede the merge-path diagonal d of
-// the merge of a and b (stable: on equal keys a first; keys here are unique)
-__device__ __forceinline__ long long merge_split(const unsigned long long *a, long long na,
-                                                 const unsigned long long *b, long long nb, long long d) {
-    long long lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        if (a[mid] <= b[d - 1 - mid]) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// CTA per bucket above kSegMax keys (grid-stride over the list of buckets
-// above kMidSeg, skipping those the radix CTA takes): bitonic sorts of
-// kSegMax chunks in shared memory, then merge passes doubling the run
-// length, ping-ponging between the bucket and the same range of `scratch`;
-// the record indices of the final run are written to vals.
-__global__ void __launch_bounds__(kSegThreads)
-seg_sort_large_kernel(const uint32_t *__restrict__ large_list, const unsigned int *large_count,
-                      const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ tile_cnt,
-                      unsigned long long *__restrict__ keys, unsigned long long *__restrict__ scratch,
-                      uint32_t *__restrict__ vals) {
-    __shared__ unsigned long long s[kSegMax];
+template <int THREADS, int CAP>
+__global__ void __launch_bounds__(THREADS)
+seg_sort_huge_kernel(const uint32_t *__restrict__ list, const unsigned int *list_count,
+                     const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ tile_cnt,
+                     unsigned long long *__restrict__ keys, unsigned long long *__restrict__ scratch,
+                     uint32_t *__restrict__ vals) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HugeSmem<THREADS, CAP> &H = *reinterpret_cast<HugeSmem<THREADS, CAP> *>(smem_raw);
     const int t = threadIdx.x;
-    const unsigned int nl = *large_count;
+    const unsigned int nl = *list_count;
     for (unsigned int li = blockIdx.x; li < nl; li += gridDim.x) {
-        const uint32_t gt = large_list[li];
-        const long long off = tile_off[gt], n = tile_cnt[gt];
-        if (n <= kSegMax) continue;                  // sorted by the radix CTA
-        unsigned long long *src = keys + off, *dst = scratch + off;
-        for (long long c0 = 0; c0 < n; c0 += kSegMax) {
-            const int cn = (int)min((long long)kSegMax, n - c0);
-            int P = 1;
-            while (P < cn) P <<= 1;
-            for (int i = t; i < P; i += kSegThreads) s[i] = i < cn ? src[c0 + i] : ~0ull;
-            __syncthreads();
-            block_bitonic(s, P);
-            if (n <= kSegMax) {
-                for (int i = t; i < cn; i += kSegThreads) vals[off + i] = (uint32_t)s[i];
-            } else {
-                for (int i = t; i < cn; i += kSegThreads) src[c0 + i] = s[i];
-            }
-            __syncthreads();
+        const uint32_t gt = list[li];
+        const long long off = tile_off[gt];
+        const int n = (int)tile_cnt[gt];
+        if (n <= CAP) continue;                      // sorted in shared memory by the radix CTA
+        // A = (depth keys, record indices) split into the scratch range,
+        // B = the same layout over the key range
+        uint32_t *kA = reinterpret_cast<uint32_t *>(scratch + off), *vA = kA + n;
+        uint32_t *kB = reinterpret_cast<uint32_t *>(keys + off), *vB = kB + n;
+        for (int i = t; i < 4 * 256; i += THREADS) (&H.hist[0][0])[i] = 0;
+        if (t == 0) {
+            H.r.kand = 0xFFFFFFFFu;
+            H.r.kor = 0u;
         }
-        if (n <= kSegMax) continue;
-        // merge passes: runs of length L in src -> runs of 2L in dst
-        for (long long L = kSegMax; L < n; L <<= 1) {
-            const bool last = 2 * L >= n;
-            for (long long a0 = 0; a0 < n; a0 += 2 * L) {
-                const long long na = min(L, n - a0), nb = min(L, max(0ll, n - a0 - L));
-                const unsigned long long *A = src + a0, *B = src + a0 + na;
-                const long long tot = na + nb;
-                const long long per = (tot + kSegThreads - 1) / kSegThreads;
-                const long long d0 = min(tot, per * t), d1 = min(tot, per * (t + 1));
-                long long ia = merge_split(A, na, B, nb, d0), ib = d0 - ia;
-                for (long long d = d0; d < d1; ++d) {
-                    const bool fa = ib >= nb || (ia < na && A[ia] <= B[ib]);
-                    const unsigned long long v = fa ? A[ia++] : B[ib++];
-                    if (last) vals[off + a0 + d] = (uint32_t)v;
-                    else dst[a0 + d] = v;
+        __syncthreads();
+        uint32_t ka = 0xFFFFFFFFu, ko = 0u;
+        const int lane = t & 31;
+        for (int i0 = 0; i0 < n; i0 += THREADS) {
+            const int i = i0 + t;
+            const bool valid = i < n;
+            uint32_t k = 0;
+            if (valid) {
+                const unsigned long long kv = keys[off + i];
+                k = (uint32_t)(kv >> 32);
+                kA[i] = k;
+                vA[i] = (uint32_t)kv;
+                ka &= k;
+                ko |= k;
+            }
+            // digit counts: one shared atomic per distinct digit of the warp
+            // (depth digits are skewed: many keys share the high bytes)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const uint32_t d = valid ? (k >> (8 * p)) & 255u : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                if (valid && lane == __ffs(peers) - 1) atomicAdd(&H.hist[p][d], (unsigned)__popc(peers));
+            }
+        }
+        atomicAnd(&H.r.kand, ka);
+        atomicOr(&H.r.kor, ko);
+        __syncthreads();
+        const uint32_t differ = H.r.kand ^ H.r.kor;
+        bool inA = true;
+        for (int pass = 0; pass < 4; ++pass) {
+            if (((differ >> (8 * pass)) & 255u) == 0) continue;   // one digit value: identity pass
+            // digit starts of this pass (exclusive scan of the bucket's histogram)
+            if (t < 32) {
+                uint32_t c[8], sum = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    c[q] = H.hist[pass][t * 8 + q];
+                    sum += c[q];
+                }
+                uint32_t incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (t >= o) incl += y;
+                }
+                uint32_t runv = incl - sum;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    H.base[t * 8 + q] = runv;
+                    H.run[t * 8 + q] = 0;
+                    runv += c[q];
                 }
             }
             __syncthreads();
-            unsigned long long *tmp = src;
-            src = dst;
-            dst = tmp;
+            const uint32_t *ks = inA ? kA : kB, *vs = inA ? vA : vB;
+            uint32_t *kd = inA ? kB : kA, *vd = inA ? vB : vA;
+            for (int c0 = 0; c0 < n; c0 += CAP)
+                huge_chunk_pass<THREADS, CAP>(H, ks, vs, kd, vd, c0, min(CAP, n - c0), 8 * pass);
+            inA = !inA;
         }
+        __syncthreads();
+        uint32_t *kf = inA ? kA : kB, *vf = inA ? vA : vB;
+        // runs of equal depth: order by record index (a thread per run start)
+        for (int i = t; i < n; i += THREADS) {
+            const uint32_t k = kf[i];
+            if (i > 0 && kf[i - 1] == k) continue;
+            int e = i + 1;
+            while (e < n && kf[e] == k) ++e;
+            for (int a = i + 1; a < e; ++a) {
+                const uint32_t x = vf[a];
+                int b = a - 1;
+                while (b >= i && vf[b] > x) {
+                    vf[b + 1] = vf[b];
+                    --b;
+                }
+                vf[b + 1] = x;
+            }
+        }
+        __syncthreads();
+        for (int i = t; i < n; i += THREADS) vals[off + i] = vf[i];
+        __syncthreads();
     }
 }
 
@@ -704,7 +875,17 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     e = launch_radix_buckets<256, kSegMax>(b.big_list, b.counts + 1, b.tile_off, b.tile_cnt, b.keys, pair_vals,
                                           148 * 2, s);
     if (e != cudaSuccess) return cuda_status(e);
-    seg_sort_large_kernel<<<148 * 2, kSegThreads, 0, s>>>(b.big_list, b.counts + 1, b.tile_off, b.tile_cnt,
-                                                          b.keys, b.scratch, pair_vals);
+    {
+        static bool huge_attr = false;
+        const int smem = (int)sizeof(HugeSmem<256, kSegMax>);
+        if (!huge_attr) {
+            e = cudaFuncSetAttribute(seg_sort_huge_kernel<256, kSegMax>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            huge_attr = true;
+        }
+        seg_sort_huge_kernel<256, kSegMax><<<148 * 2, 256, smem, s>>>(b.big_list, b.counts + 1, b.tile_off,
+                                                                        b.tile_cnt, b.keys, b.scratch, pair_vals);
+    }
     return cuda_status(cudaGetLastError());
 }
