@@ -117,7 +117,10 @@ class Renderer:
         if self.has_mesh:
             self.set_item_capacity(item_capacity if item_capacity else max(1024, 4 * self.V * self.n_faces))
         self.bwd_ws = None
-        self.overlap = True
+        # side-stream overlap pays inside a CUDA graph (fork and join are
+        # graph edges); launched eagerly the stream synchronisation costs more
+        # than it hides, so it is off by default and on in GraphStep
+        self.overlap = False
         self._side = None
 
     # per-pixel (and per-tile) storage: (name, elements per pixel or per tile, dtype)
@@ -406,10 +409,10 @@ class GraphStep:
 
     def _body(self):
         r = self.r
-        r.forward(*self.params, self.mesh)
+        r.forward(*self.params, self.mesh, overlap=True)
         if self.dI is not None:
             r.backward(*self.params, self.dI, self.dT, mesh=self.mesh, tex_grad=self.tex_grad,
-                       out=self.grads, zero=True)
+                       out=self.grads, zero=True, overlap=True)
 
     def capture(self):
         r = self.r
