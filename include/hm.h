@@ -220,6 +220,9 @@ hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, co
  *  Inputs: the forward's parameters, records, sorted pairs and ranges, mesh
  *  outputs (depth, rgb, uv; NULL for no mesh), out_T and last_idx, and
  *  dL_drgb (planar, like out_rgb) and dL_dT (per pixel, may be NULL).
+ *  dL_dmesh (planar, may be NULL): the gradient of a loss on the mesh colour
+ *  I_m itself (such as the texture loss of hm_hybrid_loss), added to the
+ *  T * dL/dI_h the texels receive through the composite.
  *  Outputs, ACCUMULATED into caller-zeroed buffers: d_means [n][3],
  *  d_scales [n][3], d_quats [n][4], d_opacity [n], d_sh [n][K][3] float32
  *  (also for F16 SH storage), d_tex [tex_h][tex_w][3] float32 (may be NULL).
@@ -234,9 +237,9 @@ hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, c
                             const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
                             int32_t tex_h, const hm_options *opt, const float *out_T,
                             const uint32_t *last_idx, const float *dL_drgb, const float *dL_dT,
-                            float *d_means, float *d_scales, float *d_quats, float *d_opacity,
-                            float *d_sh, float *d_tex, int32_t *d_status, void *ws, size_t ws_bytes,
-                            void *stream);
+                            const float *dL_dmesh, float *d_means, float *d_scales, float *d_quats,
+                            float *d_opacity, float *d_sh, float *d_tex, int32_t *d_status, void *ws,
+                            size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* hm_blend_backward_noalloc -- hm_blend_backward for callers that cannot
@@ -272,6 +275,36 @@ hm_status hm_blend_backward_noalloc(const hm_camera *cams, int32_t n_views, int3
 
 /* Number of tiles of all cameras for the tile shape in `opt`. */
 int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options *opt);
+
+/* ------------------------------------------------------------------------ */
+/* hm_hybrid_loss -- the joint-optimisation loss of the hybrid representation
+ * and its gradients (Eq. 3 and Sec. 3.4):
+ *   L   = (1 - lambda_ssim) L1(I, I_h) + lambda_ssim (1 - SSIM(I, I_h)) + lambda_t L_t
+ *   L_t = M_T * ||I~ - I~_m||^2,  M_T = 1 / (1 + exp(-k (T - 0.5)))
+ * where I~, I~_m are the target and the mesh colour on pixels with a
+ * triangle (mesh_depth finite) and 0 elsewhere.  Every term is a mean over
+ * all pixel-channel elements of all cameras; SSIM uses an 11 x 11 Gaussian
+ * window (sigma 1.5, zero outside the image), C1 = 0.01^2, C2 = 0.03^2;
+ * M_T is a mask (no gradient to T).
+ *  out_rgb (I_h), target (I): planar per camera like hm_blend_forward's
+ *  output.  mesh_rgb, out_T, mesh_depth, dL_dmesh: all NULL (no texture
+ *  loss) or all given.
+ *  Outputs: loss_out (device double[4]: L1, mean SSIM, L_t, L), dL_drgb
+ *  (dL/dI_h, planar, written), dL_dmesh (lambda_t dL_t/dI_m, planar,
+ *  written; pass it to hm_blend_backward).
+ */
+typedef struct hm_loss_params {
+    float lambda_ssim;       /* weight of D-SSIM in the photometric loss (0.2) */
+    float lambda_t;          /* weight of the texture loss (0.1; 0 in the warm-up) */
+    float k;                 /* slope of the transmittance mask (20) */
+} hm_loss_params;
+
+void hm_default_loss_params(hm_loss_params *p);
+size_t hm_hybrid_loss_workspace_size(const hm_camera *cams, int32_t n_views);
+hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *out_rgb,
+                         const float *target, const float *mesh_rgb, const float *out_T,
+                         const float *mesh_depth, const hm_loss_params *p, double *loss_out,
+                         float *dL_drgb, float *dL_dmesh, void *ws, size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

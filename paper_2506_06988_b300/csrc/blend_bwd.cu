@@ -282,8 +282,8 @@ constexpr int kTexCap = 1024;
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH)
 texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const float *__restrict__ uv,
-                   const float *__restrict__ out_T, const float *__restrict__ dL_drgb, int tw, int th,
-                   float *__restrict__ d_tex) {
+                   const float *__restrict__ out_T, const float *__restrict__ dL_drgb,
+                   const float *__restrict__ dL_dmesh, int tw, int th, float *__restrict__ d_tex) {
     constexpr int NT = TW * TH;
     __shared__ int s_acc[kTexCap * 3];
     __shared__ int s_box[4];
@@ -305,6 +305,10 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         const float T = out_T[gp];
         const float *g = dL_drgb + 3 * V.pix_off + lp;
         g0 = T * g[0]; g1 = T * g[npx]; g2 = T * g[2 * npx];
+        if (dL_dmesh) {   // a loss on the mesh colour itself (no T factor)
+            const float *gm = dL_dmesh + 3 * V.pix_off + lp;
+            g0 += gm[0]; g1 += gm[npx]; g2 += gm[2 * npx];
+        }
         const float *u = uv + 2 * V.pix_off + lp;
         const float ss = u[0] * (float)tw - 0.5f, tt = u[npx] * (float)th - 0.5f;
         const float x0 = floorf(ss), y0 = floorf(tt);
@@ -635,9 +639,10 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
                                        const float *mesh_uv, int32_t tex_w, int32_t tex_h,
                                        const hm_options *opt, const float *out_T,
                                        const uint32_t *last_idx, const float *dL_drgb,
-                                       const float *dL_dT, float *d_means, float *d_scales,
-                                       float *d_quats, float *d_opacity, float *d_sh, float *d_tex,
-                                       int32_t *d_status, void *ws, size_t ws_bytes, void *stream) {
+                                       const float *dL_dT, const float *dL_dmesh, float *d_means,
+                                       float *d_scales, float *d_quats, float *d_opacity, float *d_sh,
+                                       float *d_tex, int32_t *d_status, void *ws, size_t ws_bytes,
+                                       void *stream) {
     ViewTable vt;
     if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
@@ -663,7 +668,8 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (d_tex && (stages & HM_BWD_TEXTURE)) {
         dim3 tg(vt.total_tiles);
 #define HM_TBWD(TW, TH) \
-    texture_bwd_kernel<TW, TH><<<tg, TW * TH, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, tex_w, tex_h, d_tex)
+    texture_bwd_kernel<TW, TH><<<tg, TW * TH, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, dL_dmesh, tex_w, tex_h, \
+                                                  d_tex)
         if (opt->tile_w == 16) HM_TBWD(16, 16);
         else if (opt->tile_w == 32) HM_TBWD(32, 8);
         else HM_TBWD(8, 8);
@@ -752,7 +758,7 @@ extern "C" hm_status hm_blend_backward_noalloc(
     if (st != HM_OK) return st;
     return hm_blend_backward(cams, n_views, n, means, scales, quats, opacity, sh, sh_degree,
                              sh_format, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb,
-                             mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means,
-                             d_scales, d_quats, d_opacity, d_sh, d_tex, d_status, ws,
+                             mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, nullptr,
+                             d_means, d_scales, d_quats, d_opacity, d_sh, d_tex, d_status, ws,
                              HM_BWD_NOALLOC_BYTES, stream);
 }

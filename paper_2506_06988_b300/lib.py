@@ -40,6 +40,7 @@ EXPORTS = [
     "hm_bin_sort_workspace_size", "hm_bin_sort",
     "hm_blend_forward",
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
+    "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss",
 ]
 
 
@@ -54,6 +55,10 @@ class HmOptions(ctypes.Structure):
                 ("bg", c_float * 3), ("bwd_stages", c_int32), ("ellipse_cull", c_int32)]
 
 
+class HmLossParams(ctypes.Structure):
+    _fields_ = [("lambda_ssim", c_float), ("lambda_t", c_float), ("k", c_float)]
+
+
 class HmError(RuntimeError):
     pass
 
@@ -61,6 +66,7 @@ class HmError(RuntimeError):
 _lib = None
 _CAM_P = POINTER(HmCamera)
 _OPT_P = POINTER(HmOptions)
+_LOSS_P = POINTER(HmLossParams)
 
 _SIGS = {
     "hm_default_options": (None, [_OPT_P]),
@@ -86,7 +92,11 @@ _SIGS = {
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                     _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                    c_void_p, c_size_t, c_void_p]),
+                                    c_void_p, c_void_p, c_size_t, c_void_p]),
+    "hm_default_loss_params": (None, [_LOSS_P]),
+    "hm_hybrid_loss_workspace_size": (c_size_t, [_CAM_P, c_int32]),
+    "hm_hybrid_loss": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 _LOSS_P, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_blend_backward_noalloc": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
@@ -206,15 +216,15 @@ def hm_blend_backward_workspace_size(n_views, n) -> int:
 def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format, records,
                       pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w, tex_h, opt,
                       out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats, d_opacity, d_sh,
-                      d_tex, d_status, ws, ws_bytes, stream):
+                      d_tex, d_status, ws, ws_bytes, stream, dL_dmesh=None):
     return load().hm_blend_backward(cams, len(cams), n, _ptr(means), _ptr(scales), _ptr(quats),
                                     _ptr(opacity), _ptr(sh), sh_degree, sh_format, _ptr(records),
                                     _ptr(pair_vals), _ptr(tile_ranges), _ptr(mesh_depth),
                                     _ptr(mesh_rgb), _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
                                     _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
-                                    _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_opacity),
-                                    _ptr(d_sh), _ptr(d_tex), _ptr(d_status), _ptr(ws), ws_bytes,
-                                    stream)
+                                    _ptr(dL_dmesh), _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
+                                    _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex), _ptr(d_status), _ptr(ws),
+                                    ws_bytes, stream)
 
 
 def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format,
@@ -232,3 +242,26 @@ def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_deg
                                             _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
                                             _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex),
                                             _ptr(d_status), stream)
+
+
+def loss_params(lambda_ssim=None, lambda_t=None, k=None) -> HmLossParams:
+    p = HmLossParams()
+    load().hm_default_loss_params(ctypes.byref(p))
+    if lambda_ssim is not None:
+        p.lambda_ssim = float(lambda_ssim)
+    if lambda_t is not None:
+        p.lambda_t = float(lambda_t)
+    if k is not None:
+        p.k = float(k)
+    return p
+
+
+def hm_hybrid_loss_workspace_size(cams) -> int:
+    return load().hm_hybrid_loss_workspace_size(cams, len(cams))
+
+
+def hm_hybrid_loss(cams, out_rgb, target, mesh_rgb, out_T, mesh_depth, params, loss_out, dL_drgb,
+                   dL_dmesh, ws, ws_bytes, stream):
+    return load().hm_hybrid_loss(cams, len(cams), _ptr(out_rgb), _ptr(target), _ptr(mesh_rgb), _ptr(out_T),
+                                 _ptr(mesh_depth), ctypes.byref(params), _ptr(loss_out), _ptr(dL_drgb),
+                                 _ptr(dL_dmesh), _ptr(ws), ws_bytes, stream)

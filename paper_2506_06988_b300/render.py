@@ -276,13 +276,16 @@ class Renderer:
 
     def backward(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT=None,
                  mesh: Optional[MeshInput] = None, tex_grad: bool = False, out=None,
-                 stages: int = 0, zero: bool = True, overlap: Optional[bool] = None):
+                 stages: int = 0, zero: bool = True, overlap: Optional[bool] = None,
+                 dL_dmesh: Optional[torch.Tensor] = None):
         """Gradients of the last forward, accumulated into fresh zero tensors
         (or into ``out``, a dict from ``grad_buffers``, zeroed first unless
         ``zero`` is False).  ``stages``: HM_BWD_* bits to run (0 = all).
         With ``overlap`` (default ``self.overlap``) the texel gradients run on
         a side stream concurrently with the blend and projection gradients
-        (they share no output) and join the current stream at the end."""
+        (they share no output) and join the current stream at the end.
+        ``dL_dmesh`` (planar like ``rgb``): the gradient of a loss on the mesh
+        colour itself, added to what the texels receive through I_h."""
         want_tex = tex_grad and self.has_mesh
         if (self.overlap if overlap is None else overlap) and want_tex and stages == 0:
             g = out if out is not None else self.grad_buffers(mesh.texture.shape[:2])
@@ -297,7 +300,7 @@ class Renderer:
                 if out is not None and zero:
                     g["texture"].zero_()
                 self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
-                                    lib.HM_BWD_TEXTURE)
+                                    lib.HM_BWD_TEXTURE, dL_dmesh)
             self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
                                 lib.HM_BWD_BLEND | lib.HM_BWD_PROJECT)
             main.wait_stream(side)
@@ -310,10 +313,11 @@ class Renderer:
                 for v in g.values():
                     v.zero_()
         self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh if want_tex else None,
-                            g, stages)
+                            g, stages, dL_dmesh)
         return g
 
-    def _backward_call(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g, stages):
+    def _backward_call(self, means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g, stages,
+                       dL_dmesh=None):
         """One hm_blend_backward call on the current stream (texel gradients
         when ``mesh`` is given and ``g`` holds a texture buffer)."""
         if self.bwd_ws is None:
@@ -332,7 +336,32 @@ class Renderer:
             self.uv if self.has_mesh else None, tw, th, self.opt, self.T, self.last_idx,
             dL_drgb.contiguous(), None if dL_dT is None else dL_dT.contiguous(),
             g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], d_tex, self.status_word,
-            self.bwd_ws, self.bwd_ws.numel(), _stream()), "hm_blend_backward")
+            self.bwd_ws, self.bwd_ws.numel(), _stream(),
+            dL_dmesh=None if (dL_dmesh is None or d_tex is None) else dL_dmesh.contiguous()),
+            "hm_blend_backward")
+
+    # -- the joint-optimisation loss ------------------------------------------------
+    def loss(self, target: torch.Tensor, params=None, texture_loss: bool = True):
+        """The joint loss of the last frame against ``target`` (planar like
+        ``rgb``) by hm_hybrid_loss: returns (terms, dL/drgb, dL/dmesh) with
+        terms = device float64 [L1, mean SSIM, L_t, L] and dL/dmesh None
+        without a mesh or with ``texture_loss`` off.  Pass both gradients to
+        ``backward`` (``dL_drgb`` and ``dL_dmesh``)."""
+        d = self.device
+        if getattr(self, "_loss_ws", None) is None:
+            self._loss_ws = torch.empty(lib.hm_hybrid_loss_workspace_size(self.cams), dtype=torch.uint8,
+                                        device=d)
+            self._loss_out = torch.empty(4, dtype=torch.float64, device=d)
+            self._dI = torch.empty(3 * self.npix, dtype=torch.float32, device=d)
+            self._dM = torch.empty(3 * self.npix, dtype=torch.float32, device=d) if self.has_mesh else None
+        p = params if params is not None else lib.loss_params()
+        use_mesh = self.has_mesh and texture_loss
+        lib.check(lib.hm_hybrid_loss(self.cams, self.rgb, target.contiguous(),
+                                     self.mesh_rgb if use_mesh else None, self.T if use_mesh else None,
+                                     self.mesh_depth if use_mesh else None, p, self._loss_out, self._dI,
+                                     self._dM if use_mesh else None, self._loss_ws, self._loss_ws.numel(),
+                                     _stream()), "hm_hybrid_loss")
+        return self._loss_out, self._dI, (self._dM if use_mesh else None)
 
     # -- views of the outputs -------------------------------------------------------
     def image(self, k: int, which: str = "rgb") -> torch.Tensor:

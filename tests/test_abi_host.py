@@ -114,3 +114,28 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower() or f == "scenes.py", f
+
+
+def test_texture_loss_schedule_follows_the_paper():
+    """lambda_t: 0 in the 3k-iteration warm-up, 0.1 until densification ends
+    at 15k, 0 afterwards (Sec. 3.4, Sec. 4.1)."""
+    from paper_2506_06988_b300.schedule import texture_loss_weight
+    assert texture_loss_weight(0) == 0.0
+    assert texture_loss_weight(2999) == 0.0
+    assert texture_loss_weight(3000) == 0.1
+    assert texture_loss_weight(14999) == 0.1
+    assert texture_loss_weight(15000) == 0.0
+
+
+def test_loss_defaults_and_invalid_args():
+    p = lib.loss_params()
+    assert abs(p.lambda_ssim - 0.2) < 1e-7 and abs(p.lambda_t - 0.1) < 1e-7 and p.k == 20.0
+    cams = lib.cameras([scenes._identity_cam(16, 16)])
+    assert lib.hm_hybrid_loss_workspace_size(cams) >= 9 * 16 * 16 * 4
+    st = lib.hm_hybrid_loss(cams, 16, 16, 16, None, None, p, 16, 16, None, 16, 1, 0)
+    assert st == lib.HM_ERR_INVALID_ARG and "mesh" in lib.last_error()
+    bad = lib.loss_params(lambda_ssim=1.5)
+    st = lib.hm_hybrid_loss(cams, 16, 16, None, None, None, bad, 16, 16, None, 16, 1 << 20, 0)
+    assert st == lib.HM_ERR_INVALID_ARG
+    st = lib.hm_hybrid_loss(cams, 16, 16, None, None, None, p, 16, 16, None, 16, 8, 0)
+    assert st == lib.HM_ERR_WORKSPACE
