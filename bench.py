@@ -522,14 +522,19 @@ def run_batched16(args, dev, dist):
 
 
 def run_joint_opt(args, dev, dist):
-    """One joint optimisation step of Gaussians and FP32 texels (Sec. 3.4)
-    through the autograd Function: the room at 1296x968 with 500k Gaussians
-    (SH degree 3) and a 2048^2 FP32 learnable texture; L1 loss against a
-    target rendered from perturbed parameters (means + N(0, 0.01), colours +
-    N(0, 0.05)); activations in PyTorch; Adam (PyTorch's fused kernel)."""
+    """One joint optimisation step of Gaussians and FP32 texels (Sec. 3.4):
+    the room at 1296x968 with 500k Gaussians (SH degree 3) and a 2048^2 FP32
+    learnable texture, against a target rendered from perturbed parameters
+    (means + N(0, 0.01), colours + N(0, 0.05)); activations in PyTorch; Adam
+    (PyTorch's fused kernel).  Two losses:
+    * ``l1``: a plain L1 in PyTorch through the HybridRender autograd Function;
+    * ``paper``: the joint loss of Eq. 3 + Sec. 3.4 (0.8 L1 + 0.2 D-SSIM +
+      0.1 transmittance-aware texture loss) by the fused hm_hybrid_loss, its
+      dL/dI_h and dL/dI_m fed straight to hm_blend_backward."""
     import torch
-    from paper_2506_06988_b300 import scenes
+    from paper_2506_06988_b300 import lib, scenes
     from paper_2506_06988_b300.render import HybridRender, MeshInput, Renderer
+    from paper_2506_06988_b300.schedule import texture_loss_weight
     scene = scenes.config2_scene()
     g = scene.gaussians
     tgt = scenes.config2_target_params(scene)
@@ -546,9 +551,13 @@ def run_joint_opt(args, dev, dist):
     logit = torch.logit(T(g.opacity)).requires_grad_()
     sh = T(g.sh).requires_grad_()
     tex = mesh.texture.clone().requires_grad_()
-    opt = torch.optim.Adam([means, log_s, quats, logit, sh, tex], lr=1e-4, fused=True)
+    params = [means, log_s, quats, logit, sh, tex]
+    init = [p.detach().clone() for p in params]
+    opt = torch.optim.Adam(params, lr=1e-4, fused=True)
+    lp = lib.loss_params(lambda_t=texture_loss_weight(5000))
+    mesh_t = MeshInput(mesh.verts, mesh.uvs, mesh.faces, tex.detach())
 
-    def step():
+    def step_l1():
         opt.zero_grad(set_to_none=False)
         rgb, _ = HybridRender.apply(r, mesh, means, torch.exp(log_s), quats, torch.sigmoid(logit), sh, tex)
         loss = (rgb - target).abs().mean()
@@ -556,25 +565,65 @@ def run_joint_opt(args, dev, dist):
         opt.step()
         return loss
 
-    first = float(step().item())
-    for _ in range(2):
-        step()
-    steps = max(5, min(args.steps, 20))
+    def step_paper():
+        opt.zero_grad(set_to_none=False)
+        s_, o_ = torch.exp(log_s), torch.sigmoid(logit)
+        P = (means.detach(), s_.detach(), quats.detach(), o_.detach(), sh.detach())
+        r.render(*P, mesh_t)
+        terms, dI, dM = r.loss(target, lp)
+        gr = r.backward(*P, dI, None, mesh=mesh_t, tex_grad=True, dL_dmesh=dM)
+        torch.autograd.backward([s_, o_], [gr["scales"], gr["opacity"]])
+        means.grad.add_(gr["means"])
+        quats.grad.add_(gr["quats"])
+        sh.grad.add_(gr["sh"])
+        tex.grad.add_(gr["texture"])
+        opt.step()
+        return terms[3]
+
     stream = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    _barrier(dist)
-    for k in range(steps):
-        ev[k][0].record(stream)
-        loss = step()
-        ev[k][1].record(stream)
-    _barrier(dist)
-    ms = _max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dist)
-    W, H = scene.cameras[0].width, scene.cameras[0].height
     out = {"workload": "joint optimisation step: room at 1296x968, 500k Gaussians SH3, 2048^2 FP32 "
-                       "learnable texels, L1 vs a target rendered from perturbed parameters; "
-                       "HybridRender autograd + fused Adam",
-           "frames_per_s": 1e3 / ms, "ms_per_step": ms, "mpixel_per_s": W * H * 1e3 / ms / 1e6,
-           "loss_first": first, "loss_last": float(loss.item()), "steps": steps}
+                       "learnable texels vs a target rendered from perturbed parameters; fused Adam"}
+    W, H = scene.cameras[0].width, scene.cameras[0].height
+    for name, step in (("l1", step_l1), ("paper", step_paper)):
+        with torch.no_grad():
+            for p, p0 in zip(params, init):
+                p.copy_(p0)
+        opt = torch.optim.Adam(params, lr=1e-4, fused=True)
+        first = float(step().item())
+        for _ in range(2):
+            step()
+        steps = max(5, min(args.steps, 20))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        _barrier(dist)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            loss = step()
+            ev[k][1].record(stream)
+        _barrier(dist)
+        ms = _max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dist)
+        out[name] = {"frames_per_s": 1e3 / ms, "ms_per_step": ms, "mpixel_per_s": W * H * 1e3 / ms / 1e6,
+                     "loss_first": first, "loss_last": float(loss.item()), "steps": steps}
+    out["l1"]["loss"] = "mean |I_h - I| in PyTorch, HybridRender autograd"
+    out["paper"]["loss"] = ("0.8 L1 + 0.2 (1 - SSIM 11x11) + 0.1 M_T |I - I_m|^2 by the fused "
+                            "hm_hybrid_loss (lambda_t of iteration 5000 of the warm-up schedule)")
+    # the fused loss alone (forward terms and both gradients, one frame)
+    for _ in range(3):
+        r.loss(target, lp)
+    n_l = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_l):
+        r.loss(target, lp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lm = e0.elapsed_time(e1) / n_l
+    # algorithmic bytes: read I_h, I, I_m (3 planes each) + T + depth, write
+    # dL/dI_h and dL/dI_m; the SSIM statistics (9 floats per pixel) are
+    # written once and read once by the gradient pass
+    npx = W * H
+    alg = npx * 4 * (3 + 3 + 3 + 1 + 1 + 3 + 3 + 2 * 9)
+    out["loss_kernel"] = {"ms": lm, "alg_bytes": alg, "achieved_gbs": alg / lm / 1e6,
+                          "launches": 3, "note": "ssim_fwd + ssim_bwd + final, 16x16 tiles x 3 channels"}
     del r, opt
     torch.cuda.empty_cache()
     return out
