@@ -6,27 +6,35 @@
 // 11 x 11 Gaussian window (sigma 1.5, separable, zero outside the image),
 // C1 = 0.01^2, C2 = 0.03^2.  M_T is a mask (no gradient to T).
 //
-// Two passes over 16 x 16 tiles, a CTA per (tile, channel):
+// Two passes over 32 x 32 tiles, a CTA of 256 threads per (tile, channel):
 //  * ssim_fwd: the five window sums (mu_x, mu_y, E[x^2], E[y^2], E[xy]) by
-//    a horizontal then a vertical 11-tap pass through shared memory (halo 5),
+//    a horizontal then a vertical 11-tap pass through shared memory (halo 5;
+//    each thread computes 4 adjacent outputs of a pass from 14 loaded values;
+//    the vertical pass carries map pairs in FP32x2 FMAs),
 //    the SSIM map and its partial derivatives with respect to the window
 //    sums -- D_mu = dS/dmu_x, D_xx = dS/dE[x^2], D_xy = dS/dE[xy] -- to
-//    global scratch; the pointwise L1 and texture-loss terms, dL/dI_m; the
-//    three sums (FP64 atomics, one per CTA).
+//    global scratch ((D_mu, D_xx) interleaved, D_xy a plane of its own); the pointwise L1 and texture-loss terms, dL/dI_m; the
+//    CTA's three partial sums (FP64) to its own slot.
 //  * ssim_bwd: since mu_x, E[x^2], E[xy] at pixel p are window sums of x,
 //    x^2 and x y, dSSIM_total/dx(q) = (w * D_mu)(q) + 2 x(q) (w * D_xx)(q)
 //    + y(q) (w * D_xy)(q): the same separable window over the three maps,
 //    then dL/dI_h = ((1 - ls) sign(x - y) - ls dSSIM/dx) / N.
+//  * loss_final: the partial sums in a fixed order (the loss is bitwise
+//    reproducible) and the weighted total.
 #include "hm_host.h"
 
 namespace hm {
 
 namespace {
 
-constexpr int kLT = 16;              // output tile edge
+constexpr int kLT = 32;              // output tile edge
+constexpr int kNT = 256;             // threads per CTA
 constexpr int kRad = 5;              // window radius
 constexpr int kTaps = 2 * kRad + 1;  // 11
-constexpr int kHalo = kLT + 2 * kRad;
+constexpr int kHalo = kLT + 2 * kRad;   // 42 rows / columns with the halo
+constexpr int kHS = 48;              // halo row stride (float4-aligned, >= 4*7 + 16)
+constexpr int kOut = 4;              // outputs per thread per pass
+constexpr int kSpan = kOut + kTaps - 1;   // 14 inputs per 4 outputs
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -34,122 +42,111 @@ struct Taps {
     float g[kTaps];
 };
 
-__device__ __forceinline__ double block_sum(double v, double *s_red) {
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (t == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += s_red[k];
-    __syncthreads();
-    return r;
+// visit the (kLT + 2 kRad)^2 halo elements (row r, column c) of a tile,
+// kNT apart in row-major order, stepping (r, c) without divisions
+template <class F>
+__device__ __forceinline__ void for_halo(F &&f) {
+    int r = threadIdx.x / kHalo, c = threadIdx.x - r * kHalo;
+    for (int i = threadIdx.x; i < kHalo * kHalo; i += kNT) {
+        f(r, c);
+        r += kNT / kHalo;
+        c += kNT % kHalo;
+        if (c >= kHalo) {
+            c -= kHalo;
+            ++r;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(kLT *kLT)
+__device__ __forceinline__ void load_span(const float *row, float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 f = *reinterpret_cast<const float4 *>(row + 4 * q);
+        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+    }
+}
+
+// out[o] = sum_k g[k] v[o + k], o < 4
+__device__ __forceinline__ void taps4(const Taps &tp, const float *v, float (&out)[kOut]) {
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) out[o] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kTaps; ++k)
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) out[o] = fmaf(tp.g[k], v[o + k], out[o]);
+}
+
+// horizontal pass of one plane for (row r, columns c0 .. c0 + 3); the
+// result goes to lane `half` (0: x, 1: y) of a float2 plane or to a float plane
+__device__ __forceinline__ void horiz_store2(const Taps &tp, const float *row, float2 *dst, int half) {
+    float v[16], o[kOut];
+    load_span(row, v);
+    taps4(tp, v, o);
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) reinterpret_cast<float *>(dst + q)[half] = o[q];
+}
+
+// vertical pass, thread (column c, rows 4 rg .. 4 rg + 3): each loaded row
+// value feeds the (up to 4) outputs whose window covers it
+__device__ __forceinline__ void vert4x2(const Taps &tp, const float2 (*sh)[kLT], int c, int rg,
+                                        float2 (&out)[kOut]) {
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) out[o] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kSpan; ++j) {
+        const float2 v = sh[kOut * rg + j][c];
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) {
+            const int k = j - o;
+            if (k >= 0 && k < kTaps) out[o] = __ffma2_rn(make_float2(tp.g[k], tp.g[k]), v, out[o]);
+        }
+    }
+}
+
+__device__ __forceinline__ void vert4x1(const Taps &tp, const float (*sh)[kLT], int c, int rg, float (&out)[kOut]) {
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) out[o] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kSpan; ++j) {
+        const float v = sh[kOut * rg + j][c];
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) {
+            const int k = j - o;
+            if (k >= 0 && k < kTaps) out[o] = fmaf(tp.g[k], v, out[o]);
+        }
+    }
+}
+
+__device__ __forceinline__ void block_sum3(double (&v)[3], double (*s_red)[kNT / 32]) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) s_red[q][w] = v[q];
+    }
+    __syncthreads();
+    if (t < 3) {
+        double r = 0.0;
+        for (int k = 0; k < kNT / 32; ++k) r += s_red[t][k];
+        s_red[t][0] = r;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = s_red[q][0];
+}
+
+__global__ void __launch_bounds__(kNT)
 ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
                 const float *__restrict__ m_all, const float *__restrict__ T_all,
                 const float *__restrict__ md_all, float k_mask, float mesh_grad_scale,
-                float *__restrict__ d_mu, float *__restrict__ d_xx, float *__restrict__ d_xy,
-                float *__restrict__ dL_dmesh, double *__restrict__ sums) {
-    __shared__ float s_x[kHalo][kHalo], s_y[kHalo][kHalo];
-    __shared__ float s_h[5][kHalo][kLT];
-    __shared__ double s_red[kLT * kLT / 32];
-    const int gt = blockIdx.x, ch = blockIdx.y;
-    const int v = view_of_tile(vt, gt);
-    const ViewDev &V = vt.v[v];
-    const int local = gt - V.tile_off;
-    const int px0 = (local % V.tiles_x) * kLT, py0 = (local / V.tiles_x) * kLT;
-    const long long npx = (long long)V.W * V.H;
-    const float *x = x_all + 3 * V.pix_off + ch * npx;
-    const float *y = y_all + 3 * V.pix_off + ch * npx;
-    const int t = threadIdx.x;
-    for (int i = t; i < kHalo * kHalo; i += kLT * kLT) {
-        const int r = i / kHalo, c = i % kHalo;
-        const int gx = px0 - kRad + c, gy = py0 - kRad + r;
-        float xv = 0.f, yv = 0.f;
-        if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
-            xv = x[(long long)gy * V.W + gx];
-            yv = y[(long long)gy * V.W + gx];
-        }
-        s_x[r][c] = xv;
-        s_y[r][c] = yv;
-    }
-    __syncthreads();
-    for (int i = t; i < kHalo * kLT; i += kLT * kLT) {
-        const int r = i / kLT, c = i % kLT;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
-#pragma unroll
-        for (int k = 0; k < kTaps; ++k) {
-            const float g = tp.g[k], xv = s_x[r][c + k], yv = s_y[r][c + k];
-            a = fmaf(g, xv, a);
-            b = fmaf(g, yv, b);
-            aa = fmaf(g, xv * xv, aa);
-            bb = fmaf(g, yv * yv, bb);
-            ab = fmaf(g, xv * yv, ab);
-        }
-        s_h[0][r][c] = a; s_h[1][r][c] = b; s_h[2][r][c] = aa; s_h[3][r][c] = bb; s_h[4][r][c] = ab;
-    }
-    __syncthreads();
-    const int r = t / kLT, c = t % kLT;
-    const int px = px0 + c, py = py0 + r;
-    const bool in = px < V.W && py < V.H;
-    double ssum = 0.0, l1 = 0.0, lt = 0.0;
-    if (in) {
-        float mx = 0.f, my = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
-#pragma unroll
-        for (int k = 0; k < kTaps; ++k) {
-            const float g = tp.g[k];
-            mx = fmaf(g, s_h[0][r + k][c], mx);
-            my = fmaf(g, s_h[1][r + k][c], my);
-            sxx = fmaf(g, s_h[2][r + k][c], sxx);
-            syy = fmaf(g, s_h[3][r + k][c], syy);
-            sxy = fmaf(g, s_h[4][r + k][c], sxy);
-        }
-        const float vx = sxx - mx * mx, vy = syy - my * my, cxy = sxy - mx * my;
-        const float A1 = fmaf(2.f * mx, my, kC1), A2 = fmaf(2.f, cxy, kC2);
-        const float B1 = fmaf(mx, mx, fmaf(my, my, kC1)), B2 = vx + vy + kC2;
-        const float S = (A1 * A2) / (B1 * B2);
-        // dS/d(mu_x, E[x^2], E[xy]) with sigma_x^2 = E[x^2] - mu_x^2 and
-        // sigma_xy = E[xy] - mu_x mu_y
-        const long long lp = (long long)py * V.W + px;
-        const long long o = 3 * V.pix_off + ch * npx + lp;
-        d_mu[o] = S * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
-        d_xx[o] = -S / B2;
-        d_xy[o] = 2.f * S / A2;
-        ssum = S;
-        const float xv = s_x[r + kRad][c + kRad], yv = s_y[r + kRad][c + kRad];
-        l1 = fabsf(xv - yv);
-        if (m_all) {
-            const float *m = m_all + 3 * V.pix_off + ch * npx;
-            const bool hit = md_all[V.pix_off + lp] < INFINITY;
-            float g = 0.f;
-            if (hit) {
-                const float mt = 1.f / (1.f + expf(-k_mask * (T_all[V.pix_off + lp] - 0.5f)));
-                const float d = yv - m[lp];
-                lt = (double)(mt * d * d);
-                g = mesh_grad_scale * mt * -d;     // d/dm of mt (y - m)^2, times lt / N
-            }
-            dL_dmesh[o] = g;
-        }
-    }
-    ssum = block_sum(ssum, s_red);
-    l1 = block_sum(l1, s_red);
-    lt = block_sum(lt, s_red);
-    if (t == 0) {
-        atomicAdd(&sums[0], l1);
-        atomicAdd(&sums[1], ssum);
-        atomicAdd(&sums[2], lt);
-    }
-}
-
-__global__ void __launch_bounds__(kLT *kLT)
-ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
-                const float *__restrict__ d_mu, const float *__restrict__ d_xx, const float *__restrict__ d_xy,
-                float l1_scale, float ssim_scale, float *__restrict__ dL_drgb) {
-    __shared__ float s_d[3][kHalo][kHalo];
-    __shared__ float s_h[3][kHalo][kLT];
+                float2 *__restrict__ d_mu_xx, float *__restrict__ d_xy,
+                float *__restrict__ dL_dmesh, double *__restrict__ partials) {
+    __shared__ __align__(16) float s_in[2][kHalo][kHS];
+    __shared__ __align__(16) float2 s_m[kHalo][kLT];    // (w*x, w*y) along rows
+    __shared__ __align__(16) float2 s_q[kHalo][kLT];    // (w*x^2, w*y^2)
+    __shared__ __align__(16) float s_c[kHalo][kLT];     // w*(x y)
+    __shared__ double s_red[3][kNT / 32];
     const int gt = blockIdx.x, ch = blockIdx.y;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -158,65 +155,202 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     const long long npx = (long long)V.W * V.H;
     const long long base = 3 * V.pix_off + ch * npx;
     const int t = threadIdx.x;
-    for (int i = t; i < kHalo * kHalo; i += kLT * kLT) {
-        const int r = i / kHalo, c = i % kHalo;
-        const int gx = px0 - kRad + c, gy = py0 - kRad + r;
-        float a = 0.f, b = 0.f, e = 0.f;
-        if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
-            const long long o = base + (long long)gy * V.W + gx;
-            a = d_mu[o];
-            b = d_xx[o];
-            e = d_xy[o];
-        }
-        s_d[0][r][c] = a;
-        s_d[1][r][c] = b;
-        s_d[2][r][c] = e;
+    {
+        const float *x = x_all + base, *y = y_all + base;
+        const int W = V.W, H = V.H;
+        for_halo([&](int r, int c) {
+            const int gx = px0 - kRad + c, gy = py0 - kRad + r;
+            float xv = 0.f, yv = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const long long o = (long long)gy * W + gx;
+                xv = x[o];
+                yv = y[o];
+            }
+            s_in[0][r][c] = xv;
+            s_in[1][r][c] = yv;
+        });
     }
     __syncthreads();
-    for (int i = t; i < kHalo * kLT; i += kLT * kLT) {
-        const int r = i / kLT, c = i % kLT;
-        float a = 0.f, b = 0.f, e = 0.f;
+    // horizontal: (row r, columns c0 .. c0 + 3) of the five products
+    for (int i = t; i < kHalo * (kLT / kOut); i += kNT) {
+        const int r = i / (kLT / kOut), c0 = kOut * (i % (kLT / kOut));
+        float xs[16], ys[16], p[kSpan], o[kOut];
+        load_span(&s_in[0][r][c0], xs);
+        load_span(&s_in[1][r][c0], ys);
+        float2 mm[kOut], qq[kOut];
+        taps4(tp, xs, o);
 #pragma unroll
-        for (int k = 0; k < kTaps; ++k) {
-            const float g = tp.g[k];
-            a = fmaf(g, s_d[0][r][c + k], a);
-            b = fmaf(g, s_d[1][r][c + k], b);
-            e = fmaf(g, s_d[2][r][c + k], e);
-        }
-        s_h[0][r][c] = a; s_h[1][r][c] = b; s_h[2][r][c] = e;
+        for (int q = 0; q < kOut; ++q) mm[q].x = o[q];
+        taps4(tp, ys, o);
+#pragma unroll
+        for (int q = 0; q < kOut; ++q) mm[q].y = o[q];
+#pragma unroll
+        for (int j = 0; j < kSpan; ++j) p[j] = xs[j] * xs[j];
+        taps4(tp, p, o);
+#pragma unroll
+        for (int q = 0; q < kOut; ++q) qq[q].x = o[q];
+#pragma unroll
+        for (int j = 0; j < kSpan; ++j) p[j] = ys[j] * ys[j];
+        taps4(tp, p, o);
+#pragma unroll
+        for (int q = 0; q < kOut; ++q) qq[q].y = o[q];
+#pragma unroll
+        for (int j = 0; j < kSpan; ++j) p[j] = xs[j] * ys[j];
+        taps4(tp, p, o);
+        float4 *dm = reinterpret_cast<float4 *>(&s_m[r][c0]);
+        float4 *dq = reinterpret_cast<float4 *>(&s_q[r][c0]);
+        dm[0] = make_float4(mm[0].x, mm[0].y, mm[1].x, mm[1].y);
+        dm[1] = make_float4(mm[2].x, mm[2].y, mm[3].x, mm[3].y);
+        dq[0] = make_float4(qq[0].x, qq[0].y, qq[1].x, qq[1].y);
+        dq[1] = make_float4(qq[2].x, qq[2].y, qq[3].x, qq[3].y);
+        *reinterpret_cast<float4 *>(&s_c[r][c0]) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
-    const int r = t / kLT, c = t % kLT;
-    const int px = px0 + c, py = py0 + r;
-    if (px >= V.W || py >= V.H) return;
-    float a = 0.f, b = 0.f, e = 0.f;
+    const int c = t & 31, rg = t >> 5;
+    float2 mu[kOut], ex2[kOut];
+    float exy[kOut];
+    vert4x2(tp, s_m, c, rg, mu);
+    vert4x2(tp, s_q, c, rg, ex2);
+    vert4x1(tp, s_c, c, rg, exy);
+    const int px = px0 + c;
+    float ssum = 0.f, l1 = 0.f, lt = 0.f;
 #pragma unroll
-    for (int k = 0; k < kTaps; ++k) {
-        const float g = tp.g[k];
-        a = fmaf(g, s_h[0][r + k][c], a);
-        b = fmaf(g, s_h[1][r + k][c], b);
-        e = fmaf(g, s_h[2][r + k][c], e);
+    for (int q = 0; q < kOut; ++q) {
+        const int r = kOut * rg + q, py = py0 + r;
+        if (px >= V.W || py >= V.H) continue;
+        const float mx = mu[q].x, my = mu[q].y;
+        const float vx = ex2[q].x - mx * mx, vy = ex2[q].y - my * my, cxy = exy[q] - mx * my;
+        const float A1 = fmaf(2.f * mx, my, kC1), A2 = fmaf(2.f, cxy, kC2);
+        const float B1 = fmaf(mx, mx, fmaf(my, my, kC1)), B2 = vx + vy + kC2;
+        const float rA1 = __frcp_rn(A1), rA2 = __frcp_rn(A2), rB1 = __frcp_rn(B1), rB2 = __frcp_rn(B2);
+        const float S = (A1 * A2) * (rB1 * rB2);
+        // dS/d(mu_x, E[x^2], E[xy]) with sigma_x^2 = E[x^2] - mu_x^2 and
+        // sigma_xy = E[xy] - mu_x mu_y
+        const long long lp = (long long)py * V.W + px;
+        const long long o = base + lp;
+        const float dmu = 2.f * S * fmaf(my, rA1 - rA2, mx * (rB2 - rB1));
+        d_mu_xx[o] = make_float2(dmu, -S * rB2);
+        d_xy[o] = 2.f * S * rA2;
+        ssum += S;
+        const float xv = s_in[0][r + kRad][c + kRad], yv = s_in[1][r + kRad][c + kRad];
+        l1 += fabsf(xv - yv);
+        if (m_all) {
+            const bool hit = md_all[V.pix_off + lp] < INFINITY;
+            float g = 0.f;
+            if (hit) {
+                const float mt = 1.f / (1.f + expf(-k_mask * (T_all[V.pix_off + lp] - 0.5f)));
+                const float d = yv - m_all[o];
+                lt = fmaf(mt * d, d, lt);
+                g = mesh_grad_scale * mt * -d;     // d/dm of mt (y - m)^2, times lt / N
+            }
+            dL_dmesh[o] = g;
+        }
     }
-    const long long o = base + (long long)py * V.W + px;
-    const float xv = x_all[o], yv = y_all[o];
-    const float dS = fmaf(2.f * xv, b, fmaf(yv, e, a));
-    const float sg = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
-    dL_drgb[o] = fmaf(l1_scale, sg, -ssim_scale * dS);
+    double sums[3] = {(double)l1, (double)ssum, (double)lt};
+    block_sum3(sums, s_red);
+    if (t < 3) partials[3 * ((long long)ch * gridDim.x + gt) + t] = s_red[t][0];
 }
 
-__global__ void loss_final_kernel(const double *sums, double inv_n, double ls, double lt, double *out) {
-    const double l1 = sums[0] * inv_n, ss = sums[1] * inv_n, t = sums[2] * inv_n;
-    out[0] = l1;
-    out[1] = ss;
-    out[2] = t;
-    out[3] = (1.0 - ls) * l1 + ls * (1.0 - ss) + lt * t;
+__global__ void __launch_bounds__(kNT)
+ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
+                const float2 *__restrict__ d_mu_xx, const float *__restrict__ d_xy,
+                float l1_scale, float ssim_scale, float *__restrict__ dL_drgb) {
+    __shared__ __align__(16) float s_d[3][kHalo][kHS];
+    __shared__ __align__(16) float2 s_ab[kHalo][kLT];   // w*D_mu, w*D_xx along rows
+    __shared__ __align__(16) float s_e[kHalo][kLT];     // w*D_xy
+    const int gt = blockIdx.x, ch = blockIdx.y;
+    const int v = view_of_tile(vt, gt);
+    const ViewDev &V = vt.v[v];
+    const int local = gt - V.tile_off;
+    const int px0 = (local % V.tiles_x) * kLT, py0 = (local / V.tiles_x) * kLT;
+    const long long npx = (long long)V.W * V.H;
+    const long long base = 3 * V.pix_off + ch * npx;
+    const int t = threadIdx.x;
+    {
+        const float2 *ab = d_mu_xx + base;
+        const float *e = d_xy + base;
+        const int W = V.W, H = V.H;
+        for_halo([&](int r, int c) {
+            const int gx = px0 - kRad + c, gy = py0 - kRad + r;
+            float2 a = make_float2(0.f, 0.f);
+            float ev = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const long long o = (long long)gy * W + gx;
+                a = ab[o];
+                ev = e[o];
+            }
+            s_d[0][r][c] = a.x;
+            s_d[1][r][c] = a.y;
+            s_d[2][r][c] = ev;
+        });
+    }
+    __syncthreads();
+    for (int i = t; i < kHalo * (kLT / kOut); i += kNT) {
+        const int r = i / (kLT / kOut), c0 = kOut * (i % (kLT / kOut));
+        horiz_store2(tp, &s_d[0][r][c0], &s_ab[r][c0], 0);
+        horiz_store2(tp, &s_d[1][r][c0], &s_ab[r][c0], 1);
+        float vs[16], o[kOut];
+        load_span(&s_d[2][r][c0], vs);
+        taps4(tp, vs, o);
+        *reinterpret_cast<float4 *>(&s_e[r][c0]) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    __syncthreads();
+    const int c = t & 31, rg = t >> 5;
+    float2 ab[kOut];
+    float e[kOut];
+    vert4x2(tp, s_ab, c, rg, ab);
+    vert4x1(tp, s_e, c, rg, e);
+    const int px = px0 + c;
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) {
+        const int py = py0 + kOut * rg + q;
+        if (px >= V.W || py >= V.H) continue;
+        const long long o = base + (long long)py * V.W + px;
+        const float xv = x_all[o], yv = y_all[o];
+        const float dS = fmaf(2.f * xv, ab[q].y, fmaf(yv, e[q], ab[q].x));
+        const float sg = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
+        dL_drgb[o] = fmaf(l1_scale, sg, -ssim_scale * dS);
+    }
 }
 
+// one CTA: each thread sums a strided subset of the CTA partials, then a
+// fixed-shape tree -- the same order on every call
+__global__ void __launch_bounds__(kNT)
+loss_final_kernel(const double *__restrict__ partials, int n_part, double inv_n, double ls, double lt,
+                  double *__restrict__ out) {
+    __shared__ double s_red[3][kNT / 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n_part; i += kNT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] += partials[3 * (long long)i + q];
+    block_sum3(v, s_red);
+    if (threadIdx.x == 0) {
+        const double l1 = v[0] * inv_n, ss = v[1] * inv_n, t = v[2] * inv_n;
+        out[0] = l1;
+        out[1] = ss;
+        out[2] = t;
+        out[3] = (1.0 - ls) * l1 + ls * (1.0 - ss) + lt * t;
+    }
+}
+
+// the camera table with kLT x kLT loss tiles (validated as 16 x 16 render
+// tiles, then re-tiled)
 bool loss_view_table(const hm_camera *cams, int32_t n_views, ViewTable *vt) {
     hm_options o;
     hm_default_options(&o);
-    o.tile_w = o.tile_h = kLT;
-    return build_view_table(cams, n_views, &o, vt);
+    o.tile_w = o.tile_h = 16;
+    if (!build_view_table(cams, n_views, &o, vt)) return false;
+    vt->tile_w = vt->tile_h = kLT;
+    int tiles = 0;
+    for (int v = 0; v < vt->n_views; ++v) {
+        ViewDev &d = vt->v[v];
+        d.tiles_x = (d.W + kLT - 1) / kLT;
+        d.tiles_y = (d.H + kLT - 1) / kLT;
+        d.tile_off = tiles;
+        tiles += d.tiles_x * d.tiles_y;
+    }
+    vt->total_tiles = tiles;
+    return true;
 }
 
 }  // namespace
@@ -235,7 +369,7 @@ extern "C" void hm_default_loss_params(hm_loss_params *p) {
 extern "C" size_t hm_hybrid_loss_workspace_size(const hm_camera *cams, int32_t n_views) {
     ViewTable vt;
     if (!loss_view_table(cams, n_views, &vt)) return 0;
-    return sizeof(float) * 9 * (size_t)vt.total_pixels + 3 * 256 + 256;
+    return sizeof(float) * 9 * (size_t)vt.total_pixels + sizeof(double) * 9 * (size_t)vt.total_tiles + 4 * 256;
 }
 
 extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *out_rgb,
@@ -256,10 +390,10 @@ extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, cons
     cudaStream_t s = (cudaStream_t)stream;
     WsCarver c(ws);
     const size_t np3 = 3 * (size_t)vt.total_pixels;
-    float *d_mu = c.take<float>(np3), *d_xx = c.take<float>(np3), *d_xy = c.take<float>(np3);
-    double *sums = c.take<double>(3);
-    cudaError_t e = cudaMemsetAsync(sums, 0, 3 * sizeof(double), s);
-    if (e != cudaSuccess) return cuda_status(e);
+    float2 *d_mu_xx = c.take<float2>(np3);
+    float *d_xy = c.take<float>(np3);
+    double *partials = c.take<double>(9 * (size_t)vt.total_tiles);
+    cudaError_t e;
     Taps tp;
     {
         double g[kTaps], tot = 0.0;
@@ -272,14 +406,15 @@ extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, cons
     }
     const double n_el = (double)np3;
     dim3 grid(vt.total_tiles, 3);
-    ssim_fwd_kernel<<<grid, kLT * kLT, 0, s>>>(vt, tp, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T,
-                                               mesh_depth, p->k, (float)(2.0 * p->lambda_t / n_el), d_mu, d_xx,
-                                               d_xy, dL_dmesh, sums);
+    ssim_fwd_kernel<<<grid, kNT, 0, s>>>(vt, tp, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T,
+                                               mesh_depth, p->k, (float)(2.0 * p->lambda_t / n_el), d_mu_xx,
+                                         d_xy, dL_dmesh, partials);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    ssim_bwd_kernel<<<grid, kLT * kLT, 0, s>>>(vt, tp, out_rgb, target, d_mu, d_xx, d_xy,
+    ssim_bwd_kernel<<<grid, kNT, 0, s>>>(vt, tp, out_rgb, target, d_mu_xx, d_xy,
                                                (float)((1.0 - p->lambda_ssim) / n_el),
                                                (float)(p->lambda_ssim / n_el), dL_drgb);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    loss_final_kernel<<<1, 1, 0, s>>>(sums, 1.0 / n_el, p->lambda_ssim, p->lambda_t, loss_out);
+    loss_final_kernel<<<1, kNT, 0, s>>>(partials, 3 * vt.total_tiles, 1.0 / n_el, p->lambda_ssim, p->lambda_t,
+                                        loss_out);
     return cuda_status(cudaGetLastError());
 }

@@ -35,7 +35,7 @@ def _flat(views, key):
                            device="cuda")
 
 
-@pytest.mark.parametrize("sizes", [((37, 23),), ((16, 16), (5, 7), (70, 33))])
+@pytest.mark.parametrize("sizes", [((37, 23),), ((16, 16), (5, 7), (70, 33)), ((100, 70), (33, 64))])
 def test_hybrid_loss_matches_oracle(sizes):
     rng = np.random.default_rng(len(sizes))
     cams_np, views = _case(rng, sizes)
@@ -59,6 +59,12 @@ def test_hybrid_loss_matches_oracle(sizes):
     got = out.cpu().numpy()
     want = np.array([l1, ss, lt, L])
     assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-9), (got, want)
+    # the partial sums are reduced in a fixed order: a second call repeats every bit
+    out2, dI2 = torch.empty_like(out), torch.empty_like(dI)
+    lib.check(lib.hm_hybrid_loss(cams, x, y, m, T, depth, lib.loss_params(), out2, dI2, dM, ws, ws.numel(),
+                                 torch.cuda.current_stream().cuda_stream), "hm_hybrid_loss")
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2) and torch.equal(dI, dI2)
     g_ref = np.concatenate([g.reshape(-1) for g in gx])
     g = dI.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
