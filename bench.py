@@ -54,8 +54,8 @@ KERNEL_SOURCES = {
     "project": ("project.cu", "sh.cuh", "hm_internal.cuh"),
 }
 NCU_TRAFFIC = {
-    "blend_forward": (654_741_760, "a6abda8acbf15397"),
-    "blend_backward": (566_785_280, "e21bb9e258335d56"),
+    "blend_forward": (654_977_024, "9a2fffed4933752d"),
+    "blend_backward": (566_698_240, "fb9e8648addd12e8"),
 }
 
 
