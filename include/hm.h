@@ -278,7 +278,7 @@ int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options 
 
 /* ------------------------------------------------------------------------ */
 /* hm_hybrid_loss -- the joint-optimisation loss of the hybrid representation
- * and its gradients (Eq. 3 and Sec. 3.4):
+ * and its gradients (Sec. 3.4; Eq. 3, Eq. 5, Eq. 6, Eq. 7):
  *   L   = (1 - lambda_ssim) L1(I, I_h) + lambda_ssim (1 - SSIM(I, I_h)) + lambda_t L_t
  *   L_t = M_T * ||I~ - I~_m||^2,  M_T = 1 / (1 + exp(-k (T - 0.5)))
  * where I~, I~_m are the target and the mesh colour on pixels with a
@@ -291,7 +291,13 @@ int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options 
  *  loss) or all given.
  *  Outputs: loss_out (device double[4]: L1, mean SSIM, L_t, L), dL_drgb
  *  (dL/dI_h, planar, written), dL_dmesh (lambda_t dL_t/dI_m, planar,
- *  written; pass it to hm_blend_backward).
+ *  written; pass it to hm_blend_backward).  The partial sums are reduced in
+ *  a fixed order, so equal inputs give bitwise-equal results.
+ *  ws: hm_hybrid_loss_workspace_size(cams, n_views) bytes of device memory.
+ *  Errors: HM_ERR_INVALID_ARG (bad cameras, null pointers, an incomplete
+ *  mesh set, lambda_ssim outside [0, 1] or lambda_t < 0), HM_ERR_WORKSPACE
+ *  (ws too small), HM_ERR_CUDA (launch failure).  Launches only; runs on
+ *  `stream` and never synchronises.
  */
 typedef struct hm_loss_params {
     float lambda_ssim;       /* weight of D-SSIM in the photometric loss (0.2) */

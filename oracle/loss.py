@@ -3,10 +3,11 @@
 The paper supervises the hybrid render I_h with the photometric loss of
 Eq. 3, L_c = (1 - lambda_s) L1(I, I_h) + lambda_s D-SSIM(I, I_h) with
 lambda_s = 0.2, and the textured mesh with the transmittance-aware texture
-loss of Sec. 3.4, L_t = M_T ||I~ - I~_m||^2 with the mask
-M_T = 1 / (1 + exp(-k (T - 0.5))), k = 20, where I~ and I~_m are the target
-and the mesh colour on pixels with a triangle and 0 elsewhere; the joint
-loss is L = L_c + lambda_t L_t with lambda_t = 0.1 (Sec. 3.4, Sec. 4.1).
+loss of Sec. 3.4, L_t = M_T ||I~ - I~_m||^2 (Eq. 5) with the mask
+M_T = 1 / (1 + exp(-k (T - 0.5))) (Eq. 6), k = 20, where I~ and I~_m are the
+target and the mesh colour on pixels with a triangle and 0 elsewhere; the
+joint loss is L = L_c + lambda_t L_t (Eq. 7) with lambda_t = 0.1
+(supplementary implementation details).
 
 Readings (the paper leaves them open):
 * every term is a mean over all pixel-channel elements of all cameras;

@@ -1,7 +1,8 @@
 // loss.cu -- the joint-optimisation loss of the hybrid representation and
 // its gradients, fused per image tile:
-//   L = (1 - ls) L1(I, I_h) + ls (1 - SSIM(I, I_h)) + lt L_t          (Eq. 3, Sec. 3.4)
-//   L_t = mean over pixel-channels of M_T hit (I - I_m)^2,  M_T = 1 / (1 + e^{-k (T - 1/2)})
+//   L = (1 - ls) L1(I, I_h) + ls (1 - SSIM(I, I_h)) + lt L_t          (Eq. 3, Eq. 7)
+//   L_t = mean over pixel-channels of M_T hit (I - I_m)^2              (Eq. 5)
+//   M_T = 1 / (1 + e^{-k (T - 1/2)})                                   (Eq. 6)
 // over all pixel-channel elements of all cameras (N of them); SSIM with the
 // 11 x 11 Gaussian window (sigma 1.5, separable, zero outside the image),
 // C1 = 0.01^2, C2 = 0.03^2.  M_T is a mask (no gradient to T).

@@ -117,14 +117,16 @@ def test_product_package_does_not_import_the_oracle():
 
 
 def test_texture_loss_schedule_follows_the_paper():
-    """lambda_t: 0 in the 3k-iteration warm-up, 0.1 until densification ends
-    at 15k, 0 afterwards (Sec. 3.4, Sec. 4.1)."""
+    """lambda_t: 0 through the 3k-iteration warm-up, 0.1 strictly between it
+    and the end of densification at 15k, 0 afterwards (Sec. 3.4, Sec. 4.1,
+    Algorithm 1's strict comparisons)."""
     from paper_2506_06988_b300.schedule import texture_loss_weight
     assert texture_loss_weight(0) == 0.0
-    assert texture_loss_weight(2999) == 0.0
-    assert texture_loss_weight(3000) == 0.1
+    assert texture_loss_weight(3000) == 0.0
+    assert texture_loss_weight(3001) == 0.1
     assert texture_loss_weight(14999) == 0.1
     assert texture_loss_weight(15000) == 0.0
+    assert texture_loss_weight(30000) == 0.0
 
 
 def test_loss_defaults_and_invalid_args():

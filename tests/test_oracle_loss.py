@@ -85,3 +85,42 @@ def test_loss_gradients_match_central_differences():
         assert abs(fd - ad) <= 1e-6 * max(1.0, abs(ad)) + 1e-8, (name, idx, fd, ad)
         checked += 1
     assert checked >= 30
+
+
+def test_ssim_of_affinely_related_images_closed_form():
+    """y = alpha x + beta: sigma_y^2 = alpha^2 sigma_x^2 and sigma_xy =
+    alpha sigma_x^2, so SSIM reduces to a function of scipy-filtered mean
+    and variance of x alone -- pins the cross term and the variance terms."""
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, (1, 21, 19))
+    alpha, beta = -0.6, 0.7
+    y = alpha * x + beta
+    f = lambda a: ndi.gaussian_filter(a, sigma=1.5, mode="constant", cval=0.0, truncate=5.0 / 1.5)  # noqa: E731
+    mx = f(x[0])
+    vx = f(x[0] * x[0]) - mx * mx
+    # the window sums run over the zero padding too, so y's mean is
+    # alpha mx + beta * (window mass inside the image)
+    mass = f(np.ones_like(x[0]))
+    my = alpha * mx + beta * mass
+    vy = f(y[0] * y[0]) - my * my
+    cxy = f(x[0] * y[0]) - mx * my
+    inner = (slice(5, -5), slice(5, -5))       # mass = 1 there: vy = a^2 vx, cxy = a vx
+    assert np.allclose(vy[inner], alpha ** 2 * vx[inner], atol=1e-12)
+    assert np.allclose(cxy[inner], alpha * vx[inner], atol=1e-12)
+    want = ((2 * mx * my + LO.C1) / (mx ** 2 + my ** 2 + LO.C1)
+            * (2 * alpha * vx + LO.C2) / ((1 + alpha ** 2) * vx + LO.C2))
+    got = LO.ssim_map(torch.tensor(x), torch.tensor(y)).numpy()[0]
+    assert np.abs(got[inner] - want[inner]).max() < 1e-12
+
+
+def test_transmittance_mask_special_values():
+    """M_T is 1/2 at T = 1/2 and tends to 1 (mesh dominates) as T -> 1 and
+    to 0 as T -> 0 (Sec. 3.4): L_t at those constant transmittances."""
+    rng = np.random.default_rng(5)
+    vs = _views(rng, shapes=((6, 8),))
+    n = vs[0]["x"].size
+    base = (vs[0]["hit"][None] * (vs[0]["y"] - vs[0]["m"]) ** 2).sum() / n
+    for T0, scale in ((0.5, 0.5), (1.0, 1.0), (0.0, 0.0)):
+        vs[0]["T"] = np.full_like(vs[0]["T"], T0)
+        (_, _, lt, _), _, gm = LO.loss_and_grads(vs)
+        assert abs(lt - scale * base) <= 5e-5 * base + 1e-15, (T0, lt, base)
