@@ -386,20 +386,11 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     }
 }
 
-__device__ __forceinline__ float ratio_ff(double x, float zf, float zl, float rz) {
-    float xf = __double2float_rn(x);
-    float xl = __double2float_rn(x - (double)xf);
-    float q0 = xf * rz;
-    float e = fmaf(-q0, zf, xf);
-    e += xl - q0 * zl;
-    return fmaf(e, rz, q0);
-}
-
 template <int DEG, bool F16>
 __global__ void __launch_bounds__(128, 4)
 project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
                    const float *__restrict__ scales, const float *__restrict__ quats,
-                   const float *__restrict__ opac, const void *__restrict__ sh_raw, float near_z,
+                   const float *__restrict__ opac, const void *__restrict__ sh_raw,
                    const float *__restrict__ g2d, float *__restrict__ d_means,
                    float *__restrict__ d_scales, float *__restrict__ d_quats,
                    float *__restrict__ d_opac, float *__restrict__ d_sh) {
@@ -435,7 +426,6 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 #pragma unroll
     for (int k = 0; k < K * 3; ++k) gsh[k][tl] = 0.f;
     float gop = 0.f;
-    const double dxw = mx, dyw = my, dzw = mz;
     for (int v = 0; v < vt.n_views; ++v) {
         const float *gg = g2d + ((size_t)v * n + i) * kG;
         float g[kG];
@@ -445,16 +435,18 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
             g[q] = gg[q];
             any |= g[q] != 0.f;
         }
+        // a record with gradient was blended, so the forward kept it (its
+        // FP64-rounded depth passed the near plane); the Jacobian only needs
+        // the view position to FP32 accuracy, so it is recomputed in FP32
+        // here (the FP64 pipe is ~1/64 of the FP32 rate)
         if (!any) continue;
         const ViewDev &V = vt.v[v];
-        const double tzd = fma((double)V.R[6], dxw, fma((double)V.R[7], dyw, fma((double)V.R[8], dzw, (double)V.t[2])));
-        const float zf = __double2float_rn(tzd);
-        if (!(zf > near_z)) continue;
-        const double txd = fma((double)V.R[0], dxw, fma((double)V.R[1], dyw, fma((double)V.R[2], dzw, (double)V.t[0])));
-        const double tyd = fma((double)V.R[3], dxw, fma((double)V.R[4], dyw, fma((double)V.R[5], dzw, (double)V.t[1])));
-        const float zl = __double2float_rn(tzd - (double)zf);
+        const float zf = fmaf(V.R[6], mx, fmaf(V.R[7], my, fmaf(V.R[8], mz, V.t[2])));
+        if (!(zf > 0.f)) continue;
+        const float txf = fmaf(V.R[0], mx, fmaf(V.R[1], my, fmaf(V.R[2], mz, V.t[0])));
+        const float tyf = fmaf(V.R[3], mx, fmaf(V.R[4], my, fmaf(V.R[5], mz, V.t[1])));
         const float rz = __frcp_rn(zf);
-        const float rx = ratio_ff(txd, zf, zl, rz), ry = ratio_ff(tyd, zf, zl, rz);
+        const float rx = txf * rz, ry = tyf * rz;
         const float limx = 1.3f * (0.5f * (float)V.W / V.fx), limy = 1.3f * (0.5f * (float)V.H / V.fy);
         const bool inx = rx > -limx && rx < limx, iny = ry > -limy && ry < limy;
         const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
@@ -608,14 +600,14 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 
 template <int DEG>
 cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const float *scales,
-                        const float *quats, const float *opac, const void *sh, bool f16, float near_z,
+                        const float *quats, const float *opac, const void *sh, bool f16,
                         const float *g2d, float *dm, float *ds, float *dq, float *dop, float *dsh,
                         cudaStream_t s) {
     dim3 grid((n + 127) / 128);
     if (f16)
-        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, g2d, dm, ds, dq, dop, dsh);
+        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, g2d, dm, ds, dq, dop, dsh);
     else
-        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, g2d, dm, ds, dq, dop, dsh);
+        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, g2d, dm, ds, dq, dop, dsh);
     return cudaGetLastError();
 }
 
@@ -698,10 +690,10 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (!(stages & HM_BWD_PROJECT)) return HM_OK;
     const bool f16 = sh_format == HM_SH_F16;
     switch (sh_degree) {
-        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
     }
     return cuda_status(e);
 }

@@ -172,7 +172,8 @@ def test_stream_overlap_gives_the_sequential_results():
     gen.manual_seed(6)
     dI = torch.randn(3 * r.npix, device="cuda", generator=gen)
     r.forward(*_params(P), mesh, overlap=False)
-    seq = {k: getattr(r, k).clone() for k in ("rgb", "T", "n_contrib", "mesh_depth", "tri_id")}
+    seq = {k: getattr(r, k).clone() for k in ("rgb", "T", "n_contrib", "mesh_depth", "tri_id", "mesh_rgb",
+                                               "uv", "tile_max", "ranges")}
     g_seq = r.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True, overlap=False)
     r.forward(*_params(P), mesh, overlap=True)
     g_ovl = r.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True, overlap=True)
