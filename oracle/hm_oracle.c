@@ -352,14 +352,28 @@ void or_sh_basis(int deg, const double *d, double *Y) {
  *   visible[i]   1 iff the FP32 depth key z > 0.2 and det(Sigma') > 0
  *   depth[i]     FP32 depth key (defined for every Gaussian)
  *   mean2d[2i..] projected mean in pixels (continuous coordinates)
- *   cov2d[3i..]  Sigma' (xx, xy, yy) including the 0.3 dilation
+ *   cov2d[3i..]  Sigma' (xx, xy, yy) including the screen-space kernel
  *   conic[3i..]  Sigma'^{-1} (xx, xy, yy)
  *   color[3i..]  max(0, 0.5 + SH(view direction))
  *   clamped[3i+ch] 1 iff the colour channel was clamped at 0
+ *   opac_scale[i] factor on the opacity (1 without the Mip-Splatting filters)
+ *
+ * Filters (the 3DGS defaults: filt3d NULL, kernel2d 0.3, antialias 0).
+ * Mip-Splatting (Yu et al., CVPR 2024), the second Gaussian back-end the
+ * paper pairs with the mesh (Tab. 1), low-passes every Gaussian twice:
+ *   - 3D smoothing: Sigma + v_i I with a per-Gaussian variance v_i = filt3d[i]
+ *     (from the cameras' sampling rates, see the Python front end); as R is
+ *     orthonormal this is R diag(s_k^2 + v_i) R^T, and the opacity is scaled
+ *     by sqrt(det Sigma / det(Sigma + v_i I)) = prod_k s_k / sqrt(s_k^2 + v_i);
+ *   - 2D Mip filter: Sigma2D + kernel2d I (kernel2d 0.1, a one-pixel box
+ *     approximated by a Gaussian) instead of the 0.3 dilation, and with
+ *     antialias the opacity is scaled by sqrt(det Sigma2D / det(Sigma2D +
+ *     kernel2d I)) (0 where det Sigma2D <= 0).
  */
 void or_project(const double *cam, int W, int H, int n, const double *means, const double *scales,
-                const double *quats, const double *sh, int sh_degree, int *visible, float *depth,
-                double *mean2d, double *cov2d, double *conic, double *color, int *clamped) {
+                const double *quats, const double *sh, int sh_degree, const double *filt3d,
+                double kernel2d, int antialias, int *visible, float *depth, double *mean2d,
+                double *cov2d, double *conic, double *color, int *clamped, double *opac_scale) {
     const double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
     const double limx = 1.3 * (0.5 * W / fx), limy = 1.3 * (0.5 * H / fy);
     const int K = (sh_degree + 1) * (sh_degree + 1);
@@ -376,6 +390,7 @@ void or_project(const double *cam, int W, int H, int n, const double *means, con
         visible[i] = 0;
         mean2d[2 * i] = mean2d[2 * i + 1] = 0;
         for (int k = 0; k < 3; k++) cov2d[3 * i + k] = conic[3 * i + k] = color[3 * i + k] = 0, clamped[3 * i + k] = 0;
+        opac_scale[i] = 1.0;
         if (!(zf > 0.2f)) continue;
         /* rotation from the normalised quaternion (w,x,y,z) */
         const double *q = quats + 4 * (int64_t)i;
@@ -386,11 +401,17 @@ void or_project(const double *cam, int W, int H, int n, const double *means, con
             {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
             {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
         const double *s = scales + 3 * (int64_t)i;
+        const double v3 = filt3d ? filt3d[i] : 0.0;
+        double rho3 = 1.0, s2k[3];
+        for (int k = 0; k < 3; k++) {
+            s2k[k] = s[k] * s[k] + v3;
+            if (v3 > 0) rho3 *= s[k] / sqrt(s2k[k]);
+        }
         double Sig[3][3];
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) {
                 double acc = 0;
-                for (int k = 0; k < 3; k++) acc += Rq[a][k] * s[k] * s[k] * Rq[b][k];
+                for (int k = 0; k < 3; k++) acc += Rq[a][k] * s2k[k] * Rq[b][k];
                 Sig[a][b] = acc;
             }
         /* J with the half-FOV clamp of the view-space x/z, y/z */
@@ -415,10 +436,16 @@ void or_project(const double *cam, int W, int H, int n, const double *means, con
                     for (int l = 0; l < 3; l++) acc += T[a][k] * Sig[k][l] * T[b][l];
                 S2[a][b] = acc;
             }
-        double a_ = S2[0][0] + 0.3, b_ = S2[0][1], c_ = S2[1][1] + 0.3;
+        double a_ = S2[0][0] + kernel2d, b_ = S2[0][1], c_ = S2[1][1] + kernel2d;
         double det = a_ * c_ - b_ * b_;
         if (!(det > 0)) continue;
         visible[i] = 1;
+        double rho2 = 1.0;
+        if (antialias) {
+            const double det0 = S2[0][0] * S2[1][1] - S2[0][1] * S2[0][1];
+            rho2 = det0 > 0 ? sqrt(det0 / det) : 0.0;
+        }
+        opac_scale[i] = rho3 * rho2;
         cov2d[3 * i] = a_; cov2d[3 * i + 1] = b_; cov2d[3 * i + 2] = c_;
         conic[3 * i] = c_ / det; conic[3 * i + 1] = -b_ / det; conic[3 * i + 2] = a_ / det;
         mean2d[2 * i] = fx * tx / tz + cx;

@@ -139,13 +139,17 @@ def sh_basis(deg: int, d) -> np.ndarray:
     return out
 
 
-def project(cam, g, W=None, H=None):
+def project(cam, g, W=None, H=None, filt3d=None, kernel2d=0.3, antialias=False):
+    """Projection of every Gaussian for one camera; ``filt3d`` (per-Gaussian
+    3D filter variance), ``kernel2d`` and ``antialias`` select the
+    Mip-Splatting filters (``opac_scale`` is the opacity factor they imply)."""
     W = int(cam.width) if W is None else W
     H = int(cam.height) if H is None else H
     n = int(np.asarray(g.means).shape[0])
     c = cam_array(cam)
     means, scales, quats = _d(g.means), _d(g.scales), _d(g.quats)
     sh = _d(np.asarray(g.sh).astype(np.float64))
+    f3 = _d(filt3d) if filt3d is not None else None
     vis = np.empty(n, np.int32)
     dep = np.empty(n, np.float32)
     m2 = np.empty((n, 2))
@@ -153,10 +157,37 @@ def project(cam, g, W=None, H=None):
     con = np.empty((n, 3))
     col = np.empty((n, 3))
     clamped = np.empty((n, 3), np.int32)
+    osc = np.empty(n)
     lib().or_project(_p(c), W, H, n, _p(means), _p(scales), _p(quats), _p(sh), int(g.sh_degree),
-                     _p(vis), _p(dep), _p(m2), _p(cov), _p(con), _p(col), _p(clamped))
+                     _p(f3) if f3 is not None else None, ctypes.c_double(kernel2d), int(bool(antialias)),
+                     _p(vis), _p(dep), _p(m2), _p(cov), _p(con), _p(col), _p(clamped), _p(osc))
     return SimpleNamespace(visible=vis, depth=dep, mean2d=m2, cov2d=cov, conic=con, color=col,
-                           clamped=clamped)
+                           clamped=clamped, opac_scale=osc)
+
+
+def filter_3d(cameras, means, s2=0.2, near=0.2):
+    """Mip-Splatting's 3D smoothing-filter variance per Gaussian (Yu et al.,
+    CVPR 2024): v = s2 / nu^2 with nu the largest sampling rate f / z over
+    the cameras that see the Gaussian's centre, f = max(fx, fy), z its view
+    depth.  Readings: a camera sees the centre iff z > near and the
+    projected centre lies in [0, W] x [0, H]; a Gaussian no camera sees gets
+    v = 0 (no filter).  Plain FP64 numpy."""
+    m = np.asarray(means, np.float64)
+    best = np.zeros(len(m))                   # largest f / z so far (0: unseen)
+    for cam in cameras:
+        c = cam_array(cam)
+        R, t = c[:9].reshape(3, 3), c[9:12]
+        fx, fy, cx, cy = c[12:16]
+        p = m @ R.T + t
+        z = p[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = fx * p[:, 0] / z + cx
+            w = fy * p[:, 1] / z + cy
+            rate = max(fx, fy) / z
+        seen = (z > near) & (u >= 0) & (u <= cam.width) & (w >= 0) & (w <= cam.height)
+        best = np.where(seen & (rate > best), rate, best)
+    with np.errstate(divide="ignore"):
+        return np.where(best > 0, s2 / (best * best), 0.0)
 
 
 def sort_order(proj) -> np.ndarray:
@@ -220,10 +251,11 @@ def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, cell
 
 
 def render(scene, view=0, pix=None, eps=DEFAULT_EPS, mode="brute", gaussians=None, tex=None,
-           rows=None, znear=0.01):
+           rows=None, znear=0.01, filt3d=None, kernel2d=0.3, antialias=False):
     """Full hybrid render of one view: mesh pass, projection, blend.  Returns
     a namespace with the mesh pass (``mesh``), the projection (``proj``) and
-    the blend (``out``)."""
+    the blend (``out``).  ``filt3d``, ``kernel2d``, ``antialias``: the
+    Mip-Splatting filters (see ``project``)."""
     cam = scene.cameras[view]
     g = scene.gaussians if gaussians is None else gaussians
     bg = np.asarray(scene.bg, np.float64)
@@ -235,9 +267,10 @@ def render(scene, view=0, pix=None, eps=DEFAULT_EPS, mode="brute", gaussians=Non
         mr = mesh_raster(cam, scene.mesh, bg=bg, znear=znear, pix=pix, tex=tex)
     else:
         mr = empty_mesh_result(n, bg)
-    pr = project(cam, g)
+    pr = project(cam, g, filt3d=filt3d, kernel2d=kernel2d, antialias=antialias)
+    opac = np.asarray(g.opacity, np.float64) * pr.opac_scale
     if mode == "grid":
-        out = blend_grid(cam, pr, g.opacity, mr, bg=bg, eps=eps, rows=rows)
+        out = blend_grid(cam, pr, opac, mr, bg=bg, eps=eps, rows=rows)
     else:
-        out = blend(cam, pr, g.opacity, mr, bg=bg, eps=eps, pix=pix)
+        out = blend(cam, pr, opac, mr, bg=bg, eps=eps, pix=pix)
     return SimpleNamespace(mesh=mr, proj=pr, out=out)

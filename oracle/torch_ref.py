@@ -85,9 +85,11 @@ def quat_to_rot(q):
     ], 1)
 
 
-def project_torch(cam, means, scales, quats, sh, sh_degree):
+def project_torch(cam, means, scales, quats, sh, sh_degree, filt3d=None, kernel2d=0.3, antialias=False):
     """Differentiable projection of every Gaussian (visibility decided
-    elsewhere).  Returns mean2d [N,2], conic [N,3] (xx,xy,yy), color [N,3]."""
+    elsewhere).  Returns mean2d [N,2], conic [N,3] (xx,xy,yy), color [N,3]
+    and the opacity factor [N] of the Mip-Splatting filters (1 without them;
+    the 3D filter variance ``filt3d`` is a constant, not differentiated)."""
     c = O.cam_array(cam)
     Rc = _t(c[:9].reshape(3, 3))
     tc = _t(c[9:12])
@@ -102,15 +104,27 @@ def project_torch(cam, means, scales, quats, sh, sh_degree):
     J = torch.stack([torch.stack([fx / tz, zero, -fx * txz / tz], 1),
                      torch.stack([zero, fy / tz, -fy * tyz / tz], 1)], 1)        # [N,2,3]
     Rq = quat_to_rot(quats)
-    M = Rq * scales[:, None, :]
+    if filt3d is not None:
+        v = _t(filt3d)[:, None]
+        s_eff = torch.sqrt(scales * scales + v)                 # Sigma + v I = R diag(s^2 + v) R^T
+        rho3 = torch.prod(scales / s_eff, dim=1)
+    else:
+        s_eff = scales
+        rho3 = torch.ones_like(tz)
+    M = Rq * s_eff[:, None, :]
     Sig = M @ M.transpose(1, 2)
     T = J @ Rc                                                                      # [N,2,3]
     S2 = T @ Sig @ T.transpose(1, 2)
-    a = S2[:, 0, 0] + 0.3
+    a = S2[:, 0, 0] + kernel2d
     b = S2[:, 0, 1]
-    cc = S2[:, 1, 1] + 0.3
+    cc = S2[:, 1, 1] + kernel2d
     det = a * cc - b * b
     conic = torch.stack([cc / det, -b / det, a / det], 1)
+    if antialias:
+        det0 = S2[:, 0, 0] * S2[:, 1, 1] - b * b
+        rho2 = torch.sqrt(torch.clamp(det0, min=0.0) / det)
+    else:
+        rho2 = torch.ones_like(tz)
     mean2d = torch.stack([fx * tx / tz + cx, fy * ty / tz + cy], 1)
     C = -(Rc.T @ tc)
     d = means - C
@@ -118,7 +132,7 @@ def project_torch(cam, means, scales, quats, sh, sh_degree):
     Y = sh_basis_torch(sh_degree, d)                                                # [N,K]
     col = 0.5 + torch.einsum("nk,nkc->nc", Y, sh)
     col = torch.clamp(col, min=0.0)
-    return mean2d, conic, col
+    return mean2d, conic, col, rho3 * rho2
 
 
 # --------------------------------------------------------------------------
@@ -179,7 +193,8 @@ def blend_torch(pxy, mean2d, conic, opacity, color, depth_f32, order, hit, Dm, I
     return rgb, T
 
 
-def render_grad(scene, view, gI, gT=None, pix=None, gaussians=None, tex=None, chunk=1024):
+def render_grad(scene, view, gI, gT=None, pix=None, gaussians=None, tex=None, chunk=1024, filt3d=None,
+                kernel2d=0.3, antialias=False):
     """Gradient of L = sum_p gI[:,p] . I_h(p) + gT[p] T(p) over the listed
     pixels (all if None) of one view, with respect to means, scales, quats,
     opacity, sh (all as given, i.e. activated) and, if the scene has a mesh,
@@ -197,7 +212,7 @@ def render_grad(scene, view, gI, gT=None, pix=None, gaussians=None, tex=None, ch
         mr = O.mesh_raster(cam, scene.mesh, bg=bg, pix=pix, tex=texture)
     else:
         mr = O.empty_mesh_result(len(pix), bg)
-    pr = O.project(cam, g)
+    pr = O.project(cam, g, filt3d=filt3d, kernel2d=kernel2d, antialias=antialias)
     order = O.sort_order(pr)
 
     means = _t(g.means).requires_grad_()
@@ -206,12 +221,14 @@ def render_grad(scene, view, gI, gT=None, pix=None, gaussians=None, tex=None, ch
     opac = _t(g.opacity).requires_grad_()
     sh = _t(np.asarray(g.sh).astype(np.float64)).requires_grad_()
     texT = _t(texture).requires_grad_() if texture is not None else None
-    mean2d, conic, color = project_torch(cam, means, scales, quats, sh, g.sh_degree)
+    mean2d, conic, color, osc = project_torch(cam, means, scales, quats, sh, g.sh_degree, filt3d=filt3d,
+                                              kernel2d=kernel2d, antialias=antialias)
+    opac_eff = opac * osc
     # blend against detached leaves, then push their gradients through the projection
     l_m2 = mean2d.detach().requires_grad_()
     l_co = conic.detach().requires_grad_()
     l_cl = color.detach().requires_grad_()
-    l_op = opac.detach().requires_grad_()
+    l_op = opac_eff.detach().requires_grad_()
     gI = np.asarray(gI, np.float64).reshape(3, -1)
     gT = np.zeros(len(pix)) if gT is None else np.asarray(gT, np.float64)
     loss = 0.0
@@ -231,7 +248,7 @@ def render_grad(scene, view, gI, gT=None, pix=None, gaussians=None, tex=None, ch
         L = (rgb * _t(gI[:, s:e].T)).sum() + (T * _t(gT[s:e])).sum()
         L.backward()
         loss += float(L.detach())
-    outs, grads = [mean2d, conic, color, opac], [l_m2.grad, l_co.grad, l_cl.grad, l_op.grad]
+    outs, grads = [mean2d, conic, color, opac_eff], [l_m2.grad, l_co.grad, l_cl.grad, l_op.grad]
     keep = [(o, gr) for o, gr in zip(outs, grads) if gr is not None]
     torch.autograd.backward([o for o, _ in keep], [gr for _, gr in keep])
     leaves = dict(means=(means, g.means), scales=(scales, g.scales), quats=(quats, g.quats),
@@ -243,7 +260,8 @@ def render_grad(scene, view, gI, gT=None, pix=None, gaussians=None, tex=None, ch
     return loss, res
 
 
-def render_forward(scene, view, pix=None, gaussians=None, tex=None):
+def render_forward(scene, view, pix=None, gaussians=None, tex=None, filt3d=None, kernel2d=0.3,
+                   antialias=False):
     """Forward only (for cross-checking against the C oracle)."""
     cam = scene.cameras[view]
     g = scene.gaussians if gaussians is None else gaussians
@@ -257,15 +275,16 @@ def render_forward(scene, view, pix=None, gaussians=None, tex=None):
     else:
         texture = None
         mr = O.empty_mesh_result(len(pix), bg)
-    pr = O.project(cam, g)
+    pr = O.project(cam, g, filt3d=filt3d, kernel2d=kernel2d, antialias=antialias)
     order = O.sort_order(pr)
     with torch.no_grad():
-        mean2d, conic, color = project_torch(cam, _t(g.means), _t(g.scales), _t(g.quats),
-                                             _t(np.asarray(g.sh).astype(np.float64)), g.sh_degree)
+        mean2d, conic, color, osc = project_torch(cam, _t(g.means), _t(g.scales), _t(g.quats),
+                                                  _t(np.asarray(g.sh).astype(np.float64)), g.sh_degree,
+                                                  filt3d=filt3d, kernel2d=kernel2d, antialias=antialias)
         q = np.asarray(pix)
         pxy = _t(np.stack([q % W + 0.5, q // W + 0.5], 1))
         hit = mr.tri_id >= 0
         Im = _t(mr.rgb.T.copy())
-        rgb, T = blend_torch(pxy, mean2d, conic, _t(g.opacity), color, pr.depth, order, hit,
+        rgb, T = blend_torch(pxy, mean2d, conic, _t(g.opacity) * osc, color, pr.depth, order, hit,
                              mr.depth, Im)
     return SimpleNamespace(rgb=rgb.numpy().T, T=T.numpy(), mesh=mr, proj=pr)

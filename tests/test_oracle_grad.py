@@ -24,14 +24,17 @@ def _as64(g):
                            sh=np.array(g.sh, np.float64), sh_degree=g.sh_degree)
 
 
-def _loss(scene, g, tex, gI, gT):
-    r = O.render(scene, gaussians=g, tex=tex)
+def _loss(scene, g, tex, gI, gT, flt):
+    r = O.render(scene, gaussians=g, tex=tex, **flt)
     L = float((r.out.rgb * gI).sum() + (r.out.T * gT).sum())
     key = (r.out.fp.tobytes(), r.proj.clamped.tobytes(), r.proj.visible.tobytes())
     return L, key
 
 
-def _check(scene, n_per_kind, seed, rtol=2e-5):
+def _check(scene, n_per_kind, seed, rtol=2e-5, flt=None):
+    """``flt``: projection filter options (the Mip-Splatting ones) passed to
+    both oracles."""
+    flt = dict(flt or {})
     rng = np.random.default_rng(seed)
     cam = scene.cameras[0]
     npx = cam.n_pixels
@@ -39,8 +42,8 @@ def _check(scene, n_per_kind, seed, rtol=2e-5):
     gT = rng.standard_normal(npx)
     g = _as64(scene.gaussians)
     tex = O.texture_unit(scene.mesh.texture).copy() if scene.mesh is not None else None
-    _, grads = TR.render_grad(scene, 0, gI, gT, gaussians=g, tex=tex)
-    base = O.render(scene, gaussians=g, tex=tex)
+    _, grads = TR.render_grad(scene, 0, gI, gT, gaussians=g, tex=tex, **flt)
+    base = O.render(scene, gaussians=g, tex=tex, **flt)
     # Gaussians that are blended somewhere (non-trivial gradients)
     contributing = np.nonzero(np.abs(grads["opacity"]) > 1e-3)[0]
     assert len(contributing) > 20
@@ -71,9 +74,9 @@ def _check(scene, n_per_kind, seed, rtol=2e-5):
             # |dL| / h with |dL| ~ 1e-13 for this loss stays ~1e-8 at h = 1e-5 |v|
             h = 1e-5 * max(abs(v0), 1e-2)
             arr[idx] = v0 + h
-            Lp, kp = _loss(scene, g, tex, gI, gT)
+            Lp, kp = _loss(scene, g, tex, gI, gT, flt)
             arr[idx] = v0 - h
-            Lm, km = _loss(scene, g, tex, gI, gT)
+            Lm, km = _loss(scene, g, tex, gI, gT, flt)
             arr[idx] = v0
             k0 = (base.out.fp.tobytes(), base.proj.clamped.tobytes(), base.proj.visible.tobytes())
             if kp != k0 or km != k0:
