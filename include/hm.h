@@ -94,6 +94,10 @@ typedef struct hm_options {
     int32_t bwd_stages;      /* hm_blend_backward parts to run (HM_BWD_* bits; 0 = all) */
     int32_t ellipse_cull;    /* 1: bin a Gaussian only into tiles whose pixel-centre
                                 rectangle its 3-sigma ellipse reaches (result-preserving) */
+    float kernel_2d;         /* variance (px^2) added to the projected covariance: 0.3 the
+                                3DGS dilation, 0.1 the 2D Mip filter of Mip-Splatting */
+    int32_t antialias;       /* 1: scale each opacity by sqrt(det Sigma2D / det(Sigma2D +
+                                kernel_2d I)) (Mip-Splatting's 2D Mip filter) */
 } hm_options;
 
 /* hm_blend_backward parts.  HM_BWD_PROJECT consumes the per-record partials
@@ -105,7 +109,7 @@ typedef struct hm_options {
 
 /* Fill `opt` with the defaults: 16x16 tiles, batch 256, mesh_cull 1,
  * ellipse_cull 1, near planes 0.2 / 0.01, black background, all backward
- * parts. */
+ * parts, the 3DGS screen-space kernel (kernel_2d 0.3, antialias 0). */
 void hm_default_options(hm_options *opt);
 
 /* Thread-local text of the last host-side error. */
@@ -149,20 +153,42 @@ hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, const float 
 /* hm_project_gaussians -- Eq. 1 and Sec. 3.1: per (camera, Gaussian) the
  * 48-byte record consumed by hm_bin_sort / hm_blend_*:
  *   mean2d (FP32 pixels), conic = Sigma'^-1 (xx, xy, yy) with
- *   Sigma' = J W R S S^T R^T W^T J^T + 0.3 I (J: affine Jacobian with the view
- *   x/z, y/z clamped to 1.3 x the half field of view), opacity, depth key
+ *   Sigma' = J W R S S^T R^T W^T J^T + kernel_2d I (J: affine Jacobian with the
+ *   view x/z, y/z clamped to 1.3 x the half field of view), opacity, depth key
  *   z = fp32(fma(R20,x,fma(R21,y,fma(R22,z,t2)))) in FP64, colour
  *   max(0, 0.5 + SH(normalised mean - camera centre)) and the tile rectangle
  *   covering the 3-sigma ellipse d^2 <= 9.  Culled (z <= near_gauss, or no
  *   tile) records carry an empty rectangle.
+ *  filter_3d [n] float32 >= 0 or NULL: the per-Gaussian variance v of
+ *   Mip-Splatting's 3D smoothing filter (hm_mip_filter_3d): the covariance
+ *   becomes R (S^2 + v I) R^T and the opacity is scaled by
+ *   prod_k s_k / sqrt(s_k^2 + v).  With opt->antialias the opacity is also
+ *   scaled by sqrt(det Sigma2D / det Sigma') (Mip-Splatting's 2D Mip filter,
+ *   kernel_2d 0.1).  The paper pairs the mesh with this back-end (Tab. 1).
  *  sh [n][(sh_degree+1)^2][3] in sh_format; sh_degree 0..3.
  *  records: n_views*n*48 bytes, 16-byte aligned.
  */
 hm_status hm_project_gaussians(const hm_camera *cams, int32_t n_views, int32_t n,
                                const float *means, const float *scales, const float *quats,
-                               const float *opacity, const void *sh, int32_t sh_degree,
-                               int32_t sh_format, const hm_options *opt, void *records,
-                               void *stream);
+                               const float *opacity, const float *filter_3d, const void *sh,
+                               int32_t sh_degree, int32_t sh_format, const hm_options *opt,
+                               void *records, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* hm_mip_filter_3d -- the variance of Mip-Splatting's 3D smoothing filter per
+ * Gaussian (Yu et al., CVPR 2024; the second back-end of Tab. 1):
+ *   v_i = s2 / nu_i^2,  nu_i = max over the cameras that see mean i of f / z,
+ * f = max(fx, fy), z the FP32 view depth; a camera sees the mean iff
+ * z > near_z and the projected mean lies in [0, W] x [0, H].  A Gaussian no
+ * camera sees gets v = 0.  s2 > 0 is the filter size in squared sampling
+ * intervals (Mip-Splatting: 0.2).  The cameras are the training views; the
+ * result is a constant of the projection (no gradient flows into it).
+ *  means [n][3] float32 (device); filter_3d [n] float32 (device, written).
+ *  Errors: HM_ERR_INVALID_ARG (cameras, n < 0, s2 <= 0, null pointers),
+ *  HM_ERR_CUDA.  Launches only.
+ */
+hm_status hm_mip_filter_3d(const hm_camera *cams, int32_t n_views, int32_t n, const float *means,
+                           float s2, float near_z, float *filter_3d, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* hm_bin_sort -- the tile-wise sort the paper's rasteriser relies on (Sec. 1:
@@ -217,9 +243,12 @@ hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, co
  * T * bilinear weight * dL/dI_h on pixels with a triangle).  Discrete
  * decisions (the blended set, clamps, the mesh hit) carry no gradient; vertex
  * positions and UVs get none.
- *  Inputs: the forward's parameters, records, sorted pairs and ranges, mesh
- *  outputs (depth, rgb, uv; NULL for no mesh), out_T and last_idx, and
- *  dL_drgb (planar, like out_rgb) and dL_dT (per pixel, may be NULL).
+ *  Inputs: the forward's parameters (with the same filter_3d and options:
+ *  the gradients follow the Mip-Splatting filters' opacity factors and the
+ *  3D filter's effective scales; v itself is a constant), records, sorted
+ *  pairs and ranges, mesh outputs (depth, rgb, uv; NULL for no mesh), out_T
+ *  and last_idx, and dL_drgb (planar, like out_rgb) and dL_dT (per pixel,
+ *  may be NULL).
  *  dL_dmesh (planar, may be NULL): the gradient of a loss on the mesh colour
  *  I_m itself (such as the texture loss of hm_hybrid_loss), added to the
  *  T * dL/dI_h the texels receive through the composite.
@@ -231,7 +260,8 @@ hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, co
 size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n);
 hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, const float *means,
                             const float *scales, const float *quats, const float *opacity,
-                            const void *sh, int32_t sh_degree, int32_t sh_format,
+                            const float *filter_3d, const void *sh, int32_t sh_degree,
+                            int32_t sh_format,
                             const void *records, const uint32_t *pair_vals,
                             const uint32_t *tile_ranges, const float *mesh_depth,
                             const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
@@ -262,8 +292,8 @@ hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, c
 #define HM_BWD_NOALLOC_BYTES (16u << 20)
 hm_status hm_blend_backward_noalloc(const hm_camera *cams, int32_t n_views, int32_t n,
                                     const float *means, const float *scales, const float *quats,
-                                    const float *opacity, const void *sh, int32_t sh_degree,
-                                    int32_t sh_format, const void *records,
+                                    const float *opacity, const float *filter_3d, const void *sh,
+                                    int32_t sh_degree, int32_t sh_format, const void *records,
                                     const uint32_t *pair_vals, const uint32_t *tile_ranges,
                                     const float *mesh_depth, const float *mesh_rgb,
                                     const float *mesh_uv, int32_t tex_w, int32_t tex_h,

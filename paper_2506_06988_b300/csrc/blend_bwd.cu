@@ -390,7 +390,7 @@ template <int DEG, bool F16>
 __global__ void __launch_bounds__(128, 4)
 project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
                    const float *__restrict__ scales, const float *__restrict__ quats,
-                   const float *__restrict__ opac, const void *__restrict__ sh_raw,
+                   const float *__restrict__ opac, const void *__restrict__ sh_raw, Filters flt,
                    const float *__restrict__ g2d, float *__restrict__ d_means,
                    float *__restrict__ d_scales, float *__restrict__ d_quats,
                    float *__restrict__ d_opac, float *__restrict__ d_sh) {
@@ -404,6 +404,19 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
     const int tl = threadIdx.x;
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
     const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+    // Mip-Splatting's 3D filter: effective scales se_k = sqrt(s_k^2 + v) and
+    // the opacity factor rho3 = prod_k s_k / se_k (v is a constant)
+    const float v3 = flt.f3d ? flt.f3d[i] : 0.f;
+    float se[3] = {s[0], s[1], s[2]}, rho3 = 1.f;
+    if (v3 > 0.f) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            se[k] = sqrtf(fmaf(s[k], s[k], v3));
+            rho3 *= s[k] / se[k];
+        }
+    }
+    const float op_i = opac[i];
+    float g_rho3 = 0.f;                 // dL/drho3 over the views
     const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
     const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
     const float qinv = rsqrtf(qn2);
@@ -415,7 +428,7 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) M[a][k] = R[a][k] * s[k];
+        for (int k = 0; k < 3; ++k) M[a][k] = R[a][k] * se[k];
     // SH coefficients are re-read (L1-resident after the first view) where
     // they are used instead of being held across the view loop
     const __half *sh_h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
@@ -463,12 +476,15 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
             V0[k] = T0[0] * M[0][k] + T0[1] * M[1][k] + T0[2] * M[2][k];
             V1[k] = T1[0] * M[0][k] + T1[1] * M[1][k] + T1[2] * M[2][k];
         }
-        const float a = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2] + 0.3f;
-        const float c = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2] + 0.3f;
+        const float h = flt.kernel;
+        const float A0 = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2];
+        const float C0 = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2];
+        const float a = A0 + h, c = C0 + h;
         const float b = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
         const float cx_ = V0[1] * V1[2] - V0[2] * V1[1], cy_ = V0[2] * V1[0] - V0[0] * V1[2],
                     cz_ = V0[0] * V1[1] - V0[1] * V1[0];
-        const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + 0.3f * (a + c - 0.6f) + 0.09f;
+        const float det0 = cx_ * cx_ + cy_ * cy_ + cz_ * cz_;      // det(Sigma2D)
+        const float det = det0 + h * (A0 + C0) + h * h;
         const float rd2 = 1.f / (det * det);
         // the blend's moments S of dL/dq (q = K d^2): dL/dmean2d = -2K conic S_(dx,dy),
         // dL/dconic = K (S_dx2, 2 S_dxdy, S_dy2)
@@ -478,9 +494,23 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
         const float gmy = -2.f * kConicScale * (cxy * g[0] + cyy * g[1]);
         // conic (c/det, -b/det, a/det) -> Sigma' entries
         const float gA = kConicScale * g[2], gB = 2.f * kConicScale * g[3], gC = kConicScale * g[4];
-        const float ga = (-c * c * gA + b * c * gB - b * b * gC) * rd2;
-        const float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * rd2;
-        const float gc = (-b * b * gA + a * b * gB - a * a * gC) * rd2;
+        float ga = (-c * c * gA + b * c * gB - b * b * gC) * rd2;
+        float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * rd2;
+        float gc = (-b * b * gA + a * b * gB - a * a * gC) * rd2;
+        // the record's opacity is op rho3 rho2; with the 2D Mip filter
+        // rho2 = sqrt(D0 / D1), D0 = A0 C0 - b^2, D1 = (A0 + h)(C0 + h) - b^2, so
+        // drho2 = rho2 / 2 (dD0 / D0 - dD1 / D1)
+        float rho2 = 1.f;
+        if (flt.antialias) {
+            rho2 = det0 > 0.f ? sqrtf(det0 * rdet) : 0.f;
+            if (det0 > 0.f) {
+                const float k2 = 0.5f * g[5] * op_i * rho3 * rho2, r0 = 1.f / det0;
+                ga += k2 * (C0 * r0 - c * rdet);
+                gc += k2 * (A0 * r0 - a * rdet);
+                gb += 2.f * k2 * b * (rdet - r0);
+            }
+        }
+        g_rho3 += g[5] * op_i * rho2;
         // Sigma' = V V^T: dV0 = 2 ga V0 + gb V1, dV1 = gb V0 + 2 gc V1
         float gV0[3], gV1[3];
 #pragma unroll
@@ -527,7 +557,7 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
         // t = W mean + t_cam
 #pragma unroll
         for (int k = 0; k < 3; ++k) gmean[k] += V.R[k] * gtx + V.R[3 + k] * gty + V.R[6 + k] * gtz;
-        gop += g[5];
+        gop += g[5] * rho3 * rho2;
         // colour
         float d0 = mx - V.campos[0], d1 = my - V.campos[1], d2 = mz - V.campos[2];
         const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -565,8 +595,14 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             gs[k] += gM[a][k] * R[a][k];
-            gR[a][k] = gM[a][k] * s[k];
+            gR[a][k] = gM[a][k] * se[k];
         }
+    // through se_k = sqrt(s_k^2 + v) and rho3 = prod_j s_j / se_j:
+    // dse_k/ds_k = s_k / se_k, drho3/ds_k = rho3 v / (s_k se_k^2)
+    if (v3 > 0.f) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gs[k] = gs[k] * (s[k] / se[k]) + g_rho3 * rho3 * v3 / (s[k] * se[k] * se[k]);
+    }
     // R(q^) -> q^ (w, x, y, z)
     float gqw = 2.f * (qz * (gR[1][0] - gR[0][1]) + qy * (gR[0][2] - gR[2][0]) + qx * (gR[2][1] - gR[1][2]));
     float gqx = 2.f * (qy * (gR[0][1] + gR[1][0]) + qz * (gR[0][2] + gR[2][0]) + qw * (gR[2][1] - gR[1][2])) -
@@ -600,14 +636,14 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 
 template <int DEG>
 cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const float *scales,
-                        const float *quats, const float *opac, const void *sh, bool f16,
+                        const float *quats, const float *opac, const void *sh, bool f16, Filters flt,
                         const float *g2d, float *dm, float *ds, float *dq, float *dop, float *dsh,
                         cudaStream_t s) {
     dim3 grid((n + 127) / 128);
     if (f16)
-        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, g2d, dm, ds, dq, dop, dsh);
+        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, dm, ds, dq, dop, dsh);
     else
-        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, g2d, dm, ds, dq, dop, dsh);
+        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, dm, ds, dq, dop, dsh);
     return cudaGetLastError();
 }
 
@@ -624,8 +660,8 @@ extern "C" size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n) {
 
 extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n,
                                        const float *means, const float *scales, const float *quats,
-                                       const float *opacity, const void *sh, int32_t sh_degree,
-                                       int32_t sh_format, const void *records,
+                                       const float *opacity, const float *filter_3d, const void *sh,
+                                       int32_t sh_degree, int32_t sh_format, const void *records,
                                        const uint32_t *pair_vals, const uint32_t *tile_ranges,
                                        const float *mesh_depth, const float *mesh_rgb,
                                        const float *mesh_uv, int32_t tex_w, int32_t tex_h,
@@ -640,6 +676,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
     if (sh_degree < 0 || sh_degree > 3) return fail(HM_ERR_INVALID_ARG, "sh_degree must be 0..3");
     if (sh_format != HM_SH_F32 && sh_format != HM_SH_F16) return fail(HM_ERR_INVALID_ARG, "sh_format");
+    if (!(opt->kernel_2d >= 0.f && opt->kernel_2d < 1e6f)) return fail(HM_ERR_INVALID_ARG, "kernel_2d");
     if (opt->batch < 1 || opt->batch > opt->tile_w * opt->tile_h)
         return fail(HM_ERR_INVALID_ARG, "batch must be in 1..%d for this tile shape", opt->tile_w * opt->tile_h);
     if (!tile_ranges || !out_T || !last_idx || !dL_drgb) return fail(HM_ERR_INVALID_ARG, "null pointer");
@@ -657,6 +694,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     cudaError_t e;
     const float *bg = opt->bg;
     const int stages = opt->bwd_stages ? opt->bwd_stages : (HM_BWD_TEXTURE | HM_BWD_BLEND | HM_BWD_PROJECT);
+    const Filters flt{filter_3d, opt->kernel_2d, opt->antialias ? 1 : 0};
     if (d_tex && (stages & HM_BWD_TEXTURE)) {
         dim3 tg(vt.total_tiles);
 #define HM_TBWD(TW, TH) \
@@ -690,10 +728,10 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (!(stages & HM_BWD_PROJECT)) return HM_OK;
     const bool f16 = sh_format == HM_SH_F16;
     switch (sh_degree) {
-        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
     }
     return cuda_status(e);
 }
@@ -732,8 +770,8 @@ hm_status noalloc_scratch(void **out) {
 
 extern "C" hm_status hm_blend_backward_noalloc(
     const hm_camera *cams, int32_t n_views, int32_t n, const float *means, const float *scales,
-    const float *quats, const float *opacity, const void *sh, int32_t sh_degree, int32_t sh_format,
-    const void *records, const uint32_t *pair_vals, const uint32_t *tile_ranges,
+    const float *quats, const float *opacity, const float *filter_3d, const void *sh, int32_t sh_degree,
+    int32_t sh_format, const void *records, const uint32_t *pair_vals, const uint32_t *tile_ranges,
     const float *mesh_depth, const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
     int32_t tex_h, const hm_options *opt, const float *out_T, const uint32_t *last_idx,
     const float *dL_drgb, const float *dL_dT, float *d_means, float *d_scales, float *d_quats,
@@ -748,7 +786,7 @@ extern "C" hm_status hm_blend_backward_noalloc(
     void *ws = nullptr;
     const hm_status st = noalloc_scratch(&ws);
     if (st != HM_OK) return st;
-    return hm_blend_backward(cams, n_views, n, means, scales, quats, opacity, sh, sh_degree,
+    return hm_blend_backward(cams, n_views, n, means, scales, quats, opacity, filter_3d, sh, sh_degree,
                              sh_format, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb,
                              mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, nullptr,
                              d_means, d_scales, d_quats, d_opacity, d_sh, d_tex, d_status, ws,

@@ -89,6 +89,8 @@ extern "C" void hm_default_options(hm_options *opt) {
     opt->near_mesh = 0.01f;
     opt->bwd_stages = 0;
     opt->ellipse_cull = 1;
+    opt->kernel_2d = 0.3f;
+    opt->antialias = 0;
 }
 
 extern "C" const char *hm_last_error(void) { return g_err; }

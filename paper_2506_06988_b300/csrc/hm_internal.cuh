@@ -31,6 +31,16 @@ struct ViewTable {
 };
 
 // camera owning global tile `gt` (tile_off is increasing)
+// Screen-space kernel and the Mip-Splatting filters (see hm_options and
+// hm_project_gaussians): f3d the per-Gaussian 3D smoothing variance or null,
+// kernel the variance added to the projected covariance, antialias the 2D
+// Mip filter's opacity compensation.
+struct Filters {
+    const float *f3d;
+    float kernel;
+    int antialias;
+};
+
 __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int gt) {
     int v = 0;
     for (int k = 1; k < vt.n_views; ++k)

@@ -86,14 +86,24 @@ __global__ void __launch_bounds__(128)
 project_kernel(ViewTable vt, int n, const float *__restrict__ means,
                const float *__restrict__ scales, const float *__restrict__ quats,
                const float *__restrict__ opac, const void *__restrict__ sh_raw, float near_z,
-               Record *__restrict__ out) {
+               Filters flt, Record *__restrict__ out) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-    const float s0 = scales[3 * i], s1 = scales[3 * i + 1], s2 = scales[3 * i + 2];
+    float s0 = scales[3 * i], s1 = scales[3 * i + 1], s2 = scales[3 * i + 2];
     const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
-    const float op = opac[i];
+    float op = opac[i];
+    // Mip-Splatting's 3D smoothing filter: R S^2 R^T + v I = R (S^2 + v I) R^T,
+    // opacity scaled by prod_k s_k / sqrt(s_k^2 + v)
+    const float v3 = flt.f3d ? flt.f3d[i] : 0.f;
+    if (v3 > 0.f) {
+        const float e0 = sqrtf(fmaf(s0, s0, v3)), e1 = sqrtf(fmaf(s1, s1, v3)), e2 = sqrtf(fmaf(s2, s2, v3));
+        op *= (s0 / e0) * (s1 / e1) * (s2 / e2);
+        s0 = e0;
+        s1 = e1;
+        s2 = e2;
+    }
     float sh[K][3];
     if (F16) {
         const __half *h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
@@ -167,9 +177,13 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
             const float cx_ = diff_prod(V0[1], V1[2], V0[2], V1[1]);
             const float cy_ = diff_prod(V0[2], V1[0], V0[0], V1[2]);
             const float cz_ = diff_prod(V0[0], V1[1], V0[1], V1[0]);
-            const float a = A + 0.3f, c = C + 0.3f;
-            const float det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + 0.3f * (A + C) + 0.09f;
+            const float h = flt.kernel;
+            const float a = A + h, c = C + h;
+            const float det0 = cx_ * cx_ + cy_ * cy_ + cz_ * cz_;      // det(Sigma2D), Lagrange's identity
+            const float det = det0 + h * (A + C) + h * h;
             const float rd = 1.0f / det;
+            // 2D Mip filter: opacity x sqrt(det Sigma2D / det(Sigma2D + h I))
+            const float opv = flt.antialias ? op * sqrtf(det0 * rd) : op;
             // 3-sigma rectangle (inflated by 1e-4 relative + 1e-3 px: a superset)
             const float hx = 3.0f * sqrtf(a) * 1.0001f + 1e-3f;
             const float hy = 3.0f * sqrtf(c) * 1.0001f + 1e-3f;
@@ -201,7 +215,7 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
             }
             // conic (c, -B, a) / det, pre-multiplied by K (and 2K for xy)
             r.a = make_float4(u, w, __fmul_rn(kConicScale, c * rd), __fmul_rn(2.f * kConicScale, -B * rd));
-            r.b = make_float4(__fmul_rn(kConicScale, a * rd), op, zf, __uint_as_float(xr));
+            r.b = make_float4(__fmul_rn(kConicScale, a * rd), opv, zf, __uint_as_float(xr));
             r.c = make_float4(col[0], col[1], col[2], __uint_as_float(yr));
         }
         Record *o = out + (size_t)v * n + i;
@@ -214,13 +228,36 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
 template <int DEG>
 cudaError_t launch_deg(const ViewTable &vt, int n, const float *means, const float *scales,
                        const float *quats, const float *opac, const void *sh, bool f16,
-                       float near_z, Record *out, cudaStream_t s) {
+                       float near_z, Filters flt, Record *out, cudaStream_t s) {
     dim3 grid((n + 127) / 128);
     if (f16)
-        project_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, out);
+        project_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, flt, out);
     else
-        project_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, out);
+        project_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, near_z, flt, out);
     return cudaGetLastError();
+}
+
+// Mip-Splatting's 3D filter variance: v = s2 (z / f)^2 at the camera with the
+// highest sampling rate f / z among those that see the mean (z > near, the
+// projected mean inside [0, W] x [0, H]); 0 if none does
+__global__ void __launch_bounds__(256)
+mip_filter3d_kernel(ViewTable vt, int n, const float *__restrict__ means, float s2, float near_z,
+                    float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    float best = 0.f;                                  // largest f / z so far
+    for (int v = 0; v < vt.n_views; ++v) {
+        const ViewDev &V = vt.v[v];
+        const float z = fmaf(V.R[6], mx, fmaf(V.R[7], my, fmaf(V.R[8], mz, V.t[2])));
+        if (!(z > near_z)) continue;
+        const float x = fmaf(V.R[0], mx, fmaf(V.R[1], my, fmaf(V.R[2], mz, V.t[0])));
+        const float y = fmaf(V.R[3], mx, fmaf(V.R[4], my, fmaf(V.R[5], mz, V.t[1])));
+        const float u = fmaf(V.fx, x / z, V.cx), w = fmaf(V.fy, y / z, V.cy);
+        if (!(u >= 0.f && u <= (float)V.W && w >= 0.f && w <= (float)V.H)) continue;
+        best = fmaxf(best, fmaxf(V.fx, V.fy) / z);
+    }
+    out[i] = best > 0.f ? s2 / (best * best) : 0.f;
 }
 
 }  // namespace
@@ -232,13 +269,15 @@ using namespace hm;
 extern "C" hm_status hm_project_gaussians(const hm_camera *cams, int32_t n_views, int32_t n,
                                           const float *means, const float *scales,
                                           const float *quats, const float *opacity,
-                                          const void *sh, int32_t sh_degree, int32_t sh_format,
-                                          const hm_options *opt, void *records, void *stream) {
+                                          const float *filter_3d, const void *sh, int32_t sh_degree,
+                                          int32_t sh_format, const hm_options *opt, void *records,
+                                          void *stream) {
     ViewTable vt;
     if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
     if (sh_degree < 0 || sh_degree > 3) return fail(HM_ERR_INVALID_ARG, "sh_degree must be 0..3");
     if (sh_format != HM_SH_F32 && sh_format != HM_SH_F16) return fail(HM_ERR_INVALID_ARG, "sh_format");
+    if (!(opt->kernel_2d >= 0.f && opt->kernel_2d < 1e6f)) return fail(HM_ERR_INVALID_ARG, "kernel_2d");
     if (n == 0) return HM_OK;
     if (!means || !scales || !quats || !opacity || !sh || !records)
         return fail(HM_ERR_INVALID_ARG, "null pointer");
@@ -247,12 +286,27 @@ extern "C" hm_status hm_project_gaussians(const hm_camera *cams, int32_t n_views
     cudaStream_t s = (cudaStream_t)stream;
     const bool f16 = sh_format == HM_SH_F16;
     Record *out = reinterpret_cast<Record *>(records);
+    const Filters flt{filter_3d, opt->kernel_2d, opt->antialias ? 1 : 0};
     cudaError_t e;
     switch (sh_degree) {
-        case 0: e = launch_deg<0>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, out, s); break;
-        case 1: e = launch_deg<1>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, out, s); break;
-        case 2: e = launch_deg<2>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, out, s); break;
-        default: e = launch_deg<3>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, out, s); break;
+        case 0: e = launch_deg<0>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, flt, out, s); break;
+        case 1: e = launch_deg<1>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, flt, out, s); break;
+        case 2: e = launch_deg<2>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, flt, out, s); break;
+        default: e = launch_deg<3>(vt, n, means, scales, quats, opacity, sh, f16, opt->near_gauss, flt, out, s); break;
     }
     return cuda_status(e);
+}
+
+extern "C" hm_status hm_mip_filter_3d(const hm_camera *cams, int32_t n_views, int32_t n, const float *means,
+                                      float s2, float near_z, float *filter_3d, void *stream) {
+    hm_options o;
+    hm_default_options(&o);
+    ViewTable vt;
+    if (!build_view_table(cams, n_views, &o, &vt)) return HM_ERR_INVALID_ARG;
+    if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
+    if (!(s2 > 0.f) || !(near_z >= 0.f)) return fail(HM_ERR_INVALID_ARG, "s2 must be > 0, near_z >= 0");
+    if (n == 0) return HM_OK;
+    if (!means || !filter_3d) return fail(HM_ERR_INVALID_ARG, "null pointer");
+    mip_filter3d_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(vt, n, means, s2, near_z, filter_3d);
+    return cuda_status(cudaGetLastError());
 }

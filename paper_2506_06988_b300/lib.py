@@ -36,7 +36,7 @@ HM_BWD_NOALLOC_BYTES = 16 << 20
 EXPORTS = [
     "hm_default_options", "hm_last_error", "hm_total_tiles",
     "hm_rasterize_mesh_workspace_size", "hm_rasterize_mesh",
-    "hm_project_gaussians",
+    "hm_project_gaussians", "hm_mip_filter_3d",
     "hm_bin_sort_workspace_size", "hm_bin_sort",
     "hm_blend_forward",
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
@@ -52,7 +52,8 @@ class HmCamera(ctypes.Structure):
 class HmOptions(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32),
                 ("mesh_cull", c_int32), ("near_gauss", c_float), ("near_mesh", c_float),
-                ("bg", c_float * 3), ("bwd_stages", c_int32), ("ellipse_cull", c_int32)]
+                ("bg", c_float * 3), ("bwd_stages", c_int32), ("ellipse_cull", c_int32),
+                ("kernel_2d", c_float), ("antialias", c_int32)]
 
 
 class HmLossParams(ctypes.Structure):
@@ -78,8 +79,10 @@ _SIGS = {
                                     c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                     c_void_p, c_size_t, c_void_p]),
     "hm_project_gaussians": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
-                                       c_void_p, c_void_p, c_int32, c_int32, _OPT_P, c_void_p,
-                                       c_void_p]),
+                                       c_void_p, c_void_p, c_void_p, c_int32, c_int32, _OPT_P,
+                                       c_void_p, c_void_p]),
+    "hm_mip_filter_3d": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_float, c_float, c_void_p,
+                                   c_void_p]),
     "hm_bin_sort_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int64, _OPT_P]),
     "hm_bin_sort": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, _OPT_P, c_void_p,
                               c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -88,7 +91,7 @@ _SIGS = {
                                    c_void_p, c_void_p, c_void_p]),
     "hm_blend_backward_workspace_size": (c_size_t, [c_int32, c_int32]),
     "hm_blend_backward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
-                                    c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                     _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -98,7 +101,8 @@ _SIGS = {
     "hm_hybrid_loss": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  _LOSS_P, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_blend_backward_noalloc": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
-                                            c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                            c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
+                                            c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                             _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -142,9 +146,13 @@ def cameras(cams) -> ctypes.Array:
 
 
 def options(tile=(16, 16), batch=None, mesh_cull=True, bg=(0.0, 0.0, 0.0), near_gauss=0.2,
-            near_mesh=0.01, ellipse_cull=True) -> HmOptions:
+            near_mesh=0.01, ellipse_cull=True, mip=False) -> HmOptions:
+    """hm_options; ``mip`` selects Mip-Splatting's 2D Mip filter (kernel 0.1
+    with opacity compensation) instead of the 3DGS 0.3 dilation."""
     o = HmOptions()
     load().hm_default_options(ctypes.byref(o))
+    if mip:
+        o.kernel_2d, o.antialias = 0.1, 1
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
     o.batch = int(batch) if batch is not None else int(tile[0] * tile[1])
     o.mesh_cull = int(bool(mesh_cull))
@@ -184,10 +192,14 @@ def hm_rasterize_mesh(cams, verts, uvs, n_verts, faces, n_faces, tex, tex_w, tex
 
 
 def hm_project_gaussians(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format, opt,
-                         records, stream):
+                         records, stream, filter_3d=None):
     return load().hm_project_gaussians(cams, len(cams), n, _ptr(means), _ptr(scales), _ptr(quats),
-                                       _ptr(opacity), _ptr(sh), sh_degree, sh_format,
+                                       _ptr(opacity), _ptr(filter_3d), _ptr(sh), sh_degree, sh_format,
                                        ctypes.byref(opt), _ptr(records), stream)
+
+
+def hm_mip_filter_3d(cams, n, means, s2, near_z, filter_3d, stream):
+    return load().hm_mip_filter_3d(cams, len(cams), n, _ptr(means), s2, near_z, _ptr(filter_3d), stream)
 
 
 def hm_bin_sort_workspace_size(cams, n, capacity, opt) -> int:
@@ -216,9 +228,10 @@ def hm_blend_backward_workspace_size(n_views, n) -> int:
 def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format, records,
                       pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w, tex_h, opt,
                       out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats, d_opacity, d_sh,
-                      d_tex, d_status, ws, ws_bytes, stream, dL_dmesh=None):
+                      d_tex, d_status, ws, ws_bytes, stream, dL_dmesh=None, filter_3d=None):
     return load().hm_blend_backward(cams, len(cams), n, _ptr(means), _ptr(scales), _ptr(quats),
-                                    _ptr(opacity), _ptr(sh), sh_degree, sh_format, _ptr(records),
+                                    _ptr(opacity), _ptr(filter_3d), _ptr(sh), sh_degree, sh_format,
+                                    _ptr(records),
                                     _ptr(pair_vals), _ptr(tile_ranges), _ptr(mesh_depth),
                                     _ptr(mesh_rgb), _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
                                     _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
@@ -230,11 +243,12 @@ def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_
 def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format,
                               records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w,
                               tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats,
-                              d_opacity, d_sh, d_tex, d_status, stream):
+                              d_opacity, d_sh, d_tex, d_status, stream, filter_3d=None):
     """hm_blend_backward without a workspace argument: the scratch is the
     library's static 16 MiB device array (for callers that cannot allocate)."""
     return load().hm_blend_backward_noalloc(cams, len(cams), n, _ptr(means), _ptr(scales),
-                                            _ptr(quats), _ptr(opacity), _ptr(sh), sh_degree,
+                                            _ptr(quats), _ptr(opacity), _ptr(filter_3d), _ptr(sh),
+                                            sh_degree,
                                             sh_format, _ptr(records), _ptr(pair_vals),
                                             _ptr(tile_ranges), _ptr(mesh_depth), _ptr(mesh_rgb),
                                             _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),

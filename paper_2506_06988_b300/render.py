@@ -66,7 +66,8 @@ class Renderer:
                  n_verts: int = 0, n_faces: int = 0, tex_shape=None, tile=(16, 16),
                  batch: Optional[int] = None, mesh_cull: bool = True, bg=(0.0, 0.0, 0.0),
                  pair_capacity: Optional[int] = None, item_capacity: Optional[int] = None,
-                 ellipse_cull: bool = True, pixel_buffers: Optional[dict] = None, device="cuda"):
+                 ellipse_cull: bool = True, pixel_buffers: Optional[dict] = None, mip: bool = False,
+                 device="cuda"):
         lib.load()
         self.device = torch.device(device)
         self.cam_list = list(cams)
@@ -77,7 +78,11 @@ class Renderer:
         self.K = (self.sh_degree + 1) ** 2
         self.sh_format = lib.HM_SH_F16 if sh_f16 else lib.HM_SH_F32
         self.opt = lib.options(tile=tile, batch=batch, mesh_cull=mesh_cull, bg=bg,
-                               ellipse_cull=ellipse_cull)
+                               ellipse_cull=ellipse_cull, mip=mip)
+        # Mip-Splatting back-end (mip=True): the 2D Mip filter in the options and
+        # the per-Gaussian 3D smoothing variance (set_filter_3d / mip_filter_3d)
+        self.mip = bool(mip)
+        self.filter_3d: Optional[torch.Tensor] = None
         self.bg = tuple(float(x) for x in bg)
         self.sizes = [(int(c.width), int(c.height)) for c in self.cam_list]
         self.pix_off = np.concatenate([[0], np.cumsum([w * h for w, h in self.sizes])]).astype(np.int64)
@@ -188,10 +193,27 @@ class Renderer:
                                         self.status_word, self.raster_ws, self.raster_ws.numel(), s),
                   "hm_rasterize_mesh")
 
+    def mip_filter_3d(self, means, s2: float = 0.2, cams=None) -> torch.Tensor:
+        """Compute (and keep for the projections) Mip-Splatting's 3D
+        smoothing variance per Gaussian from ``cams`` (default: this
+        renderer's cameras -- the training views)."""
+        cams = self.cams if cams is None else lib.cameras(cams)
+        if self.filter_3d is None or self.filter_3d.numel() != self.n:
+            self.filter_3d = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        lib.check(lib.hm_mip_filter_3d(cams, self.n, means.contiguous(), float(s2), float(self.opt.near_gauss),
+                                       self.filter_3d, _stream()), "hm_mip_filter_3d")
+        return self.filter_3d
+
+    def set_filter_3d(self, v: Optional[torch.Tensor]):
+        """Use ``v`` ([n] float32, device) as the 3D smoothing variance (None: off)."""
+        if v is not None and (v.dtype != torch.float32 or v.numel() != self.n or not v.is_contiguous()):
+            raise ValueError(f"filter_3d: need {self.n} contiguous float32")
+        self.filter_3d = v
+
     def project(self, means, scales, quats, opacity, sh):
         lib.check(lib.hm_project_gaussians(self.cams, self.n, means, scales, quats, opacity, sh,
                                            self.sh_degree, self.sh_format, self.opt, self.records,
-                                           _stream()), "hm_project_gaussians")
+                                           _stream(), filter_3d=self.filter_3d), "hm_project_gaussians")
 
     def bin_sort(self):
         tmax = self.tile_max if self.has_mesh else None
@@ -337,7 +359,8 @@ class Renderer:
             dL_drgb.contiguous(), None if dL_dT is None else dL_dT.contiguous(),
             g["means"], g["scales"], g["quats"], g["opacity"], g["sh"], d_tex, self.status_word,
             self.bwd_ws, self.bwd_ws.numel(), _stream(),
-            dL_dmesh=None if (dL_dmesh is None or d_tex is None) else dL_dmesh.contiguous()),
+            dL_dmesh=None if (dL_dmesh is None or d_tex is None) else dL_dmesh.contiguous(),
+            filter_3d=self.filter_3d),
             "hm_blend_backward")
 
     # -- the joint-optimisation loss ------------------------------------------------
@@ -504,6 +527,14 @@ class ChunkedRenderer:
         self.tile_max = torch.empty(int(self.tile_off[-1]), dtype=torch.float32, device=d) if self.has_mesh else None
         self.chunks = [list(range(i, min(i + self.chunk, self.V))) for i in range(0, self.V, self.chunk)]
         self._renderers = {}
+        self.filter_3d: Optional[torch.Tensor] = None
+
+    def set_filter_3d(self, v: Optional[torch.Tensor]):
+        """Mip-Splatting's 3D smoothing variance for every chunk's projection
+        (compute it over all cameras, e.g. with ``Renderer.mip_filter_3d``)."""
+        self.filter_3d = v
+        for r in self._renderers.values():
+            r.set_filter_3d(v)
 
     def _bufs(self, idx):
         a, b = int(self.pix_off[idx[0]]), int(self.pix_off[idx[-1] + 1])
@@ -524,6 +555,7 @@ class ChunkedRenderer:
         if r is None:
             r = Renderer(cams, self.n, self.sh_degree, pixel_buffers=self._bufs(idx), device=self.device,
                          **self.kw)
+            r.set_filter_3d(self.filter_3d)
             self._renderers[key] = r
         else:
             r.retarget(cams, self._bufs(idx))
