@@ -342,6 +342,54 @@ hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *ou
                          const float *mesh_depth, const hm_loss_params *p, double *loss_out,
                          float *dL_drgb, float *dL_dmesh, void *ws, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* hm_mesh_prune -- the mesh-pruning metrics of Sec. 3.3 / Algorithm 1
+ * (stage 1), which prepare the mesh before the joint optimisation.  Per
+ * triangle (bits of flags[f]; flags[f] == 0 keeps it):
+ *   HM_PRUNE_NORMAL  per view, the floor(alpha_normal % of the covered pixels)
+ *                    ranking first by (total variation of the prior normal
+ *                    map descending, pixel index ascending) mark the triangle
+ *                    tri_id names there.  TV(x,y) = sum_c |N_c(x+1,y) -
+ *                    N_c(x,y)| + |N_c(x,y+1) - N_c(x,y)| in FP32 (absent
+ *                    neighbours 0), channel by channel in that order;
+ *   HM_PRUNE_ANGLE   a triangle sharing an edge has a normal more than
+ *                    angle_deg away: n_f . n_g < cos(angle) sqrt(|n_f|^2 |n_g|^2),
+ *                    n = (v1 - v0) x (v2 - v0) in FP64 (winding as given;
+ *                    zero-area triangles take no part);
+ *   HM_PRUNE_AREA    the floor(alpha_area % of F) first by (|n|^2, index);
+ *   HM_PRUNE_GROUP   triangles no metric above removed, in edge-connected
+ *                    pieces of those triangles with fewer than alpha_group.
+ * The metrics are keep masks combined with && (the paper's M_N && M_A && M_S).
+ * Hole closing and smoothing (later steps of stage 1) are not part of it.
+ *  cams[n_views] give the image sizes of tri_id (hm_rasterize_mesh output,
+ *  per pixel of all views) and normals (planar [3][H][W] per view, float32);
+ *  with n_views == 0 or either NULL the normal metric is skipped.
+ *  verts [n_verts][3] float32, faces [n_faces][3] int32 (device).
+ *  Outputs: flags [n_faces] uint8; label [n_faces] int32 (may be NULL): the
+ *  smallest triangle index of the piece, -1 where a metric removed it.
+ *  Errors: HM_ERR_INVALID_ARG (sizes, parameters, a face index or tri_id out
+ *  of range), HM_ERR_WORKSPACE, HM_ERR_CUDA.  SYNCHRONISES `stream` (the
+ *  piece labelling iterates until no label changes, at most 64 rounds).
+ */
+#define HM_PRUNE_NORMAL 1
+#define HM_PRUNE_ANGLE 2
+#define HM_PRUNE_AREA 4
+#define HM_PRUNE_GROUP 8
+typedef struct hm_prune_params {
+    float alpha_normal;      /* percent of covered pixels per view (20) */
+    float alpha_area;        /* percent of triangles (50) */
+    float angle_deg;         /* adjacent-angle limit (45) */
+    int32_t alpha_group;     /* smallest piece kept, in triangles (100) */
+} hm_prune_params;
+
+void hm_default_prune_params(hm_prune_params *p);
+size_t hm_mesh_prune_workspace_size(const hm_camera *cams, int32_t n_views, int32_t n_verts,
+                                    int32_t n_faces);
+hm_status hm_mesh_prune(const hm_camera *cams, int32_t n_views, const float *verts, int32_t n_verts,
+                        const int32_t *faces, int32_t n_faces, const int32_t *tri_id,
+                        const float *normals, const hm_prune_params *p, uint8_t *flags,
+                        int32_t *label, void *ws, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,6 +41,7 @@ EXPORTS = [
     "hm_blend_forward",
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
     "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss",
+    "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
 ]
 
 
@@ -60,6 +61,11 @@ class HmLossParams(ctypes.Structure):
     _fields_ = [("lambda_ssim", c_float), ("lambda_t", c_float), ("k", c_float)]
 
 
+class HmPruneParams(ctypes.Structure):
+    _fields_ = [("alpha_normal", c_float), ("alpha_area", c_float), ("angle_deg", c_float),
+                ("alpha_group", c_int32)]
+
+
 class HmError(RuntimeError):
     pass
 
@@ -67,6 +73,7 @@ class HmError(RuntimeError):
 _lib = None
 _CAM_P = POINTER(HmCamera)
 _OPT_P = POINTER(HmOptions)
+_PRUNE_P = POINTER(HmPruneParams)
 _LOSS_P = POINTER(HmLossParams)
 
 _SIGS = {
@@ -97,6 +104,10 @@ _SIGS = {
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_default_loss_params": (None, [_LOSS_P]),
+    "hm_default_prune_params": (None, [_PRUNE_P]),
+    "hm_mesh_prune_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int32]),
+    "hm_mesh_prune": (c_int32, [_CAM_P, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p,
+                                _PRUNE_P, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_hybrid_loss_workspace_size": (c_size_t, [_CAM_P, c_int32]),
     "hm_hybrid_loss": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  _LOSS_P, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -256,6 +267,30 @@ def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_deg
                                             _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
                                             _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex),
                                             _ptr(d_status), stream)
+
+
+HM_PRUNE_NORMAL, HM_PRUNE_ANGLE, HM_PRUNE_AREA, HM_PRUNE_GROUP = 1, 2, 4, 8
+
+
+def prune_params(alpha_normal=None, alpha_area=None, angle_deg=None, alpha_group=None) -> HmPruneParams:
+    p = HmPruneParams()
+    load().hm_default_prune_params(ctypes.byref(p))
+    for k, v in (("alpha_normal", alpha_normal), ("alpha_area", alpha_area), ("angle_deg", angle_deg),
+                 ("alpha_group", alpha_group)):
+        if v is not None:
+            setattr(p, k, v)
+    return p
+
+
+def hm_mesh_prune_workspace_size(cams, n_verts, n_faces) -> int:
+    return load().hm_mesh_prune_workspace_size(cams, len(cams) if cams is not None else 0, n_verts, n_faces)
+
+
+def hm_mesh_prune(cams, verts, n_verts, faces, n_faces, tri_id, normals, params, flags, label, ws, ws_bytes,
+                  stream):
+    return load().hm_mesh_prune(cams, len(cams) if cams is not None else 0, _ptr(verts), n_verts, _ptr(faces),
+                                n_faces, _ptr(tri_id), _ptr(normals), ctypes.byref(params), _ptr(flags),
+                                _ptr(label), _ptr(ws), ws_bytes, stream)
 
 
 def loss_params(lambda_ssim=None, lambda_t=None, k=None) -> HmLossParams:

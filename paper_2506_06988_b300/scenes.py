@@ -530,3 +530,33 @@ def micro_quad_only(tex=None, w=32, h=32, f=32.0, z=3.0, seed=5) -> Scene:
 
 def with_fields(obj, **kw):
     return dataclasses.replace(obj, **kw)
+
+
+# --------------------------------------------------------------------------
+# prior normal maps for the mesh-pruning metrics (stand-ins for the monocular
+# normal prior the paper takes from a pre-trained model)
+# --------------------------------------------------------------------------
+
+def prior_normal_maps(cameras, seed: int = 0, cutoff_px: float = 4.0, strength: float = 0.6,
+                      n_patches: int = 6):
+    """Per camera a planar [3, H, W] float32 field of unit normals: a smooth
+    field (band-limited noise of ``cutoff_px`` correlation length around the
+    view axis, tilted by ``strength``) with ``n_patches`` rectangles of
+    high-frequency noise (where a prior would see clutter)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for cam in cameras:
+        W, H = int(cam.width), int(cam.height)
+        size = 1 << int(np.ceil(np.log2(max(W, H))))
+        field = _band_limited_noise(rng, size, cutoff_px)[:H, :W].astype(np.float64) / 255.0 - 0.5
+        n = np.empty((3, H, W))
+        n[0] = strength * field[..., 0]
+        n[1] = strength * field[..., 1]
+        n[2] = -1.0 + 0.2 * field[..., 2]
+        for _ in range(n_patches):
+            w, h = int(rng.integers(4, max(5, W // 6))), int(rng.integers(4, max(5, H // 6)))
+            x, y = int(rng.integers(0, max(1, W - w))), int(rng.integers(0, max(1, H - h)))
+            n[:, y:y + h, x:x + w] += rng.normal(0.0, 0.5, (3, h, w))
+        n /= np.linalg.norm(n, axis=0, keepdims=True)
+        out.append(n.astype(np.float32))
+    return out
