@@ -407,6 +407,7 @@ def run_ours(args):
     if not args.no_extra:
         extra["batched16"] = run_batched16(args, dev, dist)
         extra["mip"] = run_mip(args, dev, dist)
+        extra["prune"] = run_prune(args, dev, dist)
         extra["plain"] = run_plain(args, dev, dist)
         extra["joint_opt"] = run_joint_opt(args, dev, dist)
         extra["large"] = run_large(args, dev, dist)
@@ -577,6 +578,73 @@ def run_mip(args, dev, dist):
            "fwd_ms_per_step": ms_f, "pairs": npairs, "filter_3d_ms": f3_ms,
            "filter_3d_seen_fraction": seen, "steps": steps}
     del gs, gf, r
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_prune(args, dev, dist):
+    """The mesh-pruning metrics (Sec. 3.3, Algorithm 1 stage 1) by
+    hm_mesh_prune with the paper's parameters (alpha_normal 20, alpha_area
+    50, 45 degrees, alpha_group 100):
+    * ``room``: the headline room's 50k-face mesh (coincident vertices welded
+      so walls share their corner edges) seen by its 8 cameras at 1920x1080,
+      pixel -> triangle maps from hm_rasterize_mesh, seeded prior normal maps;
+    * ``large``: the 2x2-room mesh of 1M triangles (15% pruned), geometric
+      metrics only (angle, area, pieces).
+    The call synchronises (the piece labelling iterates on the host)."""
+    import torch
+    from paper_2506_06988_b300 import lib, scenes
+    from paper_2506_06988_b300.render import MeshInput, Renderer
+    out = {"workload": "mesh-pruning metrics (normal-map variation, adjacent angle, area rank, "
+                       "small pieces) with the paper's parameters"}
+    p = lib.prune_params()
+
+    def weld(m):
+        uniq, inv = np.unique(np.asarray(m.verts, np.float32), axis=0, return_inverse=True)
+        return uniq, inv.reshape(-1)[np.asarray(m.faces)].astype(np.int32)
+
+    def time_prune(cams, verts, faces, tri, nrm, reps):
+        v = torch.as_tensor(verts, device=dev).contiguous()
+        f = torch.as_tensor(faces, device=dev).contiguous()
+        cam_arr = lib.cameras(cams) if cams else None
+        ws = torch.empty(max(1, lib.hm_mesh_prune_workspace_size(cam_arr, len(verts), len(faces))),
+                         dtype=torch.uint8, device=dev)
+        flags = torch.empty(len(faces), dtype=torch.uint8, device=dev)
+        label = torch.empty(len(faces), dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream().cuda_stream
+        call = lambda: lib.check(lib.hm_mesh_prune(cam_arr, v, len(verts), f, len(faces), tri, nrm, p, flags,  # noqa: E731
+                                                   label, ws, ws.numel(), stream), "hm_mesh_prune")
+        call()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            call()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        fl = flags.cpu().numpy()
+        return float(np.median(ts)), {name: int(((fl & b) > 0).sum()) for name, b in
+                                      (("normal", 1), ("angle", 2), ("area", 4), ("group", 8))}, int((fl == 0).sum())
+
+    scene = scenes.config1_scene()
+    verts, faces = weld(scene.mesh)
+    mesh = MeshInput.from_numpy(scene.mesh, device=dev)
+    g = scene.gaussians
+    r = Renderer(scene.cameras, g.n, g.sh_degree, n_verts=len(scene.mesh.verts), n_faces=len(scene.mesh.faces),
+                 tex_shape=scene.mesh.texture.shape, bg=tuple(scene.bg), device=dev)
+    r.rasterize_mesh(mesh)
+    nm = torch.as_tensor(np.concatenate([n.reshape(-1) for n in scenes.prior_normal_maps(scene.cameras, seed=9)]),
+                         device=dev)
+    ms, counts, kept = time_prune(scene.cameras, verts, faces, r.tri_id, nm, 5)
+    npix = sum(c.width * c.height for c in scene.cameras)
+    out["room"] = {"faces": len(faces), "views": len(scene.cameras), "pixels": npix, "ms": ms,
+                   "mpixel_per_s": npix / ms / 1e3, "removed": counts, "kept": kept}
+    del r, nm, mesh
+    big = scenes.room_scene(4, rooms=(2, 2), n_tris=1_000_000, prune_frac=0.15, atlas=64, n_gauss=1,
+                            resolutions=((64, 64),))
+    verts, faces = weld(big.mesh)
+    ms, counts, kept = time_prune(None, verts, faces, None, None, 5)
+    out["large"] = {"faces": len(faces), "ms": ms, "mfaces_per_s": len(faces) / ms / 1e3, "removed": counts,
+                    "kept": kept}
     torch.cuda.empty_cache()
     return out
 
@@ -866,7 +934,8 @@ def run_leg(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     lib.load()
-    fn = {"batched16": run_batched16, "mip": run_mip, "plain": run_plain, "joint_opt": run_joint_opt,
+    fn = {"batched16": run_batched16, "mip": run_mip, "prune": run_prune, "plain": run_plain,
+          "joint_opt": run_joint_opt,
           "large": run_large}
     out = fn[args.leg](args, dev, dist)
     if rank == 0:
@@ -884,7 +953,7 @@ def main():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--leg", default=None, choices=["batched16", "mip", "plain", "joint_opt", "large"],
+    ap.add_argument("--leg", default=None, choices=["batched16", "mip", "prune", "plain", "joint_opt", "large"],
                     help="run only this secondary workload and print its JSON (for profiling)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 16-view batched, plain single-view, joint-optimisation and "
