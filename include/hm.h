@@ -343,6 +343,19 @@ hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *ou
                          float *dL_drgb, float *dL_dmesh, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* hm_adam_update -- one Adam step (Kingma and Ba, 2015) on n float32 values
+ * in place, for optimised buffers such as the texture map in the texture-only
+ * optimisation that initialises it from the images (Sec. 3.3):
+ *   m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2,
+ *   p <- p - lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps).
+ *  param, m, v (device, updated), grad (device); step >= 1 counts from 1.
+ *  Errors: HM_ERR_INVALID_ARG (n < 0, step < 1, betas outside [0, 1),
+ *  eps or lr < 0, null pointers), HM_ERR_CUDA.  Launches only.
+ */
+hm_status hm_adam_update(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+                         float beta1, float beta2, float eps, int32_t step, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* hm_mesh_prune -- the mesh-pruning metrics of Sec. 3.3 / Algorithm 1
  * (stage 1), which prepare the mesh before the joint optimisation.  Per
  * triangle (bits of flags[f]; flags[f] == 0 keeps it):

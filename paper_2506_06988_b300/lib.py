@@ -42,6 +42,7 @@ EXPORTS = [
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
     "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss",
     "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
+    "hm_adam_update",
 ]
 
 
@@ -105,6 +106,8 @@ _SIGS = {
                                     c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_default_loss_params": (None, [_LOSS_P]),
     "hm_default_prune_params": (None, [_PRUNE_P]),
+    "hm_adam_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float,
+                                 c_float, c_int32, c_void_p]),
     "hm_mesh_prune_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int32]),
     "hm_mesh_prune": (c_int32, [_CAM_P, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p,
                                 _PRUNE_P, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -291,6 +294,11 @@ def hm_mesh_prune(cams, verts, n_verts, faces, n_faces, tri_id, normals, params,
     return load().hm_mesh_prune(cams, len(cams) if cams is not None else 0, _ptr(verts), n_verts, _ptr(faces),
                                 n_faces, _ptr(tri_id), _ptr(normals), ctypes.byref(params), _ptr(flags),
                                 _ptr(label), _ptr(ws), ws_bytes, stream)
+
+
+def hm_adam_update(param, grad, m, v, n, lr, beta1, beta2, eps, step, stream):
+    return load().hm_adam_update(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, step,
+                                 stream)
 
 
 def loss_params(lambda_ssim=None, lambda_t=None, k=None) -> HmLossParams:
