@@ -145,23 +145,35 @@ sel_hist_kernel(long long n, const Key *__restrict__ keys, const int32_t *__rest
     if (s_h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_h[threadIdx.x]);
 }
 
-__global__ void sel_pick_kernel(SelState *st, unsigned int *hist, int shift) {
-    if (st->active) {
-        long long before = 0;
-        int b = 0;
-        for (; b < 256; ++b) {
-            if (st->rank < before + (long long)hist[b]) break;
-            before += hist[b];
-        }
-        if (b == 256) {
-            st->active = 0;   // fewer candidates than the rank (cannot happen for k <= count)
-        } else {
-            st->rank -= before;
+// one CTA of 256 threads: thread b holds bin b; an exclusive scan of the
+// counts finds the bin holding the target rank; the histogram is cleared
+// for the next pass
+__global__ void __launch_bounds__(256) sel_pick_kernel(SelState *st, unsigned int *hist, int shift) {
+    __shared__ unsigned long long s_w[8];
+    const int b = threadIdx.x, lane = b & 31, w = b >> 5;
+    const int active = st->active;      // read by every thread before the one owner writes
+    const long long r = st->rank;
+    const unsigned long long h = hist[b];
+    unsigned long long x = h;           // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    unsigned long long before = x - h;
+    for (int k = 0; k < w; ++k) before += s_w[k];
+    if (active) {
+        if (r >= (long long)before && r < (long long)(before + h)) {
+            st->rank = r - (long long)before;
             st->prefix |= (unsigned long long)b << shift;
             st->mask |= 255ull << shift;
+        } else if (b == 255 && r >= (long long)(before + h)) {
+            st->active = 0;   // fewer candidates than the rank (cannot happen for k <= count)
         }
     }
-    for (int i = 0; i < 256; ++i) hist[i] = 0u;
+    hist[b] = 0u;
 }
 
 // k = floor(alpha * count / 100) -> the target rank k - 1
@@ -363,7 +375,7 @@ cudaError_t run_select(const Key *keys, long long n, const int32_t *valid, int n
     const int g = (int)(blocks(n) < 148 * 8 ? blocks(n) : 148 * 8);
     for (int shift = n_bits - 8; shift >= 0; shift -= 8) {
         sel_hist_kernel<Key><<<g, 256, 0, s>>>(n, keys, valid, w.sel, shift, w.hist);
-        sel_pick_kernel<<<1, 1, 0, s>>>(w.sel, w.hist, shift);
+        sel_pick_kernel<<<1, 256, 0, s>>>(w.sel, w.hist, shift);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sel_eq_kernel<Key><<<blocks(n), 256, 0, s>>>(n, keys, valid, w.sel, w.eq);
