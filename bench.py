@@ -54,8 +54,8 @@ KERNEL_SOURCES = {
     "project": ("project.cu", "sh.cuh", "hm_internal.cuh"),
 }
 NCU_TRAFFIC = {
-    "blend_forward": (654_977_024, "9a2fffed4933752d"),
-    "blend_backward": (566_698_240, "fb9e8648addd12e8"),
+    "blend_forward": (654_179_328, "6586889e0c4fc130"),
+    "blend_backward": (566_473_472, "9ba23cced0ce12a1"),
 }
 
 
