@@ -931,23 +931,40 @@ def run_plain(args, dev, dist):
 def run_e2e(args, scene, r, mesh, dev, dist, frames):
     """Through the public API (HybridRender autograd Function + an L1 loss):
     every step copies the Gaussian parameters and the 8 target images (uint8)
-    from pinned host memory, renders forward+backward and reads the loss back."""
+    from pinned host memory, renders forward+backward and reads the loss back.
+    The copies of step k+1 run on a copy stream into a second set of device
+    buffers while step k computes (double buffering, as a data loader's
+    prefetch does); each step still moves its own inputs across the bus
+    inside the timed region."""
     import torch
     from paper_2506_06988_b300.render import HybridRender
     g = scene.gaussians
     host = {k: torch.as_tensor(getattr(g, k)).contiguous().pin_memory()
             for k in ("means", "scales", "quats", "opacity", "sh")}
     tgt_host = (torch.rand(3 * r.npix, generator=torch.Generator().manual_seed(5)) * 255).to(torch.uint8).pin_memory()
-    devp = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    tgt = torch.empty(3 * r.npix, dtype=torch.uint8, device=dev)
+    bufs = [({k: torch.empty_like(v, device=dev) for k, v in host.items()},
+             torch.empty(3 * r.npix, dtype=torch.uint8, device=dev)) for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + tgt_host.numel()
     d2h = 4
+    compute = torch.cuda.current_stream()
+    copy = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def step():
-        for k in host:
-            devp[k].copy_(host[k], non_blocking=True)
-        tgt.copy_(tgt_host, non_blocking=True)
-        params = {k: v.requires_grad_() for k, v in devp.items()}
+    def issue_copy(k):
+        devp, tgt = bufs[k % 2]
+        with torch.cuda.stream(copy):
+            copy.wait_event(used[k % 2])           # the step that last read this buffer set is done
+            for name in host:
+                devp[name].copy_(host[name], non_blocking=True)
+            tgt.copy_(tgt_host, non_blocking=True)
+            copied[k % 2].record(copy)
+
+    def step(k):
+        devp, tgt = bufs[k % 2]
+        compute.wait_event(copied[k % 2])
+        issue_copy(k + 1)                          # prefetch the next step's inputs
+        params = {name: v.requires_grad_() for name, v in devp.items()}
         rgb, T = HybridRender.apply(r, mesh, params["means"], params["scales"], params["quats"],
                                     params["opacity"], params["sh"], None)
         loss = (rgb - tgt.float() * (1.0 / 255.0)).abs().mean()
@@ -955,19 +972,25 @@ def run_e2e(args, scene, r, mesh, dev, dist, frames):
         for v in devp.values():
             v.grad = None
             v.requires_grad_(False)
+        used[k % 2].record(compute)
         return float(loss.item())
 
-    for _ in range(3):
-        step()
+    for ev in used:
+        ev.record(compute)
+    issue_copy(0)
+    for k in range(3):
+        step(k)
     n = max(3, min(args.steps, 10))
     _barrier(dist)
     t0 = time.perf_counter()
-    for _ in range(n):
-        step()
+    for k in range(3, 3 + n):
+        step(k)
     _barrier(dist)
     sec = _max_over_ranks((time.perf_counter() - t0) / n, dist)
+    torch.cuda.synchronize()
     return {"value": frames / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
-            "ms_per_step": sec * 1e3, "api": "HybridRender.apply + L1 loss + backward; loss.item()"}
+            "ms_per_step": sec * 1e3, "api": "HybridRender.apply + L1 loss + backward; loss.item(); inputs "
+                                             "double-buffered (next step's copy overlaps this step's compute)"}
 
 
 def run_leg(args):
