@@ -44,12 +44,13 @@ keep = flags == 0, and the component label (-1 where a metric removed it).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 from scipy.sparse import coo_matrix
 from scipy.sparse.csgraph import connected_components
 
 F_NORMAL, F_ANGLE, F_AREA, F_GROUP = 1, 2, 4, 8
-COS45 = float(np.cos(np.pi / 4))
 
 
 def face_normals(verts, faces):
@@ -127,7 +128,7 @@ def prune(verts, faces, tri_ids, normal_maps, alpha_normal=20.0, alpha_area=50.0
     # adjacent angles
     nrm, n2 = face_normals(verts, faces)
     pairs = edge_pairs(faces)
-    cos_t = float(np.cos(np.deg2rad(angle_deg)))
+    cos_t = math.cos(float(angle_deg) * (math.pi / 180.0))
     if len(pairs):
         f, g = pairs[:, 0], pairs[:, 1]
         ok = (n2[f] > 0) & (n2[g] > 0)
