@@ -86,5 +86,5 @@ def loss_and_grads(views_np, lambda_s=0.2, lambda_t=0.1, k=20.0):
                           hit=torch.tensor(np.asarray(v["hit"], bool))))
     l1, ss, lt, L = loss_terms(views, lambda_s, lambda_t, k)
     L.backward()
-    terms = tuple(float(t) for t in (l1, ss, lt, L))
+    terms = tuple(float(t.detach()) if torch.is_tensor(t) else float(t) for t in (l1, ss, lt, L))
     return terms, [v["x"].grad.numpy() for v in views], [v["m"].grad.numpy() for v in views]
