@@ -11,8 +11,8 @@ beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N>1) every rank renders its own 8 views of the scene (weak
-scaling; no collective on the data path) and rank 0 prints the line with the
+Under torchrun (N>1) every rank renders its own block of 8 views of the same
+room (weak scaling; no collective on the data path) and rank 0 prints the line with the
 max-over-ranks time.  ``--impl reference`` times the CPU FP64 oracle (the
 correctness reference; there is no other implementation of this path) on the
 host cores over a bounded sample of the same workload.
@@ -141,32 +141,51 @@ class ClockSampler:
 
 
 def _dist():
+    """(rank, world, local rank, torch.distributed or None) from the torchrun
+    environment; NCCL between the GPUs (HM_BENCH_BACKEND=gloo runs the same
+    host logic on CPU processes, for tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, 0, None
     import torch
     import torch.distributed as dist
     rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    backend = os.environ.get("HM_BENCH_BACKEND", "nccl")
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
     return rank, ws, local, dist
+
+
+def _on_gpu(dist) -> bool:
+    return dist is None or dist.get_backend() == "nccl"
 
 
 def _max_over_ranks(x, dist):
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _on_gpu(dist) else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def _barrier(dist):
     import torch
-    torch.cuda.synchronize()
+    gpu = _on_gpu(dist) and torch.cuda.is_available()
+    if gpu:
+        torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
+    if gpu:
+        torch.cuda.synchronize()
+
+
+def view_block_scene(rank: int):
+    """The headline scene with rank ``rank``'s own block of 8 poses of the
+    same room (data parallel over views: no collective on the data path)."""
+    from paper_2506_06988_b300 import scenes
+    return scenes.config1_scene(view_block=rank)
 
 
 # ----------------------------------------------------------------------------
@@ -263,7 +282,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     lib.load()
-    scene = scenes.config1_scene()
+    scene = view_block_scene(rank)
     scene.cameras = scene.cameras[:args.views]
     g = scene.gaussians
     tile = tuple(int(x) for x in args.tile.split("x"))

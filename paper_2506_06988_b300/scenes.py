@@ -329,14 +329,17 @@ def room_scene(seed: int, *, rooms=(1, 1), n_tris=50_000, prune_frac=0.10, atlas
                n_gauss=300_000, log_scale=(-4.0, 0.6), logit_opacity=(0.5, 1.0),
                sh_degree=3, sh_std=0.2, sh_f16=False, resolutions=((1920, 1080),) * 8,
                focal_per_width=1100.0 / 1920.0, n_boxes_per_room=20, texture_f32=False,
-               with_mesh=True, wall_gaussians=0, name="room") -> Scene:
+               with_mesh=True, wall_gaussians=0, name="room", view_block: int = 0) -> Scene:
     """Indoor room scene: a box room (or a grid of connected rooms) whose walls,
     floor and ceiling are triangulated into ~``n_tris`` triangles with
     ``prune_frac`` removed in seeded clusters (pruned holes); a band-limited
     noise RGB8 texture atlas; ``n_gauss`` Gaussians, 70% clustered around
     furniture boxes and 30% near the holes; cameras inside the room(s) at least
     0.3 m from every surface.  ``wall_gaussians`` adds flat textured Gaussians
-    covering the walls (the Gaussian-only comparison scene)."""
+    covering the walls (the Gaussian-only comparison scene).  ``view_block``
+    k selects the k-th block of poses of the same room (block 0 = the first
+    len(resolutions) poses of the seeded sequence): distinct views of one
+    scene, e.g. one block per rank."""
     (r_prune, r_tex, r_box, r_g1, r_g2, r_attr, r_pose, r_wall) = _rngs(seed, 8)
     rects, (X, Y, Z) = _room_rects(*rooms)
     verts, uvs, faces_all, _ = _grid_mesh(rects, n_tris, atlas)
@@ -402,7 +405,7 @@ def room_scene(seed: int, *, rooms=(1, 1), n_tris=50_000, prune_frac=0.10, atlas
     margin = 0.8
     bmin = bpos - np.array([0.5, 0.0, 0.5]) * bsize - 0.3
     bmax = bpos + np.array([0.5, 1.0, 0.5]) * bsize + 0.3
-    for (w, h) in resolutions:
+    for (w, h) in list(resolutions) * (view_block + 1):
         while True:
             C = r_pose.uniform([margin, 0.8, margin], [X - margin, Y - 0.8, Z - margin])
             inside = np.any(np.all((C > bmin) & (C < bmax), axis=1))
@@ -421,6 +424,7 @@ def room_scene(seed: int, *, rooms=(1, 1), n_tris=50_000, prune_frac=0.10, atlas
         fwd = np.array([np.cos(pitch) * np.sin(yaw), np.sin(pitch), np.cos(pitch) * np.cos(yaw)])
         f = focal_per_width * w
         cams.append(camera_lookat(C, fwd, w, h, f))
+    cams = cams[view_block * len(resolutions):]
 
     mesh = Mesh(verts, uvs, faces.astype(np.int32), tex) if with_mesh else None
     return Scene(name, seed, g, mesh, cams,
@@ -428,10 +432,11 @@ def room_scene(seed: int, *, rooms=(1, 1), n_tris=50_000, prune_frac=0.10, atlas
                             n_removed=int(len(removed))))
 
 
-def config1_scene(seed: int = 1, n_views: int = 8) -> Scene:
+def config1_scene(seed: int = 1, n_views: int = 8, view_block: int = 0) -> Scene:
     """Indoor room, 1920x1080 (fx=fy=1100), 8 poses, 50k triangles with 10%
-    pruned, 2048^2 RGB8 atlas, 300k Gaussians, SH degree 3."""
-    return room_scene(seed, resolutions=((1920, 1080),) * n_views, name="config1")
+    pruned, 2048^2 RGB8 atlas, 300k Gaussians, SH degree 3 (``view_block``:
+    another block of 8 poses of the same room)."""
+    return room_scene(seed, resolutions=((1920, 1080),) * n_views, name="config1", view_block=view_block)
 
 
 def config1_plain_scene(seed: int = 1, n_views: int = 8) -> Scene:
