@@ -355,6 +355,32 @@ hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *ou
 hm_status hm_adam_update(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
                          float beta1, float beta2, float eps, int32_t step, void *stream);
 
+/* hm_adam_update_dev -- the same update with the bias corrections read from
+ * device memory, d_rc[2] = (1 / (1 - beta1^t), 1 / (1 - beta2^t)) as kept by
+ * hm_adam_advance, so that a training step can be captured in a CUDA graph
+ * once and replayed.  d_status (device int32, may be NULL): when nonzero (a
+ * stage of the step reported an error, e.g. a capacity overflow) the update
+ * is skipped.  Errors as hm_adam_update.
+ * hm_adam_advance -- ++*d_step and d_rc for the new step, skipped when
+ * *d_status is nonzero.  d_step (device int32, 0 before the first step). */
+hm_status hm_adam_update_dev(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+                             float beta1, float beta2, float eps, const float *d_rc,
+                             const int32_t *d_status, void *stream);
+hm_status hm_adam_advance(int32_t *d_step, float beta1, float beta2, float *d_rc,
+                          const int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* hm_activate / hm_activate_backward -- the 3DGS parameterisation the joint
+ * optimisation (Sec. 3.4) trains: scales = exp(log_scales) [n][3],
+ * opacity = 1 / (1 + exp(-logit)) [n]; and the chain rule back,
+ * d_log_scales = d_scales * scales, d_logit = d_opacity * opacity (1 - opacity)
+ * (written, not accumulated).  Device pointers; launches only. */
+hm_status hm_activate(int64_t n, const float *log_scales, const float *logit, float *scales,
+                      float *opacity, void *stream);
+hm_status hm_activate_backward(int64_t n, const float *scales, const float *opacity,
+                               const float *d_scales, const float *d_opacity, float *d_log_scales,
+                               float *d_logit, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* hm_mesh_prune -- the mesh-pruning metrics of Sec. 3.3 / Algorithm 1
  * (stage 1), which prepare the mesh before the joint optimisation.  Per

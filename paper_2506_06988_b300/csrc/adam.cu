@@ -18,9 +18,18 @@ __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, flo
     p -= lr * (m * rc1) / (sqrtf(v * rc2) + eps);
 }
 
+// rc = (1 / (1 - b1^t), 1 / (1 - b2^t)) from the host (rc_dev null) or from
+// device memory (a step captured in a CUDA graph); a nonzero *status (an
+// earlier stage reported an error) skips the update
 __global__ void __launch_bounds__(256)
 adam_kernel(long long n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-            float *__restrict__ v, float lr, float b1, float b2, float rc1, float rc2, float eps, bool vec4) {
+            float *__restrict__ v, float lr, float b1, float b2, float rc1, float rc2, float eps, bool vec4,
+            const float *__restrict__ rc_dev, const int32_t *__restrict__ status) {
+    if (status && *status) return;
+    if (rc_dev) {
+        rc1 = rc_dev[0];
+        rc2 = rc_dev[1];
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long tail = 0;
@@ -49,6 +58,17 @@ adam_kernel(long long n, float *__restrict__ p, const float *__restrict__ g, flo
 
 using namespace hm;
 
+static hm_status launch_adam(float *param, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
+                             float beta2, float eps, float rc1, float rc2, const float *d_rc, const int32_t *d_status,
+                             void *stream) {
+    const bool vec4 = (((uintptr_t)param | (uintptr_t)grad | (uintptr_t)m | (uintptr_t)v) & 15) == 0;
+    const long long work = vec4 ? (n >> 2) + 1 : n;
+    const int grid = (int)((work + 255) / 256 < 148 * 8 ? (work + 255) / 256 : 148 * 8);
+    adam_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, param, grad, m, v, lr, beta1, beta2, rc1, rc2, eps, vec4,
+                                                        d_rc, d_status);
+    return cuda_status(cudaGetLastError());
+}
+
 extern "C" hm_status hm_adam_update(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
                                     float beta1, float beta2, float eps, int32_t step, void *stream) {
     if (n < 0 || step < 1) return fail(HM_ERR_INVALID_ARG, "n < 0 or step < 1");
@@ -56,11 +76,18 @@ extern "C" hm_status hm_adam_update(float *param, const float *grad, float *m, f
         return fail(HM_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
     if (n == 0) return HM_OK;
     if (!param || !grad || !m || !v) return fail(HM_ERR_INVALID_ARG, "null pointer");
-    const bool vec4 = (((uintptr_t)param | (uintptr_t)grad | (uintptr_t)m | (uintptr_t)v) & 15) == 0;
     const float rc1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
     const float rc2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
-    const long long work = vec4 ? (n >> 2) + 1 : n;
-    const int grid = (int)((work + 255) / 256 < 148 * 8 ? (work + 255) / 256 : 148 * 8);
-    adam_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, param, grad, m, v, lr, beta1, beta2, rc1, rc2, eps, vec4);
-    return cuda_status(cudaGetLastError());
+    return launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, rc1, rc2, nullptr, nullptr, stream);
+}
+
+extern "C" hm_status hm_adam_update_dev(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+                                        float beta1, float beta2, float eps, const float *d_rc,
+                                        const int32_t *d_status, void *stream) {
+    if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
+    if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f) || !(lr >= 0.f))
+        return fail(HM_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+    if (n == 0) return HM_OK;
+    if (!param || !grad || !m || !v || !d_rc) return fail(HM_ERR_INVALID_ARG, "null pointer");
+    return launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, 1.f, 1.f, d_rc, d_status, stream);
 }

@@ -42,7 +42,7 @@ EXPORTS = [
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
     "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss",
     "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
-    "hm_adam_update",
+    "hm_adam_update", "hm_adam_update_dev", "hm_adam_advance", "hm_activate", "hm_activate_backward",
 ]
 
 
@@ -108,6 +108,12 @@ _SIGS = {
     "hm_default_prune_params": (None, [_PRUNE_P]),
     "hm_adam_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float,
                                  c_float, c_int32, c_void_p]),
+    "hm_adam_update_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float,
+                                     c_float, c_void_p, c_void_p, c_void_p]),
+    "hm_adam_advance": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
+    "hm_activate": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hm_activate_backward": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p]),
     "hm_mesh_prune_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int32]),
     "hm_mesh_prune": (c_int32, [_CAM_P, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p,
                                 _PRUNE_P, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -299,6 +305,24 @@ def hm_mesh_prune(cams, verts, n_verts, faces, n_faces, tri_id, normals, params,
 def hm_adam_update(param, grad, m, v, n, lr, beta1, beta2, eps, step, stream):
     return load().hm_adam_update(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, step,
                                  stream)
+
+
+def hm_adam_update_dev(param, grad, m, v, n, lr, beta1, beta2, eps, d_rc, d_status, stream):
+    return load().hm_adam_update_dev(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps,
+                                     _ptr(d_rc), _ptr(d_status), stream)
+
+
+def hm_adam_advance(d_step, beta1, beta2, d_rc, d_status, stream):
+    return load().hm_adam_advance(_ptr(d_step), beta1, beta2, _ptr(d_rc), _ptr(d_status), stream)
+
+
+def hm_activate(n, log_scales, logit, scales, opacity, stream):
+    return load().hm_activate(n, _ptr(log_scales), _ptr(logit), _ptr(scales), _ptr(opacity), stream)
+
+
+def hm_activate_backward(n, scales, opacity, d_scales, d_opacity, d_log_scales, d_logit, stream):
+    return load().hm_activate_backward(n, _ptr(scales), _ptr(opacity), _ptr(d_scales), _ptr(d_opacity),
+                                       _ptr(d_log_scales), _ptr(d_logit), stream)
 
 
 def loss_params(lambda_ssim=None, lambda_t=None, k=None) -> HmLossParams:

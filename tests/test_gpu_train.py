@@ -1,0 +1,132 @@
+"""The joint-optimisation step as one CUDA graph (JointTrainStep) against a
+reference built from plain PyTorch pieces around the same renderer calls:
+activations and their chain rule by torch autograd, the optimiser by
+torch.optim.Adam (FP32), the render / loss / gradients by eager library
+calls.  After one and three steps the parameters agree within FP32 rounding
+except where a gradient is within rounding of zero (Adam's step is then
++-lr either way): at most 0.5 % of the values, each off by at most 2 lr per
+step.  Also: the activation kernels against FP64 formulas, and a step whose
+pair capacity overflows leaves every parameter untouched and is redone by
+step(check=True)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2506_06988_b300 import lib, scenes
+from paper_2506_06988_b300.render import MeshInput
+from paper_2506_06988_b300.train import GROUPS, JointTrainStep
+
+from gpu_util import make_renderer  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_activation_kernels():
+    rng = np.random.default_rng(0)
+    n = 1001
+    ls = torch.as_tensor(rng.normal(-4, 1, (n, 3)).astype(np.float32), device="cuda")
+    lg = torch.as_tensor(rng.normal(0, 3, n).astype(np.float32), device="cuda")
+    sc, op = torch.empty_like(ls), torch.empty_like(lg)
+    st = torch.cuda.current_stream().cuda_stream
+    lib.check(lib.hm_activate(n, ls, lg, sc, op, st), "hm_activate")
+    dsc = torch.as_tensor(rng.standard_normal((n, 3)).astype(np.float32), device="cuda")
+    dop = torch.as_tensor(rng.standard_normal(n).astype(np.float32), device="cuda")
+    dls, dlg = torch.empty_like(ls), torch.empty_like(lg)
+    lib.check(lib.hm_activate_backward(n, sc, op, dsc, dop, dls, dlg, st), "hm_activate_backward")
+    torch.cuda.synchronize()
+    L, G = ls.double().cpu(), lg.double().cpu()
+    assert torch.allclose(sc.double().cpu(), L.exp(), rtol=4e-7, atol=0)
+    assert torch.allclose(op.double().cpu(), torch.sigmoid(G), rtol=4e-7, atol=1e-12)
+    # the chain rule from the kernel's own (FP32) activations: 1 - opacity
+    # cancels for opacities near 1, as in any FP32 sigmoid backward
+    S, O_ = sc.double().cpu(), op.double().cpu()
+    assert torch.allclose(dls.double().cpu(), dsc.double().cpu() * S, rtol=1e-6, atol=0)
+    assert torch.allclose(dlg.double().cpu(), dop.double().cpu() * O_ * (1 - O_), rtol=1e-6, atol=1e-12)
+
+
+def _setup(seed=3):
+    s = scenes.config0_scene(seed=seed)
+    s.bg = np.array([0.2, 0.3, 0.4], np.float32)
+    s.mesh.texture = s.mesh.texture.astype(np.float32) / 255.0
+    g = s.gaussians
+    r_t = make_renderer(s)
+    tgt = scenes.config2_target_params(s, seed=7)
+    mesh = MeshInput.from_numpy(s.mesh)
+    T = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda").contiguous()  # noqa: E731
+    r_t.render(T(tgt.means), T(tgt.scales), T(tgt.quats), T(tgt.opacity), T(tgt.sh), mesh)
+    target = r_t.rgb.clone()
+    p0 = dict(means=T(g.means), log_scales=torch.log(T(g.scales)), quats=T(g.quats),
+              logit=torch.logit(T(g.opacity)), sh=T(g.sh), texture=mesh.texture.clone())
+    return s, target, p0
+
+
+def _reference_steps(s, target, p0, lrs, steps, lambda_t):
+    r = make_renderer(s)
+    P = {k: v.clone().requires_grad_() for k, v in p0.items()}
+    opt = torch.optim.Adam([{"params": [P[k]], "lr": lrs[k]} for k in GROUPS], betas=(0.9, 0.999), eps=1e-15,
+                           foreach=False, fused=False)
+    md = MeshInput.from_numpy(s.mesh)
+    lp = lib.loss_params(lambda_t=lambda_t)
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=False)
+        sc, op = torch.exp(P["log_scales"]), torch.sigmoid(P["logit"])
+        mesh = MeshInput(md.verts, md.uvs, md.faces, P["texture"].detach())
+        A = (P["means"].detach(), sc.detach(), P["quats"].detach(), op.detach(), P["sh"].detach())
+        r.render(*A, mesh)
+        _, dI, dM = r.loss(target, lp, texture_loss=lambda_t > 0)
+        g = r.backward(*A, dI, None, mesh=mesh, tex_grad=True, dL_dmesh=dM)
+        torch.autograd.backward([sc, op], [g["scales"], g["opacity"]])
+        for k in ("means", "quats", "sh", "texture"):
+            P[k].grad = g[k].clone()
+        opt.step()
+    torch.cuda.synchronize()
+    return {k: v.detach() for k, v in P.items()}
+
+
+@pytest.mark.parametrize("lambda_t", [0.0, 0.1])
+def test_joint_train_step_matches_reference(lambda_t):
+    s, target, p0 = _setup()
+    lrs = dict(means=1e-3, log_scales=5e-3, quats=1e-3, logit=5e-2, sh=2.5e-3, texture=1e-2)
+    for steps in (1, 3):
+        p = {k: v.clone() for k, v in p0.items()}
+        mesh = MeshInput.from_numpy(s.mesh)
+        mesh = MeshInput(mesh.verts, mesh.uvs, mesh.faces, p["texture"])
+        ts = JointTrainStep(make_renderer(s), p, mesh, target, lrs=lrs, lambda_t=lambda_t)
+        for _ in range(steps):
+            ts.step()
+        torch.cuda.synchronize()
+        assert ts.iteration == steps
+        ref = _reference_steps(s, target, p0, lrs, steps, lambda_t)
+        for k in GROUPS:
+            d = (p[k] - ref[k]).abs().cpu().numpy().ravel()
+            moved = (p[k] - p0[k]).abs().cpu().numpy().ravel()
+            assert moved.max() > 0, k
+            tol = 1e-6 + 2e-7 * p0[k].abs().cpu().numpy().ravel()
+            off = d > tol
+            assert off.mean() <= 5e-3, (k, steps, off.mean())
+            assert d.max() <= 2 * lrs[k] * steps + 1e-6, (k, steps, d.max())
+
+
+def test_overflow_skips_the_update_and_check_redoes_it():
+    s, target, p0 = _setup(seed=4)
+    p = {k: v.clone() for k, v in p0.items()}
+    mesh = MeshInput.from_numpy(s.mesh)
+    mesh = MeshInput(mesh.verts, mesh.uvs, mesh.faces, p["texture"])
+    r = make_renderer(s)
+    ts = JointTrainStep(r, p, mesh, target)
+    r.set_pair_capacity(64)                        # far too small: the next replays overflow
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ts._body()
+    ts.graph = g
+    before = {k: v.clone() for k, v in p.items()}
+    ts.step()
+    torch.cuda.synchronize()
+    assert r.status()[0] & lib.HM_DEV_CAPACITY
+    for k in GROUPS:
+        assert torch.equal(p[k], before[k]), k
+    assert ts.iteration == 0
+    ts.step(check=True)                            # grows, captures again, redoes the step
+    torch.cuda.synchronize()
+    assert ts.iteration == 1 and r.status()[0] == 0
+    assert any(not torch.equal(p[k], before[k]) for k in GROUPS)
