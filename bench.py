@@ -793,6 +793,35 @@ def run_joint_opt(args, dev, dist):
         ms = _max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dist)
         out[name] = {"frames_per_s": 1e3 / ms, "ms_per_step": ms, "mpixel_per_s": W * H * 1e3 / ms / 1e6,
                      "loss_first": first, "loss_last": float(loss.item()), "steps": steps}
+    # the same paper-loss step as one CUDA graph (JointTrainStep: activations,
+    # render, fused loss, gradients and Adam all in library kernels)
+    from paper_2506_06988_b300.train import JointTrainStep
+    with torch.no_grad():
+        for p, p0 in zip(params, init):
+            p.copy_(p0)
+    pj = dict(means=means.detach().clone(), log_scales=log_s.detach().clone(), quats=quats.detach().clone(),
+              logit=logit.detach().clone(), sh=sh.detach().clone())
+    mesh_j = MeshInput(mesh.verts, mesh.uvs, mesh.faces, tex.detach().clone())
+    ts = JointTrainStep(r, pj, mesh_j, target, lrs=dict(means=1e-4, log_scales=1e-4, quats=1e-4, logit=1e-4,
+                                                        sh=1e-4, texture=1e-4),
+                        eps=1e-8, lambda_t=texture_loss_weight(5000))
+    first = float(ts.step()[3])
+    for _ in range(2):
+        ts.step()
+    steps = max(5, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    _barrier(dist)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        terms = ts.step()
+        ev[k][1].record(stream)
+    _barrier(dist)
+    ms = _max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dist)
+    out["paper_graph"] = {"frames_per_s": 1e3 / ms, "ms_per_step": ms, "mpixel_per_s": W * H * 1e3 / ms / 1e6,
+                          "loss_first": first, "loss_last": float(terms[3]), "steps": steps,
+                          "loss": "as 'paper', the whole step (activations, render, loss, gradients, Adam) "
+                                  "one CUDA graph replay (JointTrainStep)"}
+    del ts
     out["l1"]["loss"] = "mean |I_h - I| in PyTorch, HybridRender autograd"
     out["paper"]["loss"] = ("0.8 L1 + 0.2 (1 - SSIM 11x11) + 0.1 M_T |I - I_m|^2 by the fused "
                             "hm_hybrid_loss (lambda_t of iteration 5000 of the warm-up schedule)")
