@@ -297,8 +297,7 @@ def test_depth_key_is_rounded_fp64_fma_chain():
     with exact rational arithmetic of FP32 inputs and a single FP32 rounding
     (the FMA chain in FP64 is exact for these short-mantissa inputs)."""
     from fractions import Fraction
-    s = scenes.config1_scene(n_views=1) if False else scenes.room_scene(5, n_tris=2000, n_gauss=500,
-                                                                         resolutions=((64, 48),))
+    s = scenes.room_scene(5, n_tris=2000, n_gauss=500, resolutions=((64, 48),))
     cam = s.cameras[0]
     p = O.project(cam, s.gaussians)
     R, t = cam.R.astype(np.float32), cam.t.astype(np.float32)
