@@ -429,6 +429,18 @@ hm_status hm_mesh_prune(const hm_camera *cams, int32_t n_views, const float *ver
                         const float *normals, const hm_prune_params *p, uint8_t *flags,
                         int32_t *label, void *ws, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* hm_selftest_bounded_waits -- failure detection without a fault: one thread
+ * runs the library's two bounded waits (the scans' look-back wait and the
+ * blend kernels' mbarrier wait) on a slot that is never published
+ * (d_zero_slot: device uint64, zero) and an mbarrier nothing arrives at.
+ * Each gives up after its poll limit (well under a second in total), ORs
+ * HM_DEV_TIMEOUT into *d_status and the kernel returns, leaving the context
+ * usable.  d_out[2] (device int32): 1 where a wait completed (expected 0, 0).
+ * Launches only. */
+hm_status hm_selftest_bounded_waits(const unsigned long long *d_zero_slot, int32_t *d_status,
+                                    int32_t *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,21 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Bounded wait for a decoupled look-back slot to be published (its top two
+// bits nonzero): false after kSpinLimit polls, with HM_DEV_TIMEOUT set.
+__device__ __forceinline__ bool wait_published(const unsigned long long *slot, unsigned long long &val,
+                                               int32_t *d_status) {
+    for (int spins = 0;; ++spins) {
+        val = ld_volatile_u64(slot);
+        if ((val >> 62) != 0) return true;
+        if (spins >= kSpinLimit) {
+            set_status(d_status, HM_DEV_TIMEOUT);
+            return false;
+        }
+        __nanosleep(100);
+    }
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

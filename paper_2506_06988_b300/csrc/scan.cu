@@ -6,7 +6,9 @@
 // to a CTA that is already running: the look-back always terminates.  Each
 // wait is still bounded; on expiry HM_DEV_TIMEOUT is set and the CTA
 // proceeds with what it has.
+#include "hm_host.h"
 #include "hm_internal.cuh"
+#include "tma.cuh"
 
 namespace hm {
 
@@ -81,17 +83,9 @@ scan_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ idx,
             } else {
                 st_volatile_u64(&tstat[tile], kFlagAgg | agg);
                 long long p = tile - 1;
-                int spins = 0;
                 while (p >= 0) {
-                    unsigned long long s = ld_volatile_u64(&tstat[p]);
-                    if ((s >> 62) == 0) {
-                        if (++spins > kSpinLimit) {
-                            set_status(d_status, HM_DEV_TIMEOUT);
-                            break;
-                        }
-                        __nanosleep(100);
-                        continue;
-                    }
+                    unsigned long long s;
+                    if (!wait_published(&tstat[p], s, d_status)) break;
                     prefix += s & kValMask;
                     if ((s >> 62) == 2) break;
                     --p;
@@ -148,3 +142,32 @@ cudaError_t launch_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, 
 }
 
 }  // namespace hm
+
+namespace hm {
+namespace {
+
+// The failure-detection self-test: the library's two bounded waits, each on
+// something nothing completes -- a look-back slot never published and an
+// mbarrier nobody arrives at -- must give up, report HM_DEV_TIMEOUT and return.
+__global__ void selftest_waits_kernel(const unsigned long long *never, int32_t *d_status, int32_t *out) {
+    __shared__ uint64_t bar;
+    unsigned long long v = 0;
+    const bool got_slot = wait_published(never, v, d_status);
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    const bool got_bar = mbar_wait(&bar, 0);
+    if (!got_bar) set_status(d_status, HM_DEV_TIMEOUT);
+    mbar_inval(&bar);
+    out[0] = got_slot ? 1 : 0;
+    out[1] = got_bar ? 1 : 0;
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_selftest_bounded_waits(const unsigned long long *d_zero_slot, int32_t *d_status,
+                                               int32_t *d_out, void *stream) {
+    if (!d_zero_slot || !d_status || !d_out) return hm::fail(HM_ERR_INVALID_ARG, "null pointer");
+    hm::selftest_waits_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_zero_slot, d_status, d_out);
+    return hm::cuda_status(cudaGetLastError());
+}

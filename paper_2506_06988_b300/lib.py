@@ -43,6 +43,7 @@ EXPORTS = [
     "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss",
     "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
     "hm_adam_update", "hm_adam_update_dev", "hm_adam_advance", "hm_activate", "hm_activate_backward",
+    "hm_selftest_bounded_waits",
 ]
 
 
@@ -112,6 +113,7 @@ _SIGS = {
                                      c_float, c_void_p, c_void_p, c_void_p]),
     "hm_adam_advance": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "hm_activate": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hm_selftest_bounded_waits": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hm_activate_backward": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p]),
     "hm_mesh_prune_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int32]),
@@ -314,6 +316,10 @@ def hm_adam_update_dev(param, grad, m, v, n, lr, beta1, beta2, eps, d_rc, d_stat
 
 def hm_adam_advance(d_step, beta1, beta2, d_rc, d_status, stream):
     return load().hm_adam_advance(_ptr(d_step), beta1, beta2, _ptr(d_rc), _ptr(d_status), stream)
+
+
+def hm_selftest_bounded_waits(d_zero_slot, d_status, d_out, stream):
+    return load().hm_selftest_bounded_waits(_ptr(d_zero_slot), _ptr(d_status), _ptr(d_out), stream)
 
 
 def hm_activate(n, log_scales, logit, scales, opacity, stream):
