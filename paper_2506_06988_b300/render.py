@@ -215,11 +215,21 @@ class Renderer:
                                            self.sh_degree, self.sh_format, self.opt, self.records,
                                            _stream(), filter_3d=self.filter_3d), "hm_project_gaussians")
 
-    def bin_sort(self):
-        tmax = self.tile_max if self.has_mesh else None
-        lib.check(lib.hm_bin_sort(self.cams, self.n, self.records, tmax, self.opt, self.pair_vals,
-                                  self._pair_cap, self.n_pairs, self.ranges, self.status_word,
-                                  self.bin_ws, self.bin_ws.numel(), _stream()), "hm_bin_sort")
+    def bin_sort(self, mesh_cull: Optional[bool] = None):
+        """Binning and the per-tile depth sort; ``mesh_cull`` False bins
+        without the tiles' mesh depths (so it can run before the mesh pass
+        ends): longer lists, the same images -- the blend cuts every pixel at
+        its mesh depth and the culled pairs are a depth-sorted suffix."""
+        cull = self.opt.mesh_cull if mesh_cull is None else int(bool(mesh_cull))
+        tmax = self.tile_max if (self.has_mesh and cull) else None
+        saved = self.opt.mesh_cull
+        self.opt.mesh_cull = cull
+        try:
+            lib.check(lib.hm_bin_sort(self.cams, self.n, self.records, tmax, self.opt, self.pair_vals,
+                                      self._pair_cap, self.n_pairs, self.ranges, self.status_word,
+                                      self.bin_ws, self.bin_ws.numel(), _stream()), "hm_bin_sort")
+        finally:
+            self.opt.mesh_cull = saved
 
     def blend(self, eval_stats: Optional[torch.Tensor] = None):
         md = self.mesh_depth if self.has_mesh else None
@@ -246,9 +256,10 @@ class Renderer:
                 overlap: Optional[bool] = None):
         """All four stages, asynchronously on the current stream.  With
         ``overlap`` (default ``self.overlap``) the mesh pass runs on a side
-        stream concurrently with the projection (they are independent; the
-        binning needs both) and joins the current stream before the binning
-        -- inside a graph capture this becomes a fork and a join."""
+        stream while the projection and the binning (without the tile mesh
+        cull, which would wait for the mesh pass) run on the current stream;
+        the blend joins them -- inside a graph capture a fork and a join.
+        The images, counts and stop indices are the same either way."""
         self.status_word.zero_()
         if self.has_mesh and (self.overlap if overlap is None else overlap):
             main = torch.cuda.current_stream(self.device)
@@ -257,7 +268,10 @@ class Renderer:
             with torch.cuda.stream(side):
                 self.rasterize_mesh(mesh)
             self.project(means, scales, quats, opacity, sh)
+            self.bin_sort(mesh_cull=False)
             main.wait_stream(side)
+            self.blend()
+            return
         else:
             if self.has_mesh:
                 self.rasterize_mesh(mesh)
@@ -271,11 +285,11 @@ class Renderer:
         return st, npairs, nitems
 
     def render(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None,
-               max_retries: int = 3):
+               max_retries: int = 3, overlap: Optional[bool] = None):
         """forward() plus the capacity check; grows the buffers and re-runs
         when a capacity was exceeded.  Raises on HM_DEV_TIMEOUT."""
         for _ in range(max_retries + 1):
-            self.forward(means, scales, quats, opacity, sh, mesh)
+            self.forward(means, scales, quats, opacity, sh, mesh, overlap=overlap)
             st, npairs, nitems = self.status()
             if st & lib.HM_DEV_TIMEOUT:
                 raise lib.HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
@@ -468,7 +482,7 @@ class GraphStep:
 
     def capture(self):
         r = self.r
-        r.render(*self.params, self.mesh)                 # settles the capacities
+        r.render(*self.params, self.mesh, overlap=True)   # settles the capacities the graph needs
         side = torch.cuda.Stream(device=r.device)
         side.wait_stream(torch.cuda.current_stream(r.device))
         with torch.cuda.stream(side):                    # lazy workspaces, first-call set-up

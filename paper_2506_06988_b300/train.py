@@ -106,7 +106,7 @@ class JointTrainStep:
         # settle the pair / work-item capacities with the current parameters
         s = torch.cuda.current_stream(r.device).cuda_stream
         lib.check(lib.hm_activate(r.n, p["log_scales"], p["logit"], self.scales, self.opacity, s), "hm_activate")
-        r.render(p["means"], self.scales, p["quats"], self.opacity, p["sh"], self.mesh)
+        r.render(p["means"], self.scales, p["quats"], self.opacity, p["sh"], self.mesh, overlap=True)
         side = torch.cuda.Stream(device=r.device)
         side.wait_stream(torch.cuda.current_stream(r.device))
         with torch.cuda.stream(side):                    # lazy workspaces; no parameter update
