@@ -322,7 +322,9 @@ int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options 
  *  Outputs: loss_out (device double[4]: L1, mean SSIM, L_t, L), dL_drgb
  *  (dL/dI_h, planar, written), dL_dmesh (lambda_t dL_t/dI_m, planar,
  *  written; pass it to hm_blend_backward).  The partial sums are reduced in
- *  a fixed order, so equal inputs give bitwise-equal results.
+ *  a fixed order, so equal inputs give bitwise-equal results.  With
+ *  lambda_ssim == 0 the SSIM term is not evaluated: one pointwise pass,
+ *  dL/dI_h = sign(I_h - I) / N (0 on ties), and loss_out[1] is 0.
  *  ws: hm_hybrid_loss_workspace_size(cams, n_views) bytes of device memory.
  *  Errors: HM_ERR_INVALID_ARG (bad cameras, null pointers, an incomplete
  *  mesh set, lambda_ssim outside [0, 1] or lambda_t < 0), HM_ERR_WORKSPACE
@@ -334,6 +336,13 @@ typedef struct hm_loss_params {
     float lambda_t;          /* weight of the texture loss (0.1; 0 in the warm-up) */
     float k;                 /* slope of the transmittance mask (20) */
 } hm_loss_params;
+
+/* hm_decode_u8 -- 8-bit image codes to the [0, 1] intensities the loss
+ * compares against: dst[i] = src[i] / 255 (correctly rounded FP32), for
+ * loading a target image.  src (n bytes) and dst (n floats) are device
+ * memory, 16-byte aligned.  Errors: HM_ERR_INVALID_ARG (n < 0, null or
+ * misaligned pointers), HM_ERR_CUDA.  Launches only. */
+hm_status hm_decode_u8(const uint8_t *src, int64_t n, float *dst, void *stream);
 
 void hm_default_loss_params(hm_loss_params *p);
 size_t hm_hybrid_loss_workspace_size(const hm_camera *cams, int32_t n_views);

@@ -314,6 +314,47 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     }
 }
 
+// The loss without its SSIM term (lambda_ssim == 0): pointwise, a thread per
+// pixel of all cameras over its three channels -- L1 and its gradient
+// sign(x - y) / N, and the texture loss as in the tiled pass; per-CTA
+// partial sums for the fixed-order final reduction (the SSIM slot is 0).
+__global__ void __launch_bounds__(kNT)
+l1_loss_kernel(ViewTable vt, const float *__restrict__ x_all, const float *__restrict__ y_all,
+               const float *__restrict__ m_all, const float *__restrict__ T_all, const float *__restrict__ md_all,
+               float k_mask, float l1_scale, float mesh_grad_scale, float *__restrict__ dL_drgb,
+               float *__restrict__ dL_dmesh, double *__restrict__ partials) {
+    __shared__ double s_red[3][kNT / 32];
+    float l1 = 0.f, lt = 0.f;
+    for (long long gp = (long long)blockIdx.x * kNT + threadIdx.x; gp < vt.total_pixels;
+         gp += (long long)gridDim.x * kNT) {
+        const int v = view_of_pixel(vt, gp);
+        const ViewDev &V = vt.v[v];
+        const long long lp = gp - V.pix_off, npx = (long long)V.W * V.H;
+        float mt = 0.f;
+        const bool hit = m_all && md_all[gp] < INFINITY;
+        if (hit) mt = 1.f / (1.f + expf(-k_mask * (T_all[gp] - 0.5f)));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long o = 3 * V.pix_off + c * npx + lp;
+            const float xv = x_all[o], yv = y_all[o];
+            l1 += fabsf(xv - yv);
+            dL_drgb[o] = xv > yv ? l1_scale : (xv < yv ? -l1_scale : 0.f);
+            if (m_all) {
+                float g = 0.f;
+                if (hit) {
+                    const float d = yv - m_all[o];
+                    lt = fmaf(mt * d, d, lt);
+                    g = mesh_grad_scale * mt * -d;
+                }
+                dL_dmesh[o] = g;
+            }
+        }
+    }
+    double sums[3] = {(double)l1, 0.0, (double)lt};
+    block_sum3(sums, s_red);
+    if (threadIdx.x < 3) partials[3 * (long long)blockIdx.x + threadIdx.x] = s_red[threadIdx.x][0];
+}
+
 // one CTA: each thread sums a strided subset of the CTA partials, then a
 // fixed-shape tree -- the same order on every call
 __global__ void __launch_bounds__(kNT)
@@ -321,7 +362,22 @@ loss_final_kernel(const double *__restrict__ partials, int n_part, double inv_n,
                   double *__restrict__ out) {
     __shared__ double s_red[3][kNT / 32];
     double v[3] = {0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < n_part; i += kNT)
+    // eight strided partials loaded before they are added (in the same order
+    // as one at a time): the loads overlap instead of serialising
+    constexpr int kDepth = 8;
+    int i = threadIdx.x;
+    for (; i + (kDepth - 1) * kNT < n_part; i += kDepth * kNT) {
+        double b[kDepth][3];
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) b[d][q] = partials[3 * (long long)(i + d * kNT) + q];
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] += b[d][q];
+    }
+    for (; i < n_part; i += kNT)
 #pragma unroll
         for (int q = 0; q < 3; ++q) v[q] += partials[3 * (long long)i + q];
     block_sum3(v, s_red);
@@ -332,6 +388,28 @@ loss_final_kernel(const double *__restrict__ partials, int n_part, double inv_n,
         out[2] = t;
         out[3] = (1.0 - ls) * l1 + ls * (1.0 - ss) + lt * t;
     }
+}
+
+// 8-bit image codes to [0, 1]: 16 codes per thread step (one uint4 load,
+// four float4 stores), the ragged tail one by one
+__global__ void __launch_bounds__(kNT)
+decode_u8_kernel(const uint8_t *__restrict__ src, long long n, float *__restrict__ dst) {
+    const long long n16 = n / 16;
+    const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (long long i = (long long)blockIdx.x * kNT + threadIdx.x; i < n16; i += (long long)gridDim.x * kNT) {
+        const uint4 w = s16[i];
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float f[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) f[b] = __fdiv_rn((float)((ww[q] >> (8 * b)) & 0xFFu), 255.f);
+            d4[4 * i + q] = make_float4(f[0], f[1], f[2], f[3]);
+        }
+    }
+    for (long long i = 16 * n16 + (long long)blockIdx.x * kNT + threadIdx.x; i < n; i += (long long)gridDim.x * kNT)
+        dst[i] = __fdiv_rn((float)src[i], 255.f);
 }
 
 // the camera table with kLT x kLT loss tiles (validated as 16 x 16 render
@@ -406,6 +484,22 @@ extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, cons
         for (int k = 0; k < kTaps; ++k) tp.g[k] = (float)(g[k] / tot);
     }
     const double n_el = (double)np3;
+    if (p->lambda_ssim == 0.f) {
+        // no SSIM term: one pointwise pass; mean SSIM is reported as 0
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long blocks = (vt.total_pixels + kNT - 1) / kNT;
+        long long g1l = blocks < 8LL * sms ? blocks : 8LL * sms;
+        if (g1l > 3LL * vt.total_tiles) g1l = 3LL * vt.total_tiles;   // the partials buffer holds 3 per tile
+        const int g1 = (int)g1l;
+        l1_loss_kernel<<<g1, kNT, 0, s>>>(vt, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T, mesh_depth, p->k,
+                                          (float)(1.0 / n_el), (float)(2.0 * p->lambda_t / n_el), dL_drgb,
+                                          dL_dmesh, partials);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        loss_final_kernel<<<1, kNT, 0, s>>>(partials, g1, 1.0 / n_el, 0.0, p->lambda_t, loss_out);
+        return cuda_status(cudaGetLastError());
+    }
     dim3 grid(vt.total_tiles, 3);
     ssim_fwd_kernel<<<grid, kNT, 0, s>>>(vt, tp, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T,
                                                mesh_depth, p->k, (float)(2.0 * p->lambda_t / n_el), d_mu_xx,
@@ -417,5 +511,20 @@ extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     loss_final_kernel<<<1, kNT, 0, s>>>(partials, 3 * vt.total_tiles, 1.0 / n_el, p->lambda_ssim, p->lambda_t,
                                         loss_out);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" hm_status hm_decode_u8(const uint8_t *src, int64_t n, float *dst, void *stream) {
+    if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return HM_OK;
+    if (!src || !dst) return fail(HM_ERR_INVALID_ARG, "null pointer");
+    if (((uintptr_t)src & 15) || ((uintptr_t)dst & 15))
+        return fail(HM_ERR_INVALID_ARG, "src and dst must be 16-byte aligned");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long need = (n / 16 + kNT - 1) / kNT + 1;
+    const int grid = (int)(need < 8LL * sms ? need : 8LL * sms);
+    decode_u8_kernel<<<grid, kNT, 0, (cudaStream_t)stream>>>(src, n, dst);
     return cuda_status(cudaGetLastError());
 }

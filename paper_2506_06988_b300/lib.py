@@ -40,7 +40,7 @@ EXPORTS = [
     "hm_bin_sort_workspace_size", "hm_bin_sort",
     "hm_blend_forward",
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
-    "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss",
+    "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss", "hm_decode_u8",
     "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
     "hm_adam_update", "hm_adam_update_dev", "hm_adam_advance", "hm_activate", "hm_activate_backward",
     "hm_selftest_bounded_waits",
@@ -120,6 +120,7 @@ _SIGS = {
     "hm_mesh_prune": (c_int32, [_CAM_P, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p,
                                 _PRUNE_P, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_hybrid_loss_workspace_size": (c_size_t, [_CAM_P, c_int32]),
+    "hm_decode_u8": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p]),
     "hm_hybrid_loss": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  _LOSS_P, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_blend_backward_noalloc": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
@@ -341,6 +342,10 @@ def loss_params(lambda_ssim=None, lambda_t=None, k=None) -> HmLossParams:
     if k is not None:
         p.k = float(k)
     return p
+
+
+def hm_decode_u8(src, n, dst, stream):
+    return load().hm_decode_u8(_ptr(src), n, _ptr(dst), stream)
 
 
 def hm_hybrid_loss_workspace_size(cams) -> int:

@@ -457,18 +457,38 @@ class GraphStep:
     The capture follows an eager frame that settles the pair and work-item
     capacities; ``replay(check=True)`` synchronises, and on a capacity
     overflow grows the buffers eagerly and captures again.
+
+    With a ``target`` (planar like ``rgb``; float32 in [0, 1], or uint8
+    codes decoded in the graph by hm_decode_u8) the graph also evaluates the
+    joint loss (hm_hybrid_loss with ``loss_params``) and back-propagates its
+    gradient; ``loss_terms`` is then the device float64 [L1, mean SSIM,
+    L_t, L] of the last replay.
     """
 
     def __init__(self, renderer: Renderer, params, mesh: Optional[MeshInput] = None,
                  dL_drgb: Optional[torch.Tensor] = None, dL_dT: Optional[torch.Tensor] = None,
-                 grads=None, tex_grad: bool = False):
+                 grads=None, tex_grad: bool = False, target: Optional[torch.Tensor] = None,
+                 loss_params=None):
         self.r = renderer
         self.params = tuple(params)
         self.mesh = mesh
         self.dI, self.dT = dL_drgb, dL_dT
+        if target is not None and dL_drgb is not None:
+            raise ValueError("give either an upstream gradient or a target, not both")
+        self.target = target
+        self.target_f = None
+        if target is not None:
+            if target.numel() != 3 * renderer.npix or not target.is_contiguous():
+                raise ValueError("target: a contiguous planar image of every camera")
+            if target.dtype == torch.uint8:
+                self.target_f = torch.empty(3 * renderer.npix, dtype=torch.float32, device=renderer.device)
+            elif target.dtype != torch.float32:
+                raise ValueError("target: uint8 or float32")
+        self.loss_params = loss_params if loss_params is not None else lib.loss_params()
+        self.loss_terms = None
         self.tex_grad = bool(tex_grad and renderer.has_mesh)
         self.grads = grads
-        if self.dI is not None and self.grads is None:
+        if (self.dI is not None or target is not None) and self.grads is None:
             self.grads = renderer.grad_buffers(mesh.texture.shape[:2] if self.tex_grad else None)
         self.graph = None
         self.capture()
@@ -476,9 +496,17 @@ class GraphStep:
     def _body(self):
         r = self.r
         r.forward(*self.params, self.mesh, overlap=True)
-        if self.dI is not None:
-            r.backward(*self.params, self.dI, self.dT, mesh=self.mesh, tex_grad=self.tex_grad,
-                       out=self.grads, zero=True, overlap=True)
+        dI, dM = self.dI, None
+        if self.target is not None:
+            tgt = self.target
+            if self.target_f is not None:
+                lib.check(lib.hm_decode_u8(tgt, tgt.numel(), self.target_f, _stream()), "hm_decode_u8")
+                tgt = self.target_f
+            self.loss_terms, dI, dM = r.loss(tgt, self.loss_params,
+                                             texture_loss=self.tex_grad and self.loss_params.lambda_t > 0)
+        if dI is not None:
+            r.backward(*self.params, dI, self.dT, mesh=self.mesh, tex_grad=self.tex_grad,
+                       out=self.grads, zero=True, overlap=True, dL_dmesh=dM)
 
     def capture(self):
         r = self.r

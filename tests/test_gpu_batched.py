@@ -63,6 +63,40 @@ def test_graph_step_matches_eager_frame():
         _grads_close(gs.grads, ref_g)
 
 
+@pytest.mark.parametrize("lambda_ssim", [0.0, 0.2])
+def test_graph_step_with_target_matches_eager_loss(lambda_ssim):
+    # the graph decodes the uint8 target, evaluates the loss and back-propagates
+    # it: the loss terms equal the eager hm_hybrid_loss on the decoded target,
+    # and the gradients the eager backward of its dL/dI
+    from paper_2506_06988_b300 import lib
+    s = _room(seed=33)
+    r, P, mesh = gpu_render(s)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    tgt8 = torch.randint(0, 256, (3 * r.npix,), dtype=torch.uint8, device="cuda", generator=gen)
+    tgt = torch.from_numpy(tgt8.cpu().numpy().astype(np.float32) / np.float32(255.0)).cuda()
+    lp = lib.loss_params(lambda_ssim=lambda_ssim, lambda_t=0.0)
+    terms, dI, _ = r.loss(tgt, lp, texture_loss=False)
+    ref_terms = terms.clone()
+    ref_g = r.backward(*_params(P), dI.clone(), None, mesh=mesh, tex_grad=True)
+    gs = GraphStep(r, _params(P), mesh, target=tgt8, loss_params=lp, tex_grad=True)
+    gs.replay(check=True)
+    torch.cuda.synchronize()
+    assert torch.equal(gs.loss_terms, ref_terms)
+    _grads_close(gs.grads, ref_g)
+
+
+def test_decode_u8_is_exact():
+    from paper_2506_06988_b300 import lib
+    for n in (0, 5, 16, 1000, 4099):
+        src = torch.arange(n, dtype=torch.int64).mul(37).remainder(256).to(torch.uint8).cuda()
+        dst = torch.full((max(n, 1),), -1.0, device="cuda")
+        lib.check(lib.hm_decode_u8(src, n, dst, torch.cuda.current_stream().cuda_stream), "hm_decode_u8")
+        torch.cuda.synchronize()
+        want = src.cpu().numpy().astype(np.float32) / np.float32(255.0)
+        assert np.array_equal(dst[:n].cpu().numpy(), want)
+
+
 def test_graph_step_reads_current_parameters():
     s = _room(seed=32)
     r, P, mesh = gpu_render(s)

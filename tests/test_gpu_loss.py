@@ -131,3 +131,41 @@ def test_joint_loss_texel_gradient_scatter():
     got = g["texture"].cpu().numpy().astype(np.float64)
     assert np.linalg.norm(got - want) <= 1e-4 * np.linalg.norm(want)
     assert np.all(np.abs(got - want) <= 1e-4 * np.abs(want) + 1e-6 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("sizes", [((37, 23),), ((16, 16), (5, 7), (70, 33))])
+def test_hybrid_loss_without_ssim_term(sizes):
+    # lambda_ssim = 0 takes the pointwise pass: L1, L_t and L as the oracle's,
+    # dL/dI_h = sign(x - y) / N exactly, mean SSIM reported as 0
+    rng = np.random.default_rng(20 + len(sizes))
+    cams_np, views = _case(rng, sizes)
+    cams = lib.cameras(cams_np)
+    x, y, m, T = _flat(views, "x"), _flat(views, "y"), _flat(views, "m"), _flat(views, "T")
+    x[::7] = y[::7]                      # ties: the subgradient 0
+    depth = torch.as_tensor(np.concatenate([np.where(v["hit"], 2.0, np.inf).reshape(-1) for v in views]),
+                            dtype=torch.float32, device="cuda")
+    xs = x.cpu().numpy()
+    off = 0
+    for v in views:
+        n = v["x"].size
+        v["x"] = xs[off:off + n].reshape(v["x"].shape).astype(np.float64)
+        off += n
+        for k in ("y", "m", "T"):
+            v[k] = np.asarray(v[k], np.float32).astype(np.float64)
+    (l1, _, lt, L), gx, gm = LO.loss_and_grads(views, lambda_s=0.0, lambda_t=0.1, k=20.0)
+    ws = torch.empty(lib.hm_hybrid_loss_workspace_size(cams), dtype=torch.uint8, device="cuda")
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    dI, dM = torch.empty_like(x), torch.empty_like(x)
+    lp = lib.loss_params(lambda_ssim=0.0, lambda_t=0.1)
+    lib.check(lib.hm_hybrid_loss(cams, x, y, m, T, depth, lp, out, dI, dM, ws, ws.numel(),
+                                 torch.cuda.current_stream().cuda_stream), "hm_hybrid_loss")
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert got[1] == 0.0
+    want = np.array([l1, lt, L])
+    assert np.all(np.abs(got[[0, 2, 3]] - want) <= 1e-5 * np.abs(want) + 1e-9), (got, want)
+    g_ref = np.concatenate([g.reshape(-1) for g in gx])
+    assert np.array_equal(dI.cpu().numpy(), g_ref.astype(np.float32))
+    gm_ref = np.concatenate([gg.reshape(-1) for gg in gm])
+    gmv = dM.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gmv - gm_ref) <= 1e-5 * np.abs(gm_ref) + 1e-12 * max(1.0, np.abs(gm_ref).max()))
