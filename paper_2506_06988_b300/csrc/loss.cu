@@ -9,13 +9,16 @@
 //
 // Two passes over 32 x 32 tiles, a CTA of 256 threads per (tile, channel):
 //  * ssim_fwd: the five window sums (mu_x, mu_y, E[x^2], E[y^2], E[xy]) by
-//    a horizontal then a vertical 11-tap pass through shared memory (halo 5;
-//    each thread computes 4 adjacent outputs of a pass from 14 loaded values;
-//    the vertical pass carries map pairs in FP32x2 FMAs),
+//    a horizontal then a vertical 11-tap pass through shared memory (halo 5,
+//    (x, y) interleaved; each thread computes 4 adjacent outputs of a pass
+//    from 14 loaded values; both passes carry the (x, y) pairs in FP32x2
+//    FMAs; all halo loads are issued before the first shared store),
 //    the SSIM map and its partial derivatives with respect to the window
 //    sums -- D_mu = dS/dmu_x, D_xx = dS/dE[x^2], D_xy = dS/dE[xy] -- to
 //    global scratch ((D_mu, D_xx) interleaved, D_xy a plane of its own); the pointwise L1 and texture-loss terms, dL/dI_m; the
-//    CTA's three partial sums (FP64) to its own slot.
+//    CTA's three partial sums (FP32 within a warp, FP64 across warps) to
+//    its own slot.  The SSIM quotient uses the hardware's approximate
+//    reciprocal (relative error ~2^-23).
 //  * ssim_bwd: since mu_x, E[x^2], E[xy] at pixel p are window sums of x,
 //    x^2 and x y, dSSIM_total/dx(q) = (w * D_mu)(q) + 2 x(q) (w * D_xx)(q)
 //    + y(q) (w * D_xy)(q): the same separable window over the three maps,
@@ -43,20 +46,39 @@ struct Taps {
     float g[kTaps];
 };
 
-// visit the (kLT + 2 kRad)^2 halo elements (row r, column c) of a tile,
-// kNT apart in row-major order, stepping (r, c) without divisions
-template <class F>
-__device__ __forceinline__ void for_halo(F &&f) {
-    int r = threadIdx.x / kHalo, c = threadIdx.x - r * kHalo;
-    for (int i = threadIdx.x; i < kHalo * kHalo; i += kNT) {
-        f(r, c);
-        r += kNT / kHalo;
-        c += kNT % kHalo;
-        if (c >= kHalo) {
-            c -= kHalo;
-            ++r;
-        }
+constexpr int kHaloSlots = (kHalo * kHalo + kNT - 1) / kNT;   // 7 halo elements per thread
+
+// halo element s of this thread: row r, column c; false past the halo
+__device__ __forceinline__ bool halo_slot(int s, int &r, int &c) {
+    const int i = threadIdx.x + s * kNT;
+    r = i / kHalo;
+    c = i - r * kHalo;
+    return i < kHalo * kHalo;
+}
+
+__device__ __forceinline__ void load_span2(const float2 *row, float2 (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 f = *reinterpret_cast<const float4 *>(row + 2 * q);
+        v[2 * q] = make_float2(f.x, f.y);
+        v[2 * q + 1] = make_float2(f.z, f.w);
     }
+}
+
+// out[o] = sum_k g[k] v[o + k] on both lanes of a pair, o < 4
+__device__ __forceinline__ void taps4x2(const Taps &tp, const float2 *v, float2 (&out)[kOut]) {
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) out[o] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kTaps; ++k)
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) out[o] = __ffma2_rn(make_float2(tp.g[k], tp.g[k]), v[o + k], out[o]);
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ void load_span(const float *row, float (&v)[16]) {
@@ -75,16 +97,6 @@ __device__ __forceinline__ void taps4(const Taps &tp, const float *v, float (&ou
     for (int k = 0; k < kTaps; ++k)
 #pragma unroll
         for (int o = 0; o < kOut; ++o) out[o] = fmaf(tp.g[k], v[o + k], out[o]);
-}
-
-// horizontal pass of one plane for (row r, columns c0 .. c0 + 3); the
-// result goes to lane `half` (0: x, 1: y) of a float2 plane or to a float plane
-__device__ __forceinline__ void horiz_store2(const Taps &tp, const float *row, float2 *dst, int half) {
-    float v[16], o[kOut];
-    load_span(row, v);
-    taps4(tp, v, o);
-#pragma unroll
-    for (int q = 0; q < kOut; ++q) reinterpret_cast<float *>(dst + q)[half] = o[q];
 }
 
 // vertical pass, thread (column c, rows 4 rg .. 4 rg + 3): each loaded row
@@ -118,6 +130,25 @@ __device__ __forceinline__ void vert4x1(const Taps &tp, const float (*sh)[kLT], 
     }
 }
 
+// FP32 warp sums (each lane holds a few pixels), then the eight warp sums in
+// FP64 in a fixed order; the result lands in s_red[q][0]
+__device__ __forceinline__ void block_sum3_warps(float (&v)[3], double (*s_red)[kNT / 32]) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) s_red[q][w] = (double)v[q];
+    }
+    __syncthreads();
+    if (t < 3) {
+        double r = 0.0;
+        for (int k = 0; k < kNT / 32; ++k) r += s_red[t][k];
+        s_red[t][0] = r;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void block_sum3(double (&v)[3], double (*s_red)[kNT / 32]) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 #pragma unroll
@@ -143,7 +174,7 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
                 const float *__restrict__ md_all, float k_mask, float mesh_grad_scale,
                 float2 *__restrict__ d_mu_xx, float *__restrict__ d_xy,
                 float *__restrict__ dL_dmesh, double *__restrict__ partials) {
-    __shared__ __align__(16) float s_in[2][kHalo][kHS];
+    __shared__ __align__(16) float2 s_in[kHalo][kHS];   // (x, y) interleaved
     __shared__ __align__(16) float2 s_m[kHalo][kLT];    // (w*x, w*y) along rows
     __shared__ __align__(16) float2 s_q[kHalo][kLT];    // (w*x^2, w*y^2)
     __shared__ __align__(16) float s_c[kHalo][kLT];     // w*(x y)
@@ -157,47 +188,43 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     const long long base = 3 * V.pix_off + ch * npx;
     const int t = threadIdx.x;
     {
+        // every load of the halo issued before the first shared-memory store
         const float *x = x_all + base, *y = y_all + base;
         const int W = V.W, H = V.H;
-        for_halo([&](int r, int c) {
+        float2 hv[kHaloSlots];
+#pragma unroll
+        for (int k = 0; k < kHaloSlots; ++k) {
+            int r, c;
+            const bool in = halo_slot(k, r, c);
             const int gx = px0 - kRad + c, gy = py0 - kRad + r;
-            float xv = 0.f, yv = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            hv[k] = make_float2(0.f, 0.f);
+            if (in && gx >= 0 && gx < W && gy >= 0 && gy < H) {
                 const long long o = (long long)gy * W + gx;
-                xv = x[o];
-                yv = y[o];
+                hv[k] = make_float2(x[o], y[o]);
             }
-            s_in[0][r][c] = xv;
-            s_in[1][r][c] = yv;
-        });
+        }
+#pragma unroll
+        for (int k = 0; k < kHaloSlots; ++k) {
+            int r, c;
+            if (halo_slot(k, r, c)) s_in[r][c] = hv[k];
+        }
     }
     __syncthreads();
-    // horizontal: (row r, columns c0 .. c0 + 3) of the five products
+    // horizontal: (row r, columns c0 .. c0 + 3) of the five products, the
+    // (x, y) pairs in FP32x2
     for (int i = t; i < kHalo * (kLT / kOut); i += kNT) {
         const int r = i / (kLT / kOut), c0 = kOut * (i % (kLT / kOut));
-        float xs[16], ys[16], p[kSpan], o[kOut];
-        load_span(&s_in[0][r][c0], xs);
-        load_span(&s_in[1][r][c0], ys);
-        float2 mm[kOut], qq[kOut];
-        taps4(tp, xs, o);
+        float2 xy[16], sq[kSpan], mm[kOut], qq[kOut];
+        float pr[kSpan], o[kOut];
+        load_span2(&s_in[r][c0], xy);
 #pragma unroll
-        for (int q = 0; q < kOut; ++q) mm[q].x = o[q];
-        taps4(tp, ys, o);
-#pragma unroll
-        for (int q = 0; q < kOut; ++q) mm[q].y = o[q];
-#pragma unroll
-        for (int j = 0; j < kSpan; ++j) p[j] = xs[j] * xs[j];
-        taps4(tp, p, o);
-#pragma unroll
-        for (int q = 0; q < kOut; ++q) qq[q].x = o[q];
-#pragma unroll
-        for (int j = 0; j < kSpan; ++j) p[j] = ys[j] * ys[j];
-        taps4(tp, p, o);
-#pragma unroll
-        for (int q = 0; q < kOut; ++q) qq[q].y = o[q];
-#pragma unroll
-        for (int j = 0; j < kSpan; ++j) p[j] = xs[j] * ys[j];
-        taps4(tp, p, o);
+        for (int j = 0; j < kSpan; ++j) {
+            sq[j] = __fmul2_rn(xy[j], xy[j]);
+            pr[j] = xy[j].x * xy[j].y;
+        }
+        taps4x2(tp, xy, mm);
+        taps4x2(tp, sq, qq);
+        taps4(tp, pr, o);
         float4 *dm = reinterpret_cast<float4 *>(&s_m[r][c0]);
         float4 *dq = reinterpret_cast<float4 *>(&s_q[r][c0]);
         dm[0] = make_float4(mm[0].x, mm[0].y, mm[1].x, mm[1].y);
@@ -223,7 +250,7 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
         const float vx = ex2[q].x - mx * mx, vy = ex2[q].y - my * my, cxy = exy[q] - mx * my;
         const float A1 = fmaf(2.f * mx, my, kC1), A2 = fmaf(2.f, cxy, kC2);
         const float B1 = fmaf(mx, mx, fmaf(my, my, kC1)), B2 = vx + vy + kC2;
-        const float rA1 = __frcp_rn(A1), rA2 = __frcp_rn(A2), rB1 = __frcp_rn(B1), rB2 = __frcp_rn(B2);
+        const float rA1 = rcp_approx(A1), rA2 = rcp_approx(A2), rB1 = rcp_approx(B1), rB2 = rcp_approx(B2);
         const float S = (A1 * A2) * (rB1 * rB2);
         // dS/d(mu_x, E[x^2], E[xy]) with sigma_x^2 = E[x^2] - mu_x^2 and
         // sigma_xy = E[xy] - mu_x mu_y
@@ -233,7 +260,8 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
         d_mu_xx[o] = make_float2(dmu, -S * rB2);
         d_xy[o] = 2.f * S * rA2;
         ssum += S;
-        const float xv = s_in[0][r + kRad][c + kRad], yv = s_in[1][r + kRad][c + kRad];
+        const float2 xyc = s_in[r + kRad][c + kRad];
+        const float xv = xyc.x, yv = xyc.y;
         l1 += fabsf(xv - yv);
         if (m_all) {
             const bool hit = md_all[V.pix_off + lp] < INFINITY;
@@ -247,8 +275,8 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
             dL_dmesh[o] = g;
         }
     }
-    double sums[3] = {(double)l1, (double)ssum, (double)lt};
-    block_sum3(sums, s_red);
+    float sums[3] = {l1, ssum, lt};
+    block_sum3_warps(sums, s_red);
     if (t < 3) partials[3 * ((long long)ch * gridDim.x + gt) + t] = s_red[t][0];
 }
 
@@ -256,7 +284,8 @@ __global__ void __launch_bounds__(kNT)
 ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
                 const float2 *__restrict__ d_mu_xx, const float *__restrict__ d_xy,
                 float l1_scale, float ssim_scale, float *__restrict__ dL_drgb) {
-    __shared__ __align__(16) float s_d[3][kHalo][kHS];
+    __shared__ __align__(16) float2 s_d[kHalo][kHS];    // (D_mu, D_xx) interleaved
+    __shared__ __align__(16) float s_dxy[kHalo][kHS];   // D_xy
     __shared__ __align__(16) float2 s_ab[kHalo][kLT];   // w*D_mu, w*D_xx along rows
     __shared__ __align__(16) float s_e[kHalo][kLT];     // w*D_xy
     const int gt = blockIdx.x, ch = blockIdx.y;
@@ -267,31 +296,57 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     const long long npx = (long long)V.W * V.H;
     const long long base = 3 * V.pix_off + ch * npx;
     const int t = threadIdx.x;
+    // this thread's four output pixels: x and y fetched now, used at the end
+    float xo[kOut], yo[kOut];
+#pragma unroll
+    for (int q = 0; q < kOut; ++q) {
+        const int px = px0 + (t & 31), py = py0 + kOut * (t >> 5) + q;
+        xo[q] = yo[q] = 0.f;
+        if (px < V.W && py < V.H) {
+            const long long o = base + (long long)py * V.W + px;
+            xo[q] = x_all[o];
+            yo[q] = y_all[o];
+        }
+    }
     {
         const float2 *ab = d_mu_xx + base;
         const float *e = d_xy + base;
         const int W = V.W, H = V.H;
-        for_halo([&](int r, int c) {
+        float2 ha[kHaloSlots];
+        float he[kHaloSlots];
+#pragma unroll
+        for (int k = 0; k < kHaloSlots; ++k) {
+            int r, c;
+            const bool in = halo_slot(k, r, c);
             const int gx = px0 - kRad + c, gy = py0 - kRad + r;
-            float2 a = make_float2(0.f, 0.f);
-            float ev = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            ha[k] = make_float2(0.f, 0.f);
+            he[k] = 0.f;
+            if (in && gx >= 0 && gx < W && gy >= 0 && gy < H) {
                 const long long o = (long long)gy * W + gx;
-                a = ab[o];
-                ev = e[o];
+                ha[k] = ab[o];
+                he[k] = e[o];
             }
-            s_d[0][r][c] = a.x;
-            s_d[1][r][c] = a.y;
-            s_d[2][r][c] = ev;
-        });
+        }
+#pragma unroll
+        for (int k = 0; k < kHaloSlots; ++k) {
+            int r, c;
+            if (halo_slot(k, r, c)) {
+                s_d[r][c] = ha[k];
+                s_dxy[r][c] = he[k];
+            }
+        }
     }
     __syncthreads();
     for (int i = t; i < kHalo * (kLT / kOut); i += kNT) {
         const int r = i / (kLT / kOut), c0 = kOut * (i % (kLT / kOut));
-        horiz_store2(tp, &s_d[0][r][c0], &s_ab[r][c0], 0);
-        horiz_store2(tp, &s_d[1][r][c0], &s_ab[r][c0], 1);
+        float2 dv[16], oab[kOut];
+        load_span2(&s_d[r][c0], dv);
+        taps4x2(tp, dv, oab);
+        float4 *dst = reinterpret_cast<float4 *>(&s_ab[r][c0]);
+        dst[0] = make_float4(oab[0].x, oab[0].y, oab[1].x, oab[1].y);
+        dst[1] = make_float4(oab[2].x, oab[2].y, oab[3].x, oab[3].y);
         float vs[16], o[kOut];
-        load_span(&s_d[2][r][c0], vs);
+        load_span(&s_dxy[r][c0], vs);
         taps4(tp, vs, o);
         *reinterpret_cast<float4 *>(&s_e[r][c0]) = make_float4(o[0], o[1], o[2], o[3]);
     }
@@ -307,7 +362,7 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
         const int py = py0 + kOut * rg + q;
         if (px >= V.W || py >= V.H) continue;
         const long long o = base + (long long)py * V.W + px;
-        const float xv = x_all[o], yv = y_all[o];
+        const float xv = xo[q], yv = yo[q];
         const float dS = fmaf(2.f * xv, ab[q].y, fmaf(yv, e[q], ab[q].x));
         const float sg = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
         dL_drgb[o] = fmaf(l1_scale, sg, -ssim_scale * dS);

