@@ -23,8 +23,9 @@
 //    x^2 and x y, dSSIM_total/dx(q) = (w * D_mu)(q) + 2 x(q) (w * D_xx)(q)
 //    + y(q) (w * D_xy)(q): the same separable window over the three maps,
 //    then dL/dI_h = ((1 - ls) sign(x - y) - ls dSSIM/dx) / N.
-//  * loss_final: the partial sums in a fixed order (the loss is bitwise
-//    reproducible) and the weighted total.
+//  * loss_reduce / loss_final: the partial sums in a fixed order over a
+//    fixed partition (the loss is bitwise reproducible) and the weighted
+//    total.
 #include "hm_host.h"
 
 namespace hm {
@@ -410,6 +411,23 @@ l1_loss_kernel(ViewTable vt, const float *__restrict__ x_all, const float *__res
     if (threadIdx.x < 3) partials[3 * (long long)blockIdx.x + threadIdx.x] = s_red[threadIdx.x][0];
 }
 
+// first level of the SSIM path's reduction (one partial per tile and channel,
+// tens of thousands): CTA b sums partials [b kChunk, (b + 1) kChunk) into
+// out[3 b .. 3 b + 2], so the FP64 additions spread over many SMs; the
+// partition is fixed, so the order is the same on every call
+constexpr int kChunk = 512;
+__global__ void __launch_bounds__(kNT)
+loss_reduce_kernel(const double *__restrict__ partials, int n_part, double *__restrict__ out) {
+    __shared__ double s_red[3][kNT / 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    const int lo = blockIdx.x * kChunk, hi = min(n_part, lo + kChunk);
+    for (int i = lo + threadIdx.x; i < hi; i += kNT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] += partials[3 * (long long)i + q];
+    block_sum3(v, s_red);
+    if (threadIdx.x < 3) out[3 * blockIdx.x + threadIdx.x] = s_red[threadIdx.x][0];
+}
+
 // one CTA: each thread sums a strided subset of the CTA partials, then a
 // fixed-shape tree -- the same order on every call
 __global__ void __launch_bounds__(kNT)
@@ -564,8 +582,11 @@ extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, cons
                                                (float)((1.0 - p->lambda_ssim) / n_el),
                                                (float)(p->lambda_ssim / n_el), dL_drgb);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    loss_final_kernel<<<1, kNT, 0, s>>>(partials, 3 * vt.total_tiles, 1.0 / n_el, p->lambda_ssim, p->lambda_t,
-                                        loss_out);
+    const int n_part = 3 * vt.total_tiles, n_red = (n_part + kChunk - 1) / kChunk;
+    double *level2 = partials + 3 * (size_t)n_part;     // 3 n_red <= 6 total_tiles doubles
+    loss_reduce_kernel<<<n_red, kNT, 0, s>>>(partials, n_part, level2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    loss_final_kernel<<<1, kNT, 0, s>>>(level2, n_red, 1.0 / n_el, p->lambda_ssim, p->lambda_t, loss_out);
     return cuda_status(cudaGetLastError());
 }
 
