@@ -865,11 +865,53 @@ def run_joint_opt(args, dev, dist):
     npx = W * H
     alg = npx * 4 * (3 + 3 + 3 + 1 + 1 + 3 + 3 + 2 * 9)
     out["loss_kernel"] = {"ms": lm, "alg_bytes": alg, "achieved_gbs": alg / lm / 1e6,
-                          "launches": 3, "note": "ssim_fwd + ssim_bwd + final over 32x32 tiles x 3 channels, "
-                                                        "20 calls in one CUDA graph (inputs L2-resident)"}
+                          "launches": 4, "note": "ssim_fwd + ssim_bwd + two reduction levels over 32x32 tiles "
+                                                 "x 3 channels, 20 calls in one CUDA graph (inputs L2-resident)"}
     del r, opt
     torch.cuda.empty_cache()
+    out["loss_kernel_8x1080p"] = time_loss_8x1080p(dev)
     return out
+
+
+def time_loss_8x1080p(dev):
+    """hm_hybrid_loss on 8 views of 1920x1080 (each input plane 199 MB, past
+    the L2): the Eq. 3 loss with D-SSIM, and the L1-only pointwise path."""
+    import torch
+    from paper_2506_06988_b300 import lib, scenes
+    cams = lib.cameras([scenes._identity_cam(1920, 1080) for _ in range(8)])
+    npx = 8 * 1920 * 1080
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    x = torch.rand(3 * npx, device=dev, generator=gen)
+    y = torch.rand(3 * npx, device=dev, generator=gen)
+    ws = torch.empty(lib.hm_hybrid_loss_workspace_size(cams), dtype=torch.uint8, device=dev)
+    lout = torch.empty(4, dtype=torch.float64, device=dev)
+    dI = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, lam, alg_per_px in (("ssim", 0.2, 4 * (3 + 3 + 3 + 2 * 9)), ("l1_only", 0.0, 4 * (3 + 3 + 3))):
+        lp = lib.loss_params(lambda_ssim=lam, lambda_t=0.0)
+
+        def call():
+            lib.check(lib.hm_hybrid_loss(cams, x, y, None, None, None, lp, lout, dI, None, ws, ws.numel(),
+                                         stream.cuda_stream), "hm_hybrid_loss")
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        alg = npx * alg_per_px
+        res[name] = {"ms": ms, "alg_bytes": alg, "achieved_gbs": alg / ms / 1e6}
+    res["note"] = ("algorithmic bytes: I_h, I read, dL/dI_h written; with D-SSIM also the 9 window "
+                   "statistics per pixel written and read once; back-to-back calls, inputs past the L2")
+    del x, y, ws, dI
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_large(args, dev, dist):
