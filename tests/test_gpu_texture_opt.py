@@ -95,3 +95,31 @@ def test_texture_recovery_on_gpu():
     assert last < 0.2 * first
     err = np.abs(opt.texture.cpu().numpy() - true_tex).mean()
     assert err < 0.5 * np.abs(0.5 - true_tex).mean()
+
+
+def test_texture_graph_step_matches_eager():
+    # the captured step replays the eager one: the same first loss bit for
+    # bit, the same step count, and texels that agree after three steps up
+    # to the order of the texel gradients' global additions
+    s = scenes.config0_scene(seed=2)
+    rng = np.random.default_rng(5)
+    tex0 = rng.uniform(0.2, 0.8, s.mesh.texture.shape).astype(np.float32)
+    true_tex = O.texture_unit(s.mesh.texture)
+    cam = s.cameras[0]
+    target = O.mesh_raster(cam, s.mesh, bg=np.asarray(s.bg, np.float64), tex=true_tex).rgb.astype(np.float32)
+    s.mesh.texture = tex0
+    tgt = torch.as_tensor(target.reshape(-1), device="cuda")
+    bg = tuple(np.asarray(s.bg, np.float64))
+    eager = TextureOptimizer(s.cameras, MeshInput.from_numpy(s.mesh), tgt, lr=0.01, bg=bg)
+    graph = TextureOptimizer(s.cameras, MeshInput.from_numpy(s.mesh), tgt, lr=0.01, bg=bg).capture()
+    firsts = []
+    for _ in range(3):
+        a = eager.step(check=True).clone()
+        b = graph.step(check=True).clone()
+        firsts.append((a, b))
+    torch.cuda.synchronize()
+    assert torch.equal(firsts[0][0], firsts[0][1])
+    assert eager.t == 3 and graph.t == 3
+    d = (eager.texture - graph.texture).abs()
+    assert float(d.max()) <= 2 * 0.01 * 3
+    assert float((d > 1e-5).float().mean()) <= 1e-2
