@@ -1075,7 +1075,8 @@ def run_e2e(args, scene, r, mesh, dev, dist, frames):
     forward, L1 loss by hm_hybrid_loss, backward with the texel gradients,
     all in one CUDA graph).  Every step copies its data -- the 8 target
     images, uint8 codes decoded in the graph -- from pinned host memory and
-    reads the loss back; the Gaussian parameters and the mesh are the
+    reads its loss back (after the next step is queued, as an asynchronous
+    training loop logs it); the Gaussian parameters and the mesh are the
     model's state and stay resident, as in a training loop.  The copy of
     step k+1 runs on a copy stream into a second target buffer (a second
     graph) while step k computes (double buffering, as a data loader's
@@ -1089,9 +1090,9 @@ def run_e2e(args, scene, r, mesh, dev, dist, frames):
     params = [torch.as_tensor(getattr(g, k)).to(dev).contiguous() for k in names]
     tgt_host = (torch.rand(3 * r.npix, generator=torch.Generator().manual_seed(5)) * 255).to(torch.uint8).pin_memory()
     bufs = [tgt_host.to(dev) for _ in range(2)]
-    loss_host = torch.empty(4, dtype=torch.float64).pin_memory()
+    loss_host = [torch.empty(4, dtype=torch.float64).pin_memory() for _ in range(2)]
     h2d = tgt_host.numel() * tgt_host.element_size()
-    d2h = loss_host.numel() * loss_host.element_size()
+    d2h = loss_host[0].numel() * loss_host[0].element_size()
     lp = lib.loss_params(lambda_ssim=0.0, lambda_t=0.0)
     grads = r.grad_buffers(tuple(mesh.texture.shape[:2]))
     graphs = [GraphStep(r, params, mesh, target=b, loss_params=lp, grads=grads, tex_grad=True) for b in bufs]
@@ -1099,6 +1100,8 @@ def run_e2e(args, scene, r, mesh, dev, dist, frames):
     copy = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     used = [torch.cuda.Event(), torch.cuda.Event()]
+    landed = [torch.cuda.Event(), torch.cuda.Event()]
+    losses = []
 
     def issue_copy(k):
         with torch.cuda.stream(copy):
@@ -1107,36 +1110,48 @@ def run_e2e(args, scene, r, mesh, dev, dist, frames):
             copied[k % 2].record(copy)
 
     def step(k):
+        # step k is queued before step k - 1's loss is waited for, so the
+        # device never idles on the host's read
         gs = graphs[k % 2]
         compute.wait_event(copied[k % 2])
         issue_copy(k + 1)                          # prefetch the next step's images
         gs.replay()
         used[k % 2].record(compute)
-        loss_host.copy_(gs.loss_terms, non_blocking=True)
-        compute.synchronize()
-        return float(loss_host[3])
+        loss_host[k % 2].copy_(gs.loss_terms, non_blocking=True)   # ordered before step k + 1 overwrites it
+        landed[k % 2].record(compute)
+
+    def read(k):
+        landed[k % 2].synchronize()
+        losses.append(float(loss_host[k % 2][3]))
+
+    def run(k0, k1):
+        for k in range(k0, k1):
+            step(k)
+            if k > k0:
+                read(k - 1)
+        read(k1 - 1)
 
     for ev in used:
         ev.record(compute)
     issue_copy(0)
-    for k in range(3):
-        step(k)
+    run(0, 3)
     st, _, _ = r.status()
     if st:
         raise RuntimeError(f"renderer status {st:#x} in the end-to-end step")
     n = max(10, min(args.steps, 50))
     _barrier(dist)
     t0 = time.perf_counter()
-    for k in range(3, 3 + n):
-        step(k)
+    run(3, 3 + n)
     _barrier(dist)
     sec = _max_over_ranks((time.perf_counter() - t0) / n, dist)
     torch.cuda.synchronize()
     return {"value": frames / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": sec * 1e3,
-            "api": "GraphStep(target=uint8 images, L1 loss) replay + loss read-back; the step's images "
-                   "copied from pinned host memory, double-buffered (next step's copy overlaps this "
-                   "step's compute); parameters resident"}
+            "losses_read": len(losses),
+            "api": "GraphStep(target=uint8 images, L1 loss) replay + every step's loss read back (step k's "
+                   "read waited for after step k + 1 is queued); the step's images copied from pinned host "
+                   "memory, double-buffered (next step's copy overlaps this step's compute); parameters "
+                   "resident"}
 
 
 def run_leg(args):
