@@ -107,7 +107,7 @@ typedef struct hm_options {
 #define HM_BWD_BLEND 2         /* blend replay -> per-record partials (workspace) */
 #define HM_BWD_PROJECT 4       /* partials -> Gaussian parameter gradients */
 
-/* Fill `opt` with the defaults: 16x16 tiles, batch 256, mesh_cull 1,
+/* Fill `opt` with the defaults: 16x16 tiles, batch 128, mesh_cull 1,
  * ellipse_cull 1, near planes 0.2 / 0.01, black background, all backward
  * parts, the 3DGS screen-space kernel (kernel_2d 0.3, antialias 0). */
 void hm_default_options(hm_options *opt);

@@ -67,17 +67,26 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
     return y;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2, 6)
+// Pixel layout of the replay: a warp covers 8 columns x 8 PP rows of the
+// tile; lane l owns column l % 8 and, for p < PP, the pixel pair of rows
+// l / 8 + 8 p and l / 8 + 8 p + 4 (PP = 1 is the forward's layout).  With
+// PP = 2 a thread holds two pairs of one column: the column part of q and
+// the warp reduction of the nine partials are shared by four pixels.  The
+// staged records live in dynamic shared memory sized by the batch.
+template <int TW, int TH, int PP>
+__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 12)
 blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                  const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2,
                  const float *__restrict__ out_T, const uint32_t *__restrict__ last_idx,
                  const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, int batch,
                  float *__restrict__ g2d, int32_t *__restrict__ d_status) {
-    constexpr int NT = TW * TH, NTH = NT / 2;
-    __shared__ Record s_rec[2][NT];
-    __shared__ uint32_t s_item[2][NT];
+    constexpr int NTH = TW * TH / (2 * PP);
+    constexpr int PER = (TW * TH + NTH - 1) / NTH;       // staged records per thread and round, at most
+    static_assert(TW % 8 == 0 && TH % (8 * PP) == 0, "tile shape");
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    Record *s_rec0 = reinterpret_cast<Record *>(s_dyn);              // [2][batch]
+    uint32_t *s_item0 = reinterpret_cast<uint32_t *>(s_rec0 + 2 * batch);   // [2][batch]
     __shared__ uint64_t s_bar[2];
     __shared__ uint32_t s_hi;
     const int gt = blockIdx.x;
@@ -86,29 +95,42 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x, lane = t & 31;
-    int px, pya, pyb;
-    pixel_pair<TW>(t, tx * TW, ty * TH, px, pya, pyb);
-    const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
+    constexpr int WX = TW / 8;
+    const int px = tx * TW + ((t >> 5) % WX) * 8 + (lane & 7);
+    const int row0 = ty * TH + ((t >> 5) / WX) * (8 * PP) + (lane >> 3);
     const long long npx = (long long)V.W * V.H;
-    const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
-    float2 Tf = make_float2(1.f, 1.f), gI0 = make_float2(0.f, 0.f), gI1 = gI0, gI2 = gI0, gT = gI0;
-    float2 B0 = make_float2(bg0, bg0), B1 = make_float2(bg1, bg1), B2 = make_float2(bg2, bg2);
-    uint32_t last_a = 0, last_b = 0;
     const float *gI = dL_drgb + 3 * V.pix_off;
     const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
-    if (in_a) {
-        Tf.x = out_T[V.pix_off + lpa];
-        last_a = last_idx[V.pix_off + lpa];
-        gI0.x = gI[lpa]; gI1.x = gI[npx + lpa]; gI2.x = gI[2 * npx + lpa];
-        if (dL_dT) gT.x = dL_dT[V.pix_off + lpa];
-        if (mr) { B0.x = mr[lpa]; B1.x = mr[npx + lpa]; B2.x = mr[2 * npx + lpa]; }
-    }
-    if (in_b) {
-        Tf.y = out_T[V.pix_off + lpb];
-        last_b = last_idx[V.pix_off + lpb];
-        gI0.y = gI[lpb]; gI1.y = gI[npx + lpb]; gI2.y = gI[2 * npx + lpb];
-        if (dL_dT) gT.y = dL_dT[V.pix_off + lpb];
-        if (mr) { B0.y = mr[lpb]; B1.y = mr[npx + lpb]; B2.y = mr[2 * npx + lpb]; }
+    float2 Tf[PP], gI0[PP], gI1[PP], gI2[PP], gT[PP], B0[PP], B1[PP], B2[PP], fpy[PP];
+    uint32_t la[PP], lb[PP];
+    uint32_t my_hi = 0;
+#pragma unroll
+    for (int p = 0; p < PP; ++p) {
+        const int pya = row0 + 8 * p, pyb = pya + 4;
+        const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
+        const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
+        Tf[p] = make_float2(1.f, 1.f);
+        gI0[p] = gI1[p] = gI2[p] = gT[p] = make_float2(0.f, 0.f);
+        B0[p] = make_float2(bg0, bg0);
+        B1[p] = make_float2(bg1, bg1);
+        B2[p] = make_float2(bg2, bg2);
+        la[p] = lb[p] = 0;
+        fpy[p] = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
+        if (in_a) {
+            Tf[p].x = out_T[V.pix_off + lpa];
+            la[p] = last_idx[V.pix_off + lpa];
+            gI0[p].x = gI[lpa]; gI1[p].x = gI[npx + lpa]; gI2[p].x = gI[2 * npx + lpa];
+            if (dL_dT) gT[p].x = dL_dT[V.pix_off + lpa];
+            if (mr) { B0[p].x = mr[lpa]; B1[p].x = mr[npx + lpa]; B2[p].x = mr[2 * npx + lpa]; }
+        }
+        if (in_b) {
+            Tf[p].y = out_T[V.pix_off + lpb];
+            lb[p] = last_idx[V.pix_off + lpb];
+            gI0[p].y = gI[lpb]; gI1[p].y = gI[npx + lpb]; gI2[p].y = gI[2 * npx + lpb];
+            if (dL_dT) gT[p].y = dL_dT[V.pix_off + lpb];
+            if (mr) { B0[p].y = mr[lpb]; B1[p].y = mr[npx + lpb]; B2[p].y = mr[2 * npx + lpb]; }
+        }
+        my_hi = max(my_hi, max(la[p], lb[p]));
     }
     const uint32_t begin = ranges[2 * gt];
     if (t == 0) {
@@ -118,14 +140,15 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         mbar_fence_init();
     }
     __syncthreads();
-    const uint32_t my_hi = max(last_a, last_b);
     if (my_hi > 0) atomicMax(&s_hi, my_hi);
     __syncthreads();
     const uint32_t hi_all = s_hi;
     // rounds walk the list back to front: round r covers [lo_r, hi_r) with
     // hi_r = hi_all - r batch, lo_r = max(begin, hi_r - batch)
     const uint32_t n_rounds = hi_all > begin ? (hi_all - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
-    uint32_t nxt0 = 0, nxt1 = 0;
+    uint32_t nxt[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) nxt[e] = 0;
     auto round_lo = [&](uint32_t r, uint32_t &lo, uint32_t &nb) {
         const uint32_t hi = hi_all - r * (uint32_t)batch;
         lo = hi - begin > (uint32_t)batch ? hi - (uint32_t)batch : begin;
@@ -134,25 +157,24 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     auto load_idx = [&](uint32_t r) {
         uint32_t lo, nb;
         round_lo(r, lo, nb);
-        if ((uint32_t)t < nb) nxt0 = vals[lo + t];
-        if ((uint32_t)(t + NTH) < nb) nxt1 = vals[lo + t + NTH];
+#pragma unroll
+        for (int e = 0; e < PER; ++e)
+            if ((uint32_t)(t + e * NTH) < nb) nxt[e] = vals[lo + t + e * NTH];
     };
     auto issue = [&](uint32_t r) {
         const int buf = r & 1;
         uint32_t lo, nb;
         round_lo(r, lo, nb);
         if (t == 0) mbar_arrive_expect_tx(&s_bar[buf], nb * (uint32_t)sizeof(Record));
-        if ((uint32_t)t < nb) {
-            uint32_t it = nxt0;
-            if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
-            s_item[buf][t] = it;
-            bulk_g2s(&s_rec[buf][t], rec + it, sizeof(Record), &s_bar[buf]);
-        }
-        if ((uint32_t)(t + NTH) < nb) {
-            uint32_t it = nxt1;
-            if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
-            s_item[buf][t + NTH] = it;
-            bulk_g2s(&s_rec[buf][t + NTH], rec + it, sizeof(Record), &s_bar[buf]);
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const uint32_t k = (uint32_t)(t + e * NTH);
+            if (k < nb) {
+                uint32_t it = nxt[e];
+                if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
+                s_item0[buf * batch + k] = it;
+                bulk_g2s(&s_rec0[buf * batch + k], rec + it, sizeof(Record), &s_bar[buf]);
+            }
         }
     };
     if (n_rounds > 0) {
@@ -161,9 +183,12 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     }
     if (n_rounds > 1) load_idx(1);
     const float fpx = (float)px + 0.5f;
-    const float2 fpy = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
-    float2 T = Tf;
-    const float2 gTT = __fmul2_rn(gT, Tf);
+    float2 T[PP], gTT[PP];
+#pragma unroll
+    for (int p = 0; p < PP; ++p) {
+        T[p] = Tf[p];
+        gTT[p] = __fmul2_rn(gT[p], Tf[p]);
+    }
     bool ok = true;
     for (uint32_t r = 0; r < n_rounds; ++r) {
         // ends every thread's use of round r - 1, whose buffers round r + 1
@@ -182,65 +207,81 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         uint32_t lo, nb_u;
         round_lo(r, lo, nb_u);
         const int nb = ok ? (int)nb_u : 0;
-        const Record *sr = s_rec[buf];
-        const uint32_t *si = s_item[buf];
+        const Record *sr = s_rec0 + buf * batch;
+        const uint32_t *si = s_item0 + buf * batch;
         for (int k = nb - 1; k >= 0; --k) {
             const uint32_t j = lo + k;
-            bool ea = j < last_a, eb = j < last_b;
-            if (!__any_sync(0xffffffffu, ea || eb)) continue;
-            float g[kG];
+            bool ea[PP], eb[PP];
+            bool act = false;
+#pragma unroll
+            for (int p = 0; p < PP; ++p) {
+                ea[p] = j < la[p];
+                eb[p] = j < lb[p];
+                act = act || ea[p] || eb[p];
+            }
+            if (!__any_sync(0xffffffffu, act)) continue;
             const float4 A = sr[k].a, Bs = sr[k].b, c = sr[k].c;
-            float dx;
-            float2 dy;
-            const float2 q = eval_q2(A, Bs, fpx, fpy, dx, dy);
-            ea = ea && q.x >= kQ3;
-            eb = eb && q.y >= kQ3;
-            float2 G, araw;
-            const float2 al = eval_alpha2(Bs.y, q, G, araw);
-            ea = ea && al.x >= kAlphaMin;                  // the forward blended it
-            eb = eb && al.y >= kAlphaMin;
+            const QCol qc = eval_qcol(A, fpx);
+            float2 dy[PP], G[PP], araw[PP], al[PP];
+            act = false;
+#pragma unroll
+            for (int p = 0; p < PP; ++p) {
+                const float2 q = eval_qrows(A, Bs, qc, fpy[p], dy[p]);
+                ea[p] = ea[p] && q.x >= kQ3;
+                eb[p] = eb[p] && q.y >= kQ3;
+                al[p] = eval_alpha2(Bs.y, q, G[p], araw[p]);
+                ea[p] = ea[p] && al[p].x >= kAlphaMin;        // the forward blended it
+                eb[p] = eb[p] && al[p].y >= kAlphaMin;
+                act = act || ea[p] || eb[p];
+            }
             // entries the forward blended at none of the warp's pixels need no
             // gradient math and no reduction
-            if (!__any_sync(0xffffffffu, ea || eb)) continue;
-            const float2 ae = make_float2(ea ? al.x : 0.f, eb ? al.y : 0.f);
-            const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
-            const float2 r = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-            const float2 Ti = make_float2(ea ? T.x * r.x : T.x, eb ? T.y * r.y : T.y);
-            // colour: dI/dc = alpha T_i
-            const float2 wgt = __fmul2_rn(ae, Ti);
-            float2 p = __fmul2_rn(wgt, gI0);
-            g[6] = p.x + p.y;
-            p = __fmul2_rn(wgt, gI1);
-            g[7] = p.x + p.y;
-            p = __fmul2_rn(wgt, gI2);
-            g[8] = p.x + p.y;
-            // dL/dalpha = T_i (gI . (c - B)) - dL/dT T_final / (1 - alpha)
-            float2 sdot = __fmul2_rn(gI0, __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0.x, -B0.y)));
-            sdot = __ffma2_rn(gI1, __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1.x, -B1.y)), sdot);
-            sdot = __ffma2_rn(gI2, __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2.x, -B2.y)), sdot);
-            float2 dLda = __ffma2_rn(make_float2(-gTT.x, -gTT.y), r, __fmul2_rn(Ti, sdot));
-            dLda = make_float2(ea ? dLda.x : 0.f, eb ? dLda.y : 0.f);
-            // through alpha = o 2^q when not clamped at 0.99
-            const float2 dLa_u = make_float2(araw.x < kAlphaMax ? dLda.x : 0.f, araw.y < kAlphaMax ? dLda.y : 0.f);
-            const float2 gq = __fmul2_rn(__fmul2_rn(dLa_u, araw), make_float2(kLn2, kLn2));   // dL/dq
-            // the pixel-space moments of dL/dq (the mean and conic gradients
-            // follow per record from them: dq/dmean = -2K conic (dx, dy),
-            // dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared by the pair
-            const float sgq = gq.x + gq.y;
-            const float2 gqdy = __fmul2_rn(gq, dy);
-            const float2 gqdy2 = __fmul2_rn(gqdy, dy);
-            g[0] = dx * sgq;                                              // sum gq dx
-            g[1] = gqdy.x + gqdy.y;                                       // sum gq dy
-            g[2] = dx * g[0];                                             // sum gq dx^2
-            g[3] = dx * g[1];                                             // sum gq dx dy
-            g[4] = gqdy2.x + gqdy2.y;                                     // sum gq dy^2
-            p = __fmul2_rn(dLa_u, G);
-            g[5] = p.x + p.y;                                             // dalpha/do = G
-            // colour behind the previous Gaussian (normalised), then T_i
-            B0 = __ffma2_rn(ae, make_float2(c.x, c.x), __fmul2_rn(om, B0));
-            B1 = __ffma2_rn(ae, make_float2(c.y, c.y), __fmul2_rn(om, B1));
-            B2 = __ffma2_rn(ae, make_float2(c.z, c.z), __fmul2_rn(om, B2));
-            T = Ti;
+            if (!__any_sync(0xffffffffu, act)) continue;
+            float g[kG];
+            float sgq = 0.f;
+#pragma unroll
+            for (int p = 0; p < PP; ++p) {
+                const float2 ae = make_float2(ea[p] ? al[p].x : 0.f, eb[p] ? al[p].y : 0.f);
+                const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
+                const float2 rr = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                const float2 Ti = make_float2(ea[p] ? T[p].x * rr.x : T[p].x, eb[p] ? T[p].y * rr.y : T[p].y);
+                // colour: dI/dc = alpha T_i
+                const float2 wgt = __fmul2_rn(ae, Ti);
+                const float2 c0 = __fmul2_rn(wgt, gI0[p]), c1 = __fmul2_rn(wgt, gI1[p]),
+                             c2 = __fmul2_rn(wgt, gI2[p]);
+                // dL/dalpha = T_i (gI . (c - B)) - dL/dT T_final / (1 - alpha)
+                float2 sdot = __fmul2_rn(gI0[p], __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0[p].x, -B0[p].y)));
+                sdot = __ffma2_rn(gI1[p], __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1[p].x, -B1[p].y)), sdot);
+                sdot = __ffma2_rn(gI2[p], __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2[p].x, -B2[p].y)), sdot);
+                float2 dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, __fmul2_rn(Ti, sdot));
+                dLda = make_float2(ea[p] ? dLda.x : 0.f, eb[p] ? dLda.y : 0.f);
+                // through alpha = o 2^q when not clamped at 0.99
+                const float2 dLa_u = make_float2(araw[p].x < kAlphaMax ? dLda.x : 0.f,
+                                                 araw[p].y < kAlphaMax ? dLda.y : 0.f);
+                const float2 gq = __fmul2_rn(__fmul2_rn(dLa_u, araw[p]), make_float2(kLn2, kLn2));   // dL/dq
+                // the pixel-space moments of dL/dq (the mean and conic
+                // gradients follow per record from them: dq/dmean = -2K conic
+                // (dx, dy), dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared
+                // by the thread's pixels
+                const float2 gqdy = __fmul2_rn(gq, dy[p]);
+                const float2 gqdy2 = __fmul2_rn(gqdy, dy[p]);
+                const float2 pg = __fmul2_rn(dLa_u, G[p]);
+                const float s_gq = gq.x + gq.y, s_dy = gqdy.x + gqdy.y, s_dy2 = gqdy2.x + gqdy2.y,
+                            s_op = pg.x + pg.y, s_r = c0.x + c0.y, s_g = c1.x + c1.y, s_b = c2.x + c2.y;
+                if (p == 0) {
+                    sgq = s_gq; g[1] = s_dy; g[4] = s_dy2; g[5] = s_op; g[6] = s_r; g[7] = s_g; g[8] = s_b;
+                } else {
+                    sgq += s_gq; g[1] += s_dy; g[4] += s_dy2; g[5] += s_op; g[6] += s_r; g[7] += s_g; g[8] += s_b;
+                }
+                // colour behind the previous Gaussian (normalised), then T_i
+                B0[p] = __ffma2_rn(ae, make_float2(c.x, c.x), __fmul2_rn(om, B0[p]));
+                B1[p] = __ffma2_rn(ae, make_float2(c.y, c.y), __fmul2_rn(om, B1[p]));
+                B2[p] = __ffma2_rn(ae, make_float2(c.z, c.z), __fmul2_rn(om, B2[p]));
+                T[p] = Ti;
+            }
+            g[0] = qc.dx * sgq;                                           // sum gq dx
+            g[2] = qc.dx * g[0];                                          // sum gq dx^2
+            g[3] = qc.dx * g[1];                                          // sum gq dx dy
             float *dst = g2d + (size_t)si[k] * kG;
             const float y = warp_sum8(g, lane);
             float z = g[8];
@@ -714,14 +755,14 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     e = cudaMemsetAsync(g2d, 0, sizeof(float) * kG * (size_t)n_views * n, s);
     if (e != cudaSuccess) return cuda_status(e);
     const uint32_t n_rec = (uint32_t)((long long)n_views * n);
-#define HM_BBWD(TW, TH)                                                                          \
-    blend_bwd_kernel<TW, TH><<<grid, TW * TH / 2, 0, s>>>(vt, rec, n_rec, pair_vals, tile_ranges,  \
-                                                      mesh_rgb, bg[0], bg[1], bg[2], out_T,      \
-                                                      last_idx, dL_drgb, dL_dT, opt->batch, g2d, \
-                                                      d_status)
-    if (opt->tile_w == 16) HM_BBWD(16, 16);
-    else if (opt->tile_w == 32) HM_BBWD(32, 8);
-    else HM_BBWD(8, 8);
+    const size_t bwd_smem = 2 * (size_t)opt->batch * (sizeof(Record) + sizeof(uint32_t));
+#define HM_BBWD(TW, TH, PP)                                                                                    \
+    blend_bwd_kernel<TW, TH, PP><<<grid, TW * TH / (2 * PP), bwd_smem, s>>>(                                  \
+        vt, rec, n_rec, pair_vals, tile_ranges, mesh_rgb, bg[0], bg[1], bg[2], out_T, last_idx, dL_drgb, dL_dT, \
+        opt->batch, g2d, d_status)
+    if (opt->tile_w == 16) HM_BBWD(16, 16, 2);
+    else if (opt->tile_w == 32) HM_BBWD(32, 8, 1);
+    else HM_BBWD(8, 8, 1);
 #undef HM_BBWD
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }

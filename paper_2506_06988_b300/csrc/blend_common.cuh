@@ -37,16 +37,31 @@ __device__ __forceinline__ void pixel_pair(int t, int x0, int y0, int &px, int &
 }
 
 // q = K d^2 at two pixel centres of one column, (fpx, fpy.x) and (fpx, fpy.y),
-// in packed FP32x2: dx is shared, K a dx^2 and 2K b dx once per Gaussian,
-// then q = K a dx^2 + dy (2K b dx + K c dy) for both pixels.
+// in packed FP32x2: dx is shared, K a dx^2 and 2K b dx once per Gaussian
+// (eval_qcol), then q = K a dx^2 + dy (2K b dx + K c dy) for both pixels
+// (eval_qrows; a thread with several pixel pairs of one column evaluates the
+// column part once).
+struct QCol {
+    float dx, adx, bdx;
+};
+__device__ __forceinline__ QCol eval_qcol(const float4 &A, float fpx) {
+    QCol c;
+    c.dx = __fsub_rn(fpx, A.x);
+    c.adx = __fmul_rn(__fmul_rn(A.z, c.dx), c.dx);
+    c.bdx = __fmul_rn(A.w, c.dx);
+    return c;
+}
+__device__ __forceinline__ float2 eval_qrows(const float4 &A, const float4 &B, const QCol &c, float2 fpy,
+                                             float2 &dy) {
+    dy = __fadd2_rn(fpy, make_float2(-A.y, -A.y));
+    const float2 t = __ffma2_rn(make_float2(B.x, B.x), dy, make_float2(c.bdx, c.bdx));
+    return __ffma2_rn(dy, t, make_float2(c.adx, c.adx));
+}
 __device__ __forceinline__ float2 eval_q2(const float4 &A, const float4 &B, float fpx, float2 fpy,
                                           float &dx, float2 &dy) {
-    dx = __fsub_rn(fpx, A.x);
-    dy = __fadd2_rn(fpy, make_float2(-A.y, -A.y));
-    const float adx = __fmul_rn(__fmul_rn(A.z, dx), dx);
-    const float bdx = __fmul_rn(A.w, dx);
-    const float2 t = __ffma2_rn(make_float2(B.x, B.x), dy, make_float2(bdx, bdx));
-    return __ffma2_rn(dy, t, make_float2(adx, adx));
+    const QCol c = eval_qcol(A, fpx);
+    dx = c.dx;
+    return eval_qrows(A, B, c, fpy, dy);
 }
 
 // alpha = min(0.99, o 2^q) for both pixels; G = 2^q, araw = o G

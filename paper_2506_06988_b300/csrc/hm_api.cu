@@ -83,7 +83,7 @@ extern "C" void hm_default_options(hm_options *opt) {
     memset(opt, 0, sizeof(*opt));
     opt->tile_w = 16;
     opt->tile_h = 16;
-    opt->batch = 256;
+    opt->batch = 128;
     opt->mesh_cull = 1;
     opt->near_gauss = 0.2f;
     opt->near_mesh = 0.01f;

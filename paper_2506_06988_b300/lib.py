@@ -171,13 +171,15 @@ def cameras(cams) -> ctypes.Array:
 def options(tile=(16, 16), batch=None, mesh_cull=True, bg=(0.0, 0.0, 0.0), near_gauss=0.2,
             near_mesh=0.01, ellipse_cull=True, mip=False) -> HmOptions:
     """hm_options; ``mip`` selects Mip-Splatting's 2D Mip filter (kernel 0.1
-    with opacity compensation) instead of the 3DGS 0.3 dilation."""
+    with opacity compensation) instead of the 3DGS 0.3 dilation.  The
+    staging batch defaults to 128 list entries (the tile's pixel count if
+    smaller)."""
     o = HmOptions()
     load().hm_default_options(ctypes.byref(o))
     if mip:
         o.kernel_2d, o.antialias = 0.1, 1
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
-    o.batch = int(batch) if batch is not None else int(tile[0] * tile[1])
+    o.batch = int(batch) if batch is not None else min(128, int(tile[0] * tile[1]))
     o.mesh_cull = int(bool(mesh_cull))
     o.ellipse_cull = int(bool(ellipse_cull))
     o.near_gauss, o.near_mesh = float(near_gauss), float(near_mesh)

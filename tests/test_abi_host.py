@@ -47,7 +47,7 @@ def test_library_is_built_for_sm_103a():
 def test_default_options(hm):
     o = lib.HmOptions()
     hm.hm_default_options(ctypes.byref(o))
-    assert (o.tile_w, o.tile_h, o.batch, o.mesh_cull, o.ellipse_cull, o.bwd_stages) == (16, 16, 256, 1, 1, 0)
+    assert (o.tile_w, o.tile_h, o.batch, o.mesh_cull, o.ellipse_cull, o.bwd_stages) == (16, 16, 128, 1, 1, 0)
     assert abs(o.near_gauss - 0.2) < 1e-7 and abs(o.near_mesh - 0.01) < 1e-9
     assert list(o.bg) == [0.0, 0.0, 0.0]
 
