@@ -54,8 +54,8 @@ KERNEL_SOURCES = {
     "project": ("project.cu", "sh.cuh", "hm_internal.cuh"),
 }
 NCU_TRAFFIC = {
-    "blend_forward": (654_179_328, "6586889e0c4fc130"),
-    "blend_backward": (566_473_472, "9ba23cced0ce12a1"),
+    "blend_forward": (651_455_744, "2887610f3b398375"),
+    "blend_backward": (566_399_488, "4572b32758f84624"),
 }
 
 
