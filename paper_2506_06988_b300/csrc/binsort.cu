@@ -183,20 +183,15 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const floa
                     mask |= 1u << ((ty - r.y0) * nx + (tx - r.x0));
         }
     }
-    // per-tile counts, one atomic per distinct tile and round across the warp
-    // (consecutive records often share tiles; hot tiles take thousands)
+    // per-tile counts: one reduction per kept tile (no return value, so the
+    // adds of hot tiles queue in L2 without stalling the warp)
     {
         const int nx = (int)(geo & 0xFFFFu), tiles_x = (int)(geo >> 16);
         uint32_t bits = mask;
-        while (__any_sync(0xffffffffu, bits != 0)) {
-            uint32_t gt = 0xFFFFFFFFu;
-            if (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                gt = g0 + (b / nx) * tiles_x + b % nx;
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, gt);
-            if (gt != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&tile_cnt[gt], (unsigned)__popc(peers));
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            atomicAdd(&tile_cnt[g0 + (b / nx) * tiles_x + b % nx], 1u);
         }
     }
     // large rectangles: the whole warp, one record at a time, lanes over tiles
@@ -235,40 +230,29 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
     if (*n_sort == 0) return;
     const long long m = (long long)vt.n_views * n;
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
     const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint4 dsc = it < m ? desc[it] : make_uint4(0u, 0u, 0u, 0u);
     const uint32_t mask = dsc.x;
     const unsigned long long key = ((unsigned long long)dsc.y << 32) | (uint32_t)it;
     const int nx = (int)(dsc.w & 0xFFFFu), tiles_x = (int)(dsc.w >> 16);
-    // round r offers each lane's r-th kept tile; the lanes that offer the
-    // same tile share one atomic and a block of slots.  Rounds go in groups
-    // of kRounds whose atomics are all issued before any result is used, so
-    // their latencies overlap.
-    constexpr int kRounds = 8;
+    // each kept tile takes a slot from the tile's cursor; a small rectangle
+    // has at most kSmallRect tiles, whose atomics are all issued before any
+    // slot is used, so their latencies overlap
     uint32_t bits = mask != kMaskRecompute ? mask : 0u;
-    while (__any_sync(0xffffffffu, bits != 0)) {
-        uint32_t gts[kRounds], base[kRounds];
-        unsigned peers[kRounds];
+    if (bits) {
+        uint32_t slot[kSmallRect];
 #pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-            uint32_t gt = 0xFFFFFFFFu;
+        for (int r = 0; r < kSmallRect; ++r) {
+            slot[r] = 0xFFFFFFFFu;
             if (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
-                gt = dsc.z + (b / nx) * tiles_x + b % nx;
+                slot[r] = atomicAdd(&cursor[dsc.z + (b / nx) * tiles_x + b % nx], 1u);
             }
-            gts[r] = gt;
-            peers[r] = __match_any_sync(0xffffffffu, gt);
-            base[r] = 0;
-            if (gt != 0xFFFFFFFFu && lane == __ffs(peers[r]) - 1)
-                base[r] = atomicAdd(&cursor[gt], (unsigned)__popc(peers[r]));
         }
 #pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-            const uint32_t b0 = __shfl_sync(0xffffffffu, base[r], __ffs(peers[r]) - 1);
-            if (gts[r] != 0xFFFFFFFFu) keys[b0 + __popc(peers[r] & lt)] = key;
-        }
+        for (int r = 0; r < kSmallRect; ++r)
+            if (slot[r] != 0xFFFFFFFFu) keys[slot[r]] = key;
     }
     // large rectangles: the whole warp, one record at a time, lanes over tiles
     BinRec r = BinRec{};
@@ -294,6 +278,18 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
 // ---------------------------------------------------------------------------
 // segmented sort of the tile buckets
 // ---------------------------------------------------------------------------
+
+// The lanes of the warp whose 9-bit value d (a digit, or 256 for no key)
+// equals this lane's: one ballot per bit, keeping the lanes that agree on it.
+__device__ __forceinline__ uint32_t same_digit_lanes(uint32_t d) {
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const uint32_t one = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        m &= ((d >> b) & 1u) ? one : ~one;
+    }
+    return m;
+}
 constexpr int kWarpSeg = 256;      // bucket sizes sorted by one warp in registers
 constexpr int kMidSeg = 1024;      // ... by a 128-thread CTA in shared memory (radix)
 constexpr int kSegMax = 4096;      // ... by a 256-thread CTA in shared memory (radix)
@@ -411,7 +407,8 @@ seg_sort_small_kernel(uint32_t n_tiles, const uint32_t *__restrict__ tile_off,
 // The sort key is the depth (the high word of the 64-bit pair key) with the
 // record index as payload: 4 stable LSD passes of 8 bits, skipping passes in
 // which every key has the same digit.  A pass ranks the keys warp by warp
-// (match.any gives each key its rank among equal digits in input order),
+// (one ballot per digit bit gives each key its rank among equal digits in
+// input order),
 // turns the per-warp digit counts into offsets and scatters -- stable, so
 // equal depths keep their input order, which the emission left arbitrary:
 // a final fix-up sorts each run of equal depths by record index, which
@@ -448,7 +445,7 @@ __device__ void radix_pass(RadixSmem<THREADS, CAP> &S, int src, int n, int shift
         val[j] = valid ? S.v[src][e] : 0u;
         const int d = valid ? (int)((key[j] >> shift) & 255u) : 256;
         dig[j] = d;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = same_digit_lanes((uint32_t)d);
         const uint32_t before = S.whist[w][d];
         __syncwarp();
         if ((peers & lt) == 0) S.whist[w][d] = before + __popc(peers);
@@ -626,7 +623,7 @@ __device__ void huge_chunk_pass(HugeSmem<THREADS, CAP> &H, const uint32_t *ks, c
         val[j] = valid ? S.v[0][e] : 0u;
         const int d = valid ? (int)((key[j] >> shift) & 255u) : 256;
         dig[j] = d;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = same_digit_lanes((uint32_t)d);
         const uint32_t before = S.whist[w][d];
         __syncwarp();
         if ((peers & lt) == 0) S.whist[w][d] = before + __popc(peers);
@@ -705,7 +702,7 @@ seg_sort_huge_kernel(const uint32_t *__restrict__ list, const unsigned int *list
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const uint32_t d = valid ? (k >> (8 * p)) & 255u : 256u;
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const unsigned peers = same_digit_lanes(d);
                 if (valid && lane == __ffs(peers) - 1) atomicAdd(&H.hist[p][d], (unsigned)__popc(peers));
             }
         }
