@@ -386,7 +386,8 @@ def run_ours(args):
     # per single-kernel stage: (kernel, bound, algorithmic units, work per unit)
     kern = {
         "blend_forward": ("blend_fwd_kernel" + tsuf, "alu", n_eval, FLOPS_PER_EVAL, "evaluated (pixel, Gaussian) pairs"),
-        "blend_backward": ("blend_bwd_kernel" + tsuf, "alu", n_blended, FLOPS_PER_EVAL_BWD, "replayed blended pairs"),
+        "blend_backward": ("blend_bwd_kernel" + tsuf[:-1] + (",2>" if tuple(tile) == (16, 16) else ",1>"), "alu",
+                           n_blended, FLOPS_PER_EVAL_BWD, "replayed blended pairs"),
         "project": ("project_kernel<3,false>", "hbm", N, 12 + 12 + 16 + 4 + 12 * K + V * 48, "Gaussians (params read + V records written, bytes)"),
         "project_backward": ("project_bwd_kernel<3,false>", "hbm", N, 2 * (12 + 12 + 16 + 4 + 12 * K) + 12 + 12 + 16 + 4 + 12 * K + V * 36,
                              "Gaussians (params read, grads read+written, V partial rows read, bytes)"),
@@ -405,8 +406,14 @@ def run_ours(args):
             per_kernel[st_name] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm,
                                    "unit": "GB/s", "frac": ach / hbm, "units": units, "per_unit": per,
                                    "unit_kind": what, "ms": stage_ms[st_name]}
+    for st_name, e in per_kernel.items():
+        # DRAM bytes read + written per launch from the committed ncu capture
+        # (None when that kernel's sources or the workload differ from it)
+        e["traffic"] = _traffic(st_name, V, tile)
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     roof = dict(per_kernel[dom])
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                              "(profiles/blend_kernels_room1080p_8views.md)")
     roof["peak_source"] = (f"FP32: {nsm} SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (unit counts x max clock)"
                            if roof["bound"] == "alu" else f"HBM copy bandwidth, {peak_kind}")
     if roof["bound"] == "alu" and clocks.get("sm_mhz"):
