@@ -3,9 +3,10 @@
 // parameters and the texels (the texture map is optimisable, Sec. 3.4).
 //
 // Three kernels:
-//  * blend_bwd: per tile, per pixel (two pixels of a column per thread, as in
-//    the forward, in packed FP32x2), the blended Gaussians are replayed back
-//    to front from the pixel's last blended list position.  With
+//  * blend_bwd: per tile, per pixel (pixel pairs of a column in packed
+//    FP32x2, as in the forward; two pairs per thread on 16x16 tiles), the
+//    blended Gaussians are replayed back to front from the pixel's last
+//    blended list position.  With
 //    B = (colour behind Gaussian i) / T_{i+1}, running from B = back:
 //        dI/dc_i     = alpha_i T_i
 //        dI/dalpha_i = T_i (c_i - B),  dT_final/dalpha_i = -T_final/(1-alpha_i)
@@ -13,8 +14,9 @@
 //    Decisions are re-evaluated with the forward's exact arithmetic
 //    (blend_common.cuh).  Per Gaussian the 9 partials (five pixel-space
 //    moments of dL/dq from which the mean2d and conic gradients follow,
-//    opacity, colour) are summed over the warp with shuffles and added to
-//    per-record accumulators with one atomic per value per warp.
+//    opacity, colour) are summed over the thread's pixels, then over the
+//    warp with shuffles, and added to per-record accumulators with one
+//    atomic per value per warp.
 //  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
 //    triangle (the mesh colour enters I_h weighted by T), summed per screen
 //    tile in shared memory (fixed point) before the global reductions.
