@@ -25,7 +25,7 @@ def _check(name, g, ref, rel=1e-3, floor=1e-4):
     return check_grad(name, g, ref, rel, floor)
 
 
-def _run(scene, tex_grad, seed=0):
+def _run(scene, tex_grad, seed=0, tile=(16, 16), batch=None):
     cam = scene.cameras[0]
     npx = cam.n_pixels
     rng = np.random.default_rng(seed)
@@ -37,7 +37,7 @@ def _run(scene, tex_grad, seed=0):
     gT[amb] = 0.0
     tex = O.texture_unit(scene.mesh.texture) if scene.mesh is not None else None
     _, ref = TR.render_grad(scene, 0, gI, gT, tex=tex)
-    r, P, mesh = gpu_render(scene)
+    r, P, mesh = gpu_render(scene, tile=tile, batch=batch)
     g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"],
                    torch.as_tensor(gI.reshape(-1), dtype=torch.float32, device="cuda"),
                    torch.as_tensor(gT, dtype=torch.float32, device="cuda"), mesh=mesh, tex_grad=tex_grad)
@@ -91,6 +91,15 @@ def test_backward_sh3_gaussian_only():
 def test_backward_room_sh3_hybrid():
     s = scenes.room_scene(21, n_tris=3000, n_gauss=5000, resolutions=((128, 96),))
     print(_run(s, tex_grad=True, seed=2))
+
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 32), ((16, 16), 256), ((32, 8), 64), ((8, 8), 64)])
+def test_backward_tile_shapes_and_batches(tile, batch):
+    # every launch shape of the replay (two pixel pairs per thread on 16x16
+    # tiles, one elsewhere; staged rounds of 32 to 256 records) on a view
+    # whose size is no multiple of the tile (ragged right and bottom tiles)
+    s = scenes.room_scene(22, n_tris=3000, n_gauss=5000, resolutions=((120, 90),))
+    print(_run(s, tex_grad=True, seed=3, tile=tile, batch=batch))
 
 
 def test_autograd_function_matches_direct_backward():
