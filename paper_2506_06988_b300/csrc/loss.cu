@@ -37,7 +37,19 @@ constexpr int kNT = 256;             // threads per CTA
 constexpr int kRad = 5;              // window radius
 constexpr int kTaps = 2 * kRad + 1;  // 11
 constexpr int kHalo = kLT + 2 * kRad;   // 42 rows / columns with the halo
-constexpr int kHS = 48;              // halo row stride (float4-aligned, >= 4*7 + 16)
+constexpr int kHS = 48;              // float halo row stride (float4-aligned, >= 4*7 + 16; 192 B)
+constexpr int kHS2 = 50;             // float2 halo row stride (400 B: rows r, r+1 16 B apart mod 128)
+// The horizontal pass gives the eight threads of a shared-memory phase two
+// adjacent rows and four column groups each (see horiz_item), so with these
+// strides their 16-byte accesses fall in distinct bank groups.  The pass's
+// outputs have unpadded rows; odd rows are stored with their columns
+// swizzled (float2 maps: column ^ 2, float maps: column ^ 16), which does the
+// same for the stores, and the vertical pass reads them back through the
+// same swizzle.
+__device__ __forceinline__ void horiz_item(int i, int &r, int &c0) {
+    r = 2 * (i >> 4) + ((i >> 2) & 1);
+    c0 = 4 * ((i & 3) | (((i >> 3) & 1) << 2));
+}
 constexpr int kOut = 4;              // outputs per thread per pass
 constexpr int kSpan = kOut + kTaps - 1;   // 14 inputs per 4 outputs
 constexpr float kC1 = 0.01f * 0.01f;
@@ -101,14 +113,15 @@ __device__ __forceinline__ void taps4(const Taps &tp, const float *v, float (&ou
 }
 
 // vertical pass, thread (column c, rows 4 rg .. 4 rg + 3): each loaded row
-// value feeds the (up to 4) outputs whose window covers it
+// value feeds the (up to 4) outputs whose window covers it; odd rows are
+// read through the column swizzle (rows 4 rg + j have the parity of j)
 __device__ __forceinline__ void vert4x2(const Taps &tp, const float2 (*sh)[kLT], int c, int rg,
                                         float2 (&out)[kOut]) {
 #pragma unroll
     for (int o = 0; o < kOut; ++o) out[o] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < kSpan; ++j) {
-        const float2 v = sh[kOut * rg + j][c];
+        const float2 v = sh[kOut * rg + j][(j & 1) ? (c ^ 2) : c];
 #pragma unroll
         for (int o = 0; o < kOut; ++o) {
             const int k = j - o;
@@ -122,7 +135,7 @@ __device__ __forceinline__ void vert4x1(const Taps &tp, const float (*sh)[kLT], 
     for (int o = 0; o < kOut; ++o) out[o] = 0.f;
 #pragma unroll
     for (int j = 0; j < kSpan; ++j) {
-        const float v = sh[kOut * rg + j][c];
+        const float v = sh[kOut * rg + j][(j & 1) ? (c ^ 16) : c];
 #pragma unroll
         for (int o = 0; o < kOut; ++o) {
             const int k = j - o;
@@ -169,13 +182,13 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double (*s_red)[kNT /
     for (int q = 0; q < 3; ++q) v[q] = s_red[q][0];
 }
 
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kNT, 5)
 ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
                 const float *__restrict__ m_all, const float *__restrict__ T_all,
                 const float *__restrict__ md_all, float k_mask, float mesh_grad_scale,
                 float2 *__restrict__ d_mu_xx, float *__restrict__ d_xy,
                 float *__restrict__ dL_dmesh, double *__restrict__ partials) {
-    __shared__ __align__(16) float2 s_in[kHalo][kHS];   // (x, y) interleaved
+    __shared__ __align__(16) float2 s_in[kHalo][kHS2];  // (x, y) interleaved
     __shared__ __align__(16) float2 s_m[kHalo][kLT];    // (w*x, w*y) along rows
     __shared__ __align__(16) float2 s_q[kHalo][kLT];    // (w*x^2, w*y^2)
     __shared__ __align__(16) float s_c[kHalo][kLT];     // w*(x y)
@@ -214,7 +227,8 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     // horizontal: (row r, columns c0 .. c0 + 3) of the five products, the
     // (x, y) pairs in FP32x2
     for (int i = t; i < kHalo * (kLT / kOut); i += kNT) {
-        const int r = i / (kLT / kOut), c0 = kOut * (i % (kLT / kOut));
+        int r, c0;
+        horiz_item(i, r, c0);
         float2 xy[16], sq[kSpan], mm[kOut], qq[kOut];
         float pr[kSpan], o[kOut];
         load_span2(&s_in[r][c0], xy);
@@ -226,13 +240,12 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
         taps4x2(tp, xy, mm);
         taps4x2(tp, sq, qq);
         taps4(tp, pr, o);
-        float4 *dm = reinterpret_cast<float4 *>(&s_m[r][c0]);
-        float4 *dq = reinterpret_cast<float4 *>(&s_q[r][c0]);
-        dm[0] = make_float4(mm[0].x, mm[0].y, mm[1].x, mm[1].y);
-        dm[1] = make_float4(mm[2].x, mm[2].y, mm[3].x, mm[3].y);
-        dq[0] = make_float4(qq[0].x, qq[0].y, qq[1].x, qq[1].y);
-        dq[1] = make_float4(qq[2].x, qq[2].y, qq[3].x, qq[3].y);
-        *reinterpret_cast<float4 *>(&s_c[r][c0]) = make_float4(o[0], o[1], o[2], o[3]);
+        const int sw2 = (r & 1) * 2, sw1 = (r & 1) * 16;     // odd rows: swizzled columns
+        *reinterpret_cast<float4 *>(&s_m[r][c0 ^ sw2]) = make_float4(mm[0].x, mm[0].y, mm[1].x, mm[1].y);
+        *reinterpret_cast<float4 *>(&s_m[r][(c0 + 2) ^ sw2]) = make_float4(mm[2].x, mm[2].y, mm[3].x, mm[3].y);
+        *reinterpret_cast<float4 *>(&s_q[r][c0 ^ sw2]) = make_float4(qq[0].x, qq[0].y, qq[1].x, qq[1].y);
+        *reinterpret_cast<float4 *>(&s_q[r][(c0 + 2) ^ sw2]) = make_float4(qq[2].x, qq[2].y, qq[3].x, qq[3].y);
+        *reinterpret_cast<float4 *>(&s_c[r][c0 ^ sw1]) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
     const int c = t & 31, rg = t >> 5;
@@ -285,7 +298,7 @@ __global__ void __launch_bounds__(kNT)
 ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
                 const float2 *__restrict__ d_mu_xx, const float *__restrict__ d_xy,
                 float l1_scale, float ssim_scale, float *__restrict__ dL_drgb) {
-    __shared__ __align__(16) float2 s_d[kHalo][kHS];    // (D_mu, D_xx) interleaved
+    __shared__ __align__(16) float2 s_d[kHalo][kHS2];   // (D_mu, D_xx) interleaved
     __shared__ __align__(16) float s_dxy[kHalo][kHS];   // D_xy
     __shared__ __align__(16) float2 s_ab[kHalo][kLT];   // w*D_mu, w*D_xx along rows
     __shared__ __align__(16) float s_e[kHalo][kLT];     // w*D_xy
@@ -339,17 +352,18 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     }
     __syncthreads();
     for (int i = t; i < kHalo * (kLT / kOut); i += kNT) {
-        const int r = i / (kLT / kOut), c0 = kOut * (i % (kLT / kOut));
+        int r, c0;
+        horiz_item(i, r, c0);
+        const int sw2 = (r & 1) * 2, sw1 = (r & 1) * 16;     // odd rows: swizzled columns
         float2 dv[16], oab[kOut];
         load_span2(&s_d[r][c0], dv);
         taps4x2(tp, dv, oab);
-        float4 *dst = reinterpret_cast<float4 *>(&s_ab[r][c0]);
-        dst[0] = make_float4(oab[0].x, oab[0].y, oab[1].x, oab[1].y);
-        dst[1] = make_float4(oab[2].x, oab[2].y, oab[3].x, oab[3].y);
+        *reinterpret_cast<float4 *>(&s_ab[r][c0 ^ sw2]) = make_float4(oab[0].x, oab[0].y, oab[1].x, oab[1].y);
+        *reinterpret_cast<float4 *>(&s_ab[r][(c0 + 2) ^ sw2]) = make_float4(oab[2].x, oab[2].y, oab[3].x, oab[3].y);
         float vs[16], o[kOut];
         load_span(&s_dxy[r][c0], vs);
         taps4(tp, vs, o);
-        *reinterpret_cast<float4 *>(&s_e[r][c0]) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(&s_e[r][c0 ^ sw1]) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
     const int c = t & 31, rg = t >> 5;
