@@ -323,11 +323,13 @@ __device__ __forceinline__ void red_texel(float *d_tex, size_t t, float r, float
 constexpr int kTexCap = 1024;
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH)
+__global__ void __launch_bounds__(TW *TH / 2)
 texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const float *__restrict__ uv,
                    const float *__restrict__ out_T, const float *__restrict__ dL_drgb,
                    const float *__restrict__ dL_dmesh, int tw, int th, float *__restrict__ d_tex) {
-    constexpr int NT = TW * TH;
+    // a thread owns two pixels of one column, rows y and y + TH / 2, so the
+    // tile's box and scale set-up is shared by two pixels
+    constexpr int NT = TW * TH / 2;
     __shared__ int s_acc[kTexCap * 3];
     __shared__ int s_box[4];
     __shared__ int s_max[3];
@@ -336,44 +338,59 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const ViewDev &V = vt.v[v];
     const int local = gt - V.tile_off;
     const int t = threadIdx.x;
-    const int px = (local % V.tiles_x) * TW + (t % TW), py = (local / V.tiles_x) * TH + (t / TW);
-    const bool inside = px < V.W && py < V.H;
+    const int px = (local % V.tiles_x) * TW + (t % TW);
     const long long npx = (long long)V.W * V.H;
-    const long long lp = (long long)py * V.W + px;
-    const long long gp = V.pix_off + lp;
-    bool act = inside && mesh_depth[gp] < INFINITY;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, fx = 0.f, fy = 0.f;
-    int ix = 0, iy = 0;
-    if (act) {
-        const float T = out_T[gp];
-        const float *g = dL_drgb + 3 * V.pix_off + lp;
-        g0 = T * g[0]; g1 = T * g[npx]; g2 = T * g[2 * npx];
-        if (dL_dmesh) {   // a loss on the mesh colour itself (no T factor)
-            const float *gm = dL_dmesh + 3 * V.pix_off + lp;
-            g0 += gm[0]; g1 += gm[npx]; g2 += gm[2 * npx];
+    bool act[2];
+    float g0[2], g1[2], g2[2], fx[2], fy[2];
+    int xa[2], xb[2], ya[2], yb[2];
+    int mx0 = 0x7fffffff, mx1 = -1, my0 = 0x7fffffff, my1 = -1, m0 = 0, m1 = 0, m2 = 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int py = (local / V.tiles_x) * TH + (t / TW) + q * (TH / 2);
+        const bool inside = px < V.W && py < V.H;
+        const long long lp = (long long)py * V.W + px;
+        const long long gp = V.pix_off + lp;
+        act[q] = inside && mesh_depth[gp] < INFINITY;
+        g0[q] = g1[q] = g2[q] = fx[q] = fy[q] = 0.f;
+        int ix = 0, iy = 0;
+        if (act[q]) {
+            const float T = out_T[gp];
+            const float *g = dL_drgb + 3 * V.pix_off + lp;
+            g0[q] = T * g[0]; g1[q] = T * g[npx]; g2[q] = T * g[2 * npx];
+            if (dL_dmesh) {   // a loss on the mesh colour itself (no T factor)
+                const float *gm = dL_dmesh + 3 * V.pix_off + lp;
+                g0[q] += gm[0]; g1[q] += gm[npx]; g2[q] += gm[2 * npx];
+            }
+            const float *u = uv + 2 * V.pix_off + lp;
+            const float ss = u[0] * (float)tw - 0.5f, tt = u[npx] * (float)th - 0.5f;
+            const float x0 = floorf(ss), y0 = floorf(tt);
+            fx[q] = ss - x0; fy[q] = tt - y0;
+            ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f);
+            iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
         }
-        const float *u = uv + 2 * V.pix_off + lp;
-        const float ss = u[0] * (float)tw - 0.5f, tt = u[npx] * (float)th - 0.5f;
-        const float x0 = floorf(ss), y0 = floorf(tt);
-        fx = ss - x0; fy = tt - y0;
-        ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f);
-        iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
+        xa[q] = min(max(ix, 0), tw - 1); xb[q] = min(max(ix + 1, 0), tw - 1);
+        ya[q] = min(max(iy, 0), th - 1); yb[q] = min(max(iy + 1, 0), th - 1);
+        if (act[q]) {
+            mx0 = min(mx0, xa[q]); mx1 = max(mx1, xb[q]);
+            my0 = min(my0, ya[q]); my1 = max(my1, yb[q]);
+            m0 = max(m0, __float_as_int(fabsf(g0[q])));
+            m1 = max(m1, __float_as_int(fabsf(g1[q])));
+            m2 = max(m2, __float_as_int(fabsf(g2[q])));
+        }
     }
-    const int xa = min(max(ix, 0), tw - 1), xb = min(max(ix + 1, 0), tw - 1);
-    const int ya = min(max(iy, 0), th - 1), yb = min(max(iy + 1, 0), th - 1);
     if (t == 0) {
         s_box[0] = 0x7fffffff; s_box[1] = -1; s_box[2] = 0x7fffffff; s_box[3] = -1;
         s_max[0] = s_max[1] = s_max[2] = 0;
     }
     __syncthreads();
     {
-        const int mx0 = __reduce_min_sync(0xffffffffu, act ? xa : 0x7fffffff);
-        const int mx1 = __reduce_max_sync(0xffffffffu, act ? xb : -1);
-        const int my0 = __reduce_min_sync(0xffffffffu, act ? ya : 0x7fffffff);
-        const int my1 = __reduce_max_sync(0xffffffffu, act ? yb : -1);
-        const int m0 = __reduce_max_sync(0xffffffffu, __float_as_int(fabsf(g0)));
-        const int m1 = __reduce_max_sync(0xffffffffu, __float_as_int(fabsf(g1)));
-        const int m2 = __reduce_max_sync(0xffffffffu, __float_as_int(fabsf(g2)));
+        mx0 = __reduce_min_sync(0xffffffffu, mx0);
+        mx1 = __reduce_max_sync(0xffffffffu, mx1);
+        my0 = __reduce_min_sync(0xffffffffu, my0);
+        my1 = __reduce_max_sync(0xffffffffu, my1);
+        m0 = __reduce_max_sync(0xffffffffu, m0);
+        m1 = __reduce_max_sync(0xffffffffu, m1);
+        m2 = __reduce_max_sync(0xffffffffu, m2);
         if ((t & 31) == 0 && mx1 >= 0) {
             atomicMin(&s_box[0], mx0); atomicMax(&s_box[1], mx1);
             atomicMin(&s_box[2], my0); atomicMax(&s_box[3], my1);
@@ -384,21 +401,26 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const int bx0 = s_box[0], by0 = s_box[2];
     if (s_box[1] < 0) return;
     const int bw = s_box[1] - bx0 + 1, bh = s_box[3] - by0 + 1;
-    const float w[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
-    const int xs[4] = {xa, xb, xa, xb}, ys[4] = {ya, ya, yb, yb};
     if ((long long)bw * bh > kTexCap) {
-        if (act) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!act[q]) continue;
+            const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
+                                fx[q] * fy[q]};
+            const int xs[4] = {xa[q], xb[q], xa[q], xb[q]}, ys[4] = {ya[q], ya[q], yb[q], yb[q]};
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (w[k] != 0.f) red_texel(d_tex, (size_t)ys[k] * tw + xs[k], w[k] * g0, w[k] * g1, w[k] * g2);
+                if (w[k] != 0.f)
+                    red_texel(d_tex, (size_t)ys[k] * tw + xs[k], w[k] * g0[q], w[k] * g1[q], w[k] * g2[q]);
         }
         return;
     }
     // Fixed point per channel: the tile's largest |T dL/dI| maps to
     // [2^21, 2^22).  A pixel's taps have weights summing to 1, so a texel
-    // receives at most the tile's 256 pixels' worth: |sum| < 2^30 + 512 (one
-    // rounding per tap) fits int32.  Integer shared atomics are native and
-    // the sum is exact; each tap is rounded to 2^-22 of the tile maximum.
+    // receives at most the tile's pixels' worth (256 at 16x16): |sum| <
+    // 2^30 + 512 (one rounding per tap) fits int32.  Integer shared atomics
+    // are native and the sum is exact; each tap is rounded to 2^-22 of the
+    // tile maximum.
     float sc[3], isc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -410,14 +432,19 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const int ncell = bw * bh;
     for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0;
     __syncthreads();
-    if (act) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (!act[q]) continue;
+        const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
+                            fx[q] * fy[q]};
+        const int xs[4] = {xa[q], xb[q], xa[q], xb[q]}, ys[4] = {ya[q], ya[q], yb[q], yb[q]};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (w[k] == 0.f) continue;
             int *a = s_acc + 3 * ((ys[k] - by0) * bw + (xs[k] - bx0));
-            atomicAdd(a, __float2int_rn(w[k] * g0 * sc[0]));
-            atomicAdd(a + 1, __float2int_rn(w[k] * g1 * sc[1]));
-            atomicAdd(a + 2, __float2int_rn(w[k] * g2 * sc[2]));
+            atomicAdd(a, __float2int_rn(w[k] * g0[q] * sc[0]));
+            atomicAdd(a + 1, __float2int_rn(w[k] * g1[q] * sc[1]));
+            atomicAdd(a + 2, __float2int_rn(w[k] * g2[q] * sc[2]));
         }
     }
     __syncthreads();
@@ -741,7 +768,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (d_tex && (stages & HM_BWD_TEXTURE)) {
         dim3 tg(vt.total_tiles);
 #define HM_TBWD(TW, TH) \
-    texture_bwd_kernel<TW, TH><<<tg, TW * TH, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, dL_dmesh, tex_w, tex_h, \
+    texture_bwd_kernel<TW, TH><<<tg, TW * TH / 2, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, dL_dmesh, tex_w, tex_h, \
                                                   d_tex)
         if (opt->tile_w == 16) HM_TBWD(16, 16);
         else if (opt->tile_w == 32) HM_TBWD(32, 8);
