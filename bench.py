@@ -55,7 +55,7 @@ KERNEL_SOURCES = {
 }
 NCU_TRAFFIC = {
     "blend_forward": (651_455_744, "2887610f3b398375"),
-    "blend_backward": (566_399_488, "226aeeb8e52012f2"),
+    "blend_backward": (566_773_248, "d5751a32ff776980"),
 }
 
 

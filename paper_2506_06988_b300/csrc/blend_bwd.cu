@@ -322,14 +322,15 @@ __device__ __forceinline__ void red_texel(float *d_tex, size_t t, float r, float
 // (it straddles charts) reduces straight to global memory.
 constexpr int kTexCap = 1024;
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2)
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(TW *TH / PX)
 texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const float *__restrict__ uv,
                    const float *__restrict__ out_T, const float *__restrict__ dL_drgb,
                    const float *__restrict__ dL_dmesh, int tw, int th, float *__restrict__ d_tex) {
-    // a thread owns two pixels of one column, rows y and y + TH / 2, so the
-    // tile's box and scale set-up is shared by two pixels
-    constexpr int NT = TW * TH / 2;
+    // a thread owns PX pixels of one column, rows y + q TH / PX, so the
+    // tile's box, scale and flush set-up is shared by PX pixels
+    constexpr int NT = TW * TH / PX;
+    static_assert(NT % 32 == 0 && TH % PX == 0, "whole warps");
     __shared__ int s_acc[kTexCap * 3];
     __shared__ int s_box[4];
     __shared__ int s_max[3];
@@ -340,13 +341,13 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const int t = threadIdx.x;
     const int px = (local % V.tiles_x) * TW + (t % TW);
     const long long npx = (long long)V.W * V.H;
-    bool act[2];
-    float g0[2], g1[2], g2[2], fx[2], fy[2];
-    int xa[2], xb[2], ya[2], yb[2];
+    bool act[PX];
+    float g0[PX], g1[PX], g2[PX], fx[PX], fy[PX];
+    int xa[PX], xb[PX], ya[PX], yb[PX];
     int mx0 = 0x7fffffff, mx1 = -1, my0 = 0x7fffffff, my1 = -1, m0 = 0, m1 = 0, m2 = 0;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int py = (local / V.tiles_x) * TH + (t / TW) + q * (TH / 2);
+    for (int q = 0; q < PX; ++q) {
+        const int py = (local / V.tiles_x) * TH + (t / TW) + q * (TH / PX);
         const bool inside = px < V.W && py < V.H;
         const long long lp = (long long)py * V.W + px;
         const long long gp = V.pix_off + lp;
@@ -403,7 +404,7 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const int bw = s_box[1] - bx0 + 1, bh = s_box[3] - by0 + 1;
     if ((long long)bw * bh > kTexCap) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < PX; ++q) {
             if (!act[q]) continue;
             const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
                                 fx[q] * fy[q]};
@@ -433,7 +434,7 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0;
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < PX; ++q) {
         if (!act[q]) continue;
         const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
                             fx[q] * fy[q]};
@@ -767,12 +768,12 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     const Filters flt{filter_3d, opt->kernel_2d, opt->antialias ? 1 : 0};
     if (d_tex && (stages & HM_BWD_TEXTURE)) {
         dim3 tg(vt.total_tiles);
-#define HM_TBWD(TW, TH) \
-    texture_bwd_kernel<TW, TH><<<tg, TW * TH / 2, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, dL_dmesh, tex_w, tex_h, \
-                                                  d_tex)
-        if (opt->tile_w == 16) HM_TBWD(16, 16);
-        else if (opt->tile_w == 32) HM_TBWD(32, 8);
-        else HM_TBWD(8, 8);
+#define HM_TBWD(TW, TH, PX) \
+    texture_bwd_kernel<TW, TH, PX><<<tg, TW * TH / PX, 0, s>>>(vt, mesh_depth, mesh_uv, out_T, dL_drgb, dL_dmesh, \
+                                                           tex_w, tex_h, d_tex)
+        if (opt->tile_w == 16) HM_TBWD(16, 16, 2);
+        else if (opt->tile_w == 32) HM_TBWD(32, 8, 2);
+        else HM_TBWD(8, 8, 2);
 #undef HM_TBWD
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
