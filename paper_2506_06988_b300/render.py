@@ -252,24 +252,35 @@ class Renderer:
             self._side = torch.cuda.Stream(device=self.device)
         return self._side
 
+    def _bin_stream(self) -> torch.cuda.Stream:
+        """High-priority stream for the critical chains of an overlapped
+        frame -- projection and binning (many short dependent kernels) in
+        the forward, blend and projection gradients in the backward -- so
+        their launches take SMs first while the mesh pass or the texel
+        gradients on the current stream fill the rest."""
+        if getattr(self, "_bin", None) is None:
+            self._bin = torch.cuda.Stream(device=self.device, priority=-1)
+        return self._bin
+
     def forward(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None,
                 overlap: Optional[bool] = None):
         """All four stages, asynchronously on the current stream.  With
-        ``overlap`` (default ``self.overlap``) the mesh pass runs on a side
-        stream while the projection and the binning (without the tile mesh
-        cull, which would wait for the mesh pass) run on the current stream;
-        the blend joins them -- inside a graph capture a fork and a join.
-        The images, counts and stop indices are the same either way."""
+        ``overlap`` (default ``self.overlap``) the projection and the binning
+        (without the tile mesh cull, which would wait for the mesh pass) run
+        on a high-priority side stream while the mesh pass runs on the
+        current stream; the blend joins them -- inside a graph capture a
+        fork and a join.  The images, counts and stop indices are the same
+        either way."""
         self.status_word.zero_()
         if self.has_mesh and (self.overlap if overlap is None else overlap):
             main = torch.cuda.current_stream(self.device)
-            side = self._side_stream()
-            side.wait_stream(main)
-            with torch.cuda.stream(side):
-                self.rasterize_mesh(mesh)
-            self.project(means, scales, quats, opacity, sh)
-            self.bin_sort(mesh_cull=False)
-            main.wait_stream(side)
+            hi = self._bin_stream()
+            hi.wait_stream(main)
+            with torch.cuda.stream(hi):
+                self.project(means, scales, quats, opacity, sh)
+                self.bin_sort(mesh_cull=False)
+            self.rasterize_mesh(mesh)
+            main.wait_stream(hi)
             self.blend()
             return
         else:
@@ -317,9 +328,10 @@ class Renderer:
         """Gradients of the last forward, accumulated into fresh zero tensors
         (or into ``out``, a dict from ``grad_buffers``, zeroed first unless
         ``zero`` is False).  ``stages``: HM_BWD_* bits to run (0 = all).
-        With ``overlap`` (default ``self.overlap``) the texel gradients run on
-        a side stream concurrently with the blend and projection gradients
-        (they share no output) and join the current stream at the end.
+        With ``overlap`` (default ``self.overlap``) the blend and projection
+        gradients run on a high-priority side stream concurrently with the
+        texel gradients on the current stream (they share no output) and
+        join it at the end.
         ``dL_dmesh`` (planar like ``rgb``): the gradient of a loss on the mesh
         colour itself, added to what the texels receive through I_h."""
         want_tex = tex_grad and self.has_mesh
@@ -330,16 +342,16 @@ class Renderer:
                     if k != "texture":
                         v.zero_()
             main = torch.cuda.current_stream(self.device)
-            side = self._side_stream()
-            side.wait_stream(main)
-            with torch.cuda.stream(side):
-                if out is not None and zero:
-                    g["texture"].zero_()
+            hi = self._bin_stream()
+            hi.wait_stream(main)
+            with torch.cuda.stream(hi):
                 self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
-                                    lib.HM_BWD_TEXTURE, dL_dmesh)
+                                    lib.HM_BWD_BLEND | lib.HM_BWD_PROJECT)
+            if out is not None and zero:
+                g["texture"].zero_()
             self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
-                                lib.HM_BWD_BLEND | lib.HM_BWD_PROJECT)
-            main.wait_stream(side)
+                                lib.HM_BWD_TEXTURE, dL_dmesh)
+            main.wait_stream(hi)
             return g
         if out is None:
             g = self.grad_buffers(mesh.texture.shape[:2] if want_tex else None)
