@@ -507,12 +507,22 @@ class GraphStep:
 
     def _body(self):
         r = self.r
+        main = torch.cuda.current_stream(r.device)
+        side = None
+        if self.target_f is not None:
+            # the target's decode depends on nothing the frame computes: it
+            # runs beside the forward and joins before the loss
+            side = r._side_stream()
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                lib.check(lib.hm_decode_u8(self.target, self.target.numel(), self.target_f, _stream()),
+                          "hm_decode_u8")
         r.forward(*self.params, self.mesh, overlap=True)
         dI, dM = self.dI, None
         if self.target is not None:
             tgt = self.target
-            if self.target_f is not None:
-                lib.check(lib.hm_decode_u8(tgt, tgt.numel(), self.target_f, _stream()), "hm_decode_u8")
+            if side is not None:
+                main.wait_stream(side)
                 tgt = self.target_f
             self.loss_terms, dI, dM = r.loss(tgt, self.loss_params,
                                              texture_loss=self.tex_grad and self.loss_params.lambda_t > 0)
