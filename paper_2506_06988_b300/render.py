@@ -328,29 +328,33 @@ class Renderer:
         """Gradients of the last forward, accumulated into fresh zero tensors
         (or into ``out``, a dict from ``grad_buffers``, zeroed first unless
         ``zero`` is False).  ``stages``: HM_BWD_* bits to run (0 = all).
-        With ``overlap`` (default ``self.overlap``) the blend and projection
-        gradients run on a high-priority side stream concurrently with the
-        texel gradients on the current stream (they share no output) and
-        join it at the end.
+        With ``overlap`` (default ``self.overlap``) the blend replay and the
+        projection gradients run on a high-priority side stream while the
+        gradient zeroing and the texel gradients run on the current stream
+        (the replay writes only its scratch; the projection gradients wait
+        for the zeroing), and the streams join at the end.
         ``dL_dmesh`` (planar like ``rgb``): the gradient of a loss on the mesh
         colour itself, added to what the texels receive through I_h."""
         want_tex = tex_grad and self.has_mesh
         if (self.overlap if overlap is None else overlap) and want_tex and stages == 0:
             g = out if out is not None else self.grad_buffers(mesh.texture.shape[:2])
-            if out is not None and zero:
-                for k, v in g.items():
-                    if k != "texture":
-                        v.zero_()
             main = torch.cuda.current_stream(self.device)
             hi = self._bin_stream()
             hi.wait_stream(main)
-            with torch.cuda.stream(hi):
+            with torch.cuda.stream(hi):          # the blend replay writes only its scratch
                 self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
-                                    lib.HM_BWD_BLEND | lib.HM_BWD_PROJECT)
-            if out is not None and zero:
-                g["texture"].zero_()
+                                    lib.HM_BWD_BLEND)
+            if out is not None and zero:         # zeroed beside the replay
+                for v in g.values():
+                    v.zero_()
+            zeroed = torch.cuda.Event()
+            zeroed.record(main)
             self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
                                 lib.HM_BWD_TEXTURE, dL_dmesh)
+            hi.wait_event(zeroed)
+            with torch.cuda.stream(hi):
+                self._backward_call(means, scales, quats, opacity, sh, dL_drgb, dL_dT, mesh, g,
+                                    lib.HM_BWD_PROJECT)
             main.wait_stream(hi)
             return g
         if out is None:
