@@ -86,6 +86,31 @@ def test_graph_step_with_target_matches_eager_loss(lambda_ssim):
     _grads_close(gs.grads, ref_g)
 
 
+def test_graph_step_with_texture_loss_matches_eager():
+    # a float32 target with the transmittance-aware texture loss on: the graph
+    # passes dL/dI_m to the texel gradients like the eager call does
+    from paper_2506_06988_b300 import lib
+    s = _room(seed=34)
+    r, P, mesh = gpu_render(s)
+    mesh = MeshInput(mesh.verts, mesh.uvs, mesh.faces, mesh.texture.float() / 255.0
+                     if mesh.texture.dtype == torch.uint8 else mesh.texture)
+    r.render(*_params(P), mesh)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    tgt = torch.rand(3 * r.npix, device="cuda", generator=gen)
+    lp = lib.loss_params(lambda_ssim=0.2, lambda_t=0.1)
+    terms, dI, dM = r.loss(tgt, lp, texture_loss=True)
+    assert dM is not None
+    ref_terms = terms.clone()
+    ref_g = r.backward(*_params(P), dI.clone(), None, mesh=mesh, tex_grad=True, dL_dmesh=dM.clone())
+    gs = GraphStep(r, _params(P), mesh, target=tgt, loss_params=lp, tex_grad=True)
+    gs.replay(check=True)
+    torch.cuda.synchronize()
+    assert torch.equal(gs.loss_terms, ref_terms)
+    assert float(ref_terms[2]) > 0.0
+    _grads_close(gs.grads, ref_g)
+
+
 def test_decode_u8_is_exact():
     from paper_2506_06988_b300 import lib
     for n in (0, 5, 16, 1000, 4099):
