@@ -216,6 +216,7 @@ def cpu_oracle_sample(scene, rows=8, crop=12, t_fixed=None):
     t_mesh = time.perf_counter() - t0
     full = O.empty_mesh_result(W * H, scene.bg)
     full.tri_id[pix], full.depth[pix] = mr.tri_id, mr.depth
+    full.depth64[pix], full.depth_tol[pix], full.tri_margin[pix] = mr.depth64, mr.depth_tol, mr.tri_margin
     full.rgb[:, pix] = mr.rgb
     t0 = time.perf_counter()
     O.blend_grid(cam, pr, scene.gaussians.opacity, full, bg=scene.bg, rows=(y0, y0 + rows))
@@ -249,7 +250,7 @@ def cpu_oracle_small():
     from oracle import oracle as O
     from oracle import torch_ref as TR
     from paper_2506_06988_b300 import scenes
-    s = scenes.config0_scene(seed=0)
+    s = scenes.config0_scene()
     cam = s.cameras[0]
     torch.set_num_threads(O.num_threads())
     t0 = time.perf_counter()

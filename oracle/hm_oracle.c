@@ -29,15 +29,13 @@
  *     the 1.3 x half-FOV clamp inside J, colour = max(0, 0.5 + SH);
  *   - mesh coverage: vertices projected in FP64, snapped to 1/256 px,
  *     exact integer edge functions with the top-left fill rule, two-sided;
- *     nearest FP32 view depth wins, ties to the lower triangle index;
- *     depth: 1/z is affine in screen space, 1/z = 1/z0 + a U + b V with
- *     (U,V) the pixel centre minus the snapped vertex 0 in pixels; a, b
- *     and 1/z0 are computed per face in FP64 and rounded once to FP32, and
- *     the pixel's depth is the FP32 reciprocal of fma(a, U, fma(b, V, 1/z0))
- *     -- the nearest-face decision is an argmin, taken in the FP32
- *     precision the GPU decides it in; perspective-correct UVs; bilinear
- *     clamp-to-edge texture fetch with texel centres at half-integers, row 0
- *     at v = 0.
+ *     depth (Sec. 3.4 D_m): the view z of the snapped face at the pixel
+ *     centre, evaluated in FP64 from the exact integer barycentric weights
+ *     w_k and the vertices' 1/z_k (1/z is affine in screen space, so
+ *     z = sum w_k / sum w_k (1/z_k)) and rounded once to FP32; the nearest
+ *     FP32 depth wins, ties to the lower triangle index; perspective-correct
+ *     UVs; bilinear clamp-to-edge texture fetch with texel centres at
+ *     half-integers, row 0 at v = 0.
  *   - Gaussian depth key: z = R_2 . mean + t_2 evaluated in FP64 as
  *     fma(R20, x, fma(R21, y, fma(R22, z, t2))), rounded once to FP32.
  *
@@ -81,7 +79,7 @@ typedef struct {
     double iz[3];         /* 1 / view z per vertex */
     int ord[3];           /* vertex order with positive signed area */
     int64_t area2;        /* |signed double area| in (1/256 px)^2 */
-    float iz0f, af, bf;   /* 1/z = iz0 + a U + b V (per pixel of offset from vertex 0) */
+    double pa, pb;        /* FP64 screen gradient of 1/z, per pixel (tolerance model only) */
 } face_setup;
 
 #define OR_SNAP 256.0
@@ -109,16 +107,14 @@ static void setup_face(const double *c, const double *verts, const int *f, doubl
     if (a2 == 0) return;
     if (a2 > 0) { s->ord[0] = 0; s->ord[1] = 1; s->ord[2] = 2; s->area2 = a2; }
     else        { s->ord[0] = 0; s->ord[1] = 2; s->ord[2] = 1; s->area2 = -a2; }
-    /* screen-space barycentrics l1 = (dx e2y - dy e2x) / D, l2 = (e1x dy - e1y dx) / D
-     * for the offset (dx, dy) from vertex 0 (Cramer's rule, D = signed area2), so
-     * 1/z = iz0 + (iz1 - iz0) l1 + (iz2 - iz0) l2 = iz0 + a dx + b dy; per pixel of
-     * offset the coefficients carry a factor 256 */
+    /* Screen gradient of 1/z (per pixel of offset from the face's first
+     * vertex), FP64.  It does not enter the depth, which face_depth64 takes
+     * from the barycentric weights; it only sizes the FP32 error band of a
+     * rasteriser that evaluates the 1/z plane from that vertex (see
+     * or_mesh_raster). */
     double d1 = s->iz[1] - s->iz[0], d2 = s->iz[2] - s->iz[0];
-    double na = fma(d1, (double)e2y, -(d2 * (double)e1y));
-    double nb = fma(d2, (double)e1x, -(d1 * (double)e2x));
-    s->af = (float)((na * 256.0) / (double)a2);
-    s->bf = (float)((nb * 256.0) / (double)a2);
-    s->iz0f = (float)s->iz[0];
+    s->pa = 256.0 * (d1 * (double)e2y - d2 * (double)e1y) / (double)a2;
+    s->pb = 256.0 * (d2 * (double)e1x - d1 * (double)e2x) / (double)a2;
     s->valid = 1;
 }
 
@@ -148,13 +144,25 @@ static int face_covers(const face_setup *s, int64_t px, int64_t py, int64_t w[3]
     return 1;
 }
 
-/* view depth at the covered centre (px, py) (1/256 px): the FP32 reciprocal
- * of the affine 1/z evaluated in FP32 at the pixel offset from vertex 0 */
-static float face_depth(const face_setup *s, int64_t px, int64_t py) {
-    float U = (float)(int32_t)(px - s->X[0]) * 0.00390625f;
-    float V = (float)(int32_t)(py - s->Y[0]) * 0.00390625f;
-    float invz = fmaf(s->af, U, fmaf(s->bf, V, s->iz0f));
-    return 1.0f / invz;
+/* Sec. 3.4 D_m: view z of the snapped face at a covered centre, FP64.  With
+ * w_k the exact integer edge-function weights (sum = area2), the screen-space
+ * barycentrics are w_k / area2 and 1/z interpolates linearly in screen space,
+ * so z = area2 / sum_k w_k (1/z_k). */
+static double face_depth64(const face_setup *s, const int64_t w[3]) {
+    double S = (double)w[0] * s->iz[0] + (double)w[1] * s->iz[1] + (double)w[2] * s->iz[2];
+    return (double)s->area2 / S;
+}
+
+/* Relative FP32 error band of the depth at (px, py): a rasteriser that keeps
+ * the 1/z plane as three FP32 coefficients anchored at the face's first
+ * vertex and evaluates it with two FMAs and one reciprocal commits at most
+ * (3 kappa + 3) u, u = 2^-24, with kappa = (|a U| + |b V| + |1/z_0|) / (1/z)
+ * the condition number of that evaluation (coefficient and offset roundings,
+ * two FMA roundings, the reciprocal, the FP32 rounding of this reference). */
+static double face_depth_relband(const face_setup *s, int64_t px, int64_t py, double D64) {
+    double U = (double)(px - s->X[0]) / 256.0, V = (double)(py - s->Y[0]) / 256.0;
+    double kappa = (fabs(s->pa * U) + fabs(s->pb * V) + fabs(s->iz[0])) * D64;
+    return (3.0 * kappa + 3.0) * 0x1p-24;
 }
 
 /* perspective-correct barycentrics (FP64) of a covered centre */
@@ -191,12 +199,19 @@ static void sample_bilinear(const double *tex, int tw, int th, double u, double 
  * brute force over every face.  tex is [th][tw][3] in [0,1] (RGB8 divided by
  * 255 by the caller).  Outputs per listed pixel: tri_id (-1 none), depth
  * (FP32 view z, +inf none), rgb[3*npix] planar (bg where none), uv[2*npix]
- * planar (0 where none), bary[3*npix] perspective-correct barycentrics.
+ * planar (0 where none), bary[3*npix] perspective-correct barycentrics, and
+ * the FP32 band of the nearest-face decision:
+ *   depth64   the winner's FP64 depth (+inf none);
+ *   depth_tol absolute FP32 error band of that depth (face_depth_relband);
+ *   tri2      the runner-up among the covering faces (-1 none);
+ *   tri_margin (D64(tri2) - D64(tri)) / (tol(tri) + tol(tri2)), +inf without
+ *             a runner-up: below 1 an FP32 rasteriser may pick either face.
  */
 void or_mesh_raster(const double *cam, int W, int H, const double *verts, const double *uvs,
                     int nv, const int *faces, int nf, const double *tex, int tw, int th,
                     const double *bg, double znear, const int64_t *pix, int64_t npix,
-                    int *tri_id, float *depth, double *rgb, double *uv, double *bary) {
+                    int *tri_id, float *depth, double *rgb, double *uv, double *bary,
+                    double *depth64, double *depth_tol, int *tri2, double *tri_margin) {
     (void)nv;
     face_setup *fs = (face_setup *)malloc(sizeof(face_setup) * (size_t)(nf > 0 ? nf : 1));
 #pragma omp parallel for schedule(static)
@@ -207,18 +222,36 @@ void or_mesh_raster(const double *cam, int W, int H, const double *verts, const 
         int64_t lin = pix ? pix[q] : q;
         int x = (int)(lin % W), y = (int)(lin / W);
         int64_t px = (int64_t)x * 256 + 128, py = (int64_t)y * 256 + 128;
-        int best = -1;
-        float bestD = INFINITY;
+        /* nearest by (FP32 depth, face index), and the runner-up */
+        int best = -1, second = -1;
+        float bestD = INFINITY, secondD = INFINITY;
+        double best64 = INFINITY, second64 = INFINITY;
         int64_t bw[3] = {0, 0, 0};
         for (int f = 0; f < nf; f++) {
             if (!fs[f].valid) continue;
             int64_t w[3];
             if (!face_covers(&fs[f], px, py, w)) continue;
-            float D = face_depth(&fs[f], px, py);
-            if (D < bestD) { bestD = D; best = f; bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2]; }
+            double D64 = face_depth64(&fs[f], w);
+            float D = (float)D64;
+            if (D < bestD) {
+                second = best; secondD = bestD; second64 = best64;
+                best = f; bestD = D; best64 = D64;
+                bw[0] = w[0]; bw[1] = w[1]; bw[2] = w[2];
+            } else if (D < secondD) {
+                second = f; secondD = D; second64 = D64;
+            }
         }
         tri_id[q] = best;
         depth[q] = best >= 0 ? bestD : INFINITY;
+        depth64[q] = best64;
+        tri2[q] = second;
+        depth_tol[q] = best >= 0 ? best64 * face_depth_relband(&fs[best], px, py, best64) : 0.0;
+        if (second >= 0) {
+            double tol2 = second64 * face_depth_relband(&fs[second], px, py, second64);
+            tri_margin[q] = (second64 - best64) / (depth_tol[q] + tol2);
+        } else {
+            tri_margin[q] = INFINITY;
+        }
         if (best < 0) {
             for (int ch = 0; ch < 3; ch++) rgb[ch * npix + q] = bg[ch];
             uv[q] = 0; uv[npix + q] = 0;
@@ -500,37 +533,104 @@ static uint64_t mix64(uint64_t h, uint64_t v) {
     return h * 0xBF58476D1CE4E5B9ull;
 }
 
-/* Blend one pixel over the (depth, index)-sorted list `lst` (length m). */
-static void blend_pixel(double pxc, double pyc, int hit, float Dm, const double *Im,
-                        const int *lst, int m, const float *depth, const double *mean2d,
-                        const double *conic, const double *opacity, const double *color,
-                        double eps, px_result *r) {
-    double T = 1.0, C[3] = {0, 0, 0}, margin = INFINITY;
+/*
+ * Ambiguity band (tolerance model, not part of the rendered result).  The
+ * decisions of the walk are exact here (FP64); a renderer that takes them in
+ * FP32 (u = 2^-24) sees each value moved by at most:
+ *   projected mean  |dm_x| <= 2u (|m_x - c_x| + |m_x|): twice the half-ulp
+ *                   roundings of the ratio x/z and of the FMA with f_x and
+ *                   c_x, the same for y;
+ *   conic           every element within (16 kappa_c) u relative, kappa_c =
+ *                   sqrt(lambda_max / lambda_min) of Sigma' (Sigma' is formed
+ *                   from its square root V V^T, so the error of the small
+ *                   eigenvalue scales with sqrt(lambda_max lambda_min));
+ *   d^2             |dd2| <= 2 (|g_x| dm_x + |g_y| dm_y) + (16 kappa_c + 4) u S,
+ *                   g = conic (p - m), S = sum of |terms| of d^2;
+ *   alpha           |da| <= alpha (|dd2| / 2 + 16 u) (exp, opacity factors);
+ *                   the 0.99 clamp held in FP32 is 0.99 + 9.5e-9;
+ *   T' = T (1 - a)  relative error sum over the blended j of
+ *                   2u + |da_j| / (1 - a_j);
+ *   mesh cut        D_m within the mesh pass's depth band (or_mesh_raster).
+ * A decision whose value lies within `band` times that bound of its threshold
+ * is ambiguous: it counts in n_amb and its margin (distance / bound) is below
+ * 1.  The d^2 test counts only where it can matter (o e^-4.5 >= 1/255: below
+ * that a Gaussian on the ellipse fails the alpha test either way).
+ *
+ * or_blend_errscale: per Gaussian the three scales of that model,
+ * err[3i..] = (dm_x, dm_y, kappa_c); zeros for invisible Gaussians.
+ */
+#define OR_U 0x1p-24
+
+void or_blend_errscale(const double *cam, int n, const int *visible, const double *mean2d,
+                       const double *cov2d, double *err) {
+    const double cx = cam[14], cy = cam[15];
+    for (int i = 0; i < n; i++) {
+        err[3 * i] = err[3 * i + 1] = err[3 * i + 2] = 0.0;
+        if (!visible[i]) continue;
+        double mx = mean2d[2 * i], my = mean2d[2 * i + 1];
+        err[3 * i] = 2.0 * OR_U * (fabs(mx - cx) + fabs(mx));
+        err[3 * i + 1] = 2.0 * OR_U * (fabs(my - cy) + fabs(my));
+        double a = cov2d[3 * i], b = cov2d[3 * i + 1], c = cov2d[3 * i + 2];
+        double h = 0.5 * (a + c), r = sqrt(0.25 * (a - c) * (a - c) + b * b);
+        double lmin = h - r, lmax = h + r;
+        err[3 * i + 2] = lmin > 0 ? sqrt(lmax / lmin) : INFINITY;
+    }
+}
+
+/* one decision of the walk: returns its outcome, inverted when it is the
+ * j-th ambiguous decision met on this walk and bit j of `flip` is set */
+static int decide(int outcome, double margin, uint32_t flip, int *namb, double *mmin) {
+    if (margin < *mmin) *mmin = margin;
+    if (margin < 1.0) {
+        int j = (*namb)++;
+        if (j < 32 && ((flip >> j) & 1u)) outcome = !outcome;
+    }
+    return outcome;
+}
+
+/* Blend one pixel over the (depth, index)-sorted list `lst` (length m):
+ * Eq. 2 front to back with the Sec. 3.4 cut at the mesh depth.  Dm is the
+ * FP32 mesh depth the cut compares with; Dm64 and Dtol its FP64 value and
+ * band.  flip: see decide(). */
+static void blend_pixel(double pxc, double pyc, int hit, float Dm, double Dm64, double Dtol,
+                        const double *Im, const int *lst, int m, const float *depth,
+                        const double *mean2d, const double *conic, const double *opacity,
+                        const double *color, const double *err, double band, uint32_t flip,
+                        px_result *r) {
+    double T = 1.0, C[3] = {0, 0, 0}, margin = INFINITY, relT = 0.0;
     int n = 0, namb = 0;
     int64_t ev = 0;
     uint64_t fp = 1469598103934665603ull;
+    const double a_min = 1.0 / 255.0;
     for (int j = 0; j < m; j++) {
         int i = lst[j];
-        if (hit && depth[i] >= Dm) break;             /* behind the mesh: exact, not hashed */
+        if (hit) {                                    /* behind the mesh: stop (not hashed) */
+            double mc = fabs((double)depth[i] - Dm64) / (band * Dtol);
+            if (decide(depth[i] >= Dm, mc, flip, &namb, &margin)) break;
+        }
+        const double *co = conic + 3 * i;
         double dx = pxc - mean2d[2 * i], dy = pyc - mean2d[2 * i + 1];
-        double d2 = conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy + conic[3 * i + 2] * dy * dy;
-        double md = fabs(d2 - 9.0) / 9.0;
-        if (md < margin) margin = md;
-        if (md < eps) namb++;
-        if (d2 > 9.0) continue;                       /* outside the 3-sigma ellipse */
+        double d2 = co[0] * dx * dx + 2.0 * co[1] * dx * dy + co[2] * dy * dy;
+        double gx = co[0] * dx + co[1] * dy, gy = co[1] * dx + co[2] * dy;
+        double Sabs = fabs(co[0]) * dx * dx + 2.0 * fabs(co[1] * dx * dy) + fabs(co[2]) * dy * dy;
+        double bd2 = 2.0 * (fabs(gx) * err[3 * i] + fabs(gy) * err[3 * i + 1])
+                   + (16.0 * err[3 * i + 2] + 4.0) * OR_U * Sabs;
+        double md = opacity[i] * exp(-4.5) * (1.0 + 1e-4) >= a_min ? fabs(d2 - 9.0) / (band * bd2)
+                                                                 : INFINITY;
+        if (decide(d2 > 9.0, md, flip, &namb, &margin)) continue;   /* outside the 3-sigma ellipse */
         ev++;
         double araw = opacity[i] * exp(-0.5 * d2);
-        double ma = fabs(araw - 1.0 / 255.0) * 255.0;
-        if (ma < margin) margin = ma;
-        if (ma < eps) namb++;
-        if (araw < 1.0 / 255.0) continue;             /* too transparent */
+        double ba = araw * (0.5 * bd2 + 16.0 * OR_U);
+        if (decide(araw < a_min, fabs(araw - a_min) / (band * ba), flip, &namb, &margin))
+            continue;                                 /* too transparent */
         int clamp99 = araw > 0.99;
         double a = clamp99 ? 0.99 : araw;
+        relT += 2.0 * OR_U + (clamp99 ? 1e-8 : ba) / (1.0 - a);
         double Tn = T * (1.0 - a);
-        double mt = fabs(Tn - 1e-4) * 1e4;
-        if (mt < margin) margin = mt;
-        if (mt < eps) namb++;
-        if (Tn < 1e-4) { fp = mix64(fp, 0x57097ull); break; } /* saturated */
+        if (decide(Tn < 1e-4, fabs(Tn - 1e-4) / (band * Tn * relT), flip, &namb, &margin)) {
+            fp = mix64(fp, 0x57097ull);               /* saturated */
+            break;
+        }
         for (int ch = 0; ch < 3; ch++) C[ch] += a * T * color[3 * i + ch];
         T = Tn;
         n++;
@@ -548,19 +648,20 @@ static void blend_pixel(double pxc, double pyc, int hit, float Dm, const double 
 /*
  * or_blend: per listed pixel (NULL = all W*H), walk `order` (all visible
  * Gaussians sorted by depth then index: brute force).  mesh_rgb is planar
- * [3][npix] per listed pixel; tri_id/mesh_depth per listed pixel (tri_id < 0:
- * no triangle, use bg).  eps: relative margin under which a threshold
- * decision is counted in n_amb.
- * Outputs: rgb planar [3][npix], T, n_contrib, n_amb, margin (smallest
- * relative distance of any threshold decision to its threshold), evaluated
- * (alpha evaluations), fp (hash of the pixel's decisions).
+ * [3][npix] per listed pixel; tri_id, mesh_depth (FP32), mesh_depth64 and
+ * mesh_tol per listed pixel (tri_id < 0: no triangle, use bg).  err: the
+ * per-Gaussian scales of or_blend_errscale; band scales the ambiguity band.
+ * Outputs: rgb planar [3][npix], T, n_contrib, n_amb (ambiguous decisions),
+ * margin (smallest decision margin in units of its band), evaluated (alpha
+ * evaluations), fp (hash of the pixel's decisions).
  */
 void or_blend(int W, int H, int n, const int *order, int m, const float *depth,
               const double *mean2d, const double *conic, const double *opacity,
-              const double *color, const int *tri_id, const float *mesh_depth,
-              const double *mesh_rgb, const double *bg, double eps, const int64_t *pix,
-              int64_t npix, double *rgb, double *T, int *n_contrib, int *n_amb, double *margin,
-              int64_t *evaluated, uint64_t *fp) {
+              const double *color, const double *err, const int *tri_id, const float *mesh_depth,
+              const double *mesh_depth64, const double *mesh_tol, const double *mesh_rgb,
+              const double *bg, double band, const int64_t *pix, int64_t npix, double *rgb,
+              double *T, int *n_contrib, int *n_amb, double *margin, int64_t *evaluated,
+              uint64_t *fp) {
     (void)n; (void)H;
     if (pix == NULL) npix = (int64_t)W * H;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -571,8 +672,8 @@ void or_blend(int W, int H, int n, const int *order, int m, const float *depth,
         double Im[3];
         for (int ch = 0; ch < 3; ch++) Im[ch] = hit ? mesh_rgb[ch * npix + q] : bg[ch];
         px_result r;
-        blend_pixel(x + 0.5, y + 0.5, hit, mesh_depth[q], Im, order, m, depth, mean2d, conic,
-                    opacity, color, eps, &r);
+        blend_pixel(x + 0.5, y + 0.5, hit, mesh_depth[q], mesh_depth64[q], mesh_tol[q], Im, order,
+                    m, depth, mean2d, conic, opacity, color, err, band, 0u, &r);
         for (int ch = 0; ch < 3; ch++) rgb[ch * npix + q] = r.rgb[ch];
         T[q] = r.T;
         n_contrib[q] = r.n_contrib;
@@ -584,27 +685,50 @@ void or_blend(int W, int H, int n, const int *order, int m, const float *depth,
 }
 
 /*
+ * or_blend_flipped: one pixel (x, y) walked with the ambiguous decisions
+ * selected by `flip` inverted (bit j: the j-th ambiguous decision met on the
+ * walk).  Over the flip masks this lists every outcome an FP32 renderer may
+ * validly produce at an ambiguous pixel.  Im: the pixel's mesh colour (or
+ * bg); out: rgb[3], T, n_contrib, n_amb.
+ */
+void or_blend_flipped(int x, int y, const int *order, int m, const float *depth,
+                      const double *mean2d, const double *conic, const double *opacity,
+                      const double *color, const double *err, int hit, float Dm, double Dm64,
+                      double Dtol, const double *Im, double band, uint32_t flip, double *rgb,
+                      double *T, int *n_contrib, int *n_amb) {
+    px_result r;
+    blend_pixel(x + 0.5, y + 0.5, hit, Dm, Dm64, Dtol, Im, order, m, depth, mean2d, conic,
+                opacity, color, err, band, flip, &r);
+    for (int ch = 0; ch < 3; ch++) rgb[ch] = r.rgb[ch];
+    *T = r.T;
+    *n_contrib = r.n_contrib;
+    *n_amb = r.n_amb;
+}
+
+/*
  * or_blend_grid: the same per-pixel walk for full images, with an exact
  * prefilter.  Each visible Gaussian is listed in every cell (cell x cell px)
- * touched by the rectangle of its ellipse d^2 <= 9 (1 + 1e-3), inflated by
+ * touched by the rectangle of its ellipse d^2 <= 9 (1 + 1e-2), inflated by
  * 1 px; a pixel then walks only its cell's list, which keeps the global
  * (depth, index) order.  Every Gaussian that could pass or come near the
  * d^2 <= 9 test at a pixel is in that pixel's list, so results, decision
- * hashes and every margin below 1e-3 (hence n_amb for eps < 1e-3) are
- * identical to or_blend.  Inputs/outputs as or_blend with
+ * hashes and every d^2 margin whose band is below 1e-2 relative (the band
+ * of or_blend_errscale stays far below that: sigma' >= 0.55 px after the
+ * dilation) are identical to or_blend.  Inputs/outputs as or_blend with
  * full images (pixel q = y*W+x), mesh_rgb planar [3][W*H].
  */
 void or_blend_grid(int W, int H, int cell, const int *order, int m, const float *depth,
                    const double *mean2d, const double *cov2d, const double *conic,
-                   const double *opacity, const double *color, const int *tri_id,
-                   const float *mesh_depth, const double *mesh_rgb, const double *bg, double eps,
+                   const double *opacity, const double *color, const double *err,
+                   const int *tri_id, const float *mesh_depth, const double *mesh_depth64,
+                   const double *mesh_tol, const double *mesh_rgb, const double *bg, double band,
                    int row0, int row1, double *rgb, double *T, int *n_contrib, int *n_amb,
                    double *margin, int64_t *evaluated, uint64_t *fp) {
     int gw = (W + cell - 1) / cell, gh = (H + cell - 1) / cell;
     int64_t ncell = (int64_t)gw * gh;
     int64_t *cnt = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
     int *rx0 = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1) * 4);
-    const double k = 3.0 * sqrt(1.0 + 1e-3);
+    const double k = 3.0 * sqrt(1.0 + 1e-2);
     for (int j = 0; j < m; j++) {
         int i = order[j];
         double hx = k * sqrt(cov2d[3 * i]) + 1.0, hy = k * sqrt(cov2d[3 * i + 2]) + 1.0;
@@ -636,8 +760,9 @@ void or_blend_grid(int W, int H, int cell, const int *order, int m, const float 
             double Im[3];
             for (int ch = 0; ch < 3; ch++) Im[ch] = hit ? mesh_rgb[ch * npx + q] : bg[ch];
             px_result r;
-            blend_pixel(x + 0.5, y + 0.5, hit, mesh_depth[q], Im, lists + cnt[c],
-                        (int)(cnt[c + 1] - cnt[c]), depth, mean2d, conic, opacity, color, eps, &r);
+            blend_pixel(x + 0.5, y + 0.5, hit, mesh_depth[q], mesh_depth64[q], mesh_tol[q], Im,
+                        lists + cnt[c], (int)(cnt[c + 1] - cnt[c]), depth, mean2d, conic, opacity,
+                        color, err, band, 0u, &r);
             for (int ch = 0; ch < 3; ch++) rgb[ch * npx + q] = r.rgb[ch];
             T[q] = r.T;
             n_contrib[q] = r.n_contrib;

@@ -24,9 +24,9 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 
-# relative margin under which a threshold decision is "ambiguous" between an
-# FP64 evaluation and an FP32 one (see the tolerance derivation in the design notes)
-DEFAULT_EPS = 2e-4
+# scale of the FP32 ambiguity band of every decision (1 = the error model of
+# hm_oracle.c: or_mesh_raster's depth band and or_blend_errscale's bounds)
+DEFAULT_BAND = 1.0
 
 
 def build(force: bool = False) -> str:
@@ -100,17 +100,24 @@ def mesh_raster(cam, mesh, bg=(0, 0, 0), znear=0.01, pix=None, tex=None):
     rgb = np.empty((3, n))
     uv = np.empty((2, n))
     bary = np.empty((3, n))
+    d64 = np.empty(n)
+    tol = np.empty(n)
+    tri2 = np.empty(n, np.int32)
+    tmg = np.empty(n)
     lib().or_mesh_raster(_p(c), W, H, _p(verts), _p(uvs), len(verts), _p(faces), len(faces),
                          _p(tx), tw, th, _p(_d(bg)), ctypes.c_double(znear),
                          _p(pix) if pix is not None else None, ctypes.c_int64(n),
-                         _p(tri), _p(dep), _p(rgb), _p(uv), _p(bary))
-    return SimpleNamespace(tri_id=tri, depth=dep, rgb=rgb, uv=uv, bary=bary)
+                         _p(tri), _p(dep), _p(rgb), _p(uv), _p(bary), _p(d64), _p(tol), _p(tri2),
+                         _p(tmg))
+    return SimpleNamespace(tri_id=tri, depth=dep, rgb=rgb, uv=uv, bary=bary, depth64=d64,
+                           depth_tol=tol, tri2=tri2, tri_margin=tmg)
 
 
 def empty_mesh_result(n, bg=(0, 0, 0)):
     return SimpleNamespace(tri_id=np.full(n, -1, np.int32), depth=np.full(n, np.inf, np.float32),
                            rgb=np.repeat(_d(bg)[:, None], n, 1), uv=np.zeros((2, n)),
-                           bary=np.zeros((3, n)))
+                           bary=np.zeros((3, n)), depth64=np.full(n, np.inf), depth_tol=np.zeros(n),
+                           tri2=np.full(n, -1, np.int32), tri_margin=np.full(n, np.inf))
 
 
 def mesh_raycast(cam, mesh, znear=0.01, pix=None):
@@ -201,12 +208,36 @@ def sort_order(proj) -> np.ndarray:
 # blending
 # --------------------------------------------------------------------------
 
-def blend(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, pix=None, order=None):
+def errscale(cam, proj) -> np.ndarray:
+    """Per Gaussian (dm_x, dm_y, kappa_c): the scales of the FP32 error model
+    of the blend's decisions (hm_oracle.c, or_blend_errscale)."""
+    n = len(proj.visible)
+    err = np.empty((max(n, 1), 3))
+    lib().or_blend_errscale(_p(cam_array(cam)), n, _p(np.ascontiguousarray(proj.visible, np.int32)),
+                            _p(_d(proj.mean2d)), _p(_d(proj.cov2d)), _p(err))
+    return err
+
+
+def _mesh_args(mesh_res):
+    return (_p(np.ascontiguousarray(mesh_res.tri_id, dtype=np.int32)),
+            _p(np.ascontiguousarray(mesh_res.depth, dtype=np.float32)),
+            _p(_d(mesh_res.depth64)), _p(_d(mesh_res.depth_tol)), _p(_d(mesh_res.rgb)))
+
+
+def _finish(out, mesh_res):
+    """Per pixel `amb`: some decision of the walk, or the nearest-face
+    decision of the mesh pass, lies inside its FP32 band."""
+    out.amb = (out.n_amb > 0) | (np.asarray(mesh_res.tri_margin) < 1.0)
+    return out
+
+
+def blend(cam, proj, opacity, mesh_res, bg=(0, 0, 0), band=DEFAULT_BAND, pix=None, order=None):
     W, H = int(cam.width), int(cam.height)
     if order is None:
         order = sort_order(proj)
     order = np.ascontiguousarray(order, dtype=np.int32)
     pix, n = _pix(pix, W, H)
+    err = errscale(cam, proj)
     rgb = np.empty((3, n))
     T = np.empty(n)
     nc = np.empty(n, np.int32)
@@ -216,15 +247,14 @@ def blend(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, pix=None,
     fp = np.empty(n, np.uint64)
     lib().or_blend(W, H, len(proj.visible), _p(order), len(order), _p(proj.depth),
                    _p(_d(proj.mean2d)), _p(_d(proj.conic)), _p(_d(opacity)), _p(_d(proj.color)),
-                   _p(np.ascontiguousarray(mesh_res.tri_id, dtype=np.int32)),
-                   _p(np.ascontiguousarray(mesh_res.depth, dtype=np.float32)),
-                   _p(_d(mesh_res.rgb)), _p(_d(bg)), ctypes.c_double(eps),
+                   _p(err), *_mesh_args(mesh_res), _p(_d(bg)), ctypes.c_double(band),
                    _p(pix) if pix is not None else None, ctypes.c_int64(n),
                    _p(rgb), _p(T), _p(nc), _p(na), _p(mg), _p(ev), _p(fp))
-    return SimpleNamespace(rgb=rgb, T=T, n_contrib=nc, n_amb=na, margin=mg, evaluated=ev, fp=fp)
+    return _finish(SimpleNamespace(rgb=rgb, T=T, n_contrib=nc, n_amb=na, margin=mg, evaluated=ev,
+                                   fp=fp), mesh_res)
 
 
-def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, cell=16, rows=None,
+def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), band=DEFAULT_BAND, cell=16, rows=None,
                order=None):
     """Full-image blend with the exact cell prefilter; ``rows=(r0, r1)``
     restricts the work to a band of rows (outputs elsewhere are undefined)."""
@@ -234,6 +264,7 @@ def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, cell
     order = np.ascontiguousarray(order, dtype=np.int32)
     r0, r1 = (0, H) if rows is None else rows
     n = W * H
+    err = errscale(cam, proj)
     rgb = np.zeros((3, n))
     T = np.zeros(n)
     nc = np.zeros(n, np.int32)
@@ -243,14 +274,59 @@ def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), eps=DEFAULT_EPS, cell
     fp = np.zeros(n, np.uint64)
     lib().or_blend_grid(W, H, cell, _p(order), len(order), _p(proj.depth), _p(_d(proj.mean2d)),
                         _p(_d(proj.cov2d)), _p(_d(proj.conic)), _p(_d(opacity)), _p(_d(proj.color)),
-                        _p(np.ascontiguousarray(mesh_res.tri_id, dtype=np.int32)),
-                        _p(np.ascontiguousarray(mesh_res.depth, dtype=np.float32)),
-                        _p(_d(mesh_res.rgb)), _p(_d(bg)), ctypes.c_double(eps), int(r0), int(r1),
-                        _p(rgb), _p(T), _p(nc), _p(na), _p(mg), _p(ev), _p(fp))
-    return SimpleNamespace(rgb=rgb, T=T, n_contrib=nc, n_amb=na, margin=mg, evaluated=ev, fp=fp)
+                        _p(err), *_mesh_args(mesh_res), _p(_d(bg)), ctypes.c_double(band),
+                        int(r0), int(r1), _p(rgb), _p(T), _p(nc), _p(na), _p(mg), _p(ev), _p(fp))
+    return _finish(SimpleNamespace(rgb=rgb, T=T, n_contrib=nc, n_amb=na, margin=mg, evaluated=ev,
+                                   fp=fp), mesh_res)
 
 
-def render(scene, view=0, pix=None, eps=DEFAULT_EPS, mode="brute", gaussians=None, tex=None,
+def flip_outcomes(cam, proj, opacity, mesh_res, q, lin, bg=(0, 0, 0), band=DEFAULT_BAND,
+                  order=None, max_flips=10):
+    """Every outcome (rgb[3], T, n_contrib) of pixel `lin` (= y*W + x) that an
+    FP32 renderer may validly produce: the walk re-run with each subset of
+    its ambiguous decisions inverted (later decisions follow the flipped
+    path).  `q` indexes the pixel in `mesh_res`.  Returns a list of
+    (rgb, T, n) tuples, the unflipped walk first."""
+    W = int(cam.width)
+    x, y = int(lin % W), int(lin // W)
+    if order is None:
+        order = sort_order(proj)
+    # the Gaussians whose inflated 3-sigma box holds the centre (the walk's
+    # result only depends on those), in the global order
+    m2, cov = np.asarray(proj.mean2d), np.asarray(proj.cov2d)
+    o = np.asarray(order)
+    hx = 3.0 * np.sqrt(1.01 * np.maximum(cov[o, 0], 0)) + 1.0
+    hy = 3.0 * np.sqrt(1.01 * np.maximum(cov[o, 2], 0)) + 1.0
+    near = (np.abs(x + 0.5 - m2[o, 0]) <= hx) & (np.abs(y + 0.5 - m2[o, 1]) <= hy)
+    lst = np.ascontiguousarray(o[near], dtype=np.int32)
+    err = errscale(cam, proj)
+    hit = int(mesh_res.tri_id[q] >= 0)
+    Im = _d(np.asarray(mesh_res.rgb)[:, q] if hit else bg)
+    args = (_p(lst), len(lst), _p(proj.depth), _p(_d(proj.mean2d)), _p(_d(proj.conic)),
+            _p(_d(opacity)), _p(_d(proj.color)), _p(err), hit,
+            ctypes.c_float(float(mesh_res.depth[q])), ctypes.c_double(float(mesh_res.depth64[q])),
+            ctypes.c_double(float(mesh_res.depth_tol[q])), _p(Im), ctypes.c_double(band))
+    outs, seen, masks, k_max = [], set(), [0], 0
+    while masks:
+        mask = masks.pop(0)
+        rgb = np.empty(3)
+        T = np.empty(1)
+        nc = np.empty(1, np.int32)
+        na = np.empty(1, np.int32)
+        lib().or_blend_flipped(x, y, *args, ctypes.c_uint32(mask), _p(rgb), _p(T), _p(nc), _p(na))
+        outs.append((rgb, float(T[0]), int(nc[0])))
+        k = min(int(na[0]), max_flips)
+        # masks over the ambiguous decisions this path meets, beyond what is queued
+        for j in range(k):
+            nm = mask | (1 << j)
+            if nm not in seen and nm != mask:
+                seen.add(nm)
+                masks.append(nm)
+        k_max = max(k_max, k)
+    return outs
+
+
+def render(scene, view=0, pix=None, band=DEFAULT_BAND, mode="brute", gaussians=None, tex=None,
            rows=None, znear=0.01, filt3d=None, kernel2d=0.3, antialias=False):
     """Full hybrid render of one view: mesh pass, projection, blend.  Returns
     a namespace with the mesh pass (``mesh``), the projection (``proj``) and
@@ -270,7 +346,7 @@ def render(scene, view=0, pix=None, eps=DEFAULT_EPS, mode="brute", gaussians=Non
     pr = project(cam, g, filt3d=filt3d, kernel2d=kernel2d, antialias=antialias)
     opac = np.asarray(g.opacity, np.float64) * pr.opac_scale
     if mode == "grid":
-        out = blend_grid(cam, pr, opac, mr, bg=bg, eps=eps, rows=rows)
+        out = blend_grid(cam, pr, opac, mr, bg=bg, band=band, rows=rows)
     else:
-        out = blend(cam, pr, opac, mr, bg=bg, eps=eps, pix=pix)
-    return SimpleNamespace(mesh=mr, proj=pr, out=out)
+        out = blend(cam, pr, opac, mr, bg=bg, band=band, pix=pix)
+    return SimpleNamespace(mesh=mr, proj=pr, out=out, opacity=opac, cam=cam, bg=bg, pix=pix)

@@ -165,8 +165,10 @@ def _band_limited_noise(rng, size, cutoff_px=6.0):
 # config 0: 2k Gaussians in front of / behind one textured quad, 128x128
 # --------------------------------------------------------------------------
 
-def config0_scene(seed: int = 0, n: int = 2000) -> Scene:
-    """2,000 Gaussians, means U[-1,1]^3 + (0,0,2.5), log-scales N(-3.5,0.5),
+def config0_scene(seed: int = 1, n: int = 2000) -> Scene:
+    """The default seed is one at which no decision of the render lies in
+    the FP32 ambiguity band of an FP32 renderer (the exact checks then cover
+    every pixel).  2,000 Gaussians, means U[-1,1]^3 + (0,0,2.5), log-scales N(-3.5,0.5),
     uniform unit quaternions, opacity sigmoid(N(0,1)), SH degree 0 with DC
     coefficients U[0,1]; a 2-triangle quad at z=3 that fills a 128x128 view
     (fx=fy=128, centred principal point, identity pose) with a 64x64 RGB8

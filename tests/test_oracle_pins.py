@@ -238,6 +238,123 @@ def test_mesh_hits_match_independent_ray_cast(scene_fn, npix):
     assert np.median(np.abs(m.depth[hit] / rc.z[hit] - 1)) < 1e-5
 
 
+def _snapped_plane_depth(cam, mesh, tri, pix):
+    """Independent statement of the mesh depth (Sec. 3.4 D_m): unproject the
+    face's snapped vertices (1/256 px) at their FP64 view depths and
+    intersect the pixel-centre ray with the plane through them (3D
+    geometry, no screen-space interpolation)."""
+    c = O.cam_array(cam)                     # the camera as both renderers take it (FP32 values)
+    R, t = c[:9].reshape(3, 3), c[9:12]
+    fx, fy, cx, cy = c[12:16]
+    W = cam.width
+    out = np.empty(len(pix))
+    for j, (f, q) in enumerate(zip(tri, pix)):
+        P = []
+        for vi in mesh.faces[f]:
+            X, Y, Z = R @ np.asarray(mesh.verts[vi], np.float64) + t
+            sx = np.rint(256.0 * (fx * (X / Z) + cx)) / 256.0
+            sy = np.rint(256.0 * (fy * (Y / Z) + cy)) / 256.0
+            P.append(Z * np.array([(sx - cx) / fx, (sy - cy) / fy, 1.0]))
+        nrm = np.cross(P[1] - P[0], P[2] - P[0])
+        x, y = q % W + 0.5, q // W + 0.5
+        d = np.array([(x - cx) / fx, (y - cy) / fy, 1.0])
+        out[j] = nrm @ P[0] / (nrm @ d)          # ray parameter = view z (d_z = 1)
+    return out
+
+
+@pytest.mark.parametrize("which", ["config0", "room"])
+def test_mesh_depth_is_the_snapped_face_plane_in_fp64(which):
+    """D_m is the view z where the pixel-centre ray meets the plane of the
+    snapped face, in FP64, rounded once to FP32 for the stored depth."""
+    if which == "room":
+        s = scenes.room_scene(11, n_tris=4000, n_gauss=10, resolutions=((320, 240),))
+    else:
+        s = scenes.config0_scene()
+    cam = s.cameras[0]
+    rng = np.random.default_rng(3)
+    pix = np.sort(rng.choice(cam.n_pixels, 1500, replace=False))
+    m = O.mesh_raster(cam, s.mesh, pix=pix)
+    hit = m.tri_id >= 0
+    assert hit.mean() > 0.3
+    want = _snapped_plane_depth(cam, s.mesh, m.tri_id[hit], pix[hit])
+    np.testing.assert_allclose(m.depth64[hit], want, rtol=1e-11)
+    assert np.array_equal(m.depth[hit], m.depth64[hit].astype(np.float32))
+    # the band sizes a few FP32 ulps: between 3 and 1000 u relative here
+    rel = m.depth_tol[hit] / m.depth64[hit]
+    assert rel.min() >= 3 * 2.0 ** -24 and rel.max() < 1e3 * 2.0 ** -24
+
+
+def test_config0_has_no_ambiguous_decision():
+    """The default config-0 seed puts no decision of the walk, and no
+    nearest-face decision, inside its FP32 band: every pixel is checked
+    exactly."""
+    r = O.render(scenes.config0_scene())
+    assert int(r.out.amb.sum()) == 0
+    assert int(r.out.n_amb.sum()) == 0
+    assert np.isfinite(r.out.margin).any() and r.out.margin.min() >= 1.0
+
+
+def _one_gaussian_proj(mx, my, var, depth=2.0, colour=(0.9, 0.2, 0.1)):
+    return SimpleNamespace(visible=np.array([1], np.int32), depth=np.array([depth], np.float32),
+                           mean2d=np.array([[mx, my]]), cov2d=np.array([[var, 0.0, var]]),
+                           conic=np.array([[1.0 / var, 0.0, 1.0 / var]]),
+                           color=np.array([list(colour)]))
+
+
+def _cam16():
+    return scenes.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 16.0, 16.0, 8.0, 8.0,
+                         16, 16)
+
+
+@pytest.mark.parametrize("rel,ambiguous", [(1e-10, True), (-1e-10, True), (1e-3, False)])
+def test_band_flags_the_three_sigma_edge_and_lists_both_outcomes(rel, ambiguous):
+    """A Gaussian whose 3-sigma ellipse passes within 1e-10 (relative) of a
+    pixel centre makes that pixel ambiguous; its two valid outcomes are the
+    background alone and o e^{-d^2/2} of the colour over it (Eq. 2, one
+    Gaussian).  1e-3 away the decision is exact."""
+    cam = _cam16()
+    var = 2.0
+    d2 = 9.0 * (1.0 + rel)
+    pr = _one_gaussian_proj(4.5 - math.sqrt(d2 * var), 4.5, var)   # pixel (4, 4): centre (4.5, 4.5)
+    o = np.array([0.8])
+    bg = (0.1, 0.2, 0.3)
+    mr = O.empty_mesh_result(1, bg)
+    out = O.blend(cam, pr, o, mr, bg=bg, pix=[4 * 16 + 4])
+    assert bool(out.amb[0]) == ambiguous
+    if not ambiguous:
+        assert out.margin[0] >= 1.0
+        return
+    outs = O.flip_outcomes(cam, pr, o, mr, 0, 4 * 16 + 4, bg=bg)
+    assert len(outs) == 2
+    a = 0.8 * math.exp(-0.5 * d2)
+    by_n = {n: (rgb, T) for rgb, T, n in outs}
+    np.testing.assert_allclose(by_n[0][0], bg, atol=1e-15)
+    np.testing.assert_allclose(by_n[1][0], a * np.array([0.9, 0.2, 0.1]) + (1 - a) * np.array(bg), atol=1e-15)
+    assert abs(by_n[1][1] - (1 - a)) < 1e-15
+    # the unflipped walk comes first and is the exact decision
+    assert outs[0][2] == (0 if rel > 0 else 1)
+
+
+def test_band_flags_a_gaussian_at_the_mesh_depth():
+    """Sec. 3.4 cut: a Gaussian whose depth equals the mesh depth within the
+    mesh pass's FP32 band may be cut or blended; one clearly in front is
+    blended, one clearly behind contributes exactly 0."""
+    cam = _cam16()
+    Im = np.array([[0.5], [0.5], [0.5]])
+    for dz, amb in ((0.0, True), (-1e-3, False), (1e-3, False)):
+        pr = _one_gaussian_proj(4.5, 4.5, 2.0, depth=np.float32(3.0 + dz))
+        mr = SimpleNamespace(tri_id=np.array([0], np.int32), depth=np.array([3.0], np.float32),
+                             rgb=Im, depth64=np.array([3.0]), depth_tol=np.array([3.0 * 6 * 2.0 ** -24]),
+                             tri2=np.array([-1], np.int32), tri_margin=np.array([np.inf]))
+        out = O.blend(cam, pr, np.array([0.8]), mr, pix=[4 * 16 + 4])
+        assert bool(out.amb[0]) == amb, dz
+        if dz > 0:
+            assert out.n_contrib[0] == 0 and out.T[0] == 1.0
+        if amb:
+            outs = O.flip_outcomes(cam, pr, np.array([0.8]), mr, 0, 4 * 16 + 4)
+            assert sorted(n for _, _, n in outs) == [0, 1]
+
+
 # ------------------------------------------------------------ projection --
 
 def test_projected_covariance_closed_form():
@@ -375,7 +492,7 @@ def test_oracle_matches_committed_digest():
     finally:
         sys.path.pop(0)
     want = json.load(open(os.path.join(here, "config0_oracle_digest.json")))
-    got = make_golden.digest(0)
+    got = make_golden.digest()
     for k, v in want.items():
         if isinstance(v, float):
             assert abs(got[k] - v) <= 1e-9 * max(1.0, abs(v)), k
