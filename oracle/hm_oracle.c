@@ -550,7 +550,11 @@ static uint64_t mix64(uint64_t h, uint64_t v) {
  *                   the 0.99 clamp held in FP32 is 0.99 + 9.5e-9;
  *   T' = T (1 - a)  relative error sum over the blended j of
  *                   2u + |da_j| / (1 - a_j);
- *   mesh cut        D_m within the mesh pass's depth band (or_mesh_raster).
+ *   mesh cut        D_m within the mesh pass's depth band (or_mesh_raster);
+ *                   the cut of a Gaussian in that band can change the pixel
+ *                   only if it, or a later Gaussian still in the band, could
+ *                   be blended there (d^2 and alpha within their bands of
+ *                   passing), so only then is it counted.
  * A decision whose value lies within `band` times that bound of its threshold
  * is ambiguous: it counts in n_amb and its margin (distance / bound) is below
  * 1.  The d^2 test counts only where it can matter (o e^-4.5 >= 1/255: below
@@ -588,6 +592,28 @@ static int decide(int outcome, double margin, uint32_t flip, int *namb, double *
     return outcome;
 }
 
+/* Band of d^2 at the pixel for Gaussian i (see the model above); *d2 gets d^2. */
+static double d2_band(double pxc, double pyc, int i, const double *mean2d, const double *conic,
+                      const double *err, double *d2) {
+    const double *co = conic + 3 * i;
+    double dx = pxc - mean2d[2 * i], dy = pyc - mean2d[2 * i + 1];
+    *d2 = co[0] * dx * dx + 2.0 * co[1] * dx * dy + co[2] * dy * dy;
+    double gx = co[0] * dx + co[1] * dy, gy = co[1] * dx + co[2] * dy;
+    double Sabs = fabs(co[0]) * dx * dx + 2.0 * fabs(co[1] * dx * dy) + fabs(co[2]) * dy * dy;
+    return 2.0 * (fabs(gx) * err[3 * i] + fabs(gy) * err[3 * i + 1])
+         + (16.0 * err[3 * i + 2] + 4.0) * OR_U * Sabs;
+}
+
+/* could an FP32 evaluation blend Gaussian i at the pixel? */
+static int maybe_blended(double pxc, double pyc, int i, const double *mean2d, const double *conic,
+                         const double *opacity, const double *err, double band) {
+    double d2, bd2 = band * d2_band(pxc, pyc, i, mean2d, conic, err, &d2);
+    double dmin = d2 - bd2 > 0.0 ? d2 - bd2 : 0.0;
+    if (dmin > 9.0) return 0;
+    double amax = opacity[i] * exp(-0.5 * dmin) * (1.0 + band * 16.0 * OR_U);
+    return amax >= 1.0 / 255.0;
+}
+
 /* Blend one pixel over the (depth, index)-sorted list `lst` (length m):
  * Eq. 2 front to back with the Sec. 3.4 cut at the mesh depth.  Dm is the
  * FP32 mesh depth the cut compares with; Dm64 and Dtol its FP64 value and
@@ -606,15 +632,19 @@ static void blend_pixel(double pxc, double pyc, int hit, float Dm, double Dm64, 
         int i = lst[j];
         if (hit) {                                    /* behind the mesh: stop (not hashed) */
             double mc = fabs((double)depth[i] - Dm64) / (band * Dtol);
+            if (mc < 1.0) {
+                /* in the band: it matters only if this or a later Gaussian
+                 * of the band could be blended here */
+                int matters = 0;
+                for (int k = j; k < m && !matters; k++) {
+                    if ((double)depth[lst[k]] > Dm64 + band * Dtol) break;
+                    matters = maybe_blended(pxc, pyc, lst[k], mean2d, conic, opacity, err, band);
+                }
+                if (!matters) mc = INFINITY;
+            }
             if (decide(depth[i] >= Dm, mc, flip, &namb, &margin)) break;
         }
-        const double *co = conic + 3 * i;
-        double dx = pxc - mean2d[2 * i], dy = pyc - mean2d[2 * i + 1];
-        double d2 = co[0] * dx * dx + 2.0 * co[1] * dx * dy + co[2] * dy * dy;
-        double gx = co[0] * dx + co[1] * dy, gy = co[1] * dx + co[2] * dy;
-        double Sabs = fabs(co[0]) * dx * dx + 2.0 * fabs(co[1] * dx * dy) + fabs(co[2]) * dy * dy;
-        double bd2 = 2.0 * (fabs(gx) * err[3 * i] + fabs(gy) * err[3 * i + 1])
-                   + (16.0 * err[3 * i + 2] + 4.0) * OR_U * Sabs;
+        double d2, bd2 = d2_band(pxc, pyc, i, mean2d, conic, err, &d2);
         double md = opacity[i] * exp(-4.5) * (1.0 + 1e-4) >= a_min ? fabs(d2 - 9.0) / (band * bd2)
                                                                  : INFINITY;
         if (decide(d2 > 9.0, md, flip, &namb, &margin)) continue;   /* outside the 3-sigma ellipse */

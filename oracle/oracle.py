@@ -281,7 +281,7 @@ def blend_grid(cam, proj, opacity, mesh_res, bg=(0, 0, 0), band=DEFAULT_BAND, ce
 
 
 def flip_outcomes(cam, proj, opacity, mesh_res, q, lin, bg=(0, 0, 0), band=DEFAULT_BAND,
-                  order=None, max_flips=10):
+                  order=None, err=None, max_flips=10):
     """Every outcome (rgb[3], T, n_contrib) of pixel `lin` (= y*W + x) that an
     FP32 renderer may validly produce: the walk re-run with each subset of
     its ambiguous decisions inverted (later decisions follow the flipped
@@ -299,14 +299,14 @@ def flip_outcomes(cam, proj, opacity, mesh_res, q, lin, bg=(0, 0, 0), band=DEFAU
     hy = 3.0 * np.sqrt(1.01 * np.maximum(cov[o, 2], 0)) + 1.0
     near = (np.abs(x + 0.5 - m2[o, 0]) <= hx) & (np.abs(y + 0.5 - m2[o, 1]) <= hy)
     lst = np.ascontiguousarray(o[near], dtype=np.int32)
-    err = errscale(cam, proj)
+    err = errscale(cam, proj) if err is None else err
     hit = int(mesh_res.tri_id[q] >= 0)
     Im = _d(np.asarray(mesh_res.rgb)[:, q] if hit else bg)
     args = (_p(lst), len(lst), _p(proj.depth), _p(_d(proj.mean2d)), _p(_d(proj.conic)),
             _p(_d(opacity)), _p(_d(proj.color)), _p(err), hit,
             ctypes.c_float(float(mesh_res.depth[q])), ctypes.c_double(float(mesh_res.depth64[q])),
             ctypes.c_double(float(mesh_res.depth_tol[q])), _p(Im), ctypes.c_double(band))
-    outs, seen, masks, k_max = [], set(), [0], 0
+    outs, seen, masks = [], {0}, [0]
     while masks:
         mask = masks.pop(0)
         rgb = np.empty(3)
@@ -319,10 +319,9 @@ def flip_outcomes(cam, proj, opacity, mesh_res, q, lin, bg=(0, 0, 0), band=DEFAU
         # masks over the ambiguous decisions this path meets, beyond what is queued
         for j in range(k):
             nm = mask | (1 << j)
-            if nm not in seen and nm != mask:
+            if nm not in seen:
                 seen.add(nm)
                 masks.append(nm)
-        k_max = max(k_max, k)
     return outs
 
 
@@ -345,8 +344,20 @@ def render(scene, view=0, pix=None, band=DEFAULT_BAND, mode="brute", gaussians=N
         mr = empty_mesh_result(n, bg)
     pr = project(cam, g, filt3d=filt3d, kernel2d=kernel2d, antialias=antialias)
     opac = np.asarray(g.opacity, np.float64) * pr.opac_scale
+    order = sort_order(pr)
     if mode == "grid":
-        out = blend_grid(cam, pr, opac, mr, bg=bg, band=band, rows=rows)
+        out = blend_grid(cam, pr, opac, mr, bg=bg, band=band, rows=rows, order=order)
     else:
-        out = blend(cam, pr, opac, mr, bg=bg, band=band, pix=pix)
-    return SimpleNamespace(mesh=mr, proj=pr, out=out, opacity=opac, cam=cam, bg=bg, pix=pix)
+        out = blend(cam, pr, opac, mr, bg=bg, band=band, pix=pix, order=order)
+    return SimpleNamespace(mesh=mr, proj=pr, out=out, opacity=opac, cam=cam, bg=bg, pix=pix,
+                           order=order, band=band)
+
+
+def outcomes_at(orc, j):
+    """flip_outcomes for entry j of a render() result (pixel pix[j], or j
+    for a full image)."""
+    lin = int(orc.pix[j]) if orc.pix is not None else int(j)
+    if not hasattr(orc, "err"):
+        orc.err = errscale(orc.cam, orc.proj)
+    return flip_outcomes(orc.cam, orc.proj, orc.opacity, orc.mesh, j, lin, bg=orc.bg, band=orc.band,
+                         order=orc.order, err=orc.err)

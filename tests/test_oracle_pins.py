@@ -353,6 +353,11 @@ def test_band_flags_a_gaussian_at_the_mesh_depth():
         if amb:
             outs = O.flip_outcomes(cam, pr, np.array([0.8]), mr, 0, 4 * 16 + 4)
             assert sorted(n for _, _, n in outs) == [0, 1]
+        # the same Gaussian 5 sigma away from the pixel: cut or not, it adds
+        # nothing there, so its cut is not a decision of that pixel
+        far = _one_gaussian_proj(4.5 + 5 * math.sqrt(2.0), 4.5, 2.0, depth=np.float32(3.0 + dz))
+        out = O.blend(cam, far, np.array([0.8]), mr, pix=[4 * 16 + 4])
+        assert not out.amb[0] and out.n_contrib[0] == 0 and out.T[0] == 1.0
 
 
 # ------------------------------------------------------------ projection --
