@@ -16,7 +16,7 @@ from oracle import torch_ref as TR
 from paper_2506_06988_b300 import scenes
 from paper_2506_06988_b300.render import HybridRender, MeshInput
 
-from gpu_util import EPS, check_grad, gpu_render, gaussians_to_torch, make_renderer  # noqa: E402
+from gpu_util import check_grad, gpu_render, gaussians_to_torch, make_renderer  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,7 @@ def _run(scene, tex_grad, seed=0, tile=(16, 16), batch=None):
     gI = rng.standard_normal((3, npx))
     gT = rng.standard_normal(npx)
     orc = O.render(scene)
-    amb = orc.out.margin < EPS
+    amb = orc.out.amb
     gI[:, amb] = 0.0
     gT[amb] = 0.0
     tex = O.texture_unit(scene.mesh.texture) if scene.mesh is not None else None
@@ -146,7 +146,7 @@ def test_config1_full_size_backward_sampled_pixels():
     cand = np.sort(rng.choice(s.cameras[v].n_pixels, 4000, replace=False))
     orc = O.render(s, v, pix=cand)
     # unambiguous pixels where Gaussians are blended (most wall pixels have none)
-    pix = cand[(orc.out.margin >= EPS) & (orc.out.n_contrib > 0)][:64]
+    pix = cand[(~orc.out.amb) & (orc.out.n_contrib > 0)][:64]
     assert len(pix) == 64
     gI = rng.standard_normal((3, len(pix)))
     dI = np.zeros((3 * r.npix,), np.float64)

@@ -10,8 +10,15 @@ from paper_2506_06988_b300.render import MeshInput
 
 pytestmark = pytest.mark.gpu
 
-from gpu_util import (EPS, compare_blend, expected_pairs, gaussians_to_torch, gpu_render, oracle_view,  # noqa: E402
-                      records_np, view_outputs)
+from gpu_util import (compare_blend, compare_mesh, expected_pairs, gaussians_to_torch, gpu_render,  # noqa: E402
+                      oracle_view, records_np, view_outputs)
+
+# Ambiguous pixels (a decision inside its FP32 band) are checked against the
+# oracle's list of valid outcomes; their share is bounded by what the band
+# measures on these scenes: 0 on config 0, at most 5.5e-4 on the small rooms
+# and 1.7e-3 on 1080p rows (an FP32 mean at ~1000 px carries a half-ulp of
+# ~3e-5 px, which the d^2 band has to admit).
+AMB_ROOM = 2e-3
 
 
 def _small_room(seed=11, res=((160, 120),), n_gauss=6000, n_tris=3000, **kw):
@@ -27,10 +34,9 @@ def test_mesh_raster_config0_bit_exact(tile):
     r, _, _ = gpu_render(s, tile=tile)
     g = view_outputs(r, 0)
     m = O.mesh_raster(s.cameras[0], s.mesh, bg=s.bg)
+    st = compare_mesh(g, m, rgb_tol=1e-5)
+    assert st["tri_ambiguous"] == 0 and st["tri_swapped"] == 0
     assert np.array_equal(g.tri_id, m.tri_id)
-    assert np.array_equal(g.depth, m.depth)
-    assert np.abs(g.mesh_rgb - m.rgb).max() < 1e-5
-    assert np.abs(g.uv - m.uv).max() < 1e-6
 
 
 def test_mesh_raster_room_multiview_ragged():
@@ -44,19 +50,23 @@ def test_mesh_raster_room_multiview_ragged():
     for v, cam in enumerate(s.cameras):
         g = view_outputs(r, v)
         m = O.mesh_raster(cam, s.mesh, bg=s.bg)
-        assert np.array_equal(g.tri_id, m.tri_id)
-        assert np.array_equal(g.depth, m.depth)
+        print(v, compare_mesh(g, m))
         hit = m.tri_id >= 0
         misses += int((~hit).sum())
         assert hit.mean() > 0.3
-        assert np.abs(g.mesh_rgb - m.rgb).max() < 1e-4
         W, H = cam.width, cam.height
         tx_n, ty_n = (W + 15) // 16, (H + 15) // 16
-        D = m.depth.reshape(H, W)
+        Dg = g.depth.reshape(H, W)
+        D64 = np.where(hit, m.depth64, np.inf).reshape(H, W)
+        tol = m.depth_tol.reshape(H, W)
         for ty in range(ty_n):
             for tx in range(tx_n):
-                blk = D[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
-                assert tmax[toff + ty * tx_n + tx] == blk.max()
+                b = np.s_[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
+                # the tile's farthest mesh depth: the maximum of the GPU's own
+                # depths, within the band of the FP64 maximum
+                assert tmax[toff + ty * tx_n + tx] == Dg[b].max()
+                if np.isfinite(D64[b].max()):
+                    assert abs(tmax[toff + ty * tx_n + tx] - D64[b].max()) <= tol[b].max()
         toff += tx_n * ty_n
     assert misses > 0            # the pruned holes show through somewhere
 
@@ -69,9 +79,8 @@ def test_mesh_f32_texture_and_background():
     r, _, _ = gpu_render(s)
     g = view_outputs(r, 0)
     m = O.mesh_raster(s.cameras[0], s.mesh, bg=s.bg)
-    assert np.array_equal(g.tri_id, m.tri_id)
-    assert np.array_equal(g.depth, m.depth)
-    assert np.abs(g.mesh_rgb - m.rgb).max() < 1e-5
+    st = compare_mesh(g, m, rgb_tol=1e-5)
+    assert st["tri_swapped"] == 0
 
 
 # ------------------------------------------------------------- projection --
@@ -92,6 +101,27 @@ def test_projection_records_match_oracle():
         scale = np.sqrt(np.abs(p.conic[on, 0] * p.conic[on, 2]))
         c_err = np.abs(rec.conic[sl][on] - p.conic[on]) / scale[:, None]
         assert c_err.max() < 1e-4, c_err.max()
+        # the FP32 band the oracle puts on every d^2 decision covers the
+        # records' actual error: the mean within its model, and d^2 of the
+        # record at 16 points of the oracle's 3-sigma ellipse within the
+        # position and conic parts of the band
+        err = O.errscale(cam, p)[on]
+        assert (m_err <= err[:, :2]).all(), float((m_err / err[:, :2]).max())
+        cov = p.cov2d[on]
+        L = np.stack([np.sqrt(cov[:, 0]), cov[:, 1] / np.sqrt(cov[:, 0]),
+                      np.sqrt(cov[:, 2] - cov[:, 1] ** 2 / cov[:, 0])], 1)   # Cholesky of Sigma'
+        for ang in np.linspace(0, 2 * np.pi, 16, endpoint=False):
+            ux, uy = 3 * np.cos(ang), 3 * np.sin(ang)                         # d^2 = 9 exactly
+            dx, dy = L[:, 0] * ux, L[:, 1] * ux + L[:, 2] * uy
+            px, py = p.mean2d[on, 0] + dx, p.mean2d[on, 1] + dy
+            rc = rec.conic[sl][on]
+            rx, ry = px - rec.mean[sl][on, 0], py - rec.mean[sl][on, 1]
+            d2r = rc[:, 0] * rx * rx + 2 * rc[:, 1] * rx * ry + rc[:, 2] * ry * ry
+            co = p.conic[on]
+            gx, gy = co[:, 0] * dx + co[:, 1] * dy, co[:, 1] * dx + co[:, 2] * dy
+            S = np.abs(co[:, 0]) * dx * dx + 2 * np.abs(co[:, 1] * dx * dy) + np.abs(co[:, 2]) * dy * dy
+            band = 2 * (np.abs(gx) * err[:, 0] + np.abs(gy) * err[:, 1]) + 16 * err[:, 2] * 2.0 ** -24 * S
+            assert (np.abs(d2r - 9.0) <= band).all(), float((np.abs(d2r - 9.0) / band).max())
         assert np.abs(rec.color[sl][on] - p.color[on]).max() < 1e-5
         assert np.array_equal(rec.opacity[sl], s.gaussians.opacity)
         # tile rectangle covers the oracle's 3-sigma bounding box
@@ -212,7 +242,7 @@ def test_hybrid_render_config0(tile, batch):
     s = scenes.config0_scene()
     r, _, _ = gpu_render(s, tile=tile, batch=batch)
     st = compare_blend(view_outputs(r, 0), oracle_view(s, 0))
-    assert st["amb_frac"] < 0.01
+    assert st["ambiguous"] == 0          # the default seed has no decision in its band
     print(st)
 
 
@@ -241,7 +271,7 @@ def test_hybrid_render_room_multiview():
     r, _, _ = gpu_render(s)
     for v in range(3):
         st = compare_blend(view_outputs(r, v), oracle_view(s, v, mode="grid"))
-        assert st["amb_frac"] < 0.01, st
+        assert st["amb_frac"] < AMB_ROOM, st
         print(v, st)
 
 
@@ -250,14 +280,14 @@ def test_gaussian_only_scene_no_mesh():
     s.bg = np.array([0.3, 0.3, 0.3], np.float32)
     r, _, _ = gpu_render(s)
     st = compare_blend(view_outputs(r, 0), oracle_view(s, 0, mode="grid"))
-    assert st["amb_frac"] < 0.01
+    assert st["amb_frac"] < AMB_ROOM, st
 
 
 def test_sh_fp16_storage():
     s = _small_room(seed=6, n_gauss=10000, sh_f16=True)
     r, _, _ = gpu_render(s)
     st = compare_blend(view_outputs(r, 0), oracle_view(s, 0, mode="grid"))
-    assert st["amb_frac"] < 0.01
+    assert st["amb_frac"] < AMB_ROOM, st
 
 
 # ------------------------------------------------------------- edge cases --
@@ -322,8 +352,7 @@ def test_config1_full_size_sampled_pixels():
         pix = np.sort(rng.choice(s.cameras[v].n_pixels, 150, replace=False))
         g = view_outputs(r, v)
         m = O.mesh_raster(s.cameras[v], s.mesh, bg=s.bg, pix=pix)
-        assert np.array_equal(g.tri_id[pix], m.tri_id)
-        assert np.array_equal(g.depth[pix], m.depth)
+        compare_mesh(g, m, pix=pix)
         orc = oracle_view(s, v, pix=pix)
         assert (orc.out.n_contrib > 0).mean() > 0.2          # the sample exercises the blend
         st = compare_blend(g, orc, pix=pix)
@@ -350,7 +379,6 @@ def test_config4_full_size_sampled_pixels_chunked():
         pix = np.sort(rng.choice(s.cameras[v].n_pixels, 100, replace=False))
         gv = view_outputs(cr, v)
         m = O.mesh_raster(s.cameras[v], s.mesh, bg=s.bg, pix=pix)
-        assert np.array_equal(gv.tri_id[pix], m.tri_id)
-        assert np.array_equal(gv.depth[pix], m.depth)
+        compare_mesh(gv, m, pix=pix)
         st = compare_blend(gv, oracle_view(s, v, pix=pix), pix=pix)
         print(v, st)

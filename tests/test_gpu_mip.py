@@ -16,7 +16,7 @@ from oracle import oracle as O
 from oracle import torch_ref as TR
 from paper_2506_06988_b300 import scenes
 
-from gpu_util import EPS, check_grad, compare_blend, gaussians_to_torch, make_renderer, records_np, view_outputs  # noqa: E402,E501
+from gpu_util import check_grad, compare_blend, gaussians_to_torch, make_renderer, records_np, view_outputs  # noqa: E402,E501
 
 pytestmark = pytest.mark.gpu
 
@@ -94,7 +94,7 @@ def test_mip_hybrid_render_config0(tile):
     r, _, _ = _mip_render(s, v32, tile=tile)
     orc = O.render(s, 0, filt3d=v64, kernel2d=0.1, antialias=True)
     st = compare_blend(view_outputs(r, 0), orc)
-    assert st["amb_frac"] < 0.01, st
+    assert st["amb_frac"] < 2e-3, st
 
 
 def test_mip_backward_matches_gradient_oracle():
@@ -107,7 +107,7 @@ def test_mip_backward_matches_gradient_oracle():
     gI = rng.standard_normal((3, npx))
     gT = rng.standard_normal(npx)
     orc = O.render(s, **flt)
-    amb = orc.out.margin < EPS
+    amb = orc.out.amb
     gI[:, amb] = 0.0
     gT[amb] = 0.0
     _, ref = TR.render_grad(s, 0, gI, gT, tex=O.texture_unit(s.mesh.texture), **flt)
