@@ -382,7 +382,8 @@ void or_sh_basis(int deg, const double *d, double *Y) {
 
 /*
  * Per Gaussian i:
- *   visible[i]   1 iff the FP32 depth key z > 0.2 and det(Sigma') > 0
+ *   visible[i]   1 iff the FP32 depth key z > 0.2, det(Sigma') > 0 and every
+ *                parameter (opacity if given) and the colour are finite
  *   depth[i]     FP32 depth key (defined for every Gaussian)
  *   mean2d[2i..] projected mean in pixels (continuous coordinates)
  *   cov2d[3i..]  Sigma' (xx, xy, yy) including the screen-space kernel
@@ -404,7 +405,8 @@ void or_sh_basis(int deg, const double *d, double *Y) {
  *     kernel2d I)) (0 where det Sigma2D <= 0).
  */
 void or_project(const double *cam, int W, int H, int n, const double *means, const double *scales,
-                const double *quats, const double *sh, int sh_degree, const double *filt3d,
+                const double *quats, const double *opacity, const double *sh, int sh_degree,
+                const double *filt3d,
                 double kernel2d, int antialias, int *visible, float *depth, double *mean2d,
                 double *cov2d, double *conic, double *color, int *clamped, double *opac_scale) {
     const double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
@@ -425,6 +427,18 @@ void or_project(const double *cam, int W, int H, int n, const double *means, con
         for (int k = 0; k < 3; k++) cov2d[3 * i + k] = conic[3 * i + k] = color[3 * i + k] = 0, clamped[3 * i + k] = 0;
         opac_scale[i] = 1.0;
         if (!(zf > 0.2f)) continue;
+        /* reading (the paper does not define them): a Gaussian with a
+         * non-finite mean, scale, quaternion, opacity or 3D-filter variance,
+         * or a zero quaternion, is culled like one behind the near plane */
+        {
+            const double *qq = quats + 4 * (int64_t)i, *ss = scales + 3 * (int64_t)i;
+            int fin = isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && (!opacity || isfinite(opacity[i]));
+            for (int k = 0; k < 3; k++) fin = fin && isfinite(ss[k]);
+            for (int k = 0; k < 4; k++) fin = fin && isfinite(qq[k]);
+            fin = fin && (qq[0] != 0 || qq[1] != 0 || qq[2] != 0 || qq[3] != 0);
+            if (filt3d) fin = fin && isfinite(filt3d[i]);
+            if (!fin) continue;
+        }
         /* rotation from the normalised quaternion (w,x,y,z) */
         const double *q = quats + 4 * (int64_t)i;
         double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -494,6 +508,7 @@ void or_project(const double *cam, int W, int H, int n, const double *means, con
             for (int k = 0; k < K; k++) acc += Y[k] * sh[((int64_t)i * K + k) * 3 + ch];
             clamped[3 * i + ch] = acc < 0;
             color[3 * i + ch] = acc < 0 ? 0 : acc;
+            if (!isfinite(acc)) visible[i] = 0;       /* non-finite SH: culled (same reading) */
         }
     }
 }

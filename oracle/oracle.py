@@ -165,7 +165,8 @@ def project(cam, g, W=None, H=None, filt3d=None, kernel2d=0.3, antialias=False):
     col = np.empty((n, 3))
     clamped = np.empty((n, 3), np.int32)
     osc = np.empty(n)
-    lib().or_project(_p(c), W, H, n, _p(means), _p(scales), _p(quats), _p(sh), int(g.sh_degree),
+    op = _d(g.opacity) if getattr(g, "opacity", None) is not None else None
+    lib().or_project(_p(c), W, H, n, _p(means), _p(scales), _p(quats), _p(op) if op is not None else None, _p(sh), int(g.sh_degree),
                      _p(f3) if f3 is not None else None, ctypes.c_double(kernel2d), int(bool(antialias)),
                      _p(vis), _p(dep), _p(m2), _p(cov), _p(con), _p(col), _p(clamped), _p(osc))
     return SimpleNamespace(visible=vis, depth=dep, mean2d=m2, cov2d=cov, conic=con, color=col,

@@ -97,6 +97,12 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
     // Mip-Splatting's 3D smoothing filter: R S^2 R^T + v I = R (S^2 + v I) R^T,
     // opacity scaled by prod_k s_k / sqrt(s_k^2 + v)
     const float v3 = flt.f3d ? flt.f3d[i] : 0.f;
+    // a Gaussian with a non-finite parameter, a zero quaternion or a
+    // non-finite colour is culled (empty tile range, in no list)
+    bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) && isfinite(s1) &&
+                  isfinite(s2) && isfinite(q4.x) && isfinite(q4.y) && isfinite(q4.z) && isfinite(q4.w) &&
+                  isfinite(op) && isfinite(v3) &&
+                  (q4.x != 0.f || q4.y != 0.f || q4.z != 0.f || q4.w != 0.f);
     if (v3 > 0.f) {
         const float e0 = sqrtf(fmaf(s0, s0, v3)), e1 = sqrtf(fmaf(s1, s1, v3)), e2 = sqrtf(fmaf(s2, s2, v3));
         op *= (s0 / e0) * (s1 / e1) * (s2 / e2);
@@ -142,7 +148,7 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
         r.a = make_float4(0.f, 0.f, 0.f, 0.f);
         r.b = make_float4(0.f, op, zf, __uint_as_float(kEmptyRange));
         r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(kEmptyRange));
-        if (zf > near_z) {
+        if (zf > near_z && finite) {
             float xh, xl, yh, yl, zh, zl;
             dot3t_ff(&V.R[0], V.t[0], mx, my, mz, xh, xl);
             dot3t_ff(&V.R[3], V.t[1], mx, my, mz, yh, yl);
@@ -206,13 +212,16 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
             float Y[K];
             sh_basis<DEG>(d0, d1, d2, Y);
             float col[3];
+            bool col_ok = true;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 float acc = 0.5f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
+                col_ok = col_ok && isfinite(acc);
                 col[ch] = fmaxf(acc, 0.f);
             }
+            if (!col_ok) xr = yr = kEmptyRange;
             // conic (c, -B, a) / det, pre-multiplied by K (and 2K for xy)
             r.a = make_float4(u, w, __fmul_rn(kConicScale, c * rd), __fmul_rn(2.f * kConicScale, -B * rd));
             r.b = make_float4(__fmul_rn(kConicScale, a * rd), opv, zf, __uint_as_float(xr));

@@ -360,6 +360,45 @@ def test_band_flags_a_gaussian_at_the_mesh_depth():
         assert not out.amb[0] and out.n_contrib[0] == 0 and out.T[0] == 1.0
 
 
+def _poison(g, rng, k=12):
+    """Copy of g with k Gaussians' parameters made non-finite (NaN or +-Inf
+    in the mean, scale, quaternion, opacity or SH) or the quaternion zero."""
+    import copy
+    h = copy.deepcopy(g)
+    idx = rng.choice(g.n, k, replace=False)
+    kinds = ["mean", "scale", "quat", "opacity", "sh", "zeroquat"]
+    for j, i in enumerate(idx):
+        bad = [np.nan, np.inf, -np.inf][j % 3]
+        kind = kinds[j % len(kinds)]
+        if kind == "mean":
+            h.means[i, j % 3] = bad
+        elif kind == "scale":
+            h.scales[i, j % 3] = bad
+        elif kind == "quat":
+            h.quats[i, j % 4] = bad
+        elif kind == "opacity":
+            h.opacity[i] = bad
+        elif kind == "sh":
+            h.sh[i, 0, j % 3] = bad
+        else:
+            h.quats[i] = 0.0
+    return h, np.sort(idx)
+
+
+def test_non_finite_gaussians_are_culled():
+    """Reading: a Gaussian with a non-finite parameter (or a zero
+    quaternion) takes no part in the render -- the image, T and counts are
+    bit-identical to the render without it."""
+    s = scenes.config0_scene()
+    bad_g, idx = _poison(s.gaussians, np.random.default_rng(5))
+    keep = np.setdiff1d(np.arange(s.gaussians.n), idx)
+    a = O.render(s, gaussians=bad_g)
+    assert not a.proj.visible[idx].any()
+    b = O.render(s, gaussians=s.gaussians.subset(keep))
+    for k in ("rgb", "T", "n_contrib"):
+        assert np.array_equal(getattr(a.out, k), getattr(b.out, k)), k
+
+
 # ------------------------------------------------------------ projection --
 
 def test_projected_covariance_closed_form():
