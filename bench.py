@@ -36,11 +36,23 @@ METRIC = "hybrid render frames/s & Mpixel/s at 1080p (fwd, fwd+bwd) and % of roo
 UNIT = "frames/s"
 WORKLOAD = ("indoor room 1920x1080 x 8 poses, 300k Gaussians SH3, 50k-triangle room mesh "
             "(10% pruned), 2048^2 RGB8 atlas; forward + backward")
-# FP32 work per evaluated (pixel, Gaussian) pair in the blend: the quadratic
-# form (2 sub, 2 mul, 2 fma), alpha (mul, min, 2 compares), T update (fma,
-# compare), weight (mul), colour (3 fma), counting an FMA as 2 FLOPs
-FLOPS_PER_EVAL = 26
-FLOPS_PER_EVAL_BWD = 70
+# Work of the blend kernels per (pixel, Gaussian) pair, two counts:
+# * the survey's count of the method's arithmetic per evaluated pair (inside
+#   the 3-sigma ellipse): ~12 FP32 operations + 1 ex2 forward, ~40 + 1 ex2
+#   backward, counted as FLOPs against the FP32 peak (an FMA as two);
+# * the count read off the kernel sources (per evaluated pair forward, per
+#   blended pair backward; an FMA as two, packed FP32x2 ops per pixel):
+#   forward q 7 (dx, a dx^2 and 2b dx shared by the pixel pair), the 3-sigma,
+#   alpha and T-stop compares 3, alpha 2 (o 2^q, min), T' 2, the alpha
+#   select 1, weight 1, colour 6, T 2, mesh cut 1 = 25; backward q 6 (the
+#   column part shared by four pixels), the 3-sigma and alpha compares 2,
+#   alpha 2, the alpha select 1, 1 - alpha 1, T_i 2, weight 1, colour
+#   partials 3, dL/dalpha 11 (c - B, the dot with dL/dI, the T term) and its
+#   select 1, the clamp test 2, dL/dq 2, the moments 3, the per-pair sums
+#   and their accumulation 7, the colour behind 9, the entry's share of the
+#   moment products and of the warp reduction 4 = 58 (+ ex2 and rcp).
+SURVEY_FLOPS = {"blend_forward": 12, "blend_backward": 40}
+SOURCE_FLOPS = {"blend_forward": 25, "blend_backward": 58}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # `ncu --set full` capture of this workload (8 views, 16x16 tiles), with the
 # sources the kernel was built from: a figure is reported only while those
@@ -57,6 +69,10 @@ NCU_TRAFFIC = {
     "blend_forward": (651_455_744, "2887610f3b398375"),
     "blend_backward": (566_773_248, "d5751a32ff776980"),
 }
+# warp instructions per launch (smsp__inst_executed.sum) of the same kind of
+# capture, for the issue-slot roofline of the ALU-bound blend kernels (same
+# source-hash rule as NCU_TRAFFIC; scaled from the capture's views to 8)
+NCU_INST = {}
 
 
 def _traffic(stage, views, tile):
@@ -71,6 +87,23 @@ def _traffic(stage, views, tile):
             h.update(fh.read())
     nbytes, digest = NCU_TRAFFIC[stage]
     return nbytes if h.hexdigest()[:16] == digest else None
+
+
+def _source_hash(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[stage]:
+        with open(os.path.join(ROOT, "paper_2506_06988_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _warp_inst(stage, views, tile):
+    """Warp instructions per launch from the committed capture, or None."""
+    if stage not in NCU_INST or tuple(tile) != (16, 16):
+        return None
+    inst, cap_views, digest = NCU_INST[stage]
+    return inst * views / cap_views if _source_hash(stage) == digest else None
 
 
 KERNELS_PER_STEP = {"rasterize_mesh": 6, "project": 1, "bin_sort": 8, "blend_forward": 1,
@@ -436,22 +469,37 @@ def run_ours(args):
     K = (g.sh_degree + 1) ** 2
     # per single-kernel stage: (kernel, bound, algorithmic units, work per unit)
     kern = {
-        "blend_forward": ("blend_fwd_kernel" + tsuf, "alu", n_eval, FLOPS_PER_EVAL, "evaluated (pixel, Gaussian) pairs"),
+        "blend_forward": ("blend_fwd_kernel" + tsuf, "alu", n_eval, SURVEY_FLOPS["blend_forward"],
+                          "evaluated (pixel, Gaussian) pairs (inside 3 sigma), survey count"),
         "blend_backward": ("blend_bwd_kernel" + tsuf[:-1] + (",2>" if tuple(tile) == (16, 16) else ",1>"), "alu",
-                           n_blended, FLOPS_PER_EVAL_BWD, "replayed blended pairs"),
+                           n_eval, SURVEY_FLOPS["blend_backward"],
+                           "evaluated (pixel, Gaussian) pairs (inside 3 sigma), survey count"),
         "project": ("project_kernel<3,false>", "hbm", N, 12 + 12 + 16 + 4 + 12 * K + V * 48, "Gaussians (params read + V records written, bytes)"),
         "project_backward": ("project_bwd_kernel<3,false>", "hbm", N, 2 * (12 + 12 + 16 + 4 + 12 * K) + 12 + 12 + 16 + 4 + 12 * K + V * 36,
                              "Gaussians (params read, grads read+written, V partial rows read, bytes)"),
         "texture_backward": ("texture_bwd_kernel", "hbm", n_mesh_px, 4 + 4 + 8 + 12, "mesh pixels (depth, T, uv, dL/dI read, bytes)"),
     }
     per_kernel = {}
+    issue_peak = nsm * 4 * sm_max * 1e6 / 1e9          # warp instructions / s (G), one per SMSP per clock
     for st_name, (kname, bound, units, per, what) in kern.items():
         t = stage_ms[st_name] * 1e-3
         if bound == "alu":
             ach = units * per / t / 1e12
+            src_units = n_eval if st_name == "blend_forward" else n_blended
+            src = src_units * SOURCE_FLOPS[st_name] / t / 1e12
             per_kernel[st_name] = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": fp32_peak,
                                    "unit": "TFLOP/s", "frac": ach / fp32_peak, "units": units,
-                                   "per_unit": per, "unit_kind": what, "ms": stage_ms[st_name]}
+                                   "per_unit": per, "unit_kind": what, "ms": stage_ms[st_name],
+                                   "source_count": {"per_unit": SOURCE_FLOPS[st_name], "units": src_units,
+                                                    "unit_kind": ("evaluated pairs" if st_name == "blend_forward"
+                                                                  else "blended pairs"),
+                                                    "achieved": src, "frac": src / fp32_peak}}
+            wi = _warp_inst(st_name, V, tile)
+            per_kernel[st_name]["issue"] = (
+                {"warp_inst_per_launch": wi, "achieved_ginst_s": wi / t / 1e9, "peak_ginst_s": issue_peak,
+                 "frac": wi / t / 1e9 / issue_peak,
+                 "thread_inst_per_blended_pair": wi * 32 / max(n_blended, 1)}
+                if wi is not None else None)
         else:
             ach = units * per / t / 1e9
             per_kernel[st_name] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm,
@@ -569,6 +617,50 @@ def _time_replays(gs, steps, flush, stream, dist):
     return _max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dist)
 
 
+STAGES = ["rasterize_mesh", "project", "bin_sort", "blend_forward", "zero_grads",
+          "texture_backward", "blend_backward", "project_backward"]
+
+
+def _eager_stage_ms(r, PM, mesh, dI, grads, flush, stream, steps):
+    """Mean ms of each stage of a forward+backward frame launched stage by
+    stage with CUDA events between the stages (L2 flushed between frames)."""
+    import torch
+    from paper_2506_06988_b300 import lib
+
+    def step(ev=None):
+        def mark(j):
+            if ev is not None:
+                ev[j].record(stream)
+        mark(0)
+        r.status_word.zero_()
+        if r.has_mesh:
+            r.rasterize_mesh(mesh)
+        mark(1)
+        r.project(*PM)
+        mark(2)
+        r.bin_sort()
+        mark(3)
+        r.blend()
+        mark(4)
+        for v in grads.values():
+            v.zero_()
+        mark(5)
+        for j, stg in ((6, lib.HM_BWD_TEXTURE), (7, lib.HM_BWD_BLEND), (8, lib.HM_BWD_PROJECT)):
+            r.backward(*PM, dI, None, mesh=mesh, tex_grad=True, out=grads, stages=stg, zero=False)
+            mark(j)
+
+    for _ in range(2):
+        step()
+        flush.fill_(1.0)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(steps)]
+    for k in range(steps):
+        step(events[k])
+        flush.fill_(float(k))
+    torch.cuda.synchronize()
+    t = np.array([[events[k][j].elapsed_time(events[k][j + 1]) for j in range(8)] for k in range(steps)])
+    return {n: float(t[:, j].mean()) for j, n in enumerate(STAGES)}
+
+
 def run_batched16(args, dev, dist):
     """16 cameras of uneven resolution (4 each at 640x480, 1024x768, 1296x968,
     1920x1080) of a room with 1M Gaussians (SH degree 3 stored as FP16,
@@ -604,14 +696,31 @@ def run_batched16(args, dev, dist):
     st, npairs, _ = r.status()
     if st:
         raise RuntimeError(f"device status {st} in the batched replays")
+    # both launch modes of the blend kernels at the tuned tile and batch: the
+    # graph replay and the stage breakdown of an eager frame
+    launches = {}
+    grads = r.grad_buffers(scene.mesh.texture.shape[:2])
+    for pers in (False, True):
+        r.opt.persistent = int(pers)
+        gsl = GraphStep(r, P, mesh, dL_drgb=dI, tex_grad=True)
+        for _ in range(3):
+            gsl.replay()
+            flush.fill_(1.0)
+        launches["persistent" if pers else "grid"] = {
+            "ms_per_step": _time_replays(gsl, steps, flush, stream, dist),
+            "stage_ms": _eager_stage_ms(r, P, mesh, dI, grads, flush, stream, max(3, steps // 3))}
+        del gsl
+    r.opt.persistent = int(res.persistent)
     V = len(scene.cameras)
     out = {"workload": "16 views of uneven resolution (4 x 640x480, 4 x 1024x768, 4 x 1296x968, "
                        "4 x 1920x1080), room with 1M Gaussians SH3 stored FP16, 200k triangles (10% pruned), "
                        "4096^2 RGB8 atlas; forward+backward with texel gradients, one CUDA graph per step",
            "frames_per_s": V * 1e3 / ms, "mpixel_per_s": npix * 1e3 / ms / 1e6, "ms_per_step": ms,
            "views": V, "pixels": npix, "gaussians": g.n, "faces": len(scene.mesh.faces), "pairs": npairs,
-           "tile": list(res.tile), "batch": res.batch, "steps": steps,
-           "autotune": {"seconds": tune_s, "ms_per_frame": [[list(t), b, m] for t, b, m in res.table]}}
+           "tile": list(res.tile), "batch": res.batch, "persistent": res.persistent, "steps": steps,
+           "launches": launches,
+           "autotune": {"seconds": tune_s,
+                        "ms_per_frame": [[list(t), b, "persistent" if p else "grid", m] for t, b, p, m in res.table]}}
     del gs, r, res
     torch.cuda.empty_cache()
     return out

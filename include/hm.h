@@ -98,6 +98,10 @@ typedef struct hm_options {
                                 3DGS dilation, 0.1 the 2D Mip filter of Mip-Splatting */
     int32_t antialias;       /* 1: scale each opacity by sqrt(det Sigma2D / det(Sigma2D +
                                 kernel_2d I)) (Mip-Splatting's 2D Mip filter) */
+    int32_t persistent;      /* 1: the blend kernels run as one persistent grid of resident
+                                CTAs that claim (view, tile) work items of all cameras from
+                                a counter (hm_blend_forward's `work`, the backward's
+                                workspace); 0: one CTA per tile.  Same results. */
 } hm_options;
 
 /* hm_blend_backward parts.  HM_BWD_PROJECT consumes the per-record partials
@@ -121,11 +125,14 @@ const char *hm_last_error(void);
  * Per pixel: the nearest covering triangle (two-sided; vertices projected in
  * FP64, snapped to 1/256 px, exact integer edge functions, top-left fill
  * rule; faces with a vertex at z <= near_mesh or beyond +-2^21 px culled),
- * its view depth z = 1 / fma(a, U, fma(b, V, 1/z0)) in FP32, where 1/z is
- * affine in screen space, (U,V) is the pixel centre minus the snapped vertex
- * 0 in pixels and a, b, 1/z0 are the face's coefficients computed in FP64
- * and rounded once to FP32 (nearest FP32 depth wins, ties to the lower face
- * index), perspective-correct UVs and a bilinear,
+ * its view depth D_m (the view z of the snapped face at the pixel centre).
+ * 1/z is affine in screen space; it is evaluated in FP32 as
+ * fma(a, U, fma(b, V, 1/z0)), (U,V) the pixel centre minus the snapped
+ * vertex 0 in pixels and a, b, 1/z0 the face's coefficients computed in
+ * FP64 and rounded once to FP32; the largest FP32 1/z wins (ties to the
+ * lower face index) and D_m is its FP32 reciprocal -- within a few FP32
+ * ulps of the FP64 depth (the band is 3 + 3 kappa ulps, kappa the condition
+ * number of that evaluation); perspective-correct UVs and a bilinear,
  * clamp-to-edge texture fetch (texel centres at half-integers, row 0 at v=0).
  *
  *  verts [n_verts][3], uvs [n_verts][2] float32; faces [n_faces][3] int32.
@@ -227,6 +234,9 @@ hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t n, const v
  *  of (pixel, Gaussian) pairs whose alpha was evaluated (inside the 3-sigma
  *  ellipse, before the pixel stopped) and [1] += the list entries examined.
  *  d_status (device int32, may be NULL): HM_DEV_TIMEOUT / HM_DEV_BAD_INDEX.
+ *  work (device uint32, 4-byte aligned): the tile counter of the persistent
+ *  launch (opt->persistent = 1; zeroed by the call, so concurrent calls need
+ *  their own); may be NULL otherwise.
  *  Records are staged into shared memory by bulk asynchronous copies (TMA),
  *  opt->batch list entries per round, double buffered.
  */
@@ -234,7 +244,8 @@ hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, int32_t n, co
                            const uint32_t *pair_vals, const uint32_t *tile_ranges,
                            const float *mesh_depth, const float *mesh_rgb, const hm_options *opt,
                            float *out_rgb, float *out_T, uint32_t *n_contrib, uint32_t *last_idx,
-                           unsigned long long *eval_stats, int32_t *d_status, void *stream);
+                           unsigned long long *eval_stats, int32_t *d_status, uint32_t *work,
+                           void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* hm_blend_backward -- gradients of a loss L through hm_blend_forward and
@@ -278,16 +289,20 @@ hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, c
  * runtime), or a real-time loop that must not allocate.  The paper has no
  * counterpart; it is a convenience of this library.
  *
- * Same arguments and results as hm_blend_backward, without ws/ws_bytes: the
- * scratch is a library-owned static device array of HM_BWD_NOALLOC_BYTES
- * bytes (16 MiB), which every GPU that loads the library holds until the
- * process exits.  Problems needing more (9 floats per record: n_views * n
- * above 466,026) are rejected with HM_ERR_INVALID_ARG and a message.  The
- * first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
- * call shares the one array, which keeps the last call's contents (the call
- * clears what it needs): calls that overlap on the GPU -- on two streams, or
- * a HM_BWD_PROJECT-only call after another call's HM_BWD_BLEND -- race and
+ * Same arguments (dL_dmesh included) and results as hm_blend_backward,
+ * without ws/ws_bytes: the scratch is a library-owned static device array of
+ * HM_BWD_NOALLOC_BYTES bytes (16 MiB), which every GPU that loads the library
+ * holds until the process exits.  Problems needing more (9 floats per
+ * record: n_views * n above 466,026) are rejected with HM_ERR_INVALID_ARG and
+ * a message.  The array's device address belongs to the current context: a
+ * call outside a stream capture looks it up again (with the caller's device
+ * current), a call under capture uses the address the last uncaptured call
+ * on that device found.  So the first call on a device -- and the first
+ * after a context reset (cudaDeviceReset) -- must come before any stream
+ * capture; otherwise the call returns HM_ERR_INVALID_ARG.  Every call shares
+ * the one array, which keeps the last call's contents (the call clears what
+ * it needs): calls that overlap on the GPU -- on two streams, or a
+ * HM_BWD_PROJECT-only call after another call's HM_BWD_BLEND -- race and
  * give wrong gradients.  No allocation happens in this call. */
 #define HM_BWD_NOALLOC_BYTES (16u << 20)
 hm_status hm_blend_backward_noalloc(const hm_camera *cams, int32_t n_views, int32_t n,
@@ -299,9 +314,9 @@ hm_status hm_blend_backward_noalloc(const hm_camera *cams, int32_t n_views, int3
                                     const float *mesh_uv, int32_t tex_w, int32_t tex_h,
                                     const hm_options *opt, const float *out_T,
                                     const uint32_t *last_idx, const float *dL_drgb,
-                                    const float *dL_dT, float *d_means, float *d_scales,
-                                    float *d_quats, float *d_opacity, float *d_sh, float *d_tex,
-                                    int32_t *d_status, void *stream);
+                                    const float *dL_dT, const float *dL_dmesh, float *d_means,
+                                    float *d_scales, float *d_quats, float *d_opacity, float *d_sh,
+                                    float *d_tex, int32_t *d_status, void *stream);
 
 /* Number of tiles of all cameras for the tile shape in `opt`. */
 int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const hm_options *opt);

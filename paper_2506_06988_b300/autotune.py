@@ -1,4 +1,4 @@
-"""Tile-shape and staging-batch autotuner for the renderer.
+"""Tile-shape, staging-batch and launch-mode autotuner for the renderer.
 
 The image does not depend on either choice (the 3-sigma test is per pixel,
 so the per-pixel candidate set is the same for every tile shape, and the
@@ -6,8 +6,10 @@ staging batch only changes how the depth-sorted list is walked), but the
 cost does: small tiles duplicate more (Gaussian, tile) pairs in the sort,
 large tiles make more pixels walk entries that miss them, and the batch
 trades shared-memory rounds against entries staged past a tile's early
-exit.  ``tune`` times the whole frame (forward, and backward when an
-upstream gradient is given) for every valid (tile, batch) pair on the
+exit.  The launch mode (one CTA per tile, or a persistent grid of resident
+CTAs claiming (view, tile) work from a counter) does not change the result
+either.  ``tune`` times the whole frame (forward, and backward when an
+upstream gradient is given) for every valid (tile, batch, launch) on the
 caller's own cameras and scene, with CUDA events on the current stream, and
 returns the fastest with its renderer ready to use.
 """
@@ -20,10 +22,11 @@ import torch
 
 from .render import MeshInput, Renderer
 
-__all__ = ["TILES", "BATCHES", "TuneResult", "tune"]
+__all__ = ["TILES", "BATCHES", "LAUNCHES", "TuneResult", "tune"]
 
 TILES = ((16, 16), (32, 8), (8, 8))
 BATCHES = (32, 64, 128, None)          # None: one tile's worth of pixels
+LAUNCHES = (False, True)               # persistent work-queue launch of the blend kernels
 
 
 @dataclass
@@ -32,7 +35,8 @@ class TuneResult:
     batch: int
     ms: float
     renderer: Renderer
-    table: list = field(default_factory=list)   # (tile, batch, ms per frame)
+    table: list = field(default_factory=list)   # (tile, batch, persistent, ms per frame)
+    persistent: bool = False
 
 
 def _time_frames(r: Renderer, params, mesh, dI, grads, tex_grad, warmup, iters):
@@ -55,9 +59,9 @@ def _time_frames(r: Renderer, params, mesh, dI, grads, tex_grad, warmup, iters):
 
 def tune(cams, n: int, sh_degree: int, params, mesh: Optional[MeshInput] = None, *,
          dL_drgb: Optional[torch.Tensor] = None, tex_grad: bool = False,
-         tiles: Sequence = TILES, batches: Sequence = BATCHES, warmup: int = 2, iters: int = 5,
-         **renderer_kw) -> TuneResult:
-    """Time every valid (tile, batch) and return the fastest.
+         tiles: Sequence = TILES, batches: Sequence = BATCHES, launches: Sequence = LAUNCHES,
+         warmup: int = 2, iters: int = 5, **renderer_kw) -> TuneResult:
+    """Time every valid (tile, batch, launch) and return the fastest.
 
     ``params`` = (means, scales, quats, opacity, sh) on the device; the
     remaining keyword arguments go to ``Renderer`` (sh_f16, n_verts, n_faces,
@@ -79,12 +83,14 @@ def tune(cams, n: int, sh_degree: int, params, mesh: Optional[MeshInput] = None,
                 continue
             tried.add(bb)
             r.opt.batch = bb
-            ms = _time_frames(r, params, mesh, dL_drgb, grads, tex_grad, warmup, iters)
-            table.append((tuple(tile), bb, ms))
-            if best is None or ms < best[2]:
-                best = (tuple(tile), bb, ms)
+            for pers in launches:
+                r.opt.persistent = int(bool(pers))
+                ms = _time_frames(r, params, mesh, dL_drgb, grads, tex_grad, warmup, iters)
+                table.append((tuple(tile), bb, bool(pers), ms))
+                if best is None or ms < best[3]:
+                    best = (tuple(tile), bb, bool(pers), ms)
         del r, grads
-    tile, batch, ms = best
-    r = Renderer(cams, n, sh_degree, tile=tile, batch=batch, **renderer_kw)
+    tile, batch, pers, ms = best
+    r = Renderer(cams, n, sh_degree, tile=tile, batch=batch, persistent=pers, **renderer_kw)
     r.render(*params, mesh)
-    return TuneResult(tile=tile, batch=batch, ms=ms, renderer=r, table=table)
+    return TuneResult(tile=tile, batch=batch, ms=ms, renderer=r, table=table, persistent=pers)

@@ -75,23 +75,20 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
 // PP = 2 a thread holds two pairs of one column: the column part of q and
 // the warp reduction of the nine partials are shared by four pixels.  The
 // staged records live in dynamic shared memory sized by the batch.
+// One tile's replay.  ph[b] counts the phases of barrier b completed before
+// this tile (the wait parity of round r is (ph[r & 1] + r / 2) & 1); every
+// round issued here is waited for before the return.  Returns false
+// (block-uniform) after a timed-out wait.
 template <int TW, int TH, int PP>
-__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 12)
-blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
-                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-                 const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2,
-                 const float *__restrict__ out_T, const uint32_t *__restrict__ last_idx,
-                 const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, int batch,
-                 float *__restrict__ g2d, int32_t *__restrict__ d_status) {
+__device__ __forceinline__ bool blend_bwd_tile(
+    const int gt, const ViewTable &vt, const Record *__restrict__ rec, uint32_t n_rec,
+    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+    const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2, const float *__restrict__ out_T,
+    const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
+    const float *__restrict__ dL_dT, int batch, float *__restrict__ g2d, int32_t *__restrict__ d_status,
+    Record *s_rec0, uint32_t *s_item0, uint64_t *s_bar, uint32_t &s_hi, uint32_t *ph) {
     constexpr int NTH = TW * TH / (2 * PP);
     constexpr int PER = (TW * TH + NTH - 1) / NTH;       // staged records per thread and round, at most
-    static_assert(TW % 8 == 0 && TH % (8 * PP) == 0, "tile shape");
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    Record *s_rec0 = reinterpret_cast<Record *>(s_dyn);              // [2][batch]
-    uint32_t *s_item0 = reinterpret_cast<uint32_t *>(s_rec0 + 2 * batch);   // [2][batch]
-    __shared__ uint64_t s_bar[2];
-    __shared__ uint32_t s_hi;
-    const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
     const int local = gt - V.tile_off;
@@ -135,12 +132,7 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         my_hi = max(my_hi, max(la[p], lb[p]));
     }
     const uint32_t begin = ranges[2 * gt];
-    if (t == 0) {
-        s_hi = 0;
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        mbar_fence_init();
-    }
+    if (t == 0) s_hi = 0;
     __syncthreads();
     if (my_hi > 0) atomicMax(&s_hi, my_hi);
     __syncthreads();
@@ -192,20 +184,26 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         gTT[p] = __fmul2_rn(gT[p], Tf[p]);
     }
     bool ok = true;
+    // rounds [consumed, issued) have copies that may still be in flight
+    uint32_t issued = n_rounds > 0 ? 1u : 0u, consumed = 0;
     for (uint32_t r = 0; r < n_rounds; ++r) {
         // ends every thread's use of round r - 1, whose buffers round r + 1
-        // refills, and publishes round r's record indices
-        __syncthreads();
+        // refills, and publishes round r's record indices; after a timed-out
+        // wait anywhere in the CTA nothing more is issued
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
         if (r + 1 < n_rounds) {
             issue(r + 1);
+            issued = r + 2;
             if (r + 2 < n_rounds) load_idx(r + 2);
         }
         const int buf = r & 1;
-        if (!mbar_wait(&s_bar[buf], (r >> 1) & 1)) {
+        if (!mbar_wait(&s_bar[buf], (ph[buf] + (r >> 1)) & 1u)) {
             set_status(d_status, HM_DEV_TIMEOUT);
             ok = false;
         }
         ok = __all_sync(0xffffffffu, ok);   // the replay below uses warp shuffles
+        if (ok) consumed = r + 1;
         uint32_t lo, nb_u;
         round_lo(r, lo, nb_u);
         const int nb = ok ? (int)nb_u : 0;
@@ -225,6 +223,7 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             const float4 A = sr[k].a, Bs = sr[k].b, c = sr[k].c;
             const QCol qc = eval_qcol(A, fpx);
             float2 dy[PP], G[PP], araw[PP], al[PP];
+            bool actp[PP];
             act = false;
 #pragma unroll
             for (int p = 0; p < PP; ++p) {
@@ -234,15 +233,19 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                 al[p] = eval_alpha2(Bs.y, q, G[p], araw[p]);
                 ea[p] = ea[p] && al[p].x >= kAlphaMin;        // the forward blended it
                 eb[p] = eb[p] && al[p].y >= kAlphaMin;
-                act = act || ea[p] || eb[p];
+                // pair p of some lane blended it (warp-uniform)
+                actp[p] = __any_sync(0xffffffffu, ea[p] || eb[p]);
+                act = act || actp[p];
             }
             // entries the forward blended at none of the warp's pixels need no
-            // gradient math and no reduction
-            if (!__any_sync(0xffffffffu, act)) continue;
-            float g[kG];
+            // gradient math and no reduction; within an entry, a pair row no
+            // lane blended is skipped (its updates would be the identity)
+            if (!act) continue;
+            float g[kG] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float sgq = 0.f;
 #pragma unroll
             for (int p = 0; p < PP; ++p) {
+                if (!actp[p]) continue;
                 const float2 ae = make_float2(ea[p] ? al[p].x : 0.f, eb[p] ? al[p].y : 0.f);
                 const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
                 const float2 rr = make_float2(rcp_approx(om.x), rcp_approx(om.y));
@@ -268,13 +271,13 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                 const float2 gqdy = __fmul2_rn(gq, dy[p]);
                 const float2 gqdy2 = __fmul2_rn(gqdy, dy[p]);
                 const float2 pg = __fmul2_rn(dLa_u, G[p]);
-                const float s_gq = gq.x + gq.y, s_dy = gqdy.x + gqdy.y, s_dy2 = gqdy2.x + gqdy2.y,
-                            s_op = pg.x + pg.y, s_r = c0.x + c0.y, s_g = c1.x + c1.y, s_b = c2.x + c2.y;
-                if (p == 0) {
-                    sgq = s_gq; g[1] = s_dy; g[4] = s_dy2; g[5] = s_op; g[6] = s_r; g[7] = s_g; g[8] = s_b;
-                } else {
-                    sgq += s_gq; g[1] += s_dy; g[4] += s_dy2; g[5] += s_op; g[6] += s_r; g[7] += s_g; g[8] += s_b;
-                }
+                sgq += gq.x + gq.y;
+                g[1] += gqdy.x + gqdy.y;
+                g[4] += gqdy2.x + gqdy2.y;
+                g[5] += pg.x + pg.y;
+                g[6] += c0.x + c0.y;
+                g[7] += c1.x + c1.y;
+                g[8] += c2.x + c2.y;
                 // colour behind the previous Gaussian (normalised), then T_i
                 B0[p] = __ffma2_rn(ae, make_float2(c.x, c.x), __fmul2_rn(om, B0[p]));
                 B1[p] = __ffma2_rn(ae, make_float2(c.y, c.y), __fmul2_rn(om, B1[p]));
@@ -293,12 +296,64 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
         }
     }
-    // after a timed-out wait, the copies still in flight must land before
-    // the CTA's shared memory is released (every round was waited for)
+    // after a timed-out wait, every copy issued and not yet waited for must
+    // land (bounded waits) before the buffers are reused or the CTA's shared
+    // memory is released
+    ok = __syncthreads_and(ok);
     if (!ok && t == 0) {
-        for (uint32_t r = n_rounds >= 2 ? n_rounds - 2 : 0; r < n_rounds; ++r) mbar_wait(&s_bar[r & 1], (r >> 1) & 1);
+        for (uint32_t r = consumed; r < issued; ++r) mbar_wait(&s_bar[r & 1], (ph[r & 1] + (r >> 1)) & 1u);
+    }
+    ph[0] += (issued + 1) >> 1;                      // rounds 0, 2, 4, ... used barrier 0
+    ph[1] += issued >> 1;
+    return ok;
+}
+
+// Grid launch (PERSIST false): one CTA per tile.  Persistent launch: a grid
+// of resident CTAs that claim tiles of all views from the counter `work`
+// (zeroed before the launch) until none is left; a claim is one atomic on a
+// counter that only grows, so no CTA waits on another.
+template <int TW, int TH, int PP, bool PERSIST>
+__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 12)
+blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
+                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+                 const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2,
+                 const float *__restrict__ out_T, const uint32_t *__restrict__ last_idx,
+                 const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, int batch,
+                 float *__restrict__ g2d, int32_t *__restrict__ d_status, unsigned int *__restrict__ work) {
+    static_assert(TW % 8 == 0 && TH % (8 * PP) == 0, "tile shape");
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    Record *s_rec0 = reinterpret_cast<Record *>(s_dyn);              // [2][batch]
+    uint32_t *s_item0 = reinterpret_cast<uint32_t *>(s_rec0 + 2 * batch);   // [2][batch]
+    __shared__ uint64_t s_bar[2];
+    __shared__ uint32_t s_hi;
+    __shared__ int s_tile;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
+    uint32_t ph[2] = {0u, 0u};
+    if (!PERSIST) {
+        __syncthreads();                              // barriers initialised
+        blend_bwd_tile<TW, TH, PP>(blockIdx.x, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
+                                   last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
+                                   s_hi, ph);
+        return;
+    }
+    for (;;) {
+        __syncthreads();                              // the previous tile's shared reads are done
+        if (t == 0) s_tile = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int gt = s_tile;
+        if (gt >= vt.total_tiles) return;
+        if (!blend_bwd_tile<TW, TH, PP>(gt, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
+                                        last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
+                                        s_hi, ph))
+            return;                                   // a wait timed out: phases unknown, stop claiming
     }
 }
+
 
 // add (r,g,b) to texel t of a [.][.][3] float array: texel t starts at float
 // 3t, so (r,g) is 8-byte aligned for even t and (g,b) for odd t -- one
@@ -317,10 +372,10 @@ __device__ __forceinline__ void red_texel(float *d_tex, size_t t, float r, float
 // One CTA per screen tile.  Each pixel with a triangle contributes
 // T * w_k * dL/dI_h to the 4 texels of its bilinear footprint.  The tile's
 // taps fall in a small texel box when the tile lies on one chart: they are
-// summed in shared memory (int32 fixed point) and every touched texel is
+// summed in shared memory (per-texel fixed point) and every touched texel is
 // flushed with one global reduction; a tile whose box exceeds kTexCap texels
 // (it straddles charts) reduces straight to global memory.
-constexpr int kTexCap = 1024;
+constexpr int kTexCap = 768;
 
 template <int TW, int TH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX)
@@ -331,9 +386,8 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     // tile's box, scale and flush set-up is shared by PX pixels
     constexpr int NT = TW * TH / PX;
     static_assert(NT % 32 == 0 && TH % PX == 0, "whole warps");
-    __shared__ int s_acc[kTexCap * 3];
+    __shared__ int s_acc[kTexCap * 4];      // per texel: 3 fixed-point sums, then (after them) the largest tap
     __shared__ int s_box[4];
-    __shared__ int s_max[3];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -344,7 +398,7 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     bool act[PX];
     float g0[PX], g1[PX], g2[PX], fx[PX], fy[PX];
     int xa[PX], xb[PX], ya[PX], yb[PX];
-    int mx0 = 0x7fffffff, mx1 = -1, my0 = 0x7fffffff, my1 = -1, m0 = 0, m1 = 0, m2 = 0;
+    int mx0 = 0x7fffffff, mx1 = -1, my0 = 0x7fffffff, my1 = -1;
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
         const int py = (local / V.tiles_x) * TH + (t / TW) + q * (TH / PX);
@@ -374,14 +428,10 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         if (act[q]) {
             mx0 = min(mx0, xa[q]); mx1 = max(mx1, xb[q]);
             my0 = min(my0, ya[q]); my1 = max(my1, yb[q]);
-            m0 = max(m0, __float_as_int(fabsf(g0[q])));
-            m1 = max(m1, __float_as_int(fabsf(g1[q])));
-            m2 = max(m2, __float_as_int(fabsf(g2[q])));
         }
     }
     if (t == 0) {
         s_box[0] = 0x7fffffff; s_box[1] = -1; s_box[2] = 0x7fffffff; s_box[3] = -1;
-        s_max[0] = s_max[1] = s_max[2] = 0;
     }
     __syncthreads();
     {
@@ -389,13 +439,9 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         mx1 = __reduce_max_sync(0xffffffffu, mx1);
         my0 = __reduce_min_sync(0xffffffffu, my0);
         my1 = __reduce_max_sync(0xffffffffu, my1);
-        m0 = __reduce_max_sync(0xffffffffu, m0);
-        m1 = __reduce_max_sync(0xffffffffu, m1);
-        m2 = __reduce_max_sync(0xffffffffu, m2);
         if ((t & 31) == 0 && mx1 >= 0) {
             atomicMin(&s_box[0], mx0); atomicMax(&s_box[1], mx1);
             atomicMin(&s_box[2], my0); atomicMax(&s_box[3], my1);
-            atomicMax(&s_max[0], m0); atomicMax(&s_max[1], m1); atomicMax(&s_max[2], m2);
         }
     }
     __syncthreads();
@@ -416,23 +462,41 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         }
         return;
     }
-    // Fixed point per channel: the tile's largest |T dL/dI| maps to
-    // [2^21, 2^22).  A pixel's taps have weights summing to 1, so a texel
-    // receives at most the tile's pixels' worth (256 at 16x16): |sum| <
-    // 2^30 + 512 (one rounding per tap) fits int32.  Integer shared atomics
-    // are native and the sum is exact; each tap is rounded to 2^-22 of the
-    // tile maximum.
-    float sc[3], isc[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int e = ((s_max[c] >> 23) & 0xff) - 127;
-        const int se = min(max(21 - e, -126), 127);
-        sc[c] = __int_as_float((se + 127) << 23);
-        isc[c] = __int_as_float((127 - se) << 23);
-    }
+    // Per-texel fixed point (native int32 shared atomics, exact and
+    // order-independent sums).  Pass 1 takes, per texel, the largest tap
+    // magnitude M over its three channels (the bits of a non-negative float
+    // order like the float).  Pass 2 adds each tap in units of 2^(e - 19),
+    // 2^e <= M < 2^(e+1): a tap is rounded to at most 2^-20 M, so a texel's
+    // sums carry the rounding of its own taps whatever the tile's other
+    // texels receive.  A pixel sends at most weight 1 to a texel (its taps
+    // coincide only at a clamped edge), so |sum| <= 256 M < 2^28 units at
+    // 16x16.
+    int *mx = s_acc + kTexCap * 3;
     const int ncell = bw * bh;
     for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0;
+    for (int i = t; i < ncell; i += NT) mx[i] = 0;
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PX; ++q) {
+        if (!act[q]) continue;
+        const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
+                            fx[q] * fy[q]};
+        const int xs[4] = {xa[q], xb[q], xa[q], xb[q]}, ys[4] = {ya[q], ya[q], yb[q], yb[q]};
+        const float gm = fmaxf(fabsf(g0[q]), fmaxf(fabsf(g1[q]), fabsf(g2[q])));
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (w[k] != 0.f) atomicMax(mx + (ys[k] - by0) * bw + (xs[k] - bx0), __float_as_int(w[k] * gm));
+    }
+    __syncthreads();
+    // 2^(19 - e) and 2^(e - 19) for the texel whose largest tap has exponent e
+    auto unit_inv = [](int mbits) {
+        const int e = ((mbits >> 23) & 0xff) - 127;
+        return __int_as_float((min(max(19 - e, -126), 127) + 127) << 23);
+    };
+    auto unit = [](int mbits) {
+        const int e = ((mbits >> 23) & 0xff) - 127;
+        return __int_as_float((127 - min(max(19 - e, -126), 127)) << 23);
+    };
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
         if (!act[q]) continue;
@@ -442,18 +506,21 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (w[k] == 0.f) continue;
-            int *a = s_acc + 3 * ((ys[k] - by0) * bw + (xs[k] - bx0));
-            atomicAdd(a, __float2int_rn(w[k] * g0[q] * sc[0]));
-            atomicAdd(a + 1, __float2int_rn(w[k] * g1[q] * sc[1]));
-            atomicAdd(a + 2, __float2int_rn(w[k] * g2[q] * sc[2]));
+            const int c = (ys[k] - by0) * bw + (xs[k] - bx0);
+            const float ui = unit_inv(mx[c]);
+            atomicAdd(s_acc + 3 * c, __float2int_rn(w[k] * g0[q] * ui));
+            atomicAdd(s_acc + 3 * c + 1, __float2int_rn(w[k] * g1[q] * ui));
+            atomicAdd(s_acc + 3 * c + 2, __float2int_rn(w[k] * g2[q] * ui));
         }
     }
     __syncthreads();
     for (int i = t; i < ncell; i += NT) {
         const int r = s_acc[3 * i], gg = s_acc[3 * i + 1], b = s_acc[3 * i + 2];
-        if (r != 0 || gg != 0 || b != 0)
-            red_texel(d_tex, (size_t)(by0 + i / bw) * tw + (bx0 + i % bw), (float)r * isc[0],
-                      (float)gg * isc[1], (float)b * isc[2]);
+        if (r != 0 || gg != 0 || b != 0) {
+            const float u = unit(mx[i]);
+            red_texel(d_tex, (size_t)(by0 + i / bw) * tw + (bx0 + i % bw), (float)r * u, (float)gg * u,
+                      (float)b * u);
+        }
     }
 }
 
@@ -510,6 +577,7 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
 #pragma unroll
     for (int k = 0; k < K * 3; ++k) gsh[k][tl] = 0.f;
     float gop = 0.f;
+    bool touched = false;           // some view blended it
     for (int v = 0; v < vt.n_views; ++v) {
         const float *gg = g2d + ((size_t)v * n + i) * kG;
         float g[kG];
@@ -527,6 +595,7 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
         const ViewDev &V = vt.v[v];
         const float zf = fmaf(V.R[6], mx, fmaf(V.R[7], my, fmaf(V.R[8], mz, V.t[2])));
         if (!(zf > 0.f)) continue;
+        touched = true;
         const float txf = fmaf(V.R[0], mx, fmaf(V.R[1], my, fmaf(V.R[2], mz, V.t[0])));
         const float tyf = fmaf(V.R[3], mx, fmaf(V.R[4], my, fmaf(V.R[5], mz, V.t[1])));
         const float rz = __frcp_rn(zf);
@@ -658,6 +727,9 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
             gmean[2] += (gd[2] - dd * d2) * dinv;
         }
     }
+    // a Gaussian no view blended has no gradient: nothing to add (this also
+    // keeps culled, non-finite parameters out of the chain rule)
+    if (!touched) return;
     // M = R S: dS_k = sum_a dM[a][k] R[a][k], dR[a][k] = dM[a][k] s_k
     float gR[3][3];
     float gs[3] = {0.f, 0.f, 0.f};
@@ -722,6 +794,33 @@ cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const fl
 
 }  // namespace hm
 
+namespace hm {
+namespace {
+
+// resident CTAs of a kernel at a block size and dynamic shared memory, over
+// all SMs (cached per device and batch; the batch sets the shared memory)
+template <typename K>
+int resident_ctas(K kernel, int threads, int smem, int slot) {
+    static int cache[64][3][8] = {};
+    static int cache_smem[64][3][8] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const int b = smem <= 2048 ? 0 : smem <= 8192 ? 1 : smem <= 16384 ? 2 : smem <= 32768 ? 3 : 4;
+    int &c = cache[dev][slot][b];
+    if (c == 0 || cache_smem[dev][slot][b] != smem) {
+        int per_sm = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        c = per_sm * nsm;
+        cache_smem[dev][slot][b] = smem;
+    }
+    return c;
+}
+
+}  // namespace
+}  // namespace hm
+
 using namespace hm;
 
 extern "C" size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n) {
@@ -780,19 +879,35 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (n == 0) return HM_OK;
     float *g2d = reinterpret_cast<float *>(ws);
     const Record *rec = reinterpret_cast<const Record *>(records);
-    dim3 grid(vt.total_tiles);
     if (stages & HM_BWD_BLEND) {
-    e = cudaMemsetAsync(g2d, 0, sizeof(float) * kG * (size_t)n_views * n, s);
+    const size_t g2d_bytes = sizeof(float) * kG * (size_t)n_views * n;
+    // the persistent launch's tile counter sits after the partials (the
+    // workspace's 256 spare bytes)
+    unsigned int *wq = opt->persistent ? reinterpret_cast<unsigned int *>(
+                                             reinterpret_cast<unsigned char *>(ws) + ((g2d_bytes + 15) & ~(size_t)15))
+                                       : nullptr;
+    e = cudaMemsetAsync(g2d, 0, wq ? ((g2d_bytes + 15) & ~(size_t)15) + 16 : g2d_bytes, s);
     if (e != cudaSuccess) return cuda_status(e);
     const uint32_t n_rec = (uint32_t)((long long)n_views * n);
     const size_t bwd_smem = 2 * (size_t)opt->batch * (sizeof(Record) + sizeof(uint32_t));
-#define HM_BBWD(TW, TH, PP)                                                                                    \
-    blend_bwd_kernel<TW, TH, PP><<<grid, TW * TH / (2 * PP), bwd_smem, s>>>(                                  \
-        vt, rec, n_rec, pair_vals, tile_ranges, mesh_rgb, bg[0], bg[1], bg[2], out_T, last_idx, dL_drgb, dL_dT, \
-        opt->batch, g2d, d_status)
-    if (opt->tile_w == 16) HM_BBWD(16, 16, 2);
-    else if (opt->tile_w == 32) HM_BBWD(32, 8, 1);
-    else HM_BBWD(8, 8, 1);
+#define HM_BBWD(TW, TH, PP, SLOT)                                                                                \
+    do {                                                                                                         \
+        auto kern = wq ? blend_bwd_kernel<TW, TH, PP, true> : blend_bwd_kernel<TW, TH, PP, false>;              \
+        int grid = vt.total_tiles;                                                                               \
+        if (wq) {                                                                                                \
+            grid = resident_ctas(kern, TW * TH / (2 * PP), (int)bwd_smem, SLOT);                                 \
+            if (grid <= 0) return fail(HM_ERR_CUDA, "occupancy query failed");                                  \
+            grid = grid < vt.total_tiles ? grid : vt.total_tiles;                                                \
+        }                                                                                                        \
+        kern<<<grid, TW * TH / (2 * PP), bwd_smem, s>>>(                                                          \
+            vt, rec, n_rec, pair_vals, tile_ranges, mesh_rgb, bg[0], bg[1], bg[2], out_T, last_idx, dL_drgb,    \
+            dL_dT, opt->batch, g2d, d_status, wq);                                                               \
+    } while (0)
+    if (vt.total_tiles > 0) {
+        if (opt->tile_w == 16) HM_BBWD(16, 16, 2, 0);
+        else if (opt->tile_w == 32) HM_BBWD(32, 8, 1, 1);
+        else HM_BBWD(8, 8, 1, 2);
+    }
 #undef HM_BBWD
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
@@ -816,21 +931,33 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_bwd_noalloc_scratch[HM_BWD_NOALLOC_BYTES];
 
-// device address of the array per device, looked up once with that device current
+// Device address of the array.  The address belongs to the current context
+// (a cudaDeviceReset, or a library loaded under another context, moves it),
+// so it is looked up again on every call outside a stream capture; a call
+// under capture, where the lookup may not run, uses the address the last
+// uncaptured call on this device found.
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[64] = {};
 
-hm_status noalloc_scratch(void **out) {
+hm_status noalloc_scratch(cudaStream_t stream, void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 0 || dev >= 64) return fail(HM_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cs);
+    const bool capturing = e != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (e != cudaSuccess) (void)cudaGetLastError();      // the query's own error is not the call's
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!capturing) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_bwd_noalloc_scratch);
         if (e != cudaSuccess) return cuda_status(e);
         g_noalloc_ptr[dev] = p;
+    } else if (!g_noalloc_ptr[dev]) {
+        return fail(HM_ERR_INVALID_ARG,
+                    "hm_blend_backward_noalloc: the first call on device %d (after any context "
+                    "reset) must come before a stream capture", dev);
     }
     *out = g_noalloc_ptr[dev];
     return HM_OK;
@@ -845,8 +972,8 @@ extern "C" hm_status hm_blend_backward_noalloc(
     int32_t sh_format, const void *records, const uint32_t *pair_vals, const uint32_t *tile_ranges,
     const float *mesh_depth, const float *mesh_rgb, const float *mesh_uv, int32_t tex_w,
     int32_t tex_h, const hm_options *opt, const float *out_T, const uint32_t *last_idx,
-    const float *dL_drgb, const float *dL_dT, float *d_means, float *d_scales, float *d_quats,
-    float *d_opacity, float *d_sh, float *d_tex, int32_t *d_status, void *stream) {
+    const float *dL_drgb, const float *dL_dT, const float *dL_dmesh, float *d_means, float *d_scales,
+    float *d_quats, float *d_opacity, float *d_sh, float *d_tex, int32_t *d_status, void *stream) {
     if (n_views < 1 || n < 0) return fail(HM_ERR_INVALID_ARG, "bad n_views or n");
     const size_t need = hm_blend_backward_workspace_size(n_views, n);
     if (need > HM_BWD_NOALLOC_BYTES)
@@ -855,11 +982,11 @@ extern "C" hm_status hm_blend_backward_noalloc(
                     "of hm_blend_backward_noalloc; use hm_blend_backward with a workspace",
                     (long long)n_views * n, need, (unsigned)HM_BWD_NOALLOC_BYTES);
     void *ws = nullptr;
-    const hm_status st = noalloc_scratch(&ws);
+    const hm_status st = noalloc_scratch((cudaStream_t)stream, &ws);
     if (st != HM_OK) return st;
     return hm_blend_backward(cams, n_views, n, means, scales, quats, opacity, filter_3d, sh, sh_degree,
                              sh_format, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb,
-                             mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, nullptr,
+                             mesh_uv, tex_w, tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, dL_dmesh,
                              d_means, d_scales, d_quats, d_opacity, d_sh, d_tex, d_status, ws,
                              HM_BWD_NOALLOC_BYTES, stream);
 }

@@ -27,19 +27,21 @@ namespace hm {
 
 namespace {
 
+// One tile: the whole Eq. 2 walk of its pixels.  ph[b] counts the phases of
+// barrier b completed before this tile (the wait parity of round r is
+// (ph[r & 1] + r / 2) & 1); every round issued here is waited for before the
+// return, so the counts stay exact.  Returns false (block-uniform) after a
+// timed-out wait: the barriers' phases are then unknown.
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW *TH / 2, 8)
-blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
-                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-                 const float *__restrict__ mesh_depth, const float *__restrict__ mesh_rgb, float bg0,
-                 float bg1, float bg2, int batch, float *__restrict__ out_rgb,
-                 float *__restrict__ out_T, uint32_t *__restrict__ n_contrib,
-                 uint32_t *__restrict__ last_idx, unsigned long long *__restrict__ eval_stats,
-                 int32_t *__restrict__ d_status) {
+__device__ __forceinline__ bool blend_fwd_tile(
+    const int gt, const ViewTable &vt, const Record *__restrict__ rec, uint32_t n_rec,
+    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+    const float *__restrict__ mesh_depth, const float *__restrict__ mesh_rgb, float bg0, float bg1,
+    float bg2, int batch, float *__restrict__ out_rgb, float *__restrict__ out_T,
+    uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ last_idx,
+    unsigned long long *__restrict__ eval_stats, int32_t *__restrict__ d_status,
+    Record (*s_rec)[TW * TH], uint64_t *s_bar, int &s_timeout, uint32_t *ph) {
     constexpr int NT = TW * TH, NTH = NT / 2;
-    __shared__ Record s_rec[2][NT];
-    __shared__ uint64_t s_bar[2];
-    const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
     const int local = gt - V.tile_off;
@@ -52,11 +54,8 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
     const uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
     const uint32_t n_rounds = end > begin ? (end - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
-    if (t == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        mbar_fence_init();
-    }
+    auto parity = [&](uint32_t r) { return (ph[r & 1] + (r >> 1)) & 1u; };
+    if (t == 0) s_timeout = 0;                        // published by the barrier before the first issue
     // record indices of the next round to issue (entries t and t + NTH)
     uint32_t nxt0 = 0, nxt1 = 0;
     auto load_idx = [&](uint32_t r) {
@@ -98,24 +97,29 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     float2 C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
     uint32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0, n_eval = 0, n_exam = 0;
     uint32_t issued = n_rounds > 0 ? 1u : 0u, consumed = 0;
+    bool all_landed = true;
     for (uint32_t r = 0; r < n_rounds; ++r) {
-        // every pixel has stopped: leave the list.  The barrier also ends
-        // every thread's reads of round r - 1, whose buffer round r + 1 refills.
-        if (__syncthreads_count(done_a && done_b) == NTH) break;
+        // every pixel has stopped, or a wait of the CTA timed out: leave the
+        // list.  The barrier also ends every thread's reads of round r - 1,
+        // whose buffer round r + 1 refills, and publishes s_timeout.
+        if (__syncthreads_count(done_a && done_b) == NTH || s_timeout) break;
         if (r + 1 < n_rounds) {
             issue(r + 1);
             ++issued;
             if (r + 2 < n_rounds) load_idx(r + 2);
         }
         const int buf = r & 1;
-        if (!mbar_wait(&s_bar[buf], (r >> 1) & 1)) {
+        if (mbar_wait(&s_bar[buf], parity(r))) {
+            consumed = r + 1;                        // this thread saw round r land
+        } else {
             set_status(d_status, HM_DEV_TIMEOUT);
+            all_landed = false;
+            s_timeout = 1;
             done_a = done_b = true;
         }
-        consumed = r + 1;
-        if (done_a && done_b) continue;
         const uint32_t b0 = begin + r * (uint32_t)batch;
         const int nb = (int)min((uint32_t)batch, end - b0);
+        if (done_a && done_b) continue;
         const Record *sr = s_rec[buf];
         for (int k = 0; k < nb; ++k) {
             const float4 A = sr[k].a;
@@ -151,12 +155,19 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             if (eb) last_b = b0 + k + 1;
         }
     }
-    // a round issued but never consumed (early exit) must land before the
-    // CTA's shared memory is released
+    // a round issued but not seen landing by thread 0 (early exit, or a
+    // timed-out wait) must land before the buffers are reused or the CTA's
+    // shared memory is released
+    bool drained = true;
     if (t == 0) {
         for (uint32_t r = consumed; r < issued; ++r)
-            if (!mbar_wait(&s_bar[r & 1], (r >> 1) & 1)) set_status(d_status, HM_DEV_TIMEOUT);
+            if (!mbar_wait(&s_bar[r & 1], parity(r))) {
+                set_status(d_status, HM_DEV_TIMEOUT);
+                drained = false;
+            }
     }
+    ph[0] += (issued + 1) >> 1;                      // rounds 0, 2, 4, ... used barrier 0
+    ph[1] += issued >> 1;
     const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
     float *o = out_rgb + 3 * V.pix_off;
     if (in_a) {
@@ -187,9 +198,71 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             atomicAdd(eval_stats + 1, x);
         }
     }
+    return __syncthreads_and(all_landed && drained);
+}
+
+// Grid launch (PERSIST false): one CTA per tile.  Persistent launch: a grid
+// of resident CTAs that claim tiles of all views from the counter `work`
+// (zeroed before the launch) until none is left -- the (view, tile) work
+// queue.  A claim is one atomic on a counter that only grows, so no CTA
+// waits on another.
+template <int TW, int TH, bool COUNT, bool PERSIST>
+__global__ void __launch_bounds__(TW *TH / 2, 8)
+blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
+                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+                 const float *__restrict__ mesh_depth, const float *__restrict__ mesh_rgb, float bg0,
+                 float bg1, float bg2, int batch, float *__restrict__ out_rgb,
+                 float *__restrict__ out_T, uint32_t *__restrict__ n_contrib,
+                 uint32_t *__restrict__ last_idx, unsigned long long *__restrict__ eval_stats,
+                 int32_t *__restrict__ d_status, unsigned int *__restrict__ work) {
+    __shared__ Record s_rec[2][TW * TH];
+    __shared__ uint64_t s_bar[2];
+    __shared__ int s_tile, s_timeout;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
+    }
+    uint32_t ph[2] = {0u, 0u};
+    if (!PERSIST) {
+        __syncthreads();                              // barriers initialised
+        blend_fwd_tile<TW, TH, COUNT>(blockIdx.x, vt, rec, n_rec, vals, ranges, mesh_depth, mesh_rgb, bg0, bg1,
+                                      bg2, batch, out_rgb, out_T, n_contrib, last_idx, eval_stats, d_status,
+                                      s_rec, s_bar, s_timeout, ph);
+        return;
+    }
+    for (;;) {
+        __syncthreads();                              // the previous tile's shared reads are done
+        if (t == 0) s_tile = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int gt = s_tile;
+        if (gt >= vt.total_tiles) return;
+        if (!blend_fwd_tile<TW, TH, COUNT>(gt, vt, rec, n_rec, vals, ranges, mesh_depth, mesh_rgb, bg0, bg1, bg2,
+                                           batch, out_rgb, out_T, n_contrib, last_idx, eval_stats, d_status,
+                                           s_rec, s_bar, s_timeout, ph))
+            return;                                   // a wait timed out: phases unknown, stop claiming
+    }
 }
 
 }  // namespace
+
+// resident CTAs per SM of a kernel at a block size (cached per device)
+template <typename K>
+int resident_ctas(K kernel, int threads, int slot) {
+    static int cache[64][8] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int &c = cache[dev][slot];
+    if (c == 0) {
+        int per_sm = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        c = per_sm * nsm;
+    }
+    return c;
+}
 
 }  // namespace hm
 
@@ -201,7 +274,7 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
                                       const float *mesh_rgb, const hm_options *opt,
                                       float *out_rgb, float *out_T, uint32_t *n_contrib,
                                       uint32_t *last_idx, unsigned long long *eval_stats,
-                                      int32_t *d_status, void *stream) {
+                                      int32_t *d_status, uint32_t *work, void *stream) {
     ViewTable vt;
     if (!build_view_table(cams, n_views, opt, &vt)) return HM_ERR_INVALID_ARG;
     if (n < 0) return fail(HM_ERR_INVALID_ARG, "n < 0");
@@ -211,25 +284,38 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
     if (!tile_ranges || !out_rgb || !out_T || !n_contrib || (n > 0 && (!records || !pair_vals)))
         return fail(HM_ERR_INVALID_ARG, "null pointer");
     if ((uintptr_t)records & 15) return fail(HM_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    if (opt->persistent && (!work || ((uintptr_t)work & 3)))
+        return fail(HM_ERR_INVALID_ARG, "a persistent launch needs a 4-byte aligned work counter");
     cudaStream_t s = (cudaStream_t)stream;
     const Record *rec = reinterpret_cast<const Record *>(records);
-    dim3 grid(vt.total_tiles);
     const float *bg = opt->bg;
-#define HM_BLEND(TW, TH)                                                                              \
+    unsigned int *wq = opt->persistent ? reinterpret_cast<unsigned int *>(work) : nullptr;
+    if (wq) {
+        const cudaError_t e = cudaMemsetAsync(wq, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+#define HM_BLEND(TW, TH, SLOT)                                                                        \
     do {                                                                                              \
-        if (eval_stats)                                                                               \
-            blend_fwd_kernel<TW, TH, true><<<grid, TW * TH / 2, 0, s>>>(                              \
-                vt, rec, n_rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2],     \
-                opt->batch, out_rgb, out_T, n_contrib, last_idx, eval_stats, d_status);               \
-        else                                                                                          \
-            blend_fwd_kernel<TW, TH, false><<<grid, TW * TH / 2, 0, s>>>(                             \
-                vt, rec, n_rec, pair_vals, tile_ranges, mesh_depth, mesh_rgb, bg[0], bg[1], bg[2],     \
-                opt->batch, out_rgb, out_T, n_contrib, last_idx, nullptr, d_status);                  \
+        auto kern = wq ? (eval_stats ? blend_fwd_kernel<TW, TH, true, true>                           \
+                                     : blend_fwd_kernel<TW, TH, false, true>)                         \
+                       : (eval_stats ? blend_fwd_kernel<TW, TH, true, false>                          \
+                                     : blend_fwd_kernel<TW, TH, false, false>);                       \
+        int grid = vt.total_tiles;                                                                    \
+        if (wq) {                                                                                     \
+            grid = resident_ctas(kern, TW * TH / 2, SLOT + (eval_stats ? 1 : 0));                     \
+            if (grid <= 0) return fail(HM_ERR_CUDA, "occupancy query failed");                        \
+            grid = grid < vt.total_tiles ? grid : vt.total_tiles;                                     \
+        }                                                                                             \
+        kern<<<grid, TW * TH / 2, 0, s>>>(vt, rec, n_rec, pair_vals, tile_ranges, mesh_depth,         \
+                                          mesh_rgb, bg[0], bg[1], bg[2], opt->batch, out_rgb, out_T,  \
+                                          n_contrib, last_idx, eval_stats, d_status, wq);             \
     } while (0)
     const uint32_t n_rec = (uint32_t)((long long)n_views * n);
-    if (opt->tile_w == 16) HM_BLEND(16, 16);
-    else if (opt->tile_w == 32) HM_BLEND(32, 8);
-    else HM_BLEND(8, 8);
+    if (vt.total_tiles > 0) {
+        if (opt->tile_w == 16) HM_BLEND(16, 16, 0);
+        else if (opt->tile_w == 32) HM_BLEND(32, 8, 2);
+        else HM_BLEND(8, 8, 4);
+    }
 #undef HM_BLEND
     return cuda_status(cudaGetLastError());
 }

@@ -56,7 +56,7 @@ class HmOptions(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32),
                 ("mesh_cull", c_int32), ("near_gauss", c_float), ("near_mesh", c_float),
                 ("bg", c_float * 3), ("bwd_stages", c_int32), ("ellipse_cull", c_int32),
-                ("kernel_2d", c_float), ("antialias", c_int32)]
+                ("kernel_2d", c_float), ("antialias", c_int32), ("persistent", c_int32)]
 
 
 class HmLossParams(ctypes.Structure):
@@ -97,7 +97,7 @@ _SIGS = {
                               c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_blend_forward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p,
-                                   c_void_p, c_void_p, c_void_p]),
+                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "hm_blend_backward_workspace_size": (c_size_t, [c_int32, c_int32]),
     "hm_blend_backward": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
@@ -129,7 +129,7 @@ _SIGS = {
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                             _OPT_P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                            c_void_p]),
+                                            c_void_p, c_void_p]),
 }
 
 
@@ -146,6 +146,18 @@ def load():
             f.argtypes = args
         _lib = lib
     return _lib
+
+
+def check_device_status(st: int) -> int:
+    """Raise HmError for the device status bits that invalidate a result
+    (HM_DEV_TIMEOUT: a bounded wait gave up; HM_DEV_BAD_INDEX: a pair list
+    held an out-of-range record index, so a placeholder record was used);
+    returns ``st`` (HM_DEV_CAPACITY is the caller's to handle)."""
+    if st & HM_DEV_TIMEOUT:
+        raise HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
+    if st & HM_DEV_BAD_INDEX:
+        raise HmError("a pair list held an out-of-range record index (HM_DEV_BAD_INDEX)")
+    return st
 
 
 def last_error() -> str:
@@ -169,13 +181,15 @@ def cameras(cams) -> ctypes.Array:
 
 
 def options(tile=(16, 16), batch=None, mesh_cull=True, bg=(0.0, 0.0, 0.0), near_gauss=0.2,
-            near_mesh=0.01, ellipse_cull=True, mip=False) -> HmOptions:
+            near_mesh=0.01, ellipse_cull=True, mip=False, persistent=False) -> HmOptions:
     """hm_options; ``mip`` selects Mip-Splatting's 2D Mip filter (kernel 0.1
-    with opacity compensation) instead of the 3DGS 0.3 dilation.  The
-    staging batch defaults to 128 list entries (the tile's pixel count if
-    smaller)."""
+    with opacity compensation) instead of the 3DGS 0.3 dilation; with
+    ``persistent`` the blend kernels claim (view, tile) work from a counter.
+    The staging batch defaults to 128 list entries (the tile's pixel count
+    if smaller)."""
     o = HmOptions()
     load().hm_default_options(ctypes.byref(o))
+    o.persistent = int(bool(persistent))
     if mip:
         o.kernel_2d, o.antialias = 0.1, 1
     o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
@@ -239,11 +253,11 @@ def hm_bin_sort(cams, n, records, tile_max_depth, opt, pair_vals, capacity, n_pa
 
 
 def hm_blend_forward(cams, n, records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, opt, out_rgb,
-                     out_T, n_contrib, last_idx, eval_stats, d_status, stream):
+                     out_T, n_contrib, last_idx, eval_stats, d_status, stream, work=None):
     return load().hm_blend_forward(cams, len(cams), n, _ptr(records), _ptr(pair_vals),
                                    _ptr(tile_ranges), _ptr(mesh_depth), _ptr(mesh_rgb),
                                    ctypes.byref(opt), _ptr(out_rgb), _ptr(out_T), _ptr(n_contrib),
-                                   _ptr(last_idx), _ptr(eval_stats), _ptr(d_status), stream)
+                                   _ptr(last_idx), _ptr(eval_stats), _ptr(d_status), _ptr(work), stream)
 
 
 def hm_blend_backward_workspace_size(n_views, n) -> int:
@@ -268,7 +282,7 @@ def hm_blend_backward(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_
 def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_degree, sh_format,
                               records, pair_vals, tile_ranges, mesh_depth, mesh_rgb, mesh_uv, tex_w,
                               tex_h, opt, out_T, last_idx, dL_drgb, dL_dT, d_means, d_scales, d_quats,
-                              d_opacity, d_sh, d_tex, d_status, stream, filter_3d=None):
+                              d_opacity, d_sh, d_tex, d_status, stream, filter_3d=None, dL_dmesh=None):
     """hm_blend_backward without a workspace argument: the scratch is the
     library's static 16 MiB device array (for callers that cannot allocate)."""
     return load().hm_blend_backward_noalloc(cams, len(cams), n, _ptr(means), _ptr(scales),
@@ -278,7 +292,7 @@ def hm_blend_backward_noalloc(cams, n, means, scales, quats, opacity, sh, sh_deg
                                             _ptr(tile_ranges), _ptr(mesh_depth), _ptr(mesh_rgb),
                                             _ptr(mesh_uv), tex_w, tex_h, ctypes.byref(opt),
                                             _ptr(out_T), _ptr(last_idx), _ptr(dL_drgb), _ptr(dL_dT),
-                                            _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
+                                            _ptr(dL_dmesh), _ptr(d_means), _ptr(d_scales), _ptr(d_quats),
                                             _ptr(d_opacity), _ptr(d_sh), _ptr(d_tex),
                                             _ptr(d_status), stream)
 

@@ -67,7 +67,7 @@ class Renderer:
                  batch: Optional[int] = None, mesh_cull: bool = True, bg=(0.0, 0.0, 0.0),
                  pair_capacity: Optional[int] = None, item_capacity: Optional[int] = None,
                  ellipse_cull: bool = True, pixel_buffers: Optional[dict] = None, mip: bool = False,
-                 device="cuda"):
+                 persistent: bool = False, device="cuda"):
         lib.load()
         self.device = torch.device(device)
         self.cam_list = list(cams)
@@ -78,7 +78,7 @@ class Renderer:
         self.K = (self.sh_degree + 1) ** 2
         self.sh_format = lib.HM_SH_F16 if sh_f16 else lib.HM_SH_F32
         self.opt = lib.options(tile=tile, batch=batch, mesh_cull=mesh_cull, bg=bg,
-                               ellipse_cull=ellipse_cull, mip=mip)
+                               ellipse_cull=ellipse_cull, mip=mip, persistent=persistent)
         # Mip-Splatting back-end (mip=True): the 2D Mip filter in the options and
         # the per-Gaussian 3D smoothing variance (set_filter_3d / mip_filter_3d)
         self.mip = bool(mip)
@@ -101,6 +101,7 @@ class Renderer:
         self.n_pairs = torch.zeros(1, dtype=torch.int64, device=d)
         self.n_items = torch.zeros(1, dtype=torch.int64, device=d)
         self.status_word = torch.zeros(1, dtype=i32, device=d)
+        self.work = torch.zeros(1, dtype=i32, device=d)      # tile counter of the persistent blend
         if pixel_buffers is not None:
             self.use_pixel_buffers(pixel_buffers)
         else:
@@ -236,7 +237,8 @@ class Renderer:
         mr = self.mesh_rgb if self.has_mesh else None
         lib.check(lib.hm_blend_forward(self.cams, self.n, self.records, self.pair_vals, self.ranges,
                                        md, mr, self.opt, self.rgb, self.T, self.n_contrib,
-                                       self.last_idx, eval_stats, self.status_word, _stream()),
+                                       self.last_idx, eval_stats, self.status_word, _stream(),
+                                       work=self.work),
                   "hm_blend_forward")
 
     def count_evaluations(self):
@@ -298,12 +300,12 @@ class Renderer:
     def render(self, means, scales, quats, opacity, sh, mesh: Optional[MeshInput] = None,
                max_retries: int = 3, overlap: Optional[bool] = None):
         """forward() plus the capacity check; grows the buffers and re-runs
-        when a capacity was exceeded.  Raises on HM_DEV_TIMEOUT."""
+        when a capacity was exceeded.  Raises on HM_DEV_TIMEOUT and
+        HM_DEV_BAD_INDEX."""
         for _ in range(max_retries + 1):
             self.forward(means, scales, quats, opacity, sh, mesh, overlap=overlap)
             st, npairs, nitems = self.status()
-            if st & lib.HM_DEV_TIMEOUT:
-                raise lib.HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
+            lib.check_device_status(st)
             if not st & lib.HM_DEV_CAPACITY:
                 return self
             if npairs > self._pair_cap:
@@ -553,8 +555,7 @@ class GraphStep:
         self.graph.replay()
         if check:
             st, npairs, nitems = self.r.status()
-            if st & lib.HM_DEV_TIMEOUT:
-                raise lib.HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
+            lib.check_device_status(st)
             if st & lib.HM_DEV_CAPACITY:
                 self.capture()                            # grows the buffers, then re-captures
                 self.graph.replay()
@@ -642,12 +643,13 @@ class ChunkedRenderer:
             self.renderer(ci).forward(means, scales, quats, opacity, sh, mesh)
         return self
 
-    def status(self):
-        """OR of the chunk renderers' status bits -- synchronises."""
+    def status(self, check: bool = False):
+        """OR of the chunk renderers' status bits -- synchronises.  With
+        ``check``, raises on HM_DEV_TIMEOUT and HM_DEV_BAD_INDEX."""
         st = 0
         for r in self._renderers.values():
             st |= r.status()[0]
-        return st
+        return lib.check_device_status(st) if check else st
 
     def grad_buffers(self, tex_shape=None):
         d = self.device

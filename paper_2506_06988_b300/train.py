@@ -128,8 +128,7 @@ class JointTrainStep:
         self.graph.replay()
         if check:
             st, _, _ = self.r.status()
-            if st & lib.HM_DEV_TIMEOUT:
-                raise lib.HmError("a bounded device wait timed out (HM_DEV_TIMEOUT)")
+            lib.check_device_status(st)
             if st & lib.HM_DEV_CAPACITY:
                 self.capture()
                 self.graph.replay()

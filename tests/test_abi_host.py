@@ -88,6 +88,10 @@ def test_invalid_arguments_are_rejected_on_the_host(hm):
     # misaligned records
     st = lib.hm_blend_forward(cams, 10, 4, 8, 8, 0, 0, o, 8, 8, 8, 0, None, None, 0)
     assert st == lib.HM_ERR_INVALID_ARG and "aligned" in lib.last_error()
+    # a persistent launch without its work counter
+    op = lib.options(persistent=True)
+    st = lib.hm_blend_forward(cams, 10, 16, 8, 8, 0, 0, op, 8, 8, 8, 0, None, None, 0)
+    assert st == lib.HM_ERR_INVALID_ARG and "work counter" in lib.last_error()
     # workspace too small
     st = lib.hm_bin_sort(cams, 10, 16, None, o, 16, 1000, 16, 16, 0, 16, 8, 0)
     assert st == lib.HM_ERR_WORKSPACE

@@ -13,7 +13,7 @@ import torch
 
 from oracle import oracle as O
 from oracle import torch_ref as TR
-from paper_2506_06988_b300 import scenes
+from paper_2506_06988_b300 import lib, scenes
 from paper_2506_06988_b300.render import HybridRender, MeshInput
 
 from gpu_util import check_grad, gpu_render, gaussians_to_torch, make_renderer  # noqa: E402
@@ -166,3 +166,54 @@ def test_config1_full_size_backward_sampled_pixels():
         _check(k, g[k].cpu().numpy(), ref[k])
     gt = g["texture"].cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gt - ref["texture"]) <= 1e-3 * np.linalg.norm(ref["texture"])
+
+
+def test_texel_gradients_keep_relative_accuracy_across_1e6_of_range():
+    """dL/dI_h spanning six decades inside every tile (log-uniform
+    magnitudes, random signs): each texel gradient within 1e-3 relative of
+    an FP64 scatter of the same inputs (the kernel's own uv, T and dL/dI),
+    element by element with no floor scaled by the largest gradient."""
+    s = scenes.config0_scene()
+    s.mesh.texture = s.mesh.texture.astype(np.float32) / 255.0
+    r, P, mesh = gpu_render(s)
+    rng = np.random.default_rng(9)
+    mag = 10.0 ** rng.uniform(-6.0, 0.0, (3, r.npix))
+    dI_np = (mag * rng.choice([-1.0, 1.0], (3, r.npix))).astype(np.float32)
+    dI = torch.as_tensor(dI_np.reshape(-1), device="cuda")
+    g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, mesh=mesh, tex_grad=True,
+                   stages=lib.HM_BWD_TEXTURE)
+    torch.cuda.synchronize()
+    got = g["texture"].cpu().numpy().astype(np.float64)
+    th, tw = s.mesh.texture.shape[:2]
+    uv = r.uv.view(2, -1).cpu().numpy().astype(np.float64)
+    T = r.T.cpu().numpy().astype(np.float64)
+    hit = np.isfinite(r.mesh_depth.cpu().numpy())
+    # FP64 scatter with the kernel's FP32 footprint (the same texel indices
+    # and weights): texel centres at half-integers, clamp to the edge
+    ss = (uv[0] * np.float32(tw)).astype(np.float32) - np.float32(0.5)
+    tt = (uv[1] * np.float32(th)).astype(np.float32) - np.float32(0.5)
+    x0, y0 = np.floor(ss), np.floor(tt)
+    fx, fy = (ss - x0).astype(np.float64), (tt - y0).astype(np.float64)
+    want = np.zeros((th, tw, 3))
+    sabs = np.zeros((th, tw, 3))                # sum of |taps| per texel
+    ntap = np.zeros((th, tw, 3))                # taps per texel
+    mtap = np.zeros((th, tw, 3))                # largest |tap| per texel
+    gpx = T[None, :] * dI_np.astype(np.float64)
+    for dx, dy, w in ((0, 0, (1 - fx) * (1 - fy)), (1, 0, fx * (1 - fy)), (0, 1, (1 - fx) * fy), (1, 1, fx * fy)):
+        xi = np.clip(x0 + dx, 0, tw - 1).astype(int)
+        yi = np.clip(y0 + dy, 0, th - 1).astype(int)
+        for c in range(3):
+            np.add.at(want[:, :, c], (yi[hit], xi[hit]), (w * gpx[c])[hit])
+            np.add.at(sabs[:, :, c], (yi[hit], xi[hit]), np.abs(w * gpx[c])[hit])
+            np.add.at(ntap[:, :, c], (yi[hit], xi[hit]), (w != 0)[hit].astype(float))
+            np.maximum.at(mtap[:, :, c], (yi[hit], xi[hit]), np.abs(w * gpx[c])[hit])
+    nz = sabs != 0
+    # 1e-3 of the texel's own gradient, plus the rounding of its own taps:
+    # the kernel's per-texel fixed point (2^-20 of the texel's largest tap
+    # over its channels, per tap) and the FP32 products -- nothing scaled by
+    # other texels
+    err = np.abs(got[nz] - want[nz])
+    floor = (ntap * 2.0 ** -20 * mtap.max(2, keepdims=True))[nz] + 1e-6 * sabs[nz]
+    assert (err <= 1e-3 * np.abs(want[nz]) + floor).all(), float((err / np.abs(want[nz])).max())
+    assert (np.abs(want[nz]) < 1e-3 * sabs.max()).mean() > 0.05       # many texels far below the maximum
+    assert not got[~nz].any()

@@ -10,6 +10,9 @@
   FP16 SH storage equal the sum over cameras of the FP64 gradient oracle.
 * The chunked renderer (one chunk's lists at a time, recomputed in the
   backward pass) reproduces the batched renderer's images and gradients.
+* The persistent launch (resident CTAs claiming (view, tile) work from a
+  counter) gives the grid launch's images bit for bit, its gradients up to
+  atomic order, and matches the oracle.
 """
 import numpy as np
 import pytest
@@ -20,7 +23,8 @@ from oracle import torch_ref as TR
 from paper_2506_06988_b300 import autotune, scenes
 from paper_2506_06988_b300.render import GraphStep, MeshInput
 
-from gpu_util import check_grad, gaussians_to_torch, gpu_render, make_renderer  # noqa: E402
+from gpu_util import (check_grad, compare_blend, gaussians_to_torch, gpu_render, make_renderer,  # noqa: E402
+                      oracle_view, view_outputs)
 
 pytestmark = pytest.mark.gpu
 
@@ -152,12 +156,12 @@ def test_autotune_covers_the_grid_and_does_not_change_the_image():
     dI = torch.randn(3 * npix, device="cuda", generator=gen)
     res = autotune.tune(s.cameras, g.n, g.sh_degree, _params(P), mesh, dL_drgb=dI, tex_grad=True,
                         warmup=1, iters=2, **kw)
-    combos = {(t, b) for t, b, _ in res.table}
+    combos = {(t, b, p) for t, b, p, _ in res.table}
     want = {((16, 16), b) for b in (32, 64, 128, 256)} | {((32, 8), b) for b in (32, 64, 128, 256)} \
         | {((8, 8), b) for b in (32, 64)}
-    assert combos == want
-    assert all(np.isfinite(ms) and ms > 0 for _, _, ms in res.table)
-    assert (res.tile, res.batch) in combos
+    assert combos == {(t, b, p) for t, b in want for p in (False, True)}
+    assert all(np.isfinite(ms) and ms > 0 for _, _, _, ms in res.table)
+    assert (res.tile, res.batch, res.persistent) in combos
     ref, _, _ = gpu_render(s)
     r = res.renderer
     r.render(*_params(P), mesh)
@@ -167,8 +171,9 @@ def test_autotune_covers_the_grid_and_does_not_change_the_image():
     assert torch.equal(r.n_contrib, ref.n_contrib)
 
 
-@pytest.mark.parametrize("tile,batch", [((16, 16), 32), ((32, 8), 128), ((8, 8), 64)])
-def test_batched_uneven_fp16_backward_matches_oracle(tile, batch):
+@pytest.mark.parametrize("tile,batch,persistent", [((16, 16), 32, False), ((32, 8), 128, False), ((8, 8), 64, False),
+                                                   ((16, 16), 128, True), ((8, 8), 32, True)])
+def test_batched_uneven_fp16_backward_matches_oracle(tile, batch, persistent):
     s = _room(seed=34)
     rng = np.random.default_rng(7)
     gI_views, gT_views = [], []
@@ -184,7 +189,7 @@ def test_batched_uneven_fp16_backward_matches_oracle(tile, batch):
         ref = gv if ref is None else {k: ref[k] + gv[k] for k in ref}
         gI_views.append(gI)
         gT_views.append(gT)
-    r, P, mesh = gpu_render(s, tile=tile, batch=batch)
+    r, P, mesh = gpu_render(s, tile=tile, batch=batch, persistent=persistent)
     dI = torch.as_tensor(np.concatenate([g.reshape(-1) for g in gI_views]), dtype=torch.float32, device="cuda")
     dT = torch.as_tensor(np.concatenate(gT_views), dtype=torch.float32, device="cuda")
     g = r.backward(*_params(P), dI, dT, mesh=mesh, tex_grad=True)
@@ -243,3 +248,26 @@ def test_stream_overlap_gives_the_sequential_results():
     for k, v in seq.items():
         assert torch.equal(getattr(r, k), v), k
     _grads_close(g_ovl, g_seq)
+
+
+@pytest.mark.parametrize("tile,batch", [((16, 16), 128), ((32, 8), 64), ((8, 8), 32)])
+def test_persistent_launch_matches_grid_launch_and_oracle(tile, batch):
+    """The (view, tile) work-queue launch of the blend kernels over three
+    cameras of uneven size: the grid launch's outputs bit for bit, the same
+    gradients up to FP32 atomic order, and the oracle's images."""
+    s = _room(seed=35)
+    a, P, mesh = gpu_render(s, tile=tile, batch=batch)
+    b, _, _ = gpu_render(s, tile=tile, batch=batch, persistent=True)
+    assert b.status()[0] == 0
+    for k in ("rgb", "T", "n_contrib", "last_idx"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    for v in range(len(s.cameras)):
+        compare_blend(view_outputs(b, v), oracle_view(s, v))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    dI = torch.randn(3 * a.npix, device="cuda", generator=gen)
+    ga = a.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True)
+    gb = b.backward(*_params(P), dI, None, mesh=mesh, tex_grad=True)
+    torch.cuda.synchronize()
+    assert b.status()[0] == 0
+    _grads_close(gb, ga)

@@ -31,3 +31,24 @@ def test_bounded_waits_time_out_and_the_context_stays_usable():
     r, _, _ = gpu_render(s)
     assert r.status()[0] == 0
     compare_blend(view_outputs(r, 0), oracle_view(s, 0))
+
+
+def test_out_of_range_record_index_is_reported_not_returned():
+    """A pair list holding a record index past the records (possible only
+    after an earlier failure left the list invalid) is caught by the blend
+    kernel's index guard: HM_DEV_BAD_INDEX in the status word, and the
+    renderer's checked paths raise instead of returning the image."""
+    s = scenes.micro_two_gaussians()
+    r, P, mesh = gpu_render(s)
+    assert int(r.n_pairs.item()) > 0
+    r.pair_vals[0] = r.V * r.n + 1000                  # out of range; the guard substitutes record 0
+    r.blend()
+    torch.cuda.synchronize()
+    st = r.status()[0]
+    assert st & lib.HM_DEV_BAD_INDEX
+    with pytest.raises(lib.HmError, match="HM_DEV_BAD_INDEX"):
+        lib.check_device_status(st)
+    # a full render (fresh lists) clears the status and succeeds
+    r.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh)
+    assert r.status()[0] == 0
+    compare_blend(view_outputs(r, 0), oracle_view(s, 0))

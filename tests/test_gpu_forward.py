@@ -337,6 +337,32 @@ def test_huge_gaussian_covering_every_tile():
     compare_blend(view_outputs(r, 0), oracle_view(s, 0))
 
 
+def test_non_finite_gaussians_are_culled_on_gpu():
+    """NaN / Inf means, scales, quaternions, opacities and SH coefficients
+    (and zero quaternions): the image equals the oracle's, which culls those
+    Gaussians, the status word stays clear and every gradient is finite,
+    zero for the culled Gaussians."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_pins import _poison
+    s = scenes.config0_scene()
+    s.gaussians, idx = _poison(s.gaussians, np.random.default_rng(5))
+    r, P, mesh = gpu_render(s)
+    assert r.status()[0] == 0
+    st = compare_blend(view_outputs(r, 0), oracle_view(s, 0))
+    assert st["ambiguous"] == 0
+    rec = records_np(r)
+    assert (rec.x0[idx] > rec.x1[idx]).all()                # in no tile's list
+    dI = torch.ones(3 * r.npix, device="cuda")
+    g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, mesh=mesh, tex_grad=True)
+    torch.cuda.synchronize()
+    for k, v in g.items():
+        v = v.cpu().numpy()
+        assert np.isfinite(v).all(), k
+        if k != "texture":
+            assert not v[idx].any(), k
+
+
 # ----------------------------------------------- full size, sampled pixels --
 
 def test_config1_full_size_sampled_pixels():
