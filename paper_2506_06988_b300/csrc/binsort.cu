@@ -5,13 +5,16 @@
 // pairs are bucketed by tile first and each tile's bucket is then sorted on
 // its own (a segmented sort), instead of a global radix sort on a
 // (tile, depth) key:
-//  1. count: per record, the tiles it keeps (mesh cull, ellipse test) -- a
-//     bit mask for small rectangles -- and per tile the number of records
-//     that keep it (atomic counts);
+//  1. count: per (record, tile) of each record's tile rectangle, whether the
+//     tile is kept (mesh cull, ellipse test), and per tile the number of
+//     records that keep it (atomic counts); the candidates of a block of
+//     records are spread evenly over the CTA's threads (load-balanced
+//     expansion: most records are culled, and the visible ones span from
+//     one to a thousand tiles);
 //  2. scan of the per-tile counts: each tile's [begin, end) in the output,
 //     the pair count and the capacity check;
-//  3. emit: every kept (record, tile) writes the 64-bit key
-//     (depth bits << 32 | record index) into its tile's bucket at an
+//  3. emit: the same expansion; every kept (record, tile) writes the 64-bit
+//     key (depth bits << 32 | record index) into its tile's bucket at an
 //     atomically taken slot (bucket order is arbitrary at this point);
 //  4. sort each bucket by that key -- a warp per tile in registers (bitonic)
 //     for up to 256 pairs, a CTA in shared memory (radix) for up to 4096, a
@@ -65,18 +68,6 @@ __device__ __forceinline__ int rec_tiles(const BinRec &r) {
     return (r.x0 <= r.x1 && r.y0 <= r.y1) ? (r.x1 - r.x0 + 1) * (r.y1 - r.y0 + 1) : 0;
 }
 
-__device__ __forceinline__ BinRec shfl_rec(const BinRec &r, int src) {
-    BinRec o;
-    o.mx = __shfl_sync(0xffffffffu, r.mx, src); o.my = __shfl_sync(0xffffffffu, r.my, src);
-    o.a = __shfl_sync(0xffffffffu, r.a, src); o.b = __shfl_sync(0xffffffffu, r.b, src);
-    o.c = __shfl_sync(0xffffffffu, r.c, src); o.depth = __shfl_sync(0xffffffffu, r.depth, src);
-    o.x0 = __shfl_sync(0xffffffffu, r.x0, src); o.x1 = __shfl_sync(0xffffffffu, r.x1, src);
-    o.y0 = __shfl_sync(0xffffffffu, r.y0, src); o.y1 = __shfl_sync(0xffffffffu, r.y1, src);
-    o.v = __shfl_sync(0xffffffffu, r.v, src);
-    return o;
-}
-
-
 // Is the pair (record, tile) kept (ra, rc = 1 / conic_xx, 1 / conic_yy)?  Mesh cull: the tile's farthest mesh depth
 // must lie behind the record (Sec. 3.4 blends only D_gs < D_m).  Ellipse
 // test: the 3-sigma ellipse must reach the rectangle of the tile's in-image
@@ -98,120 +89,106 @@ __device__ __forceinline__ bool keep_tile(const ViewTable &vt, const float *tmax
     return m <= 9.0f * 1.002f;
 }
 
-// Tiles of row ty that the (0.2%-inflated) 3-sigma ellipse reaches, as the
-// column range [lo, hi] clipped to the record's rectangle (lo > hi: none).
-// The ellipse meets a tile's rectangle of pixel centres iff its slice by
-// the tile row's band of pixel-centre rows, projected on x, meets the tile's
-// column range: an exact, per-row alternative to keep_tile's per-tile
-// test.  With the conic (a, b, c), det = ac - b^2 (a compensated difference
-// of products: thin ellipses cancel), R = 9 * 1.002, the slice at dy spans
-// dx in (-b dy -+ sqrt(a R - det dy^2)) / a; its leftmost point over the
-// band is the ellipse's own leftmost point (dx = -xe, dy = b xe / c, with
-// xe = sqrt(R c / det)) when that lies in the band, else an end of the band
-// (the left boundary is convex in dy), and symmetrically on the right.
-__device__ __forceinline__ void row_span(const ViewTable &vt, const ViewDev &V, const BinRec &r, int ty,
-                                         int &lo, int &hi) {
-    constexpr float R = 9.0f * 1.002f;
-    lo = r.x0;
-    hi = r.x1;
-    const float bb = r.b * r.b;
-    const float det = __fmaf_rn(r.a, r.c, -bb) + __fmaf_rn(-r.b, r.b, bb);
-    if (!(det > 0.f)) return;                    // degenerate: the whole rectangle row
-    const float ye = sqrtf(R * r.a / det), xe = sqrtf(R * r.c / det);
-    float s0 = (float)(ty * vt.tile_h) + 0.5f - r.my;
-    float s1 = (float)(min((ty + 1) * vt.tile_h, V.H) - 1) + 0.5f - r.my;
-    s0 = fmaxf(s0, -ye);
-    s1 = fminf(s1, ye);
-    if (s0 > s1) {
-        lo = 1;
-        hi = 0;
-        return;
+// Binning of a block of records by load-balanced expansion.  A CTA takes
+// kBinThreads consecutive records; each thread loads one and counts the
+// tiles of its rectangle (0 for a culled record), a block-wide exclusive
+// scan lays the records' (record, tile) candidates end to end, and every
+// thread of the CTA then takes candidates c = t, t + kBinThreads, ... : the
+// record is the last slot whose offset is <= c (binary search over the
+// offsets in shared memory), the tile follows from c - offset.  A record
+// spanning a thousand tiles and a block of single-tile records keep every
+// thread equally busy, and a CTA's candidate loads and atomics are in
+// flight together.  Each candidate takes the mesh cull and the ellipse test
+// (keep_tile); count and emission run the same expansion, so they keep the
+// same pairs.
+constexpr int kBinThreads = 256;
+
+struct BinBlock {
+    uint32_t off[kBinThreads + 1];   // exclusive prefix of the rectangles' tile counts; [256] = total
+    uint32_t wsum[kBinThreads / 32];
+    float mx[kBinThreads], my[kBinThreads], a[kBinThreads], b[kBinThreads], c[kBinThreads];
+    float ra[kBinThreads], rc[kBinThreads], depth[kBinThreads];
+    int x0[kBinThreads], y0[kBinThreads], nx[kBinThreads], v[kBinThreads];
+};
+
+// Loads the CTA's records and scans their rectangle sizes; returns the total.
+__device__ __forceinline__ uint32_t bin_block_load(BinBlock &S, const Record *__restrict__ rec, long long m,
+                                                   int n) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const long long it = (long long)blockIdx.x * kBinThreads + t;
+    uint32_t cnt = 0;
+    if (it < m) {
+        const BinRec r = load_bin_rec(rec, it, n);
+        cnt = (uint32_t)rec_tiles(r);
+        if (cnt) {
+            S.mx[t] = r.mx; S.my[t] = r.my;
+            S.a[t] = r.a; S.b[t] = r.b; S.c[t] = r.c;
+            S.ra[t] = 1.f / r.a; S.rc[t] = 1.f / r.c;
+            S.depth[t] = r.depth;
+            S.x0[t] = r.x0; S.y0[t] = r.y0; S.nx[t] = r.x1 - r.x0 + 1; S.v[t] = r.v;
+        }
     }
-    const float ra = 1.f / r.a;
-    const float sq0 = sqrtf(fmaxf(0.f, r.a * R - det * s0 * s0));
-    const float sq1 = sqrtf(fmaxf(0.f, r.a * R - det * s1 * s1));
-    const float yl = r.b * xe / r.c, yr = -yl;
-    const float xmin = (yl >= s0 && yl <= s1) ? -xe : fminf((-r.b * s0 - sq0) * ra, (-r.b * s1 - sq1) * ra);
-    const float xmax = (yr >= s0 && yr <= s1) ? xe : fmaxf((-r.b * s0 + sq0) * ra, (-r.b * s1 + sq1) * ra);
-    // tile tx spans pixel centres [tx TW + 1/2, (tx + 1) TW - 1/2] (clipped to
-    // the image at the last column of tiles)
-    const float u0 = r.mx + xmin, u1 = r.mx + xmax;
-    lo = max(lo, (int)ceilf((u0 + 0.5f) / (float)vt.tile_w) - 1);
-    hi = min(hi, (int)floorf((u1 - 0.5f) / (float)vt.tile_w));
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) S.wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t ws = lane < kBinThreads / 32 ? S.wsum[lane] : 0u;
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < kBinThreads / 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kBinThreads / 32) S.wsum[lane] = wi - ws;          // exclusive over warps
+        if (lane == kBinThreads / 32 - 1) S.off[kBinThreads] = wi;   // total
+    }
+    __syncthreads();
+    S.off[t] = S.wsum[w] + incl - cnt;
+    __syncthreads();
+    return S.off[kBinThreads];
 }
 
-// records with more tiles than this are binned by the whole warp
-constexpr int kSmallRect = 8;
-// record whose kept tiles are recomputed at emission (large rectangle)
-constexpr uint32_t kMaskRecompute = 0x80000000u;
-
-// Per record, what the emission needs (16 B, so that it does not re-read the
-// 48-B record): {mask, depth bits, first tile's global id, nx | tiles_x << 16}
-// with mask = the kept tiles of a small rectangle as bits (bit
-// (ty - y0) * nx + (tx - x0)), kMaskRecompute for a large rectangle, 0 for
-// none.  Per tile: atomic count of the records that keep it.  Small
-// rectangles are walked by their own thread (the ellipse's tile columns per
-// tile row from row_span); large ones by the whole warp, one record at a
-// time, lanes over tiles.
-__global__ void __launch_bounds__(256)
-bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                 int ellipse, uint4 *__restrict__ desc, uint32_t *__restrict__ tile_cnt) {
-    const long long m = (long long)vt.n_views * n;
-    const int lane = threadIdx.x & 31;
-    // one record per thread, consecutive records in a warp (coalesced loads)
-    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = it < m;
+// Candidate c of the block: its record slot j and tile (tx, ty); true if
+// the pair is kept.
+__device__ __forceinline__ bool bin_candidate(const BinBlock &S, const ViewTable &vt, const float *tmax,
+                                              int ellipse, uint32_t c, int &j, int &tx, int &ty) {
+    int lo = 0, hi = kBinThreads;                    // off[lo] <= c < off[hi]
+#pragma unroll
+    for (int step = 0; step < 8; ++step) {
+        const int mid = (lo + hi) >> 1;
+        if (S.off[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    j = lo;
+    const uint32_t o = c - S.off[j];
+    const int nx = S.nx[j];
+    tx = S.x0[j] + (int)(o % (uint32_t)nx);
+    ty = S.y0[j] + (int)(o / (uint32_t)nx);
     BinRec r;
-    int nt = 0;
-    if (valid) {
-        r = load_bin_rec(rec, it, n);
-        nt = rec_tiles(r);
-    } else {
-        r = BinRec{};
-    }
-    uint32_t mask = 0, g0 = 0, geo = 0;
-    if (nt > 0 && nt <= kSmallRect) {
-        const ViewDev &V = vt.v[r.v];
-        g0 = V.tile_off + r.y0 * V.tiles_x + r.x0;
-        geo = (uint32_t)(r.x1 - r.x0 + 1) | ((uint32_t)V.tiles_x << 16);
-        const int nx = r.x1 - r.x0 + 1;
-        for (int ty = r.y0; ty <= r.y1; ++ty) {
-            int lo = r.x0, hi = r.x1;
-            if (ellipse) row_span(vt, V, r, ty, lo, hi);
-            for (int tx = lo; tx <= hi; ++tx)
-                if (tmax == nullptr || r.depth < tmax[V.tile_off + ty * V.tiles_x + tx])
-                    mask |= 1u << ((ty - r.y0) * nx + (tx - r.x0));
+    r.mx = S.mx[j]; r.my = S.my[j]; r.a = S.a[j]; r.b = S.b[j]; r.c = S.c[j]; r.depth = S.depth[j];
+    r.v = S.v[j];
+    return keep_tile(vt, tmax, ellipse, r, S.ra[j], S.rc[j], tx, ty);
+}
+
+// Per tile: the number of records that keep it (atomic counts).
+__global__ void __launch_bounds__(kBinThreads)
+bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
+                 int ellipse, uint32_t *__restrict__ tile_cnt) {
+    __shared__ BinBlock S;
+    const uint32_t total = bin_block_load(S, rec, (long long)vt.n_views * n, n);
+    for (uint32_t c = threadIdx.x; c < total; c += kBinThreads) {
+        int j, tx, ty;
+        if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
+            const ViewDev &V = vt.v[S.v[j]];
+            // a reduction (no return value): hot tiles' adds queue in L2
+            atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
         }
     }
-    // per-tile counts: one reduction per kept tile (no return value, so the
-    // adds of hot tiles queue in L2 without stalling the warp)
-    {
-        const int nx = (int)(geo & 0xFFFFu), tiles_x = (int)(geo >> 16);
-        uint32_t bits = mask;
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            atomicAdd(&tile_cnt[g0 + (b / nx) * tiles_x + b % nx], 1u);
-        }
-    }
-    // large rectangles: the whole warp, one record at a time, lanes over tiles
-    unsigned big = __ballot_sync(0xffffffffu, nt > kSmallRect);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const BinRec q = shfl_rec(r, src);
-        const float ra = 1.f / q.a, rc = 1.f / q.c;
-        const ViewDev &V = vt.v[q.v];
-        const int nx = q.x1 - q.x0 + 1, ntot = nx * (q.y1 - q.y0 + 1);
-        for (int t0 = 0; t0 < ntot; t0 += 32) {
-            const int t = t0 + lane;
-            const int tx = q.x0 + t % nx, ty = q.y0 + t / nx;
-            if (t < ntot && keep_tile(vt, tmax, ellipse, q, ra, rc, tx, ty))
-                atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
-        }
-        if (lane == src) mask = kMaskRecompute;
-    }
-    if (valid) desc[it] = make_uint4(mask, __float_as_uint(r.depth), g0, geo);
 }
 
 // pairs to sort: all of them, or none when the capacity was exceeded
@@ -220,57 +197,24 @@ __global__ void clamp_count_kernel(const long long *total, long long capacity, l
     *n_out = t <= capacity ? t : 0;
 }
 
-// every kept (record, tile) of a small rectangle: its key into the tile's
-// bucket, at a slot taken from the tile's cursor (initialised to the
-// bucket's start); nothing is written when the capacity was exceeded
-__global__ void __launch_bounds__(256)
+// Every kept (record, tile): the 64-bit key (depth bits << 32 | record
+// index) into the tile's bucket, at a slot taken from the tile's cursor
+// (initialised to the bucket's start); nothing is written when the
+// capacity was exceeded.
+__global__ void __launch_bounds__(kBinThreads)
 bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                int ellipse, const uint4 *__restrict__ desc, uint32_t *__restrict__ cursor,
-                const long long *n_sort, unsigned long long *__restrict__ keys) {
+                int ellipse, uint32_t *__restrict__ cursor, const long long *n_sort,
+                unsigned long long *__restrict__ keys) {
     if (*n_sort == 0) return;
-    const long long m = (long long)vt.n_views * n;
-    const int lane = threadIdx.x & 31;
-    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint4 dsc = it < m ? desc[it] : make_uint4(0u, 0u, 0u, 0u);
-    const uint32_t mask = dsc.x;
-    const unsigned long long key = ((unsigned long long)dsc.y << 32) | (uint32_t)it;
-    const int nx = (int)(dsc.w & 0xFFFFu), tiles_x = (int)(dsc.w >> 16);
-    // each kept tile takes a slot from the tile's cursor; a small rectangle
-    // has at most kSmallRect tiles, whose atomics are all issued before any
-    // slot is used, so their latencies overlap
-    uint32_t bits = mask != kMaskRecompute ? mask : 0u;
-    if (bits) {
-        uint32_t slot[kSmallRect];
-#pragma unroll
-        for (int r = 0; r < kSmallRect; ++r) {
-            slot[r] = 0xFFFFFFFFu;
-            if (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                slot[r] = atomicAdd(&cursor[dsc.z + (b / nx) * tiles_x + b % nx], 1u);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kSmallRect; ++r)
-            if (slot[r] != 0xFFFFFFFFu) keys[slot[r]] = key;
-    }
-    // large rectangles: the whole warp, one record at a time, lanes over tiles
-    BinRec r = BinRec{};
-    if (mask == kMaskRecompute) r = load_bin_rec(rec, it, n);
-    unsigned big = __ballot_sync(0xffffffffu, mask == kMaskRecompute);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const BinRec q = shfl_rec(r, src);
-        const unsigned long long qkey = __shfl_sync(0xffffffffu, key, src);
-        const float ra = 1.f / q.a, rc = 1.f / q.c;
-        const ViewDev &V = vt.v[q.v];
-        const int qnx = q.x1 - q.x0 + 1, ntot = qnx * (q.y1 - q.y0 + 1);
-        for (int t0 = 0; t0 < ntot; t0 += 32) {
-            const int t = t0 + lane;
-            const int tx = q.x0 + t % qnx, ty = q.y0 + t / qnx;
-            if (t < ntot && keep_tile(vt, tmax, ellipse, q, ra, rc, tx, ty))
-                keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] = qkey;
+    __shared__ BinBlock S;
+    const uint32_t total = bin_block_load(S, rec, (long long)vt.n_views * n, n);
+    for (uint32_t c = threadIdx.x; c < total; c += kBinThreads) {
+        int j, tx, ty;
+        if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
+            const ViewDev &V = vt.v[S.v[j]];
+            const uint32_t it = (uint32_t)blockIdx.x * kBinThreads + (uint32_t)j;
+            keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] =
+                ((unsigned long long)__float_as_uint(S.depth[j]) << 32) | it;
         }
     }
 }
@@ -767,7 +711,6 @@ seg_sort_huge_kernel(const uint32_t *__restrict__ list, const unsigned int *list
 }
 
 struct BinWs {
-    uint4 *desc;
     uint32_t *tile_cnt, *tile_off, *tile_fill, *mid_list, *big_list;
     unsigned long long *keys, *scratch;
     unsigned int *counts;   // [0] mid-size buckets (<= kMidSeg), [1] larger buckets
@@ -778,7 +721,6 @@ struct BinWs {
 BinWs carve(void *ws, long long m, long long cap, long long tiles, size_t *bytes) {
     WsCarver c(ws);
     BinWs b;
-    b.desc = c.take<uint4>(m);
     b.tile_cnt = c.take<uint32_t>(tiles);
     b.tile_off = c.take<uint32_t>(tiles);
     b.tile_fill = c.take<uint32_t>(tiles);
@@ -846,8 +788,8 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
         return cuda_status(e);
 
     // 1. kept tiles per record, records per tile
-    const unsigned rgrid = (unsigned)((m + 255) / 256);
-    bin_count_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.desc, b.tile_cnt);
+    const unsigned rgrid = (unsigned)((m + kBinThreads - 1) / kBinThreads);
+    bin_count_kernel<<<rgrid, kBinThreads, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.tile_cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 2. tile offsets, pair count and capacity check
     e = launch_scan(b.tile_cnt, nullptr, b.tile_off, T, (long long *)n_pairs_out, capacity, d_status, b.scan, s);
@@ -856,8 +798,8 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     // 3. keys into the tile buckets (cursors start at the bucket starts)
     e = cudaMemcpyAsync(b.tile_fill, b.tile_off, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    bin_emit_kernel<<<rgrid, 256, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.desc, b.tile_fill, b.n_sort,
-                                          b.keys);
+    bin_emit_kernel<<<rgrid, kBinThreads, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.tile_fill, b.n_sort,
+                                                  b.keys);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 4. sort every bucket; tile ranges
     seg_sort_small_kernel<<<grid_for(T * 32, 256), 256, 0, s>>>((uint32_t)T, b.tile_off, b.tile_cnt, b.n_sort,

@@ -75,9 +75,9 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
 // PP = 2 a thread holds two pairs of one column: the column part of q and
 // the warp reduction of the nine partials are shared by four pixels.  The
 // staged records live in dynamic shared memory sized by the batch.
-// One tile's replay.  ph[b] counts the phases of barrier b completed before
-// this tile (the wait parity of round r is (ph[r & 1] + r / 2) & 1); every
-// round issued here is waited for before the return.  Returns false
+// One tile's replay.  ph0 / ph1 count the phases of barrier 0 / 1 completed
+// before this tile (the wait parity of round r is (ph_{r & 1} + r / 2) & 1);
+// every round issued here is waited for before the return.  Returns false
 // (block-uniform) after a timed-out wait.
 template <int TW, int TH, int PP>
 __device__ __forceinline__ bool blend_bwd_tile(
@@ -86,7 +86,7 @@ __device__ __forceinline__ bool blend_bwd_tile(
     const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2, const float *__restrict__ out_T,
     const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
     const float *__restrict__ dL_dT, int batch, float *__restrict__ g2d, int32_t *__restrict__ d_status,
-    Record *s_rec0, uint32_t *s_item0, uint64_t *s_bar, uint32_t &s_hi, uint32_t *ph) {
+    Record *s_rec0, uint32_t *s_item0, uint64_t *s_bar, uint32_t &s_hi, uint32_t &ph0, uint32_t &ph1) {
     constexpr int NTH = TW * TH / (2 * PP);
     constexpr int PER = (TW * TH + NTH - 1) / NTH;       // staged records per thread and round, at most
     const int v = view_of_tile(vt, gt);
@@ -198,7 +198,7 @@ __device__ __forceinline__ bool blend_bwd_tile(
             if (r + 2 < n_rounds) load_idx(r + 2);
         }
         const int buf = r & 1;
-        if (!mbar_wait(&s_bar[buf], (ph[buf] + (r >> 1)) & 1u)) {
+        if (!mbar_wait(&s_bar[buf], ((buf ? ph1 : ph0) + (r >> 1)) & 1u)) {
             set_status(d_status, HM_DEV_TIMEOUT);
             ok = false;
         }
@@ -241,49 +241,61 @@ __device__ __forceinline__ bool blend_bwd_tile(
             // gradient math and no reduction; within an entry, a pair row no
             // lane blended is skipped (its updates would be the identity)
             if (!act) continue;
-            float g[kG] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float sgq = 0.f;
+            // per-record sums over the thread's pairs, packed (one horizontal
+            // add per entry): dL/dq / ln 2 and its dy, dy^2 moments, dL/do,
+            // dL/dcolour
+            float2 s_gq = make_float2(0.f, 0.f), s_dy = s_gq, s_dy2 = s_gq, s_op = s_gq, s_c0 = s_gq,
+                   s_c1 = s_gq, s_c2 = s_gq;
 #pragma unroll
             for (int p = 0; p < PP; ++p) {
                 if (!actp[p]) continue;
                 const float2 ae = make_float2(ea[p] ? al[p].x : 0.f, eb[p] ? al[p].y : 0.f);
-                const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
+                const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-ae.x, -ae.y));
                 const float2 rr = make_float2(rcp_approx(om.x), rcp_approx(om.y));
                 const float2 Ti = make_float2(ea[p] ? T[p].x * rr.x : T[p].x, eb[p] ? T[p].y * rr.y : T[p].y);
                 // colour: dI/dc = alpha T_i
                 const float2 wgt = __fmul2_rn(ae, Ti);
-                const float2 c0 = __fmul2_rn(wgt, gI0[p]), c1 = __fmul2_rn(wgt, gI1[p]),
-                             c2 = __fmul2_rn(wgt, gI2[p]);
+                s_c0 = __ffma2_rn(wgt, gI0[p], s_c0);
+                s_c1 = __ffma2_rn(wgt, gI1[p], s_c1);
+                s_c2 = __ffma2_rn(wgt, gI2[p], s_c2);
                 // dL/dalpha = T_i (gI . (c - B)) - dL/dT T_final / (1 - alpha)
-                float2 sdot = __fmul2_rn(gI0[p], __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0[p].x, -B0[p].y)));
-                sdot = __ffma2_rn(gI1[p], __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1[p].x, -B1[p].y)), sdot);
-                sdot = __ffma2_rn(gI2[p], __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2[p].x, -B2[p].y)), sdot);
-                float2 dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, __fmul2_rn(Ti, sdot));
-                dLda = make_float2(ea[p] ? dLda.x : 0.f, eb[p] ? dLda.y : 0.f);
-                // through alpha = o 2^q when not clamped at 0.99
-                const float2 dLa_u = make_float2(araw[p].x < kAlphaMax ? dLda.x : 0.f,
-                                                 araw[p].y < kAlphaMax ? dLda.y : 0.f);
-                const float2 gq = __fmul2_rn(__fmul2_rn(dLa_u, araw[p]), make_float2(kLn2, kLn2));   // dL/dq
+                const float2 d0 = __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0[p].x, -B0[p].y));
+                const float2 d1 = __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1[p].x, -B1[p].y));
+                const float2 d2 = __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2[p].x, -B2[p].y));
+                float2 sdot = __fmul2_rn(gI0[p], d0);
+                sdot = __ffma2_rn(gI1[p], d1, sdot);
+                sdot = __ffma2_rn(gI2[p], d2, sdot);
+                const float2 dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, __fmul2_rn(Ti, sdot));
+                // through alpha = o 2^q where blended and not clamped at 0.99
+                const float2 dLa_u = make_float2(ea[p] && araw[p].x < kAlphaMax ? dLda.x : 0.f,
+                                                 eb[p] && araw[p].y < kAlphaMax ? dLda.y : 0.f);
                 // the pixel-space moments of dL/dq (the mean and conic
                 // gradients follow per record from them: dq/dmean = -2K conic
                 // (dx, dy), dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared
-                // by the thread's pixels
+                // by the thread's pixels.  dL/dq = ln 2 alpha dL/dalpha: the
+                // factor ln 2 is applied once per record in the projection
+                // backward
+                const float2 gq = __fmul2_rn(dLa_u, araw[p]);
                 const float2 gqdy = __fmul2_rn(gq, dy[p]);
-                const float2 gqdy2 = __fmul2_rn(gqdy, dy[p]);
-                const float2 pg = __fmul2_rn(dLa_u, G[p]);
-                sgq += gq.x + gq.y;
-                g[1] += gqdy.x + gqdy.y;
-                g[4] += gqdy2.x + gqdy2.y;
-                g[5] += pg.x + pg.y;
-                g[6] += c0.x + c0.y;
-                g[7] += c1.x + c1.y;
-                g[8] += c2.x + c2.y;
-                // colour behind the previous Gaussian (normalised), then T_i
-                B0[p] = __ffma2_rn(ae, make_float2(c.x, c.x), __fmul2_rn(om, B0[p]));
-                B1[p] = __ffma2_rn(ae, make_float2(c.y, c.y), __fmul2_rn(om, B1[p]));
-                B2[p] = __ffma2_rn(ae, make_float2(c.z, c.z), __fmul2_rn(om, B2[p]));
+                s_gq = __fadd2_rn(s_gq, gq);
+                s_dy = __fadd2_rn(s_dy, gqdy);
+                s_dy2 = __ffma2_rn(gqdy, dy[p], s_dy2);
+                s_op = __ffma2_rn(dLa_u, G[p], s_op);
+                // colour behind the previous Gaussian (normalised):
+                // alpha c + (1 - alpha) B = B + alpha (c - B); then T_i
+                B0[p] = __ffma2_rn(ae, d0, B0[p]);
+                B1[p] = __ffma2_rn(ae, d1, B1[p]);
+                B2[p] = __ffma2_rn(ae, d2, B2[p]);
                 T[p] = Ti;
             }
+            float g[kG];
+            const float sgq = s_gq.x + s_gq.y;
+            g[1] = s_dy.x + s_dy.y;
+            g[4] = s_dy2.x + s_dy2.y;
+            g[5] = s_op.x + s_op.y;
+            g[6] = s_c0.x + s_c0.y;
+            g[7] = s_c1.x + s_c1.y;
+            g[8] = s_c2.x + s_c2.y;
             g[0] = qc.dx * sgq;                                           // sum gq dx
             g[2] = qc.dx * g[0];                                          // sum gq dx^2
             g[3] = qc.dx * g[1];                                          // sum gq dx dy
@@ -301,10 +313,11 @@ __device__ __forceinline__ bool blend_bwd_tile(
     // memory is released
     ok = __syncthreads_and(ok);
     if (!ok && t == 0) {
-        for (uint32_t r = consumed; r < issued; ++r) mbar_wait(&s_bar[r & 1], (ph[r & 1] + (r >> 1)) & 1u);
+        for (uint32_t r = consumed; r < issued; ++r)
+            mbar_wait(&s_bar[r & 1], (((r & 1) ? ph1 : ph0) + (r >> 1)) & 1u);
     }
-    ph[0] += (issued + 1) >> 1;                      // rounds 0, 2, 4, ... used barrier 0
-    ph[1] += issued >> 1;
+    ph0 += (issued + 1) >> 1;                        // rounds 0, 2, 4, ... used barrier 0
+    ph1 += issued >> 1;
     return ok;
 }
 
@@ -333,24 +346,24 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         mbar_init(&s_bar[1], 1);
         mbar_fence_init();
     }
-    uint32_t ph[2] = {0u, 0u};
-    if (!PERSIST) {
+    uint32_t ph0 = 0u, ph1 = 0u;
+    if constexpr (!PERSIST) {
         __syncthreads();                              // barriers initialised
         blend_bwd_tile<TW, TH, PP>(blockIdx.x, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
                                    last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
-                                   s_hi, ph);
-        return;
-    }
-    for (;;) {
-        __syncthreads();                              // the previous tile's shared reads are done
-        if (t == 0) s_tile = (int)atomicAdd(work, 1u);
-        __syncthreads();
-        const int gt = s_tile;
-        if (gt >= vt.total_tiles) return;
-        if (!blend_bwd_tile<TW, TH, PP>(gt, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
-                                        last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
-                                        s_hi, ph))
-            return;                                   // a wait timed out: phases unknown, stop claiming
+                                   s_hi, ph0, ph1);
+    } else {
+        for (;;) {
+            __syncthreads();                              // the previous tile's shared reads are done
+            if (t == 0) s_tile = (int)atomicAdd(work, 1u);
+            __syncthreads();
+            const int gt = s_tile;
+            if (gt >= vt.total_tiles) return;
+            if (!blend_bwd_tile<TW, TH, PP>(gt, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
+                                            last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
+                                            s_hi, ph0, ph1))
+                return;                                   // a wait timed out: phases unknown, stop claiming
+        }
     }
 }
 
@@ -587,6 +600,9 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
             g[q] = gg[q];
             any |= g[q] != 0.f;
         }
+        // the replay sums the moments of dL/dq / ln 2 (q = K d^2, alpha = o 2^q)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) g[q] *= kLn2;
         // a record with gradient was blended, so the forward kept it (its
         // FP64-rounded depth passed the near plane); the Jacobian only needs
         // the view position to FP32 accuracy, so it is recomputed in FP32

@@ -27,12 +27,13 @@ namespace hm {
 
 namespace {
 
-// One tile: the whole Eq. 2 walk of its pixels.  ph[b] counts the phases of
-// barrier b completed before this tile (the wait parity of round r is
-// (ph[r & 1] + r / 2) & 1); every round issued here is waited for before the
-// return, so the counts stay exact.  Returns false (block-uniform) after a
-// timed-out wait: the barriers' phases are then unknown.
-template <int TW, int TH, bool COUNT>
+// One tile: the whole Eq. 2 walk of its pixels.  ph0 / ph1 count the phases
+// of barrier 0 / 1 completed before this tile (the wait parity of round r is
+// (ph_{r & 1} + r / 2) & 1); every round issued here is waited for before the
+// return, so the counts stay exact.  With PERSIST, returns false
+// (block-uniform) after a timed-out wait: the barriers' phases are then
+// unknown and the CTA claims no more tiles.
+template <int TW, int TH, bool COUNT, bool PERSIST>
 __device__ __forceinline__ bool blend_fwd_tile(
     const int gt, const ViewTable &vt, const Record *__restrict__ rec, uint32_t n_rec,
     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
@@ -40,7 +41,7 @@ __device__ __forceinline__ bool blend_fwd_tile(
     float bg2, int batch, float *__restrict__ out_rgb, float *__restrict__ out_T,
     uint32_t *__restrict__ n_contrib, uint32_t *__restrict__ last_idx,
     unsigned long long *__restrict__ eval_stats, int32_t *__restrict__ d_status,
-    Record (*s_rec)[TW * TH], uint64_t *s_bar, int &s_timeout, uint32_t *ph) {
+    Record (*s_rec)[TW * TH], uint64_t *s_bar, int &s_timeout, uint32_t &ph0, uint32_t &ph1) {
     constexpr int NT = TW * TH, NTH = NT / 2;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -54,7 +55,7 @@ __device__ __forceinline__ bool blend_fwd_tile(
     const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
     const uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
     const uint32_t n_rounds = end > begin ? (end - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
-    auto parity = [&](uint32_t r) { return (ph[r & 1] + (r >> 1)) & 1u; };
+    auto parity = [&](uint32_t r) { return (((r & 1) ? ph1 : ph0) + (r >> 1)) & 1u; };
     if (t == 0) s_timeout = 0;                        // published by the barrier before the first issue
     // record indices of the next round to issue (entries t and t + NTH)
     uint32_t nxt0 = 0, nxt1 = 0;
@@ -166,8 +167,8 @@ __device__ __forceinline__ bool blend_fwd_tile(
                 drained = false;
             }
     }
-    ph[0] += (issued + 1) >> 1;                      // rounds 0, 2, 4, ... used barrier 0
-    ph[1] += issued >> 1;
+    ph0 += (issued + 1) >> 1;                        // rounds 0, 2, 4, ... used barrier 0
+    ph1 += issued >> 1;
     const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
     float *o = out_rgb + 3 * V.pix_off;
     if (in_a) {
@@ -198,7 +199,8 @@ __device__ __forceinline__ bool blend_fwd_tile(
             atomicAdd(eval_stats + 1, x);
         }
     }
-    return __syncthreads_and(all_landed && drained);
+    if constexpr (PERSIST) return __syncthreads_and(all_landed && drained);
+    return true;
 }
 
 // Grid launch (PERSIST false): one CTA per tile.  Persistent launch: a grid
@@ -224,24 +226,24 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         mbar_init(&s_bar[1], 1);
         mbar_fence_init();
     }
-    uint32_t ph[2] = {0u, 0u};
-    if (!PERSIST) {
+    uint32_t ph0 = 0u, ph1 = 0u;
+    if constexpr (!PERSIST) {
         __syncthreads();                              // barriers initialised
-        blend_fwd_tile<TW, TH, COUNT>(blockIdx.x, vt, rec, n_rec, vals, ranges, mesh_depth, mesh_rgb, bg0, bg1,
-                                      bg2, batch, out_rgb, out_T, n_contrib, last_idx, eval_stats, d_status,
-                                      s_rec, s_bar, s_timeout, ph);
-        return;
-    }
-    for (;;) {
-        __syncthreads();                              // the previous tile's shared reads are done
-        if (t == 0) s_tile = (int)atomicAdd(work, 1u);
-        __syncthreads();
-        const int gt = s_tile;
-        if (gt >= vt.total_tiles) return;
-        if (!blend_fwd_tile<TW, TH, COUNT>(gt, vt, rec, n_rec, vals, ranges, mesh_depth, mesh_rgb, bg0, bg1, bg2,
-                                           batch, out_rgb, out_T, n_contrib, last_idx, eval_stats, d_status,
-                                           s_rec, s_bar, s_timeout, ph))
-            return;                                   // a wait timed out: phases unknown, stop claiming
+        blend_fwd_tile<TW, TH, COUNT, false>(blockIdx.x, vt, rec, n_rec, vals, ranges, mesh_depth, mesh_rgb, bg0,
+                                             bg1, bg2, batch, out_rgb, out_T, n_contrib, last_idx, eval_stats,
+                                             d_status, s_rec, s_bar, s_timeout, ph0, ph1);
+    } else {
+        for (;;) {
+            __syncthreads();                              // the previous tile's shared reads are done
+            if (t == 0) s_tile = (int)atomicAdd(work, 1u);
+            __syncthreads();
+            const int gt = s_tile;
+            if (gt >= vt.total_tiles) return;
+            if (!blend_fwd_tile<TW, TH, COUNT, true>(gt, vt, rec, n_rec, vals, ranges, mesh_depth, mesh_rgb, bg0,
+                                                     bg1, bg2, batch, out_rgb, out_T, n_contrib, last_idx,
+                                                     eval_stats, d_status, s_rec, s_bar, s_timeout, ph0, ph1))
+                return;                                   // a wait timed out: phases unknown, stop claiming
+        }
     }
 }
 
