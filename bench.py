@@ -53,11 +53,13 @@ WORKLOAD = ("indoor room 1920x1080 x 8 poses, 300k Gaussians SH3, 50k-triangle r
 #   moment products and of the warp reduction 4 = 58 (+ ex2 and rcp).
 SURVEY_FLOPS = {"blend_forward": 12, "blend_backward": 40}
 SOURCE_FLOPS = {"blend_forward": 25, "blend_backward": 58}
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# `ncu --set full` capture of this workload (8 views, 16x16 tiles), with the
-# sources the kernel was built from: a figure is reported only while those
-# sources hash to the recorded value, i.e. while the kernel is the one that
-# was measured (profiles/*_room1080p_8views.md hold the captures)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp
+# instructions (smsp__inst_executed.sum) of one launch of each blend kernel,
+# from an ncu capture of 3 of the 8 views (profiles/blend_*_kernel_room1080p_3views.md)
+# with the sources the kernel was built from.  A full launch's figure is the
+# capture scaled by the live workload: instructions by the kernel's units
+# (evaluated pairs forward, blended pairs backward), traffic by pixels.  A
+# figure is reported only while the sources hash to the recorded value.
 KERNEL_SOURCES = {
     "blend_forward": ("blend_fwd.cu", "blend_common.cuh", "hm_internal.cuh", "tma.cuh"),
     "blend_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh", "tma.cuh"),
@@ -65,28 +67,11 @@ KERNEL_SOURCES = {
     "project_backward": ("blend_bwd.cu", "blend_common.cuh", "hm_internal.cuh", "sh.cuh", "tma.cuh"),
     "project": ("project.cu", "sh.cuh", "hm_internal.cuh"),
 }
-NCU_TRAFFIC = {
-    "blend_forward": (651_455_744, "2887610f3b398375"),
-    "blend_backward": (566_773_248, "d5751a32ff776980"),
+NCU_CAPTURE = {
+    # stage: (warp instructions, DRAM bytes, units, unit kind, pixels, source hash)
+    "blend_forward": (202_430_460, 219_206_912, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "38b741871cc74f09"),
+    "blend_backward": (294_419_167, 212_150_272, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "7631cfebd213ff54"),
 }
-# warp instructions per launch (smsp__inst_executed.sum) of the same kind of
-# capture, for the issue-slot roofline of the ALU-bound blend kernels (same
-# source-hash rule as NCU_TRAFFIC; scaled from the capture's views to 8)
-NCU_INST = {}
-
-
-def _traffic(stage, views, tile):
-    """Measured DRAM bytes per launch, or None when the kernel's sources or
-    the workload differ from the captured ones."""
-    import hashlib
-    if stage not in NCU_TRAFFIC or views != 8 or tuple(tile) != (16, 16):
-        return None
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES[stage]:
-        with open(os.path.join(ROOT, "paper_2506_06988_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    nbytes, digest = NCU_TRAFFIC[stage]
-    return nbytes if h.hexdigest()[:16] == digest else None
 
 
 def _source_hash(stage):
@@ -98,12 +83,16 @@ def _source_hash(stage):
     return h.hexdigest()[:16]
 
 
-def _warp_inst(stage, views, tile):
-    """Warp instructions per launch from the committed capture, or None."""
-    if stage not in NCU_INST or tuple(tile) != (16, 16):
-        return None
-    inst, cap_views, digest = NCU_INST[stage]
-    return inst * views / cap_views if _source_hash(stage) == digest else None
+def _captured(stage, tile, units, pixels):
+    """(warp instructions, DRAM bytes) of one launch scaled from the
+    committed capture, or (None, None) when the kernel's sources or tile
+    shape differ from the captured ones."""
+    if stage not in NCU_CAPTURE or tuple(tile) != (16, 16):
+        return None, None
+    inst, dram, cap_units, kind, cap_px, digest = NCU_CAPTURE[stage]
+    if _source_hash(stage) != digest:
+        return None, None
+    return inst * units[kind] / cap_units, dram * pixels / cap_px
 
 
 KERNELS_PER_STEP = {"rasterize_mesh": 6, "project": 1, "bin_sort": 8, "blend_forward": 1,
@@ -494,7 +483,9 @@ def run_ours(args):
                                                     "unit_kind": ("evaluated pairs" if st_name == "blend_forward"
                                                                   else "blended pairs"),
                                                     "achieved": src, "frac": src / fp32_peak}}
-            wi = _warp_inst(st_name, V, tile)
+            wi, dram = _captured(st_name, tile, {"evaluated_pairs": n_eval, "blended_pairs": n_blended},
+                                 r.npix)
+            per_kernel[st_name]["traffic"] = dram
             per_kernel[st_name]["issue"] = (
                 {"warp_inst_per_launch": wi, "achieved_ginst_s": wi / t / 1e9, "peak_ginst_s": issue_peak,
                  "frac": wi / t / 1e9 / issue_peak,
@@ -507,20 +498,22 @@ def run_ours(args):
                                    "unit_kind": what, "ms": stage_ms[st_name]}
     for st_name, e in per_kernel.items():
         # DRAM bytes read + written per launch from the committed ncu capture
-        # (None when that kernel's sources or the workload differ from it)
-        e["traffic"] = _traffic(st_name, V, tile)
+        # (None when that kernel's sources differ from the captured ones)
+        e.setdefault("traffic", None)
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     roof = dict(per_kernel[dom])
-    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
-                              "(profiles/blend_kernels_room1080p_8views.md)")
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 3 of the 8 "
+                              "views, scaled by pixels (profiles/blend_*_kernel_room1080p_3views.md)")
+    roof["time_source"] = ("CUDA events around the kernel's library call in the eager step (the backward's "
+                           "includes the zeroing of its per-record partial sums)")
     roof["peak_source"] = (f"FP32: {nsm} SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (unit counts x max clock)"
                            if roof["bound"] == "alu" else f"HBM copy bandwidth, {peak_kind}")
     if roof["bound"] == "alu" and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = roof["achieved"] / (nsm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
-    # count (record read, mask write), emit (mask + record read), per pair the
-    # 8-B key written and read back and the 4-B index written, per tile the
-    # counts, offsets and ranges
-    sort_bytes = M * (48 + 4) * 2 + npairs * (8 + 8 + 4) + r.ntiles * 16
+    # count and emit each read every record (48 B); per pair the 8-B key
+    # written and read back and the 4-B index written; per tile the counts,
+    # offsets and ranges
+    sort_bytes = M * 48 * 2 + npairs * (8 + 8 + 4) + r.ntiles * 16
     stage_roof = {"bin_sort": {"bytes": sort_bytes, "GB/s": sort_bytes / (stage_ms["bin_sort"] * 1e-3) / 1e9}}
     stage_roof["bin_sort"]["frac_of_hbm"] = stage_roof["bin_sort"]["GB/s"] / hbm
     # the mesh pass: per pixel the 28-B G-buffer (tri_id, depth, colour, UV)

@@ -126,13 +126,13 @@ const char *hm_last_error(void);
  * FP64, snapped to 1/256 px, exact integer edge functions, top-left fill
  * rule; faces with a vertex at z <= near_mesh or beyond +-2^21 px culled),
  * its view depth D_m (the view z of the snapped face at the pixel centre).
- * 1/z is affine in screen space; it is evaluated in FP32 as
- * fma(a, U, fma(b, V, 1/z0)), (U,V) the pixel centre minus the snapped
+ * 1/z is affine in screen space; the depth is evaluated in FP32 as
+ * 1 / fma(a, U, fma(b, V, 1/z0)), (U,V) the pixel centre minus the snapped
  * vertex 0 in pixels and a, b, 1/z0 the face's coefficients computed in
- * FP64 and rounded once to FP32; the largest FP32 1/z wins (ties to the
- * lower face index) and D_m is its FP32 reciprocal -- within a few FP32
- * ulps of the FP64 depth (the band is 3 + 3 kappa ulps, kappa the condition
- * number of that evaluation); perspective-correct UVs and a bilinear,
+ * FP64 and rounded once to FP32 (nearest FP32 depth wins, ties to the lower
+ * face index) -- within a few FP32 ulps of the FP64 depth (the band is
+ * 3 + 3 kappa ulps, kappa the condition number of that evaluation);
+ * perspective-correct UVs and a bilinear,
  * clamp-to-edge texture fetch (texel centres at half-integers, row 0 at v=0).
  *
  *  verts [n_verts][3], uvs [n_verts][2] float32; faces [n_faces][3] int32.

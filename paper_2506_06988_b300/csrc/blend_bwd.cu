@@ -75,252 +75,6 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
 // PP = 2 a thread holds two pairs of one column: the column part of q and
 // the warp reduction of the nine partials are shared by four pixels.  The
 // staged records live in dynamic shared memory sized by the batch.
-// One tile's replay.  ph0 / ph1 count the phases of barrier 0 / 1 completed
-// before this tile (the wait parity of round r is (ph_{r & 1} + r / 2) & 1);
-// every round issued here is waited for before the return.  Returns false
-// (block-uniform) after a timed-out wait.
-template <int TW, int TH, int PP>
-__device__ __forceinline__ bool blend_bwd_tile(
-    const int gt, const ViewTable &vt, const Record *__restrict__ rec, uint32_t n_rec,
-    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-    const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2, const float *__restrict__ out_T,
-    const uint32_t *__restrict__ last_idx, const float *__restrict__ dL_drgb,
-    const float *__restrict__ dL_dT, int batch, float *__restrict__ g2d, int32_t *__restrict__ d_status,
-    Record *s_rec0, uint32_t *s_item0, uint64_t *s_bar, uint32_t &s_hi, uint32_t &ph0, uint32_t &ph1) {
-    constexpr int NTH = TW * TH / (2 * PP);
-    constexpr int PER = (TW * TH + NTH - 1) / NTH;       // staged records per thread and round, at most
-    const int v = view_of_tile(vt, gt);
-    const ViewDev &V = vt.v[v];
-    const int local = gt - V.tile_off;
-    const int tx = local % V.tiles_x, ty = local / V.tiles_x;
-    const int t = threadIdx.x, lane = t & 31;
-    constexpr int WX = TW / 8;
-    const int px = tx * TW + ((t >> 5) % WX) * 8 + (lane & 7);
-    const int row0 = ty * TH + ((t >> 5) / WX) * (8 * PP) + (lane >> 3);
-    const long long npx = (long long)V.W * V.H;
-    const float *gI = dL_drgb + 3 * V.pix_off;
-    const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
-    float2 Tf[PP], gI0[PP], gI1[PP], gI2[PP], gT[PP], B0[PP], B1[PP], B2[PP], fpy[PP];
-    uint32_t la[PP], lb[PP];
-    uint32_t my_hi = 0;
-#pragma unroll
-    for (int p = 0; p < PP; ++p) {
-        const int pya = row0 + 8 * p, pyb = pya + 4;
-        const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
-        const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
-        Tf[p] = make_float2(1.f, 1.f);
-        gI0[p] = gI1[p] = gI2[p] = gT[p] = make_float2(0.f, 0.f);
-        B0[p] = make_float2(bg0, bg0);
-        B1[p] = make_float2(bg1, bg1);
-        B2[p] = make_float2(bg2, bg2);
-        la[p] = lb[p] = 0;
-        fpy[p] = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
-        if (in_a) {
-            Tf[p].x = out_T[V.pix_off + lpa];
-            la[p] = last_idx[V.pix_off + lpa];
-            gI0[p].x = gI[lpa]; gI1[p].x = gI[npx + lpa]; gI2[p].x = gI[2 * npx + lpa];
-            if (dL_dT) gT[p].x = dL_dT[V.pix_off + lpa];
-            if (mr) { B0[p].x = mr[lpa]; B1[p].x = mr[npx + lpa]; B2[p].x = mr[2 * npx + lpa]; }
-        }
-        if (in_b) {
-            Tf[p].y = out_T[V.pix_off + lpb];
-            lb[p] = last_idx[V.pix_off + lpb];
-            gI0[p].y = gI[lpb]; gI1[p].y = gI[npx + lpb]; gI2[p].y = gI[2 * npx + lpb];
-            if (dL_dT) gT[p].y = dL_dT[V.pix_off + lpb];
-            if (mr) { B0[p].y = mr[lpb]; B1[p].y = mr[npx + lpb]; B2[p].y = mr[2 * npx + lpb]; }
-        }
-        my_hi = max(my_hi, max(la[p], lb[p]));
-    }
-    const uint32_t begin = ranges[2 * gt];
-    if (t == 0) s_hi = 0;
-    __syncthreads();
-    if (my_hi > 0) atomicMax(&s_hi, my_hi);
-    __syncthreads();
-    const uint32_t hi_all = s_hi;
-    // rounds walk the list back to front: round r covers [lo_r, hi_r) with
-    // hi_r = hi_all - r batch, lo_r = max(begin, hi_r - batch)
-    const uint32_t n_rounds = hi_all > begin ? (hi_all - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
-    uint32_t nxt[PER];
-#pragma unroll
-    for (int e = 0; e < PER; ++e) nxt[e] = 0;
-    auto round_lo = [&](uint32_t r, uint32_t &lo, uint32_t &nb) {
-        const uint32_t hi = hi_all - r * (uint32_t)batch;
-        lo = hi - begin > (uint32_t)batch ? hi - (uint32_t)batch : begin;
-        nb = hi - lo;
-    };
-    auto load_idx = [&](uint32_t r) {
-        uint32_t lo, nb;
-        round_lo(r, lo, nb);
-#pragma unroll
-        for (int e = 0; e < PER; ++e)
-            if ((uint32_t)(t + e * NTH) < nb) nxt[e] = vals[lo + t + e * NTH];
-    };
-    auto issue = [&](uint32_t r) {
-        const int buf = r & 1;
-        uint32_t lo, nb;
-        round_lo(r, lo, nb);
-        if (t == 0) mbar_arrive_expect_tx(&s_bar[buf], nb * (uint32_t)sizeof(Record));
-#pragma unroll
-        for (int e = 0; e < PER; ++e) {
-            const uint32_t k = (uint32_t)(t + e * NTH);
-            if (k < nb) {
-                uint32_t it = nxt[e];
-                if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
-                s_item0[buf * batch + k] = it;
-                bulk_g2s(&s_rec0[buf * batch + k], rec + it, sizeof(Record), &s_bar[buf]);
-            }
-        }
-    };
-    if (n_rounds > 0) {
-        load_idx(0);
-        issue(0);
-    }
-    if (n_rounds > 1) load_idx(1);
-    const float fpx = (float)px + 0.5f;
-    float2 T[PP], gTT[PP];
-#pragma unroll
-    for (int p = 0; p < PP; ++p) {
-        T[p] = Tf[p];
-        gTT[p] = __fmul2_rn(gT[p], Tf[p]);
-    }
-    bool ok = true;
-    // rounds [consumed, issued) have copies that may still be in flight
-    uint32_t issued = n_rounds > 0 ? 1u : 0u, consumed = 0;
-    for (uint32_t r = 0; r < n_rounds; ++r) {
-        // ends every thread's use of round r - 1, whose buffers round r + 1
-        // refills, and publishes round r's record indices; after a timed-out
-        // wait anywhere in the CTA nothing more is issued
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        if (r + 1 < n_rounds) {
-            issue(r + 1);
-            issued = r + 2;
-            if (r + 2 < n_rounds) load_idx(r + 2);
-        }
-        const int buf = r & 1;
-        if (!mbar_wait(&s_bar[buf], ((buf ? ph1 : ph0) + (r >> 1)) & 1u)) {
-            set_status(d_status, HM_DEV_TIMEOUT);
-            ok = false;
-        }
-        ok = __all_sync(0xffffffffu, ok);   // the replay below uses warp shuffles
-        if (ok) consumed = r + 1;
-        uint32_t lo, nb_u;
-        round_lo(r, lo, nb_u);
-        const int nb = ok ? (int)nb_u : 0;
-        const Record *sr = s_rec0 + buf * batch;
-        const uint32_t *si = s_item0 + buf * batch;
-        for (int k = nb - 1; k >= 0; --k) {
-            const uint32_t j = lo + k;
-            bool ea[PP], eb[PP];
-            bool act = false;
-#pragma unroll
-            for (int p = 0; p < PP; ++p) {
-                ea[p] = j < la[p];
-                eb[p] = j < lb[p];
-                act = act || ea[p] || eb[p];
-            }
-            if (!__any_sync(0xffffffffu, act)) continue;
-            const float4 A = sr[k].a, Bs = sr[k].b, c = sr[k].c;
-            const QCol qc = eval_qcol(A, fpx);
-            float2 dy[PP], G[PP], araw[PP], al[PP];
-            bool actp[PP];
-            act = false;
-#pragma unroll
-            for (int p = 0; p < PP; ++p) {
-                const float2 q = eval_qrows(A, Bs, qc, fpy[p], dy[p]);
-                ea[p] = ea[p] && q.x >= kQ3;
-                eb[p] = eb[p] && q.y >= kQ3;
-                al[p] = eval_alpha2(Bs.y, q, G[p], araw[p]);
-                ea[p] = ea[p] && al[p].x >= kAlphaMin;        // the forward blended it
-                eb[p] = eb[p] && al[p].y >= kAlphaMin;
-                // pair p of some lane blended it (warp-uniform)
-                actp[p] = __any_sync(0xffffffffu, ea[p] || eb[p]);
-                act = act || actp[p];
-            }
-            // entries the forward blended at none of the warp's pixels need no
-            // gradient math and no reduction; within an entry, a pair row no
-            // lane blended is skipped (its updates would be the identity)
-            if (!act) continue;
-            // per-record sums over the thread's pairs, packed (one horizontal
-            // add per entry): dL/dq / ln 2 and its dy, dy^2 moments, dL/do,
-            // dL/dcolour
-            float2 s_gq = make_float2(0.f, 0.f), s_dy = s_gq, s_dy2 = s_gq, s_op = s_gq, s_c0 = s_gq,
-                   s_c1 = s_gq, s_c2 = s_gq;
-#pragma unroll
-            for (int p = 0; p < PP; ++p) {
-                if (!actp[p]) continue;
-                const float2 ae = make_float2(ea[p] ? al[p].x : 0.f, eb[p] ? al[p].y : 0.f);
-                const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-ae.x, -ae.y));
-                const float2 rr = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-                const float2 Ti = make_float2(ea[p] ? T[p].x * rr.x : T[p].x, eb[p] ? T[p].y * rr.y : T[p].y);
-                // colour: dI/dc = alpha T_i
-                const float2 wgt = __fmul2_rn(ae, Ti);
-                s_c0 = __ffma2_rn(wgt, gI0[p], s_c0);
-                s_c1 = __ffma2_rn(wgt, gI1[p], s_c1);
-                s_c2 = __ffma2_rn(wgt, gI2[p], s_c2);
-                // dL/dalpha = T_i (gI . (c - B)) - dL/dT T_final / (1 - alpha)
-                const float2 d0 = __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0[p].x, -B0[p].y));
-                const float2 d1 = __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1[p].x, -B1[p].y));
-                const float2 d2 = __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2[p].x, -B2[p].y));
-                float2 sdot = __fmul2_rn(gI0[p], d0);
-                sdot = __ffma2_rn(gI1[p], d1, sdot);
-                sdot = __ffma2_rn(gI2[p], d2, sdot);
-                const float2 dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, __fmul2_rn(Ti, sdot));
-                // through alpha = o 2^q where blended and not clamped at 0.99
-                const float2 dLa_u = make_float2(ea[p] && araw[p].x < kAlphaMax ? dLda.x : 0.f,
-                                                 eb[p] && araw[p].y < kAlphaMax ? dLda.y : 0.f);
-                // the pixel-space moments of dL/dq (the mean and conic
-                // gradients follow per record from them: dq/dmean = -2K conic
-                // (dx, dy), dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared
-                // by the thread's pixels.  dL/dq = ln 2 alpha dL/dalpha: the
-                // factor ln 2 is applied once per record in the projection
-                // backward
-                const float2 gq = __fmul2_rn(dLa_u, araw[p]);
-                const float2 gqdy = __fmul2_rn(gq, dy[p]);
-                s_gq = __fadd2_rn(s_gq, gq);
-                s_dy = __fadd2_rn(s_dy, gqdy);
-                s_dy2 = __ffma2_rn(gqdy, dy[p], s_dy2);
-                s_op = __ffma2_rn(dLa_u, G[p], s_op);
-                // colour behind the previous Gaussian (normalised):
-                // alpha c + (1 - alpha) B = B + alpha (c - B); then T_i
-                B0[p] = __ffma2_rn(ae, d0, B0[p]);
-                B1[p] = __ffma2_rn(ae, d1, B1[p]);
-                B2[p] = __ffma2_rn(ae, d2, B2[p]);
-                T[p] = Ti;
-            }
-            float g[kG];
-            const float sgq = s_gq.x + s_gq.y;
-            g[1] = s_dy.x + s_dy.y;
-            g[4] = s_dy2.x + s_dy2.y;
-            g[5] = s_op.x + s_op.y;
-            g[6] = s_c0.x + s_c0.y;
-            g[7] = s_c1.x + s_c1.y;
-            g[8] = s_c2.x + s_c2.y;
-            g[0] = qc.dx * sgq;                                           // sum gq dx
-            g[2] = qc.dx * g[0];                                          // sum gq dx^2
-            g[3] = qc.dx * g[1];                                          // sum gq dx dy
-            float *dst = g2d + (size_t)si[k] * kG;
-            const float y = warp_sum8(g, lane);
-            float z = g[8];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-            if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
-            if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
-        }
-    }
-    // after a timed-out wait, every copy issued and not yet waited for must
-    // land (bounded waits) before the buffers are reused or the CTA's shared
-    // memory is released
-    ok = __syncthreads_and(ok);
-    if (!ok && t == 0) {
-        for (uint32_t r = consumed; r < issued; ++r)
-            mbar_wait(&s_bar[r & 1], (((r & 1) ? ph1 : ph0) + (r >> 1)) & 1u);
-    }
-    ph0 += (issued + 1) >> 1;                        // rounds 0, 2, 4, ... used barrier 0
-    ph1 += issued >> 1;
-    return ok;
-}
-
 // Grid launch (PERSIST false): one CTA per tile.  Persistent launch: a grid
 // of resident CTAs that claim tiles of all views from the counter `work`
 // (zeroed before the launch) until none is left; a claim is one atomic on a
@@ -340,33 +94,264 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     __shared__ uint64_t s_bar[2];
     __shared__ uint32_t s_hi;
     __shared__ int s_tile;
-    const int t = threadIdx.x;
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         mbar_fence_init();
     }
     uint32_t ph0 = 0u, ph1 = 0u;
+    // One tile's replay.  ph0 / ph1 count the phases of barrier 0 / 1 completed
+    // before this tile (the wait parity of round r is (ph_{r & 1} + r / 2) & 1);
+    // every round issued here is waited for before the return.  Returns false
+    // (block-uniform) after a timed-out wait.
+    auto replay_tile = [&](const int gt) -> bool {
+        constexpr int NTH = TW * TH / (2 * PP);
+        constexpr int PER = (TW * TH + NTH - 1) / NTH;       // staged records per thread and round, at most
+        const int v = view_of_tile(vt, gt);
+        const ViewDev &V = vt.v[v];
+        const int local = gt - V.tile_off;
+        const int tx = local % V.tiles_x, ty = local / V.tiles_x;
+        const int t = threadIdx.x, lane = t & 31;
+        constexpr int WX = TW / 8;
+        const int px = tx * TW + ((t >> 5) % WX) * 8 + (lane & 7);
+        const int row0 = ty * TH + ((t >> 5) / WX) * (8 * PP) + (lane >> 3);
+        const long long npx = (long long)V.W * V.H;
+        const float *gI = dL_drgb + 3 * V.pix_off;
+        const float *mr = mesh_rgb ? mesh_rgb + 3 * V.pix_off : nullptr;
+        float2 Tf[PP], gI0[PP], gI1[PP], gI2[PP], gT[PP], B0[PP], B1[PP], B2[PP], fpy[PP];
+        uint32_t la[PP], lb[PP];
+        uint32_t my_hi = 0;
+    #pragma unroll
+        for (int p = 0; p < PP; ++p) {
+            const int pya = row0 + 8 * p, pyb = pya + 4;
+            const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
+            const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
+            Tf[p] = make_float2(1.f, 1.f);
+            gI0[p] = gI1[p] = gI2[p] = gT[p] = make_float2(0.f, 0.f);
+            B0[p] = make_float2(bg0, bg0);
+            B1[p] = make_float2(bg1, bg1);
+            B2[p] = make_float2(bg2, bg2);
+            la[p] = lb[p] = 0;
+            fpy[p] = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
+            if (in_a) {
+                Tf[p].x = out_T[V.pix_off + lpa];
+                la[p] = last_idx[V.pix_off + lpa];
+                gI0[p].x = gI[lpa]; gI1[p].x = gI[npx + lpa]; gI2[p].x = gI[2 * npx + lpa];
+                if (dL_dT) gT[p].x = dL_dT[V.pix_off + lpa];
+                if (mr) { B0[p].x = mr[lpa]; B1[p].x = mr[npx + lpa]; B2[p].x = mr[2 * npx + lpa]; }
+            }
+            if (in_b) {
+                Tf[p].y = out_T[V.pix_off + lpb];
+                lb[p] = last_idx[V.pix_off + lpb];
+                gI0[p].y = gI[lpb]; gI1[p].y = gI[npx + lpb]; gI2[p].y = gI[2 * npx + lpb];
+                if (dL_dT) gT[p].y = dL_dT[V.pix_off + lpb];
+                if (mr) { B0[p].y = mr[lpb]; B1[p].y = mr[npx + lpb]; B2[p].y = mr[2 * npx + lpb]; }
+            }
+            my_hi = max(my_hi, max(la[p], lb[p]));
+        }
+        const uint32_t begin = ranges[2 * gt];
+        if (t == 0) s_hi = 0;
+        __syncthreads();
+        if (my_hi > 0) atomicMax(&s_hi, my_hi);
+        __syncthreads();
+        const uint32_t hi_all = s_hi;
+        // rounds walk the list back to front: round r covers [lo_r, hi_r) with
+        // hi_r = hi_all - r batch, lo_r = max(begin, hi_r - batch)
+        const uint32_t n_rounds = hi_all > begin ? (hi_all - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
+        uint32_t nxt[PER];
+    #pragma unroll
+        for (int e = 0; e < PER; ++e) nxt[e] = 0;
+        auto round_lo = [&](uint32_t r, uint32_t &lo, uint32_t &nb) {
+            const uint32_t hi = hi_all - r * (uint32_t)batch;
+            lo = hi - begin > (uint32_t)batch ? hi - (uint32_t)batch : begin;
+            nb = hi - lo;
+        };
+        auto load_idx = [&](uint32_t r) {
+            uint32_t lo, nb;
+            round_lo(r, lo, nb);
+    #pragma unroll
+            for (int e = 0; e < PER; ++e)
+                if ((uint32_t)(t + e * NTH) < nb) nxt[e] = vals[lo + t + e * NTH];
+        };
+        auto issue = [&](uint32_t r) {
+            const int buf = r & 1;
+            uint32_t lo, nb;
+            round_lo(r, lo, nb);
+            if (t == 0) mbar_arrive_expect_tx(&s_bar[buf], nb * (uint32_t)sizeof(Record));
+    #pragma unroll
+            for (int e = 0; e < PER; ++e) {
+                const uint32_t k = (uint32_t)(t + e * NTH);
+                if (k < nb) {
+                    uint32_t it = nxt[e];
+                    if (it >= n_rec) { set_status(d_status, HM_DEV_BAD_INDEX); it = 0; }
+                    s_item0[buf * batch + k] = it;
+                    bulk_g2s(&s_rec0[buf * batch + k], rec + it, sizeof(Record), &s_bar[buf]);
+                }
+            }
+        };
+        if (n_rounds > 0) {
+            load_idx(0);
+            issue(0);
+        }
+        if (n_rounds > 1) load_idx(1);
+        const float fpx = (float)px + 0.5f;
+        float2 T[PP], gTT[PP];
+    #pragma unroll
+        for (int p = 0; p < PP; ++p) {
+            T[p] = Tf[p];
+            gTT[p] = __fmul2_rn(gT[p], Tf[p]);
+        }
+        bool ok = true;
+        // rounds [consumed, issued) have copies that may still be in flight
+        uint32_t issued = n_rounds > 0 ? 1u : 0u, consumed = 0;
+        for (uint32_t r = 0; r < n_rounds; ++r) {
+            // ends every thread's use of round r - 1, whose buffers round r + 1
+            // refills, and publishes round r's record indices; after a timed-out
+            // wait anywhere in the CTA nothing more is issued
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            if (r + 1 < n_rounds) {
+                issue(r + 1);
+                issued = r + 2;
+                if (r + 2 < n_rounds) load_idx(r + 2);
+            }
+            const int buf = r & 1;
+            if (!mbar_wait(&s_bar[buf], ((buf ? ph1 : ph0) + (r >> 1)) & 1u)) {
+                set_status(d_status, HM_DEV_TIMEOUT);
+                ok = false;
+            }
+            ok = __all_sync(0xffffffffu, ok);   // the replay below uses warp shuffles
+            if (ok) consumed = r + 1;
+            uint32_t lo, nb_u;
+            round_lo(r, lo, nb_u);
+            const int nb = ok ? (int)nb_u : 0;
+            const Record *sr = s_rec0 + buf * batch;
+            const uint32_t *si = s_item0 + buf * batch;
+            for (int k = nb - 1; k >= 0; --k) {
+                const uint32_t j = lo + k;
+                bool ea[PP], eb[PP];
+                bool act = false;
+    #pragma unroll
+                for (int p = 0; p < PP; ++p) {
+                    ea[p] = j < la[p];
+                    eb[p] = j < lb[p];
+                    act = act || ea[p] || eb[p];
+                }
+                if (!__any_sync(0xffffffffu, act)) continue;
+                const float4 A = sr[k].a, Bs = sr[k].b, c = sr[k].c;
+                const QCol qc = eval_qcol(A, fpx);
+                float2 dy[PP], G[PP], araw[PP], al[PP];
+                bool actp[PP];
+                act = false;
+    #pragma unroll
+                for (int p = 0; p < PP; ++p) {
+                    const float2 q = eval_qrows(A, Bs, qc, fpy[p], dy[p]);
+                    ea[p] = ea[p] && q.x >= kQ3;
+                    eb[p] = eb[p] && q.y >= kQ3;
+                    al[p] = eval_alpha2(Bs.y, q, G[p], araw[p]);
+                    ea[p] = ea[p] && al[p].x >= kAlphaMin;        // the forward blended it
+                    eb[p] = eb[p] && al[p].y >= kAlphaMin;
+                    // pair p of some lane blended it (warp-uniform)
+                    actp[p] = __any_sync(0xffffffffu, ea[p] || eb[p]);
+                    act = act || actp[p];
+                }
+                // entries the forward blended at none of the warp's pixels need no
+                // gradient math and no reduction; within an entry, a pair row no
+                // lane blended is skipped (its updates would be the identity)
+                if (!act) continue;
+                // per-record sums over the thread's pairs, packed (one horizontal
+                // add per entry): dL/dq / ln 2 and its dy, dy^2 moments, dL/do,
+                // dL/dcolour
+                float2 s_gq = make_float2(0.f, 0.f), s_dy = s_gq, s_dy2 = s_gq, s_op = s_gq, s_c0 = s_gq,
+                       s_c1 = s_gq, s_c2 = s_gq;
+    #pragma unroll
+                for (int p = 0; p < PP; ++p) {
+                    if (!actp[p]) continue;
+                    const float2 ae = make_float2(ea[p] ? al[p].x : 0.f, eb[p] ? al[p].y : 0.f);
+                    const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-ae.x, -ae.y));
+                    const float2 rr = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                    const float2 Ti = make_float2(ea[p] ? T[p].x * rr.x : T[p].x, eb[p] ? T[p].y * rr.y : T[p].y);
+                    // colour: dI/dc = alpha T_i
+                    const float2 wgt = __fmul2_rn(ae, Ti);
+                    s_c0 = __ffma2_rn(wgt, gI0[p], s_c0);
+                    s_c1 = __ffma2_rn(wgt, gI1[p], s_c1);
+                    s_c2 = __ffma2_rn(wgt, gI2[p], s_c2);
+                    // dL/dalpha = T_i (gI . (c - B)) - dL/dT T_final / (1 - alpha)
+                    const float2 d0 = __fadd2_rn(make_float2(c.x, c.x), make_float2(-B0[p].x, -B0[p].y));
+                    const float2 d1 = __fadd2_rn(make_float2(c.y, c.y), make_float2(-B1[p].x, -B1[p].y));
+                    const float2 d2 = __fadd2_rn(make_float2(c.z, c.z), make_float2(-B2[p].x, -B2[p].y));
+                    float2 sdot = __fmul2_rn(gI0[p], d0);
+                    sdot = __ffma2_rn(gI1[p], d1, sdot);
+                    sdot = __ffma2_rn(gI2[p], d2, sdot);
+                    const float2 dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, __fmul2_rn(Ti, sdot));
+                    // through alpha = o 2^q where blended and not clamped at 0.99
+                    const float2 dLa_u = make_float2(ea[p] && araw[p].x < kAlphaMax ? dLda.x : 0.f,
+                                                     eb[p] && araw[p].y < kAlphaMax ? dLda.y : 0.f);
+                    // the pixel-space moments of dL/dq (the mean and conic
+                    // gradients follow per record from them: dq/dmean = -2K conic
+                    // (dx, dy), dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared
+                    // by the thread's pixels.  dL/dq = ln 2 alpha dL/dalpha: the
+                    // factor ln 2 is applied once per record in the projection
+                    // backward
+                    const float2 gq = __fmul2_rn(dLa_u, araw[p]);
+                    const float2 gqdy = __fmul2_rn(gq, dy[p]);
+                    s_gq = __fadd2_rn(s_gq, gq);
+                    s_dy = __fadd2_rn(s_dy, gqdy);
+                    s_dy2 = __ffma2_rn(gqdy, dy[p], s_dy2);
+                    s_op = __ffma2_rn(dLa_u, G[p], s_op);
+                    // colour behind the previous Gaussian (normalised):
+                    // alpha c + (1 - alpha) B = B + alpha (c - B); then T_i
+                    B0[p] = __ffma2_rn(ae, d0, B0[p]);
+                    B1[p] = __ffma2_rn(ae, d1, B1[p]);
+                    B2[p] = __ffma2_rn(ae, d2, B2[p]);
+                    T[p] = Ti;
+                }
+                float g[kG];
+                const float sgq = s_gq.x + s_gq.y;
+                g[1] = s_dy.x + s_dy.y;
+                g[4] = s_dy2.x + s_dy2.y;
+                g[5] = s_op.x + s_op.y;
+                g[6] = s_c0.x + s_c0.y;
+                g[7] = s_c1.x + s_c1.y;
+                g[8] = s_c2.x + s_c2.y;
+                g[0] = qc.dx * sgq;                                           // sum gq dx
+                g[2] = qc.dx * g[0];                                          // sum gq dx^2
+                g[3] = qc.dx * g[1];                                          // sum gq dx dy
+                float *dst = g2d + (size_t)si[k] * kG;
+                const float y = warp_sum8(g, lane);
+                float z = g[8];
+    #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+                if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
+                if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
+            }
+        }
+        // after a timed-out wait, every copy issued and not yet waited for must
+        // land (bounded waits) before the buffers are reused or the CTA's shared
+        // memory is released
+        ok = __syncthreads_and(ok);
+        if (!ok && t == 0) {
+            for (uint32_t r = consumed; r < issued; ++r)
+                mbar_wait(&s_bar[r & 1], (((r & 1) ? ph1 : ph0) + (r >> 1)) & 1u);
+        }
+        ph0 += (issued + 1) >> 1;                        // rounds 0, 2, 4, ... used barrier 0
+        ph1 += issued >> 1;
+        return ok;
+    };
     if constexpr (!PERSIST) {
         __syncthreads();                              // barriers initialised
-        blend_bwd_tile<TW, TH, PP>(blockIdx.x, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
-                                   last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
-                                   s_hi, ph0, ph1);
+        replay_tile(blockIdx.x);
     } else {
         for (;;) {
             __syncthreads();                              // the previous tile's shared reads are done
-            if (t == 0) s_tile = (int)atomicAdd(work, 1u);
+            if (threadIdx.x == 0) s_tile = (int)atomicAdd(work, 1u);
             __syncthreads();
             const int gt = s_tile;
             if (gt >= vt.total_tiles) return;
-            if (!blend_bwd_tile<TW, TH, PP>(gt, vt, rec, n_rec, vals, ranges, mesh_rgb, bg0, bg1, bg2, out_T,
-                                            last_idx, dL_drgb, dL_dT, batch, g2d, d_status, s_rec0, s_item0, s_bar,
-                                            s_hi, ph0, ph1))
-                return;                                   // a wait timed out: phases unknown, stop claiming
+            if (!replay_tile(gt)) return;                 // a wait timed out: phases unknown, stop claiming
         }
     }
 }
-
 
 // add (r,g,b) to texel t of a [.][.][3] float array: texel t starts at float
 // 3t, so (r,g) is 8-byte aligned for even t and (g,b) for odd t -- one

@@ -13,10 +13,10 @@
 //   tile pass     one CTA per tile, a thread per two pixels of a column:
 //                 for every face of the tile's bucket, exact int64 edge
 //                 functions with the top-left rule at the pixel centres; the
-//                 face's affine 1/z in FP32, packed with the face index into
-//                 a 64-bit key whose minimum over the faces is (largest 1/z,
-//                 i.e. nearest, lowest face index) whatever the bucket order;
-//                 then the resolve: depth = FP32 reciprocal, perspective-
+//                 depth is the FP32 reciprocal of the face's affine 1/z,
+//                 packed with the face index into a 64-bit key whose minimum
+//                 over the faces is (nearest FP32 depth, lowest face index)
+//                 whatever the bucket order; then the resolve: perspective-
 //                 correct UVs, bilinear clamp-to-edge texel fetch, outputs
 //                 and the tile's farthest mesh depth (for the Gaussian pair
 //                 cull).  No per-pixel visibility buffer and no global
@@ -42,17 +42,6 @@ struct FaceSetup {
     float izf[3];            // 1 / view z per vertex (FP32)
     float rD;                // 1 / signed double area
     float u0, v0, du1, dv1, du2, dv2;   // uv0 and uv_k - uv0
-};
-
-// What the resolve of a covered pixel needs of its face, 64 bytes (four
-// 16-byte loads): snapped vertex 0, the edge vectors as FP32, 1/(2 area),
-// 1/z at vertices 1 and 2, uv0 and the uv differences.
-struct __align__(16) FaceShade {
-    int x0, y0;
-    float e1x, e1y, e2x, e2y;
-    float rD, izf1, izf2;
-    float u0, v0, du1, dv1, du2, dv2;
-    float pad;
 };
 
 __global__ void __launch_bounds__(256)
@@ -93,7 +82,7 @@ __global__ void __launch_bounds__(256)
 mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces,
                  const float *__restrict__ uvs, const int2 *__restrict__ sxy,
                  const double *__restrict__ iz, FaceSetup *__restrict__ setup,
-                 FaceShade *__restrict__ shade, uint32_t *__restrict__ tile_fcnt) {
+                 uint32_t *__restrict__ tile_fcnt) {
     const long long m = (long long)vt.n_views * nf;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
@@ -157,20 +146,6 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
             }
         }
         setup[it] = s;
-        FaceShade h;
-        h.x0 = s.x[0];
-        h.y0 = s.y[0];
-        h.e1x = __int2float_rn(s.x[1] - s.x[0]);
-        h.e1y = __int2float_rn(s.y[1] - s.y[0]);
-        h.e2x = __int2float_rn(s.x[2] - s.x[0]);
-        h.e2y = __int2float_rn(s.y[2] - s.y[0]);
-        h.rD = s.rD;
-        h.izf1 = s.izf[1];
-        h.izf2 = s.izf[2];
-        h.u0 = s.u0; h.v0 = s.v0;
-        h.du1 = s.du1; h.dv1 = s.dv1; h.du2 = s.du2; h.dv2 = s.dv2;
-        h.pad = 0.f;
-        shade[it] = h;
     }
 }
 
@@ -209,28 +184,18 @@ struct TexTap {
     float w00, w10, w01, w11;
 };
 
-__device__ __forceinline__ FaceShade load_shade(const FaceShade *p) {
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
-    FaceShade h;
-    h.x0 = __float_as_int(a.x); h.y0 = __float_as_int(a.y);
-    h.e1x = a.z; h.e1y = a.w; h.e2x = b.x; h.e2y = b.y;
-    h.rD = b.z; h.izf1 = b.w; h.izf2 = c.x;
-    h.u0 = c.y; h.v0 = c.z; h.du1 = c.w; h.dv1 = d.x; h.du2 = d.y; h.dv2 = d.z;
-    h.pad = d.w;
-    return h;
-}
-
-__device__ __forceinline__ TexTap tex_tap(const FaceShade &s, int px, int py, float D, int tw, int th) {
+__device__ __forceinline__ TexTap tex_tap(const FaceSetup &s, int px, int py, float D, int tw, int th) {
     TexTap r;
     // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
     // screen-space ones of the offset from vertex 0 (Cramer's rule)
     // (snapped coordinates stay within +-2^29, so the differences fit int32)
-    const float dx = __int2float_rn(px * 256 + 128 - s.x0);
-    const float dy = __int2float_rn(py * 256 + 128 - s.y0);
-    const float l1 = fmaf(dx, s.e2y, -dy * s.e2x) * s.rD;
-    const float l2 = fmaf(s.e1x, dy, -s.e1y * dx) * s.rD;
-    const float b1 = l1 * s.izf1 * D, b2 = l2 * s.izf2 * D;
+    const float dx = __int2float_rn(px * 256 + 128 - s.x[0]);
+    const float dy = __int2float_rn(py * 256 + 128 - s.y[0]);
+    const float e1x = __int2float_rn(s.x[1] - s.x[0]), e1y = __int2float_rn(s.y[1] - s.y[0]);
+    const float e2x = __int2float_rn(s.x[2] - s.x[0]), e2y = __int2float_rn(s.y[2] - s.y[0]);
+    const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
+    const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
+    const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;
     // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
     // for small faces, so uv keeps close to FP32 rounding of its value
     r.u = s.u0 + fmaf(b1, s.du1, b2 * s.du2);
@@ -307,7 +272,7 @@ struct CoverFace {
 // that two dependent load chains are in flight.
 template <int TW, int TH, bool F32TEX>
 __global__ void __launch_bounds__(TW *TH / 2)
-mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup, const FaceShade *__restrict__ shade,
+mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
                  const uint32_t *__restrict__ tile_foff, const uint32_t *__restrict__ tile_fcnt,
                  const long long *n_items, const uint32_t *__restrict__ items,
                  const void *__restrict__ tex, int tw, int th, float bg0, float bg1, float bg2,
@@ -390,32 +355,28 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup, cons
                     cov1 = cov1 && E1 >= 0;
                 }
             }
-            // nearest = largest 1/z: the key holds the complement of the
-            // (positive) FP32 1/z, so the 64-bit minimum is (largest 1/z,
-            // lowest face index); the reciprocal is taken once per pixel in
-            // the resolve
             const float U = __fmul_rn(__int2float_rn(PX - s.x0), 0.00390625f);
             const unsigned long long fkey = s.f;
             if (cov0 && in[0]) {
                 const float Vv = __fmul_rn(__int2float_rn(PY - s.y0), 0.00390625f);
-                const float iz = __fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f));
-                if (iz > 0.f) key[0] = min(key[0], ((unsigned long long)~__float_as_uint(iz) << 32) | fkey);
+                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
+                key[0] = min(key[0], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
             }
             if (cov1 && in[1]) {
                 const float Vv = __fmul_rn(__int2float_rn(PY + 256 * (TH / 2) - s.y0), 0.00390625f);
-                const float iz = __fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f));
-                if (iz > 0.f) key[1] = min(key[1], ((unsigned long long)~__float_as_uint(iz) << 32) | fkey);
+                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
+                key[1] = min(key[1], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
             }
         }
     }
     bool hit[2];
-    FaceShade fs[2];
+    FaceSetup fs[2];
     float D[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         hit[q] = key[q] != ~0ull;
-        D[q] = hit[q] ? __frcp_rn(__uint_as_float(~(unsigned)(key[q] >> 32))) : INFINITY;
-        if (hit[q]) fs[q] = load_shade(shade + (long long)v * nf + (unsigned)(key[q] & 0xFFFFFFFFu));
+        D[q] = hit[q] ? __uint_as_float((unsigned)(key[q] >> 32)) : INFINITY;
+        if (hit[q]) fs[q] = setup[(long long)v * nf + (unsigned)(key[q] & 0xFFFFFFFFu)];
     }
     TexTap tap[2];
 #pragma unroll
@@ -465,7 +426,6 @@ struct RasterWs {
     int2 *sxy;
     double *iz;
     FaceSetup *setup;
-    FaceShade *shade;
     uint32_t *tile_fcnt, *tile_foff, *cursor, *items;
     long long *n_clamped;
     ScanWs scan;
@@ -477,7 +437,6 @@ RasterWs carve(void *ws, long long mv, long long mf, long long cap, long long ti
     r.sxy = c.take<int2>(mv);
     r.iz = c.take<double>(mv);
     r.setup = c.take<FaceSetup>(mf);
-    r.shade = c.take<FaceShade>(mf);
     r.tile_fcnt = c.take<uint32_t>(tiles);
     r.tile_foff = c.take<uint32_t>(tiles);
     r.cursor = c.take<uint32_t>(tiles);
@@ -554,7 +513,7 @@ extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, c
     }
     if (mf > 0) {
         mesh_face_kernel<<<grid_for(mf, 256), 256, 0, s>>>(vt, n_verts, n_faces, faces, uvs, r.sxy, r.iz, r.setup,
-                                                           r.shade, r.tile_fcnt);
+                                                           r.tile_fcnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     // per-tile bucket offsets, the item count and the capacity check
@@ -575,12 +534,12 @@ extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, c
     do {                                                                                                \
         if (f32)                                                                                        \
             mesh_tile_kernel<TW, TH, true><<<tgrid, TW * TH / 2, 0, s>>>(                               \
-                vt, n_faces, r.setup, r.shade, r.tile_foff, r.tile_fcnt, r.n_clamped, r.items, tex, tex_w,  \
-                tex_h, bg[0], bg[1], bg[2], tri_id, depth, rgb, uv, tile_max_depth);                    \
+                vt, n_faces, r.setup, r.tile_foff, r.tile_fcnt, r.n_clamped, r.items, tex, tex_w, tex_h,   \
+                bg[0], bg[1], bg[2], tri_id, depth, rgb, uv, tile_max_depth);                           \
         else                                                                                            \
             mesh_tile_kernel<TW, TH, false><<<tgrid, TW * TH / 2, 0, s>>>(                              \
-                vt, n_faces, r.setup, r.shade, r.tile_foff, r.tile_fcnt, r.n_clamped, r.items, tex, tex_w,  \
-                tex_h, bg[0], bg[1], bg[2], tri_id, depth, rgb, uv, tile_max_depth);                    \
+                vt, n_faces, r.setup, r.tile_foff, r.tile_fcnt, r.n_clamped, r.items, tex, tex_w, tex_h,   \
+                bg[0], bg[1], bg[2], tri_id, depth, rgb, uv, tile_max_depth);                           \
     } while (0)
     if (opt->tile_w == 16) HM_RASTER(16, 16);
     else if (opt->tile_w == 32) HM_RASTER(32, 8);
