@@ -129,8 +129,9 @@ const char *hm_last_error(void);
  * 1/z is affine in screen space; the depth is evaluated in FP32 as
  * 1 / fma(a, U, fma(b, V, 1/z0)), (U,V) the pixel centre minus the snapped
  * vertex 0 in pixels and a, b, 1/z0 the face's coefficients computed in
- * FP64 and rounded once to FP32 (nearest FP32 depth wins, ties to the lower
- * face index) -- within a few FP32 ulps of the FP64 depth (the band is
+ * FP64 and rounded once to FP32 (the face with the largest FP32 1/z wins,
+ * ties to the lower face index; the depth is the correctly rounded FP32
+ * reciprocal of that 1/z) -- within a few FP32 ulps of the FP64 depth (the band is
  * 3 + 3 kappa ulps, kappa the condition number of that evaluation);
  * perspective-correct UVs and a bilinear,
  * clamp-to-edge texture fetch (texel centres at half-integers, row 0 at v=0).

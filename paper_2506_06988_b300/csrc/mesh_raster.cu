@@ -13,10 +13,12 @@
 //   tile pass     one CTA per tile, a thread per two pixels of a column:
 //                 for every face of the tile's bucket, exact int64 edge
 //                 functions with the top-left rule at the pixel centres; the
-//                 depth is the FP32 reciprocal of the face's affine 1/z,
-//                 packed with the face index into a 64-bit key whose minimum
-//                 over the faces is (nearest FP32 depth, lowest face index)
-//                 whatever the bucket order; then the resolve: perspective-
+//                 face's affine 1/z in FP32, packed with the inverted face
+//                 index into a signed 64-bit key whose maximum over the faces
+//                 is (largest FP32 1/z, lowest face index) whatever the
+//                 bucket order; the depth is the FP32 reciprocal of the
+//                 winner's 1/z (one division per pixel, not per face); then
+//                 the resolve: perspective-
 //                 correct UVs, bilinear clamp-to-edge texel fetch, outputs
 //                 and the tile's farthest mesh depth (for the Gaussian pair
 //                 cull).  No per-pixel visibility buffer and no global
@@ -33,16 +35,19 @@ constexpr double kSnap = 256.0;
 constexpr double kGuard = 2097152.0;   // 2^21 px
 constexpr int kInvalid = INT_MIN;
 
-struct FaceSetup {
+// 16-byte aligned, with the fields a pass reads together in whole 16-byte
+// chunks (coverage: x, y, flip, plane; resolve: x, y, izf, rD, uv)
+struct __align__(16) FaceSetup {
     int x[3], y[3];          // snapped positions in the face's vertex order
-    long long area2;         // |signed double area| (1/256 px)^2
     int flip;                // signed area negative: traverse 0 -> 2 -> 1
-    int tx0, tx1, ty0, ty1;  // touched tiles (empty: tx0 > tx1)
     float iz0f, af, bf;      // 1/z = iz0 + a U + b V, (U,V) = centre - vertex 0 in pixels
     float izf[3];            // 1 / view z per vertex (FP32)
     float rD;                // 1 / signed double area
     float u0, v0, du1, dv1, du2, dv2;   // uv0 and uv_k - uv0
+    int tx0, tx1, ty0, ty1;  // touched tiles (empty: tx0 > tx1)
+    long long area2;         // |signed double area| (1/256 px)^2
 };
+static_assert(sizeof(FaceSetup) == 112, "face set-up layout");
 
 __global__ void __launch_bounds__(256)
 mesh_vertex_kernel(ViewTable vt, int nv, const float *__restrict__ verts, double znear,
@@ -184,18 +189,36 @@ struct TexTap {
     float w00, w10, w01, w11;
 };
 
-__device__ __forceinline__ TexTap tex_tap(const FaceSetup &s, int px, int py, float D, int tw, int th) {
+// what the resolve of a covered pixel needs of its face
+struct TexFace {
+    int x0, y0;                 // snapped vertex 0
+    int e1x, e1y, e2x, e2y;     // snapped edges from vertex 0
+    float rD, izf1, izf2;       // 1 / signed double area, 1/z of vertices 1 and 2
+    float u0, v0, du1, dv1, du2, dv2;
+};
+
+__device__ __forceinline__ TexFace tex_face(const FaceSetup &g) {
+    TexFace f;
+    f.x0 = g.x[0]; f.y0 = g.y[0];
+    f.e1x = g.x[1] - g.x[0]; f.e1y = g.y[1] - g.y[0];
+    f.e2x = g.x[2] - g.x[0]; f.e2y = g.y[2] - g.y[0];
+    f.rD = g.rD; f.izf1 = g.izf[1]; f.izf2 = g.izf[2];
+    f.u0 = g.u0; f.v0 = g.v0; f.du1 = g.du1; f.dv1 = g.dv1; f.du2 = g.du2; f.dv2 = g.dv2;
+    return f;
+}
+
+__device__ __forceinline__ TexTap tex_tap(const TexFace &s, int px, int py, float D, int tw, int th) {
     TexTap r;
     // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
     // screen-space ones of the offset from vertex 0 (Cramer's rule)
     // (snapped coordinates stay within +-2^29, so the differences fit int32)
-    const float dx = __int2float_rn(px * 256 + 128 - s.x[0]);
-    const float dy = __int2float_rn(py * 256 + 128 - s.y[0]);
-    const float e1x = __int2float_rn(s.x[1] - s.x[0]), e1y = __int2float_rn(s.y[1] - s.y[0]);
-    const float e2x = __int2float_rn(s.x[2] - s.x[0]), e2y = __int2float_rn(s.y[2] - s.y[0]);
+    const float dx = __int2float_rn(px * 256 + 128 - s.x0);
+    const float dy = __int2float_rn(py * 256 + 128 - s.y0);
+    const float e1x = __int2float_rn(s.e1x), e1y = __int2float_rn(s.e1y);
+    const float e2x = __int2float_rn(s.e2x), e2y = __int2float_rn(s.e2y);
     const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
     const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
-    const float b1 = l1 * s.izf[1] * D, b2 = l2 * s.izf[2] * D;
+    const float b1 = l1 * s.izf1 * D, b2 = l2 * s.izf2 * D;
     // uv = uv0 + b1 (uv1 - uv0) + b2 (uv2 - uv0): the corrections are small
     // for small faces, so uv keeps close to FP32 rounding of its value
     r.u = s.u0 + fmaf(b1, s.du1, b2 * s.du2);
@@ -281,6 +304,7 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     constexpr int NT = TW * TH / 2;
     __shared__ float s_max[NT / 32];
     __shared__ CoverFace s_face[NT];
+    __shared__ TexFace s_tex[NT];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
     const ViewDev &V = vt.v[v];
@@ -292,7 +316,8 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     const long long npx = (long long)V.W * V.H;
     bool in[2];
     long long lp[2];
-    unsigned long long key[2] = {~0ull, ~0ull};
+    long long key[2] = {LLONG_MIN, LLONG_MIN};     // no face
+    uint32_t slot[2] = {0u, 0u};                   // bucket position of the key's face
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         in[q] = px < V.W && py[q] < V.H;
@@ -309,7 +334,7 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         __syncthreads();                             // the previous round's faces are consumed
         if (t < nb) {
             const uint32_t vf = items[f0 + r0 + t];
-            const FaceSetup &g = setup[vf];
+            const FaceSetup g = setup[vf];
             const int b = g.flip ? 2 : 1, c = g.flip ? 1 : 2;   // oriented order 0, b, c
             const int ax[3] = {g.x[0], g.x[b], g.x[c]}, ay[3] = {g.y[0], g.y[b], g.y[c]};
             const int bx[3] = {g.x[b], g.x[c], g.x[0]}, by[3] = {g.y[b], g.y[c], g.y[0]};
@@ -334,6 +359,7 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             cf.af = g.af; cf.bf = g.bf; cf.iz0f = g.iz0f;
             cf.f = vf - (unsigned)v * (unsigned)nf;
             s_face[t] = cf;
+            s_tex[t] = tex_face(g);
         }
         __syncthreads();
         for (int k = 0; k < nb; ++k) {
@@ -355,28 +381,36 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
                     cov1 = cov1 && E1 >= 0;
                 }
             }
+            // the 1/z of the face at the pixel centre; the key orders by it
+            // (signed: a negative value, possible only through rounding at a
+            // sliver, never beats a positive one), then by the lower index
             const float U = __fmul_rn(__int2float_rn(PX - s.x0), 0.00390625f);
-            const unsigned long long fkey = s.f;
+            const unsigned long long fkey = ~s.f;
             if (cov0 && in[0]) {
                 const float Vv = __fmul_rn(__int2float_rn(PY - s.y0), 0.00390625f);
-                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
-                key[0] = min(key[0], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
+                const float iz = __fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f));
+                const long long kk = (long long)(((unsigned long long)__float_as_uint(iz) << 32) | (fkey & 0xFFFFFFFFull));
+                if (kk > key[0]) { key[0] = kk; slot[0] = r0 + k; }
             }
             if (cov1 && in[1]) {
                 const float Vv = __fmul_rn(__int2float_rn(PY + 256 * (TH / 2) - s.y0), 0.00390625f);
-                const float D = __frcp_rn(__fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f)));
-                key[1] = min(key[1], ((unsigned long long)__float_as_uint(D) << 32) | fkey);
+                const float iz = __fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f));
+                const long long kk = (long long)(((unsigned long long)__float_as_uint(iz) << 32) | (fkey & 0xFFFFFFFFull));
+                if (kk > key[1]) { key[1] = kk; slot[1] = r0 + k; }
             }
         }
     }
     bool hit[2];
-    FaceSetup fs[2];
+    TexFace fs[2];
     float D[2];
+    uint32_t fid[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        hit[q] = key[q] != ~0ull;
-        D[q] = hit[q] ? __uint_as_float((unsigned)(key[q] >> 32)) : INFINITY;
-        if (hit[q]) fs[q] = setup[(long long)v * nf + (unsigned)(key[q] & 0xFFFFFFFFu)];
+        hit[q] = key[q] != LLONG_MIN;
+        fid[q] = ~(uint32_t)((unsigned long long)key[q] & 0xFFFFFFFFull);
+        D[q] = hit[q] ? __frcp_rn(__uint_as_float((uint32_t)((unsigned long long)key[q] >> 32))) : INFINITY;
+        // the bucket's faces are still staged when it fits one round
+        if (hit[q]) fs[q] = fc <= (uint32_t)NT ? s_tex[slot[q]] : tex_face(setup[(long long)v * nf + fid[q]]);
     }
     TexTap tap[2];
 #pragma unroll
@@ -396,7 +430,7 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         if (!in[q]) continue;
         m = fmaxf(m, D[q]);
         const long long gp = V.pix_off + lp[q];
-        if (tri_id) tri_id[gp] = hit[q] ? (int)(unsigned)(key[q] & 0xFFFFFFFFu) : -1;
+        if (tri_id) tri_id[gp] = hit[q] ? (int)fid[q] : -1;
         if (depth) depth[gp] = D[q];
         if (rgb) {
             float *o = rgb + 3 * V.pix_off + lp[q];
