@@ -90,18 +90,21 @@ __device__ __forceinline__ bool keep_tile(const ViewTable &vt, const float *tmax
 }
 
 // Binning of a block of records by load-balanced expansion.  A CTA takes
-// kBinThreads consecutive records; each thread loads one and counts the
-// tiles of its rectangle (0 for a culled record), a block-wide exclusive
-// scan lays the records' (record, tile) candidates end to end, and every
-// thread of the CTA then takes candidates c = t, t + kBinThreads, ... : the
-// record is the last slot whose offset is <= c (binary search over the
-// offsets in shared memory), the tile follows from c - offset.  A record
-// spanning a thousand tiles and a block of single-tile records keep every
-// thread equally busy, and a CTA's candidate loads and atomics are in
-// flight together.  Each candidate takes the mesh cull and the ellipse test
-// (keep_tile); count and emission run the same expansion, so they keep the
-// same pairs.
+// kBinThreads records; each thread loads one and counts the tiles of its
+// rectangle (0 for a culled record), a block-wide exclusive scan lays the
+// records' (record, tile) candidates end to end, and every thread of the
+// CTA then takes candidates c = t, t + kBinThreads, ... : the record is the
+// last slot whose offset is <= c (binary search over the offsets in shared
+// memory), the tile follows from c - offset.  A record spanning a thousand
+// tiles and a block of single-tile records keep every thread equally busy,
+// and a CTA's candidate loads and atomics are in flight together.  Each
+// candidate takes the mesh cull and the ellipse test (keep_tile); count and
+// emission run the same expansion, so they keep the same pairs.  The count
+// walks all records in index order and appends the ones with a non-empty
+// rectangle (a few percent at 1080p) to a list; the emission walks only
+// that list.
 constexpr int kBinThreads = 256;
+constexpr int kEmitRecs = 64;      // listed records per block of the emission
 
 struct BinBlock {
     uint32_t off[kBinThreads + 1];   // exclusive prefix of the rectangles' tile counts; [256] = total
@@ -109,15 +112,21 @@ struct BinBlock {
     float mx[kBinThreads], my[kBinThreads], a[kBinThreads], b[kBinThreads], c[kBinThreads];
     float ra[kBinThreads], rc[kBinThreads], depth[kBinThreads];
     int x0[kBinThreads], y0[kBinThreads], nx[kBinThreads], v[kBinThreads];
+    uint32_t idx[kBinThreads];       // record index
 };
 
-// Loads the CTA's records and scans their rectangle sizes; returns the total.
-__device__ __forceinline__ uint32_t bin_block_load(BinBlock &S, const Record *__restrict__ rec, long long m,
-                                                   int n) {
+// Loads the block's records -- for t < nrec and first + t < limit, record
+// `first + t` (list == nullptr) or list[first + t] -- and scans their
+// rectangle sizes; returns the total, `cnt` the thread's own record's count.
+__device__ __forceinline__ uint32_t bin_block_load(BinBlock &S, const Record *__restrict__ rec,
+                                                   const uint32_t *__restrict__ list, uint32_t first,
+                                                   uint32_t limit, int nrec, int n, uint32_t &cnt,
+                                                   uint32_t &it) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const long long it = (long long)blockIdx.x * kBinThreads + t;
-    uint32_t cnt = 0;
-    if (it < m) {
+    cnt = 0;
+    it = 0;
+    if (t < nrec && first + (uint32_t)t < limit) {
+        it = list ? list[first + t] : first + (uint32_t)t;
         const BinRec r = load_bin_rec(rec, it, n);
         cnt = (uint32_t)rec_tiles(r);
         if (cnt) {
@@ -126,6 +135,7 @@ __device__ __forceinline__ uint32_t bin_block_load(BinBlock &S, const Record *__
             S.ra[t] = 1.f / r.a; S.rc[t] = 1.f / r.c;
             S.depth[t] = r.depth;
             S.x0[t] = r.x0; S.y0[t] = r.y0; S.nx[t] = r.x1 - r.x0 + 1; S.v[t] = r.v;
+            S.idx[t] = it;
         }
     }
     uint32_t incl = cnt;
@@ -175,12 +185,25 @@ __device__ __forceinline__ bool bin_candidate(const BinBlock &S, const ViewTable
     return keep_tile(vt, tmax, ellipse, r, S.ra[j], S.rc[j], tx, ty);
 }
 
-// Per tile: the number of records that keep it (atomic counts).
+// Per tile: the number of records that keep it (atomic counts); the
+// records with a non-empty rectangle are appended to `vis` (order
+// arbitrary: the emitted keys carry the record index).
 __global__ void __launch_bounds__(kBinThreads)
 bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                 int ellipse, uint32_t *__restrict__ tile_cnt) {
+                 int ellipse, uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ vis,
+                 unsigned int *__restrict__ n_vis) {
     __shared__ BinBlock S;
-    const uint32_t total = bin_block_load(S, rec, (long long)vt.n_views * n, n);
+    uint32_t mine, it;
+    const uint32_t total = bin_block_load(S, rec, nullptr, blockIdx.x * kBinThreads,
+                                          (uint32_t)((long long)vt.n_views * n), kBinThreads, n, mine, it);
+    {
+        const int lane = threadIdx.x & 31;
+        const unsigned bal = __ballot_sync(0xffffffffu, mine > 0);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(n_vis, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (mine > 0) vis[base + __popc(bal & ((1u << lane) - 1u))] = it;
+    }
     for (uint32_t c = threadIdx.x; c < total; c += kBinThreads) {
         int j, tx, ty;
         if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
@@ -200,21 +223,29 @@ __global__ void clamp_count_kernel(const long long *total, long long capacity, l
 // Every kept (record, tile): the 64-bit key (depth bits << 32 | record
 // index) into the tile's bucket, at a slot taken from the tile's cursor
 // (initialised to the bucket's start); nothing is written when the
-// capacity was exceeded.
+// capacity was exceeded.  The CTAs walk the list of records with a
+// non-empty rectangle, kEmitRecs at a time (grid-stride): such a record
+// spans tens of tiles, so a few records already give every thread of the
+// CTA candidates, and many CTAs keep the cursors' returning atomics in
+// flight together.
 __global__ void __launch_bounds__(kBinThreads)
 bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float *__restrict__ tmax,
-                int ellipse, uint32_t *__restrict__ cursor, const long long *n_sort,
-                unsigned long long *__restrict__ keys) {
+                int ellipse, const uint32_t *__restrict__ vis, const unsigned int *n_vis,
+                uint32_t *__restrict__ cursor, const long long *n_sort, unsigned long long *__restrict__ keys) {
     if (*n_sort == 0) return;
     __shared__ BinBlock S;
-    const uint32_t total = bin_block_load(S, rec, (long long)vt.n_views * n, n);
-    for (uint32_t c = threadIdx.x; c < total; c += kBinThreads) {
-        int j, tx, ty;
-        if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
-            const ViewDev &V = vt.v[S.v[j]];
-            const uint32_t it = (uint32_t)blockIdx.x * kBinThreads + (uint32_t)j;
-            keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] =
-                ((unsigned long long)__float_as_uint(S.depth[j]) << 32) | it;
+    const uint32_t nv = *n_vis;
+    for (uint32_t first = blockIdx.x * kEmitRecs; first < nv; first += gridDim.x * kEmitRecs) {
+        __syncthreads();                             // the previous block's shared reads are done
+        uint32_t mine, it;
+        const uint32_t total = bin_block_load(S, rec, vis, first, nv, kEmitRecs, n, mine, it);
+        for (uint32_t c = threadIdx.x; c < total; c += kBinThreads) {
+            int j, tx, ty;
+            if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
+                const ViewDev &V = vt.v[S.v[j]];
+                keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] =
+                    ((unsigned long long)__float_as_uint(S.depth[j]) << 32) | S.idx[j];
+            }
         }
     }
 }
@@ -711,9 +742,9 @@ seg_sort_huge_kernel(const uint32_t *__restrict__ list, const unsigned int *list
 }
 
 struct BinWs {
-    uint32_t *tile_cnt, *tile_off, *tile_fill, *mid_list, *big_list;
+    uint32_t *tile_cnt, *tile_off, *tile_fill, *mid_list, *big_list, *vis;
     unsigned long long *keys, *scratch;
-    unsigned int *counts;   // [0] mid-size buckets (<= kMidSeg), [1] larger buckets
+    unsigned int *counts;   // [0] mid-size buckets (<= kMidSeg), [1] larger buckets, [2] listed records
     long long *n_sort;
     ScanWs scan;
 };
@@ -728,7 +759,8 @@ BinWs carve(void *ws, long long m, long long cap, long long tiles, size_t *bytes
     b.big_list = c.take<uint32_t>(tiles);
     b.keys = c.take<unsigned long long>(cap);
     b.scratch = c.take<unsigned long long>(cap);
-    b.counts = c.take<unsigned int>(2);
+    b.vis = c.take<uint32_t>(m);
+    b.counts = c.take<unsigned int>(3);
     b.n_sort = c.take<long long>(1);
     b.scan.tile_status = c.take<unsigned long long>(scan_tiles(tiles) + 1);
     b.scan.ticket = c.take<unsigned int>(1);
@@ -784,12 +816,13 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     if (e != cudaSuccess) return cuda_status(e);
     if (m == 0) return cuda_status(cudaMemsetAsync(n_pairs_out, 0, sizeof(long long), s));
     if ((e = cudaMemsetAsync(b.tile_cnt, 0, sizeof(uint32_t) * (size_t)T, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(b.counts, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess)
+        (e = cudaMemsetAsync(b.counts, 0, 3 * sizeof(unsigned int), s)) != cudaSuccess)
         return cuda_status(e);
 
     // 1. kept tiles per record, records per tile
     const unsigned rgrid = (unsigned)((m + kBinThreads - 1) / kBinThreads);
-    bin_count_kernel<<<rgrid, kBinThreads, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.tile_cnt);
+    bin_count_kernel<<<rgrid, kBinThreads, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.tile_cnt, b.vis,
+                                                   b.counts + 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 2. tile offsets, pair count and capacity check
     e = launch_scan(b.tile_cnt, nullptr, b.tile_off, T, (long long *)n_pairs_out, capacity, d_status, b.scan, s);
@@ -798,8 +831,9 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     // 3. keys into the tile buckets (cursors start at the bucket starts)
     e = cudaMemcpyAsync(b.tile_fill, b.tile_off, sizeof(uint32_t) * (size_t)T, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    bin_emit_kernel<<<rgrid, kBinThreads, 0, s>>>(vt, n, rec, tmax, opt->ellipse_cull, b.tile_fill, b.n_sort,
-                                                  b.keys);
+    const unsigned egrid = (unsigned)((m + kEmitRecs - 1) / kEmitRecs);
+    bin_emit_kernel<<<egrid < 148u * 8u ? egrid : 148u * 8u, kBinThreads, 0, s>>>(
+        vt, n, rec, tmax, opt->ellipse_cull, b.vis, b.counts + 2, b.tile_fill, b.n_sort, b.keys);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     // 4. sort every bucket; tile ranges
     seg_sort_small_kernel<<<grid_for(T * 32, 256), 256, 0, s>>>((uint32_t)T, b.tile_off, b.tile_cnt, b.n_sort,
