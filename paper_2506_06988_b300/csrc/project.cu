@@ -110,20 +110,14 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
         s1 = e1;
         s2 = e2;
     }
-    float sh[K][3];
-    if (F16) {
-        const __half *h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sh[k][c] = __half2float(h[3 * k + c]);
-    } else {
-        const float *f = reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sh[k][c] = __ldg(f + 3 * k + c);
-    }
+    // SH coefficient k, channel c (read only for records with tiles: most
+    // records are off screen)
+    auto sh_coef = [&](int k, int c) -> float {
+        if constexpr (F16)
+            return __half2float(reinterpret_cast<const __half *>(sh_raw)[(size_t)i * K * 3 + 3 * k + c]);
+        else
+            return __ldg(reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3 + 3 * k + c);
+    };
     // M = R(q) S, rows a, columns k: M[a][k] = R[a][k] s_k
     float M[3][3];
     {
@@ -205,23 +199,26 @@ project_kernel(ViewTable vt, int n, const float *__restrict__ means,
                     yr = pack_range(py0 / vt.tile_h, py1 / vt.tile_h);
                 }
             }
-            // view-dependent colour: SH at the unit direction camera centre -> mean
-            float d0 = mx - V.campos[0], d1 = my - V.campos[1], d2 = mz - V.campos[2];
-            float dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            d0 *= dn; d1 *= dn; d2 *= dn;
-            float Y[K];
-            sh_basis<DEG>(d0, d1, d2, Y);
-            float col[3];
-            bool col_ok = true;
+            // view-dependent colour: SH at the unit direction camera centre ->
+            // mean, for a record with tiles (no list holds the others)
+            float col[3] = {0.f, 0.f, 0.f};
+            if (xr != kEmptyRange) {
+                float d0 = mx - V.campos[0], d1 = my - V.campos[1], d2 = mz - V.campos[2];
+                float dn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                d0 *= dn; d1 *= dn; d2 *= dn;
+                float Y[K];
+                sh_basis<DEG>(d0, d1, d2, Y);
+                bool col_ok = true;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.5f;
+                for (int ch = 0; ch < 3; ++ch) {
+                    float acc = 0.5f;
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[k][ch], acc);
-                col_ok = col_ok && isfinite(acc);
-                col[ch] = fmaxf(acc, 0.f);
+                    for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh_coef(k, ch), acc);
+                    col_ok = col_ok && isfinite(acc);
+                    col[ch] = fmaxf(acc, 0.f);
+                }
+                if (!col_ok) xr = yr = kEmptyRange;
             }
-            if (!col_ok) xr = yr = kEmptyRange;
             // conic (c, -B, a) / det, pre-multiplied by K (and 2K for xy)
             r.a = make_float4(u, w, __fmul_rn(kConicScale, c * rd), __fmul_rn(2.f * kConicScale, -B * rd));
             r.b = make_float4(__fmul_rn(kConicScale, a * rd), opv, zf, __uint_as_float(xr));
