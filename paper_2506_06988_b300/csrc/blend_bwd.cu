@@ -42,6 +42,9 @@ namespace {
 // sum gq dy^2; q = K d^2, (dx, dy) = pixel centre - mean), dL/dopacity and
 // dL/dcolour (r, g, b)
 constexpr int kG = 9;
+// Gaussians per lane that a warp of the projection backward scans for
+// gradients before it works on the ones it found
+constexpr int kPbwdWin = 4;
 
 // Warp sum of 8 per-lane values by recursive halving: at each of the first
 // three levels a lane keeps half of its values and sends the other half to
@@ -534,248 +537,294 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
     // SH gradient accumulators, one private column per thread (conflict-free
     // [k][c][thread] layout): keeps 3K values out of the register file
     __shared__ float s_gsh[K * 3][128];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float(*gsh)[128] = s_gsh;
-    const int tl = threadIdx.x;
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-    const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
-    // Mip-Splatting's 3D filter: effective scales se_k = sqrt(s_k^2 + v) and
-    // the opacity factor rho3 = prod_k s_k / se_k (v is a constant)
-    const float v3 = flt.f3d ? flt.f3d[i] : 0.f;
-    float se[3] = {s[0], s[1], s[2]}, rho3 = 1.f;
-    if (v3 > 0.f) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            se[k] = sqrtf(fmaf(s[k], s[k], v3));
-            rho3 *= s[k] / se[k];
-        }
+    // the cameras, for the lanes of a warp that walk different views at once
+    __shared__ ViewDev s_view[HM_MAX_VIEWS];
+    {
+        const int words = vt.n_views * (int)(sizeof(ViewDev) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(vt.v);
+        int *dst = reinterpret_cast<int *>(s_view);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
     }
-    const float op_i = opac[i];
-    float g_rho3 = 0.f;                 // dL/drho3 over the views
-    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
-    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
-    const float qinv = rsqrtf(qn2);
-    const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
-    const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
-                           {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
-                           {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
-    float M[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) M[a][k] = R[a][k] * se[k];
-    // SH coefficients are re-read (L1-resident after the first view) where
-    // they are used instead of being held across the view loop
-    const __half *sh_h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
-    const float *sh_f = reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3;
-    auto ld_sh = [&](int j) -> float { return F16 ? __half2float(sh_h[j]) : __ldg(sh_f + j); };
-    float gmean[3] = {0.f, 0.f, 0.f};
-    float gM[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) gsh[k][tl] = 0.f;
-    float gop = 0.f;
-    bool touched = false;           // some view blended it
-    for (int v = 0; v < vt.n_views; ++v) {
-        const float *gg = g2d + ((size_t)v * n + i) * kG;
-        float g[kG];
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < kG; ++q) {
-            g[q] = gg[q];
-            any |= g[q] != 0.f;
-        }
-        // the replay sums the moments of dL/dq / ln 2 (q = K d^2, alpha = o 2^q)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) g[q] *= kLn2;
-        // a record with gradient was blended, so the forward kept it (its
-        // FP64-rounded depth passed the near plane); the Jacobian only needs
-        // the view position to FP32 accuracy, so it is recomputed in FP32
-        // here (the FP64 pipe is ~1/64 of the FP32 rate)
-        if (!any) continue;
-        const ViewDev &V = vt.v[v];
-        const float zf = fmaf(V.R[6], mx, fmaf(V.R[7], my, fmaf(V.R[8], mz, V.t[2])));
-        if (!(zf > 0.f)) continue;
-        touched = true;
-        const float txf = fmaf(V.R[0], mx, fmaf(V.R[1], my, fmaf(V.R[2], mz, V.t[0])));
-        const float tyf = fmaf(V.R[3], mx, fmaf(V.R[4], my, fmaf(V.R[5], mz, V.t[1])));
-        const float rz = __frcp_rn(zf);
-        const float rx = txf * rz, ry = tyf * rz;
-        const float limx = 1.3f * (0.5f * (float)V.W / V.fx), limy = 1.3f * (0.5f * (float)V.H / V.fy);
-        const bool inx = rx > -limx && rx < limx, iny = ry > -limy && ry < limy;
-        const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
-        const float J00 = V.fx * rz, J02 = -V.fx * rxc * rz, J11 = V.fy * rz, J12 = -V.fy * ryc * rz;
-        float T0[3], T1[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            T0[k] = fmaf(J00, V.R[k], J02 * V.R[6 + k]);
-            T1[k] = fmaf(J11, V.R[3 + k], J12 * V.R[6 + k]);
-        }
-        float V0[3], V1[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            V0[k] = T0[0] * M[0][k] + T0[1] * M[1][k] + T0[2] * M[2][k];
-            V1[k] = T1[0] * M[0][k] + T1[1] * M[1][k] + T1[2] * M[2][k];
-        }
-        const float h = flt.kernel;
-        const float A0 = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2];
-        const float C0 = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2];
-        const float a = A0 + h, c = C0 + h;
-        const float b = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
-        const float cx_ = V0[1] * V1[2] - V0[2] * V1[1], cy_ = V0[2] * V1[0] - V0[0] * V1[2],
-                    cz_ = V0[0] * V1[1] - V0[1] * V1[0];
-        const float det0 = cx_ * cx_ + cy_ * cy_ + cz_ * cz_;      // det(Sigma2D)
-        const float det = det0 + h * (A0 + C0) + h * h;
-        const float rd2 = 1.f / (det * det);
-        // the blend's moments S of dL/dq (q = K d^2): dL/dmean2d = -2K conic S_(dx,dy),
-        // dL/dconic = K (S_dx2, 2 S_dxdy, S_dy2)
-        const float rdet = 1.f / det;
-        const float cxx = c * rdet, cxy = -b * rdet, cyy = a * rdet;
-        const float gmx = -2.f * kConicScale * (cxx * g[0] + cxy * g[1]);
-        const float gmy = -2.f * kConicScale * (cxy * g[0] + cyy * g[1]);
-        // conic (c/det, -b/det, a/det) -> Sigma' entries
-        const float gA = kConicScale * g[2], gB = 2.f * kConicScale * g[3], gC = kConicScale * g[4];
-        float ga = (-c * c * gA + b * c * gB - b * b * gC) * rd2;
-        float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * rd2;
-        float gc = (-b * b * gA + a * b * gB - a * a * gC) * rd2;
-        // the record's opacity is op rho3 rho2; with the 2D Mip filter
-        // rho2 = sqrt(D0 / D1), D0 = A0 C0 - b^2, D1 = (A0 + h)(C0 + h) - b^2, so
-        // drho2 = rho2 / 2 (dD0 / D0 - dD1 / D1)
-        float rho2 = 1.f;
-        if (flt.antialias) {
-            rho2 = det0 > 0.f ? sqrtf(det0 * rdet) : 0.f;
-            if (det0 > 0.f) {
-                const float k2 = 0.5f * g[5] * op_i * rho3 * rho2, r0 = 1.f / det0;
-                ga += k2 * (C0 * r0 - c * rdet);
-                gc += k2 * (A0 * r0 - a * rdet);
-                gb += 2.f * k2 * b * (rdet - r0);
+    auto one_gaussian = [&](const int i, const uint32_t vmask) {
+        float(*gsh)[128] = s_gsh;
+        const int tl = threadIdx.x;
+        const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+        const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+        // Mip-Splatting's 3D filter: effective scales se_k = sqrt(s_k^2 + v) and
+        // the opacity factor rho3 = prod_k s_k / se_k (v is a constant)
+        const float v3 = flt.f3d ? flt.f3d[i] : 0.f;
+        float se[3] = {s[0], s[1], s[2]}, rho3 = 1.f;
+        if (v3 > 0.f) {
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                se[k] = sqrtf(fmaf(s[k], s[k], v3));
+                rho3 *= s[k] / se[k];
             }
         }
-        g_rho3 += g[5] * op_i * rho2;
-        // Sigma' = V V^T: dV0 = 2 ga V0 + gb V1, dV1 = gb V0 + 2 gc V1
-        float gV0[3], gV1[3];
-#pragma unroll
+        const float op_i = opac[i];
+        float g_rho3 = 0.f;                 // dL/drho3 over the views
+        const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+        const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+        const float qinv = rsqrtf(qn2);
+        const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+        const float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                               {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                               {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+        float M[3][3];
+    #pragma unroll
+        for (int a = 0; a < 3; ++a)
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) M[a][k] = R[a][k] * se[k];
+        // SH coefficients are re-read (L1-resident after the first view) where
+        // they are used instead of being held across the view loop
+        const __half *sh_h = reinterpret_cast<const __half *>(sh_raw) + (size_t)i * K * 3;
+        const float *sh_f = reinterpret_cast<const float *>(sh_raw) + (size_t)i * K * 3;
+        auto ld_sh = [&](int j) -> float { return F16 ? __half2float(sh_h[j]) : __ldg(sh_f + j); };
+        float gmean[3] = {0.f, 0.f, 0.f};
+        float gM[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    #pragma unroll
+        for (int k = 0; k < K * 3; ++k) gsh[k][tl] = 0.f;
+        float gop = 0.f;
+        bool touched = false;           // some view blended it
+        for (uint32_t m = vmask; m != 0u; m &= m - 1u) {
+            const int v = __ffs(m) - 1;
+            const float *gg = g2d + ((size_t)v * n + i) * kG;
+            float g[kG];
+    #pragma unroll
+            for (int q = 0; q < kG; ++q) g[q] = gg[q];
+            // the replay sums the moments of dL/dq / ln 2 (q = K d^2, alpha = o 2^q)
+    #pragma unroll
+            for (int q = 0; q < 5; ++q) g[q] *= kLn2;
+            // a record with gradient was blended, so the forward kept it (its
+            // FP64-rounded depth passed the near plane); the Jacobian only needs
+            // the view position to FP32 accuracy, so it is recomputed in FP32
+            // here (the FP64 pipe is ~1/64 of the FP32 rate)
+            const ViewDev &V = s_view[v];
+            const float zf = fmaf(V.R[6], mx, fmaf(V.R[7], my, fmaf(V.R[8], mz, V.t[2])));
+            if (!(zf > 0.f)) continue;
+            touched = true;
+            const float txf = fmaf(V.R[0], mx, fmaf(V.R[1], my, fmaf(V.R[2], mz, V.t[0])));
+            const float tyf = fmaf(V.R[3], mx, fmaf(V.R[4], my, fmaf(V.R[5], mz, V.t[1])));
+            const float rz = __frcp_rn(zf);
+            const float rx = txf * rz, ry = tyf * rz;
+            const float limx = 1.3f * (0.5f * (float)V.W / V.fx), limy = 1.3f * (0.5f * (float)V.H / V.fy);
+            const bool inx = rx > -limx && rx < limx, iny = ry > -limy && ry < limy;
+            const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
+            const float J00 = V.fx * rz, J02 = -V.fx * rxc * rz, J11 = V.fy * rz, J12 = -V.fy * ryc * rz;
+            float T0[3], T1[3];
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T0[k] = fmaf(J00, V.R[k], J02 * V.R[6 + k]);
+                T1[k] = fmaf(J11, V.R[3 + k], J12 * V.R[6 + k]);
+            }
+            float V0[3], V1[3];
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                V0[k] = T0[0] * M[0][k] + T0[1] * M[1][k] + T0[2] * M[2][k];
+                V1[k] = T1[0] * M[0][k] + T1[1] * M[1][k] + T1[2] * M[2][k];
+            }
+            const float h = flt.kernel;
+            const float A0 = V0[0] * V0[0] + V0[1] * V0[1] + V0[2] * V0[2];
+            const float C0 = V1[0] * V1[0] + V1[1] * V1[1] + V1[2] * V1[2];
+            const float a = A0 + h, c = C0 + h;
+            const float b = V0[0] * V1[0] + V0[1] * V1[1] + V0[2] * V1[2];
+            const float cx_ = V0[1] * V1[2] - V0[2] * V1[1], cy_ = V0[2] * V1[0] - V0[0] * V1[2],
+                        cz_ = V0[0] * V1[1] - V0[1] * V1[0];
+            const float det0 = cx_ * cx_ + cy_ * cy_ + cz_ * cz_;      // det(Sigma2D)
+            const float det = det0 + h * (A0 + C0) + h * h;
+            const float rd2 = 1.f / (det * det);
+            // the blend's moments S of dL/dq (q = K d^2): dL/dmean2d = -2K conic S_(dx,dy),
+            // dL/dconic = K (S_dx2, 2 S_dxdy, S_dy2)
+            const float rdet = 1.f / det;
+            const float cxx = c * rdet, cxy = -b * rdet, cyy = a * rdet;
+            const float gmx = -2.f * kConicScale * (cxx * g[0] + cxy * g[1]);
+            const float gmy = -2.f * kConicScale * (cxy * g[0] + cyy * g[1]);
+            // conic (c/det, -b/det, a/det) -> Sigma' entries
+            const float gA = kConicScale * g[2], gB = 2.f * kConicScale * g[3], gC = kConicScale * g[4];
+            float ga = (-c * c * gA + b * c * gB - b * b * gC) * rd2;
+            float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * rd2;
+            float gc = (-b * b * gA + a * b * gB - a * a * gC) * rd2;
+            // the record's opacity is op rho3 rho2; with the 2D Mip filter
+            // rho2 = sqrt(D0 / D1), D0 = A0 C0 - b^2, D1 = (A0 + h)(C0 + h) - b^2, so
+            // drho2 = rho2 / 2 (dD0 / D0 - dD1 / D1)
+            float rho2 = 1.f;
+            if (flt.antialias) {
+                rho2 = det0 > 0.f ? sqrtf(det0 * rdet) : 0.f;
+                if (det0 > 0.f) {
+                    const float k2 = 0.5f * g[5] * op_i * rho3 * rho2, r0 = 1.f / det0;
+                    ga += k2 * (C0 * r0 - c * rdet);
+                    gc += k2 * (A0 * r0 - a * rdet);
+                    gb += 2.f * k2 * b * (rdet - r0);
+                }
+            }
+            g_rho3 += g[5] * op_i * rho2;
+            // Sigma' = V V^T: dV0 = 2 ga V0 + gb V1, dV1 = gb V0 + 2 gc V1
+            float gV0[3], gV1[3];
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gV0[k] = 2.f * ga * V0[k] + gb * V1[k];
+                gV1[k] = gb * V0[k] + 2.f * gc * V1[k];
+            }
+            // V = T M: dM += T^T dV, dT = dV M^T
+            float gT0[3], gT1[3];
+    #pragma unroll
+            for (int r = 0; r < 3; ++r) {
+    #pragma unroll
+                for (int k = 0; k < 3; ++k) gM[r][k] += T0[r] * gV0[k] + T1[r] * gV1[k];
+                gT0[r] = gV0[0] * M[r][0] + gV0[1] * M[r][1] + gV0[2] * M[r][2];
+                gT1[r] = gV1[0] * M[r][0] + gV1[1] * M[r][1] + gV1[2] * M[r][2];
+            }
+            // T = J W (J01 = J10 = 0)
+            float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gJ00 += gT0[k] * V.R[k];
+                gJ02 += gT0[k] * V.R[6 + k];
+                gJ11 += gT1[k] * V.R[3 + k];
+                gJ12 += gT1[k] * V.R[6 + k];
+            }
+            const float rz2 = rz * rz;
+            float gtx = 0.f, gty = 0.f, gtz = 0.f;
+            gtz += -gJ00 * V.fx * rz2 - gJ11 * V.fy * rz2;
+            // J02 = -fx xc / z with xc = clamp(x/z)
+            gtz += gJ02 * V.fx * rxc * rz2;
+            gtz += gJ12 * V.fy * ryc * rz2;
+            if (inx) {
+                gtx += -gJ02 * V.fx * rz2;
+                gtz += gJ02 * V.fx * rx * rz2;
+            }
+            if (iny) {
+                gty += -gJ12 * V.fy * rz2;
+                gtz += gJ12 * V.fy * ry * rz2;
+            }
+            // mean2d = (fx x/z + cx, fy y/z + cy)
+            gtx += gmx * V.fx * rz;
+            gty += gmy * V.fy * rz;
+            gtz += -(gmx * V.fx * rx + gmy * V.fy * ry) * rz;
+            // t = W mean + t_cam
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) gmean[k] += V.R[k] * gtx + V.R[3 + k] * gty + V.R[6 + k] * gtz;
+            gop += g[5] * rho3 * rho2;
+            // colour
+            float d0 = mx - V.campos[0], d1 = my - V.campos[1], d2 = mz - V.campos[2];
+            const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            d0 *= dinv; d1 *= dinv; d2 *= dinv;
+            float Y[K];
+            sh_basis<DEG>(d0, d1, d2, Y);
+            float gcol[3] = {g[6], g[7], g[8]};
+    #pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.5f;
+    #pragma unroll
+                for (int k = 0; k < K; ++k) acc = fmaf(Y[k], ld_sh(3 * k + ch), acc);
+                if (acc < 0.f) gcol[ch] = 0.f;   // clamped at 0: no gradient
+    #pragma unroll
+                for (int k = 0; k < K; ++k) gsh[3 * k + ch][tl] += Y[k] * gcol[ch];
+            }
+            if (DEG > 0) {
+                float wk[K];
+    #pragma unroll
+                for (int k = 0; k < K; ++k)
+                    wk[k] = ld_sh(3 * k) * gcol[0] + ld_sh(3 * k + 1) * gcol[1] + ld_sh(3 * k + 2) * gcol[2];
+                float gd[3];
+                sh_grad_dot<DEG>(d0, d1, d2, wk, gd[0], gd[1], gd[2]);
+                const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+                gmean[0] += (gd[0] - dd * d0) * dinv;
+                gmean[1] += (gd[1] - dd * d1) * dinv;
+                gmean[2] += (gd[2] - dd * d2) * dinv;
+            }
+        }
+        if (!touched) return;
+        // M = R S: dS_k = sum_a dM[a][k] R[a][k], dR[a][k] = dM[a][k] s_k
+        float gR[3][3];
+        float gs[3] = {0.f, 0.f, 0.f};
+    #pragma unroll
+        for (int a = 0; a < 3; ++a)
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gs[k] += gM[a][k] * R[a][k];
+                gR[a][k] = gM[a][k] * se[k];
+            }
+        // through se_k = sqrt(s_k^2 + v) and rho3 = prod_j s_j / se_j:
+        // dse_k/ds_k = s_k / se_k, drho3/ds_k = rho3 v / (s_k se_k^2)
+        if (v3 > 0.f) {
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) gs[k] = gs[k] * (s[k] / se[k]) + g_rho3 * rho3 * v3 / (s[k] * se[k] * se[k]);
+        }
+        // R(q^) -> q^ (w, x, y, z)
+        float gqw = 2.f * (qz * (gR[1][0] - gR[0][1]) + qy * (gR[0][2] - gR[2][0]) + qx * (gR[2][1] - gR[1][2]));
+        float gqx = 2.f * (qy * (gR[0][1] + gR[1][0]) + qz * (gR[0][2] + gR[2][0]) + qw * (gR[2][1] - gR[1][2])) -
+                    4.f * qx * (gR[1][1] + gR[2][2]);
+        float gqy = 2.f * (qx * (gR[0][1] + gR[1][0]) + qz * (gR[1][2] + gR[2][1]) + qw * (gR[0][2] - gR[2][0])) -
+                    4.f * qy * (gR[0][0] + gR[2][2]);
+        float gqz = 2.f * (qx * (gR[0][2] + gR[2][0]) + qy * (gR[1][2] + gR[2][1]) + qw * (gR[1][0] - gR[0][1])) -
+                    4.f * qz * (gR[0][0] + gR[1][1]);
+        // normalisation q^ = q / |q|
+        const float dot = gqw * qw + gqx * qx + gqy * qy + gqz * qz;
+        gqw = (gqw - dot * qw) * qinv;
+        gqx = (gqx - dot * qx) * qinv;
+        gqy = (gqy - dot * qy) * qinv;
+        gqz = (gqz - dot * qz) * qinv;
+    #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            gV0[k] = 2.f * ga * V0[k] + gb * V1[k];
-            gV1[k] = gb * V0[k] + 2.f * gc * V1[k];
+            d_means[3 * i + k] += gmean[k];
+            d_scales[3 * i + k] += gs[k];
         }
-        // V = T M: dM += T^T dV, dT = dV M^T
-        float gT0[3], gT1[3];
+        d_quats[4 * i] += gqw;
+        d_quats[4 * i + 1] += gqx;
+        d_quats[4 * i + 2] += gqy;
+        d_quats[4 * i + 3] += gqz;
+        d_opac[i] += gop;
+        float *ds = d_sh + (size_t)i * K * 3;
+    #pragma unroll
+        for (int k = 0; k < K; ++k)
+    #pragma unroll
+            for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[3 * k + c][tl];
+    };
+    // the Gaussians of the warp's window with a gradient: index and view mask
+    __shared__ uint32_t s_idx[4][32 * kPbwdWin], s_msk[4][32 * kPbwdWin];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    // the views whose record of a Gaussian the replay blended (its nine
+    // partials are not all zero).  Only about 3% of the records of a 1080p
+    // view have tiles, so each warp first scans a window of 32 kPbwdWin
+    // Gaussians and lists the ones with a gradient; its lanes then take the
+    // listed Gaussians one each, and each lane walks only its Gaussian's
+    // views with a gradient.  A Gaussian no view blended has no gradient:
+    // nothing is added (this also keeps culled, non-finite parameters out
+    // of the chain rule).
+    const long long win = ((long long)blockIdx.x * 4 + wp) * (32 * kPbwdWin);
+    // (the window's loads of a view are independent: issued together)
+    uint32_t vm[kPbwdWin];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < kPbwdWin; ++r) vm[r] = 0u;
+#pragma unroll 2
+    for (int v = 0; v < vt.n_views; ++v) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gM[r][k] += T0[r] * gV0[k] + T1[r] * gV1[k];
-            gT0[r] = gV0[0] * M[r][0] + gV0[1] * M[r][1] + gV0[2] * M[r][2];
-            gT1[r] = gV1[0] * M[r][0] + gV1[1] * M[r][1] + gV1[2] * M[r][2];
-        }
-        // T = J W (J01 = J10 = 0)
-        float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
+        for (int r = 0; r < kPbwdWin; ++r) {
+            const long long gi = win + r * 32 + lane;
+            if (gi < n) {
+                const float *gg = g2d + ((size_t)v * n + gi) * kG;
+                bool any = false;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            gJ00 += gT0[k] * V.R[k];
-            gJ02 += gT0[k] * V.R[6 + k];
-            gJ11 += gT1[k] * V.R[3 + k];
-            gJ12 += gT1[k] * V.R[6 + k];
-        }
-        const float rz2 = rz * rz;
-        float gtx = 0.f, gty = 0.f, gtz = 0.f;
-        gtz += -gJ00 * V.fx * rz2 - gJ11 * V.fy * rz2;
-        // J02 = -fx xc / z with xc = clamp(x/z)
-        gtz += gJ02 * V.fx * rxc * rz2;
-        gtz += gJ12 * V.fy * ryc * rz2;
-        if (inx) {
-            gtx += -gJ02 * V.fx * rz2;
-            gtz += gJ02 * V.fx * rx * rz2;
-        }
-        if (iny) {
-            gty += -gJ12 * V.fy * rz2;
-            gtz += gJ12 * V.fy * ry * rz2;
-        }
-        // mean2d = (fx x/z + cx, fy y/z + cy)
-        gtx += gmx * V.fx * rz;
-        gty += gmy * V.fy * rz;
-        gtz += -(gmx * V.fx * rx + gmy * V.fy * ry) * rz;
-        // t = W mean + t_cam
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gmean[k] += V.R[k] * gtx + V.R[3 + k] * gty + V.R[6 + k] * gtz;
-        gop += g[5] * rho3 * rho2;
-        // colour
-        float d0 = mx - V.campos[0], d1 = my - V.campos[1], d2 = mz - V.campos[2];
-        const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        d0 *= dinv; d1 *= dinv; d2 *= dinv;
-        float Y[K];
-        sh_basis<DEG>(d0, d1, d2, Y);
-        float gcol[3] = {g[6], g[7], g[8]};
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.5f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], ld_sh(3 * k + ch), acc);
-            if (acc < 0.f) gcol[ch] = 0.f;   // clamped at 0: no gradient
-#pragma unroll
-            for (int k = 0; k < K; ++k) gsh[3 * k + ch][tl] += Y[k] * gcol[ch];
-        }
-        if (DEG > 0) {
-            float wk[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                wk[k] = ld_sh(3 * k) * gcol[0] + ld_sh(3 * k + 1) * gcol[1] + ld_sh(3 * k + 2) * gcol[2];
-            float gd[3];
-            sh_grad_dot<DEG>(d0, d1, d2, wk, gd[0], gd[1], gd[2]);
-            const float dd = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
-            gmean[0] += (gd[0] - dd * d0) * dinv;
-            gmean[1] += (gd[1] - dd * d1) * dinv;
-            gmean[2] += (gd[2] - dd * d2) * dinv;
+                for (int q = 0; q < kG; ++q) any |= gg[q] != 0.f;
+                if (any) vm[r] |= 1u << v;
+            }
         }
     }
-    // a Gaussian no view blended has no gradient: nothing to add (this also
-    // keeps culled, non-finite parameters out of the chain rule)
-    if (!touched) return;
-    // M = R S: dS_k = sum_a dM[a][k] R[a][k], dR[a][k] = dM[a][k] s_k
-    float gR[3][3];
-    float gs[3] = {0.f, 0.f, 0.f};
+    int listed = 0;                                   // warp-uniform
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            gs[k] += gM[a][k] * R[a][k];
-            gR[a][k] = gM[a][k] * se[k];
+    for (int r = 0; r < kPbwdWin; ++r) {
+        const unsigned bal = __ballot_sync(0xffffffffu, vm[r] != 0u);
+        if (vm[r] != 0u) {
+            const int pos = listed + __popc(bal & ((1u << lane) - 1u));
+            s_idx[wp][pos] = (uint32_t)(win + r * 32 + lane);
+            s_msk[wp][pos] = vm[r];
         }
-    // through se_k = sqrt(s_k^2 + v) and rho3 = prod_j s_j / se_j:
-    // dse_k/ds_k = s_k / se_k, drho3/ds_k = rho3 v / (s_k se_k^2)
-    if (v3 > 0.f) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) gs[k] = gs[k] * (s[k] / se[k]) + g_rho3 * rho3 * v3 / (s[k] * se[k] * se[k]);
+        listed += __popc(bal);
     }
-    // R(q^) -> q^ (w, x, y, z)
-    float gqw = 2.f * (qz * (gR[1][0] - gR[0][1]) + qy * (gR[0][2] - gR[2][0]) + qx * (gR[2][1] - gR[1][2]));
-    float gqx = 2.f * (qy * (gR[0][1] + gR[1][0]) + qz * (gR[0][2] + gR[2][0]) + qw * (gR[2][1] - gR[1][2])) -
-                4.f * qx * (gR[1][1] + gR[2][2]);
-    float gqy = 2.f * (qx * (gR[0][1] + gR[1][0]) + qz * (gR[1][2] + gR[2][1]) + qw * (gR[0][2] - gR[2][0])) -
-                4.f * qy * (gR[0][0] + gR[2][2]);
-    float gqz = 2.f * (qx * (gR[0][2] + gR[2][0]) + qy * (gR[1][2] + gR[2][1]) + qw * (gR[1][0] - gR[0][1])) -
-                4.f * qz * (gR[0][0] + gR[1][1]);
-    // normalisation q^ = q / |q|
-    const float dot = gqw * qw + gqx * qx + gqy * qy + gqz * qz;
-    gqw = (gqw - dot * qw) * qinv;
-    gqx = (gqx - dot * qx) * qinv;
-    gqy = (gqy - dot * qy) * qinv;
-    gqz = (gqz - dot * qz) * qinv;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        d_means[3 * i + k] += gmean[k];
-        d_scales[3 * i + k] += gs[k];
-    }
-    d_quats[4 * i] += gqw;
-    d_quats[4 * i + 1] += gqx;
-    d_quats[4 * i + 2] += gqy;
-    d_quats[4 * i + 3] += gqz;
-    d_opac[i] += gop;
-    float *ds = d_sh + (size_t)i * K * 3;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[3 * k + c][tl];
+    __syncwarp();
+    for (int e = lane; e < listed; e += 32) one_gaussian((int)s_idx[wp][e], s_msk[wp][e]);
 }
 
 template <int DEG>
@@ -783,7 +832,7 @@ cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const fl
                         const float *quats, const float *opac, const void *sh, bool f16, Filters flt,
                         const float *g2d, float *dm, float *ds, float *dq, float *dop, float *dsh,
                         cudaStream_t s) {
-    dim3 grid((n + 127) / 128);
+    dim3 grid((unsigned)(((long long)n + 128 * kPbwdWin - 1) / (128 * kPbwdWin)));
     if (f16)
         project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, dm, ds, dq, dop, dsh);
     else
