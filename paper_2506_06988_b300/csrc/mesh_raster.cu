@@ -55,7 +55,7 @@ mesh_vertex_kernel(ViewTable vt, int nv, const float *__restrict__ verts, double
     const long long m = (long long)vt.n_views * nv;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
-        const int v = (int)(it / nv);
+        const int v = (int)((uint32_t)it / (uint32_t)nv);   // m < 2^31
         const long long k = it - (long long)v * nv;
         const ViewDev &V = vt.v[v];
         const double x = verts[3 * k], y = verts[3 * k + 1], z = verts[3 * k + 2];
@@ -91,7 +91,7 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
     const long long m = (long long)vt.n_views * nf;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < m;
          it += (long long)gridDim.x * blockDim.x) {
-        const int v = (int)(it / nf);
+        const int v = (int)((uint32_t)it / (uint32_t)nf);   // m < 2^31
         const long long f = it - (long long)v * nf;
         const ViewDev &V = vt.v[v];
         FaceSetup s;
@@ -130,10 +130,12 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
                 const double d1 = izd[1] - izd[0], d2 = izd[2] - izd[0];
                 const double na = fma(d1, (double)e2y, -(d2 * (double)e1y));
                 const double nb = fma(d2, (double)e1x, -(d1 * (double)e2x));
-                s.af = __double2float_rn((na * 256.0) / (double)a2);
-                s.bf = __double2float_rn((nb * 256.0) / (double)a2);
+                // one FP64 division: 256 / a2 (a power-of-two multiple of 1 / a2)
+                const double inv = 256.0 / (double)a2;
+                s.af = __double2float_rn(na * inv);
+                s.bf = __double2float_rn(nb * inv);
                 s.iz0f = __double2float_rn(izd[0]);
-                s.rD = __double2float_rn(1.0 / (double)a2);
+                s.rD = __double2float_rn(inv * (1.0 / 256.0));
                 const long long mnx = min(s.x[0], min(s.x[1], s.x[2])), mxx = max(s.x[0], max(s.x[1], s.x[2]));
                 const long long mny = min(s.y[0], min(s.y[1], s.y[2])), mxy = max(s.y[0], max(s.y[1], s.y[2]));
                 // pixel centres 256 x + 128 inside [mn, mx]
@@ -142,8 +144,9 @@ mesh_face_kernel(ViewTable vt, int nv, int nf, const int32_t *__restrict__ faces
                 x0 = max(x0, 0ll); x1 = min(x1, (long long)V.W - 1);
                 y0 = max(y0, 0ll); y1 = min(y1, (long long)V.H - 1);
                 if (x0 <= x1 && y0 <= y1) {
-                    s.tx0 = (int)(x0 / vt.tile_w); s.tx1 = (int)(x1 / vt.tile_w);
-                    s.ty0 = (int)(y0 / vt.tile_h); s.ty1 = (int)(y1 / vt.tile_h);
+                    // (clamped to the image: 32-bit divisions)
+                    s.tx0 = (int)x0 / vt.tile_w; s.tx1 = (int)x1 / vt.tile_w;
+                    s.ty0 = (int)y0 / vt.tile_h; s.ty1 = (int)y1 / vt.tile_h;
                     for (int ty = s.ty0; ty <= s.ty1; ++ty)
                         for (int tx = s.tx0; tx <= s.tx1; ++tx)
                             atomicAdd(&tile_fcnt[V.tile_off + ty * V.tiles_x + tx], 1u);
@@ -165,7 +168,7 @@ mesh_emit_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup, cons
          it += (long long)gridDim.x * blockDim.x) {
         const FaceSetup &s = setup[it];
         if (s.tx0 > s.tx1) continue;
-        const ViewDev &V = vt.v[(int)(it / nf)];
+        const ViewDev &V = vt.v[(int)((uint32_t)it / (uint32_t)nf)];
         const int nx = s.tx1 - s.tx0 + 1, nt = nx * (s.ty1 - s.ty0 + 1);
         const uint32_t g0 = V.tile_off + s.ty0 * V.tiles_x + s.tx0;
         // slots four at a time (independent atomics in flight together), then the stores
@@ -279,14 +282,15 @@ __device__ __forceinline__ void bilinear(const void *tex, int tw, const TexTap &
 // int32 test (dx_k DY - dy_k DX) >= thr_k with thr_k = -E_k(O) clamped to
 // int32 (if |E_k(O)| >= 2^31 its sign decides alone, and the clamp keeps
 // that).  Larger faces take the exact int64 evaluation.
-struct CoverFace {
+// (16-byte aligned; what the int32 test reads fills the first 64 bytes)
+struct __align__(16) CoverFace {
     int dx[3], dy[3];   // edge vectors
     int thr[3];         // small faces: int32 thresholds
-    long long e0[3];    // E_k(O), exact
-    int small;          // the int32 test applies
     int x0, y0;         // snapped vertex 0 (depth plane origin)
-    float af, bf, iz0f;
     uint32_t f;
+    float af, bf, iz0f;
+    int small;          // the int32 test applies
+    long long e0[3];    // E_k(O), exact
 };
 
 // One CTA per screen tile; a thread owns two pixels of one column (rows y
@@ -294,7 +298,7 @@ struct CoverFace {
 // resolves both, their loads issued together (face set-ups, then texels) so
 // that two dependent load chains are in flight.
 template <int TW, int TH, bool F32TEX>
-__global__ void __launch_bounds__(TW *TH / 2)
+__global__ void __launch_bounds__(TW *TH / 2, 10)
 mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
                  const uint32_t *__restrict__ tile_foff, const uint32_t *__restrict__ tile_fcnt,
                  const long long *n_items, const uint32_t *__restrict__ items,
