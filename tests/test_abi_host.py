@@ -103,7 +103,7 @@ def test_workspace_sizes_grow_with_the_problem(hm):
     a = lib.hm_bin_sort_workspace_size(cams, 1000, 10_000, o)
     b = lib.hm_bin_sort_workspace_size(cams, 2000, 10_000, o)
     c = lib.hm_bin_sort_workspace_size(cams, 1000, 100_000, o)
-    assert 0 < a <= b and a < c          # per-pair and per-tile scratch; none per record
+    assert 0 < a < b and a < c           # per-record list, per-pair and per-tile scratch
     r1 = lib.hm_rasterize_mesh_workspace_size(cams, 100, 200, 5000, o)
     r2 = lib.hm_rasterize_mesh_workspace_size(cams, 100, 200, 50_000, o)
     assert 0 < r1 < r2
