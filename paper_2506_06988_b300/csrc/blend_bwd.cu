@@ -387,7 +387,10 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     // tile's box, scale and flush set-up is shared by PX pixels
     constexpr int NT = TW * TH / PX;
     static_assert(NT % 32 == 0 && TH % PX == 0, "whole warps");
-    __shared__ int s_acc[kTexCap * 4];      // per texel: 3 fixed-point sums, then (after them) the largest tap
+    // per texel: the fixed-point sums of the three channels (one plane each,
+    // so a warp's consecutive texels fall in consecutive banks), then the
+    // largest tap
+    __shared__ int s_acc[kTexCap * 4];
     __shared__ int s_box[4];
     const int gt = blockIdx.x;
     const int v = view_of_tile(vt, gt);
@@ -474,8 +477,12 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     // 16x16.
     int *mx = s_acc + kTexCap * 3;
     const int ncell = bw * bh;
-    for (int i = t; i < ncell * 3; i += NT) s_acc[i] = 0;
-    for (int i = t; i < ncell; i += NT) mx[i] = 0;
+    for (int i = t; i < ncell; i += NT) {
+        s_acc[i] = 0;
+        s_acc[kTexCap + i] = 0;
+        s_acc[2 * kTexCap + i] = 0;
+        mx[i] = 0;
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
@@ -509,14 +516,14 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
             if (w[k] == 0.f) continue;
             const int c = (ys[k] - by0) * bw + (xs[k] - bx0);
             const float ui = unit_inv(mx[c]);
-            atomicAdd(s_acc + 3 * c, __float2int_rn(w[k] * g0[q] * ui));
-            atomicAdd(s_acc + 3 * c + 1, __float2int_rn(w[k] * g1[q] * ui));
-            atomicAdd(s_acc + 3 * c + 2, __float2int_rn(w[k] * g2[q] * ui));
+            atomicAdd(s_acc + c, __float2int_rn(w[k] * g0[q] * ui));
+            atomicAdd(s_acc + kTexCap + c, __float2int_rn(w[k] * g1[q] * ui));
+            atomicAdd(s_acc + 2 * kTexCap + c, __float2int_rn(w[k] * g2[q] * ui));
         }
     }
     __syncthreads();
     for (int i = t; i < ncell; i += NT) {
-        const int r = s_acc[3 * i], gg = s_acc[3 * i + 1], b = s_acc[3 * i + 2];
+        const int r = s_acc[i], gg = s_acc[kTexCap + i], b = s_acc[2 * kTexCap + i];
         if (r != 0 || gg != 0 || b != 0) {
             const float u = unit(mx[i]);
             red_texel(d_tex, (size_t)(by0 + i / bw) * tw + (bx0 + i % bw), (float)r * u, (float)gg * u,
