@@ -195,16 +195,17 @@ struct TexTap {
 // what the resolve of a covered pixel needs of its face
 struct TexFace {
     int x0, y0;                 // snapped vertex 0
-    int e1x, e1y, e2x, e2y;     // snapped edges from vertex 0
+    float e1x, e1y, e2x, e2y;   // snapped edges from vertex 0 (exact integers, rounded to FP32 once)
     float rD, izf1, izf2;       // 1 / signed double area, 1/z of vertices 1 and 2
     float u0, v0, du1, dv1, du2, dv2;
 };
 
+// (snapped coordinates stay within +-2^29, so the differences fit int32)
 __device__ __forceinline__ TexFace tex_face(const FaceSetup &g) {
     TexFace f;
     f.x0 = g.x[0]; f.y0 = g.y[0];
-    f.e1x = g.x[1] - g.x[0]; f.e1y = g.y[1] - g.y[0];
-    f.e2x = g.x[2] - g.x[0]; f.e2y = g.y[2] - g.y[0];
+    f.e1x = __int2float_rn(g.x[1] - g.x[0]); f.e1y = __int2float_rn(g.y[1] - g.y[0]);
+    f.e2x = __int2float_rn(g.x[2] - g.x[0]); f.e2y = __int2float_rn(g.y[2] - g.y[0]);
     f.rD = g.rD; f.izf1 = g.izf[1]; f.izf2 = g.izf[2];
     f.u0 = g.u0; f.v0 = g.v0; f.du1 = g.du1; f.dv1 = g.dv1; f.du2 = g.du2; f.dv2 = g.dv2;
     return f;
@@ -214,11 +215,9 @@ __device__ __forceinline__ TexTap tex_tap(const TexFace &s, int px, int py, floa
     TexTap r;
     // perspective-correct barycentrics b_k = l_k (1/z_k) z, l_k the
     // screen-space ones of the offset from vertex 0 (Cramer's rule)
-    // (snapped coordinates stay within +-2^29, so the differences fit int32)
     const float dx = __int2float_rn(px * 256 + 128 - s.x0);
     const float dy = __int2float_rn(py * 256 + 128 - s.y0);
-    const float e1x = __int2float_rn(s.e1x), e1y = __int2float_rn(s.e1y);
-    const float e2x = __int2float_rn(s.e2x), e2y = __int2float_rn(s.e2y);
+    const float e1x = s.e1x, e1y = s.e1y, e2x = s.e2x, e2y = s.e2y;
     const float l1 = fmaf(dx, e2y, -dy * e2x) * s.rD;
     const float l2 = fmaf(e1x, dy, -e1y * dx) * s.rD;
     const float b1 = l1 * s.izf1 * D, b2 = l2 * s.izf2 * D;
