@@ -69,8 +69,8 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURE = {
     # stage: (warp instructions, DRAM bytes, units, unit kind, pixels, source hash)
-    "blend_forward": (202_430_460, 219_206_912, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "38b741871cc74f09"),
-    "blend_backward": (294_419_167, 212_150_272, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "7631cfebd213ff54"),
+    "blend_forward": (202_430_464, 219_355_648, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "38b741871cc74f09"),
+    "blend_backward": (294_419_167, 212_260_096, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "1a62c30581c8c6ec"),
 }
 
 
