@@ -378,15 +378,28 @@ __device__ __forceinline__ void red_texel(float *d_tex, size_t t, float r, float
 // (it straddles charts) reduces straight to global memory.
 constexpr int kTexCap = 768;
 
+// The bilinear footprint of one pixel: its four texels (clamped), weights and
+// the T-weighted upstream gradient.
+struct TexTaps {
+    bool act;
+    float g0, g1, g2, gm;        // gradient per channel, its largest magnitude
+    int xa, xb, ya, yb;          // texel columns and rows
+    float w[4];                  // weights of (xa,ya), (xb,ya), (xa,yb), (xb,yb)
+};
+
+// A thread owns two horizontally adjacent pixels of one row (x, x + 1), so
+// the tile's box, scale and flush set-up is shared by them; where the
+// texture is magnified they usually sample the same four texels, and their
+// taps are then merged in registers before the shared-memory atomics
+// (neighbouring pixels' atomics on one texel serialise).
 template <int TW, int TH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX)
 texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const float *__restrict__ uv,
                    const float *__restrict__ out_T, const float *__restrict__ dL_drgb,
                    const float *__restrict__ dL_dmesh, int tw, int th, float *__restrict__ d_tex) {
-    // a thread owns PX pixels of one column, rows y + q TH / PX, so the
-    // tile's box, scale and flush set-up is shared by PX pixels
-    constexpr int NT = TW * TH / PX;
-    static_assert(NT % 32 == 0 && TH % PX == 0, "whole warps");
+    static_assert(PX == 2 && TW % 2 == 0, "pixel pairs along a row");
+    constexpr int NT = TW * TH / 2;
+    static_assert(NT % 32 == 0, "whole warps");
     // per texel: the fixed-point sums of the three channels (one plane each,
     // so a warp's consecutive texels fall in consecutive banks), then the
     // largest tap
@@ -397,41 +410,47 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const ViewDev &V = vt.v[v];
     const int local = gt - V.tile_off;
     const int t = threadIdx.x;
-    const int px = (local % V.tiles_x) * TW + (t % TW);
+    const int px0 = (local % V.tiles_x) * TW + (t % (TW / 2)) * 2;
+    const int py = (local / V.tiles_x) * TH + t / (TW / 2);
     const long long npx = (long long)V.W * V.H;
-    bool act[PX];
-    float g0[PX], g1[PX], g2[PX], fx[PX], fy[PX];
-    int xa[PX], xb[PX], ya[PX], yb[PX];
+    TexTaps tp[2];
     int mx0 = 0x7fffffff, mx1 = -1, my0 = 0x7fffffff, my1 = -1;
 #pragma unroll
-    for (int q = 0; q < PX; ++q) {
-        const int py = (local / V.tiles_x) * TH + (t / TW) + q * (TH / PX);
+    for (int q = 0; q < 2; ++q) {
+        TexTaps &a = tp[q];
+        const int px = px0 + q;
         const bool inside = px < V.W && py < V.H;
         const long long lp = (long long)py * V.W + px;
         const long long gp = V.pix_off + lp;
-        act[q] = inside && mesh_depth[gp] < INFINITY;
-        g0[q] = g1[q] = g2[q] = fx[q] = fy[q] = 0.f;
+        a.act = inside && mesh_depth[gp] < INFINITY;
+        a.g0 = a.g1 = a.g2 = 0.f;
+        float fx = 0.f, fy = 0.f;
         int ix = 0, iy = 0;
-        if (act[q]) {
+        if (a.act) {
             const float T = out_T[gp];
             const float *g = dL_drgb + 3 * V.pix_off + lp;
-            g0[q] = T * g[0]; g1[q] = T * g[npx]; g2[q] = T * g[2 * npx];
+            a.g0 = T * g[0]; a.g1 = T * g[npx]; a.g2 = T * g[2 * npx];
             if (dL_dmesh) {   // a loss on the mesh colour itself (no T factor)
                 const float *gm = dL_dmesh + 3 * V.pix_off + lp;
-                g0[q] += gm[0]; g1[q] += gm[npx]; g2[q] += gm[2 * npx];
+                a.g0 += gm[0]; a.g1 += gm[npx]; a.g2 += gm[2 * npx];
             }
             const float *u = uv + 2 * V.pix_off + lp;
             const float ss = u[0] * (float)tw - 0.5f, tt = u[npx] * (float)th - 0.5f;
             const float x0 = floorf(ss), y0 = floorf(tt);
-            fx[q] = ss - x0; fy[q] = tt - y0;
+            fx = ss - x0; fy = tt - y0;
             ix = (int)fmaxf(fminf(x0, 1e8f), -1e8f);
             iy = (int)fmaxf(fminf(y0, 1e8f), -1e8f);
         }
-        xa[q] = min(max(ix, 0), tw - 1); xb[q] = min(max(ix + 1, 0), tw - 1);
-        ya[q] = min(max(iy, 0), th - 1); yb[q] = min(max(iy + 1, 0), th - 1);
-        if (act[q]) {
-            mx0 = min(mx0, xa[q]); mx1 = max(mx1, xb[q]);
-            my0 = min(my0, ya[q]); my1 = max(my1, yb[q]);
+        a.gm = fmaxf(fabsf(a.g0), fmaxf(fabsf(a.g1), fabsf(a.g2)));
+        a.xa = min(max(ix, 0), tw - 1); a.xb = min(max(ix + 1, 0), tw - 1);
+        a.ya = min(max(iy, 0), th - 1); a.yb = min(max(iy + 1, 0), th - 1);
+        a.w[0] = (1.f - fx) * (1.f - fy);
+        a.w[1] = fx * (1.f - fy);
+        a.w[2] = (1.f - fx) * fy;
+        a.w[3] = fx * fy;
+        if (a.act) {
+            mx0 = min(mx0, a.xa); mx1 = max(mx1, a.xb);
+            my0 = min(my0, a.ya); my1 = max(my1, a.yb);
         }
     }
     if (t == 0) {
@@ -452,29 +471,32 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     const int bx0 = s_box[0], by0 = s_box[2];
     if (s_box[1] < 0) return;
     const int bw = s_box[1] - bx0 + 1, bh = s_box[3] - by0 + 1;
+    // the pair's footprints coincide: one merged set of four taps
+    const bool same = tp[0].act && tp[1].act && tp[0].xa == tp[1].xa && tp[0].xb == tp[1].xb &&
+                      tp[0].ya == tp[1].ya && tp[0].yb == tp[1].yb;
     if ((long long)bw * bh > kTexCap) {
 #pragma unroll
-        for (int q = 0; q < PX; ++q) {
-            if (!act[q]) continue;
-            const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
-                                fx[q] * fy[q]};
-            const int xs[4] = {xa[q], xb[q], xa[q], xb[q]}, ys[4] = {ya[q], ya[q], yb[q], yb[q]};
+        for (int q = 0; q < 2; ++q) {
+            const TexTaps &a = tp[q];
+            if (!a.act) continue;
+            const int xs[4] = {a.xa, a.xb, a.xa, a.xb}, ys[4] = {a.ya, a.ya, a.yb, a.yb};
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (w[k] != 0.f)
-                    red_texel(d_tex, (size_t)ys[k] * tw + xs[k], w[k] * g0[q], w[k] * g1[q], w[k] * g2[q]);
+                if (a.w[k] != 0.f)
+                    red_texel(d_tex, (size_t)ys[k] * tw + xs[k], a.w[k] * a.g0, a.w[k] * a.g1, a.w[k] * a.g2);
         }
         return;
     }
     // Per-texel fixed point (native int32 shared atomics, exact and
     // order-independent sums).  Pass 1 takes, per texel, the largest tap
     // magnitude M over its three channels (the bits of a non-negative float
-    // order like the float).  Pass 2 adds each tap in units of 2^(e - 19),
-    // 2^e <= M < 2^(e+1): a tap is rounded to at most 2^-20 M, so a texel's
-    // sums carry the rounding of its own taps whatever the tile's other
-    // texels receive.  A pixel sends at most weight 1 to a texel (its taps
-    // coincide only at a clamped edge), so |sum| <= 256 M < 2^28 units at
-    // 16x16.
+    // order like the float; a merged pair's tap counts as one).  Pass 2 adds
+    // each tap in units of
+    // 2^(e - 19), 2^e <= M < 2^(e+1): a tap is rounded to at most 2^-20 M, so
+    // a texel's sums carry the rounding of its own taps whatever the tile's
+    // other texels receive.  Every tap is at most M, a footprint's four taps
+    // coincide only at a clamped corner and a tile holds at most 256
+    // footprints, so |sum| <= 1024 M < 2^30 units.
     int *mx = s_acc + kTexCap * 3;
     const int ncell = bw * bh;
     for (int i = t; i < ncell; i += NT) {
@@ -484,16 +506,32 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         mx[i] = 0;
     }
     __syncthreads();
+    // tap k of the thread's footprint(s): value per channel and its largest
+    // magnitude (0 for a zero weight)
+    auto taps = [&](int q, int k, float &v0, float &v1, float &v2, float &m) {
+        if (same) {
+            const float wa = tp[0].w[k], wb = tp[1].w[k];
+            v0 = fmaf(wa, tp[0].g0, wb * tp[1].g0);
+            v1 = fmaf(wa, tp[0].g1, wb * tp[1].g1);
+            v2 = fmaf(wa, tp[0].g2, wb * tp[1].g2);
+            m = fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2)));
+        } else {
+            const float w = tp[q].w[k];
+            v0 = w * tp[q].g0; v1 = w * tp[q].g1; v2 = w * tp[q].g2;
+            m = w * tp[q].gm;
+        }
+    };
+    const int nq = same ? 1 : 2;
+    for (int q = 0; q < nq; ++q) {
+        if (!tp[q].act) continue;
+        const int xs[4] = {tp[q].xa, tp[q].xb, tp[q].xa, tp[q].xb};
+        const int ys[4] = {tp[q].ya, tp[q].ya, tp[q].yb, tp[q].yb};
 #pragma unroll
-    for (int q = 0; q < PX; ++q) {
-        if (!act[q]) continue;
-        const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
-                            fx[q] * fy[q]};
-        const int xs[4] = {xa[q], xb[q], xa[q], xb[q]}, ys[4] = {ya[q], ya[q], yb[q], yb[q]};
-        const float gm = fmaxf(fabsf(g0[q]), fmaxf(fabsf(g1[q]), fabsf(g2[q])));
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (w[k] != 0.f) atomicMax(mx + (ys[k] - by0) * bw + (xs[k] - bx0), __float_as_int(w[k] * gm));
+        for (int k = 0; k < 4; ++k) {
+            float v0, v1, v2, m;
+            taps(q, k, v0, v1, v2, m);
+            if (m != 0.f) atomicMax(mx + (ys[k] - by0) * bw + (xs[k] - bx0), __float_as_int(m));
+        }
     }
     __syncthreads();
     // 2^(19 - e) and 2^(e - 19) for the texel whose largest tap has exponent e
@@ -505,20 +543,20 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
         const int e = ((mbits >> 23) & 0xff) - 127;
         return __int_as_float((127 - min(max(19 - e, -126), 127)) << 23);
     };
-#pragma unroll
-    for (int q = 0; q < PX; ++q) {
-        if (!act[q]) continue;
-        const float w[4] = {(1.f - fx[q]) * (1.f - fy[q]), fx[q] * (1.f - fy[q]), (1.f - fx[q]) * fy[q],
-                            fx[q] * fy[q]};
-        const int xs[4] = {xa[q], xb[q], xa[q], xb[q]}, ys[4] = {ya[q], ya[q], yb[q], yb[q]};
+    for (int q = 0; q < nq; ++q) {
+        if (!tp[q].act) continue;
+        const int xs[4] = {tp[q].xa, tp[q].xb, tp[q].xa, tp[q].xb};
+        const int ys[4] = {tp[q].ya, tp[q].ya, tp[q].yb, tp[q].yb};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (w[k] == 0.f) continue;
+            float v0, v1, v2, m;
+            taps(q, k, v0, v1, v2, m);
+            if (m == 0.f) continue;
             const int c = (ys[k] - by0) * bw + (xs[k] - bx0);
             const float ui = unit_inv(mx[c]);
-            atomicAdd(s_acc + c, __float2int_rn(w[k] * g0[q] * ui));
-            atomicAdd(s_acc + kTexCap + c, __float2int_rn(w[k] * g1[q] * ui));
-            atomicAdd(s_acc + 2 * kTexCap + c, __float2int_rn(w[k] * g2[q] * ui));
+            atomicAdd(s_acc + c, __float2int_rn(v0 * ui));
+            atomicAdd(s_acc + kTexCap + c, __float2int_rn(v1 * ui));
+            atomicAdd(s_acc + 2 * kTexCap + c, __float2int_rn(v2 * ui));
         }
     }
     __syncthreads();
