@@ -10,7 +10,7 @@
 //   scan + emit   per-tile offsets; each face's index into the bucket of
 //                 every tile it touches (atomic slots: the order within a
 //                 bucket does not matter);
-//   tile pass     one CTA per tile, a thread per two pixels of a column:
+//   tile pass     one CTA per tile, a thread per two adjacent pixels of a row:
 //                 for every face of the tile's bucket, exact int64 edge
 //                 functions with the top-left rule at the pixel centres; the
 //                 face's affine 1/z in FP32, packed with the inverted face
@@ -242,32 +242,43 @@ __device__ __forceinline__ TexTap tex_tap(const TexFace &s, int px, int py, floa
 }
 
 // bilinear clamp-to-edge fetch: the four texels' channels are read at
-// immediate offsets from per-texel base pointers; RGB8 sums the weighted
-// bytes and scales by 1/255 once per channel
+// immediate offsets from per-texel base pointers (RGB8: the byte values);
+// the mix sums the weighted values and, for RGB8, scales by 1/255 once per
+// channel
 template <bool F32TEX>
-__device__ __forceinline__ void bilinear(const void *tex, int tw, const TexTap &a, float &c0, float &c1,
-                                         float &c2) {
+__device__ __forceinline__ void texels(const void *tex, int tw, const TexTap &a, float (&tv)[4][3]) {
     const size_t r0 = (size_t)a.y0 * (size_t)tw * 3, r1 = (size_t)a.y1 * (size_t)tw * 3;
     const int x0 = a.x0 * 3, x1 = a.x1 * 3;
-    float cc[3];
     if (F32TEX) {
         const float *T = reinterpret_cast<const float *>(tex);
         const float *p00 = T + r0 + x0, *p10 = T + r0 + x1, *p01 = T + r1 + x0, *p11 = T + r1 + x1;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch)
-            cc[ch] = a.w00 * __ldg(p00 + ch) + a.w10 * __ldg(p10 + ch) + a.w01 * __ldg(p01 + ch) +
-                     a.w11 * __ldg(p11 + ch);
+        for (int ch = 0; ch < 3; ++ch) {
+            tv[0][ch] = __ldg(p00 + ch);
+            tv[1][ch] = __ldg(p10 + ch);
+            tv[2][ch] = __ldg(p01 + ch);
+            tv[3][ch] = __ldg(p11 + ch);
+        }
     } else {
         const unsigned char *T = reinterpret_cast<const unsigned char *>(tex);
         const unsigned char *p00 = T + r0 + x0, *p10 = T + r0 + x1, *p01 = T + r1 + x0, *p11 = T + r1 + x1;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch)
-            cc[ch] = (a.w00 * (float)__ldg(p00 + ch) + a.w10 * (float)__ldg(p10 + ch) +
-                      a.w01 * (float)__ldg(p01 + ch) + a.w11 * (float)__ldg(p11 + ch)) * (1.0f / 255.0f);
+        for (int ch = 0; ch < 3; ++ch) {
+            tv[0][ch] = (float)__ldg(p00 + ch);
+            tv[1][ch] = (float)__ldg(p10 + ch);
+            tv[2][ch] = (float)__ldg(p01 + ch);
+            tv[3][ch] = (float)__ldg(p11 + ch);
+        }
     }
-    c0 = cc[0];
-    c1 = cc[1];
-    c2 = cc[2];
+}
+
+template <bool F32TEX>
+__device__ __forceinline__ void bilinear_mix(const TexTap &a, const float (&tv)[4][3], float *c) {
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float s = a.w00 * tv[0][ch] + a.w10 * tv[1][ch] + a.w01 * tv[2][ch] + a.w11 * tv[3][ch];
+        c[ch] = F32TEX ? s : s * (1.0f / 255.0f);
+    }
 }
 
 // What the coverage test of a tile needs of a face, prepared once per
@@ -292,10 +303,12 @@ struct __align__(16) CoverFace {
     long long e0[3];    // E_k(O), exact
 };
 
-// One CTA per screen tile; a thread owns two pixels of one column (rows y
-// and y + TH/2): it finds their nearest faces among the tile's bucket, then
-// resolves both, their loads issued together (face set-ups, then texels) so
-// that two dependent load chains are in flight.
+// One CTA per screen tile; a thread owns two horizontally adjacent pixels of
+// one row (x, x + 1): it finds their nearest faces among the tile's bucket
+// (the plane's b V + 1/z0 term is shared by the pair), then resolves both --
+// one texel fetch when both sample the same four texels, as they mostly do
+// where the texture is magnified -- and stores the pair's G-buffer entries
+// as 8-byte vectors when they are aligned.
 template <int TW, int TH, bool F32TEX>
 __global__ void __launch_bounds__(TW *TH / 2, 10)
 mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
@@ -304,6 +317,7 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
                  const void *__restrict__ tex, int tw, int th, float bg0, float bg1, float bg2,
                  int32_t *__restrict__ tri_id, float *__restrict__ depth, float *__restrict__ rgb,
                  float *__restrict__ uv_out, float *__restrict__ tile_max) {
+    static_assert(TW % 2 == 0, "pixel pairs along a row");
     constexpr int NT = TW * TH / 2;
     __shared__ float s_max[NT / 32];
     __shared__ CoverFace s_face[NT];
@@ -314,24 +328,19 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     const int local = gt - V.tile_off;
     const int tx = local % V.tiles_x, ty = local / V.tiles_x;
     const int t = threadIdx.x;
-    const int px = tx * TW + (t % TW);
-    const int py[2] = {ty * TH + (t / TW), ty * TH + (t / TW) + TH / 2};
+    const int lx = (t % (TW / 2)) * 2, ly = t / (TW / 2);   // pixel a's place in the tile
+    const int px = tx * TW + lx, py = ty * TH + ly;         // pixel a; pixel b is (px + 1, py)
     const long long npx = (long long)V.W * V.H;
-    bool in[2];
-    long long lp[2];
+    const bool in[2] = {px < V.W && py < V.H, px + 1 < V.W && py < V.H};
+    const long long lp = (long long)py * V.W + px;
     long long key[2] = {LLONG_MIN, LLONG_MIN};     // no face
     uint32_t slot[2] = {0u, 0u};                   // bucket position of the key's face
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        in[q] = px < V.W && py[q] < V.H;
-        lp[q] = (long long)py[q] * V.W + px;
-    }
     // coverage: every face of the bucket against both pixel centres.  The
     // faces' edge and depth data are staged in shared memory NT at a time
     // (one face per thread, loads in parallel), then every thread walks them.
     const uint32_t fc = *n_items > 0 ? tile_fcnt[gt] : 0u, f0 = tile_foff[gt];
-    const int PX = px * 256 + 128, PY = py[0] * 256 + 128;
-    const int DX = (t % TW) * 256, DY = (t / TW) * 256;   // offset from the tile's first pixel centre
+    const int PX = px * 256 + 128, PY = py * 256 + 128;
+    const int DX = lx * 256, DY = ly * 256;         // offset from the tile's first pixel centre
     for (uint32_t r0 = 0; r0 < fc; r0 += NT) {
         const int nb = (int)min((uint32_t)NT, fc - r0);
         __syncthreads();                             // the previous round's faces are consumed
@@ -367,19 +376,20 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         __syncthreads();
         for (int k = 0; k < nb; ++k) {
             const CoverFace &s = s_face[k];
+            // pixel b lies 256 units right of a: E_k(b) = E_k(a) - 256 dy_k
             bool cov0 = true, cov1 = true;
             if (s.small) {
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
                     const int d0 = s.dx[e] * DY - s.dy[e] * DX;
                     cov0 = cov0 && d0 >= s.thr[e];
-                    cov1 = cov1 && d0 + s.dx[e] * (256 * (TH / 2)) >= s.thr[e];
+                    cov1 = cov1 && d0 - s.dy[e] * 256 >= s.thr[e];
                 }
             } else {
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
                     const long long E0 = s.e0[e] + (long long)s.dx[e] * DY - (long long)s.dy[e] * DX;
-                    const long long E1 = E0 + (long long)s.dx[e] * (256 * (TH / 2));
+                    const long long E1 = E0 - (long long)s.dy[e] * 256;
                     cov0 = cov0 && E0 >= 0;
                     cov1 = cov1 && E1 >= 0;
                 }
@@ -387,17 +397,19 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
             // the 1/z of the face at the pixel centre; the key orders by it
             // (signed: a negative value, possible only through rounding at a
             // sliver, never beats a positive one), then by the lower index
-            const float U = __fmul_rn(__int2float_rn(PX - s.x0), 0.00390625f);
+            if (!((cov0 && in[0]) || (cov1 && in[1]))) continue;
+            const float Vv = __fmul_rn(__int2float_rn(PY - s.y0), 0.00390625f);
+            const float bv = __fmaf_rn(s.bf, Vv, s.iz0f);
             const unsigned long long fkey = ~s.f;
             if (cov0 && in[0]) {
-                const float Vv = __fmul_rn(__int2float_rn(PY - s.y0), 0.00390625f);
-                const float iz = __fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f));
+                const float U = __fmul_rn(__int2float_rn(PX - s.x0), 0.00390625f);
+                const float iz = __fmaf_rn(s.af, U, bv);
                 const long long kk = (long long)(((unsigned long long)__float_as_uint(iz) << 32) | (fkey & 0xFFFFFFFFull));
                 if (kk > key[0]) { key[0] = kk; slot[0] = r0 + k; }
             }
             if (cov1 && in[1]) {
-                const float Vv = __fmul_rn(__int2float_rn(PY + 256 * (TH / 2) - s.y0), 0.00390625f);
-                const float iz = __fmaf_rn(s.af, U, __fmaf_rn(s.bf, Vv, s.iz0f));
+                const float U = __fmul_rn(__int2float_rn(PX + 256 - s.x0), 0.00390625f);
+                const float iz = __fmaf_rn(s.af, U, bv);
                 const long long kk = (long long)(((unsigned long long)__float_as_uint(iz) << 32) | (fkey & 0xFFFFFFFFull));
                 if (kk > key[1]) { key[1] = kk; slot[1] = r0 + k; }
             }
@@ -418,33 +430,65 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
     TexTap tap[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-        if (hit[q]) tap[q] = tex_tap(fs[q], px, py[q], D[q], tw, th);
-    float c[2][3];
+        if (hit[q]) tap[q] = tex_tap(fs[q], px + q, py, D[q], tw, th);
+    float c[2][3] = {{bg0, bg1, bg2}, {bg0, bg1, bg2}};
+    if (hit[0] && hit[1] && tap[0].x0 == tap[1].x0 && tap[0].x1 == tap[1].x1 && tap[0].y0 == tap[1].y0 &&
+        tap[0].y1 == tap[1].y1) {
+        float tv[4][3];
+        texels<F32TEX>(tex, tw, tap[0], tv);
+        bilinear_mix<F32TEX>(tap[0], tv, c[0]);
+        bilinear_mix<F32TEX>(tap[1], tv, c[1]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        c[q][0] = bg0;
-        c[q][1] = bg1;
-        c[q][2] = bg2;
-        if (hit[q]) bilinear<F32TEX>(tex, tw, tap[q], c[q][0], c[q][1], c[q][2]);
+        for (int q = 0; q < 2; ++q)
+            if (hit[q]) {
+                float tv[4][3];
+                texels<F32TEX>(tex, tw, tap[q], tv);
+                bilinear_mix<F32TEX>(tap[q], tv, c[q]);
+            }
     }
     float m = -INFINITY;   // neutral for the max over in-image pixels
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (!in[q]) continue;
-        m = fmaxf(m, D[q]);
-        const long long gp = V.pix_off + lp[q];
-        if (tri_id) tri_id[gp] = hit[q] ? (int)fid[q] : -1;
-        if (depth) depth[gp] = D[q];
+    if (in[0]) m = D[0];
+    if (in[1]) m = fmaxf(m, D[1]);
+    const int32_t id[2] = {hit[0] ? (int)fid[0] : -1, hit[1] ? (int)fid[1] : -1};
+    const float uu[2] = {hit[0] ? tap[0].u : 0.f, hit[1] ? tap[1].u : 0.f};
+    const float ww[2] = {hit[0] ? tap[0].w : 0.f, hit[1] ? tap[1].w : 0.f};
+    const long long gp = V.pix_off + lp;
+    // 8-byte vector stores: both pixels in the image, every plane offset and
+    // output pointer even in elements
+    const bool vec = in[1] && ((V.pix_off | lp | npx) & 1) == 0 &&
+                     (((uintptr_t)tri_id | (uintptr_t)depth | (uintptr_t)rgb | (uintptr_t)uv_out) & 7) == 0;
+    if (vec) {
+        if (tri_id) *reinterpret_cast<int2 *>(tri_id + gp) = make_int2(id[0], id[1]);
+        if (depth) *reinterpret_cast<float2 *>(depth + gp) = make_float2(D[0], D[1]);
         if (rgb) {
-            float *o = rgb + 3 * V.pix_off + lp[q];
-            o[0] = c[q][0];
-            o[npx] = c[q][1];
-            o[2 * npx] = c[q][2];
+            float *o = rgb + 3 * V.pix_off + lp;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                *reinterpret_cast<float2 *>(o + ch * npx) = make_float2(c[0][ch], c[1][ch]);
         }
         if (uv_out) {
-            float *o = uv_out + 2 * V.pix_off + lp[q];
-            o[0] = hit[q] ? tap[q].u : 0.f;
-            o[npx] = hit[q] ? tap[q].w : 0.f;
+            float *o = uv_out + 2 * V.pix_off + lp;
+            *reinterpret_cast<float2 *>(o) = make_float2(uu[0], uu[1]);
+            *reinterpret_cast<float2 *>(o + npx) = make_float2(ww[0], ww[1]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!in[q]) continue;
+            if (tri_id) tri_id[gp + q] = id[q];
+            if (depth) depth[gp + q] = D[q];
+            if (rgb) {
+                float *o = rgb + 3 * V.pix_off + lp + q;
+                o[0] = c[q][0];
+                o[npx] = c[q][1];
+                o[2 * npx] = c[q][2];
+            }
+            if (uv_out) {
+                float *o = uv_out + 2 * V.pix_off + lp + q;
+                o[0] = uu[q];
+                o[npx] = ww[q];
+            }
         }
     }
     // farthest mesh depth of the tile (+inf if any in-image pixel misses)
