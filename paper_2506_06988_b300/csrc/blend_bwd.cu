@@ -136,16 +136,18 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             B2[p] = make_float2(bg2, bg2);
             la[p] = lb[p] = 0;
             fpy[p] = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
-            if (in_a) {
+            // a pixel that blended nothing has nothing to replay: its other
+            // inputs are not read
+            if (in_a) la[p] = last_idx[V.pix_off + lpa];
+            if (in_b) lb[p] = last_idx[V.pix_off + lpb];
+            if (la[p] > 0) {
                 Tf[p].x = out_T[V.pix_off + lpa];
-                la[p] = last_idx[V.pix_off + lpa];
                 gI0[p].x = gI[lpa]; gI1[p].x = gI[npx + lpa]; gI2[p].x = gI[2 * npx + lpa];
                 if (dL_dT) gT[p].x = dL_dT[V.pix_off + lpa];
                 if (mr) { B0[p].x = mr[lpa]; B1[p].x = mr[npx + lpa]; B2[p].x = mr[2 * npx + lpa]; }
             }
-            if (in_b) {
+            if (lb[p] > 0) {
                 Tf[p].y = out_T[V.pix_off + lpb];
-                lb[p] = last_idx[V.pix_off + lpb];
                 gI0[p].y = gI[lpb]; gI1[p].y = gI[npx + lpb]; gI2[p].y = gI[2 * npx + lpb];
                 if (dL_dT) gT[p].y = dL_dT[V.pix_off + lpb];
                 if (mr) { B0[p].y = mr[lpb]; B1[p].y = mr[npx + lpb]; B2[p].y = mr[2 * npx + lpb]; }
