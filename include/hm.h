@@ -166,7 +166,8 @@ hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, const float 
  *   z = fp32(fma(R20,x,fma(R21,y,fma(R22,z,t2)))) in FP64, colour
  *   max(0, 0.5 + SH(normalised mean - camera centre)) and the tile rectangle
  *   covering the 3-sigma ellipse d^2 <= 9.  Culled (z <= near_gauss, or no
- *   tile) records carry an empty rectangle.
+ *   tile) records carry an empty rectangle; the colour is evaluated only for
+ *   records with tiles (0 in the others, which no list holds).
  *  filter_3d [n] float32 >= 0 or NULL: the per-Gaussian variance v of
  *   Mip-Splatting's 3D smoothing filter (hm_mip_filter_3d): the covariance
  *   becomes R (S^2 + v I) R^T and the opacity is scaled by
