@@ -82,7 +82,7 @@ __device__ __forceinline__ float warp_sum8(const float *v, int lane) {
 // of resident CTAs that claim tiles of all views from the counter `work`
 // (zeroed before the launch) until none is left; a claim is one atomic on a
 // counter that only grows, so no CTA waits on another.
-template <int TW, int TH, int PP, bool PERSIST>
+template <int TW, int TH, int PP, bool PERSIST, bool HAS_DT>
 __global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 12)
 blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
@@ -143,13 +143,13 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             if (la[p] > 0) {
                 Tf[p].x = out_T[V.pix_off + lpa];
                 gI0[p].x = gI[lpa]; gI1[p].x = gI[npx + lpa]; gI2[p].x = gI[2 * npx + lpa];
-                if (dL_dT) gT[p].x = dL_dT[V.pix_off + lpa];
+                if constexpr (HAS_DT) gT[p].x = dL_dT[V.pix_off + lpa];
                 if (mr) { B0[p].x = mr[lpa]; B1[p].x = mr[npx + lpa]; B2[p].x = mr[2 * npx + lpa]; }
             }
             if (lb[p] > 0) {
                 Tf[p].y = out_T[V.pix_off + lpb];
                 gI0[p].y = gI[lpb]; gI1[p].y = gI[npx + lpb]; gI2[p].y = gI[2 * npx + lpb];
-                if (dL_dT) gT[p].y = dL_dT[V.pix_off + lpb];
+                if constexpr (HAS_DT) gT[p].y = dL_dT[V.pix_off + lpb];
                 if (mr) { B0[p].y = mr[lpb]; B1[p].y = mr[npx + lpb]; B2[p].y = mr[2 * npx + lpb]; }
             }
             my_hi = max(my_hi, max(la[p], lb[p]));
@@ -288,7 +288,8 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                     float2 sdot = __fmul2_rn(gI0[p], d0);
                     sdot = __ffma2_rn(gI1[p], d1, sdot);
                     sdot = __ffma2_rn(gI2[p], d2, sdot);
-                    const float2 dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, __fmul2_rn(Ti, sdot));
+                    float2 dLda = __fmul2_rn(Ti, sdot);
+                    if constexpr (HAS_DT) dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, dLda);
                     // through alpha = o 2^q where blended and not clamped at 0.99
                     const float2 dLa_u = make_float2(ea[p] && araw[p].x < kAlphaMax ? dLda.x : 0.f,
                                                      eb[p] && araw[p].y < kAlphaMax ? dLda.y : 0.f);
@@ -898,8 +899,8 @@ namespace {
 // all SMs (cached per device and batch; the batch sets the shared memory)
 template <typename K>
 int resident_ctas(K kernel, int threads, int smem, int slot) {
-    static int cache[64][3][8] = {};
-    static int cache_smem[64][3][8] = {};
+    static int cache[64][6][8] = {};
+    static int cache_smem[64][6][8] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     const int b = smem <= 2048 ? 0 : smem <= 8192 ? 1 : smem <= 16384 ? 2 : smem <= 32768 ? 3 : 4;
@@ -989,10 +990,11 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     const size_t bwd_smem = 2 * (size_t)opt->batch * (sizeof(Record) + sizeof(uint32_t));
 #define HM_BBWD(TW, TH, PP, SLOT)                                                                                \
     do {                                                                                                         \
-        auto kern = wq ? blend_bwd_kernel<TW, TH, PP, true> : blend_bwd_kernel<TW, TH, PP, false>;              \
+        auto kern = wq ? (dL_dT ? blend_bwd_kernel<TW, TH, PP, true, true> : blend_bwd_kernel<TW, TH, PP, true, false>) \
+                       : (dL_dT ? blend_bwd_kernel<TW, TH, PP, false, true> : blend_bwd_kernel<TW, TH, PP, false, false>); \
         int grid = vt.total_tiles;                                                                               \
         if (wq) {                                                                                                \
-            grid = resident_ctas(kern, TW * TH / (2 * PP), (int)bwd_smem, SLOT);                                 \
+            grid = resident_ctas(kern, TW * TH / (2 * PP), (int)bwd_smem, 2 * SLOT + (dL_dT ? 1 : 0));           \
             if (grid <= 0) return fail(HM_ERR_CUDA, "occupancy query failed");                                  \
             grid = grid < vt.total_tiles ? grid : vt.total_tiles;                                                \
         }                                                                                                        \
