@@ -70,7 +70,7 @@ KERNEL_SOURCES = {
 NCU_CAPTURE = {
     # stage: (warp instructions, DRAM bytes, units, unit kind, pixels, source hash)
     "blend_forward": (202_430_464, 219_355_648, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "38b741871cc74f09"),
-    "blend_backward": (291_051_393, 122_490_112, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "2e56788a81c533a8"),
+    "blend_backward": (282_105_216, 122_254_080, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "d8eac24d15b655e1"),
 }
 
 
