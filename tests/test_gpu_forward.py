@@ -123,6 +123,8 @@ def test_projection_records_match_oracle():
             band = 2 * (np.abs(gx) * err[:, 0] + np.abs(gy) * err[:, 1]) + 16 * err[:, 2] * 2.0 ** -24 * S
             assert (np.abs(d2r - 9.0) <= band).all(), float((np.abs(d2r - 9.0) / band).max())
         assert np.abs(rec.color[sl][on] - p.color[on]).max() < 1e-5
+        # the colour is evaluated only for records with tiles (no list holds the others)
+        assert np.all(rec.color[sl][rec.x0[sl] > rec.x1[sl]] == 0.0)
         assert np.array_equal(rec.opacity[sl], s.gaussians.opacity)
         # tile rectangle covers the oracle's 3-sigma bounding box
         hx = 3 * np.sqrt(p.cov2d[on, 0])
