@@ -268,6 +268,7 @@ __device__ __forceinline__ uint32_t same_digit_lanes(uint32_t d) {
 constexpr int kWarpSeg = 256;      // bucket sizes sorted by one warp in registers
 constexpr int kMidSeg = 1024;      // ... by a 128-thread CTA in shared memory (radix)
 constexpr int kSegMax = 4096;      // ... by a 256-thread CTA in shared memory (radix)
+constexpr int kBigSeg = 8192;      // ... by a 512-thread CTA in shared memory (radix)
 
 // compare-exchange of a (low, high) element pair for an ascending (asc) or
 // descending bitonic stage: afterwards lo holds the min if asc, else the max
@@ -378,7 +379,7 @@ seg_sort_small_kernel(uint32_t n_tiles, const uint32_t *__restrict__ tile_off,
     }
 }
 
-// ---- CTA radix sort of one bucket of up to kSegMax keys in shared memory.
+// ---- CTA radix sort of one bucket of up to CAP keys in shared memory.
 // The sort key is the depth (the high word of the 64-bit pair key) with the
 // record index as payload: 4 stable LSD passes of 8 bits, skipping passes in
 // which every key has the same digit.  A pass ranks the keys warp by warp
@@ -479,7 +480,7 @@ __device__ void radix_pass(RadixSmem<THREADS, CAP> &S, int src, int n, int shift
 }
 
 // CTA per bucket of at most CAP keys (grid-stride over its list).
-template <int THREADS, int CAP>
+template <int THREADS, int CAP, int LOWER = 0>
 __global__ void __launch_bounds__(THREADS)
 seg_sort_radix_kernel(const uint32_t *__restrict__ list, const unsigned int *list_count,
                       const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ tile_cnt,
@@ -492,7 +493,7 @@ seg_sort_radix_kernel(const uint32_t *__restrict__ list, const unsigned int *lis
         const uint32_t gt = list[li];
         const uint32_t off = tile_off[gt];
         const int n = (int)tile_cnt[gt];
-        if (n > CAP) continue;                       // a larger bucket: the merge path's
+        if (n > CAP || n <= LOWER) continue;         // another tier's bucket
         if (t == 0) {
             S.kand = 0xFFFFFFFFu;
             S.kor = 0u;
@@ -539,23 +540,24 @@ seg_sort_radix_kernel(const uint32_t *__restrict__ list, const unsigned int *lis
     }
 }
 
-template <int THREADS, int CAP>
+template <int THREADS, int CAP, int LOWER = 0>
 cudaError_t launch_radix_buckets(const uint32_t *list, const unsigned int *count, const uint32_t *tile_off,
                                  const uint32_t *tile_cnt, const unsigned long long *keys, uint32_t *vals,
                                  int grid, cudaStream_t s) {
     static bool attr = false;
     const int smem = (int)sizeof(RadixSmem<THREADS, CAP>);
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(seg_sort_radix_kernel<THREADS, CAP>,
+        cudaError_t e = cudaFuncSetAttribute(seg_sort_radix_kernel<THREADS, CAP, LOWER>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    seg_sort_radix_kernel<THREADS, CAP><<<grid, THREADS, smem, s>>>(list, count, tile_off, tile_cnt, keys, vals);
+    seg_sort_radix_kernel<THREADS, CAP, LOWER><<<grid, THREADS, smem, s>>>(list, count, tile_off, tile_cnt, keys,
+                                                                        vals);
     return cudaGetLastError();
 }
 
-// ---- buckets above kSegMax keys: one CTA, LSD radix passes through global
+// ---- buckets above kBigSeg keys: one CTA, LSD radix passes through global
 // memory in chunks of kSegMax.  The depth keys are split from the record
 // indices into two uint32 arrays (ping-pong between the bucket's range of
 // `scratch` and of the key array itself).  One read counts every pass's
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(THREADS)
 seg_sort_huge_kernel(const uint32_t *__restrict__ list, const unsigned int *list_count,
                      const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ tile_cnt,
                      unsigned long long *__restrict__ keys, unsigned long long *__restrict__ scratch,
-                     uint32_t *__restrict__ vals) {
+                     uint32_t *__restrict__ vals, int min_n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HugeSmem<THREADS, CAP> &H = *reinterpret_cast<HugeSmem<THREADS, CAP> *>(smem_raw);
     const int t = threadIdx.x;
@@ -647,7 +649,7 @@ seg_sort_huge_kernel(const uint32_t *__restrict__ list, const unsigned int *list
         const uint32_t gt = list[li];
         const long long off = tile_off[gt];
         const int n = (int)tile_cnt[gt];
-        if (n <= CAP) continue;                      // sorted in shared memory by the radix CTA
+        if (n <= min_n) continue;                    // sorted in shared memory by a radix CTA
         // A = (depth keys, record indices) split into the scratch range,
         // B = the same layout over the key range
         uint32_t *kA = reinterpret_cast<uint32_t *>(scratch + off), *vA = kA + n;
@@ -843,10 +845,14 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     e = launch_radix_buckets<128, kMidSeg>(b.mid_list, b.counts, b.tile_off, b.tile_cnt, b.keys, pair_vals,
                                           148 * 10, s);
     if (e != cudaSuccess) return cuda_status(e);
-    // buckets above kMidSeg: the 4096-key radix CTA, and beyond that chunk
-    // sorts and merges (each kernel skips the sizes it does not take)
+    // buckets above kMidSeg: the 4096-key and 8192-key radix CTAs, and
+    // beyond that chunked passes through global memory (each kernel skips
+    // the sizes it does not take)
     e = launch_radix_buckets<256, kSegMax>(b.big_list, b.counts + 1, b.tile_off, b.tile_cnt, b.keys, pair_vals,
                                           148 * 2, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = launch_radix_buckets<512, kBigSeg, kSegMax>(b.big_list, b.counts + 1, b.tile_off, b.tile_cnt, b.keys,
+                                                    pair_vals, 148, s);
     if (e != cudaSuccess) return cuda_status(e);
     {
         static bool huge_attr = false;
@@ -858,7 +864,8 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
             huge_attr = true;
         }
         seg_sort_huge_kernel<256, kSegMax><<<148 * 2, 256, smem, s>>>(b.big_list, b.counts + 1, b.tile_off,
-                                                                        b.tile_cnt, b.keys, b.scratch, pair_vals);
+                                                                        b.tile_cnt, b.keys, b.scratch, pair_vals,
+                                                                        kBigSeg);
     }
     return cuda_status(cudaGetLastError());
 }

@@ -162,13 +162,14 @@ def test_bin_sort_lists_exact(cull):
         assert vals[b:e].tolist() == lst, gt
 
 
-def test_bin_sort_dense_tiles_exact():
-    """12,000 Gaussians crowded onto the 4 central tiles of a 64x64 view (no
-    mesh, ellipse test off): buckets of several thousand pairs exercise the
-    CTA and the chunk-sort-and-merge paths of the segmented sort; every list
-    must still be exactly the covering records in (depth, index) order."""
+@pytest.mark.parametrize("n, least", [(12000, 4096), (40000, 8192)])
+def test_bin_sort_dense_tiles_exact(n, least):
+    """n Gaussians crowded onto the 4 central tiles of a 64x64 view (no mesh,
+    ellipse test off): buckets of thousands of pairs exercise the CTA radix
+    tiers (up to 4096 and 8192 keys) and, above 8192, the chunked passes
+    through global memory; every list must still be exactly the covering
+    records in (depth, index) order."""
     rng = np.random.default_rng(21)
-    n = 12000
     z = rng.uniform(1.5, 3.0, n)
     means = np.stack([rng.uniform(-0.08, 0.08, n) * z, rng.uniform(-0.08, 0.08, n) * z, z], 1)
     g = scenes.Gaussians(means.astype(np.float32), np.exp(rng.normal(-4.0, 0.3, (n, 3))).astype(np.float32),
@@ -179,7 +180,7 @@ def test_bin_sort_dense_tiles_exact():
     r, _, _ = gpu_render(s, ellipse_cull=False)
     rec = records_np(r)
     want = expected_pairs(r, rec)
-    assert max(len(l) for l in want) > 4096
+    assert max(len(l) for l in want) > least
     ranges = r.ranges.cpu().numpy().astype(np.int64).reshape(-1, 2)
     vals = r.pair_vals.cpu().numpy().astype(np.int64)
     assert int(r.n_pairs.item()) == sum(len(l) for l in want)
