@@ -1235,8 +1235,8 @@ def run_e2e(args, scene, r, mesh, dev, dist, frames):
     """A training step through the public API (GraphStep with a target:
     forward, L1 loss by hm_hybrid_loss, backward with the texel gradients,
     all in one CUDA graph).  Every step copies its data -- the 8 target
-    images, uint8 codes decoded in the graph -- from pinned host memory and
-    reads its loss back (after the next step is queued, as an asynchronous
+    images, uint8 codes the loss kernels read directly -- from pinned host
+    memory and reads its loss back (after the next step is queued, as an asynchronous
     training loop logs it); the Gaussian parameters and the mesh are the
     model's state and stay resident, as in a training loop.  The copy of
     step k+1 runs on a copy stream into a second target buffer (a second

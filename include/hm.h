@@ -368,6 +368,16 @@ hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *ou
                          const float *mesh_depth, const hm_loss_params *p, double *loss_out,
                          float *dL_drgb, float *dL_dmesh, void *ws, size_t ws_bytes, void *stream);
 
+/* hm_hybrid_loss_u8 -- hm_hybrid_loss with the target given as 8-bit codes
+ * (device uint8, planar like out_rgb): every kernel reads a code c as c / 255
+ * (correctly rounded FP32), so the results equal hm_hybrid_loss on the image
+ * hm_decode_u8 writes, bit for bit, without that pass or its float image.
+ * Same arguments, workspace, outputs and errors as hm_hybrid_loss. */
+hm_status hm_hybrid_loss_u8(const hm_camera *cams, int32_t n_views, const float *out_rgb,
+                            const uint8_t *target, const float *mesh_rgb, const float *out_T,
+                            const float *mesh_depth, const hm_loss_params *p, double *loss_out,
+                            float *dL_drgb, float *dL_dmesh, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* hm_adam_update -- one Adam step (Kingma and Ba, 2015) on n float32 values
  * in place, for optimised buffers such as the texture map in the texture-only

@@ -182,8 +182,30 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double (*s_red)[kNT /
     for (int q = 0; q < 3; ++q) v[q] = s_red[q][0];
 }
 
+// Target intensity at element o: FP32 values, or 8-bit codes read as
+// code / 255 (correctly rounded, as hm_decode_u8 writes them: a 256-entry
+// table each CTA fills in shared memory), so a loss on the codes equals the
+// loss on their decoded image bit for bit.
+template <typename TT>
+struct Target {
+    const TT *y;
+    float *lut;      // 8-bit codes: the CTA's table
+    // fills the table (called by the whole CTA; ends with a barrier)
+    __device__ __forceinline__ void init() {
+        if constexpr (sizeof(TT) == 1) {
+            for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = __fdiv_rn((float)i, 255.f);
+            __syncthreads();
+        }
+    }
+    __device__ __forceinline__ float operator()(long long o) const {
+        if constexpr (sizeof(TT) == 1) return lut[y[o]];
+        else return y[o];
+    }
+};
+
+template <typename TT>
 __global__ void __launch_bounds__(kNT, 5)
-ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
+ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const TT *__restrict__ y_all,
                 const float *__restrict__ m_all, const float *__restrict__ T_all,
                 const float *__restrict__ md_all, float k_mask, float mesh_grad_scale,
                 float2 *__restrict__ d_mu_xx, float *__restrict__ d_xy,
@@ -200,10 +222,13 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     const int px0 = (local % V.tiles_x) * kLT, py0 = (local / V.tiles_x) * kLT;
     const long long npx = (long long)V.W * V.H;
     const long long base = 3 * V.pix_off + ch * npx;
+    __shared__ float s_lut[256];
+    Target<TT> tgt{y_all + base, s_lut};
+    tgt.init();
     const int t = threadIdx.x;
     {
         // every load of the halo issued before the first shared-memory store
-        const float *x = x_all + base, *y = y_all + base;
+        const float *x = x_all + base;
         const int W = V.W, H = V.H;
         float2 hv[kHaloSlots];
 #pragma unroll
@@ -214,7 +239,7 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
             hv[k] = make_float2(0.f, 0.f);
             if (in && gx >= 0 && gx < W && gy >= 0 && gy < H) {
                 const long long o = (long long)gy * W + gx;
-                hv[k] = make_float2(x[o], y[o]);
+                hv[k] = make_float2(x[o], tgt(o));
             }
         }
 #pragma unroll
@@ -294,8 +319,9 @@ ssim_fwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     if (t < 3) partials[3 * ((long long)ch * gridDim.x + gt) + t] = s_red[t][0];
 }
 
+template <typename TT>
 __global__ void __launch_bounds__(kNT)
-ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const float *__restrict__ y_all,
+ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const TT *__restrict__ y_all,
                 const float2 *__restrict__ d_mu_xx, const float *__restrict__ d_xy,
                 float l1_scale, float ssim_scale, float *__restrict__ dL_drgb) {
     __shared__ __align__(16) float2 s_d[kHalo][kHS2];   // (D_mu, D_xx) interleaved
@@ -310,6 +336,9 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
     const long long npx = (long long)V.W * V.H;
     const long long base = 3 * V.pix_off + ch * npx;
     const int t = threadIdx.x;
+    __shared__ float s_lut[256];
+    Target<TT> tgt{y_all, s_lut};
+    tgt.init();
     // this thread's four output pixels: x and y fetched now, used at the end
     float xo[kOut], yo[kOut];
 #pragma unroll
@@ -319,7 +348,7 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
         if (px < V.W && py < V.H) {
             const long long o = base + (long long)py * V.W + px;
             xo[q] = x_all[o];
-            yo[q] = y_all[o];
+            yo[q] = tgt(o);
         }
     }
     {
@@ -388,12 +417,16 @@ ssim_bwd_kernel(ViewTable vt, Taps tp, const float *__restrict__ x_all, const fl
 // pixel of all cameras over its three channels -- L1 and its gradient
 // sign(x - y) / N, and the texture loss as in the tiled pass; per-CTA
 // partial sums for the fixed-order final reduction (the SSIM slot is 0).
+template <typename TT>
 __global__ void __launch_bounds__(kNT)
-l1_loss_kernel(ViewTable vt, const float *__restrict__ x_all, const float *__restrict__ y_all,
+l1_loss_kernel(ViewTable vt, const float *__restrict__ x_all, const TT *__restrict__ y_all,
                const float *__restrict__ m_all, const float *__restrict__ T_all, const float *__restrict__ md_all,
                float k_mask, float l1_scale, float mesh_grad_scale, float *__restrict__ dL_drgb,
                float *__restrict__ dL_dmesh, double *__restrict__ partials) {
     __shared__ double s_red[3][kNT / 32];
+    __shared__ float s_lut[256];
+    Target<TT> tgt{y_all, s_lut};
+    tgt.init();
     float l1 = 0.f, lt = 0.f;
     for (long long gp = (long long)blockIdx.x * kNT + threadIdx.x; gp < vt.total_pixels;
          gp += (long long)gridDim.x * kNT) {
@@ -406,7 +439,7 @@ l1_loss_kernel(ViewTable vt, const float *__restrict__ x_all, const float *__res
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long o = 3 * V.pix_off + c * npx + lp;
-            const float xv = x_all[o], yv = y_all[o];
+            const float xv = x_all[o], yv = tgt(o);
             l1 += fabsf(xv - yv);
             dL_drgb[o] = xv > yv ? l1_scale : (xv < yv ? -l1_scale : 0.f);
             if (m_all) {
@@ -538,11 +571,15 @@ extern "C" size_t hm_hybrid_loss_workspace_size(const hm_camera *cams, int32_t n
     return sizeof(float) * 9 * (size_t)vt.total_pixels + sizeof(double) * 9 * (size_t)vt.total_tiles + 4 * 256;
 }
 
-extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *out_rgb,
-                                    const float *target, const float *mesh_rgb, const float *out_T,
-                                    const float *mesh_depth, const hm_loss_params *p,
-                                    double *loss_out, float *dL_drgb, float *dL_dmesh, void *ws,
-                                    size_t ws_bytes, void *stream) {
+namespace hm {
+namespace {
+
+// the joint loss with FP32 targets or 8-bit target codes (TT = float or uint8_t)
+template <typename TT>
+hm_status hybrid_loss(const hm_camera *cams, int32_t n_views, const float *out_rgb, const TT *target,
+                      const float *mesh_rgb, const float *out_T, const float *mesh_depth,
+                      const hm_loss_params *p, double *loss_out, float *dL_drgb, float *dL_dmesh, void *ws,
+                      size_t ws_bytes, void *stream) {
     ViewTable vt;
     if (!loss_view_table(cams, n_views, &vt)) return HM_ERR_INVALID_ARG;
     if (!p || !out_rgb || !target || !loss_out || !dL_drgb) return fail(HM_ERR_INVALID_ARG, "null pointer");
@@ -602,6 +639,27 @@ extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     loss_final_kernel<<<1, kNT, 0, s>>>(level2, n_red, 1.0 / n_el, p->lambda_ssim, p->lambda_t, loss_out);
     return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_hybrid_loss(const hm_camera *cams, int32_t n_views, const float *out_rgb,
+                                    const float *target, const float *mesh_rgb, const float *out_T,
+                                    const float *mesh_depth, const hm_loss_params *p,
+                                    double *loss_out, float *dL_drgb, float *dL_dmesh, void *ws,
+                                    size_t ws_bytes, void *stream) {
+    return hybrid_loss(cams, n_views, out_rgb, target, mesh_rgb, out_T, mesh_depth, p, loss_out, dL_drgb,
+                       dL_dmesh, ws, ws_bytes, stream);
+}
+
+extern "C" hm_status hm_hybrid_loss_u8(const hm_camera *cams, int32_t n_views, const float *out_rgb,
+                                       const uint8_t *target, const float *mesh_rgb, const float *out_T,
+                                       const float *mesh_depth, const hm_loss_params *p,
+                                       double *loss_out, float *dL_drgb, float *dL_dmesh, void *ws,
+                                       size_t ws_bytes, void *stream) {
+    return hybrid_loss(cams, n_views, out_rgb, target, mesh_rgb, out_T, mesh_depth, p, loss_out, dL_drgb,
+                       dL_dmesh, ws, ws_bytes, stream);
 }
 
 extern "C" hm_status hm_decode_u8(const uint8_t *src, int64_t n, float *dst, void *stream) {

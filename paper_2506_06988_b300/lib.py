@@ -40,7 +40,8 @@ EXPORTS = [
     "hm_bin_sort_workspace_size", "hm_bin_sort",
     "hm_blend_forward",
     "hm_blend_backward_workspace_size", "hm_blend_backward", "hm_blend_backward_noalloc",
-    "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss", "hm_decode_u8",
+    "hm_default_loss_params", "hm_hybrid_loss_workspace_size", "hm_hybrid_loss", "hm_hybrid_loss_u8",
+    "hm_decode_u8",
     "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
     "hm_adam_update", "hm_adam_update_dev", "hm_adam_advance", "hm_activate", "hm_activate_backward",
     "hm_selftest_bounded_waits",
@@ -123,6 +124,8 @@ _SIGS = {
     "hm_decode_u8": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p]),
     "hm_hybrid_loss": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  _LOSS_P, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "hm_hybrid_loss_u8": (c_int32, [_CAM_P, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    _LOSS_P, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "hm_blend_backward_noalloc": (c_int32, [_CAM_P, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                             c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p,
                                             c_void_p,
@@ -373,3 +376,10 @@ def hm_hybrid_loss(cams, out_rgb, target, mesh_rgb, out_T, mesh_depth, params, l
     return load().hm_hybrid_loss(cams, len(cams), _ptr(out_rgb), _ptr(target), _ptr(mesh_rgb), _ptr(out_T),
                                  _ptr(mesh_depth), ctypes.byref(params), _ptr(loss_out), _ptr(dL_drgb),
                                  _ptr(dL_dmesh), _ptr(ws), ws_bytes, stream)
+
+
+def hm_hybrid_loss_u8(cams, out_rgb, target, mesh_rgb, out_T, mesh_depth, params, loss_out, dL_drgb,
+                      dL_dmesh, ws, ws_bytes, stream):
+    return load().hm_hybrid_loss_u8(cams, len(cams), _ptr(out_rgb), _ptr(target), _ptr(mesh_rgb),
+                                    _ptr(out_T), _ptr(mesh_depth), ctypes.byref(params), _ptr(loss_out),
+                                    _ptr(dL_drgb), _ptr(dL_dmesh), _ptr(ws), ws_bytes, stream)

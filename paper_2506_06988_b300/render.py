@@ -398,7 +398,8 @@ class Renderer:
     # -- the joint-optimisation loss ------------------------------------------------
     def loss(self, target: torch.Tensor, params=None, texture_loss: bool = True):
         """The joint loss of the last frame against ``target`` (planar like
-        ``rgb``) by hm_hybrid_loss: returns (terms, dL/drgb, dL/dmesh) with
+        ``rgb``; float32 in [0, 1], or uint8 codes read as code / 255 by
+        hm_hybrid_loss_u8) by hm_hybrid_loss: returns (terms, dL/drgb, dL/dmesh) with
         terms = device float64 [L1, mean SSIM, L_t, L] and dL/dmesh None
         without a mesh or with ``texture_loss`` off.  Pass both gradients to
         ``backward`` (``dL_drgb`` and ``dL_dmesh``)."""
@@ -411,11 +412,17 @@ class Renderer:
             self._dM = torch.empty(3 * self.npix, dtype=torch.float32, device=d) if self.has_mesh else None
         p = params if params is not None else lib.loss_params()
         use_mesh = self.has_mesh and texture_loss
-        lib.check(lib.hm_hybrid_loss(self.cams, self.rgb, target.contiguous(),
-                                     self.mesh_rgb if use_mesh else None, self.T if use_mesh else None,
-                                     self.mesh_depth if use_mesh else None, p, self._loss_out, self._dI,
-                                     self._dM if use_mesh else None, self._loss_ws, self._loss_ws.numel(),
-                                     _stream()), "hm_hybrid_loss")
+        if target.dtype == torch.uint8:
+            fn, name = lib.hm_hybrid_loss_u8, "hm_hybrid_loss_u8"
+        elif target.dtype == torch.float32:
+            fn, name = lib.hm_hybrid_loss, "hm_hybrid_loss"
+        else:
+            raise ValueError("target: uint8 or float32")
+        lib.check(fn(self.cams, self.rgb, target.contiguous(),
+                     self.mesh_rgb if use_mesh else None, self.T if use_mesh else None,
+                     self.mesh_depth if use_mesh else None, p, self._loss_out, self._dI,
+                     self._dM if use_mesh else None, self._loss_ws, self._loss_ws.numel(),
+                     _stream()), name)
         return self._loss_out, self._dI, (self._dM if use_mesh else None)
 
     # -- views of the outputs -------------------------------------------------------
@@ -477,8 +484,9 @@ class GraphStep:
     overflow grows the buffers eagerly and captures again.
 
     With a ``target`` (planar like ``rgb``; float32 in [0, 1], or uint8
-    codes decoded in the graph by hm_decode_u8) the graph also evaluates the
-    joint loss (hm_hybrid_loss with ``loss_params``) and back-propagates its
+    codes, which the loss kernels read as code / 255) the graph also
+    evaluates the joint loss (hm_hybrid_loss with ``loss_params``) and
+    back-propagates its
     gradient; ``loss_terms`` is then the device float64 [L1, mean SSIM,
     L_t, L] of the last replay.
     """
@@ -494,13 +502,10 @@ class GraphStep:
         if target is not None and dL_drgb is not None:
             raise ValueError("give either an upstream gradient or a target, not both")
         self.target = target
-        self.target_f = None
         if target is not None:
             if target.numel() != 3 * renderer.npix or not target.is_contiguous():
                 raise ValueError("target: a contiguous planar image of every camera")
-            if target.dtype == torch.uint8:
-                self.target_f = torch.empty(3 * renderer.npix, dtype=torch.float32, device=renderer.device)
-            elif target.dtype != torch.float32:
+            if target.dtype not in (torch.uint8, torch.float32):
                 raise ValueError("target: uint8 or float32")
         self.loss_params = loss_params if loss_params is not None else lib.loss_params()
         self.loss_terms = None
@@ -513,24 +518,10 @@ class GraphStep:
 
     def _body(self):
         r = self.r
-        main = torch.cuda.current_stream(r.device)
-        side = None
-        if self.target_f is not None:
-            # the target's decode depends on nothing the frame computes: it
-            # runs beside the forward and joins before the loss
-            side = r._side_stream()
-            side.wait_stream(main)
-            with torch.cuda.stream(side):
-                lib.check(lib.hm_decode_u8(self.target, self.target.numel(), self.target_f, _stream()),
-                          "hm_decode_u8")
         r.forward(*self.params, self.mesh, overlap=True)
         dI, dM = self.dI, None
         if self.target is not None:
-            tgt = self.target
-            if side is not None:
-                main.wait_stream(side)
-                tgt = self.target_f
-            self.loss_terms, dI, dM = r.loss(tgt, self.loss_params,
+            self.loss_terms, dI, dM = r.loss(self.target, self.loss_params,
                                              texture_loss=self.tex_grad and self.loss_params.lambda_t > 0)
         if dI is not None:
             r.backward(*self.params, dI, self.dT, mesh=self.mesh, tex_grad=self.tex_grad,

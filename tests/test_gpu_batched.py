@@ -126,6 +126,31 @@ def test_decode_u8_is_exact():
         assert np.array_equal(dst[:n].cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("lam_ssim, lam_t", [(0.0, 0.0), (0.2, 0.1)])
+def test_u8_target_loss_equals_the_decoded_target_loss(lam_ssim, lam_t):
+    """hm_hybrid_loss_u8 reads each 8-bit code as code / 255 (correctly
+    rounded): its loss terms and both gradients equal hm_hybrid_loss on the
+    image hm_decode_u8 writes, bit for bit (pointwise L1 path and SSIM path
+    with the texture loss)."""
+    from paper_2506_06988_b300 import lib
+    s = _room(seed=34, res=((160, 120), (96, 64)))
+    r, P, mesh = gpu_render(s)
+    r.render(*_params(P), mesh)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(6)
+    codes = torch.randint(0, 256, (3 * r.npix,), device="cuda", generator=gen, dtype=torch.int32).to(torch.uint8)
+    dec = torch.empty(3 * r.npix, device="cuda")
+    lib.check(lib.hm_decode_u8(codes, codes.numel(), dec, torch.cuda.current_stream().cuda_stream), "hm_decode_u8")
+    lp = lib.loss_params(lambda_ssim=lam_ssim, lambda_t=lam_t)
+    t_f, dI_f, dM_f = (x.clone() if x is not None else None for x in r.loss(dec, lp, texture_loss=lam_t > 0))
+    t_u, dI_u, dM_u = r.loss(codes, lp, texture_loss=lam_t > 0)
+    torch.cuda.synchronize()
+    assert torch.equal(t_u, t_f)
+    assert torch.equal(dI_u, dI_f)
+    if lam_t > 0:
+        assert torch.equal(dM_u, dM_f)
+
+
 def test_graph_step_reads_current_parameters():
     s = _room(seed=32)
     r, P, mesh = gpu_render(s)
