@@ -95,7 +95,7 @@ def _captured(stage, tile, units, pixels):
     return inst * units[kind] / cap_units, dram * pixels / cap_px
 
 
-KERNELS_PER_STEP = {"rasterize_mesh": 6, "project": 1, "bin_sort": 8, "blend_forward": 1,
+KERNELS_PER_STEP = {"rasterize_mesh": 6, "project": 1, "bin_sort": 9, "blend_forward": 1,
                     "texture_backward": 1, "blend_backward": 1, "project_backward": 1}
 
 
