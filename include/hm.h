@@ -84,8 +84,8 @@ typedef struct hm_camera {
 typedef struct hm_options {
     int32_t tile_w, tile_h;  /* screen tile: 16x16, 32x8 or 8x8 */
     int32_t batch;           /* list entries staged in shared memory per round by the
-                                blend kernels (forward and backward): 1 .. tile pixels;
-                                the results do not depend on it */
+                                blend kernels (forward; the backward stages at most
+                                64): 1 .. tile pixels; the results do not depend on it */
     int32_t mesh_cull;       /* 1: drop (Gaussian, tile) pairs at or behind the tile's
                                 farthest mesh depth (result-preserving) */
     float near_gauss;        /* Gaussians with FP32 view depth <= this are culled (0.2) */

@@ -14,9 +14,10 @@
 //    Decisions are re-evaluated with the forward's exact arithmetic
 //    (blend_common.cuh).  Per Gaussian the 9 partials (five pixel-space
 //    moments of dL/dq from which the mean2d and conic gradients follow,
-//    opacity, colour) are summed over the thread's pixels, then over the
-//    warp with shuffles, and added to per-record accumulators with one
-//    atomic per value per warp.
+//    opacity, colour) are summed over the thread's pixels and written to a
+//    per-warp ring in shared memory; every three entries the warp sums each
+//    (entry, value) column over its 32 lanes (one lane per column, packed
+//    FP32x2 adds) and adds it to the record's accumulator with one atomic.
 //  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
 //    triangle (the mesh colour enters I_h weighted by T), summed per screen
 //    tile in shared memory (fixed point) before the global reductions.
@@ -45,32 +46,13 @@ constexpr int kG = 9;
 // Gaussians per lane that a warp of the projection backward scans for
 // gradients before it works on the ones it found
 constexpr int kPbwdWin = 4;
-
-// Warp sum of 8 per-lane values by recursive halving: at each of the first
-// three levels a lane keeps half of its values and sends the other half to
-// its partner, so 4 + 2 + 1 + 2 shuffles (instead of 8 x 5) leave the sum of
-// value (lane >> 2) in every lane with lane % 4 == 0.
-__device__ __forceinline__ float warp_sum8(const float *v, int lane) {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    float w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = b4 ? v[i] : v[i + 4];
-        const float keep = b4 ? v[i + 4] : v[i];
-        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    float x[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = b3 ? w[i] : w[i + 2];
-        const float keep = b3 ? w[i + 2] : w[i];
-        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
-    y += __shfl_xor_sync(0xffffffffu, y, 2);
-    y += __shfl_xor_sync(0xffffffffu, y, 1);
-    return y;
-}
+// list entries whose per-lane partials a warp of the replay collects before
+// it sums them over its lanes (3 x 9 columns: one flush pass of 27 lanes)
+constexpr int kRingEntries = 3;
+// the replay's staging batch: at most this many list entries per round, so
+// that the double-buffered records and the partials ring leave room for 12
+// CTAs per SM
+constexpr int kBwdBatchMax = 64;
 
 // Pixel layout of the replay: a warp covers 8 columns x 8 PP rows of the
 // tile; lane l owns column l % 8 and, for p < PP, the pixel pair of rows
@@ -97,6 +79,13 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
     __shared__ uint64_t s_bar[2];
     __shared__ uint32_t s_hi;
     __shared__ int s_tile;
+    // per-warp ring of the last RNE entries' per-lane partials: [entry][value][lane]
+    // rows padded to RRS floats, so that the flush's 16-byte column reads by
+    // eight lanes fall in distinct banks
+    constexpr int RNE = kRingEntries, RRS = 36, NW = TW * TH / (2 * PP) / 32;
+    static_assert(RNE * kG <= 32, "one flush pass");
+    __shared__ __align__(16) float s_ring[NW][RNE][kG][RRS];
+    __shared__ uint32_t s_ridx[NW][RNE];
     if (threadIdx.x == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -199,6 +188,28 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             issue(0);
         }
         if (n_rounds > 1) load_idx(1);
+        // the ring's flush: lane c < n kG sums column (entry c / kG, value c % kG)
+        // over the warp's 32 lanes and adds it to the record's partial
+        const int wid = t >> 5;
+        int nfill = 0;
+        auto ring_flush = [&](int n) {
+            __syncwarp();
+            if (lane < n * kG) {
+                const int e = lane / kG, v = lane - e * kG;
+                const float4 *p = reinterpret_cast<const float4 *>(&s_ring[wid][e][v][0]);
+                float2 acc[4];
+    #pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 a = p[2 * j], b = p[2 * j + 1];
+                    acc[j] = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), make_float2(a.z, a.w)),
+                                        __fadd2_rn(make_float2(b.x, b.y), make_float2(b.z, b.w)));
+                }
+                const float2 s2 = __fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3]));
+                const float tot = s2.x + s2.y;
+                if (tot != 0.f) atomicAdd(g2d + (size_t)s_ridx[wid][e] * kG + v, tot);
+            }
+            __syncwarp();
+        };
         const float fpx = (float)px + 0.5f;
         float2 T[PP], gTT[PP];
     #pragma unroll
@@ -323,15 +334,17 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                 g[0] = qc.dx * sgq;                                           // sum gq dx
                 g[2] = qc.dx * g[0];                                          // sum gq dx^2
                 g[3] = qc.dx * g[1];                                          // sum gq dx dy
-                float *dst = g2d + (size_t)si[k] * kG;
-                const float y = warp_sum8(g, lane);
-                float z = g[8];
+                float *row = &s_ring[wid][nfill][0][0];
     #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-                if ((lane & 3) == 0 && y != 0.f) atomicAdd(dst + (lane >> 2), y);
-                if (lane == 0 && z != 0.f) atomicAdd(dst + 8, z);
+                for (int v = 0; v < kG; ++v) row[v * RRS + lane] = g[v];
+                if (lane == 0) s_ridx[wid][nfill] = si[k];
+                if (++nfill == RNE) {
+                    ring_flush(RNE);
+                    nfill = 0;
+                }
             }
         }
+        if (nfill > 0) ring_flush(nfill);
         // after a timed-out wait, every copy issued and not yet waited for must
         // land (bounded waits) before the buffers are reused or the CTA's shared
         // memory is released
@@ -987,7 +1000,8 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     e = cudaMemsetAsync(g2d, 0, wq ? ((g2d_bytes + 15) & ~(size_t)15) + 16 : g2d_bytes, s);
     if (e != cudaSuccess) return cuda_status(e);
     const uint32_t n_rec = (uint32_t)((long long)n_views * n);
-    const size_t bwd_smem = 2 * (size_t)opt->batch * (sizeof(Record) + sizeof(uint32_t));
+    const int bwd_batch = opt->batch < kBwdBatchMax ? opt->batch : kBwdBatchMax;
+    const size_t bwd_smem = 2 * (size_t)bwd_batch * (sizeof(Record) + sizeof(uint32_t));
 #define HM_BBWD(TW, TH, PP, SLOT)                                                                                \
     do {                                                                                                         \
         auto kern = wq ? (dL_dT ? blend_bwd_kernel<TW, TH, PP, true, true> : blend_bwd_kernel<TW, TH, PP, true, false>) \
@@ -1000,7 +1014,7 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
         }                                                                                                        \
         kern<<<grid, TW * TH / (2 * PP), bwd_smem, s>>>(                                                          \
             vt, rec, n_rec, pair_vals, tile_ranges, mesh_rgb, bg[0], bg[1], bg[2], out_T, last_idx, dL_drgb,    \
-            dL_dT, opt->batch, g2d, d_status, wq);                                                               \
+            dL_dT, bwd_batch, g2d, d_status, wq);                                                               \
     } while (0)
     if (vt.total_tiles > 0) {
         if (opt->tile_w == 16) HM_BBWD(16, 16, 2, 0);

@@ -18,7 +18,9 @@
 // Per evaluated (pixel, Gaussian): q = -log2(e)/2 * d^2 from the record's
 // pre-scaled conic, one ex2, the alpha/T updates and three FMAs of colour;
 // updates are masked (alpha 0 for a pixel that does not blend) instead of
-// branched.
+// branched, for entries outside the 3-sigma ellipse too.  A pixel's only
+// loop-carried stop state is its cut depth: the mesh depth, or -inf once it
+// lies outside the image or its T would fall below 1e-4.
 #include "blend_common.cuh"
 #include "hm_host.h"
 #include "tma.cuh"
@@ -113,7 +115,12 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         }
         const float fpx = (float)px + 0.5f;
         const float2 fpy = make_float2((float)pya + 0.5f, (float)pyb + 0.5f);
-        bool done_a = !in_a, done_b = !in_b;
+        // a pixel takes entries with depth < Dm (the list is depth-ordered, so
+        // the first entry at or behind the mesh ends it); outside the image,
+        // or once its T would fall below 1e-4, Dm is -inf
+        if (!in_a) Dm_a = -INFINITY;
+        if (!in_b) Dm_b = -INFINITY;
+        bool stopped = false;                            // this thread has left the list
         float2 T = make_float2(1.f, 1.f);
         float2 C0 = make_float2(0.f, 0.f), C1 = C0, C2 = C0;
         uint32_t cnt_a = 0, cnt_b = 0, last_a = 0, last_b = 0, n_eval = 0, n_exam = 0;
@@ -124,9 +131,9 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
             // CTA timed out): leave the list.  The barrier also ends every
             // thread's reads of round r - 1, whose buffer round r + 1 refills.
             if constexpr (PERSIST) {
-                if (__syncthreads_count(done_a && done_b) == NTH || s_timeout) break;
+                if (__syncthreads_count(stopped) == NTH || s_timeout) break;
             } else {
-                if (__syncthreads_count(done_a && done_b) == NTH) break;
+                if (__syncthreads_count(stopped) == NTH) break;
             }
             if (r + 1 < n_rounds) {
                 issue(r + 1);
@@ -140,34 +147,35 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                     all_landed = false;
                     s_timeout = 1;
                 }
-                done_a = done_b = true;
+                stopped = true;
             }
             consumed = r + 1;
-            if (done_a && done_b) continue;
+            if (stopped) continue;
             const uint32_t b0 = begin + r * (uint32_t)batch;
             const int nb = (int)min((uint32_t)batch, end - b0);
             const Record *sr = s_rec[buf];
             for (int k = 0; k < nb; ++k) {
-                const float4 A = sr[k].a;
                 const float4 B = sr[k].b;
                 // at or behind the mesh: this and every later Gaussian is cut
-                done_a |= B.z >= Dm_a;
-                done_b |= B.z >= Dm_b;
-                if (done_a && done_b) break;
+                const bool la = B.z < Dm_a, lb = B.z < Dm_b;
+                if (!(la || lb)) {
+                    stopped = true;
+                    break;
+                }
+                const float4 A = sr[k].a;
                 float dx;
                 float2 dy;
                 const float2 q = eval_q2(A, B, fpx, fpy, dx, dy);
-                bool ea = !done_a && q.x >= kQ3, eb = !done_b && q.y >= kQ3;   // inside the 3-sigma ellipse
-                if (COUNT) n_exam += !done_a + !done_b, n_eval += ea + eb;
-                if (!(ea || eb)) continue;
+                bool ea = la && q.x >= kQ3, eb = lb && q.y >= kQ3;   // inside the 3-sigma ellipse
+                if (COUNT) n_exam += la + lb, n_eval += ea + eb;
                 float2 G, araw;
                 const float2 al = eval_alpha2(B.y, q, G, araw);
                 ea = ea && al.x >= kAlphaMin;
                 eb = eb && al.y >= kAlphaMin;
                 const float2 Tn = __ffma2_rn(make_float2(-T.x, -T.y), al, T);   // T (1 - alpha)
                 // stop before a Gaussian that would take T below 1e-4
-                if (ea && Tn.x < kTMin) { done_a = true; ea = false; }
-                if (eb && Tn.y < kTMin) { done_b = true; eb = false; }
+                if (ea && Tn.x < kTMin) { Dm_a = -INFINITY; ea = false; }
+                if (eb && Tn.y < kTMin) { Dm_b = -INFINITY; eb = false; }
                 const float2 ae = make_float2(ea ? al.x : 0.f, eb ? al.y : 0.f);
                 const float2 w = __fmul2_rn(ae, T);
                 const float4 c = sr[k].c;
