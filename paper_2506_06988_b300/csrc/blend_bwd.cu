@@ -50,7 +50,7 @@ constexpr int kPbwdWin = 4;
 // it sums them over its lanes (3 x 9 columns: one flush pass of 27 lanes)
 constexpr int kRingEntries = 3;
 // the replay's staging batch: at most this many list entries per round, so
-// that the double-buffered records and the partials ring leave room for 12
+// that the double-buffered records and the partials ring leave room for 14
 // CTAs per SM
 constexpr int kBwdBatchMax = 64;
 
@@ -65,7 +65,7 @@ constexpr int kBwdBatchMax = 64;
 // (zeroed before the launch) until none is left; a claim is one atomic on a
 // counter that only grows, so no CTA waits on another.
 template <int TW, int TH, int PP, bool PERSIST, bool HAS_DT>
-__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 12)
+__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 14)
 blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                  const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2,
@@ -256,19 +256,20 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                 if (!__any_sync(0xffffffffu, act)) continue;
                 const float4 A = sr[k].a, Bs = sr[k].b, c = sr[k].c;
                 const QCol qc = eval_qcol(A, fpx);
-                float2 dy[PP], G[PP], araw[PP], al[PP];
+                float2 dy[PP], ae[PP];
                 bool actp[PP];
                 act = false;
     #pragma unroll
                 for (int p = 0; p < PP; ++p) {
                     const float2 q = eval_qrows(A, Bs, qc, fpy[p], dy[p]);
-                    ea[p] = ea[p] && q.x >= kQ3;
-                    eb[p] = eb[p] && q.y >= kQ3;
-                    al[p] = eval_alpha2(Bs.y, q, G[p], araw[p]);
-                    ea[p] = ea[p] && al[p].x >= kAlphaMin;        // the forward blended it
-                    eb[p] = eb[p] && al[p].y >= kAlphaMin;
+                    float2 G, araw;
+                    const float2 al = eval_alpha2(Bs.y, q, G, araw);
+                    // the forward blended it: alpha, else 0
+                    const bool ba = ea[p] && q.x >= kQ3 && al.x >= kAlphaMin;
+                    const bool bb = eb[p] && q.y >= kQ3 && al.y >= kAlphaMin;
+                    ae[p] = make_float2(ba ? al.x : 0.f, bb ? al.y : 0.f);
                     // pair p of some lane blended it (warp-uniform)
-                    actp[p] = __any_sync(0xffffffffu, ea[p] || eb[p]);
+                    actp[p] = __any_sync(0xffffffffu, ba || bb);
                     act = act || actp[p];
                 }
                 // entries the forward blended at none of the warp's pixels need no
@@ -276,19 +277,19 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                 // lane blended is skipped (its updates would be the identity)
                 if (!act) continue;
                 // per-record sums over the thread's pairs, packed (one horizontal
-                // add per entry): dL/dq / ln 2 and its dy, dy^2 moments, dL/do,
-                // dL/dcolour
-                float2 s_gq = make_float2(0.f, 0.f), s_dy = s_gq, s_dy2 = s_gq, s_op = s_gq, s_c0 = s_gq,
-                       s_c1 = s_gq, s_c2 = s_gq;
+                // add per entry): dL/dq / ln 2 and its dy, dy^2 moments, dL/dcolour
+                float2 s_gq = make_float2(0.f, 0.f), s_dy = s_gq, s_dy2 = s_gq, s_c0 = s_gq, s_c1 = s_gq,
+                       s_c2 = s_gq;
     #pragma unroll
                 for (int p = 0; p < PP; ++p) {
                     if (!actp[p]) continue;
-                    const float2 ae = make_float2(ea[p] ? al[p].x : 0.f, eb[p] ? al[p].y : 0.f);
-                    const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-ae.x, -ae.y));
+                    // a pixel that did not blend the entry has alpha 0: 1 / (1 - 0) is
+                    // exactly 1, so its T_i, B and sums pass through unchanged
+                    const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-ae[p].x, -ae[p].y));
                     const float2 rr = make_float2(rcp_approx(om.x), rcp_approx(om.y));
-                    const float2 Ti = make_float2(ea[p] ? T[p].x * rr.x : T[p].x, eb[p] ? T[p].y * rr.y : T[p].y);
+                    const float2 Ti = __fmul2_rn(T[p], rr);
                     // colour: dI/dc = alpha T_i
-                    const float2 wgt = __fmul2_rn(ae, Ti);
+                    const float2 wgt = __fmul2_rn(ae[p], Ti);
                     s_c0 = __ffma2_rn(wgt, gI0[p], s_c0);
                     s_c1 = __ffma2_rn(wgt, gI1[p], s_c1);
                     s_c2 = __ffma2_rn(wgt, gI2[p], s_c2);
@@ -301,33 +302,32 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                     sdot = __ffma2_rn(gI2[p], d2, sdot);
                     float2 dLda = __fmul2_rn(Ti, sdot);
                     if constexpr (HAS_DT) dLda = __ffma2_rn(make_float2(-gTT[p].x, -gTT[p].y), rr, dLda);
-                    // through alpha = o 2^q where blended and not clamped at 0.99
-                    const float2 dLa_u = make_float2(ea[p] && araw[p].x < kAlphaMax ? dLda.x : 0.f,
-                                                     eb[p] && araw[p].y < kAlphaMax ? dLda.y : 0.f);
+                    // dL/dq / ln 2 = alpha dL/dalpha where blended and not clamped at
+                    // 0.99 (a clamped alpha is exactly 0.99)
+                    const float2 au = make_float2(ae[p].x < kAlphaMax ? ae[p].x : 0.f,
+                                                  ae[p].y < kAlphaMax ? ae[p].y : 0.f);
                     // the pixel-space moments of dL/dq (the mean and conic
                     // gradients follow per record from them: dq/dmean = -2K conic
                     // (dx, dy), dq/dconic = K (dx^2, 2 dx dy, dy^2)); dx is shared
-                    // by the thread's pixels.  dL/dq = ln 2 alpha dL/dalpha: the
-                    // factor ln 2 is applied once per record in the projection
-                    // backward
-                    const float2 gq = __fmul2_rn(dLa_u, araw[p]);
+                    // by the thread's pixels.  The factor ln 2 is applied once per
+                    // record in the projection backward
+                    const float2 gq = __fmul2_rn(dLda, au);
                     const float2 gqdy = __fmul2_rn(gq, dy[p]);
                     s_gq = __fadd2_rn(s_gq, gq);
                     s_dy = __fadd2_rn(s_dy, gqdy);
                     s_dy2 = __ffma2_rn(gqdy, dy[p], s_dy2);
-                    s_op = __ffma2_rn(dLa_u, G[p], s_op);
                     // colour behind the previous Gaussian (normalised):
                     // alpha c + (1 - alpha) B = B + alpha (c - B); then T_i
-                    B0[p] = __ffma2_rn(ae, d0, B0[p]);
-                    B1[p] = __ffma2_rn(ae, d1, B1[p]);
-                    B2[p] = __ffma2_rn(ae, d2, B2[p]);
+                    B0[p] = __ffma2_rn(ae[p], d0, B0[p]);
+                    B1[p] = __ffma2_rn(ae[p], d1, B1[p]);
+                    B2[p] = __ffma2_rn(ae[p], d2, B2[p]);
                     T[p] = Ti;
                 }
                 float g[kG];
                 const float sgq = s_gq.x + s_gq.y;
                 g[1] = s_dy.x + s_dy.y;
                 g[4] = s_dy2.x + s_dy2.y;
-                g[5] = s_op.x + s_op.y;
+                g[5] = sgq * rcp_approx(Bs.y);                               // dL/do = sum gq / o
                 g[6] = s_c0.x + s_c0.y;
                 g[7] = s_c1.x + s_c1.y;
                 g[8] = s_c2.x + s_c2.y;
