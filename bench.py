@@ -44,15 +44,15 @@ WORKLOAD = ("indoor room 1920x1080 x 8 poses, 300k Gaussians SH3, 50k-triangle r
 #   blended pair backward; an FMA as two, packed FP32x2 ops per pixel):
 #   forward q 7 (dx, a dx^2 and 2b dx shared by the pixel pair), the 3-sigma,
 #   alpha and T-stop compares 3, alpha 2 (o 2^q, min), T' 2, the alpha
-#   select 1, weight 1, colour 6, T 2, mesh cut 1 = 25; backward q 6 (the
-#   column part shared by four pixels), the 3-sigma and alpha compares 2,
-#   alpha 2, the alpha select 1, 1 - alpha 1, T_i 2, weight 1, colour
-#   partials 3, dL/dalpha 11 (c - B, the dot with dL/dI, the T term) and its
-#   select 1, the clamp test 2, dL/dq 2, the moments 3, the per-pair sums
-#   and their accumulation 7, the colour behind 9, the entry's share of the
-#   moment products and of the warp reduction 4 = 58 (+ ex2 and rcp).
+#   select 1, weight 1, colour 6, T 2, mesh cut 1 = 25; backward (no dL/dT)
+#   q 6 (the column part shared by four pixels), the 3-sigma and alpha
+#   compares 2, alpha 2, the blended select 1, 1 - alpha 1, T_i 1, weight
+#   1, colour partials 6, c - B 3, the dot with dL/dI 5, dL/dalpha 1, the
+#   clamp test and select 2, dL/dq 1, gq dy 1, the moment sums 4, the colour
+#   behind 6, the entry's horizontal adds and moment and dL/do products
+#   shared by the lane's four pixels 3 = 46 (+ ex2 and rcp).
 SURVEY_FLOPS = {"blend_forward": 12, "blend_backward": 40}
-SOURCE_FLOPS = {"blend_forward": 25, "blend_backward": 58}
+SOURCE_FLOPS = {"blend_forward": 25, "blend_backward": 46}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp
 # instructions (smsp__inst_executed.sum) of one launch of each blend kernel,
 # from an ncu capture of 3 of the 8 views (profiles/blend_*_kernel_room1080p_3views.md)

@@ -50,7 +50,7 @@ constexpr int kPbwdWin = 4;
 // it sums them over its lanes (3 x 9 columns: one flush pass of 27 lanes)
 constexpr int kRingEntries = 3;
 // the replay's staging batch: at most this many list entries per round, so
-// that the double-buffered records and the partials ring leave room for 14
+// that the double-buffered records and the partials ring leave room for 12
 // CTAs per SM
 constexpr int kBwdBatchMax = 64;
 
@@ -65,7 +65,7 @@ constexpr int kBwdBatchMax = 64;
 // (zeroed before the launch) until none is left; a claim is one atomic on a
 // counter that only grows, so no CTA waits on another.
 template <int TW, int TH, int PP, bool PERSIST, bool HAS_DT>
-__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 14)
+__global__ void __launch_bounds__(TW *TH / (2 * PP), PP == 1 ? 6 : 12)
 blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
                  const float *__restrict__ mesh_rgb, float bg0, float bg1, float bg2,
