@@ -43,9 +43,6 @@ namespace {
 // sum gq dy^2; q = K d^2, (dx, dy) = pixel centre - mean), dL/dopacity and
 // dL/dcolour (r, g, b)
 constexpr int kG = 9;
-// Gaussians per lane that a warp of the projection backward scans for
-// gradients before it works on the ones it found
-constexpr int kPbwdWin = 4;
 // list entries whose per-lane partials a warp of the replay collects before
 // it sums them over its lanes (3 x 9 columns: one flush pass of 27 lanes)
 constexpr int kRingEntries = 3;
@@ -586,12 +583,45 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     }
 }
 
+// The Gaussians with a gradient: those whose record the replay blended in
+// some view (its nine partials are not all zero).  Only a few percent of
+// the records of a 1080p view have tiles, so the chain rule below runs on a
+// list, not on every Gaussian: one thread per Gaussian reads its partials of
+// every view (consecutive Gaussians' records are contiguous in each view:
+// coalesced) and appends (index, mask of the views with a gradient), one
+// atomic per warp.  A Gaussian no view blended has no gradient: nothing is
+// added (this also keeps culled, non-finite parameters out of the chain
+// rule).
+__global__ void __launch_bounds__(256)
+pbwd_scan_kernel(int n, int n_views, const float *__restrict__ g2d, uint2 *__restrict__ list,
+                 unsigned int *__restrict__ count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t vm = 0u;
+    if (i < n) {
+        for (int v = 0; v < n_views; ++v) {
+            const float *gg = g2d + ((size_t)v * n + i) * kG;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < kG; ++q) any |= gg[q] != 0.f;
+            if (any) vm |= 1u << v;
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, vm != 0u);
+    if (bal == 0u) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == __ffs(bal) - 1) base = atomicAdd(count, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+    if (vm != 0u) list[base + __popc(bal & lanemask_lt())] = make_uint2((uint32_t)i, vm);
+}
+
 template <int DEG, bool F16>
 __global__ void __launch_bounds__(128, 4)
 project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
                    const float *__restrict__ scales, const float *__restrict__ quats,
                    const float *__restrict__ opac, const void *__restrict__ sh_raw, Filters flt,
-                   const float *__restrict__ g2d, float *__restrict__ d_means,
+                   const float *__restrict__ g2d, const uint2 *__restrict__ list,
+                   const unsigned int *__restrict__ count, float *__restrict__ d_means,
                    float *__restrict__ d_scales, float *__restrict__ d_quats,
                    float *__restrict__ d_opac, float *__restrict__ d_sh) {
     constexpr int K = (DEG + 1) * (DEG + 1);
@@ -842,62 +872,34 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
     #pragma unroll
             for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[3 * k + c][tl];
     };
-    // the Gaussians of the warp's window with a gradient: index and view mask
-    __shared__ uint32_t s_idx[4][32 * kPbwdWin], s_msk[4][32 * kPbwdWin];
     __syncthreads();
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    // the views whose record of a Gaussian the replay blended (its nine
-    // partials are not all zero).  Only about 3% of the records of a 1080p
-    // view have tiles, so each warp first scans a window of 32 kPbwdWin
-    // Gaussians and lists the ones with a gradient; its lanes then take the
-    // listed Gaussians one each, and each lane walks only its Gaussian's
-    // views with a gradient.  A Gaussian no view blended has no gradient:
-    // nothing is added (this also keeps culled, non-finite parameters out
-    // of the chain rule).
-    const long long win = ((long long)blockIdx.x * 4 + wp) * (32 * kPbwdWin);
-    // (the window's loads of a view are independent: issued together)
-    uint32_t vm[kPbwdWin];
-#pragma unroll
-    for (int r = 0; r < kPbwdWin; ++r) vm[r] = 0u;
-#pragma unroll 2
-    for (int v = 0; v < vt.n_views; ++v) {
-#pragma unroll
-        for (int r = 0; r < kPbwdWin; ++r) {
-            const long long gi = win + r * 32 + lane;
-            if (gi < n) {
-                const float *gg = g2d + ((size_t)v * n + gi) * kG;
-                bool any = false;
-#pragma unroll
-                for (int q = 0; q < kG; ++q) any |= gg[q] != 0.f;
-                if (any) vm[r] |= 1u << v;
-            }
-        }
+    // one listed Gaussian per thread; each walks only its views with a gradient
+    const unsigned cnt = *count;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const uint2 it = list[e];
+        one_gaussian((int)it.x, it.y);
     }
-    int listed = 0;                                   // warp-uniform
-#pragma unroll
-    for (int r = 0; r < kPbwdWin; ++r) {
-        const unsigned bal = __ballot_sync(0xffffffffu, vm[r] != 0u);
-        if (vm[r] != 0u) {
-            const int pos = listed + __popc(bal & ((1u << lane) - 1u));
-            s_idx[wp][pos] = (uint32_t)(win + r * 32 + lane);
-            s_msk[wp][pos] = vm[r];
-        }
-        listed += __popc(bal);
-    }
-    __syncwarp();
-    for (int e = lane; e < listed; e += 32) one_gaussian((int)s_idx[wp][e], s_msk[wp][e]);
 }
 
 template <int DEG>
 cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const float *scales,
                         const float *quats, const float *opac, const void *sh, bool f16, Filters flt,
-                        const float *g2d, float *dm, float *ds, float *dq, float *dop, float *dsh,
-                        cudaStream_t s) {
-    dim3 grid((unsigned)(((long long)n + 128 * kPbwdWin - 1) / (128 * kPbwdWin)));
+                        const float *g2d, uint2 *list, unsigned int *count, float *dm, float *ds,
+                        float *dq, float *dop, float *dsh, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    pbwd_scan_kernel<<<(unsigned)(((long long)n + 255) / 256), 256, 0, s>>>(n, vt.n_views, g2d, list, count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // a resident grid: the list holds a few percent of the Gaussians
+    long long g = ((long long)n + 127) / 128;
+    if (g > 148 * 4) g = 148 * 4;
+    const dim3 grid((unsigned)g);
     if (f16)
-        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, dm, ds, dq, dop, dsh);
+        project_bwd_kernel<DEG, true><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, list,
+                                                          count, dm, ds, dq, dop, dsh);
     else
-        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, dm, ds, dq, dop, dsh);
+        project_bwd_kernel<DEG, false><<<grid, 128, 0, s>>>(vt, n, means, scales, quats, opac, sh, flt, g2d, list,
+                                                           count, dm, ds, dq, dop, dsh);
     return cudaGetLastError();
 }
 
@@ -934,9 +936,36 @@ int resident_ctas(K kernel, int threads, int smem, int slot) {
 
 using namespace hm;
 
+// Workspace layout: the replay's partials (kG floats per record), 16 bytes of
+// counters (the persistent launch's tile counter, the length of the list of
+// Gaussians with a gradient), that list (index, view mask per Gaussian), and
+// 256 spare bytes.
+namespace {
+struct BwdWs {
+    float *g2d;
+    unsigned int *tiles, *count;
+    uint2 *list;
+    size_t g2d_bytes, ctr_off;
+};
+size_t bwd_ws_layout(int32_t n_views, int32_t n, void *ws, BwdWs *w) {
+    const size_t g2d_bytes = sizeof(float) * kG * (size_t)n_views * (size_t)n;
+    const size_t ctr = (g2d_bytes + 15) & ~(size_t)15, lst = ctr + 16;
+    if (w) {
+        unsigned char *b = reinterpret_cast<unsigned char *>(ws);
+        w->g2d = reinterpret_cast<float *>(b);
+        w->tiles = reinterpret_cast<unsigned int *>(b + ctr);
+        w->count = w->tiles + 1;
+        w->list = reinterpret_cast<uint2 *>(b + lst);
+        w->g2d_bytes = g2d_bytes;
+        w->ctr_off = ctr;
+    }
+    return lst + sizeof(uint2) * (size_t)n + 256;
+}
+}  // namespace
+
 extern "C" size_t hm_blend_backward_workspace_size(int32_t n_views, int32_t n) {
     if (n_views < 1 || n < 0) return 0;
-    return sizeof(float) * kG * (size_t)n_views * (size_t)n + 256;
+    return bwd_ws_layout(n_views, n, nullptr, nullptr);
 }
 
 extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n,
@@ -988,16 +1017,14 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (n == 0) return HM_OK;
-    float *g2d = reinterpret_cast<float *>(ws);
+    BwdWs w;
+    bwd_ws_layout(n_views, n, ws, &w);
+    float *g2d = w.g2d;
     const Record *rec = reinterpret_cast<const Record *>(records);
     if (stages & HM_BWD_BLEND) {
-    const size_t g2d_bytes = sizeof(float) * kG * (size_t)n_views * n;
-    // the persistent launch's tile counter sits after the partials (the
-    // workspace's 256 spare bytes)
-    unsigned int *wq = opt->persistent ? reinterpret_cast<unsigned int *>(
-                                             reinterpret_cast<unsigned char *>(ws) + ((g2d_bytes + 15) & ~(size_t)15))
-                                       : nullptr;
-    e = cudaMemsetAsync(g2d, 0, wq ? ((g2d_bytes + 15) & ~(size_t)15) + 16 : g2d_bytes, s);
+    // the partials and, for the persistent launch, its tile counter start at 0
+    unsigned int *wq = opt->persistent ? w.tiles : nullptr;
+    e = cudaMemsetAsync(g2d, 0, wq ? w.ctr_off + sizeof(unsigned int) : w.g2d_bytes, s);
     if (e != cudaSuccess) return cuda_status(e);
     const uint32_t n_rec = (uint32_t)((long long)n_views * n);
     const int bwd_batch = opt->batch < kBwdBatchMax ? opt->batch : kBwdBatchMax;
@@ -1027,10 +1054,10 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     if (!(stages & HM_BWD_PROJECT)) return HM_OK;
     const bool f16 = sh_format == HM_SH_F16;
     switch (sh_degree) {
-        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
-        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 0: e = launch_pbwd<0>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, w.list, w.count, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 1: e = launch_pbwd<1>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, w.list, w.count, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        case 2: e = launch_pbwd<2>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, w.list, w.count, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
+        default: e = launch_pbwd<3>(vt, n, means, scales, quats, opacity, sh, f16, flt, g2d, w.list, w.count, d_means, d_scales, d_quats, d_opacity, d_sh, s); break;
     }
     return cuda_status(e);
 }
