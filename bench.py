@@ -69,8 +69,8 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURE = {
     # stage: (warp instructions, DRAM bytes, units, unit kind, pixels, source hash)
-    "blend_forward": (202_430_464, 219_355_648, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "38b741871cc74f09"),
-    "blend_backward": (282_105_216, 122_254_080, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "d8eac24d15b655e1"),
+    "blend_forward": (182_410_274, 219_010_304, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "9e000290bf9ba236"),
+    "blend_backward": (256_249_321, 122_703_360, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "7163cc1eefeabb22"),
 }
 
 
