@@ -295,8 +295,8 @@ hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, int32_t n, c
  * without ws/ws_bytes: the scratch is a library-owned static device array of
  * HM_BWD_NOALLOC_BYTES bytes (16 MiB), which every GPU that loads the library
  * holds until the process exits.  Problems needing more
- * (hm_blend_backward_workspace_size: 36 bytes per record and 8 per
- * Gaussian, so n above 381,294 for one view) are rejected with
+ * (hm_blend_backward_workspace_size: 44 bytes per record, so n above
+ * 381,294 for one view) are rejected with
  * HM_ERR_INVALID_ARG and a message.  The array's device address belongs to the current context: a
  * call outside a stream capture looks it up again (with the caller's device
  * current), a call under capture uses the address the last uncaptured call

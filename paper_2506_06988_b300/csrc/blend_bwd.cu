@@ -21,12 +21,13 @@
 //  * texture_bwd: dL/dtexel += T * w_bilinear * dL/dI_h on pixels with a
 //    triangle (the mesh colour enters I_h weighted by T), summed per screen
 //    tile in shared memory (fixed point) before the global reductions.
-//  * project_bwd: one thread per Gaussian turns each view's moments into
-//    dL/dmean2d and dL/dconic with the view's conic and chains them
-//    through the conic inverse, Sigma' = V V^T, V = (J W)(R S), the clamped
-//    Jacobian, the projection of the mean, the quaternion normalisation and
-//    the SH colour (including its dependence on the mean through the view
-//    direction), summing over cameras without atomics.
+//  * project_bwd: one thread per (Gaussian, view) pair with a gradient
+//    turns the view's moments into dL/dmean2d and dL/dconic with the view's
+//    conic and chains them through the conic inverse, Sigma' = V V^T,
+//    V = (J W)(R S), the clamped Jacobian, the projection of the mean, the
+//    quaternion normalisation and the SH colour (including its dependence
+//    on the mean through the view direction); the views of a Gaussian add
+//    their (linear) contributions with atomics.
 #include <mutex>
 
 #include "blend_common.cuh"
@@ -583,36 +584,34 @@ texture_bwd_kernel(ViewTable vt, const float *__restrict__ mesh_depth, const flo
     }
 }
 
-// The Gaussians with a gradient: those whose record the replay blended in
-// some view (its nine partials are not all zero).  Only a few percent of
-// the records of a 1080p view have tiles, so the chain rule below runs on a
-// list, not on every Gaussian: one thread per Gaussian reads its partials of
-// every view (consecutive Gaussians' records are contiguous in each view:
-// coalesced) and appends (index, mask of the views with a gradient), one
-// atomic per warp.  A Gaussian no view blended has no gradient: nothing is
-// added (this also keeps culled, non-finite parameters out of the chain
-// rule).
+// The (Gaussian, view) pairs with a gradient: the records whose nine
+// partials the replay left not all zero.  Only a few percent of the records
+// of a 1080p view have tiles, so the chain rule below runs on a list of
+// those pairs, not on every Gaussian: one thread per record reads its
+// partials (consecutive records contiguous: coalesced) and appends
+// (Gaussian, view), one atomic per warp.  A Gaussian no view blended has no
+// gradient: nothing is added (this also keeps culled, non-finite parameters
+// out of the chain rule).
 __global__ void __launch_bounds__(256)
-pbwd_scan_kernel(int n, int n_views, const float *__restrict__ g2d, uint2 *__restrict__ list,
+pbwd_scan_kernel(int n, long long n_rec, const float *__restrict__ g2d, uint2 *__restrict__ list,
                  unsigned int *__restrict__ count) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t vm = 0u;
-    if (i < n) {
-        for (int v = 0; v < n_views; ++v) {
-            const float *gg = g2d + ((size_t)v * n + i) * kG;
-            bool any = false;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    if (r < n_rec) {
+        const float *gg = g2d + r * kG;
 #pragma unroll
-            for (int q = 0; q < kG; ++q) any |= gg[q] != 0.f;
-            if (any) vm |= 1u << v;
-        }
+        for (int q = 0; q < kG; ++q) any |= gg[q] != 0.f;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, vm != 0u);
+    const unsigned bal = __ballot_sync(0xffffffffu, any);
     if (bal == 0u) return;
     const int lane = threadIdx.x & 31;
     unsigned base = 0;
     if (lane == __ffs(bal) - 1) base = atomicAdd(count, (unsigned)__popc(bal));
     base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-    if (vm != 0u) list[base + __popc(bal & lanemask_lt())] = make_uint2((uint32_t)i, vm);
+    if (any) {
+        const int v = (int)(r / n);
+        list[base + __popc(bal & lanemask_lt())] = make_uint2((uint32_t)(r - (long long)v * n), (uint32_t)v);
+    }
 }
 
 template <int DEG, bool F16>
@@ -858,26 +857,39 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
         gqz = (gqz - dot * qz) * qinv;
     #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            d_means[3 * i + k] += gmean[k];
-            d_scales[3 * i + k] += gs[k];
+            atomicAdd(d_means + 3 * i + k, gmean[k]);
+            atomicAdd(d_scales + 3 * i + k, gs[k]);
         }
-        d_quats[4 * i] += gqw;
-        d_quats[4 * i + 1] += gqx;
-        d_quats[4 * i + 2] += gqy;
-        d_quats[4 * i + 3] += gqz;
-        d_opac[i] += gop;
+        // several views of a Gaussian run in parallel: atomic additions
+        // (four-float vector atomics where the rows are 16-byte aligned)
+        if (((uintptr_t)d_quats & 15) == 0) {
+            atomicAdd(reinterpret_cast<float4 *>(d_quats) + i, make_float4(gqw, gqx, gqy, gqz));
+        } else {
+            atomicAdd(d_quats + 4 * i, gqw);
+            atomicAdd(d_quats + 4 * i + 1, gqx);
+            atomicAdd(d_quats + 4 * i + 2, gqy);
+            atomicAdd(d_quats + 4 * i + 3, gqz);
+        }
+        atomicAdd(d_opac + i, gop);
         float *ds = d_sh + (size_t)i * K * 3;
+        if constexpr ((K * 3) % 4 == 0) {
+            if (((uintptr_t)ds & 15) == 0) {
     #pragma unroll
-        for (int k = 0; k < K; ++k)
+                for (int j = 0; j < K * 3; j += 4)
+                    atomicAdd(reinterpret_cast<float4 *>(ds + j),
+                              make_float4(gsh[j][tl], gsh[j + 1][tl], gsh[j + 2][tl], gsh[j + 3][tl]));
+                return;
+            }
+        }
     #pragma unroll
-            for (int c = 0; c < 3; ++c) ds[3 * k + c] += gsh[3 * k + c][tl];
+        for (int j = 0; j < K * 3; ++j) atomicAdd(ds + j, gsh[j][tl]);
     };
     __syncthreads();
-    // one listed Gaussian per thread; each walks only its views with a gradient
+    // one listed (Gaussian, view) pair per thread
     const unsigned cnt = *count;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
         const uint2 it = list[e];
-        one_gaussian((int)it.x, it.y);
+        one_gaussian((int)it.x, 1u << it.y);
     }
 }
 
@@ -888,10 +900,11 @@ cudaError_t launch_pbwd(const ViewTable &vt, int n, const float *means, const fl
                         float *dq, float *dop, float *dsh, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    pbwd_scan_kernel<<<(unsigned)(((long long)n + 255) / 256), 256, 0, s>>>(n, vt.n_views, g2d, list, count);
+    const long long n_rec = (long long)vt.n_views * n;
+    pbwd_scan_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(n, n_rec, g2d, list, count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // a resident grid: the list holds a few percent of the Gaussians
-    long long g = ((long long)n + 127) / 128;
+    // a resident grid: the list holds a few percent of the records
+    long long g = ((long long)vt.n_views * n + 127) / 128;
     if (g > 148 * 4) g = 148 * 4;
     const dim3 grid((unsigned)g);
     if (f16)
@@ -937,15 +950,15 @@ int resident_ctas(K kernel, int threads, int smem, int slot) {
 using namespace hm;
 
 // Workspace layout: the replay's partials (kG floats per record), 16 bytes of
-// counters (the persistent launch's tile counter, the length of the list of
-// Gaussians with a gradient), that list (index, view mask per Gaussian), and
-// 256 spare bytes.
+// counters (the persistent launch's tile counter, the length of the pair
+// list), the list of (Gaussian, view) pairs with a gradient, and 256 spare
+// bytes.  The replay clears the partials and the tile counter.
 namespace {
 struct BwdWs {
     float *g2d;
     unsigned int *tiles, *count;
     uint2 *list;
-    size_t g2d_bytes, ctr_off;
+    size_t clear_bytes;
 };
 size_t bwd_ws_layout(int32_t n_views, int32_t n, void *ws, BwdWs *w) {
     const size_t g2d_bytes = sizeof(float) * kG * (size_t)n_views * (size_t)n;
@@ -956,10 +969,9 @@ size_t bwd_ws_layout(int32_t n_views, int32_t n, void *ws, BwdWs *w) {
         w->tiles = reinterpret_cast<unsigned int *>(b + ctr);
         w->count = w->tiles + 1;
         w->list = reinterpret_cast<uint2 *>(b + lst);
-        w->g2d_bytes = g2d_bytes;
-        w->ctr_off = ctr;
+        w->clear_bytes = ctr + sizeof(unsigned int);
     }
-    return lst + sizeof(uint2) * (size_t)n + 256;
+    return lst + sizeof(uint2) * (size_t)n_views * (size_t)n + 256;
 }
 }  // namespace
 
@@ -1022,9 +1034,9 @@ extern "C" hm_status hm_blend_backward(const hm_camera *cams, int32_t n_views, i
     float *g2d = w.g2d;
     const Record *rec = reinterpret_cast<const Record *>(records);
     if (stages & HM_BWD_BLEND) {
-    // the partials and, for the persistent launch, its tile counter start at 0
+    // the partials and the persistent launch's tile counter start at 0
     unsigned int *wq = opt->persistent ? w.tiles : nullptr;
-    e = cudaMemsetAsync(g2d, 0, wq ? w.ctr_off + sizeof(unsigned int) : w.g2d_bytes, s);
+    e = cudaMemsetAsync(g2d, 0, wq ? w.clear_bytes : sizeof(float) * kG * (size_t)n_views * n, s);
     if (e != cudaSuccess) return cuda_status(e);
     const uint32_t n_rec = (uint32_t)((long long)n_views * n);
     const int bwd_batch = opt->batch < kBwdBatchMax ? opt->batch : kBwdBatchMax;
