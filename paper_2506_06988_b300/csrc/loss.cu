@@ -458,6 +458,82 @@ l1_loss_kernel(ViewTable vt, const float *__restrict__ x_all, const TT *__restri
     if (threadIdx.x < 3) partials[3 * (long long)blockIdx.x + threadIdx.x] = s_red[threadIdx.x][0];
 }
 
+// The same pointwise pass four pixels at a time (16-byte loads and stores of
+// each plane, one 4-byte load of 8-bit codes) when every camera's pixel count
+// is a multiple of 4 and the buffers are 16-byte aligned: the same per-element
+// arithmetic, so the gradients are those of l1_loss_kernel bit for bit.
+template <typename TT>
+__global__ void __launch_bounds__(kNT)
+l1_loss4_kernel(ViewTable vt, const float *__restrict__ x_all, const TT *__restrict__ y_all,
+                const float *__restrict__ m_all, const float *__restrict__ T_all, const float *__restrict__ md_all,
+                float k_mask, float l1_scale, float mesh_grad_scale, float *__restrict__ dL_drgb,
+                float *__restrict__ dL_dmesh, double *__restrict__ partials) {
+    __shared__ double s_red[3][kNT / 32];
+    __shared__ float s_lut[256];
+    Target<TT> tgt{y_all, s_lut};
+    tgt.init();
+    float l1 = 0.f, lt = 0.f;
+    const long long nq = vt.total_pixels / 4;
+    for (long long qd = (long long)blockIdx.x * kNT + threadIdx.x; qd < nq; qd += (long long)gridDim.x * kNT) {
+        const long long gp = 4 * qd;
+        const int v = view_of_pixel(vt, gp);
+        const ViewDev &V = vt.v[v];
+        const long long lp = gp - V.pix_off, npx = (long long)V.W * V.H;
+        float mt[4] = {0.f, 0.f, 0.f, 0.f};
+        bool hit[4] = {false, false, false, false};
+        if (m_all) {
+            const float4 md = *reinterpret_cast<const float4 *>(md_all + gp);
+            const float4 T4 = *reinterpret_cast<const float4 *>(T_all + gp);
+            const float mdv[4] = {md.x, md.y, md.z, md.w}, Tv[4] = {T4.x, T4.y, T4.z, T4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                hit[u] = mdv[u] < INFINITY;
+                if (hit[u]) mt[u] = 1.f / (1.f + expf(-k_mask * (Tv[u] - 0.5f)));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long o = 3 * V.pix_off + c * npx + lp;
+            const float4 x4 = *reinterpret_cast<const float4 *>(x_all + o);
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            float yv[4];
+            if constexpr (sizeof(TT) == 1) {
+                const uint32_t w = *reinterpret_cast<const uint32_t *>(y_all + o);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) yv[u] = s_lut[(w >> (8 * u)) & 255u];
+            } else {
+                const float4 y4 = *reinterpret_cast<const float4 *>(y_all + o);
+                yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
+            }
+            float g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                l1 += fabsf(xv[u] - yv[u]);
+                g[u] = xv[u] > yv[u] ? l1_scale : (xv[u] < yv[u] ? -l1_scale : 0.f);
+            }
+            *reinterpret_cast<float4 *>(dL_drgb + o) = make_float4(g[0], g[1], g[2], g[3]);
+            if (m_all) {
+                const float4 m4 = *reinterpret_cast<const float4 *>(m_all + o);
+                const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+                float gm[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    gm[u] = 0.f;
+                    if (hit[u]) {
+                        const float d = yv[u] - mv[u];
+                        lt = fmaf(mt[u] * d, d, lt);
+                        gm[u] = mesh_grad_scale * mt[u] * -d;
+                    }
+                }
+                *reinterpret_cast<float4 *>(dL_dmesh + o) = make_float4(gm[0], gm[1], gm[2], gm[3]);
+            }
+        }
+    }
+    double sums[3] = {(double)l1, 0.0, (double)lt};
+    block_sum3(sums, s_red);
+    if (threadIdx.x < 3) partials[3 * (long long)blockIdx.x + threadIdx.x] = s_red[threadIdx.x][0];
+}
+
 // first level of the SSIM path's reduction (one partial per tile and channel,
 // tens of thousands): CTA b sums partials [b kChunk, (b + 1) kChunk) into
 // out[3 b .. 3 b + 2], so the FP64 additions spread over many SMs; the
@@ -617,9 +693,20 @@ hm_status hybrid_loss(const hm_camera *cams, int32_t n_views, const float *out_r
         long long g1l = blocks < 8LL * sms ? blocks : 8LL * sms;
         if (g1l > 3LL * vt.total_tiles) g1l = 3LL * vt.total_tiles;   // the partials buffer holds 3 per tile
         const int g1 = (int)g1l;
-        l1_loss_kernel<<<g1, kNT, 0, s>>>(vt, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T, mesh_depth, p->k,
-                                          (float)(1.0 / n_el), (float)(2.0 * p->lambda_t / n_el), dL_drgb,
-                                          dL_dmesh, partials);
+        // four pixels a thread where every plane starts on a 16-byte boundary
+        bool quad = (((uintptr_t)out_rgb | (uintptr_t)dL_drgb) & 15) == 0 &&
+                    ((uintptr_t)target & (sizeof(TT) == 1 ? 3 : 15)) == 0;
+        if (mesh)
+            quad = quad && (((uintptr_t)mesh_rgb | (uintptr_t)out_T | (uintptr_t)mesh_depth | (uintptr_t)dL_dmesh) & 15) == 0;
+        for (int v = 0; v < vt.n_views; ++v) quad = quad && ((long long)vt.v[v].W * vt.v[v].H) % 4 == 0;
+        if (quad)
+            l1_loss4_kernel<<<g1, kNT, 0, s>>>(vt, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T, mesh_depth, p->k,
+                                               (float)(1.0 / n_el), (float)(2.0 * p->lambda_t / n_el), dL_drgb,
+                                               dL_dmesh, partials);
+        else
+            l1_loss_kernel<<<g1, kNT, 0, s>>>(vt, out_rgb, target, mesh ? mesh_rgb : nullptr, out_T, mesh_depth, p->k,
+                                              (float)(1.0 / n_el), (float)(2.0 * p->lambda_t / n_el), dL_drgb,
+                                              dL_dmesh, partials);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
         loss_final_kernel<<<1, kNT, 0, s>>>(partials, g1, 1.0 / n_el, 0.0, p->lambda_t, loss_out);
         return cuda_status(cudaGetLastError());

@@ -126,7 +126,7 @@ def test_decode_u8_is_exact():
         assert np.array_equal(dst[:n].cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("lam_ssim, lam_t", [(0.0, 0.0), (0.2, 0.1)])
+@pytest.mark.parametrize("lam_ssim, lam_t", [(0.0, 0.0), (0.0, 0.1), (0.2, 0.1)])
 def test_u8_target_loss_equals_the_decoded_target_loss(lam_ssim, lam_t):
     """hm_hybrid_loss_u8 reads each 8-bit code as code / 255 (correctly
     rounded): its loss terms and both gradients equal hm_hybrid_loss on the

@@ -133,10 +133,11 @@ def test_joint_loss_texel_gradient_scatter():
     assert np.all(np.abs(got - want) <= 1e-4 * np.abs(want) + 1e-6 * np.abs(want).max())
 
 
-@pytest.mark.parametrize("sizes", [((37, 23),), ((16, 16), (5, 7), (70, 33))])
+@pytest.mark.parametrize("sizes", [((37, 23),), ((16, 16), (5, 7), (70, 33)), ((64, 48), (32, 20))])
 def test_hybrid_loss_without_ssim_term(sizes):
     # lambda_ssim = 0 takes the pointwise pass: L1, L_t and L as the oracle's,
-    # dL/dI_h = sign(x - y) / N exactly, mean SSIM reported as 0
+    # dL/dI_h = sign(x - y) / N exactly, mean SSIM reported as 0 (cameras
+    # whose pixel counts are all multiples of 4 take the four-pixel path)
     rng = np.random.default_rng(20 + len(sizes))
     cams_np, views = _case(rng, sizes)
     cams = lib.cameras(cams_np)
