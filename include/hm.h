@@ -380,6 +380,21 @@ hm_status hm_hybrid_loss_u8(const hm_camera *cams, int32_t n_views, const float 
                             float *dL_drgb, float *dL_dmesh, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* hm_checked_status -- the index checks of the checked build.  The library
+ * built with HM_CHECKED (libhm_checked.so; same entry points) checks every
+ * index a kernel reads from a device buffer -- pair and item list entries,
+ * bucket and tile-range bounds, tile ids, slots, the backward's stop
+ * positions and gradient list -- against the bound it must respect before
+ * using it; a failed check skips the access and is recorded instead of
+ * faulting the GPU.  The paper has no counterpart: it is a debugging aid
+ * for corrupt inputs.
+ *  *bits: HM_DEV_BAD_INDEX if a check failed since the last reset, else 0;
+ *  reset != 0 clears the record.  Synchronises the device.
+ *  Errors: HM_ERR_INVALID_ARG (null bits; or the default library, which has
+ *  no checks), HM_ERR_CUDA. */
+hm_status hm_checked_status(int32_t *bits, int32_t reset);
+
+/* ------------------------------------------------------------------------ */
 /* hm_adam_update -- one Adam step (Kingma and Ba, 2015) on n float32 values
  * in place, for optimised buffers such as the texture map in the texture-only
  * optimisation that initialises it from the images (Sec. 3.3):

@@ -1,10 +1,13 @@
 """Build libhm.so (the CUDA library behind include/hm.h) in-tree for sm_103a.
 
-    python -m paper_2506_06988_b300.build [--force]
+    python -m paper_2506_06988_b300.build [--force] [--checked]
 
 Each .cu file is compiled separately (parallel, cached by mtime) with
 ``nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked
-into ``paper_2506_06988_b300/libhm.so``.
+into ``paper_2506_06988_b300/libhm.so``.  ``--checked`` builds the same
+sources with ``-DHM_CHECKED`` into ``libhm_checked.so``: every index a kernel
+reads from a device buffer is checked before use and a failed check is
+reported by ``hm_checked_status`` instead of faulting.
 """
 from __future__ import annotations
 
@@ -19,6 +22,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhm.so")
+OBJ_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libhm_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -32,11 +37,11 @@ def _deps():
         glob.glob(os.path.join(CSRC, "*.h"))
 
 
-def _compile(src: str, force: bool, verbose: bool) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+def _compile(src: str, force: bool, verbose: bool, checked: bool = False) -> str:
+    obj = os.path.join(OBJ_CHECKED if checked else OBJ, os.path.basename(src) + ".o")
     newest = max(os.path.getmtime(p) for p in [src] + _deps())
     if force or not os.path.exists(obj) or os.path.getmtime(obj) < newest:
-        cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [NVCC] + ARCH + FLAGS + (["-DHM_CHECKED"] if checked else []) + ["-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -47,18 +52,19 @@ def _compile(src: str, force: bool, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    obj_dir, lib = (OBJ_CHECKED, LIB_CHECKED) if checked else (OBJ, LIB)
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, force, verbose), srcs))
+        objs = list(ex.map(lambda s: _compile(s, force, verbose, checked), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        tmp = LIB + ".tmp"
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        tmp = lib + ".tmp"
         subprocess.check_call([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

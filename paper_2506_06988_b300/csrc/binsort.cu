@@ -209,7 +209,8 @@ bin_count_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const floa
         if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
             const ViewDev &V = vt.v[S.v[j]];
             // a reduction (no return value): hot tiles' adds queue in L2
-            atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
+            if (hm_check(tx >= 0 && tx < V.tiles_x && ty >= 0 && ty < V.tiles_y))
+                atomicAdd(&tile_cnt[V.tile_off + ty * V.tiles_x + tx], 1u);
         }
     }
 }
@@ -243,8 +244,10 @@ bin_emit_kernel(ViewTable vt, int n, const Record *__restrict__ rec, const float
             int j, tx, ty;
             if (bin_candidate(S, vt, tmax, ellipse, c, j, tx, ty)) {
                 const ViewDev &V = vt.v[S.v[j]];
-                keys[atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u)] =
-                    ((unsigned long long)__float_as_uint(S.depth[j]) << 32) | S.idx[j];
+                if (!hm_check(tx >= 0 && tx < V.tiles_x && ty >= 0 && ty < V.tiles_y)) continue;
+                const uint32_t slot = atomicAdd(&cursor[V.tile_off + ty * V.tiles_x + tx], 1u);
+                if (hm_check(slot < (unsigned long long)*n_sort))
+                    keys[slot] = ((unsigned long long)__float_as_uint(S.depth[j]) << 32) | S.idx[j];
             }
         }
     }
@@ -356,7 +359,9 @@ seg_sort_small_kernel(uint32_t n_tiles, const uint32_t *__restrict__ tile_off,
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t gt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gt < n_tiles; gt += nw) {
-        const uint32_t off = tile_off[gt], cnt = tile_cnt[gt];
+        uint32_t off = tile_off[gt], cnt = tile_cnt[gt];
+        // (checked build: a bucket beyond the pairs is left empty)
+        if (!hm_check((unsigned long long)off + cnt <= (unsigned long long)*n_sort)) off = cnt = 0;
         if (lane == 0) {
             ranges[2 * (size_t)gt] = off;
             ranges[2 * (size_t)gt + 1] = off + cnt;
@@ -869,3 +874,9 @@ extern "C" hm_status hm_bin_sort(const hm_camera *cams, int32_t n_views, int32_t
     }
     return cuda_status(cudaGetLastError());
 }
+
+#ifdef HM_CHECKED
+namespace hm {
+HM_CHECKED_READER(bin)
+}  // namespace hm
+#endif

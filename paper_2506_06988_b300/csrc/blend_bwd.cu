@@ -146,7 +146,9 @@ blend_bwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         __syncthreads();
         if (my_hi > 0) atomicMax(&s_hi, my_hi);
         __syncthreads();
-        const uint32_t hi_all = s_hi;
+        uint32_t hi_all = s_hi;
+        // (checked build: stop positions must lie in the tile's list)
+        if (!hm_check(hi_all == 0 || (begin <= hi_all && hi_all <= ranges[2 * gt + 1]))) hi_all = begin;
         // rounds walk the list back to front: round r covers [lo_r, hi_r) with
         // hi_r = hi_all - r batch, lo_r = max(begin, hi_r - batch)
         const uint32_t n_rounds = hi_all > begin ? (hi_all - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
@@ -889,7 +891,7 @@ project_bwd_kernel(ViewTable vt, int n, const float *__restrict__ means,
     const unsigned cnt = *count;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
         const uint2 it = list[e];
-        one_gaussian((int)it.x, 1u << it.y);
+        if (hm_check(it.x < (uint32_t)n && it.y < (uint32_t)vt.n_views)) one_gaussian((int)it.x, 1u << it.y);
     }
 }
 
@@ -1142,3 +1144,9 @@ extern "C" hm_status hm_blend_backward_noalloc(
                              d_means, d_scales, d_quats, d_opacity, d_sh, d_tex, d_status, ws,
                              HM_BWD_NOALLOC_BYTES, stream);
 }
+
+#ifdef HM_CHECKED
+namespace hm {
+HM_CHECKED_READER(blend_bwd)
+}  // namespace hm
+#endif

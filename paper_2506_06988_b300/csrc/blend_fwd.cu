@@ -70,7 +70,8 @@ blend_fwd_kernel(ViewTable vt, const Record *__restrict__ rec, uint32_t n_rec,
         const bool in_a = px < V.W && pya < V.H, in_b = px < V.W && pyb < V.H;
         const long long npx = (long long)V.W * V.H;
         const long long lpa = (long long)pya * V.W + px, lpb = (long long)pyb * V.W + px;
-        const uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
+        uint32_t begin = ranges[2 * gt], end = ranges[2 * gt + 1];
+        if (!hm_check(begin <= end)) begin = end = 0;   // (checked build: an inverted range is empty)
         const uint32_t n_rounds = end > begin ? (end - begin + (uint32_t)batch - 1) / (uint32_t)batch : 0u;
         // wait parity of round r (the grid launch starts every barrier at phase 0)
         auto parity = [&](uint32_t r) -> uint32_t {
@@ -328,3 +329,9 @@ extern "C" hm_status hm_blend_forward(const hm_camera *cams, int32_t n_views, in
 #undef HM_BLEND
     return cuda_status(cudaGetLastError());
 }
+
+#ifdef HM_CHECKED
+namespace hm {
+HM_CHECKED_READER(blend_fwd)
+}  // namespace hm
+#endif

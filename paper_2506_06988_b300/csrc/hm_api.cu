@@ -100,3 +100,22 @@ extern "C" int64_t hm_total_tiles(const hm_camera *cams, int32_t n_views, const 
     if (!build_view_table(cams, n_views, opt, &vt)) return -1;
     return vt.total_tiles;
 }
+
+extern "C" hm_status hm_checked_status(int32_t *bits, int32_t reset) {
+    if (!bits) return fail(HM_ERR_INVALID_ARG, "null pointer");
+#ifdef HM_CHECKED
+    const int r[4] = {hm_checked_read_mesh(reset != 0), hm_checked_read_bin(reset != 0),
+                      hm_checked_read_blend_fwd(reset != 0), hm_checked_read_blend_bwd(reset != 0)};
+    int v = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (r[k] < 0) return fail(HM_ERR_CUDA, "reading the checked-status words failed");
+        v |= r[k];
+    }
+    *bits = v ? HM_DEV_BAD_INDEX : 0;
+    return HM_OK;
+#else
+    (void)reset;
+    *bits = 0;
+    return fail(HM_ERR_INVALID_ARG, "not the checked build (libhm_checked.so)");
+#endif
+}

@@ -15,6 +15,14 @@ hm_status cuda_status(cudaError_t e);
 // Validate cameras and options and fill the by-value view table.
 bool build_view_table(const hm_camera *cams, int n_views, const hm_options *opt, ViewTable *vt);
 bool tile_shape_ok(int tw, int th);
+#ifdef HM_CHECKED
+// checked build: the checked-status words of the translation units with
+// index checks (-1 if the read failed); `reset` clears them
+int hm_checked_read_mesh(bool reset);
+int hm_checked_read_bin(bool reset);
+int hm_checked_read_blend_fwd(bool reset);
+int hm_checked_read_blend_bwd(bool reset);
+#endif
 
 // bump allocator over a caller workspace (256-byte aligned sub-buffers)
 struct WsCarver {

@@ -129,6 +129,39 @@ __device__ __forceinline__ bool wait_published(const unsigned long long *slot, u
     }
 }
 
+// ---------------------------------------------------------------------------
+// Checked build (HM_CHECKED defined: libhm_checked.so).  Every index a
+// kernel reads from a device buffer -- list entries, bucket and range
+// bounds, tile ids, slots -- is checked against the bound it must respect
+// before it is used; a failed check sets a bit in this translation unit's
+// checked-status word (read and cleared by hm_checked_status) and the access
+// is skipped, so a corrupt list is reported instead of faulting.  In the
+// default build hm_check is the constant true and the checks compile away.
+// ---------------------------------------------------------------------------
+#ifdef HM_CHECKED
+static __device__ int g_hm_checked_bad;
+__device__ __forceinline__ bool hm_check(bool ok) {
+    if (!ok) atomicOr(&g_hm_checked_bad, 1);
+    return ok;
+}
+// defines the host reader of this translation unit's word
+#define HM_CHECKED_READER(name)                                                     \
+    int hm_checked_read_##name(bool reset) {                                       \
+        int v = 0;                                                                  \
+        if (cudaMemcpyFromSymbol(&v, g_hm_checked_bad, sizeof(int)) != cudaSuccess) \
+            return -1;                                                              \
+        if (reset) {                                                                \
+            const int z = 0;                                                        \
+            if (cudaMemcpyToSymbol(g_hm_checked_bad, &z, sizeof(int)) != cudaSuccess)  \
+                return -1;                                                          \
+        }                                                                           \
+        return v;                                                                   \
+    }
+#else
+__device__ __forceinline__ constexpr bool hm_check(bool) { return true; }
+#define HM_CHECKED_READER(name)
+#endif
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -176,11 +176,13 @@ mesh_emit_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup, cons
             uint32_t pos[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (b0 + q < nt)
-                    pos[q] = atomicAdd(&cursor[g0 + ((b0 + q) / nx) * V.tiles_x + (b0 + q) % nx], 1u);
+                if (b0 + q < nt) {
+                    const uint32_t tile = g0 + ((b0 + q) / nx) * V.tiles_x + (b0 + q) % nx;
+                    pos[q] = hm_check(tile < (uint32_t)vt.total_tiles) ? atomicAdd(&cursor[tile], 1u) : ~0u;
+                }
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (b0 + q < nt) items[pos[q]] = (uint32_t)it;
+                if (b0 + q < nt && hm_check(pos[q] < (unsigned long long)*n_items)) items[pos[q]] = (uint32_t)it;
         }
     }
 }
@@ -345,7 +347,10 @@ mesh_tile_kernel(ViewTable vt, int nf, const FaceSetup *__restrict__ setup,
         const int nb = (int)min((uint32_t)NT, fc - r0);
         __syncthreads();                             // the previous round's faces are consumed
         if (t < nb) {
-            const uint32_t vf = items[f0 + r0 + t];
+            uint32_t vf = items[f0 + r0 + t];
+            // (checked build: an item beyond the faces stages face 0)
+            if (!hm_check(f0 + r0 + t < (unsigned long long)*n_items && vf < (uint32_t)vt.n_views * (uint32_t)nf))
+                vf = 0;
             const FaceSetup g = setup[vf];
             const int b = g.flip ? 2 : 1, c = g.flip ? 1 : 2;   // oriented order 0, b, c
             const int ax[3] = {g.x[0], g.x[b], g.x[c]}, ay[3] = {g.y[0], g.y[b], g.y[c]};
@@ -628,3 +633,9 @@ extern "C" hm_status hm_rasterize_mesh(const hm_camera *cams, int32_t n_views, c
 #undef HM_RASTER
     return cuda_status(cudaGetLastError());
 }
+
+#ifdef HM_CHECKED
+namespace hm {
+HM_CHECKED_READER(mesh)
+}  // namespace hm
+#endif

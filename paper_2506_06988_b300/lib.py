@@ -14,6 +14,7 @@ from ctypes import POINTER, c_float, c_int32, c_int64, c_size_t, c_void_p
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhm.so")
+LIB_CHECKED_PATH = os.path.join(_HERE, "libhm_checked.so")
 
 HM_OK = 0
 HM_ERR_INVALID_ARG = 1
@@ -44,7 +45,7 @@ EXPORTS = [
     "hm_decode_u8",
     "hm_default_prune_params", "hm_mesh_prune_workspace_size", "hm_mesh_prune",
     "hm_adam_update", "hm_adam_update_dev", "hm_adam_advance", "hm_activate", "hm_activate_backward",
-    "hm_selftest_bounded_waits",
+    "hm_selftest_bounded_waits", "hm_checked_status",
 ]
 
 
@@ -115,6 +116,7 @@ _SIGS = {
     "hm_adam_advance": (c_int32, [c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "hm_activate": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hm_selftest_bounded_waits": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hm_checked_status": (c_int32, [POINTER(c_int32), c_int32]),
     "hm_activate_backward": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p]),
     "hm_mesh_prune_workspace_size": (c_size_t, [_CAM_P, c_int32, c_int32, c_int32]),
@@ -136,19 +138,56 @@ _SIGS = {
 }
 
 
+def _open(path):
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
 def load():
     """Load libhm.so (raises HmError if it has not been built)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise HmError(f"{LIB_PATH} not built: run `python -m paper_2506_06988_b300.build`")
-        lib = ctypes.CDLL(LIB_PATH)
-        for name, (res, args) in _SIGS.items():
-            f = getattr(lib, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = lib
+        _lib = _open(LIB_PATH)
     return _lib
+
+
+_checked = None
+
+
+def load_checked():
+    """The index-checked library libhm_checked.so (same entry points; every
+    index a kernel reads from a device buffer is checked and a failure is
+    reported by hm_checked_status instead of faulting).  ``use(lib)``
+    routes this module's functions to it."""
+    global _checked
+    if _checked is None:
+        if not os.path.exists(LIB_CHECKED_PATH):
+            raise HmError(f"{LIB_CHECKED_PATH} not built: run `python -m paper_2506_06988_b300.build --checked`")
+        _checked = _open(LIB_CHECKED_PATH)
+    return _checked
+
+
+def use(handle):
+    """Route the entry points of this module to ``handle`` (``load()`` or
+    ``load_checked()``); returns the handle in use before."""
+    global _lib
+    before = load()
+    _lib = handle
+    return before
+
+
+def hm_checked_status(reset: bool = True) -> int:
+    """HM_DEV_BAD_INDEX if a check of the checked library failed since the
+    last reset, else 0 (HmError from the default library, which has none)."""
+    v = c_int32(0)
+    check(load().hm_checked_status(ctypes.byref(v), int(bool(reset))), "hm_checked_status")
+    return int(v.value)
 
 
 def check_device_status(st: int) -> int:

@@ -145,3 +145,19 @@ def test_loss_defaults_and_invalid_args():
     assert st == lib.HM_ERR_INVALID_ARG
     st = lib.hm_hybrid_loss(cams, 16, 16, None, None, None, p, 16, 16, None, 16, 8, 0)
     assert st == lib.HM_ERR_WORKSPACE
+
+
+def test_checked_library_exports_the_same_entry_points():
+    # libhm_checked.so: the same sources built with HM_CHECKED (index checks
+    # that report instead of faulting); the default library has no checks
+    build.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_CHECKED_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (hm_[a-z0-9_]+)", out))
+    assert not [d for d in _declared() if d not in exported]
+    chk = lib.load_checked()
+    assert chk is not lib.load()
+    v = ctypes.c_int32(7)
+    assert lib.load().hm_checked_status(ctypes.byref(v), 0) == lib.HM_ERR_INVALID_ARG
+    assert "not the checked build" in lib.last_error() and v.value == 0
+    assert chk.hm_checked_status(None, 0) == lib.HM_ERR_INVALID_ARG
