@@ -4,8 +4,9 @@ activations and their chain rule by torch autograd, the optimiser by
 torch.optim.Adam (FP32), the render / loss / gradients by eager library
 calls.  After one and three steps the parameters agree within FP32 rounding
 except where a gradient is within rounding of zero (Adam's step is then
-+-lr either way): at most 0.5 % of the values, each off by at most 2 lr per
-step.  Also: the activation kernels against FP64 formulas, and a step whose
++-lr either way, and the gradients' global atomic sums come in another order
+in the graph than in the eager reference): at most 1 % of the values, each
+off by at most 2 lr per step.  Also: the activation kernels against FP64 formulas, and a step whose
 pair capacity overflows leaves every parameter untouched and is redone by
 step(check=True)."""
 import numpy as np
