@@ -69,8 +69,8 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURE = {
     # stage: (warp instructions, DRAM bytes, units, unit kind, pixels, source hash)
-    "blend_forward": (182_410_274, 219_010_304, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "9e000290bf9ba236"),
-    "blend_backward": (256_249_321, 122_703_360, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "7163cc1eefeabb22"),
+    "blend_forward": (182_410_274, 219_468_288, 113_755_470, "evaluated_pairs", 3 * 1920 * 1080, "2be5ebbb112a845f"),
+    "blend_backward": (256_249_321, 122_555_136, 110_624_405, "blended_pairs", 3 * 1920 * 1080, "e614eeda23b39bd3"),
 }
 
 
