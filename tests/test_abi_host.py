@@ -107,7 +107,15 @@ def test_workspace_sizes_grow_with_the_problem(hm):
     r1 = lib.hm_rasterize_mesh_workspace_size(cams, 100, 200, 5000, o)
     r2 = lib.hm_rasterize_mesh_workspace_size(cams, 100, 200, 50_000, o)
     assert 0 < r1 < r2
-    assert lib.hm_blend_backward_workspace_size(2, 1000) >= 2 * 1000 * 9 * 4
+    # the replay's nine partials per record, then the list of (Gaussian, view)
+    # pairs with a gradient (8 bytes per record)
+    assert lib.hm_blend_backward_workspace_size(2, 1000) >= 2 * 1000 * (9 * 4 + 8)
+    assert lib.hm_blend_backward_workspace_size(2, 2000) - lib.hm_blend_backward_workspace_size(2, 1000) == \
+        2 * 1000 * (9 * 4 + 8)
+    # the no-allocation entry point's static scratch holds exactly the problems whose workspace fits
+    n_max = 381_294
+    assert lib.hm_blend_backward_workspace_size(1, n_max) <= lib.HM_BWD_NOALLOC_BYTES
+    assert lib.hm_blend_backward_workspace_size(1, n_max + 1) > lib.HM_BWD_NOALLOC_BYTES
 
 
 def test_product_package_does_not_import_the_oracle():
