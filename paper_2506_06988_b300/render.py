@@ -488,13 +488,15 @@ class GraphStep:
     evaluates the joint loss (hm_hybrid_loss with ``loss_params``) and
     back-propagates its
     gradient; ``loss_terms`` is then the device float64 [L1, mean SSIM,
-    L_t, L] of the last replay.
+    L_t, L] of the last replay.  With ``loss_host`` (a pinned float64 [4]
+    host tensor) the replay also copies the loss terms there, as the graph's
+    last operation: no separate read-back after each replay.
     """
 
     def __init__(self, renderer: Renderer, params, mesh: Optional[MeshInput] = None,
                  dL_drgb: Optional[torch.Tensor] = None, dL_dT: Optional[torch.Tensor] = None,
                  grads=None, tex_grad: bool = False, target: Optional[torch.Tensor] = None,
-                 loss_params=None):
+                 loss_params=None, loss_host: Optional[torch.Tensor] = None):
         self.r = renderer
         self.params = tuple(params)
         self.mesh = mesh
@@ -509,6 +511,13 @@ class GraphStep:
                 raise ValueError("target: uint8 or float32")
         self.loss_params = loss_params if loss_params is not None else lib.loss_params()
         self.loss_terms = None
+        if loss_host is not None:
+            if target is None:
+                raise ValueError("loss_host needs a target (the loss is evaluated in the graph)")
+            if loss_host.device.type != "cpu" or not loss_host.is_pinned() or loss_host.dtype != torch.float64 \
+                    or loss_host.numel() != 4:
+                raise ValueError("loss_host: a pinned float64 host tensor of 4 elements")
+        self.loss_host = loss_host
         self.tex_grad = bool(tex_grad and renderer.has_mesh)
         self.grads = grads
         if (self.dI is not None or target is not None) and self.grads is None:
@@ -526,6 +535,8 @@ class GraphStep:
         if dI is not None:
             r.backward(*self.params, dI, self.dT, mesh=self.mesh, tex_grad=self.tex_grad,
                        out=self.grads, zero=True, overlap=True, dL_dmesh=dM)
+        if self.loss_host is not None:
+            self.loss_host.copy_(self.loss_terms, non_blocking=True)
 
     def capture(self):
         r = self.r

@@ -151,6 +151,32 @@ def test_u8_target_loss_equals_the_decoded_target_loss(lam_ssim, lam_t):
         assert torch.equal(dM_u, dM_f)
 
 
+def test_graph_step_copies_its_loss_to_pinned_host_memory():
+    """GraphStep(loss_host=...): the replay's last node writes the loss terms
+    to the pinned host buffer -- equal to the device terms -- and a second
+    replay against another target updates it."""
+    from paper_2506_06988_b300 import lib
+    s = _room(seed=35, res=((160, 120), (96, 64)))
+    r, P, mesh = gpu_render(s)
+    r.render(*_params(P), mesh)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(8)
+    target = torch.randint(0, 256, (3 * r.npix,), device="cuda", generator=gen, dtype=torch.int32).to(torch.uint8)
+    host = torch.zeros(4, dtype=torch.float64).pin_memory()
+    lp = lib.loss_params(lambda_ssim=0.0, lambda_t=0.1)
+    gs = GraphStep(r, _params(P), mesh, target=target, loss_params=lp, tex_grad=True, loss_host=host)
+    gs.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(host, gs.loss_terms.cpu()) and float(host[3]) > 0.0
+    first = host.clone()
+    target.copy_(255 - target)                    # in place: the graph reads the new target
+    gs.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(host, gs.loss_terms.cpu()) and not torch.equal(host, first)
+    with pytest.raises(ValueError):
+        GraphStep(r, _params(P), mesh, target=target, loss_params=lp, loss_host=torch.zeros(4, dtype=torch.float64))
+
+
 def test_graph_step_reads_current_parameters():
     s = _room(seed=32)
     r, P, mesh = gpu_render(s)
