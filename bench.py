@@ -37,7 +37,7 @@ UNIT = "frames/s"
 WORKLOAD = ("indoor room 1920x1080 x 8 poses, 300k Gaussians SH3, 50k-triangle room mesh "
             "(10% pruned), 2048^2 RGB8 atlas; forward + backward")
 # Work of the blend kernels per (pixel, Gaussian) pair, two counts:
-# * the survey's count of the method's arithmetic per evaluated pair (inside
+# * the nominal count of the method's arithmetic per evaluated pair (inside
 #   the 3-sigma ellipse): ~12 FP32 operations + 1 ex2 forward, ~40 + 1 ex2
 #   backward, counted as FLOPs against the FP32 peak (an FMA as two);
 # * the count read off the kernel sources (per evaluated pair forward, per
@@ -51,7 +51,7 @@ WORKLOAD = ("indoor room 1920x1080 x 8 poses, 300k Gaussians SH3, 50k-triangle r
 #   clamp test and select 2, dL/dq 1, gq dy 1, the moment sums 4, the colour
 #   behind 6, the entry's horizontal adds and moment and dL/do products
 #   shared by the lane's four pixels 3 = 46 (+ ex2 and rcp).
-SURVEY_FLOPS = {"blend_forward": 12, "blend_backward": 40}
+METHOD_FLOPS = {"blend_forward": 12, "blend_backward": 40}
 SOURCE_FLOPS = {"blend_forward": 25, "blend_backward": 46}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp
 # instructions (smsp__inst_executed.sum) of one launch of each blend kernel,
@@ -458,11 +458,11 @@ def run_ours(args):
     K = (g.sh_degree + 1) ** 2
     # per single-kernel stage: (kernel, bound, algorithmic units, work per unit)
     kern = {
-        "blend_forward": ("blend_fwd_kernel" + tsuf, "alu", n_eval, SURVEY_FLOPS["blend_forward"],
-                          "evaluated (pixel, Gaussian) pairs (inside 3 sigma), survey count"),
+        "blend_forward": ("blend_fwd_kernel" + tsuf, "alu", n_eval, METHOD_FLOPS["blend_forward"],
+                          "evaluated (pixel, Gaussian) pairs (inside 3 sigma), nominal count of the method"),
         "blend_backward": ("blend_bwd_kernel" + tsuf[:-1] + (",2>" if tuple(tile) == (16, 16) else ",1>"), "alu",
-                           n_eval, SURVEY_FLOPS["blend_backward"],
-                           "evaluated (pixel, Gaussian) pairs (inside 3 sigma), survey count"),
+                           n_eval, METHOD_FLOPS["blend_backward"],
+                           "evaluated (pixel, Gaussian) pairs (inside 3 sigma), nominal count of the method"),
         "project": ("project_kernel<3,false>", "hbm", N, 12 + 12 + 16 + 4 + 12 * K + V * 48, "Gaussians (params read + V records written, bytes)"),
         "project_backward": ("project_bwd_kernel<3,false>", "hbm", N, 2 * (12 + 12 + 16 + 4 + 12 * K) + 12 + 12 + 16 + 4 + 12 * K + V * 36,
                              "Gaussians (params read, grads read+written, V partial rows read, bytes)"),
