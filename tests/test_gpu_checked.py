@@ -61,6 +61,7 @@ def test_checked_library_passes_valid_frames_and_matches():
         assert torch.allclose(got[k], ref[k], rtol=1e-5, atol=tol), k
 
 
+@pytest.mark.plants_bad_index
 def test_checked_library_reports_a_stop_position_beyond_the_list():
     r, PM, mesh, dI = _frame(seed=22)
     before = lib.use(lib.load_checked())

@@ -33,6 +33,7 @@ def test_bounded_waits_time_out_and_the_context_stays_usable():
     compare_blend(view_outputs(r, 0), oracle_view(s, 0))
 
 
+@pytest.mark.plants_bad_index
 def test_out_of_range_record_index_is_reported_not_returned():
     """A pair list holding a record index past the records (possible only
     after an earlier failure left the list invalid) is caught by the blend
