@@ -411,3 +411,73 @@ def test_config4_full_size_sampled_pixels_chunked():
         compare_mesh(gv, m, pix=pix)
         st = compare_blend(gv, oracle_view(s, v, pix=pix), pix=pix)
         print(v, st)
+
+
+def _tile_of_pixels(r, v, tw=16, th=16):
+    """Global tile id of every pixel of camera v (tiles row-major per camera,
+    cameras in order)."""
+    off = sum(((w + tw - 1) // tw) * ((h + th - 1) // th) for w, h in r.sizes[:v])
+    w, h = r.sizes[v]
+    ys, xs = torch.meshgrid(torch.arange(h, device="cuda"), torch.arange(w, device="cuda"), indexing="ij")
+    return (off + (ys // th) * ((w + tw - 1) // tw) + xs // tw).reshape(-1)
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_config1_full_size_every_pixel_properties(overlap):
+    """Every pixel and every list entry of the bench workload (8 x 1920x1080,
+    300k Gaussians, 50k-face room), eager with the mesh-depth tile cull and
+    in the bench's overlapped launch (binning beside the mesh pass, no cull),
+    checked by what Eq. 2 with the Sec. 3.4 mesh cut fixes at any size:
+    each tile's list is in depth order; a pixel's stop position lies in its
+    tile's list, at least its blended count past the list's start (0 for a
+    pixel that blended nothing); the last Gaussian it blended lies in front
+    of its mesh depth; T stays in [1e-4, 1]; and the image minus T times the
+    mesh colour -- the Gaussians' share -- lies between 0 and (1 - T) times
+    the largest colour of any record."""
+    s = scenes.config1_scene()
+    r, P, mesh = gpu_render(s, tile=(16, 16))
+    if overlap:
+        r.render(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], mesh, overlap=True)
+        torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    n_pairs = int(r.n_pairs.item())
+    assert n_pairs > 1_000_000
+    rec = r.records_view()
+    vals = r.pair_vals[:n_pairs].long()
+    z = rec[vals, 6]
+    rng = r.ranges.view(-1, 2).long()
+    assert rng.shape[0] == r.ntiles
+    assert bool((rng[:, 0] <= rng[:, 1]).all()) and int(rng[:, 1].max()) <= n_pairs
+    # depth order inside every list: entries i, i + 1 of one tile's range
+    ne = rng[rng[:, 1] > rng[:, 0]]
+    mark = torch.zeros(n_pairs + 1, dtype=torch.int64, device="cuda")
+    mark.index_add_(0, ne[:, 0], torch.ones(len(ne), dtype=torch.int64, device="cuda"))
+    mark.index_add_(0, ne[:, 1], -torch.ones(len(ne), dtype=torch.int64, device="cuda"))
+    inside = torch.cumsum(mark, 0)[:n_pairs] > 0
+    is_begin = torch.zeros(n_pairs, dtype=torch.bool, device="cuda")
+    is_begin[ne[:, 0]] = True
+    same = inside[:-1] & inside[1:] & ~is_begin[1:]
+    assert int(same.sum()) > n_pairs // 2
+    assert bool((z[1:] >= z[:-1])[same].all())
+    cmax = float(rec[vals, 8:11].max())
+    blended = 0
+    for v in range(r.V):
+        a, b = int(r.pix_off[v]), int(r.pix_off[v + 1])
+        gt = _tile_of_pixels(r, v)
+        begin, end = rng[gt, 0], rng[gt, 1]
+        T = r.T[a:b]
+        nc = r.n_contrib[a:b].long()
+        li = r.last_idx[a:b].long()
+        assert bool(((T >= 1e-4) & (T <= 1)).all()), v
+        assert bool(((nc == 0) == (li == 0)).all()), v
+        hit = nc > 0
+        blended += int(hit.sum())
+        assert bool((li[hit] - begin[hit] >= nc[hit]).all()), v
+        assert bool((li[hit] <= end[hit]).all()), v
+        # the hybrid cut: every blended Gaussian is nearer than the mesh
+        assert bool((z[li[hit] - 1] < r.mesh_depth[a:b][hit]).all()), v
+        img = r.rgb[3 * a:3 * b].view(3, -1)
+        share = img - T[None] * r.mesh_rgb[3 * a:3 * b].view(3, -1)
+        assert float(share.min()) >= -1e-5, v
+        assert bool((share <= (1 - T)[None] * cmax + 1e-5).all()), v
+    assert blended > 0.2 * r.npix
