@@ -217,3 +217,34 @@ def test_texel_gradients_keep_relative_accuracy_across_1e6_of_range():
     assert (err <= 1e-3 * np.abs(want[nz]) + floor).all(), float((err / np.abs(want[nz])).max())
     assert (np.abs(want[nz]) < 1e-3 * sabs.max()).mean() > 0.05       # many texels far below the maximum
     assert not got[~nz].any()
+
+
+def test_config1_full_size_colour_weights_telescope():
+    """The blend replay over every pixel of the 8-view 1080p workload, pinned
+    by an identity of Eq. 2: with dL/dI = (1, 0, 0) at every pixel and no
+    dL/dT, each Gaussian's red-colour partial is the sum of its weights
+    alpha_i T_i over the pixels that blended it, and those weights telescope
+    per pixel to 1 - T_final (T_{i+1} = T_i (1 - alpha_i)).  So the partials
+    of all records sum to sum_px (1 - T_px), while the green and blue
+    partials are exactly 0.  The replay rebuilds every T_i from T_final by
+    division, back to front, so a wrong stop position, a skipped or doubled
+    entry or a wrong (1 - alpha) breaks the sum.  The partials are read from
+    the backward workspace, whose first n_views * n * 9 floats hold them per
+    record (dL/dcolour in columns 6-8)."""
+    s = scenes.config1_scene()
+    r, P, mesh = gpu_render(s, tile=(16, 16))
+    dI = torch.zeros(3 * r.npix, device="cuda")       # planar per camera: [view][3][pixels]
+    for v in range(r.V):
+        a, b = int(r.pix_off[v]), int(r.pix_off[v + 1])
+        dI[3 * a:3 * a + (b - a)] = 1.0
+    r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, None,
+               mesh=mesh, stages=lib.HM_BWD_BLEND)
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    M = r.V * r.n
+    part = r.bwd_ws[: 4 * 9 * M].view(torch.float32).view(M, 9)
+    want = float((1.0 - r.T.double()).sum())
+    got = float(part[:, 6].double().sum())
+    assert want > 0.02 * r.npix
+    assert abs(got - want) <= 1e-4 * want, (got, want)
+    assert not bool(part[:, 7:9].any())
