@@ -220,7 +220,8 @@ def test_texel_gradients_keep_relative_accuracy_across_1e6_of_range():
 
 
 def test_config1_full_size_colour_weights_telescope():
-    """The blend replay over every pixel of the 8-view 1080p workload, pinned
+    """The blend replay and the texel gradients over every pixel of the
+    8-view 1080p workload, pinned
     by an identity of Eq. 2: with dL/dI = (1, 0, 0) at every pixel and no
     dL/dT, each Gaussian's red-colour partial is the sum of its weights
     alpha_i T_i over the pixels that blended it, and those weights telescope
@@ -237,8 +238,8 @@ def test_config1_full_size_colour_weights_telescope():
     for v in range(r.V):
         a, b = int(r.pix_off[v]), int(r.pix_off[v + 1])
         dI[3 * a:3 * a + (b - a)] = 1.0
-    r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, None,
-               mesh=mesh, stages=lib.HM_BWD_BLEND)
+    g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, None,
+                   mesh=mesh, tex_grad=True, stages=lib.HM_BWD_BLEND | lib.HM_BWD_TEXTURE)
     torch.cuda.synchronize()
     assert r.status()[0] == 0
     M = r.V * r.n
@@ -248,3 +249,12 @@ def test_config1_full_size_colour_weights_telescope():
     assert want > 0.02 * r.npix
     assert abs(got - want) <= 1e-4 * want, (got, want)
     assert not bool(part[:, 7:9].any())
+    # the texels: I_h = ... + T I_m, and I_m is a bilinear mix whose four
+    # weights sum to 1, so the red texel gradients sum to sum T over the
+    # pixels the mesh covers; green and blue receive exactly 0
+    dtex = g["texture"].reshape(-1, 3)
+    want_t = float(r.T.double()[r.tri_id >= 0].sum())
+    got_t = float(dtex[:, 0].double().sum())
+    assert want_t > 0.5 * r.npix
+    assert abs(got_t - want_t) <= 1e-5 * want_t, (got_t, want_t)
+    assert not bool(dtex[:, 1:].any())
