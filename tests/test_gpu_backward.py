@@ -239,7 +239,8 @@ def test_config1_full_size_colour_weights_telescope():
         a, b = int(r.pix_off[v]), int(r.pix_off[v + 1])
         dI[3 * a:3 * a + (b - a)] = 1.0
     g = r.backward(P["means"], P["scales"], P["quats"], P["opacity"], P["sh"], dI, None,
-                   mesh=mesh, tex_grad=True, stages=lib.HM_BWD_BLEND | lib.HM_BWD_TEXTURE)
+                   mesh=mesh, tex_grad=True,
+                   stages=lib.HM_BWD_BLEND | lib.HM_BWD_TEXTURE | lib.HM_BWD_PROJECT)
     torch.cuda.synchronize()
     assert r.status()[0] == 0
     M = r.V * r.n
@@ -258,3 +259,14 @@ def test_config1_full_size_colour_weights_telescope():
     assert want_t > 0.5 * r.npix
     assert abs(got_t - want_t) <= 1e-5 * want_t, (got_t, want_t)
     assert not bool(dtex[:, 1:].any())
+    # the projection backward: the red DC coefficient of a Gaussian gets
+    # C0 = 1 / (2 sqrt(pi)) times the red partials of its records whose
+    # colour max(0, 0.5 + SH) is not clamped (a clamped colour is exactly 0),
+    # summed over the views -- a (Gaussian, view) pair the pair list missed
+    # breaks the sum
+    rec = r.records_view()
+    live = rec[:, 8] > 0
+    want_sh = 0.28209479177387814 * float(part[live, 6].double().sum())
+    got_sh = float(g["sh"][:, 0, 0].double().sum())
+    assert abs(got_sh - want_sh) <= 1e-5 * abs(want_sh) + 1e-6, (got_sh, want_sh)
+    assert not bool(g["sh"][:, 0, 1:].any())
